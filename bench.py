@@ -1,0 +1,339 @@
+"""Benchmark: elements/s of the Newton-Schur tangent assembly on GB300.
+
+One step = one vms_assemble_newton_schur call over the whole mesh: gather, quadrature-point
+geometry and fields, FP64 residual, tangent blocks, Schur condensation of the bubble unknowns,
+scatter-add into the CSR system and the Dirichlet rows/columns. The CSR pattern is built once per
+mesh, outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank assembles its own copy of the workload (independent problems, no
+collective on the data path); `value` sums the elements over ranks and divides by the slowest
+rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elements/s Newton-Schur tangent assembly"
+UNIT = "elements/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# FP64 peak of the GB300: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz (maximum SM
+# clock) = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s FP64 figure); FP32: 152 x 128 x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# Executed FP64 flops per element (FMA = 2, add/mul = 1) of each kernel as implemented, counted
+# from the source per quadrature point and checked against ncu instruction counts (27-point rule).
+FP64_FLOPS_PER_ELEM = {
+    "residual": 14_800,          # modal field evaluation, cofactor form, monomial test sums
+    "tangent_fp64": 140_000,     # per-point geometry, 64 node-pair blocks, condensation
+    "tangent_mixed": 1_000,      # FP64 part of the mixed tangent kernel: K_ff^-1, r_e
+}
+
+WORKLOADS = {
+    # the 32^3 jittered lid-driven cavity at Re 400, random state (mixed precision by default)
+    "cavity32_re400_mixed": dict(n=32, re=400.0, jitter=0.15, state="random", seed=1002, prec=1),
+    "cavity32_re400_fp64": dict(n=32, re=400.0, jitter=0.15, state="random", seed=1002, prec=0),
+    # the 8^3 cavity at Re 100 (small case)
+    "cavity8_re100_fp64": dict(n=8, re=100.0, jitter=0.0, state="noise", seed=1001, prec=0),
+    "cavity16_re400_fp64": dict(n=16, re=400.0, jitter=0.15, state="random", seed=1002, prec=0),
+    "cavity16_re400_mixed": dict(n=16, re=400.0, jitter=0.15, state="random", seed=1002, prec=1),
+}
+DEFAULT_WORKLOAD = "cavity32_re400_mixed"
+
+
+def make_workload(name):
+    from paper_0809_4802_gb300 import inputs
+    w = WORKLOADS[name]
+    wl = inputs.cavity_workload(w["n"], re=w["re"], jitter_frac=w["jitter"], state=w["state"],
+                                seed=w["seed"])
+    return wl, w["prec"]
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+        self.path = f"/tmp/vms_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([r[0] for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[3][1:]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][1]),
+                "power_w_max": float(max(r[2] for r in rows)), "samples": len(rows),
+                "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ----------------------------------------------------------------------------------------------
+def oracle_assembly_rate(wl, target_s=10.0, max_elems=None):
+    """Elements/s of the oracle's assembly (element kernel, condensation, CSR assembly, Dirichlet)
+    on the first elements of the workload's mesh, sized to take about target_s seconds."""
+    import oracle
+    from oracle import Params
+    mesh = wl.mesh
+    p = Params(nu=wl.nu, dt=wl.dt)
+    beta = wl.beta
+
+    def run(n):
+        t0 = time.perf_counter()
+        X, U, b, Up = oracle.gather(mesh.conn[:n], mesh.xyz, wl.u, beta[:n], wl.u_prev)
+        k = oracle.element_kernel(X, U, b, p, Up)
+        S, r, _, _ = oracle.condense(*oracle.pack_element(k))
+        A, rhs = oracle.assemble(mesh.conn[:n], mesh.n_nodes, S, r)
+        oracle.apply_dirichlet(A, rhs, wl.bc.dofs)
+        return time.perf_counter() - t0
+
+    n0 = min(256, mesh.n_elems)
+    t0 = run(n0)
+    n = int(min(mesh.n_elems if max_elems is None else max_elems,
+                max(n0, n0 * target_s / max(t0, 1e-6))))
+    t = run(n)
+    return n / t, n, t
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    wl, prec = make_workload(args.workload)
+    per_step = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_assembly_rate(wl, target_s=0.0, max_elems=64)
+    rates = []
+    t_total = 0.0
+    for _ in range(args.steps):
+        rate, n, t = oracle_assembly_rate(wl, target_s=0.0, max_elems=per_step)
+        rates.append(rate)
+        t_total += t
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, wl, prec, None),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {per_step} elements of the mesh per step (numpy FP64 oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(name, wl, prec, scatter):
+    c = {"workload": name, "elements": wl.mesh.n_elems, "nodes": wl.mesh.n_nodes,
+         "reynolds": round(1.0 / wl.nu, 3), "precision": "mixed" if prec == 1 else "fp64",
+         "quad_points": 27, "l2": "flushed between timed steps (256 MB write)"}
+    if scatter is not None:
+        c["scatter"] = "colour" if scatter == 1 else "atomic"
+    return c
+
+
+def ours(args):
+    import torch
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_0809_4802_gb300 import build as vbuild, vms
+    if rank == 0 or ws == 1:
+        vbuild.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    vms.load_library()
+
+    wl, prec = make_workload(args.workload)
+    if args.precision is not None:
+        prec = {"mixed": 1, "fp64": 0}[args.precision]
+    mesh = wl.mesh
+    E = mesh.n_elems
+    stream = torch.cuda.current_stream(dev)
+    ctx = vms.Context(local, prec)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.mesh_upload(mesh.xyz, mesh.conn, wl.bc.dofs, wl.bc.vals)
+    ctx.set_params(wl.nu, scatter_mode=args.scatter)
+    u_host = torch.from_numpy(np.ascontiguousarray(wl.u)).pin_memory()
+    beta_host = torch.from_numpy(np.ascontiguousarray(wl.beta)).pin_memory()
+    ctx.state_upload(wl.u, wl.beta)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        ctx.assemble()
+    barrier()
+
+    # ---- timed region: device-resident inputs ----
+    ctx.profile_read(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            ctx.assemble()
+            ends[k].record(stream)
+        barrier()
+    counts = ctx.profile_read(reset=True)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    gpu_launches = int(sum(v[1] for v in counts.values()))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * E * args.steps / (ms / 1000.0)
+
+    # ---- per-kernel times (events inside the library, same stream) for the roofline ----
+    ctx.profile_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        ctx.assemble()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    kern = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms = kern[dom][0] / kern[dom][1]
+    key = dom if dom == "residual" else ("tangent_mixed" if prec == 1 else "tangent_fp64")
+    flops = FP64_FLOPS_PER_ELEM.get(key, 0) * E
+    achieved = flops / (dom_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+                "kernel_ms": {k: round(v[0] / v[1], 4) for k, v in kern.items()}}
+
+    # ---- end to end through the C-ABI with host buffers ----
+    rhs_host = torch.empty(4 * mesh.n_nodes, dtype=torch.float64).pin_memory()
+    e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        e_starts[k].record(stream)
+        ctx.state_upload(u_host, beta_host)
+        view = ctx.assemble()
+        rhs_dev = ctx.csr_device(view)[3]
+        rhs_host.copy_(rhs_dev, non_blocking=True)
+        e_ends[k].record(stream)
+    barrier()
+    e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends))
+    if ws > 1:
+        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e_ms = float(t.item())
+    e2e = {"value": ws * E * args.steps / (e_ms / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": int(u_host.numel() * 8 + beta_host.numel() * 8),
+           "d2h_bytes_per_step": int(rhs_host.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu_baseline:
+        rate, n, t = oracle_assembly_rate(wl, target_s=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n} of {E} elements, numpy FP64 oracle assembly ({t:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+            "config": workload_config(args.workload, wl, prec, args.scatter),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": gpu_launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default=None)
+    ap.add_argument("--scatter", type=int, choices=[0, 1], default=0)
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-sample", type=int, default=2048)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * vms.h - C-ABI of the GB300-native variational multiscale (VMS) Newton-Schur library.
+ *
+ * The library forms, on one GPU, the element-level consistent Newton tangent and residual of the
+ * two-level VMS weak form of the incompressible Navier-Stokes equations (Turner, Nakshatrala &
+ * Hjelmstad, Sections 3-4: Eqs. SC_CoarseScale_Momentum, SC_CoarseScale_Continuity,
+ * SC_FineScale_Momentum, SC_Coarse_Resid_Vec, SC_Coarse_Resid_Vec_2, SC_Fine_Resid_Vec and the
+ * backward-Euler Remark), statically condenses the per-element bubble unknowns into the Schur
+ * complement S_e = K_cc - K_cf K_ff^-1 K_fc with r_e = R_cp - K_cf K_ff^-1 R_f (Section 5, Eq.
+ * SchurUpdate), and scatter-adds S_e, r_e into a global non-symmetric CSR matrix whose sparsity
+ * pattern is built once per mesh (the assembly operator A of Section 5).
+ *
+ * Element: 8-node trilinear hexahedron, equal-order velocity/pressure, one vector bubble
+ * b = (1-xi^2)(1-eta^2)(1-zeta^2) per element (Eq. DefineBubbles3), Gauss rule of quad_order^3
+ * points. Local node order: (-,-,-) (+,-,-) (+,+,-) (-,+,-) (-,-,+) (+,-,+) (+,+,+) (-,+,+).
+ *
+ * Degrees of freedom are node-major: global coarse dof 4*node + c, c = 0,1,2 velocity, c = 3
+ * pressure. The three bubble unknowns of each element are internal (fine scale, Section 3.3).
+ *
+ * Conventions for every call:
+ *  - Every function returns VMS_OK (0) or a negative VMS_ERR_* code and never aborts the process.
+ *    vms_last_error() gives a one-line message for the last failure on that context.
+ *  - Pointers marked "host or device" may point to host memory (pageable or pinned) or to device
+ *    memory of the context's GPU; copies use unified addressing. The caller keeps ownership of
+ *    every pointer it passes; the library copies what it needs before returning (except where a
+ *    call says it writes into a caller buffer).
+ *  - Pointers returned by the library (vms_csr_view) are device pointers it owns; they stay valid
+ *    until the next call that changes the mesh or destroys the context.
+ *  - All GPU work is ordered on the context's stream (vms_set_stream; default: the legacy default
+ *    stream). Calls that return host values (norms, iteration counts) synchronise that stream.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef VMS_GB300_H
+#define VMS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------------------- */
+#define VMS_OK 0
+#define VMS_ERR_INVALID_ARG -1      /* null pointer, size out of range, bad mode */
+#define VMS_ERR_CUDA -2             /* a CUDA runtime call failed (message has the CUDA error) */
+#define VMS_ERR_OUT_OF_MEMORY -3    /* device allocation failed */
+#define VMS_ERR_NEG_JACOBIAN -4     /* det J <= 0 at a quadrature point of some element */
+#define VMS_ERR_SINGULAR_KFF -5     /* the 3x3 bubble block K_ff of some element is singular */
+#define VMS_ERR_NAN -6              /* a non-finite value appeared in a residual or matrix */
+#define VMS_ERR_KRYLOV_MAXIT -7     /* linear solve reached maxit without meeting its tolerance */
+#define VMS_ERR_NEWTON_DIVERGED -8  /* Newton residual grew by 1e6 or maxit was reached */
+#define VMS_ERR_STATE -9            /* call out of order (e.g. assemble before mesh/state upload) */
+#define VMS_ERR_UNSUPPORTED -10     /* option not available in this build */
+
+/* ---- precision modes (vms_create) ---------------------------------------------------------- */
+#define VMS_PREC_FP64 0   /* all element arithmetic, matrix values and residuals in FP64 */
+#define VMS_PREC_MIXED 1  /* tangent blocks and S_e in FP32; residual R, K_ff^-1, r_e in FP64 */
+
+/* ---- scatter modes (vms_params.scatter_mode) ----------------------------------------------- */
+#define VMS_SCATTER_ATOMIC 0  /* one launch, atomic adds into CSR values (order not fixed) */
+#define VMS_SCATTER_COLOUR 1  /* one launch per element colour, plain read-modify-write (fixed order) */
+
+typedef struct vms_ctx vms_ctx;
+
+/* Physical and discretisation parameters (Section 2 Eq. SC_Equilibrium; Section 3.2). */
+typedef struct {
+  double nu;           /* kinematic viscosity nu > 0 */
+  double visc_factor;  /* weak-form viscous coefficient nut = visc_factor * nu; 2 as printed in
+                          Eq. SC_CoarseScale_Momentum ("2 nu grad w : grad v") */
+  double dt;           /* backward-Euler time step (Remark in Section 4.1); 0 means steady */
+  double f[3];         /* constant body force b */
+  double bubble_scale; /* b = bubble_scale (1-xi^2)(1-eta^2)(1-zeta^2); S_e, r_e do not depend on it */
+  int32_t quad_order;  /* Gauss points per direction: 2, 3 or 4 (default 3) */
+  int32_t scatter_mode;/* VMS_SCATTER_* */
+} vms_params;
+
+/* View of the assembled, Dirichlet-applied condensed system S du = -r (Eq. SchurUpdate). */
+typedef struct {
+  int64_t n_rows;         /* 4 * n_nodes */
+  int64_t nnz;            /* 16 * (number of node pairs sharing an element) */
+  const int32_t* rowptr;  /* device, n_rows + 1 entries */
+  const int32_t* colidx;  /* device, nnz entries; columns sorted by (node, component) per row */
+  const void* values;     /* device, nnz entries; double (values_dtype 0) or float (1) */
+  const double* rhs;      /* device, n_rows entries: the assembled condensed residual r (FP64) */
+  int32_t values_dtype;   /* 0 = FP64, 1 = FP32 */
+  int32_t n_colours;      /* element colours used by VMS_SCATTER_COLOUR */
+} vms_csr_view;
+
+/* Create a context on CUDA device `device` in precision mode `precision` (VMS_PREC_*).
+ * *ctx receives the new context. Errors: VMS_ERR_INVALID_ARG, VMS_ERR_CUDA. */
+int vms_create(vms_ctx** ctx, int device, int precision);
+
+/* Release every device buffer of the context and the context itself. NULL is accepted. */
+int vms_destroy(vms_ctx* ctx);
+
+/* Order all later GPU work of the context on `stream` (a cudaStream_t, may be NULL = default). */
+int vms_set_stream(vms_ctx* ctx, void* stream);
+
+/* Upload a hexahedral mesh and its Dirichlet set, then build, once per mesh, the CSR pattern of
+ * the condensed coarse system, the element-to-CSR block map and an element colouring
+ * (Section 5, assembly operator A; the paper assembles after all element work, Section 6).
+ *   xyz      host or device, n_nodes x 3 doubles (row-major)
+ *   conn     host or device, n_elems x 8 int32 node indices in the local order above
+ *   dir_dof  host or device, n_dir global coarse dofs (4*node+c) with prescribed values dir_val;
+ *            their Newton increments are zero (Eq. SC_VelocityBC; a pressure pin is a c=3 entry)
+ * Replaces any previous mesh and state. Errors: VMS_ERR_INVALID_ARG (sizes, node index out of
+ * range, nnz >= 2^31), VMS_ERR_OUT_OF_MEMORY, VMS_ERR_CUDA. */
+int vms_mesh_upload(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_elems,
+                    const int32_t* conn, int64_t n_dir, const int64_t* dir_dof,
+                    const double* dir_val);
+
+/* Set nu, visc_factor, dt, body force, bubble scale, quadrature order and scatter mode.
+ * Errors: VMS_ERR_INVALID_ARG (nu <= 0, quad_order not in {2,3,4}, dt < 0, bad mode). */
+int vms_set_params(vms_ctx* ctx, const vms_params* params);
+
+/* Upload the state: nodal (v, p) u [n_nodes x 4], bubble coefficients beta [n_elems x 3] (NULL =
+ * zero), and the previous time step's nodal values u_prev [n_nodes x 4] (NULL = u; only read when
+ * dt > 0). All host or device doubles. The Dirichlet values of vms_mesh_upload are imposed on u.
+ * Errors: VMS_ERR_STATE (no mesh), VMS_ERR_INVALID_ARG. */
+int vms_state_upload(vms_ctx* ctx, const double* u, const double* beta, const double* u_prev);
+
+/* Copy the current state to caller buffers (host or device); either pointer may be NULL. */
+int vms_state_download(vms_ctx* ctx, double* u, double* beta);
+
+/* One Newton-Schur tangent assembly: for every element, gather its nodes, evaluate geometry and
+ * fields at every quadrature point, form R_c, R_p, R_f and the tangent blocks (Section 4),
+ * condense the bubble unknowns (Section 5), scatter-add S_e and r_e into the CSR system, then
+ * apply the Dirichlet rows and columns (identity rows/columns, zero right-hand side). Also keeps
+ * K_ff^-1 K_fc and K_ff^-1 R_f of every element for the fine-scale recovery.
+ * `out` (may be NULL) receives the device view of the assembled system.
+ * Errors: VMS_ERR_STATE, VMS_ERR_NEG_JACOBIAN, VMS_ERR_SINGULAR_KFF, VMS_ERR_NAN, VMS_ERR_CUDA. */
+int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out);
+
+/* Return the last assembled system without assembling again (VMS_ERR_STATE if none). */
+int vms_get_csr(vms_ctx* ctx, vms_csr_view* out);
+
+/* Residual-only evaluation in FP64 (Section 4.1 residual vectors, assembled): writes the 2-norm
+ * of [R_c, R_p on free dofs; R_f of every element] to *norm (host). If R (host or device, may
+ * be NULL) is given it receives the 4*n_nodes + 3*n_elems entries (constrained coarse entries 0).
+ * Errors: VMS_ERR_STATE, VMS_ERR_NEG_JACOBIAN, VMS_ERR_NAN. */
+int vms_residual(vms_ctx* ctx, double* norm, double* R);
+
+/* Element-level outputs for elements [first, first+count), computed by the same kernels as the
+ * assembly, written as FP64 to caller buffers (host or device; any may be NULL):
+ *   S [count x 32 x 32], r [count x 32]              condensed matrix and residual (Section 5)
+ *   Kcc [count x 32 x 32], Kcf [count x 32 x 3], Kfc [count x 3 x 32], Kff [count x 3 x 3],
+ *   Rcp [count x 32], Rf [count x 3]                 tangent blocks and residuals (Section 4)
+ * Row/column order is node-major (4a+c). Errors: VMS_ERR_INVALID_ARG (range), VMS_ERR_STATE. */
+int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, double* r,
+                         double* Kcc, double* Kcf, double* Kfc, double* Kff, double* Rcp,
+                         double* Rf);
+
+/* y = S x with the last assembled (Dirichlet-applied) CSR matrix; x, y device doubles of length
+ * 4*n_nodes. Errors: VMS_ERR_STATE (nothing assembled), VMS_ERR_INVALID_ARG. */
+int vms_apply(vms_ctx* ctx, const double* x, double* y);
+
+/* Solve S du = -r with the last assembled system by restarted GMRES(restart) with 4x4 node-block
+ * Jacobi preconditioning, FP32 inner iterations and FP64 iterative refinement in VMS_PREC_MIXED
+ * (FP64 throughout in VMS_PREC_FP64), to relative residual rtol within maxit iterations (the paper
+ * used a Krylov solver with tolerance 1e-12 and 50 iterations, Section 6). Then recovers the bubble
+ * increments du' = K_ff^-1 (-R_f - K_fc du_e) per element (Section 5) and, if update != 0, adds
+ * du and du' to the state. *iters (may be NULL) receives the Krylov iterations, *rel the final
+ * relative residual. Errors: VMS_ERR_STATE, VMS_ERR_KRYLOV_MAXIT (state left unchanged). */
+int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
+              double* rel);
+
+/* One Newton-Schur iteration (Sections 4.2 and 5): assemble, solve, recover, update. *res_norm
+ * receives the FP64 residual norm before the update. */
+int vms_newton_step(vms_ctx* ctx, double* res_norm);
+
+/* Newton-Schur iteration until ||R|| <= rtol ||R^0|| or maxit iterations; hist (may be NULL,
+ * maxit+1 doubles, host) receives the residual norms, *iters the iterations taken.
+ * Errors: VMS_ERR_NEWTON_DIVERGED, VMS_ERR_KRYLOV_MAXIT and those of the steps. */
+int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist);
+
+/* ---- kernel accounting (tracing) ----------------------------------------------------------- */
+#define VMS_K_RESIDUAL 0  /* element residual kernel (FP64) */
+#define VMS_K_TANGENT 1   /* element tangent + condensation + scatter kernel */
+#define VMS_K_FILL 2      /* zero fills */
+#define VMS_K_DIRICHLET 3 /* Dirichlet diagonal / state imposition */
+#define VMS_K_REDUCE 4    /* norms and dot products */
+#define VMS_K_SPMV 5      /* CSR matrix-vector products */
+#define VMS_K_KRYLOV 6    /* other Krylov / recovery / update kernels */
+#define VMS_K_COUNT 7
+
+/* Count every kernel launch of the context (always on) and, if `timing` != 0, bracket each launch
+ * with CUDA events on the context's stream to accumulate its GPU time per kernel kind. */
+int vms_profile_enable(vms_ctx* ctx, int timing);
+
+/* Read the accumulated GPU milliseconds (ms, VMS_K_COUNT doubles, may be NULL; only filled while
+ * timing is enabled) and launch counts (launches, VMS_K_COUNT int64, may be NULL) since the last
+ * reset; synchronises the stream. If reset != 0 the counters are cleared after reading. */
+int vms_profile_read(vms_ctx* ctx, int reset, double* ms, int64_t* launches);
+
+/* Message of the last error on this context ("" if none); valid until the next call. */
+const char* vms_last_error(vms_ctx* ctx);
+
+/* Library version string. */
+const char* vms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VMS_GB300_H */

@@ -324,18 +324,15 @@ def assemble_vector(conn, n_nodes, Rcp):
 def apply_dirichlet(A, rhs, dofs):
     """Constrained dofs get increment 0: their rows and columns are zeroed, the diagonal set to 1
     and the right-hand-side entry set to 0 (the prescribed values already sit in the state)."""
-    A = A.tolil() if not sp.isspmatrix_lil(A) else A
     dofs = np.asarray(dofs, np.int64)
     n = A.shape[0]
     keep = np.ones(n)
     keep[dofs] = 0.0
     D = sp.diags(keep)
-    A = (D @ A.tocsr() @ D).tolil()
-    for i in dofs:
-        A[i, i] = 1.0
+    A = D @ sp.csr_matrix(A) @ D + sp.diags(1.0 - keep)
     rhs = rhs.copy()
     rhs[dofs] = 0.0
-    return A.tocsr(), rhs
+    return sp.csr_matrix(A), rhs
 
 
 def residual_vector(conn, n_nodes, k, dir_dofs):

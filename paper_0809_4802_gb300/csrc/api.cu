@@ -1,0 +1,559 @@
+// C-ABI of libvms_gb300 (declared in include/vms.h): context, mesh and state upload, the
+// Newton-Schur assembly, residual evaluation and element-level outputs.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vms_internal.h"
+#include "solver.h"
+
+using namespace vms;
+
+struct vms_ctx {
+  int device = 0;
+  int precision = VMS_PREC_FP64;
+  cudaStream_t stream = nullptr;
+  vms_params params{};
+  int nq = 27;
+  QpRow* d_qp = nullptr;     // nq rows (residual kernel)
+  double* d_tab64 = nullptr; // 37 nq (tangent kernel, FP64)
+  float* d_tab32 = nullptr;  // 37 nq (tangent kernel, FP32)
+  Mesh mesh;
+  State state;
+  Work work;
+  SolverWork solver;
+  unsigned int* h_flags = nullptr;  // pinned
+  double* h_scalar = nullptr;       // pinned, 8 entries
+  double* d_scalar = nullptr;       // 8 entries
+  std::string err;
+  // kernel accounting
+  bool timing = false;
+  int64_t launches[VMS_K_COUNT] = {};
+  double ms[VMS_K_COUNT] = {};
+  struct Ev { int kind; cudaEvent_t a, b; };
+  std::vector<Ev> events;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace vms {
+
+static cudaEvent_t take_event(vms_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+KScope::KScope(vms_ctx* ctx, int k) : c(ctx), kind(k) {
+  if (c->timing) {
+    a = take_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+}
+
+KScope::~KScope() {
+  c->launches[kind] += n;
+  if (a) {
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, c->stream);
+    c->events.push_back({kind, a, b});
+  }
+}
+
+}  // namespace vms
+
+namespace {
+
+int fail(vms_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+template <typename P>
+void dfree(P*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+void free_mesh(vms_ctx* c) {
+  Mesh& m = c->mesh;
+  dfree(m.xyz); dfree(m.conn); dfree(m.rowptr); dfree(m.colidx); dfree(m.blk); dfree(m.rowlen);
+  dfree(m.dir_mask); dfree(m.dir_dof); dfree(m.dir_val); dfree(m.diag_pos); dfree(m.colour_order);
+  m = Mesh();
+  State& s = c->state;
+  dfree(s.u); dfree(s.u_prev); dfree(s.beta);
+  s = State();
+  Work& w = c->work;
+  dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recY); dfree(w.resid);
+  dfree(w.partial); dfree(w.flags);
+  w = Work();
+  free_solver(c->solver);
+}
+
+bool fp32_mode(const vms_ctx* c) { return c->precision == VMS_PREC_MIXED; }
+
+KParams kparams(const vms_ctx* c) {
+  KParams k{};
+  k.nut = c->params.visc_factor * c->params.nu;
+  k.tau = c->params.dt > 0 ? 1.0 / c->params.dt : 0.0;
+  for (int i = 0; i < 3; ++i) k.f[i] = c->params.f[i];
+  k.nq = c->nq;
+  k.transient = c->params.dt > 0 ? 1 : 0;
+  k.has_force = (k.f[0] != 0.0 || k.f[1] != 0.0 || k.f[2] != 0.0) ? 1 : 0;
+  return k;
+}
+
+// Gauss-Legendre points (ascending) and weights on [-1, 1].
+void gauss1d(int n, double* x, double* w) {
+  if (n == 2) {
+    const double a = 1.0 / std::sqrt(3.0);
+    x[0] = -a; x[1] = a; w[0] = w[1] = 1.0;
+  } else if (n == 3) {
+    const double a = std::sqrt(0.6);
+    x[0] = -a; x[1] = 0.0; x[2] = a;
+    w[0] = 5.0 / 9.0; w[1] = 8.0 / 9.0; w[2] = 5.0 / 9.0;
+  } else {
+    const double r = 2.0 / 7.0 * std::sqrt(6.0 / 5.0);
+    const double a = std::sqrt(3.0 / 7.0 - r), b = std::sqrt(3.0 / 7.0 + r);
+    const double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+    x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
+    w[0] = wb; w[1] = wa; w[2] = wa; w[3] = wb;
+  }
+}
+
+const int CORNER[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                          {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+int upload_tables(vms_ctx* ctx) {
+  const int n1 = ctx->params.quad_order;
+  const int nq = n1 * n1 * n1;
+  double x[4], w[4];
+  gauss1d(n1, x, w);
+  std::vector<QpRow> rows(nq);
+  std::vector<double> t64(37 * nq);
+  const double bs = ctx->params.bubble_scale;
+  for (int k = 0; k < n1; ++k)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n1; ++i) {
+        const int q = (k * n1 + j) * n1 + i;
+        const double p[3] = {x[i], x[j], x[k]};
+        QpRow& r = rows[q];
+        r.xi = p[0]; r.eta = p[1]; r.zeta = p[2];
+        r.xe = p[0] * p[1]; r.xz = p[0] * p[2]; r.ez = p[1] * p[2]; r.xez = p[0] * p[1] * p[2];
+        const double f0 = 1 - p[0] * p[0], f1 = 1 - p[1] * p[1], f2 = 1 - p[2] * p[2];
+        r.b = bs * f0 * f1 * f2;
+        r.db0 = bs * (-2 * p[0]) * f1 * f2;
+        r.db1 = bs * (-2 * p[1]) * f0 * f2;
+        r.db2 = bs * (-2 * p[2]) * f0 * f1;
+        r.w = w[i] * w[j] * w[k];
+        for (int a = 0; a < 8; ++a) {
+          double fac[3];
+          for (int d = 0; d < 3; ++d) fac[d] = 1.0 + CORNER[a][d] * p[d];
+          t64[8 * q + a] = fac[0] * fac[1] * fac[2] / 8.0;
+          t64[8 * nq + 24 * q + 3 * a + 0] = CORNER[a][0] * fac[1] * fac[2] / 8.0;
+          t64[8 * nq + 24 * q + 3 * a + 1] = CORNER[a][1] * fac[0] * fac[2] / 8.0;
+          t64[8 * nq + 24 * q + 3 * a + 2] = CORNER[a][2] * fac[0] * fac[1] / 8.0;
+        }
+        t64[32 * nq + q] = r.b;
+        t64[33 * nq + 3 * q + 0] = r.db0;
+        t64[33 * nq + 3 * q + 1] = r.db1;
+        t64[33 * nq + 3 * q + 2] = r.db2;
+        t64[36 * nq + q] = r.w;
+      }
+  std::vector<float> t32(t64.begin(), t64.end());
+  dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32);
+  CK(cudaMalloc(&ctx->d_qp, sizeof(QpRow) * nq));
+  CK(cudaMalloc(&ctx->d_tab64, sizeof(double) * 37 * nq));
+  CK(cudaMalloc(&ctx->d_tab32, sizeof(float) * 37 * nq));
+  CK(cudaMemcpy(ctx->d_qp, rows.data(), sizeof(QpRow) * nq, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_tab64, t64.data(), sizeof(double) * 37 * nq, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_tab32, t32.data(), sizeof(float) * 37 * nq, cudaMemcpyHostToDevice));
+  ctx->nq = nq;
+  return VMS_OK;
+}
+
+int check_flags(vms_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_flags, ctx->work.flags, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const unsigned f = *ctx->h_flags;
+  if (f & FLAG_NEG_JACOBIAN) return fail(ctx, VMS_ERR_NEG_JACOBIAN, "det J <= 0 at a quadrature point");
+  if (f & FLAG_SINGULAR_KFF) return fail(ctx, VMS_ERR_SINGULAR_KFF, "singular bubble block K_ff");
+  if (f & FLAG_NAN) return fail(ctx, VMS_ERR_NAN, "non-finite residual");
+  return VMS_OK;
+}
+
+template <typename T>
+int upload(vms_ctx* ctx, T*& dst, const void* src, size_t count) {
+  CK(cudaMalloc(&dst, sizeof(T) * (count ? count : 1)));
+  if (count && src) CK(cudaMemcpy(dst, src, sizeof(T) * count, cudaMemcpyDefault));
+  return VMS_OK;
+}
+
+#define TRY(x)                \
+  do {                        \
+    int r_ = (x);             \
+    if (r_ != VMS_OK) return r_; \
+  } while (0)
+
+}  // namespace
+
+namespace vms {
+int ctx_flags_check(vms_ctx* ctx) { return check_flags(ctx); }
+}
+
+extern "C" {
+
+const char* vms_version(void) { return "vms-gb300 0.1 (sm_103a)"; }
+
+const char* vms_last_error(vms_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int vms_create(vms_ctx** out, int device, int precision) {
+  if (!out) return VMS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (precision != VMS_PREC_FP64 && precision != VMS_PREC_MIXED) return VMS_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return VMS_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return VMS_ERR_CUDA;
+  vms_ctx* ctx = new vms_ctx();
+  ctx->device = device;
+  ctx->precision = precision;
+  ctx->params.nu = 0.01;
+  ctx->params.visc_factor = 2.0;
+  ctx->params.dt = 0.0;
+  ctx->params.bubble_scale = 1.0;
+  ctx->params.quad_order = 3;
+  ctx->params.scatter_mode = VMS_SCATTER_ATOMIC;
+  if (cudaMallocHost(&ctx->h_flags, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_scalar, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_scalar, 8 * sizeof(double)) != cudaSuccess ||
+      upload_tables(ctx) != VMS_OK) {
+    vms_destroy(ctx);
+    return VMS_ERR_CUDA;
+  }
+  *out = ctx;
+  return VMS_OK;
+}
+
+int vms_destroy(vms_ctx* ctx) {
+  if (!ctx) return VMS_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_mesh(ctx);
+  for (auto& e : ctx->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_scalar);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
+  delete ctx;
+  return VMS_OK;
+}
+
+int vms_set_stream(vms_ctx* ctx, void* stream) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return VMS_OK;
+}
+
+int vms_set_params(vms_ctx* ctx, const vms_params* p) {
+  if (!ctx || !p) return fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
+  if (!(p->nu > 0.0) || !(p->visc_factor > 0.0) || !(p->dt >= 0.0) || !(p->bubble_scale != 0.0) ||
+      p->quad_order < 2 || p->quad_order > 4 ||
+      (p->scatter_mode != VMS_SCATTER_ATOMIC && p->scatter_mode != VMS_SCATTER_COLOUR))
+    return fail(ctx, VMS_ERR_INVALID_ARG, "invalid parameters");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const bool retab = p->quad_order != ctx->params.quad_order || p->bubble_scale != ctx->params.bubble_scale;
+  ctx->params = *p;
+  if (retab) TRY(upload_tables(ctx));
+  ctx->work.assembled = false;
+  return VMS_OK;
+}
+
+int vms_mesh_upload(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_elems,
+                    const int32_t* conn, int64_t n_dir, const int64_t* dir_dof,
+                    const double* dir_val) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (n_nodes <= 0 || n_elems <= 0 || !xyz || !conn || n_dir < 0 || (n_dir > 0 && (!dir_dof || !dir_val)))
+    return fail(ctx, VMS_ERR_INVALID_ARG, "invalid mesh arguments");
+  if (n_nodes >= (int64_t)1 << 29 || n_elems >= (int64_t)1 << 28)
+    return fail(ctx, VMS_ERR_INVALID_ARG, "mesh too large for int32 indexing");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  free_mesh(ctx);
+  // bring inputs to the host (they may be device pointers)
+  std::vector<double> hx(3 * n_nodes);
+  std::vector<int32_t> hc(8 * n_elems);
+  std::vector<int64_t> hd(n_dir);
+  std::vector<double> hv(n_dir);
+  CK(cudaMemcpy(hx.data(), xyz, sizeof(double) * 3 * n_nodes, cudaMemcpyDefault));
+  CK(cudaMemcpy(hc.data(), conn, sizeof(int32_t) * 8 * n_elems, cudaMemcpyDefault));
+  if (n_dir) {
+    CK(cudaMemcpy(hd.data(), dir_dof, sizeof(int64_t) * n_dir, cudaMemcpyDefault));
+    CK(cudaMemcpy(hv.data(), dir_val, sizeof(double) * n_dir, cudaMemcpyDefault));
+  }
+  HostPattern pat;
+  const std::string perr = build_pattern(n_nodes, n_elems, hc.data(), n_dir, hd.data(), pat);
+  if (!perr.empty()) return fail(ctx, VMS_ERR_INVALID_ARG, perr);
+
+  Mesh& m = ctx->mesh;
+  m.n_nodes = n_nodes;
+  m.n_elems = n_elems;
+  m.nnz = pat.rowptr.back();
+  m.n_dir = n_dir;
+  std::vector<double4_32a> x4(n_nodes);
+  for (int64_t i = 0; i < n_nodes; ++i) x4[i] = make_double4_32a(hx[3 * i], hx[3 * i + 1], hx[3 * i + 2], 0.0);
+  TRY(upload(ctx, m.xyz, x4.data(), n_nodes));
+  TRY(upload(ctx, m.conn, hc.data(), 8 * n_elems));
+  TRY(upload(ctx, m.rowptr, pat.rowptr.data(), pat.rowptr.size()));
+  TRY(upload(ctx, m.colidx, pat.colidx.data(), pat.colidx.size()));
+  TRY(upload(ctx, m.blk, pat.blk.data(), pat.blk.size()));
+  TRY(upload(ctx, m.rowlen, pat.rowlen.data(), pat.rowlen.size()));
+  TRY(upload(ctx, m.dir_mask, pat.dir_mask.data(), pat.dir_mask.size()));
+  TRY(upload(ctx, m.dir_dof, hd.data(), n_dir));
+  TRY(upload(ctx, m.dir_val, hv.data(), n_dir));
+  TRY(upload(ctx, m.diag_pos, pat.diag_pos.data(), n_dir));
+  TRY(upload(ctx, m.colour_order, pat.colour_order.data(), pat.colour_order.size()));
+  m.colour_start = pat.colour_start;
+  m.n_colours = pat.n_colours;
+
+  State& s = ctx->state;
+  CK(cudaMalloc(&s.u, sizeof(double4_32a) * n_nodes));
+  CK(cudaMalloc(&s.u_prev, sizeof(double4_32a) * n_nodes));
+  CK(cudaMalloc(&s.beta, sizeof(double) * 3 * n_elems));
+  Work& w = ctx->work;
+  CK(cudaMalloc(&w.values, (size_t)m.nnz * sizeof(double)));
+  CK(cudaMalloc(&w.rhs, sizeof(double) * 4 * n_nodes));
+  CK(cudaMalloc(&w.elemR, sizeof(double) * 36 * n_elems));
+  CK(cudaMalloc(&w.recX, sizeof(double) * 96 * n_elems));
+  CK(cudaMalloc(&w.recY, sizeof(double) * 3 * n_elems));
+  CK(cudaMalloc(&w.resid, sizeof(double) * (4 * n_nodes + 3 * n_elems)));
+  CK(cudaMalloc(&w.partial, sizeof(double) * 1024));
+  CK(cudaMalloc(&w.flags, sizeof(unsigned int)));
+  return VMS_OK;
+}
+
+int vms_state_upload(vms_ctx* ctx, const double* u, const double* beta, const double* u_prev) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx->mesh.n_nodes) return fail(ctx, VMS_ERR_STATE, "no mesh uploaded");
+  if (!u) return fail(ctx, VMS_ERR_INVALID_ARG, "u is null");
+  CK(cudaSetDevice(ctx->device));
+  const Mesh& m = ctx->mesh;
+  State& s = ctx->state;
+  CK(cudaMemcpyAsync(s.u, u, sizeof(double4_32a) * m.n_nodes, cudaMemcpyDefault, ctx->stream));
+  { KScope k(ctx, VMS_K_DIRICHLET); k.add(launch_impose(m, s.u, ctx->stream)); }
+  if (beta) {
+    CK(cudaMemcpyAsync(s.beta, beta, sizeof(double) * 3 * m.n_elems, cudaMemcpyDefault, ctx->stream));
+  } else {
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_fill_zero(s.beta, sizeof(double) * 3 * m.n_elems, ctx->stream));
+  }
+  CK(cudaMemcpyAsync(s.u_prev, u_prev ? u_prev : u, sizeof(double4_32a) * m.n_nodes, cudaMemcpyDefault,
+                     ctx->stream));
+  CK(cudaGetLastError());
+  s.valid = true;
+  ctx->work.assembled = false;
+  return VMS_OK;
+}
+
+int vms_state_download(vms_ctx* ctx, double* u, double* beta) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "no state uploaded");
+  CK(cudaSetDevice(ctx->device));
+  if (u) CK(cudaMemcpyAsync(u, ctx->state.u, sizeof(double4_32a) * ctx->mesh.n_nodes, cudaMemcpyDefault, ctx->stream));
+  if (beta) CK(cudaMemcpyAsync(beta, ctx->state.beta, sizeof(double) * 3 * ctx->mesh.n_elems, cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VMS_OK;
+}
+
+static void fill_view(vms_ctx* ctx, vms_csr_view* out) {
+  out->n_rows = 4 * ctx->mesh.n_nodes;
+  out->nnz = ctx->mesh.nnz;
+  out->rowptr = ctx->mesh.rowptr;
+  out->colidx = ctx->mesh.colidx;
+  out->values = ctx->work.values;
+  out->rhs = ctx->work.rhs;
+  out->values_dtype = fp32_mode(ctx) ? 1 : 0;
+  out->n_colours = ctx->mesh.n_colours;
+}
+
+int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");
+  CK(cudaSetDevice(ctx->device));
+  const Mesh& m = ctx->mesh;
+  Work& w = ctx->work;
+  const bool f32 = fp32_mode(ctx);
+  const KParams kp = kparams(ctx);
+  cudaStream_t st = ctx->stream;
+  {
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_fill_zero(w.values, (size_t)m.nnz * (f32 ? sizeof(float) : sizeof(double)), st));
+    k.add(launch_fill_zero(w.rhs, sizeof(double) * 4 * m.n_nodes, st));
+    k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st));
+  }
+  {
+    KScope k(ctx, VMS_K_RESIDUAL);
+    k.add(launch_residual(m, ctx->state, kp, ctx->d_qp, w.elemR, nullptr, 0, m.n_elems, 0, w.flags, st));
+  }
+  TangentOut o;
+  o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recY = w.recY;
+  const void* tab = f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64;
+  {
+    KScope k(ctx, VMS_K_TANGENT);
+    if (ctx->params.scatter_mode == VMS_SCATTER_COLOUR) {
+      for (int c = 0; c < m.n_colours; ++c) {
+        const int64_t b = m.colour_start[c], n = m.colour_start[c + 1] - b;
+        k.add(launch_tangent(f32, m, ctx->state, kp, tab, w.elemR, o, b, n, m.colour_order, false,
+                             false, w.flags, st));
+      }
+    } else {
+      k.add(launch_tangent(f32, m, ctx->state, kp, tab, w.elemR, o, 0, m.n_elems, nullptr, false,
+                           true, w.flags, st));
+    }
+  }
+  { KScope k(ctx, VMS_K_DIRICHLET); k.add(launch_dirichlet_diag(m, w.values, f32, w.rhs, st)); }
+  CK(cudaGetLastError());
+  TRY(check_flags(ctx));
+  w.assembled = true;
+  if (out) fill_view(ctx, out);
+  return VMS_OK;
+}
+
+int vms_get_csr(vms_ctx* ctx, vms_csr_view* out) {
+  if (!ctx || !out) return fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
+  if (!ctx->work.assembled) return fail(ctx, VMS_ERR_STATE, "nothing assembled");
+  fill_view(ctx, out);
+  return VMS_OK;
+}
+
+int vms_residual(vms_ctx* ctx, double* norm, double* R) {
+  if (!ctx || !norm) return fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
+  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");
+  CK(cudaSetDevice(ctx->device));
+  const Mesh& m = ctx->mesh;
+  Work& w = ctx->work;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = 4 * m.n_nodes + 3 * m.n_elems;
+  {
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_fill_zero(w.resid, sizeof(double) * n, st));
+    k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st));
+  }
+  {
+    KScope k(ctx, VMS_K_RESIDUAL);
+    k.add(launch_residual(m, ctx->state, kparams(ctx), ctx->d_qp, nullptr, w.resid, 0, m.n_elems, 1,
+                          w.flags, st));
+  }
+  { KScope k(ctx, VMS_K_REDUCE); k.add(launch_norm2(w.resid, n, w.partial, ctx->d_scalar, st)); }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (R) CK(cudaMemcpyAsync(R, w.resid, sizeof(double) * n, cudaMemcpyDefault, st));
+  TRY(check_flags(ctx));
+  *norm = std::sqrt(ctx->h_scalar[0]);
+  return VMS_OK;
+}
+
+int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, double* r,
+                         double* Kcc, double* Kcf, double* Kfc, double* Kff, double* Rcp,
+                         double* Rf) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");
+  const Mesh& m = ctx->mesh;
+  if (first < 0 || count < 0 || first + count > m.n_elems)
+    return fail(ctx, VMS_ERR_INVALID_ARG, "element range out of bounds");
+  if (count == 0) return VMS_OK;
+  CK(cudaSetDevice(ctx->device));
+  Work& w = ctx->work;
+  cudaStream_t st = ctx->stream;
+  const KParams kp = kparams(ctx);
+  const bool f32 = fp32_mode(ctx);
+  { KScope k(ctx, VMS_K_FILL); k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st)); }
+  {
+    KScope k(ctx, VMS_K_RESIDUAL);
+    k.add(launch_residual(m, ctx->state, kp, ctx->d_qp, w.elemR, nullptr, first, count, 0, w.flags, st));
+  }
+  double* buf = nullptr;
+  const size_t per = 1024 + 32 + 1024 + 96 + 96 + 9;
+  CK(cudaMalloc(&buf, sizeof(double) * per * count));
+  TangentOut o;
+  o.S = buf; o.r = buf + 1024 * count; o.Kcc = buf + 1056 * count; o.Kcf = buf + 2080 * count;
+  o.Kfc = buf + 2176 * count; o.Kff = buf + 2272 * count;
+  {
+    KScope k(ctx, VMS_K_TANGENT);
+    k.add(launch_tangent(f32, m, ctx->state, kp,
+                         f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64, w.elemR, o,
+                         first, count, nullptr, true, true, w.flags, st));
+  }
+  cudaError_t e = cudaGetLastError();
+  struct Out { double* dst; double* src; size_t n; } outs[6] = {
+      {S, o.S, 1024}, {r, o.r, 32}, {Kcc, o.Kcc, 1024}, {Kcf, o.Kcf, 96}, {Kfc, o.Kfc, 96}, {Kff, o.Kff, 9}};
+  for (auto& x : outs)
+    if (e == cudaSuccess && x.dst)
+      e = cudaMemcpyAsync(x.dst, x.src, sizeof(double) * x.n * count, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && Rcp)
+    e = cudaMemcpy2DAsync(Rcp, 32 * sizeof(double), w.elemR + 36 * first, 36 * sizeof(double),
+                          32 * sizeof(double), count, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && Rf)
+    e = cudaMemcpy2DAsync(Rf, 3 * sizeof(double), w.elemR + 36 * first + 32, 36 * sizeof(double),
+                          3 * sizeof(double), count, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  return check_flags(ctx);
+}
+
+int vms_profile_enable(vms_ctx* ctx, int timing) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  ctx->timing = timing != 0;
+  return VMS_OK;
+}
+
+int vms_profile_read(vms_ctx* ctx, int reset, double* ms, int64_t* launches) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& e : ctx->events) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ctx->ms[e.kind] += t;
+    ctx->pool.push_back(e.a);
+    ctx->pool.push_back(e.b);
+  }
+  ctx->events.clear();
+  for (int k = 0; k < VMS_K_COUNT; ++k) {
+    if (ms) ms[k] = ctx->ms[k];
+    if (launches) launches[k] = ctx->launches[k];
+    if (reset) { ctx->ms[k] = 0.0; ctx->launches[k] = 0; }
+  }
+  return VMS_OK;
+}
+
+}  // extern "C"
+
+// Accessors used by the solver translation unit.
+namespace vms {
+const Mesh& ctx_mesh(vms_ctx* c) { return c->mesh; }
+State& ctx_state(vms_ctx* c) { return c->state; }
+Work& ctx_work(vms_ctx* c) { return c->work; }
+SolverWork& ctx_solver(vms_ctx* c) { return c->solver; }
+cudaStream_t ctx_stream(vms_ctx* c) { return c->stream; }
+int ctx_device(vms_ctx* c) { return c->device; }
+bool ctx_fp32(vms_ctx* c) { return fp32_mode(c); }
+double* ctx_dscalar(vms_ctx* c) { return c->d_scalar; }
+double* ctx_hscalar(vms_ctx* c) { return c->h_scalar; }
+int ctx_fail(vms_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
+}  // namespace vms

@@ -1,0 +1,93 @@
+// Element-level arithmetic of the VMS Newton-Schur method, shared by the residual and tangent
+// kernels. Everything here is __host__ __device__ and free of CUDA intrinsics, so the same code
+// can be exercised on the host. Section and equation names refer to Turner, Nakshatrala and
+// Hjelmstad, "A variational multiscale Newton-Schur approach for the incompressible
+// Navier-Stokes equations".
+#pragma once
+
+#include <stdint.h>
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace vms {
+
+#define VMS_HD __host__ __device__ __forceinline__
+#ifdef __CUDACC__
+#define VMS_UNROLL _Pragma("unroll")
+#else
+#define VMS_UNROLL
+#endif
+
+// Local node a <-> lattice corner bits (i,j,k): a = 0..7 <-> 000 100 110 010 001 101 111 011.
+// Forward butterfly: nodal f[8] (local order) -> monomial coefficients, scaled by 8, of
+// {1, xi, eta, zeta, xi eta, xi zeta, eta zeta, xi eta zeta}.
+template <typename T>
+VMS_HD void modal8(const T f[8], T c[8]) {
+  T S00 = f[0] + f[1], D00 = f[1] - f[0];
+  T S10 = f[3] + f[2], D10 = f[2] - f[3];
+  T S01 = f[4] + f[5], D01 = f[5] - f[4];
+  T S11 = f[7] + f[6], D11 = f[6] - f[7];
+  T SS0 = S00 + S10, SD0 = S10 - S00, DS0 = D00 + D10, DD0 = D10 - D00;
+  T SS1 = S01 + S11, SD1 = S11 - S01, DS1 = D01 + D11, DD1 = D11 - D01;
+  c[0] = SS0 + SS1; c[3] = SS1 - SS0;
+  c[2] = SD0 + SD1; c[6] = SD1 - SD0;
+  c[1] = DS0 + DS1; c[5] = DS1 - DS0;
+  c[4] = DD0 + DD1; c[7] = DD1 - DD0;
+}
+
+// Transposed butterfly: monomial sums m[8] -> r_a = sum_m s_am m_m in local node order, where
+// s_am is the product of node a's corner signs over the variables of monomial m.
+template <typename T>
+VMS_HD void nodal8(const T m[8], T r[8]) {
+  T SSm = m[0] - m[3], SSp = m[0] + m[3];
+  T SDm = m[2] - m[6], SDp = m[2] + m[6];
+  T DSm = m[1] - m[5], DSp = m[1] + m[5];
+  T DDm = m[4] - m[7], DDp = m[4] + m[7];
+  T S00 = SSm - SDm, S10 = SSm + SDm, D00 = DSm - DDm, D10 = DSm + DDm;
+  T S01 = SSp - SDp, S11 = SSp + SDp, D01 = DSp - DDp, D11 = DSp + DDp;
+  r[0] = S00 - D00; r[1] = S00 + D00; r[3] = S10 - D10; r[2] = S10 + D10;
+  r[4] = S01 - D01; r[5] = S01 + D01; r[7] = S11 - D11; r[6] = S11 + D11;
+}
+
+// Cofactor matrix cof = det(J) J^-T of J[i][al] = dx_i/dxi_al; returns det J.
+template <typename T>
+VMS_HD T cofactor3(const T J[3][3], T cof[3][3]) {
+  cof[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  cof[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  cof[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  cof[1][0] = J[2][1] * J[0][2] - J[2][2] * J[0][1];
+  cof[1][1] = J[2][2] * J[0][0] - J[2][0] * J[0][2];
+  cof[1][2] = J[2][0] * J[0][1] - J[2][1] * J[0][0];
+  cof[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  cof[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  cof[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * cof[0][0] + J[0][1] * cof[0][1] + J[0][2] * cof[0][2];
+}
+
+// FP64 inverse of a 3x3 matrix (row-major); returns the determinant.
+VMS_HD double inverse3(const double K[9], double Ki[9]) {
+  double c00 = K[4] * K[8] - K[5] * K[7];
+  double c01 = K[5] * K[6] - K[3] * K[8];
+  double c02 = K[3] * K[7] - K[4] * K[6];
+  double det = K[0] * c00 + K[1] * c01 + K[2] * c02;
+  double r = 1.0 / det;
+  Ki[0] = c00 * r;
+  Ki[1] = (K[2] * K[7] - K[1] * K[8]) * r;
+  Ki[2] = (K[1] * K[5] - K[2] * K[4]) * r;
+  Ki[3] = c01 * r;
+  Ki[4] = (K[0] * K[8] - K[2] * K[6]) * r;
+  Ki[5] = (K[2] * K[3] - K[0] * K[5]) * r;
+  Ki[6] = c02 * r;
+  Ki[7] = (K[1] * K[6] - K[0] * K[7]) * r;
+  Ki[8] = (K[0] * K[4] - K[1] * K[3]) * r;
+  return det;
+}
+
+template <typename T>
+VMS_HD T fmaT(T a, T b, T c) { return a * b + c; }
+
+}  // namespace vms

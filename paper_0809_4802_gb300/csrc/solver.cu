@@ -1,0 +1,620 @@
+// Linear solve of the condensed system S du = -r (Eq. SchurUpdate), fine-scale recovery and the
+// Newton-Schur driver (Sections 4.2 and 5; the paper used a Krylov solver with tolerance 1e-12 and
+// at most 50 iterations, Section 6).
+//
+// Solver: restarted GMRES(m), right-preconditioned by the inverses of the 4x4 diagonal node blocks,
+// classical Gram-Schmidt with one re-orthogonalisation pass (CGS2). In mixed precision the Krylov
+// vectors and the matrix are FP32 (dot products accumulate in FP64) and an outer FP64 iterative
+// refinement recomputes r = b - S x in FP64 until the tolerance is met.
+#include <cmath>
+#include <vector>
+
+#include "solver.h"
+
+namespace vms {
+
+void free_solver(SolverWork& s) {
+  void* bufs[] = {s.x, s.r, s.V, s.Z, s.Dinv, s.h, s.rfull, s.bf, s.xf};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  s = SolverWork();
+}
+
+// ---------------------------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------------------------
+template <typename T, typename VT>
+__global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ colidx,
+                                                   const T* __restrict__ val,
+                                                   const VT* __restrict__ x, VT* __restrict__ y,
+                                                   int64_t n_rows) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  const int32_t b = rowptr[row], e = rowptr[row + 1];
+  double s = 0.0;
+  for (int32_t k = b + lane; k < e; k += 32) s = fma((double)val[k], (double)x[colidx[k]], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = VT(s);
+}
+
+template <typename T, typename VT>
+static int spmv(const Mesh& m, const void* values, const VT* x, VT* y, cudaStream_t st) {
+  const int64_t n = 4 * m.n_nodes;
+  const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
+  spmv_kernel<T, VT><<<blocks, 256, 0, st>>>(m.rowptr, m.colidx, (const T*)values, x, y, n);
+  return 1;
+}
+
+int launch_spmv(const Mesh& m, const void* values, bool fp32, const double* x, double* y,
+                cudaStream_t st) {
+  return fp32 ? spmv<float, double>(m, values, x, y, st) : spmv<double, double>(m, values, x, y, st);
+}
+
+// Inverse of each node's 4x4 diagonal block (Gauss-Jordan with partial pivoting, FP64); a block
+// with a vanishing pivot is replaced by the identity.
+template <typename T>
+__global__ void block_diag_inv_kernel(const int32_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ colidx,
+                                      const T* __restrict__ val, int64_t n_nodes,
+                                      double* __restrict__ Dinv) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  const int32_t start = rowptr[4 * n];
+  const int32_t nb = (rowptr[4 * n + 1] - start) / 4;
+  int lo = 0, hi = nb;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (colidx[start + 4 * mid] < 4 * n) lo = mid + 1; else hi = mid;
+  }
+  double M[4][8];
+  for (int i = 0; i < 4; ++i) {
+    const int32_t off = rowptr[4 * n + i] + 4 * lo;
+    for (int k = 0; k < 4; ++k) {
+      M[i][k] = (double)val[off + k];
+      M[i][4 + k] = (i == k) ? 1.0 : 0.0;
+    }
+  }
+  double scale = 0.0;
+  for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 4; ++k) scale = fmax(scale, fabs(M[i][k]));
+  bool ok = scale > 0.0;
+  for (int c = 0; c < 4 && ok; ++c) {
+    int p = c;
+    for (int i = c + 1; i < 4; ++i)
+      if (fabs(M[i][c]) > fabs(M[p][c])) p = i;
+    if (!(fabs(M[p][c]) > 1e-14 * scale)) { ok = false; break; }
+    if (p != c)
+      for (int k = 0; k < 8; ++k) { const double t = M[c][k]; M[c][k] = M[p][k]; M[p][k] = t; }
+    const double inv = 1.0 / M[c][c];
+    for (int k = 0; k < 8; ++k) M[c][k] *= inv;
+    for (int i = 0; i < 4; ++i) {
+      if (i == c) continue;
+      const double f = M[i][c];
+      for (int k = 0; k < 8; ++k) M[i][k] -= f * M[c][k];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 4; ++k) Dinv[16 * n + 4 * i + k] = ok ? M[i][4 + k] : (i == k ? 1.0 : 0.0);
+}
+
+template <typename VT>
+__global__ void block_apply_kernel(const double* __restrict__ Dinv, const VT* __restrict__ v,
+                                   VT* __restrict__ z, int64_t n_nodes) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  double x[4];
+  for (int k = 0; k < 4; ++k) x[k] = (double)v[4 * n + k];
+  for (int i = 0; i < 4; ++i) {
+    const double* d = Dinv + 16 * n + 4 * i;
+    z[4 * n + i] = VT(d[0] * x[0] + d[1] * x[1] + d[2] * x[2] + d[3] * x[3]);
+  }
+}
+
+constexpr int DOT_BLOCKS = 256, DOT_THREADS = 256;
+// device scratch layout (doubles): Gram-Schmidt coefficients of the two passes, a norm, the
+// least-squares solution, then per-block partial sums
+constexpr int H_PASS1 = 0, H_PASS2 = 128, H_NORM = 256, H_Y = 384, H_PART = 512;
+constexpr int H_SIZE = H_PART + 128 * DOT_BLOCKS;
+
+__device__ __forceinline__ double block_reduce(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = threadIdx.x < DOT_THREADS / 32 ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[k][bx] = sum over this block's chunk of V_k . w, for k = blockIdx.y (FP64 accumulation)
+template <typename VT>
+__global__ void __launch_bounds__(DOT_THREADS) multidot_kernel(const VT* __restrict__ V, int64_t ld,
+                                                               const VT* __restrict__ w, int64_t n,
+                                                               double* __restrict__ partial) {
+  __shared__ double sh[DOT_THREADS / 32];
+  const int k = blockIdx.y;
+  const VT* v = V + (int64_t)k * ld;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; i < n;
+       i += (int64_t)DOT_BLOCKS * DOT_THREADS)
+    s = fma((double)v[i], (double)w[i], s);
+  s = block_reduce(s, sh);
+  if (threadIdx.x == 0) partial[k * DOT_BLOCKS + blockIdx.x] = s;
+}
+
+// out[k] = (accumulate ? out[k] : 0) + sum_b partial[k][b]
+__global__ void __launch_bounds__(DOT_THREADS) reduce_partials_kernel(const double* __restrict__ partial,
+                                                                      double* __restrict__ out,
+                                                                      int accumulate) {
+  __shared__ double sh[DOT_THREADS / 32];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < DOT_BLOCKS; b += DOT_THREADS) s += partial[k * DOT_BLOCKS + b];
+  s = block_reduce(s, sh);
+  if (threadIdx.x == 0) out[k] = (accumulate ? out[k] : 0.0) + s;
+}
+
+// w -= sum_{k < m} h[k] V_k
+template <typename VT>
+__global__ void gs_update_kernel(const VT* __restrict__ V, int64_t ld, const double* __restrict__ h,
+                                 int m, VT* __restrict__ w, int64_t n) {
+  __shared__ double hs[128];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) hs[k] = h[k];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = (double)w[i];
+    for (int k = 0; k < m; ++k) s -= hs[k] * (double)V[(int64_t)k * ld + i];
+    w[i] = VT(s);
+  }
+}
+
+// y = x / sqrt(*nrm2) (device-side normalisation, no host round trip)
+template <typename VT>
+__global__ void scale_kernel(const VT* __restrict__ x, const double* __restrict__ nrm2,
+                             VT* __restrict__ y, int64_t n) {
+  const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = VT((double)x[i] * s);
+}
+
+// t = sum_k y[k] V_k  (y on the device)
+template <typename VT>
+__global__ void combine_kernel(const VT* __restrict__ V, int64_t ld, const double* __restrict__ y,
+                               int m, VT* __restrict__ t, int64_t n) {
+  __shared__ double ys[128];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) ys[k] = y[k];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += ys[k] * (double)V[(int64_t)k * ld + i];
+    t[i] = VT(s);
+  }
+}
+
+// out = a * x + b * y (mixed vector types)
+template <typename A, typename B, typename C>
+__global__ void axpby_kernel(double a, const A* __restrict__ x, double b, const B* __restrict__ y,
+                             C* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = C(a * (double)x[i] + (y ? b * (double)y[i] : 0.0));
+}
+
+// Fine-scale recovery (Section 5): dbeta_e = -(K_ff^-1 R_f + K_ff^-1 K_fc du_e); beta += dbeta.
+template <typename T>
+__global__ void recover_kernel(const int32_t* __restrict__ conn, const T* __restrict__ recX,
+                               const double* __restrict__ recY, const double* __restrict__ du,
+                               double* __restrict__ beta, int64_t n_elems) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_elems) return;
+  double s[3] = {recY[3 * e], recY[3 * e + 1], recY[3 * e + 2]};
+  for (int a = 0; a < 8; ++a) {
+    const int64_t nd = conn[8 * e + a];
+    for (int c = 0; c < 4; ++c) {
+      const double d = du[4 * nd + c];
+      for (int m = 0; m < 3; ++m) s[m] += (double)recX[96 * e + 32 * m + 4 * a + c] * d;
+    }
+  }
+  for (int m = 0; m < 3; ++m) beta[3 * e + m] -= s[m];
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+static unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b));
+}
+
+struct Gmres {
+  vms_ctx* ctx;
+  const Mesh& m;
+  SolverWork& w;
+  cudaStream_t st;
+  int64_t n;
+
+  int sync_host(void* dst, const void* src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  }
+
+  // One restarted GMRES solve of A x = b from x = 0 in vector type VT; matrix values type T.
+  // Returns VMS_OK with *iters and *relres; x receives the solution.
+  template <typename T, typename VT>
+  int solve(const void* values, const VT* b, VT* x, double bnorm, double rtol, int maxit,
+            int restart, int* iters, double* relres) {
+    VT* V = reinterpret_cast<VT*>(w.V);
+    VT* z = reinterpret_cast<VT*>(w.Z);
+    double* hd = w.h;
+    std::vector<double> H((restart + 1) * restart, 0.0), cs(restart), sn(restart), g(restart + 1);
+    std::vector<double> hh(restart + 2);
+    KScope zs(ctx, VMS_K_FILL);
+    zs.add(1);
+    axpby_kernel<double, double, VT><<<grid_for(n), 256, 0, st>>>(0.0, (const double*)nullptr, 0.0,
+                                                                   (const double*)nullptr, x, n);
+    int it = 0;
+    double res = bnorm;
+    // r0 = b (x = 0)
+    {
+      KScope k(ctx, VMS_K_KRYLOV);
+      axpby_kernel<VT, VT, VT><<<grid_for(n), 256, 0, st>>>(1.0, b, 0.0, (const VT*)nullptr, V, n);
+      k.add(1);
+    }
+    while (it < maxit && res > rtol * bnorm) {
+      // V_0 = r / |r|
+      {
+        KScope k(ctx, VMS_K_REDUCE);
+        multidot_kernel<VT><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(V, n, V, n, hd + H_PART);
+        reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+        k.add(2);
+      }
+      int rc = sync_host(&res, hd + H_NORM, sizeof(double));
+      if (rc) return rc;
+      res = std::sqrt(res);
+      if (!(res > rtol * bnorm) || !(res == res)) break;
+      {
+        KScope k(ctx, VMS_K_KRYLOV);
+        scale_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, hd + H_NORM, V, n);
+        k.add(1);
+      }
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = res;
+      int j = 0;
+      for (; j < restart && it < maxit; ++j, ++it) {
+        VT* vj = V + (int64_t)j * n;
+        VT* vn = V + (int64_t)(j + 1) * n;
+        {
+          KScope k(ctx, VMS_K_KRYLOV);
+          block_apply_kernel<VT><<<grid_for(m.n_nodes), 256, 0, st>>>(w.Dinv, vj, z, m.n_nodes);
+          k.add(1);
+        }
+        { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, values, z, vn, st)); }
+        // CGS2 against V_0..V_j: first pass coefficients into hd[0..j], second into hd[128..]
+        const int kk = j + 1;
+        double* partial = hd + H_PART;
+        for (int pass = 0; pass < 2; ++pass) {
+          {
+            KScope k(ctx, VMS_K_REDUCE);
+            multidot_kernel<VT><<<dim3(DOT_BLOCKS, kk), DOT_THREADS, 0, st>>>(V, n, vn, n, partial);
+            reduce_partials_kernel<<<kk, DOT_THREADS, 0, st>>>(partial, hd + (pass ? H_PASS2 : H_PASS1), 0);
+            k.add(2);
+          }
+          KScope k(ctx, VMS_K_KRYLOV);
+          gs_update_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, n, hd + (pass ? H_PASS2 : H_PASS1), kk, vn, n);
+          k.add(1);
+        }
+        {
+          KScope k(ctx, VMS_K_REDUCE);
+          multidot_kernel<VT><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(vn, n, vn, n, partial);
+          reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(partial, hd + H_NORM, 0);
+          k.add(2);
+        }
+        {
+          KScope k(ctx, VMS_K_KRYLOV);
+          scale_kernel<VT><<<grid_for(n), 256, 0, st>>>(vn, hd + H_NORM, vn, n);
+          k.add(1);
+        }
+        // bring the Hessenberg column to the host
+        std::vector<double> h1(kk), h2(kk);
+        double nrm2 = 0.0;
+        if (int rc2 = sync_host(h1.data(), hd + H_PASS1, sizeof(double) * kk)) return rc2;
+        if (int rc2 = sync_host(h2.data(), hd + H_PASS2, sizeof(double) * kk)) return rc2;
+        if (int rc2 = sync_host(&nrm2, hd + H_NORM, sizeof(double))) return rc2;
+        for (int i = 0; i < kk; ++i) hh[i] = h1[i] + h2[i];
+        hh[kk] = std::sqrt(nrm2);
+        // apply previous rotations, then a new one
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * hh[i] + sn[i] * hh[i + 1];
+          hh[i + 1] = -sn[i] * hh[i] + cs[i] * hh[i + 1];
+          hh[i] = t;
+        }
+        const double den = std::hypot(hh[j], hh[j + 1]);
+        cs[j] = den > 0 ? hh[j] / den : 1.0;
+        sn[j] = den > 0 ? hh[j + 1] / den : 0.0;
+        hh[j] = den;
+        hh[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        for (int i = 0; i <= j; ++i) H[i * restart + j] = hh[i];
+        res = std::fabs(g[j + 1]);
+        if (!(res > rtol * bnorm) || nrm2 <= 0.0) { ++j; ++it; break; }
+      }
+      // y = H^-1 g (upper triangular j x j), x += M^-1 V y
+      std::vector<double> y(j, 0.0);
+      for (int i = j - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int k2 = i + 1; k2 < j; ++k2) s -= H[i * restart + k2] * y[k2];
+        y[i] = H[i * restart + i] != 0.0 ? s / H[i * restart + i] : 0.0;
+      }
+      cudaMemcpyAsync(hd + H_Y, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st);
+      {
+        KScope k(ctx, VMS_K_KRYLOV);
+        combine_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, n, hd + H_Y, j, z, n);
+        block_apply_kernel<VT><<<grid_for(m.n_nodes), 256, 0, st>>>(w.Dinv, z, V + n, m.n_nodes);
+        axpby_kernel<VT, VT, VT><<<grid_for(n), 256, 0, st>>>(1.0, x, 1.0, V + n, x, n);
+        k.add(3);
+      }
+      // restart: r = b - A x into V_0
+      { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, values, x, z, st)); }
+      {
+        KScope k(ctx, VMS_K_KRYLOV);
+        axpby_kernel<VT, VT, VT><<<grid_for(n), 256, 0, st>>>(1.0, b, -1.0, z, V, n);
+        k.add(1);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+      // true residual norm for the next cycle's test is computed at the top of the loop
+      if (!(res > rtol * bnorm)) {
+        KScope k(ctx, VMS_K_REDUCE);
+        multidot_kernel<VT><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(V, n, V, n, hd + H_PART);
+        reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+        k.add(2);
+        double r2 = 0.0;
+        if (int rc2 = sync_host(&r2, hd + H_NORM, sizeof(double))) return rc2;
+        res = std::sqrt(r2);
+      }
+    }
+    *iters = it;
+    *relres = bnorm > 0 ? res / bnorm : 0.0;
+    return VMS_OK;
+  }
+};
+
+static int ensure_solver(vms_ctx* ctx, int restart) {
+  const Mesh& m = ctx_mesh(ctx);
+  SolverWork& w = ctx_solver(ctx);
+  const int64_t n = 4 * m.n_nodes;
+  if (w.n == n && w.restart >= restart) return VMS_OK;
+  free_solver(w);
+  cudaError_t e = cudaSuccess;
+  const size_t vb = sizeof(double);  // FP64 storage serves both vector types
+  if (e == cudaSuccess) e = cudaMalloc(&w.x, vb * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.r, vb * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.V, vb * n * (restart + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&w.Z, vb * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.Dinv, sizeof(double) * 16 * m.n_nodes);
+  if (e == cudaSuccess) e = cudaMalloc(&w.h, sizeof(double) * H_SIZE);
+  if (e == cudaSuccess) e = cudaMalloc(&w.rfull, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.bf, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.xf, sizeof(float) * n);
+  if (e != cudaSuccess) {
+    free_solver(w);
+    return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
+                    cudaGetErrorString(e));
+  }
+  w.n = n;
+  w.restart = restart;
+  return VMS_OK;
+}
+
+// Solve S du = -rhs into w.x (FP64). Mixed: FP32 GMRES inside FP64 iterative refinement.
+static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* iters_out,
+                        double* rel_out) {
+  const Mesh& m = ctx_mesh(ctx);
+  Work& wk = ctx_work(ctx);
+  SolverWork& w = ctx_solver(ctx);
+  cudaStream_t st = ctx_stream(ctx);
+  const int64_t n = 4 * m.n_nodes;
+  const bool f32 = ctx_fp32(ctx);
+  if (restart < 1 || restart > 120 || maxit < 1 || !(rtol > 0.0))
+    return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid solver parameters");
+  if (int rc = ensure_solver(ctx, restart)) return rc;
+  {
+    KScope k(ctx, VMS_K_KRYLOV);
+    if (f32)
+      block_diag_inv_kernel<float><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, m.n_nodes, w.Dinv);
+    else
+      block_diag_inv_kernel<double><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, m.n_nodes, w.Dinv);
+    k.add(1);
+  }
+  // b = -rhs (FP64) in w.r
+  {
+    KScope k(ctx, VMS_K_KRYLOV);
+    axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(-1.0, wk.rhs, 0.0, (const double*)nullptr, w.r, n);
+    k.add(1);
+  }
+  double* hd = w.h;
+  double bnorm2 = 0.0;
+  {
+    KScope k(ctx, VMS_K_REDUCE);
+    multidot_kernel<double><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(w.r, n, w.r, n, hd + H_PART);
+    reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+    k.add(2);
+  }
+  Gmres G{ctx, m, w, st, n};
+  if (int rc = G.sync_host(&bnorm2, hd + H_NORM, sizeof(double))) return rc;
+  const double bnorm = std::sqrt(bnorm2);
+  if (bnorm == 0.0) {
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_fill_zero(w.x, sizeof(double) * n, st));
+    *iters_out = 0;
+    *rel_out = 0.0;
+    return VMS_OK;
+  }
+  if (!f32) {
+    int it = 0;
+    double rel = 0.0;
+    if (int rc = G.solve<double, double>(wk.values, w.r, w.x, bnorm, rtol, maxit, restart, &it, &rel)) return rc;
+    *iters_out = it;
+    *rel_out = rel;
+    return rel <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "GMRES reached maxit");
+  }
+  // mixed: x = 0; repeat { r = b - S x (FP64); solve S c = r with FP32 GMRES; x += c }
+  {
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_fill_zero(w.x, sizeof(double) * n, st));
+  }
+  int total = 0;
+  double rel = 1.0;
+  double* rfull = w.rfull;
+  float* bf = w.bf;
+  float* xf = w.xf;
+  int rc = VMS_OK;
+  for (int outer = 0; outer < 20 && total < maxit; ++outer) {
+    // FP64 residual of the refinement
+    { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, wk.values, w.x, rfull, st)); }
+    {
+      KScope k(ctx, VMS_K_KRYLOV);
+      axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.r, -1.0, rfull, rfull, n);
+      k.add(1);
+    }
+    double r2 = 0.0;
+    {
+      KScope k(ctx, VMS_K_REDUCE);
+      multidot_kernel<double><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(rfull, n, rfull, n, hd + H_PART);
+      reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+      k.add(2);
+    }
+    if ((rc = G.sync_host(&r2, hd + H_NORM, sizeof(double)))) break;
+    rel = std::sqrt(r2) / bnorm;
+    if (rel <= rtol) break;
+    {
+      KScope k(ctx, VMS_K_KRYLOV);
+      axpby_kernel<double, double, float><<<grid_for(n), 256, 0, st>>>(1.0, rfull, 0.0, (const double*)nullptr, bf, n);
+      k.add(1);
+    }
+    int it = 0;
+    double irel = 0.0;
+    const double inner = std::max(rtol / rel, 1e-3);
+    if ((rc = G.solve<float, float>(wk.values, bf, xf, std::sqrt(r2), std::min(inner, 0.5),
+                                    maxit - total, restart, &it, &irel)))
+      break;
+    total += it;
+    {
+      KScope k(ctx, VMS_K_KRYLOV);
+      axpby_kernel<double, float, double><<<grid_for(n), 256, 0, st>>>(1.0, w.x, 1.0, xf, w.x, n);
+      k.add(1);
+    }
+    if (it == 0) break;
+  }
+  if (rc) return rc;
+  *iters_out = total;
+  *rel_out = rel;
+  return rel <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "refined GMRES reached maxit");
+}
+
+static int recover_and_update(vms_ctx* ctx) {
+  const Mesh& m = ctx_mesh(ctx);
+  State& s = ctx_state(ctx);
+  Work& wk = ctx_work(ctx);
+  SolverWork& w = ctx_solver(ctx);
+  cudaStream_t st = ctx_stream(ctx);
+  KScope k(ctx, VMS_K_KRYLOV);
+  const unsigned eb = (unsigned)((m.n_elems + 127) / 128);
+  if (ctx_fp32(ctx))
+    recover_kernel<float><<<eb, 128, 0, st>>>(m.conn, (const float*)wk.recX, wk.recY, w.x, s.beta, m.n_elems);
+  else
+    recover_kernel<double><<<eb, 128, 0, st>>>(m.conn, (const double*)wk.recX, wk.recY, w.x, s.beta, m.n_elems);
+  const int64_t n = 4 * m.n_nodes;
+  double* u = reinterpret_cast<double*>(s.u);
+  axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, u, 1.0, w.x, u, n);
+  k.add(2);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // namespace vms
+
+using namespace vms;
+
+extern "C" {
+
+int vms_apply(vms_ctx* ctx, const double* x, double* y) {
+  if (!ctx || !x || !y) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
+  if (!ctx_work(ctx).assembled) return ctx_fail(ctx, VMS_ERR_STATE, "nothing assembled");
+  cudaSetDevice(ctx_device(ctx));
+  {
+    KScope k(ctx, VMS_K_SPMV);
+    k.add(launch_spmv(ctx_mesh(ctx), ctx_work(ctx).values, ctx_fp32(ctx), x, y, ctx_stream(ctx)));
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  return VMS_OK;
+}
+
+int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
+              double* rel) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx_work(ctx).assembled) return ctx_fail(ctx, VMS_ERR_STATE, "nothing assembled");
+  cudaSetDevice(ctx_device(ctx));
+  int it = 0;
+  double r = 0.0;
+  const int rc = linear_solve(ctx, rtol, maxit, restart, &it, &r);
+  if (iters) *iters = it;
+  if (rel) *rel = r;
+  if (rc != VMS_OK) return rc;
+  if (update) {
+    if (int rc2 = recover_and_update(ctx)) return rc2;
+    ctx_work(ctx).assembled = false;  // the state changed
+  }
+  const cudaError_t e = cudaStreamSynchronize(ctx_stream(ctx));
+  return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int vms_newton_step(vms_ctx* ctx, double* res_norm) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  double r = 0.0;
+  if (int rc = vms_residual(ctx, &r, nullptr)) return rc;
+  if (res_norm) *res_norm = r;
+  if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
+  int it = 0;
+  double rel = 0.0;
+  return vms_solve(ctx, 1e-10, 2000, 50, 1, &it, &rel);
+}
+
+int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist) {
+  if (!ctx || maxit < 0 || !(rtol > 0.0)) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid arguments");
+  double r0 = 0.0, r = 0.0;
+  if (int rc = vms_residual(ctx, &r0, nullptr)) return rc;
+  if (hist) hist[0] = r0;
+  r = r0;
+  int k = 0;
+  while (k < maxit && r > rtol * r0) {
+    if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
+    // inexact Newton: forcing term proportional to the current relative residual
+    const double eta = std::max(std::min(1e-2, 0.1 * r / r0), 1e-12);
+    int it = 0;
+    double rel = 0.0;
+    if (int rc = vms_solve(ctx, eta, 5000, 50, 1, &it, &rel)) return rc;
+    ++k;
+    if (int rc = vms_residual(ctx, &r, nullptr)) return rc;
+    if (hist) hist[k] = r;
+    if (!(r == r) || r > 1e6 * r0) {
+      if (iters) *iters = k;
+      return ctx_fail(ctx, VMS_ERR_NEWTON_DIVERGED, "Newton residual diverged");
+    }
+  }
+  if (iters) *iters = k;
+  if (r > rtol * r0) return ctx_fail(ctx, VMS_ERR_NEWTON_DIVERGED, "Newton reached maxit");
+  return VMS_OK;
+}
+
+}  // extern "C"

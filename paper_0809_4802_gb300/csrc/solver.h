@@ -1,0 +1,49 @@
+// Krylov solve, fine-scale recovery and Newton driver of the condensed system (Sections 4.2, 5, 6).
+#pragma once
+
+#include "vms_internal.h"
+
+namespace vms {
+
+struct SolverWork {
+  double* x = nullptr;       // n
+  double* r = nullptr;       // n
+  double* V = nullptr;       // (restart + 1) * n Krylov basis
+  double* Z = nullptr;       // n preconditioned vector (FP32 views in mixed mode)
+  double* Dinv = nullptr;    // n_nodes * 16: inverted 4x4 diagonal node blocks
+  double* h = nullptr;       // device scalars for dots
+  double* rfull = nullptr;   // n: FP64 refinement residual (mixed)
+  float* bf = nullptr;       // n: FP32 right-hand side of the inner solve (mixed)
+  float* xf = nullptr;       // n: FP32 inner correction (mixed)
+  int restart = 0;
+  int64_t n = 0;
+};
+
+void free_solver(SolverWork& s);
+
+// accessors defined in api.cu
+const Mesh& ctx_mesh(vms_ctx* c);
+State& ctx_state(vms_ctx* c);
+Work& ctx_work(vms_ctx* c);
+SolverWork& ctx_solver(vms_ctx* c);
+cudaStream_t ctx_stream(vms_ctx* c);
+int ctx_device(vms_ctx* c);
+bool ctx_fp32(vms_ctx* c);
+double* ctx_dscalar(vms_ctx* c);
+double* ctx_hscalar(vms_ctx* c);
+int ctx_fail(vms_ctx* c, int code, const char* msg);
+int ctx_flags_check(vms_ctx* c);
+
+// Kernel accounting: counts the launches made inside the scope under `kind` and, when timing is
+// enabled on the context, brackets them with CUDA events on the context's stream.
+struct KScope {
+  vms_ctx* c;
+  int kind;
+  int n = 0;
+  cudaEvent_t a = nullptr;
+  KScope(vms_ctx* c, int kind);
+  ~KScope();
+  void add(int launches) { n += launches; }
+};
+
+}  // namespace vms

@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of libvms_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vms.h"
+
+struct vms_ctx;
+
+namespace vms {
+
+// Error flags raised by kernels (bitwise OR into a device word, read back by the host).
+enum : unsigned int {
+  FLAG_NEG_JACOBIAN = 1u,
+  FLAG_SINGULAR_KFF = 2u,
+  FLAG_NAN = 4u,
+};
+
+// Reference-element tables for one Gauss rule (device memory owned by the context).
+constexpr int MAX_QP = 64;  // quad_order <= 4
+
+// Per-quadrature-point table row (FP64): coordinates and products for the modal (monomial)
+// evaluation of trilinear fields, the bubble, its reference gradient and the weight.
+struct QpRow {
+  double xi, eta, zeta, xe, xz, ez, xez;  // xi, eta, zeta, xi*eta, xi*zeta, eta*zeta, xi*eta*zeta
+  double b, db0, db1, db2;                 // bubble (times bubble_scale) and its reference gradient
+  double w;                                // Gauss weight
+};
+
+// Scalar parameters passed by value to the element kernels.
+struct KParams {
+  double nut;    // visc_factor * nu
+  double tau;    // 1/dt or 0
+  double f[3];   // body force
+  int nq;        // number of quadrature points
+  int transient; // tau != 0
+  int has_force; // f != 0
+};
+
+// The once-per-mesh pattern (host side, built by pattern.cpp).
+struct HostPattern {
+  std::vector<int32_t> rowptr;    // 4*n_nodes + 1
+  std::vector<int32_t> colidx;    // nnz
+  std::vector<int32_t> blk;       // n_elems * 64: value offset of block (a,b), row 4*na, col 4*nb
+  std::vector<int32_t> rowlen;    // n_nodes: entries per row of node n (4 * neighbours)
+  std::vector<int32_t> colour;    // n_elems
+  std::vector<int32_t> colour_order;  // elements sorted by colour
+  std::vector<int32_t> colour_start;  // n_colours + 1
+  std::vector<int64_t> diag_pos;  // per constrained dof: value index of its diagonal entry
+  std::vector<uint32_t> dir_mask; // per element: bit 4a+c set if that coarse dof is constrained
+  int n_colours = 0;
+};
+
+// Builds the CSR pattern, block map, colouring and Dirichlet masks. Returns "" or an error text.
+std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn, int64_t n_dir,
+                          const int64_t* dir_dof, HostPattern& out);
+
+// ---- device data and kernel launchers ----------------------------------------------------------
+
+struct Mesh {
+  int64_t n_nodes = 0, n_elems = 0, nnz = 0;
+  double4_32a* xyz = nullptr;        // n_nodes (x, y, z, 0)
+  int32_t* conn = nullptr;       // n_elems * 8
+  int32_t* rowptr = nullptr;     // 4 n_nodes + 1
+  int32_t* colidx = nullptr;     // nnz
+  int32_t* blk = nullptr;        // n_elems * 64
+  int32_t* rowlen = nullptr;     // n_nodes
+  uint32_t* dir_mask = nullptr;  // n_elems
+  int64_t n_dir = 0;
+  int64_t* dir_dof = nullptr;    // n_dir
+  double* dir_val = nullptr;     // n_dir
+  int64_t* diag_pos = nullptr;   // n_dir
+  int32_t* colour_order = nullptr;
+  std::vector<int32_t> colour_start;
+  int n_colours = 0;
+};
+
+struct State {
+  double4_32a* u = nullptr;       // n_nodes (v0, v1, v2, p)
+  double4_32a* u_prev = nullptr;  // n_nodes
+  double* beta = nullptr;     // n_elems * 3
+  bool valid = false;
+};
+
+struct Work {
+  void* values = nullptr;     // nnz (double or float)
+  double* rhs = nullptr;      // 4 n_nodes
+  double* elemR = nullptr;    // n_elems * 36: R_cp (32), R_f (3), pad
+  void* recX = nullptr;       // n_elems * 96 (T): K_ff^-1 K_fc
+  double* recY = nullptr;     // n_elems * 3: K_ff^-1 R_f
+  double* resid = nullptr;    // 4 n_nodes + 3 n_elems
+  double* partial = nullptr;  // reduction partials
+  unsigned int* flags = nullptr;
+  bool assembled = false;
+};
+
+// Element residual (FP64, modal evaluation). mode 0: write elemR[36*e + ...] (R_cp 32, R_f 3);
+// mode 1: accumulate the assembled residual into resid (4 n_nodes + 3 n_elems entries).
+int launch_residual(const Mesh& m, const State& s, const KParams& kp, const QpRow* qp,
+                     double* elemR, double* resid, int64_t first, int64_t count, int mode,
+                     unsigned int* flags, cudaStream_t st);
+
+// Element tangent + condensation + scatter (warp per element). T = double or float.
+struct TangentOut {
+  // scatter targets (assembly)
+  void* values = nullptr; double* rhs = nullptr;
+  void* recX = nullptr; double* recY = nullptr;
+  // element outputs (parity), FP64, may be null
+  double *S = nullptr, *r = nullptr, *Kcc = nullptr, *Kcf = nullptr, *Kfc = nullptr,
+         *Kff = nullptr;
+};
+int launch_tangent(bool fp32, const Mesh& m, const State& s, const KParams& kp,
+                    const void* tab, const double* elemR, const TangentOut& out, int64_t first,
+                    int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
+                    unsigned int* flags, cudaStream_t st);
+
+int launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
+int launch_dirichlet_diag(const Mesh& m, void* values, bool fp32, double* rhs, cudaStream_t st);
+int launch_zero_dofs(const int64_t* dofs, int64_t n, double* v, cudaStream_t st);
+int launch_impose(const Mesh& m, double4_32a* u, cudaStream_t st);
+// sum of squares of v[0..n) -> *out (device double), two passes through `partial` (>= 512)
+int launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t st);
+int launch_spmv(const Mesh& m, const void* values, bool fp32, const double* x, double* y,
+                 cudaStream_t st);
+
+}  // namespace vms

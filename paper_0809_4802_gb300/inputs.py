@@ -109,6 +109,32 @@ def _lattice(nx: int, ny: int, nz: int, lo, hi, keep_elem=None) -> Mesh:
                 meta={"dims": (nx, ny, nz), "h": h, "lo": lo, "hi": hi})
 
 
+def box_mesh(nx: int, ny: int, nz: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+             jitter_frac: float = 0.0, seed: int = 0, hole=None) -> Mesh:
+    """Lattice of nx*ny*nz hexahedra on the box [lo, hi]; `hole` = ((i0,i1),(j0,j1),(k0,k1))
+    removes the elements with lattice indices in those half-open ranges."""
+    keep = None
+    if hole is not None:
+        (i0, i1), (j0, j1), (k0, k1) = hole
+        keep = lambda i, j, k: ~((i >= i0) & (i < i1) & (j >= j0) & (j < j1) & (k >= k0) & (k < k1))  # noqa: E731
+    m = _lattice(nx, ny, nz, lo, hi, keep_elem=keep)
+    m.name = f"box{nx}x{ny}x{nz}"
+    if jitter_frac > 0:
+        jitter(m, jitter_frac, np.random.Generator(np.random.PCG64(seed)))
+    return m
+
+
+def wall_bc(mesh: Mesh, values=(0.0, 0.0, 0.0), pin_pressure_node: int | None = None) -> Dirichlet:
+    """Every velocity component prescribed on every boundary node; optionally one pressure pin."""
+    walls = np.nonzero(boundary_nodes(mesh))[0]
+    dofs = [4 * walls + c for c in range(3)]
+    vals = [np.full(walls.size, float(values[c])) for c in range(3)]
+    if pin_pressure_node is not None:
+        dofs.append(np.array([4 * pin_pressure_node + 3]))
+        vals.append(np.zeros(1))
+    return _dirichlet(dofs, vals)
+
+
 def boundary_nodes(mesh: Mesh) -> np.ndarray:
     """Boolean mask of nodes on the domain boundary (fewer than 8 incident hexahedra)."""
     count = np.bincount(mesh.conn.ravel().astype(np.int64), minlength=mesh.n_nodes)
@@ -135,7 +161,6 @@ def _dirichlet(dofs: list, vals: list) -> Dirichlet:
     d = np.concatenate(dofs).astype(np.int64)
     v = np.concatenate(vals).astype(np.float64)
     # later entries take precedence for duplicated dofs
-    order = np.arange(d.size)
     _, last = np.unique(d[::-1], return_index=True)
     keep = (d.size - 1 - last)
     keep.sort()

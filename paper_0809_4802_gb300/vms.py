@@ -1,0 +1,273 @@
+"""Thin ctypes binding of the C-ABI in include/vms.h (argument marshalling only).
+
+Every computation runs in the CUDA library libvms_gb300.so; if the library is missing this module
+raises on load. Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they are
+passed as raw pointers after a dtype and contiguity check.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvms_gb300.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_OUT_OF_MEMORY = -3
+ERR_NEG_JACOBIAN = -4
+ERR_SINGULAR_KFF = -5
+ERR_NAN = -6
+ERR_KRYLOV_MAXIT = -7
+ERR_NEWTON_DIVERGED = -8
+ERR_STATE = -9
+ERR_UNSUPPORTED = -10
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+SCATTER_ATOMIC = 0
+SCATTER_COLOUR = 1
+
+# every symbol include/vms.h declares
+EXPORTS = [
+    "vms_create", "vms_destroy", "vms_set_stream", "vms_mesh_upload", "vms_set_params",
+    "vms_state_upload", "vms_state_download", "vms_assemble_newton_schur", "vms_get_csr",
+    "vms_residual", "vms_element_matrices", "vms_apply", "vms_solve", "vms_newton_step",
+    "vms_newton_solve", "vms_last_error", "vms_version", "vms_profile_enable", "vms_profile_read",
+]
+K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov"]
+
+
+class VmsParams(ctypes.Structure):
+    _fields_ = [("nu", c_double), ("visc_factor", c_double), ("dt", c_double),
+                ("f", c_double * 3), ("bubble_scale", c_double), ("quad_order", c_int32),
+                ("scatter_mode", c_int32)]
+
+
+class CsrView(ctypes.Structure):
+    _fields_ = [("n_rows", c_int64), ("nnz", c_int64), ("rowptr", c_void_p), ("colidx", c_void_p),
+                ("values", c_void_p), ("rhs", c_void_p), ("values_dtype", c_int32),
+                ("n_colours", c_int32)]
+
+
+class VmsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"vms error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libvms_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_0809_4802_gb300.build`")
+    lib = ctypes.CDLL(path)
+    p = c_void_p
+    sig = {
+        "vms_create": (c_int, [POINTER(c_void_p), c_int, c_int]),
+        "vms_destroy": (c_int, [p]),
+        "vms_set_stream": (c_int, [p, p]),
+        "vms_mesh_upload": (c_int, [p, c_int64, p, c_int64, p, c_int64, p, p]),
+        "vms_set_params": (c_int, [p, POINTER(VmsParams)]),
+        "vms_state_upload": (c_int, [p, p, p, p]),
+        "vms_state_download": (c_int, [p, p, p]),
+        "vms_assemble_newton_schur": (c_int, [p, POINTER(CsrView)]),
+        "vms_get_csr": (c_int, [p, POINTER(CsrView)]),
+        "vms_residual": (c_int, [p, POINTER(c_double), p]),
+        "vms_element_matrices": (c_int, [p, c_int64, c_int64] + [p] * 8),
+        "vms_apply": (c_int, [p, p, p]),
+        "vms_solve": (c_int, [p, c_double, c_int, c_int, c_int, POINTER(c_int), POINTER(c_double)]),
+        "vms_newton_step": (c_int, [p, POINTER(c_double)]),
+        "vms_newton_solve": (c_int, [p, c_double, c_int, POINTER(c_int), p]),
+        "vms_last_error": (c_char_p, [p]),
+        "vms_version": (c_char_p, []),
+        "vms_profile_enable": (c_int, [p, c_int]),
+        "vms_profile_read": (c_int, [p, c_int, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, dtype, n=None, writable=False):
+    """Raw pointer of a numpy array or torch tensor with the expected dtype (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        if writable and not a.flags["WRITEABLE"]:
+            raise TypeError("array is read-only")
+        if n is not None and a.size != n:
+            raise ValueError(f"expected {n} entries, got {a.size}")
+        return a.ctypes.data
+    import torch  # noqa: PLC0415
+    if isinstance(a, torch.Tensor):
+        tmap = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64,
+                np.float32: torch.float32}
+        if a.dtype != tmap[np.dtype(dtype).type] or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {np.dtype(dtype)} tensor")
+        if n is not None and a.numel() != n:
+            raise ValueError(f"expected {n} entries, got {a.numel()}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class DeviceArray:
+    """A borrowed device buffer exposed through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+        self._owner = owner
+
+
+class Context:
+    """One library context (one GPU, one precision mode)."""
+
+    def __init__(self, device: int = 0, precision: int = PREC_FP64):
+        self.lib = load_library()
+        h = c_void_p()
+        rc = self.lib.vms_create(byref(h), device, precision)
+        if rc != OK:
+            raise VmsError(rc, "vms_create failed")
+        self.h = h
+        self.precision = precision
+        self.n_nodes = self.n_elems = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vms_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise VmsError(rc, self.lib.vms_last_error(self.h).decode())
+        return rc
+
+    # -- setup -------------------------------------------------------------------------------
+    def set_stream(self, stream_handle: int):
+        self._check(self.lib.vms_set_stream(self.h, c_void_p(stream_handle)))
+
+    def set_params(self, nu, visc_factor=2.0, dt=0.0, f=(0.0, 0.0, 0.0), bubble_scale=1.0,
+                   quad_order=3, scatter_mode=SCATTER_ATOMIC):
+        p = VmsParams(nu, visc_factor, dt, (c_double * 3)(*f), bubble_scale, quad_order,
+                      scatter_mode)
+        self._check(self.lib.vms_set_params(self.h, byref(p)))
+
+    def mesh_upload(self, xyz, conn, dir_dofs, dir_vals):
+        n_nodes = int(xyz.shape[0])
+        n_elems = int(conn.shape[0])
+        n_dir = int(dir_dofs.shape[0]) if dir_dofs is not None else 0
+        self._check(self.lib.vms_mesh_upload(
+            self.h, n_nodes, _ptr(xyz, np.float64, 3 * n_nodes), n_elems,
+            _ptr(conn, np.int32, 8 * n_elems), n_dir,
+            _ptr(dir_dofs, np.int64, n_dir) if n_dir else None,
+            _ptr(dir_vals, np.float64, n_dir) if n_dir else None))
+        self.n_nodes, self.n_elems = n_nodes, n_elems
+
+    def state_upload(self, u, beta=None, u_prev=None):
+        self._check(self.lib.vms_state_upload(
+            self.h, _ptr(u, np.float64, 4 * self.n_nodes),
+            _ptr(beta, np.float64, 3 * self.n_elems), _ptr(u_prev, np.float64, 4 * self.n_nodes)))
+
+    def state_download(self):
+        u = np.empty((self.n_nodes, 4))
+        beta = np.empty((self.n_elems, 3))
+        self._check(self.lib.vms_state_download(self.h, u.ctypes.data, beta.ctypes.data))
+        return u, beta
+
+    # -- the hot path ---------------------------------------------------------------------
+    def assemble(self) -> CsrView:
+        v = CsrView()
+        self._check(self.lib.vms_assemble_newton_schur(self.h, byref(v)))
+        return v
+
+    def csr(self) -> CsrView:
+        v = CsrView()
+        self._check(self.lib.vms_get_csr(self.h, byref(v)))
+        return v
+
+    def csr_device(self, view: CsrView | None = None):
+        """(rowptr, colidx, values, rhs) as zero-copy torch CUDA tensors of the last assembly."""
+        import torch  # noqa: PLC0415
+        v = view or self.csr()
+        vt = "<f4" if v.values_dtype == 1 else "<f8"
+        mk = lambda ptr, n, t: torch.as_tensor(DeviceArray(ptr, (n,), t, self), device="cuda")  # noqa: E731
+        return (mk(v.rowptr, v.n_rows + 1, "<i4"), mk(v.colidx, v.nnz, "<i4"),
+                mk(v.values, v.nnz, vt), mk(v.rhs, v.n_rows, "<f8"))
+
+    def csr_host(self):
+        rowptr, colidx, vals, rhs = self.csr_device()
+        return (rowptr.cpu().numpy(), colidx.cpu().numpy(), vals.cpu().numpy(), rhs.cpu().numpy())
+
+    def residual(self, want_vector=False):
+        norm = c_double()
+        R = np.empty(4 * self.n_nodes + 3 * self.n_elems) if want_vector else None
+        self._check(self.lib.vms_residual(self.h, byref(norm), _ptr(R, np.float64)))
+        return (norm.value, R) if want_vector else norm.value
+
+    def element_matrices(self, first, count, blocks=True):
+        out = {"S": np.empty((count, 32, 32)), "r": np.empty((count, 32))}
+        if blocks:
+            out.update(Kcc=np.empty((count, 32, 32)), Kcf=np.empty((count, 32, 3)),
+                       Kfc=np.empty((count, 3, 32)), Kff=np.empty((count, 3, 3)),
+                       Rcp=np.empty((count, 32)), Rf=np.empty((count, 3)))
+        g = lambda k: out[k].ctypes.data if k in out else None  # noqa: E731
+        self._check(self.lib.vms_element_matrices(self.h, first, count, g("S"), g("r"), g("Kcc"),
+                                                  g("Kcf"), g("Kfc"), g("Kff"), g("Rcp"), g("Rf")))
+        return out
+
+    def apply(self, x, y):
+        self._check(self.lib.vms_apply(self.h, _ptr(x, np.float64), _ptr(y, np.float64)))
+
+    def solve(self, rtol=1e-12, maxit=50, restart=50, update=True):
+        it = c_int()
+        rel = c_double()
+        self._check(self.lib.vms_solve(self.h, rtol, maxit, restart, int(update), byref(it),
+                                       byref(rel)))
+        return it.value, rel.value
+
+    def newton_step(self):
+        r = c_double()
+        self._check(self.lib.vms_newton_step(self.h, byref(r)))
+        return r.value
+
+    def newton_solve(self, rtol=1e-8, maxit=20):
+        it = c_int()
+        hist = np.zeros(maxit + 1)
+        self._check(self.lib.vms_newton_solve(self.h, rtol, maxit, byref(it), hist.ctypes.data))
+        return it.value, hist[: it.value + 1]
+
+    # -- kernel accounting ----------------------------------------------------------------
+    def profile_enable(self, timing: bool = True):
+        self._check(self.lib.vms_profile_enable(self.h, int(timing)))
+
+    def profile_read(self, reset: bool = True):
+        """{kind: (milliseconds, launches)} accumulated since the last reset."""
+        ms = np.zeros(len(K_NAMES))
+        n = np.zeros(len(K_NAMES), np.int64)
+        self._check(self.lib.vms_profile_read(self.h, int(reset), ms.ctypes.data, n.ctypes.data))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(K_NAMES)}
+
+
+def version() -> str:
+    return load_library().vms_version().decode()
