@@ -49,10 +49,12 @@ static cudaEvent_t take_event(vms_ctx* c) {
   return e;
 }
 
-KScope::KScope(vms_ctx* ctx, int k) : c(ctx), kind(k) {
+KScope::KScope(vms_ctx* ctx, int k) : KScope(ctx, k, ctx->stream) {}
+
+KScope::KScope(vms_ctx* ctx, int k, cudaStream_t stream) : c(ctx), kind(k), s(stream) {
   if (c->timing) {
     a = take_event(c);
-    cudaEventRecord(a, c->stream);
+    cudaEventRecord(a, s);
   }
 }
 
@@ -60,7 +62,7 @@ KScope::~KScope() {
   c->launches[kind] += n;
   if (a) {
     cudaEvent_t b = take_event(c);
-    cudaEventRecord(b, c->stream);
+    cudaEventRecord(b, s);
     c->events.push_back({kind, a, b});
   }
 }
@@ -97,9 +99,13 @@ void free_mesh(vms_ctx* c) {
   dfree(s.u); dfree(s.u_prev); dfree(s.beta);
   s = State();
   Work& w = c->work;
-  dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recY); dfree(w.resid);
-  dfree(w.partial); dfree(w.flags);
+  dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recW); dfree(w.recKinv);
+  dfree(w.recY); dfree(w.resid); dfree(w.partial); dfree(w.flags);
+  dfree(w.f32.xyz); dfree(w.f32.u); dfree(w.f32.beta);
+  cudaStream_t aux = w.aux;
+  cudaEvent_t fork = w.fork, join = w.join;
   w = Work();
+  w.aux = aux; w.fork = fork; w.join = join;
   free_solver(c->solver);
 }
 
@@ -238,7 +244,10 @@ int vms_create(vms_ctx** out, int device, int precision) {
   ctx->params.bubble_scale = 1.0;
   ctx->params.quad_order = 3;
   ctx->params.scatter_mode = VMS_SCATTER_ATOMIC;
-  if (cudaMallocHost(&ctx->h_flags, sizeof(unsigned int)) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&ctx->work.aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->work.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->work.join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_flags, sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_scalar, 8 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ctx->d_scalar, 8 * sizeof(double)) != cudaSuccess ||
       upload_tables(ctx) != VMS_OK) {
@@ -257,6 +266,9 @@ int vms_destroy(vms_ctx* ctx) {
   for (auto& e : ctx->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_scalar);
+  if (ctx->work.aux) { cudaStreamSynchronize(ctx->work.aux); cudaStreamDestroy(ctx->work.aux); }
+  if (ctx->work.fork) cudaEventDestroy(ctx->work.fork);
+  if (ctx->work.join) cudaEventDestroy(ctx->work.join);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
   delete ctx;
@@ -340,7 +352,18 @@ int vms_mesh_upload(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_
   CK(cudaMalloc(&w.rhs, sizeof(double) * 4 * n_nodes));
   CK(cudaMalloc(&w.elemR, sizeof(double) * 36 * n_elems));
   CK(cudaMalloc(&w.recX, sizeof(double) * 96 * n_elems));
+  CK(cudaMalloc(&w.recW, sizeof(double) * 96 * n_elems));
+  CK(cudaMalloc(&w.recKinv, sizeof(double) * 9 * n_elems));
   CK(cudaMalloc(&w.recY, sizeof(double) * 3 * n_elems));
+  CK(cudaMalloc(&w.f32.xyz, sizeof(float4) * n_nodes));
+  CK(cudaMalloc(&w.f32.u, sizeof(float4) * n_nodes));
+  CK(cudaMalloc(&w.f32.beta, sizeof(float) * 3 * n_elems));
+  {
+    // FP32 coordinates once per mesh (the mixed-precision tangent reads them)
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_to_fp32(m, s, w.f32, true, ctx->stream));
+  }
+  CK(cudaGetLastError());
   CK(cudaMalloc(&w.resid, sizeof(double) * (4 * n_nodes + 3 * n_elems)));
   CK(cudaMalloc(&w.partial, sizeof(double) * 1024));
   CK(cudaMalloc(&w.flags, sizeof(unsigned int)));
@@ -406,24 +429,47 @@ int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out) {
     k.add(launch_fill_zero(w.rhs, sizeof(double) * 4 * m.n_nodes, st));
     k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st));
   }
+  if (f32) {
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_to_fp32(m, ctx->state, w.f32, false, st));
+  }
+  TangentOut o;
+  o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv;
+  o.recY = w.recY;
+  const void* tab = f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64;
+  const bool colour = ctx->params.scatter_mode == VMS_SCATTER_COLOUR;
+  // the FP64 residual kernel (this stream) and the tangent kernel (auxiliary stream, FP32 or FP64
+  // pipe) are independent and run concurrently; the finish kernel joins them
+  CK(cudaEventRecord(w.fork, st));
+  CK(cudaStreamWaitEvent(w.aux, w.fork, 0));
   {
     KScope k(ctx, VMS_K_RESIDUAL);
     k.add(launch_residual(m, ctx->state, kp, ctx->d_qp, w.elemR, nullptr, 0, m.n_elems, 0, w.flags, st));
   }
-  TangentOut o;
-  o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recY = w.recY;
-  const void* tab = f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64;
   {
-    KScope k(ctx, VMS_K_TANGENT);
-    if (ctx->params.scatter_mode == VMS_SCATTER_COLOUR) {
+    KScope k(ctx, VMS_K_TANGENT, w.aux);
+    if (colour) {
       for (int c = 0; c < m.n_colours; ++c) {
         const int64_t b = m.colour_start[c], n = m.colour_start[c + 1] - b;
-        k.add(launch_tangent(f32, m, ctx->state, kp, tab, w.elemR, o, b, n, m.colour_order, false,
-                             false, w.flags, st));
+        k.add(launch_tangent(f32, m, ctx->state, w.f32, kp, tab, o, b, n, m.colour_order, false,
+                             false, w.flags, w.aux));
       }
     } else {
-      k.add(launch_tangent(f32, m, ctx->state, kp, tab, w.elemR, o, 0, m.n_elems, nullptr, false,
-                           true, w.flags, st));
+      k.add(launch_tangent(f32, m, ctx->state, w.f32, kp, tab, o, 0, m.n_elems, nullptr, false,
+                           true, w.flags, w.aux));
+    }
+  }
+  CK(cudaEventRecord(w.join, w.aux));
+  CK(cudaStreamWaitEvent(st, w.join, 0));
+  {
+    KScope k(ctx, VMS_K_DIRICHLET);
+    if (colour) {
+      for (int c = 0; c < m.n_colours; ++c) {
+        const int64_t b = m.colour_start[c], n = m.colour_start[c + 1] - b;
+        k.add(launch_finish(f32, m, w.elemR, o, b, n, m.colour_order, false, st));
+      }
+    } else {
+      k.add(launch_finish(f32, m, w.elemR, o, 0, m.n_elems, nullptr, true, st));
     }
   }
   { KScope k(ctx, VMS_K_DIRICHLET); k.add(launch_dirichlet_diag(m, w.values, f32, w.rhs, st)); }
@@ -483,6 +529,10 @@ int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, 
   const KParams kp = kparams(ctx);
   const bool f32 = fp32_mode(ctx);
   { KScope k(ctx, VMS_K_FILL); k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st)); }
+  if (f32) {
+    KScope k(ctx, VMS_K_FILL);
+    k.add(launch_to_fp32(m, ctx->state, w.f32, false, st));
+  }
   {
     KScope k(ctx, VMS_K_RESIDUAL);
     k.add(launch_residual(m, ctx->state, kp, ctx->d_qp, w.elemR, nullptr, first, count, 0, w.flags, st));
@@ -493,11 +543,16 @@ int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, 
   TangentOut o;
   o.S = buf; o.r = buf + 1024 * count; o.Kcc = buf + 1056 * count; o.Kcf = buf + 2080 * count;
   o.Kfc = buf + 2176 * count; o.Kff = buf + 2272 * count;
+  o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv; o.recY = w.recY;
   {
     KScope k(ctx, VMS_K_TANGENT);
-    k.add(launch_tangent(f32, m, ctx->state, kp,
-                         f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64, w.elemR, o,
-                         first, count, nullptr, true, true, w.flags, st));
+    k.add(launch_tangent(f32, m, ctx->state, w.f32, kp,
+                         f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64, o, first,
+                         count, nullptr, true, true, w.flags, st));
+  }
+  {
+    KScope k(ctx, VMS_K_DIRICHLET);
+    k.add(launch_finish(f32, m, w.elemR, o, first, count, nullptr, true, st));
   }
   cudaError_t e = cudaGetLastError();
   struct Out { double* dst; double* src; size_t n; } outs[6] = {

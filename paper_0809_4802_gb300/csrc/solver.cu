@@ -200,8 +200,7 @@ __global__ void combine_kernel(const VT* __restrict__ V, int64_t ld, const doubl
 
 // out = a * x + b * y (mixed vector types)
 template <typename A, typename B, typename C>
-__global__ void axpby_kernel(double a, const A* __restrict__ x, double b, const B* __restrict__ y,
-                             C* __restrict__ out, int64_t n) {
+__global__ void axpby_kernel(double a, const A* x, double b, const B* y, C* out, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = C(a * (double)x[i] + (y ? b * (double)y[i] : 0.0));
@@ -255,11 +254,11 @@ struct Gmres {
     VT* z = reinterpret_cast<VT*>(w.Z);
     double* hd = w.h;
     std::vector<double> H((restart + 1) * restart, 0.0), cs(restart), sn(restart), g(restart + 1);
-    std::vector<double> hh(restart + 2);
-    KScope zs(ctx, VMS_K_FILL);
-    zs.add(1);
-    axpby_kernel<double, double, VT><<<grid_for(n), 256, 0, st>>>(0.0, (const double*)nullptr, 0.0,
-                                                                   (const double*)nullptr, x, n);
+    std::vector<double> hh(restart + 2), hcol(H_NORM + 1);
+    {
+      KScope zs(ctx, VMS_K_FILL);
+      zs.add(launch_fill_zero(x, sizeof(VT) * n, st));
+    }
     int it = 0;
     double res = bnorm;
     // r0 = b (x = 0)
@@ -322,13 +321,10 @@ struct Gmres {
           scale_kernel<VT><<<grid_for(n), 256, 0, st>>>(vn, hd + H_NORM, vn, n);
           k.add(1);
         }
-        // bring the Hessenberg column to the host
-        std::vector<double> h1(kk), h2(kk);
-        double nrm2 = 0.0;
-        if (int rc2 = sync_host(h1.data(), hd + H_PASS1, sizeof(double) * kk)) return rc2;
-        if (int rc2 = sync_host(h2.data(), hd + H_PASS2, sizeof(double) * kk)) return rc2;
-        if (int rc2 = sync_host(&nrm2, hd + H_NORM, sizeof(double))) return rc2;
-        for (int i = 0; i < kk; ++i) hh[i] = h1[i] + h2[i];
+        // bring the Hessenberg column (both passes and the norm) to the host in one copy
+        if (int rc2 = sync_host(hcol.data(), hd, sizeof(double) * (H_NORM + 1))) return rc2;
+        const double nrm2 = hcol[H_NORM];
+        for (int i = 0; i < kk; ++i) hh[i] = hcol[H_PASS1 + i] + hcol[H_PASS2 + i];
         hh[kk] = std::sqrt(nrm2);
         // apply previous rotations, then a new one
         for (int i = 0; i < j; ++i) {
@@ -560,16 +556,23 @@ int vms_apply(vms_ctx* ctx, const double* x, double* y) {
   return VMS_OK;
 }
 
-int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
-              double* rel) {
+}  // extern "C"
+
+namespace vms {
+
+// Solve, then (if update) recover the bubble increments and update the state. A solve that stops
+// at maxit is still applied when its relative residual is below accept_below (inexact Newton).
+static int solve_impl(vms_ctx* ctx, double rtol, int maxit, int restart, int update,
+                      double accept_below, int* iters, double* rel) {
   if (!ctx) return VMS_ERR_INVALID_ARG;
   if (!ctx_work(ctx).assembled) return ctx_fail(ctx, VMS_ERR_STATE, "nothing assembled");
   cudaSetDevice(ctx_device(ctx));
   int it = 0;
   double r = 0.0;
-  const int rc = linear_solve(ctx, rtol, maxit, restart, &it, &r);
+  int rc = linear_solve(ctx, rtol, maxit, restart, &it, &r);
   if (iters) *iters = it;
   if (rel) *rel = r;
+  if (rc == VMS_ERR_KRYLOV_MAXIT && r < accept_below) rc = VMS_OK;
   if (rc != VMS_OK) return rc;
   if (update) {
     if (int rc2 = recover_and_update(ctx)) return rc2;
@@ -577,6 +580,15 @@ int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int
   }
   const cudaError_t e = cudaStreamSynchronize(ctx_stream(ctx));
   return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // namespace vms
+
+extern "C" {
+
+int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
+              double* rel) {
+  return solve_impl(ctx, rtol, maxit, restart, update, 0.0, iters, rel);
 }
 
 int vms_newton_step(vms_ctx* ctx, double* res_norm) {
@@ -587,7 +599,7 @@ int vms_newton_step(vms_ctx* ctx, double* res_norm) {
   if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
   int it = 0;
   double rel = 0.0;
-  return vms_solve(ctx, 1e-10, 2000, 50, 1, &it, &rel);
+  return solve_impl(ctx, 1e-10, 2000, 50, 1, 0.1, &it, &rel);
 }
 
 int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist) {
@@ -603,7 +615,7 @@ int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* h
     const double eta = std::max(std::min(1e-2, 0.1 * r / r0), 1e-12);
     int it = 0;
     double rel = 0.0;
-    if (int rc = vms_solve(ctx, eta, 5000, 50, 1, &it, &rel)) return rc;
+    if (int rc = solve_impl(ctx, eta, 2000, 50, 1, 0.1, &it, &rel)) return rc;
     ++k;
     if (int rc = vms_residual(ctx, &r, nullptr)) return rc;
     if (hist) hist[k] = r;

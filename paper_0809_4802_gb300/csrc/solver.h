@@ -41,7 +41,9 @@ struct KScope {
   int kind;
   int n = 0;
   cudaEvent_t a = nullptr;
+  cudaStream_t s = nullptr;
   KScope(vms_ctx* c, int kind);
+  KScope(vms_ctx* c, int kind, cudaStream_t stream);
   ~KScope();
   void add(int launches) { n += launches; }
 };

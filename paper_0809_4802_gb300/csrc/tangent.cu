@@ -1,5 +1,10 @@
 // Element tangent, Schur condensation and scatter-add into the CSR system (Sections 4.2 and 5).
 // One warp per element; the phases are in tangent_math.cuh.
+//
+// The tangent kernel does not read the residual: it stores, per element, X = K_ff^-1 K_fc,
+// W = K_cf K_ff^-1 and K_ff^-1, and the FP64 finish kernel forms r_e = R_cp - W R_f and
+// y = K_ff^-1 R_f once both the residual and the tangent kernels are done. The two element
+// kernels are therefore independent and run concurrently (FP64 pipe and FP32 pipe).
 #include "tangent_math.cuh"
 #include "vms_internal.h"
 
@@ -25,17 +30,21 @@ __device__ __forceinline__ void scatter_add(double* p, double v, bool atomic) {
   if (atomic) atomicAdd(p, v); else *p += v;
 }
 
+// Node records in the tangent's arithmetic type (FP64 mode reads the FP64 state directly).
+template <typename T> struct NodeVec;
+template <> struct NodeVec<double> { using type = double4_32a; };
+template <> struct NodeVec<float> { using type = float4; };
+
 template <typename T, bool ELEM_OUT, bool ATOMIC>
 __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
-    const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u,
-    const int32_t* __restrict__ conn, const double* __restrict__ beta,
-    const double* __restrict__ elemR, const T* __restrict__ gtab, int nq, T nut, T tau,
-    int64_t first, int64_t count, const int32_t* __restrict__ elem_list,
+    const typename NodeVec<T>::type* __restrict__ xyz, const typename NodeVec<T>::type* __restrict__ u,
+    const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
+    int nq, T nut, T tau, int64_t first, int64_t count, const int32_t* __restrict__ elem_list,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
-    const uint32_t* __restrict__ dir_mask, T* __restrict__ values, double* __restrict__ rhs,
-    T* __restrict__ recX, double* __restrict__ recY, double* __restrict__ oS,
-    double* __restrict__ oR, double* __restrict__ oKcc, double* __restrict__ oKcf,
-    double* __restrict__ oKfc, double* __restrict__ oKff, unsigned int* __restrict__ flags) {
+    const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
+    T* __restrict__ recW, double* __restrict__ recKinv, double* __restrict__ oS,
+    double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
+    double* __restrict__ oKff, unsigned int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* st = reinterpret_cast<T*>(smem);
   for (int i = threadIdx.x; i < 37 * nq; i += blockDim.x) st[i] = gtab[i];
@@ -51,17 +60,15 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
     if (lane < 8) {
       const int nd = conn[8 * e + lane];
       W.nd[lane] = nd;
-      const double4_32a x = xyz[nd];
-      const double4_32a w = u[nd];
-      W.X[lane][0] = T(x.x); W.X[lane][1] = T(x.y); W.X[lane][2] = T(x.z);
-      W.V[lane][0] = T(w.x); W.V[lane][1] = T(w.y); W.V[lane][2] = T(w.z);
+      const auto x = xyz[nd];
+      const auto w = u[nd];
+      W.X[lane][0] = x.x; W.X[lane][1] = x.y; W.X[lane][2] = x.z;
+      W.V[lane][0] = w.x; W.V[lane][1] = w.y; W.V[lane][2] = w.z;
     } else if (lane < 11) {
-      W.beta[lane - 8] = T(beta[3 * e + lane - 8]);
+      W.beta[lane - 8] = beta[3 * e + lane - 8];
     } else if (lane == 11) {
       W.flag = 0u;
     }
-    const double Rl = elemR[36 * e + lane];
-    const double Rf[3] = {elemR[36 * e + 32], elemR[36 * e + 33], elemR[36 * e + 34]};
     __syncwarp();
     LaneAcc<T> A;
     tan_zero(A);
@@ -73,8 +80,8 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
     }
     const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
     if (ELEM_OUT) {
-      double* K = oKcc ? oKcc + 1024 * it : nullptr;
-      if (K) {
+      if (oKcc) {
+        double* K = oKcc + 1024 * it;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -93,17 +100,21 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
     __syncwarp();
     tan_phase3b(lane, W);
     __syncwarp();
-    tan_phase3c(lane, W, Rf);
+    tan_phase3c(lane, W);
     __syncwarp();
-    tan_phase3d(lane, W, A, Rl);
+    tan_phase3d(lane, W);
+    __syncwarp();
+    T Wl[3];
+    tan_phase3f(lane, W, A, Wl);
     __syncwarp();
     tan_phase3e(lane, W, A);
-    // data for the fine-scale recovery: K_ff^-1 K_fc and K_ff^-1 R_f
-    if (recX) {
+    // per-element data for the finish kernel and the fine-scale recovery
 #pragma unroll
-      for (int m = 0; m < 3; ++m) recX[96 * e + 32 * m + lane] = W.Xs[m][lane];
-      if (lane < 3) recY[3 * e + lane] = W.y[lane];
+    for (int m = 0; m < 3; ++m) {
+      recX[96 * e + 32 * m + lane] = W.Xs[m][lane];
+      recW[96 * e + 3 * lane + m] = Wl[m];
     }
+    if (lane < 9) recKinv[9 * e + lane] = W.Kinv[lane];
     if (ELEM_OUT) {
       if (oS) {
         double* S = oS + 1024 * it;
@@ -115,7 +126,6 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
             S[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K1[4 * i + k];
           }
       }
-      if (oR) oR[32 * it + lane] = A.r;
       if (oKff && lane < 9) oKff[9 * it + lane] = W.Kff[lane];
     } else {
       // scatter-add (a7), skipping constrained rows and columns (a8 is completed by the
@@ -138,7 +148,6 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
           }
         }
       }
-      if (!(msk >> lane & 1u)) scatter_add(rhs + 4 * (int64_t)W.nd[lane >> 2] + (lane & 3), A.r, ATOMIC);
     }
     __syncwarp();
     // flag bits 1 (det J <= 0) and 2 (singular K_ff) coincide with FLAG_NEG_JACOBIAN/SINGULAR_KFF
@@ -147,9 +156,66 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
   }
 }
 
+// r_e = R_cp - W R_f (FP64) scattered into the right-hand side, and y = K_ff^-1 R_f stored for
+// the recovery. One thread per (element, local dof); threads 32..34 of an element write y.
+template <typename T, bool ATOMIC>
+__global__ void __launch_bounds__(256) finish_kernel(
+    const int32_t* __restrict__ conn, const double* __restrict__ elemR, const T* __restrict__ recW,
+    const double* __restrict__ recKinv, const uint32_t* __restrict__ dir_mask, int64_t first,
+    int64_t count, const int32_t* __restrict__ elem_list, double* __restrict__ rhs,
+    double* __restrict__ recY, double* __restrict__ oR) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t it = g / 36;
+  const int t = (int)(g % 36);
+  if (it >= count || t >= 35) return;
+  const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
+  const double Rf[3] = {elemR[36 * e + 32], elemR[36 * e + 33], elemR[36 * e + 34]};
+  if (t < 32) {
+    const T Wt[3] = {recW[96 * e + 3 * t], recW[96 * e + 3 * t + 1], recW[96 * e + 3 * t + 2]};
+    const double r = condensed_residual(elemR[36 * e + t], Wt, Rf);
+    if (oR) {
+      oR[32 * it + t] = r;
+    } else if (!(dir_mask[e] >> t & 1u)) {
+      double* dst = rhs + 4 * (int64_t)conn[8 * e + (t >> 2)] + (t & 3);
+      if (ATOMIC) atomicAdd(dst, r); else *dst += r;
+    }
+  } else {
+    const int m = t - 32;
+    const double* K = recKinv + 9 * e + 3 * m;
+    recY[3 * e + m] = K[0] * Rf[0] + K[1] * Rf[1] + K[2] * Rf[2];
+  }
+}
+
+// FP32 copies of the node records and bubble coefficients for the mixed-precision tangent.
+__global__ void to_fp32_kernel(const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u,
+                               const double* __restrict__ beta, float4* __restrict__ xyz32,
+                               float4* __restrict__ u32, float* __restrict__ beta32,
+                               int64_t n_nodes, int64_t n_elems, int with_xyz) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += stride) {
+    const double4_32a w = u[i];
+    u32[i] = make_float4((float)w.x, (float)w.y, (float)w.z, (float)w.w);
+    if (with_xyz) {
+      const double4_32a x = xyz[i];
+      xyz32[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+    }
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_elems; i += stride)
+    beta32[i] = (float)beta[i];
+}
+
+int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, bool with_xyz, cudaStream_t st) {
+  const int64_t n = m.n_nodes > 3 * m.n_elems ? m.n_nodes : 3 * m.n_elems;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  to_fp32_kernel<<<(unsigned)blocks, 256, 0, st>>>(m.xyz, s.u, s.beta, c.xyz, c.u, c.beta,
+                                                   m.n_nodes, m.n_elems, with_xyz ? 1 : 0);
+  return 1;
+}
+
 template <typename T, bool ELEM_OUT, bool ATOMIC>
-static void launch_t(const Mesh& m, const State& s, const KParams& kp, const T* tab,
-                     const double* elemR, const TangentOut& o, int64_t first, int64_t count,
+static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
+                     const T* tab, const TangentOut& o, int64_t first, int64_t count,
                      const int32_t* elem_list, unsigned int* flags, cudaStream_t st) {
   const int nq = kp.nq;
   const size_t smem = tan_table_bytes<T>(nq) + TAN_WARPS * tan_warp_bytes<T>(nq);
@@ -157,27 +223,55 @@ static void launch_t(const Mesh& m, const State& s, const KParams& kp, const T* 
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = (count + TAN_WARPS - 1) / TAN_WARPS;
   if (blocks > 152 * 64) blocks = 152 * 64;
+  using NV = typename NodeVec<T>::type;
+  const NV* xyz;
+  const NV* u;
+  const T* beta;
+  if constexpr (sizeof(T) == 4) {
+    xyz = c32.xyz; u = c32.u; beta = c32.beta;
+  } else {
+    xyz = m.xyz; u = s.u; beta = s.beta;
+  }
   kern<<<(unsigned)blocks, TAN_WARPS * 32, smem, st>>>(
-      m.xyz, s.u, m.conn, s.beta, elemR, tab, nq, T(kp.nut), T(kp.tau), first, count, elem_list,
-      m.blk, m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), o.rhs,
-      reinterpret_cast<T*>(o.recX), o.recY, o.S, o.r, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
+      xyz, u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), first, count, elem_list, m.blk,
+      m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
+      reinterpret_cast<T*>(o.recW), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
 }
 
-int launch_tangent(bool fp32, const Mesh& m, const State& s, const KParams& kp,
-                    const void* tab, const double* elemR, const TangentOut& out, int64_t first,
-                    int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
-                    unsigned int* flags, cudaStream_t st) {
+int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32,
+                   const KParams& kp, const void* tab, const TangentOut& out, int64_t first,
+                   int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
+                   unsigned int* flags, cudaStream_t st) {
   if (count <= 0) return 0;
   if (fp32) {
     const float* t = reinterpret_cast<const float*>(tab);
-    if (elem_outputs) launch_t<float, true, true>(m, s, kp, t, elemR, out, first, count, elem_list, flags, st);
-    else if (atomic) launch_t<float, false, true>(m, s, kp, t, elemR, out, first, count, elem_list, flags, st);
-    else launch_t<float, false, false>(m, s, kp, t, elemR, out, first, count, elem_list, flags, st);
+    if (elem_outputs) launch_t<float, true, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
+    else if (atomic) launch_t<float, false, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
+    else launch_t<float, false, false>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
   } else {
     const double* t = reinterpret_cast<const double*>(tab);
-    if (elem_outputs) launch_t<double, true, true>(m, s, kp, t, elemR, out, first, count, elem_list, flags, st);
-    else if (atomic) launch_t<double, false, true>(m, s, kp, t, elemR, out, first, count, elem_list, flags, st);
-    else launch_t<double, false, false>(m, s, kp, t, elemR, out, first, count, elem_list, flags, st);
+    if (elem_outputs) launch_t<double, true, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
+    else if (atomic) launch_t<double, false, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
+    else launch_t<double, false, false>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
+  }
+  return 1;
+}
+
+int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOut& o,
+                  int64_t first, int64_t count, const int32_t* elem_list, bool atomic,
+                  cudaStream_t st) {
+  if (count <= 0) return 0;
+  const unsigned blocks = (unsigned)((count * 36 + 255) / 256);
+  if (fp32) {
+    if (atomic)
+      finish_kernel<float, true><<<blocks, 256, 0, st>>>(m.conn, elemR, (const float*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
+    else
+      finish_kernel<float, false><<<blocks, 256, 0, st>>>(m.conn, elemR, (const float*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
+  } else {
+    if (atomic)
+      finish_kernel<double, true><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
+    else
+      finish_kernel<double, false><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
   }
   return 1;
 }

@@ -64,9 +64,9 @@ struct WarpArea {
   T Kcf[32][3];
   T Xs[3][32];
   double Kff[9];
+  double cof[9];
   double Kinv[9];
   T KinvT[9];
-  double y[3];
   unsigned int flag;
   QpRec<T> qp[1];
 };
@@ -76,7 +76,6 @@ template <typename T>
 struct LaneAcc {
   T K0[16], K1[16];  // pair blocks [i*4+k], index 3 = pressure
   T kcf[3], kfc[3], kff[9];
-  double r;          // condensed residual entry L
 };
 
 template <typename T>
@@ -232,42 +231,58 @@ VMS_HD void tan_phase3a(int lane, WarpArea<T>& W, const LaneAcc<T>& A) {
   for (int j = 0; j < 9; ++j) W.kffp[lane][j] = A.kff[j];
 }
 
-// Phase 3b: lanes 0..8 sum one K_ff entry each (FP64).
+// Phase 3b: lanes 0..8 sum one K_ff entry each over the 32 partials (in T), then widen to FP64.
 template <typename T>
 VMS_HD void tan_phase3b(int lane, WarpArea<T>& W) {
   if (lane < 9) {
-    double s = 0.0;
-    for (int l = 0; l < 32; ++l) s += (double)W.kffp[l][lane];
-    W.Kff[lane] = s;
+    T s = T(0);
+    for (int l = 0; l < 32; ++l) s += W.kffp[l][lane];
+    W.Kff[lane] = (double)s;
   }
 }
 
-// Phase 3c (lane 0): FP64 inverse of K_ff and y = K_ff^-1 R_f.
+// Phase 3c: lanes 0..8 each form one cofactor of K_ff (FP64).
 template <typename T>
-VMS_HD void tan_phase3c(int lane, WarpArea<T>& W, const double Rf[3]) {
-  if (lane != 0) return;
-  double det = inverse3(W.Kff, W.Kinv);
-  if (!(det != 0.0) || !(det == det) || !(det - det == 0.0)) {
-    W.flag |= 2u;
-    for (int j = 0; j < 9; ++j) W.Kinv[j] = 0.0;
+VMS_HD void tan_phase3c(int lane, WarpArea<T>& W) {
+  if (lane < 9) {
+    const int i = lane / 3, j = lane % 3;
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+    W.cof[lane] = W.Kff[3 * i1 + j1] * W.Kff[3 * i2 + j2] - W.Kff[3 * i1 + j2] * W.Kff[3 * i2 + j1];
   }
-  for (int m = 0; m < 3; ++m)
-    W.y[m] = W.Kinv[3 * m] * Rf[0] + W.Kinv[3 * m + 1] * Rf[1] + W.Kinv[3 * m + 2] * Rf[2];
-  for (int j = 0; j < 9; ++j) W.KinvT[j] = T(W.Kinv[j]);
 }
 
-// Phase 3d: column L of X = K_ff^-1 K_fc and row L of K_cf to shared memory; FP64 condensed
-// residual entry r_L = R_cp[L] - K_cf[L,:] y.
+// Phase 3d: determinant and one reciprocal (every lane, FP64), then lanes 0..8 write one entry of
+// K_ff^-1 = cof^T / det in FP64 and in T. A singular or non-finite K_ff raises flag bit 2.
 template <typename T>
-VMS_HD void tan_phase3d(int lane, WarpArea<T>& W, LaneAcc<T>& A, double Rcp_lane) {
+VMS_HD void tan_phase3d(int lane, WarpArea<T>& W) {
+  const double det = W.Kff[0] * W.cof[0] + W.Kff[1] * W.cof[1] + W.Kff[2] * W.cof[2];
+  const bool bad = !(det != 0.0) || !(det - det == 0.0);
+  const double r = bad ? 0.0 : 1.0 / det;
+  if (lane < 9) {
+    const double v = W.cof[3 * (lane % 3) + lane / 3] * r;
+    W.Kinv[lane] = v;
+    W.KinvT[lane] = T(v);
+  }
+  if (bad && lane == 0) W.flag |= 2u;
+}
+
+// Phase 3f: column L of X = K_ff^-1 K_fc and row L of K_cf to shared memory; row L of
+// W = K_cf K_ff^-1 (used later for r_e = R_cp - W R_f) into Wl.
+template <typename T>
+VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, T Wl[3]) {
   VMS_UNROLL
   for (int m = 0; m < 3; ++m) {
     W.Xs[m][lane] = W.KinvT[3 * m] * A.kfc[0] + W.KinvT[3 * m + 1] * A.kfc[1] +
                     W.KinvT[3 * m + 2] * A.kfc[2];
     W.Kcf[lane][m] = A.kcf[m];
+    Wl[m] = A.kcf[0] * W.KinvT[m] + A.kcf[1] * W.KinvT[3 + m] + A.kcf[2] * W.KinvT[6 + m];
   }
-  A.r = Rcp_lane - ((double)A.kcf[0] * W.y[0] + (double)A.kcf[1] * W.y[1] +
-                    (double)A.kcf[2] * W.y[2]);
+}
+
+// Condensed residual entry (FP64): r_t = R_cp[t] - sum_m W[t][m] R_f[m]; y = K_ff^-1 R_f.
+template <typename T>
+VMS_HD double condensed_residual(double Rcp_t, const T Wt[3], const double Rf[3]) {
+  return Rcp_t - ((double)Wt[0] * Rf[0] + (double)Wt[1] * Rf[1] + (double)Wt[2] * Rf[2]);
 }
 
 // Phase 3e: S blocks of the lane's two node pairs, in place in K0/K1.

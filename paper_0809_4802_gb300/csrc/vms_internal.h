@@ -86,15 +86,26 @@ struct State {
   bool valid = false;
 };
 
+struct Fp32Copy {
+  float4* xyz = nullptr;      // n_nodes (x, y, z, 0) in FP32
+  float4* u = nullptr;        // n_nodes (v, p) in FP32
+  float* beta = nullptr;      // n_elems * 3
+};
+
 struct Work {
   void* values = nullptr;     // nnz (double or float)
   double* rhs = nullptr;      // 4 n_nodes
   double* elemR = nullptr;    // n_elems * 36: R_cp (32), R_f (3), pad
   void* recX = nullptr;       // n_elems * 96 (T): K_ff^-1 K_fc
+  void* recW = nullptr;       // n_elems * 96 (T): K_cf K_ff^-1
+  double* recKinv = nullptr;  // n_elems * 9: K_ff^-1 (FP64)
   double* recY = nullptr;     // n_elems * 3: K_ff^-1 R_f
   double* resid = nullptr;    // 4 n_nodes + 3 n_elems
   double* partial = nullptr;  // reduction partials
   unsigned int* flags = nullptr;
+  Fp32Copy f32;               // mixed precision only
+  cudaStream_t aux = nullptr; // second stream for the tangent kernel
+  cudaEvent_t fork = nullptr, join = nullptr;
   bool assembled = false;
 };
 
@@ -106,17 +117,27 @@ int launch_residual(const Mesh& m, const State& s, const KParams& kp, const QpRo
 
 // Element tangent + condensation + scatter (warp per element). T = double or float.
 struct TangentOut {
-  // scatter targets (assembly)
-  void* values = nullptr; double* rhs = nullptr;
-  void* recX = nullptr; double* recY = nullptr;
+  void* values = nullptr;      // CSR values (assembly)
+  double* rhs = nullptr;       // condensed right-hand side (assembly, finish kernel)
+  void* recX = nullptr;        // per element K_ff^-1 K_fc (T)
+  void* recW = nullptr;        // per element K_cf K_ff^-1 (T)
+  double* recKinv = nullptr;   // per element K_ff^-1
+  double* recY = nullptr;      // per element K_ff^-1 R_f (finish kernel)
   // element outputs (parity), FP64, may be null
   double *S = nullptr, *r = nullptr, *Kcc = nullptr, *Kcf = nullptr, *Kfc = nullptr,
          *Kff = nullptr;
 };
-int launch_tangent(bool fp32, const Mesh& m, const State& s, const KParams& kp,
-                    const void* tab, const double* elemR, const TangentOut& out, int64_t first,
-                    int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
-                    unsigned int* flags, cudaStream_t st);
+int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32,
+                   const KParams& kp, const void* tab, const TangentOut& out, int64_t first,
+                   int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
+                   unsigned int* flags, cudaStream_t st);
+// r_e = R_cp - K_cf K_ff^-1 R_f (FP64) into rhs (or into out.r), and K_ff^-1 R_f into recY.
+int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOut& out,
+                  int64_t first, int64_t count, const int32_t* elem_list, bool atomic,
+                  cudaStream_t st);
+// FP32 copies of the node records (xyz only when with_xyz) and of beta.
+int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, bool with_xyz,
+                   cudaStream_t st);
 
 int launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
 int launch_dirichlet_diag(const Mesh& m, void* values, bool fp32, double* rhs, cudaStream_t st);
