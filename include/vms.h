@@ -192,6 +192,38 @@ int vms_profile_enable(vms_ctx* ctx, int timing);
  * reset; synchronises the stream. If reset != 0 the counters are cleared after reading. */
 int vms_profile_read(vms_ctx* ctx, int reset, double* ms, int64_t* launches);
 
+/* ---- residual norm with caller-owned memory only ------------------------------------------
+ * The paper has no counterpart to this call. It serves callers that cannot allocate device
+ * memory: processes that hand all device memory to their own pool at start-up (a framework's
+ * caching allocator, a fixed arena), and latency-critical loops that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree imply. It computes the same FP64 norm as
+ * vms_residual (R_c, R_p on free dofs and every element's R_f) without a context and without
+ * allocating: its scratch space is one fixed device array of VMS_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library holds until the process exits.
+ *   xyz [n_nodes x 3], conn [n_elems x 8] (int32), dir_dof [n_dir] (int64), u [n_nodes x 4],
+ *   beta [n_elems x 3] (NULL = zero), u_prev [n_nodes x 4] (NULL = u; read only when dt > 0):
+ *   device pointers on the current device, row-major, owned by the caller.
+ *   params: host pointer (nu, visc_factor, dt, f, bubble_scale, quad_order; scatter_mode unused).
+ *   norm (1 double) and status (1 int32): device pointers that receive the norm and VMS_OK,
+ *   VMS_ERR_NEG_JACOBIAN, VMS_ERR_NAN or VMS_ERR_INVALID_ARG (a node or dof index outside the
+ *   mesh; such entries are skipped).
+ * The work is queued on `stream` (a cudaStream_t, NULL = legacy default stream) and the call
+ * returns without waiting; *norm and *status are valid once the stream reaches that point.
+ * Returns VMS_OK, VMS_ERR_INVALID_ARG (null pointer, bad parameters), VMS_ERR_TOO_LARGE
+ * (4*n_nodes + 3*n_elems > VMS_NOALLOC_MAX_ENTRIES; nothing is queued) or VMS_ERR_CUDA.
+ * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. Every call shares
+ * the one array and clears what it needs at its start, so calls whose GPU work overlaps (other
+ * streams, other host threads) race on it: order them on one stream or serialise them. */
+#define VMS_ERR_TOO_LARGE -11
+#define VMS_NOALLOC_MAX_ENTRIES 2097152
+#define VMS_NOALLOC_SCRATCH_BYTES ((VMS_NOALLOC_MAX_ENTRIES + 4096) * 8)
+int vms_residual_norm_noalloc(int64_t n_nodes, const double* xyz, int64_t n_elems,
+                              const int32_t* conn, int64_t n_dir, const int64_t* dir_dof,
+                              const double* u, const double* beta, const double* u_prev,
+                              const vms_params* params, double* norm, int32_t* status,
+                              void* stream);
+
 /* Message of the last error on this context ("" if none); valid until the next call. */
 const char* vms_last_error(vms_ctx* ctx);
 

@@ -26,6 +26,8 @@ ERR_KRYLOV_MAXIT = -7
 ERR_NEWTON_DIVERGED = -8
 ERR_STATE = -9
 ERR_UNSUPPORTED = -10
+ERR_TOO_LARGE = -11
+NOALLOC_MAX_ENTRIES = 2097152
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -38,6 +40,7 @@ EXPORTS = [
     "vms_state_upload", "vms_state_download", "vms_assemble_newton_schur", "vms_get_csr",
     "vms_residual", "vms_element_matrices", "vms_apply", "vms_solve", "vms_newton_step",
     "vms_newton_solve", "vms_last_error", "vms_version", "vms_profile_enable", "vms_profile_read",
+    "vms_residual_norm_noalloc",
 ]
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov"]
 
@@ -92,6 +95,8 @@ def load_library(path: str = LIB_PATH):
         "vms_version": (c_char_p, []),
         "vms_profile_enable": (c_int, [p, c_int]),
         "vms_profile_read": (c_int, [p, c_int, p, p]),
+        "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
+                                              POINTER(VmsParams), p, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
