@@ -43,6 +43,12 @@ FP64_FLOPS_PER_ELEM = {
     "tangent_fp64": 129_697,
 }
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
+# same workload (profiles/residual_kernel_cavity32_re400.md); None where not captured for the
+# current kernel.
+NCU_TRAFFIC_BYTES = {("residual", "cavity32_re400_mixed"): 4_203_776,
+                     ("residual", "cavity32_re400_fp64"): 4_203_776}
+
 WORKLOADS = {
     # the 32^3 jittered lid-driven cavity at Re 400, random state (mixed precision by default)
     "cavity32_re400_mixed": dict(n=32, re=400.0, jitter=0.15, state="random", seed=1002, prec=1),
@@ -269,7 +275,8 @@ def ours(args):
     flops = FP64_FLOPS_PER_ELEM[key] * E
     achieved = flops / (dom_ms / 1000.0) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": NCU_TRAFFIC_BYTES.get((dom, args.workload)),
                 "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
                 "flops_per_element": FP64_FLOPS_PER_ELEM[key],
                 "concurrent": "residual (stream 1) and tangent (stream 2) overlap; times are in situ",
