@@ -57,6 +57,11 @@ WORKLOADS = {
     "cavity8_re100_fp64": dict(n=8, re=100.0, jitter=0.0, state="noise", seed=1001, prec=0),
     "cavity16_re400_fp64": dict(n=16, re=400.0, jitter=0.15, state="random", seed=1002, prec=0),
     "cavity16_re400_mixed": dict(n=16, re=400.0, jitter=0.15, state="random", seed=1002, prec=1),
+    # backward-facing step, h = 1/13: 518,492 elements, Re 800, rest state with parabolic inflow
+    "bfs_re800_mixed": dict(kind="bfs", prec=1),
+    "bfs_re800_fp64": dict(kind="bfs", prec=0),
+    # channel past a cube, 300x56x56 lattice: 937,860 elements, Re 1000, backward Euler dt 0.01
+    "channel_re1000_mixed": dict(kind="channel", prec=1),
 }
 DEFAULT_WORKLOAD = "cavity32_re400_mixed"
 
@@ -64,8 +69,14 @@ DEFAULT_WORKLOAD = "cavity32_re400_mixed"
 def make_workload(name):
     from paper_0809_4802_gb300 import inputs
     w = WORKLOADS[name]
-    wl = inputs.cavity_workload(w["n"], re=w["re"], jitter_frac=w["jitter"], state=w["state"],
-                                seed=w["seed"])
+    kind = w.get("kind", "cavity")
+    if kind == "bfs":
+        wl = inputs.bfs_workload(13, re=800.0, jitter_frac=0.1, seed=1003)
+    elif kind == "channel":
+        wl = inputs.channel_workload(300, 56, re=1000.0, dt=0.01, seed=1005)
+    else:
+        wl = inputs.cavity_workload(w["n"], re=w["re"], jitter_frac=w["jitter"], state=w["state"],
+                                    seed=w["seed"])
     return wl, w["prec"]
 
 
@@ -159,6 +170,19 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """The slowest rank's value (the benchmark's time is the maximum over ranks); x itself when
+    torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def reference_arm(args):
     ws, rank, local = dist_setup()
     if rank != 0:
@@ -190,7 +214,7 @@ def reference_arm(args):
 
 def workload_config(name, wl, prec, scatter):
     c = {"workload": name, "elements": wl.mesh.n_elems, "nodes": wl.mesh.n_nodes,
-         "reynolds": round(1.0 / wl.nu, 3), "precision": "mixed" if prec == 1 else "fp64",
+         "reynolds": round(1.0 / wl.nu, 3), "dt": wl.dt, "precision": "mixed" if prec == 1 else "fp64",
          "quad_points": 27, "l2": "flushed between timed steps (256 MB write)"}
     if scatter is not None:
         c["scatter"] = "colour" if scatter == 1 else "atomic"
@@ -221,10 +245,12 @@ def ours(args):
     ctx = vms.Context(local, prec)
     ctx.set_stream(stream.cuda_stream)
     ctx.mesh_upload(mesh.xyz, mesh.conn, wl.bc.dofs, wl.bc.vals)
-    ctx.set_params(wl.nu, scatter_mode=args.scatter)
+    ctx.set_params(wl.nu, dt=wl.dt, scatter_mode=args.scatter)
     u_host = torch.from_numpy(np.ascontiguousarray(wl.u)).pin_memory()
     beta_host = torch.from_numpy(np.ascontiguousarray(wl.beta)).pin_memory()
-    ctx.state_upload(wl.u, wl.beta)
+    u_prev_host = (torch.from_numpy(np.ascontiguousarray(wl.u_prev)).pin_memory()
+                   if wl.u_prev is not None else None)
+    ctx.state_upload(wl.u, wl.beta, wl.u_prev)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -253,10 +279,7 @@ def ours(args):
     counts = ctx.profile_read(reset=True)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     gpu_launches = int(sum(v[1] for v in counts.values()))
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     value = ws * E * args.steps / (ms / 1000.0)
 
     # ---- per-kernel times (events inside the library, same stream) for the roofline ----
@@ -290,19 +313,17 @@ def ours(args):
     for k in range(args.steps):
         flush.zero_()
         e_starts[k].record(stream)
-        ctx.state_upload(u_host, beta_host)
+        ctx.state_upload(u_host, beta_host, u_prev_host)
         view = ctx.assemble()
         rhs_dev = ctx.csr_device(view)[3]
         rhs_host.copy_(rhs_dev, non_blocking=True)
         e_ends[k].record(stream)
     barrier()
     e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends))
-    if ws > 1:
-        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e_ms = float(t.item())
+    e_ms = max_over_ranks(e_ms)
     e2e = {"value": ws * E * args.steps / (e_ms / 1000.0), "unit": UNIT,
-           "h2d_bytes_per_step": int(u_host.numel() * 8 + beta_host.numel() * 8),
+           "h2d_bytes_per_step": int(u_host.numel() * 8 + beta_host.numel() * 8
+                                     + (u_prev_host.numel() * 8 if u_prev_host is not None else 0)),
            "d2h_bytes_per_step": int(rhs_host.numel() * 8)}
 
     cpu = None

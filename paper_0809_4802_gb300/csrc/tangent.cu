@@ -23,11 +23,23 @@ __host__ __device__ inline size_t tan_table_bytes(int nq) {
   return ((size_t)37 * nq * sizeof(T) + 15) & ~size_t(15);
 }
 
-__device__ __forceinline__ void scatter_add(float* p, float v, bool atomic) {
-  if (atomic) atomicAdd(p, v); else *p += v;
+// Add four contiguous values (one row of a 4x4 node block; 16-byte aligned in FP32 because
+// every row offset and block offset is a multiple of 4). Constrained columns carry zeros.
+__device__ __forceinline__ void scatter_row(float* p, const float v[4], bool atomic) {
+  if (atomic) {
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  } else {
+    float4 o = *reinterpret_cast<float4*>(p);
+    o.x += v[0]; o.y += v[1]; o.z += v[2]; o.w += v[3];
+    *reinterpret_cast<float4*>(p) = o;
+  }
 }
-__device__ __forceinline__ void scatter_add(double* p, double v, bool atomic) {
-  if (atomic) atomicAdd(p, v); else *p += v;
+__device__ __forceinline__ void scatter_row(double* p, const double v[4], bool atomic) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (v[k] == 0.0) continue;
+    if (atomic) atomicAdd(p + k, v[k]); else p[k] += v[k];
+  }
 }
 
 // Node records in the tangent's arithmetic type (FP64 mode reads the FP64 state directly).
@@ -75,7 +87,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
     for (int q0 = 0; q0 < nq; q0 += 32) {
       tan_phase1(lane, q0, nq, W, tab, nut, tau, A);
       __syncwarp();
-      tan_phase2(lane, q0, nq - q0 < 32 ? nq - q0 : 32, W, tab, nut, tau, A);
+      tan_phase2(lane, nq - q0 < 32 ? nq - q0 : 32, W, nut, A);
       __syncwarp();
     }
     const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
@@ -86,8 +98,8 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            K[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K0[4 * i + k];
-            K[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K1[4 * i + k];
+            K[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].x;
+            K[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].y;
           }
       }
       if (oKcf)
@@ -122,8 +134,8 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            S[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K0[4 * i + k];
-            S[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K1[4 * i + k];
+            S[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].x;
+            S[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].y;
           }
       }
       if (oKff && lane < 9) oKff[9 * it + lane] = W.Kff[lane];
@@ -135,17 +147,16 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int a = p ? a1 : a0;
-        const T* Kp = p ? A.K1 : A.K0;
         const int32_t off = bk[8 * a + b];
         const int32_t rl = rowlen[W.nd[a]];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           if (msk >> (4 * a + i) & 1u) continue;
+          T v[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (msk >> (4 * b + k) & 1u) continue;
-            scatter_add(values + off + (int64_t)i * rl + k, Kp[4 * i + k], ATOMIC);
-          }
+          for (int k = 0; k < 4; ++k)
+            v[k] = (msk >> (4 * b + k) & 1u) ? T(0) : (p ? A.K[4 * i + k].y : A.K[4 * i + k].x);
+          scatter_row(values + off + (int64_t)i * rl, v, ATOMIC);
         }
       }
     }

@@ -16,31 +16,72 @@
 //
 // Work split inside the warp (lane L = 0..31):
 //   phase 1: lane q evaluates geometry and fields at quadrature point q and stores per-point
-//            coefficients in shared memory (up to 32 points per pass);
+//            coefficients in shared memory as 4-vectors (up to 32 points per pass);
 //   phase 2: lane L accumulates the 4x4 coarse blocks of the node pairs (L>>3, L&7) and
-//            (4 + (L>>3), L&7), row L of K_cf and column L of K_fc;
-//   phase 3: K_ff is reduced, inverted in FP64, and S_e = K_cc - K_cf K_ff^-1 K_fc and
-//            r_e = R_cp - K_cf K_ff^-1 R_f are formed (r_e in FP64).
+//            (4 + (L>>3), L&7) as packed pairs (one packed FMA serves both blocks), row L of K_cf
+//            and column L of K_fc;
+//   phase 3: K_ff is reduced and inverted in FP64, and S_e = K_cc - K_cf K_ff^-1 K_fc is formed.
 // T is the tangent arithmetic type (double in FP64 mode, float in mixed mode).
 #pragma once
+
+#include <cmath>
+
+#include <vector_functions.h>
+#include <vector_types.h>
 
 #include "element_math.cuh"
 
 namespace vms {
 
-// Per-quadrature-point coefficients (73 entries: an odd stride keeps lane-indexed rows on
-// distinct shared-memory banks).
+template <typename T>
+struct alignas(4 * sizeof(T)) Vec4 {
+  T x, y, z, w;
+};
+
+// Packed pairs: the lane's two node-pair blocks side by side.
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<double> { using type = double2; };
+
+VMS_HD float2 pk(float a, float b) { return make_float2(a, b); }
+VMS_HD double2 pk(double a, double b) { return make_double2(a, b); }
+VMS_HD float2 pfma(float2 a, float2 b, float2 c) {
+#ifdef __CUDA_ARCH__
+  return __ffma2_rn(a, b, c);
+#else
+  return make_float2(a.x * b.x + c.x, a.y * b.y + c.y);
+#endif
+}
+VMS_HD double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(a.x * b.x + c.x, a.y * b.y + c.y);
+}
+VMS_HD float2 pmul(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __fmul2_rn(a, b);
+#else
+  return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+VMS_HD double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+VMS_HD float2 padd(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+VMS_HD double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// Per-quadrature-point coefficients (29 four-vectors).
 template <typename T>
 struct QpRec {
-  T w;        // omega = w_q det J
-  T g[24];    // g[a*3+j] = dN_a/dx_j
-  T L[9];     // L[i*3+j] = dv_i/dx_j
-  T cb[8];    // v . g_b
-  T Ycf[12];  // [c*3+k]: K_cf row coefficient of N_a
-  T Yfc[12];  // [c*3+i]: K_fc column coefficient of N_b
-  T Dv[3];    // nut omega d
-  T Wv[3];    // omega b v + nut omega d
-  T pad;
+  Vec4<T> g[8];    // (dN_a/dx_j for j = 0..2, N_a)
+  Vec4<T> gw[8];   // (omega dN_a/dx_j, omega (v.g_a) + tau omega N_a)
+  Vec4<T> L[3];    // rows of L[i][j] = dv_i/dx_j (4th entry: omega)
+  Vec4<T> Ycf[4];  // row c: K_cf coefficient of N_a for dof c
+  Vec4<T> Yfc[4];  // row c: K_fc coefficient of N_b for dof c
+  Vec4<T> Dv;      // nut omega d
+  Vec4<T> Wv;      // omega b v + nut omega d
 };
 
 // Reference tables of one Gauss rule in type T.
@@ -71,17 +112,18 @@ struct WarpArea {
   QpRec<T> qp[1];
 };
 
-// Registers of one lane across the phases.
+// Registers of one lane across the phases: K[i*4+k] holds entry (i,k) of the blocks (a0,b) in .x
+// and (a1,b) in .y; index 3 is the pressure dof.
 template <typename T>
 struct LaneAcc {
-  T K0[16], K1[16];  // pair blocks [i*4+k], index 3 = pressure
+  typename PairOf<T>::type K[16];
   T kcf[3], kfc[3], kff[9];
 };
 
 template <typename T>
 VMS_HD void tan_zero(LaneAcc<T>& A) {
   VMS_UNROLL
-  for (int i = 0; i < 16; ++i) { A.K0[i] = T(0); A.K1[i] = T(0); }
+  for (int i = 0; i < 16; ++i) A.K[i] = pk(T(0), T(0));
   VMS_UNROLL
   for (int i = 0; i < 3; ++i) { A.kcf[i] = T(0); A.kfc[i] = T(0); }
   VMS_UNROLL
@@ -118,14 +160,13 @@ VMS_HD void tan_phase1(int lane, int q0, int nq, WarpArea<T>& W, const RefTab<T>
     VMS_UNROLL
     for (int j = 0; j < 3; ++j) Ji[al][j] = cof[j][al] * rdet;
   QpRec<T>& R = W.qp[lane];
+  const T om = tab.w[q] * det;
   T g[8][3];
   VMS_UNROLL
   for (int a = 0; a < 8; ++a)
     VMS_UNROLL
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < 3; ++j)
       g[a][j] = dN[3 * a] * Ji[0][j] + dN[3 * a + 1] * Ji[1][j] + dN[3 * a + 2] * Ji[2][j];
-      R.g[3 * a + j] = g[a][j];
-    }
   T d[3];
   VMS_UNROLL
   for (int j = 0; j < 3; ++j) d[j] = db[0] * Ji[0][j] + db[1] * Ji[1][j] + db[2] * Ji[2][j];
@@ -142,30 +183,32 @@ VMS_HD void tan_phase1(int lane, int q0, int nq, WarpArea<T>& W, const RefTab<T>
       VMS_UNROLL
       for (int a = 0; a < 8; ++a) t += W.V[a][i] * g[a][j];
       L[i][j] = t;
-      R.L[3 * i + j] = t;
     }
   }
   VMS_UNROLL
-  for (int a = 0; a < 8; ++a) R.cb[a] = v[0] * g[a][0] + v[1] * g[a][1] + v[2] * g[a][2];
+  for (int a = 0; a < 8; ++a) {
+    const T cb = v[0] * g[a][0] + v[1] * g[a][1] + v[2] * g[a][2];
+    R.g[a] = Vec4<T>{g[a][0], g[a][1], g[a][2], N[a]};
+    R.gw[a] = Vec4<T>{om * g[a][0], om * g[a][1], om * g[a][2], om * (cb + tau * N[a])};
+  }
+  VMS_UNROLL
+  for (int i = 0; i < 3; ++i) R.L[i] = Vec4<T>{L[i][0], L[i][1], L[i][2], om};
   const T cd = v[0] * d[0] + v[1] * d[1] + v[2] * d[2];
   const T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  const T om = tab.w[q] * det;
-  R.w = om;
   const T omb = om * bq;
   VMS_UNROLL
-  for (int c = 0; c < 3; ++c)
-    VMS_UNROLL
-    for (int k = 0; k < 3; ++k) {
-      R.Ycf[3 * c + k] = omb * L[c][k] + (c == k ? om * cd : T(0));
-      R.Yfc[3 * c + k] = omb * (L[k][c] + (c == k ? tau : T(0)));
-    }
-  VMS_UNROLL
-  for (int k = 0; k < 3; ++k) {
-    R.Ycf[9 + k] = -om * d[k];
-    R.Yfc[9 + k] = -om * d[k];
-    R.Dv[k] = nut * om * d[k];
-    R.Wv[k] = omb * v[k] + nut * om * d[k];
+  for (int c = 0; c < 3; ++c) {
+    R.Ycf[c] = Vec4<T>{omb * L[c][0] + (c == 0 ? om * cd : T(0)),
+                       omb * L[c][1] + (c == 1 ? om * cd : T(0)),
+                       omb * L[c][2] + (c == 2 ? om * cd : T(0)), T(0)};
+    R.Yfc[c] = Vec4<T>{omb * (L[0][c] + (c == 0 ? tau : T(0))),
+                       omb * (L[1][c] + (c == 1 ? tau : T(0))),
+                       omb * (L[2][c] + (c == 2 ? tau : T(0))), T(0)};
   }
+  R.Ycf[3] = Vec4<T>{-om * d[0], -om * d[1], -om * d[2], T(0)};
+  R.Yfc[3] = R.Ycf[3];
+  R.Dv = Vec4<T>{nut * om * d[0], nut * om * d[1], nut * om * d[2], T(0)};
+  R.Wv = Vec4<T>{omb * v[0] + R.Dv.x, omb * v[1] + R.Dv.y, omb * v[2] + R.Dv.z, T(0)};
   VMS_UNROLL
   for (int i = 0; i < 3; ++i)
     VMS_UNROLL
@@ -175,51 +218,63 @@ VMS_HD void tan_phase1(int lane, int q0, int nq, WarpArea<T>& W, const RefTab<T>
 
 // Phase 2 for lane `lane`: accumulate over the nqc points stored by phase 1.
 template <typename T>
-VMS_HD void tan_phase2(int lane, int q0, int nqc, const WarpArea<T>& W, const RefTab<T>& tab,
-                       T nut, T tau, LaneAcc<T>& A) {
+VMS_HD void tan_phase2(int lane, int nqc, const WarpArea<T>& W, T nut, LaneAcc<T>& A) {
+  using P = typename PairOf<T>::type;
   const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
   const int at = lane >> 2, ct = lane & 3;
+  // Kronecker masks of the lane's dof ct (constant per lane, so no per-point selects)
+  const T m0 = ct == 0 ? T(1) : T(0), m1 = ct == 1 ? T(1) : T(0), m2 = ct == 2 ? T(1) : T(0);
   for (int qq = 0; qq < nqc; ++qq) {
     const QpRec<T>& Q = W.qp[qq];
-    const T* N = tab.N + 8 * (q0 + qq);
-    const T w = Q.w;
-    const T Nb = N[b], Na0 = N[a0], Na1 = N[a1], Nat = N[at];
-    const T wNb = w * Nb;
-    const T cbt = w * Q.cb[b] + tau * wNb;
-    T wgb[3], nwgb[3], ga0[3], ga1[3], gat[3], L[9];
-    VMS_UNROLL
-    for (int j = 0; j < 3; ++j) {
-      wgb[j] = w * Q.g[3 * b + j];
-      nwgb[j] = nut * wgb[j];
-      ga0[j] = Q.g[3 * a0 + j];
-      ga1[j] = Q.g[3 * a1 + j];
-      gat[j] = Q.g[3 * at + j];
-    }
-    VMS_UNROLL
-    for (int j = 0; j < 9; ++j) L[j] = Q.L[j];
-    const T m0 = Na0 * wNb, m1 = Na1 * wNb;
-    const T s0 = Na0 * cbt + ga0[0] * nwgb[0] + ga0[1] * nwgb[1] + ga0[2] * nwgb[2];
-    const T s1 = Na1 * cbt + ga1[0] * nwgb[0] + ga1[1] * nwgb[1] + ga1[2] * nwgb[2];
+    const Vec4<T> gb = Q.g[b], gwb = Q.gw[b];
+    const Vec4<T> g0 = Q.g[a0], g1 = Q.g[a1];
+    const Vec4<T> w0 = Q.gw[a0], w1 = Q.gw[a1];
+    const Vec4<T> L0 = Q.L[0], L1 = Q.L[1], L2 = Q.L[2];
+    const T wNb = L0.w * gb.w;                 // omega N_b
+    const P Na = pk(g0.w, g1.w);               // (N_a0, N_a1)
+    const P m = pmul(Na, pk(wNb, wNb));        // omega N_a N_b
+    // s = N_a (omega c_b + tau omega N_b) + nut g_a . (omega g_b)
+    P dot = pmul(pk(g0.x, g1.x), pk(gwb.x, gwb.x));
+    dot = pfma(pk(g0.y, g1.y), pk(gwb.y, gwb.y), dot);
+    dot = pfma(pk(g0.z, g1.z), pk(gwb.z, gwb.z), dot);
+    const P s = pfma(pk(nut, nut), dot, pmul(Na, pk(gwb.w, gwb.w)));
+    const T Lr[9] = {L0.x, L0.y, L0.z, L1.x, L1.y, L1.z, L2.x, L2.y, L2.z};
     VMS_UNROLL
     for (int i = 0; i < 3; ++i) {
       VMS_UNROLL
-      for (int k = 0; k < 3; ++k) {
-        A.K0[4 * i + k] += m0 * L[3 * i + k];
-        A.K1[4 * i + k] += m1 * L[3 * i + k];
-      }
-      A.K0[5 * i] += s0;
-      A.K1[5 * i] += s1;
-      A.K0[4 * i + 3] -= ga0[i] * wNb;
-      A.K1[4 * i + 3] -= ga1[i] * wNb;
-      A.K0[12 + i] -= Na0 * wgb[i];
-      A.K1[12 + i] -= Na1 * wgb[i];
+      for (int k = 0; k < 3; ++k) A.K[4 * i + k] = pfma(m, pk(Lr[3 * i + k], Lr[3 * i + k]), A.K[4 * i + k]);
+      A.K[5 * i] = padd(A.K[5 * i], s);
     }
-    const T gdv = gat[0] * Q.Dv[0] + gat[1] * Q.Dv[1] + gat[2] * Q.Dv[2];
-    const T gwv = gat[0] * Q.Wv[0] + gat[1] * Q.Wv[1] + gat[2] * Q.Wv[2];
-    VMS_UNROLL
-    for (int k = 0; k < 3; ++k) {
-      A.kcf[k] += Nat * Q.Ycf[3 * ct + k] + (k == ct ? gdv : T(0));
-      A.kfc[k] += Nat * Q.Yfc[3 * ct + k] + (k == ct ? gwv : T(0));
+    // K_vp: -omega g_ai N_b; K_pv: -N_a omega g_bk
+    const T nNb = -gb.w;
+    A.K[3] = pfma(pk(w0.x, w1.x), pk(nNb, nNb), A.K[3]);
+    A.K[7] = pfma(pk(w0.y, w1.y), pk(nNb, nNb), A.K[7]);
+    A.K[11] = pfma(pk(w0.z, w1.z), pk(nNb, nNb), A.K[11]);
+    const P nNa = pk(-g0.w, -g1.w);
+    A.K[12] = pfma(nNa, pk(gwb.x, gwb.x), A.K[12]);
+    A.K[13] = pfma(nNa, pk(gwb.y, gwb.y), A.K[13]);
+    A.K[14] = pfma(nNa, pk(gwb.z, gwb.z), A.K[14]);
+    // row L of K_cf and column L of K_fc (node at, dof ct)
+    const Vec4<T> gt = Q.g[at];
+    const Vec4<T> yc = Q.Ycf[ct], yf = Q.Yfc[ct], dv = Q.Dv, wv = Q.Wv;
+    const T gdv = gt.x * dv.x + gt.y * dv.y + gt.z * dv.z;
+    const T gwv = gt.x * wv.x + gt.y * wv.y + gt.z * wv.z;
+    if constexpr (sizeof(T) == 4) {
+      // FP32: multiply by the 0/1 masks (cheaper than a select on the FMA pipe)
+      A.kcf[0] += gt.w * yc.x + m0 * gdv;
+      A.kcf[1] += gt.w * yc.y + m1 * gdv;
+      A.kcf[2] += gt.w * yc.z + m2 * gdv;
+      A.kfc[0] += gt.w * yf.x + m0 * gwv;
+      A.kfc[1] += gt.w * yf.y + m1 * gwv;
+      A.kfc[2] += gt.w * yf.z + m2 * gwv;
+    } else {
+      // FP64: selects run on the integer pipe, multiplies would take FP64 slots
+      A.kcf[0] += gt.w * yc.x + (ct == 0 ? gdv : T(0));
+      A.kcf[1] += gt.w * yc.y + (ct == 1 ? gdv : T(0));
+      A.kcf[2] += gt.w * yc.z + (ct == 2 ? gdv : T(0));
+      A.kfc[0] += gt.w * yf.x + (ct == 0 ? gwv : T(0));
+      A.kfc[1] += gt.w * yf.y + (ct == 1 ? gwv : T(0));
+      A.kfc[2] += gt.w * yf.z + (ct == 2 ? gwv : T(0));
     }
   }
 }
@@ -279,25 +334,29 @@ VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, T Wl[3]) 
   }
 }
 
-// Condensed residual entry (FP64): r_t = R_cp[t] - sum_m W[t][m] R_f[m]; y = K_ff^-1 R_f.
+// Condensed residual entry (FP64): r_t = R_cp[t] - sum_m W[t][m] R_f[m].
 template <typename T>
 VMS_HD double condensed_residual(double Rcp_t, const T Wt[3], const double Rf[3]) {
   return Rcp_t - ((double)Wt[0] * Rf[0] + (double)Wt[1] * Rf[1] + (double)Wt[2] * Rf[2]);
 }
 
-// Phase 3e: S blocks of the lane's two node pairs, in place in K0/K1.
+// Phase 3e: S blocks of the lane's two node pairs, in place: K -= K_cf X.
 template <typename T>
 VMS_HD void tan_phase3e(int lane, const WarpArea<T>& W, LaneAcc<T>& A) {
   const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
   VMS_UNROLL
   for (int i = 0; i < 4; ++i) {
-    const T c00 = W.Kcf[4 * a0 + i][0], c01 = W.Kcf[4 * a0 + i][1], c02 = W.Kcf[4 * a0 + i][2];
-    const T c10 = W.Kcf[4 * a1 + i][0], c11 = W.Kcf[4 * a1 + i][1], c12 = W.Kcf[4 * a1 + i][2];
+    const auto c0 = pk(-W.Kcf[4 * a0 + i][0], -W.Kcf[4 * a1 + i][0]);
+    const auto c1 = pk(-W.Kcf[4 * a0 + i][1], -W.Kcf[4 * a1 + i][1]);
+    const auto c2 = pk(-W.Kcf[4 * a0 + i][2], -W.Kcf[4 * a1 + i][2]);
     VMS_UNROLL
     for (int k = 0; k < 4; ++k) {
       const T x0 = W.Xs[0][4 * b + k], x1 = W.Xs[1][4 * b + k], x2 = W.Xs[2][4 * b + k];
-      A.K0[4 * i + k] -= c00 * x0 + c01 * x1 + c02 * x2;
-      A.K1[4 * i + k] -= c10 * x0 + c11 * x1 + c12 * x2;
+      auto acc = A.K[4 * i + k];
+      acc = pfma(c0, pk(x0, x0), acc);
+      acc = pfma(c1, pk(x1, x1), acc);
+      acc = pfma(c2, pk(x2, x2), acc);
+      A.K[4 * i + k] = acc;
     }
   }
 }
