@@ -474,7 +474,10 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
   float* bf = w.bf;
   float* xf = w.xf;
   int rc = VMS_OK;
-  for (int outer = 0; outer < 20 && total < maxit; ++outer) {
+  // The FP64 residual is recomputed after every correction, the last one included, so that the
+  // reported relative residual always belongs to the returned x.
+  int last_it = -1;
+  for (int outer = 0;; ++outer) {
     // FP64 residual of the refinement
     { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, wk.values, w.x, rfull, st)); }
     {
@@ -491,7 +494,7 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
     }
     if ((rc = G.sync_host(&r2, hd + H_NORM, sizeof(double)))) break;
     rel = std::sqrt(r2) / bnorm;
-    if (rel <= rtol) break;
+    if (rel <= rtol || !(rel == rel) || outer == 20 || total >= maxit || last_it == 0) break;
     {
       KScope k(ctx, VMS_K_KRYLOV);
       axpby_kernel<double, double, float><<<grid_for(n), 256, 0, st>>>(1.0, rfull, 0.0, (const double*)nullptr, bf, n);
@@ -509,7 +512,7 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
       axpby_kernel<double, float, double><<<grid_for(n), 256, 0, st>>>(1.0, w.x, 1.0, xf, w.x, n);
       k.add(1);
     }
-    if (it == 0) break;
+    last_it = it;
   }
   if (rc) return rc;
   *iters_out = total;

@@ -10,7 +10,9 @@
 
 namespace vms {
 
-constexpr int TAN_WARPS = 4;
+// warps per block: FP64 records are twice the size, so the FP64 kernel uses smaller blocks to keep
+// several blocks (and enough warps for the FP64 pipe) resident per SM
+template <typename T> constexpr int tan_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <typename T>
 __host__ __device__ inline size_t tan_warp_bytes(int nq) {
@@ -48,7 +50,7 @@ template <> struct NodeVec<double> { using type = double4_32a; };
 template <> struct NodeVec<float> { using type = float4; };
 
 template <typename T, bool ELEM_OUT, bool ATOMIC>
-__global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
+__global__ void __launch_bounds__(tan_warps<T>() * 32) tangent_kernel(
     const typename NodeVec<T>::type* __restrict__ xyz, const typename NodeVec<T>::type* __restrict__ u,
     const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
     int nq, T nut, T tau, int64_t first, int64_t count, const int32_t* __restrict__ elem_list,
@@ -65,8 +67,9 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) tangent_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpArea<T>& W = *reinterpret_cast<WarpArea<T>*>(smem + tan_table_bytes<T>(nq) +
                                                    warp * tan_warp_bytes<T>(nq));
-  const int64_t total = (int64_t)gridDim.x * TAN_WARPS;
-  for (int64_t it = (int64_t)blockIdx.x * TAN_WARPS + warp; it < count; it += total) {
+  constexpr int WARPS = tan_warps<T>();
+  const int64_t total = (int64_t)gridDim.x * WARPS;
+  for (int64_t it = (int64_t)blockIdx.x * WARPS + warp; it < count; it += total) {
     const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
     // gather (a1): 8 nodes and the bubble coefficients
     if (lane < 8) {
@@ -229,11 +232,12 @@ static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const K
                      const T* tab, const TangentOut& o, int64_t first, int64_t count,
                      const int32_t* elem_list, unsigned int* flags, cudaStream_t st) {
   const int nq = kp.nq;
-  const size_t smem = tan_table_bytes<T>(nq) + TAN_WARPS * tan_warp_bytes<T>(nq);
+  constexpr int WARPS = tan_warps<T>();
+  const size_t smem = tan_table_bytes<T>(nq) + WARPS * tan_warp_bytes<T>(nq);
   auto kern = tangent_kernel<T, ELEM_OUT, ATOMIC>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int64_t blocks = (count + TAN_WARPS - 1) / TAN_WARPS;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  int64_t blocks = (count + WARPS - 1) / WARPS;
+  if (blocks > 152 * 128) blocks = 152 * 128;
   using NV = typename NodeVec<T>::type;
   const NV* xyz;
   const NV* u;
@@ -243,7 +247,7 @@ static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const K
   } else {
     xyz = m.xyz; u = s.u; beta = s.beta;
   }
-  kern<<<(unsigned)blocks, TAN_WARPS * 32, smem, st>>>(
+  kern<<<(unsigned)blocks, WARPS * 32, smem, st>>>(
       xyz, u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), first, count, elem_list, m.blk,
       m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
       reinterpret_cast<T*>(o.recW), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
