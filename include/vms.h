@@ -51,10 +51,17 @@ extern "C" {
 #define VMS_ERR_NEWTON_DIVERGED -8  /* Newton residual grew by 1e6 or maxit was reached */
 #define VMS_ERR_STATE -9            /* call out of order (e.g. assemble before mesh/state upload) */
 #define VMS_ERR_UNSUPPORTED -10     /* option not available in this build */
+/* VMS_ERR_TOO_LARGE (-11) is defined with vms_residual_norm_noalloc below */
+#define VMS_ERR_ZERO_PIVOT -12      /* a diagonal block of the ILU(0) factorisation is singular */
+#define VMS_ERR_TIMEOUT -13         /* a device-side wait exceeded its limit (work abandoned) */
 
 /* ---- precision modes (vms_create) ---------------------------------------------------------- */
 #define VMS_PREC_FP64 0   /* all element arithmetic, matrix values and residuals in FP64 */
 #define VMS_PREC_MIXED 1  /* tangent blocks and S_e in FP32; residual R, K_ff^-1, r_e in FP64 */
+
+/* ---- preconditioners of the Krylov solve (vms_set_preconditioner) ---------------------------- */
+#define VMS_PRECOND_ILU0 0          /* block ILU(0), 4x4 node blocks, natural node order (default) */
+#define VMS_PRECOND_BLOCK_JACOBI 1  /* inverses of the 4x4 diagonal node blocks */
 
 /* ---- scatter modes (vms_params.scatter_mode) ----------------------------------------------- */
 #define VMS_SCATTER_ATOMIC 0  /* one launch, atomic adds into CSR values (order not fixed) */
@@ -154,13 +161,22 @@ int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, 
  * 4*n_nodes. Errors: VMS_ERR_STATE (nothing assembled), VMS_ERR_INVALID_ARG. */
 int vms_apply(vms_ctx* ctx, const double* x, double* y);
 
-/* Solve S du = -r with the last assembled system by restarted GMRES(restart) with 4x4 node-block
- * Jacobi preconditioning, FP32 inner iterations and FP64 iterative refinement in VMS_PREC_MIXED
+/* Choose the right preconditioner of vms_solve / vms_newton_*: VMS_PRECOND_ILU0 (default) or
+ * VMS_PRECOND_BLOCK_JACOBI. Section 6 solved every Newton system with a Krylov solver at its
+ * library defaults; on one process that default preconditioner is an incomplete LU factorisation
+ * without fill, which VMS_PRECOND_ILU0 computes on 4x4 node blocks (it is refactored at every
+ * solve of a newly assembled system). ILU(0) needs at most 32 neighbours per node
+ * (VMS_ERR_UNSUPPORTED otherwise). Errors: VMS_ERR_INVALID_ARG. */
+int vms_set_preconditioner(vms_ctx* ctx, int kind);
+
+/* Solve S du = -r with the last assembled system by restarted GMRES(restart), right-preconditioned
+ * (vms_set_preconditioner), FP32 inner iterations and FP64 iterative refinement in VMS_PREC_MIXED
  * (FP64 throughout in VMS_PREC_FP64), to relative residual rtol within maxit iterations (the paper
  * used a Krylov solver with tolerance 1e-12 and 50 iterations, Section 6). Then recovers the bubble
  * increments du' = K_ff^-1 (-R_f - K_fc du_e) per element (Section 5) and, if update != 0, adds
  * du and du' to the state. *iters (may be NULL) receives the Krylov iterations, *rel the final
- * relative residual. Errors: VMS_ERR_STATE, VMS_ERR_KRYLOV_MAXIT (state left unchanged). */
+ * relative residual. Errors: VMS_ERR_STATE, VMS_ERR_KRYLOV_MAXIT (state left unchanged),
+ * VMS_ERR_ZERO_PIVOT, VMS_ERR_TIMEOUT (ILU(0) only; the state is left unchanged). */
 int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
               double* rel);
 
@@ -181,7 +197,8 @@ int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* h
 #define VMS_K_REDUCE 4    /* norms and dot products */
 #define VMS_K_SPMV 5      /* CSR matrix-vector products */
 #define VMS_K_KRYLOV 6    /* other Krylov / recovery / update kernels */
-#define VMS_K_COUNT 7
+#define VMS_K_PRECOND 7   /* preconditioner set-up and application (ILU(0) factor and sweeps) */
+#define VMS_K_COUNT 8
 
 /* Count every kernel launch of the context (always on) and, if `timing` != 0, bracket each launch
  * with CUDA events on the context's stream to accumulate its GPU time per kernel kind. */

@@ -13,6 +13,7 @@ using namespace vms;
 struct vms_ctx {
   int device = 0;
   int precision = VMS_PREC_FP64;
+  int precond = VMS_PRECOND_ILU0;
   cudaStream_t stream = nullptr;
   vms_params params{};
   int nq = 27;
@@ -278,6 +279,14 @@ int vms_destroy(vms_ctx* ctx) {
 int vms_set_stream(vms_ctx* ctx, void* stream) {
   if (!ctx) return VMS_ERR_INVALID_ARG;
   ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return VMS_OK;
+}
+
+int vms_set_preconditioner(vms_ctx* ctx, int kind) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (kind != VMS_PRECOND_ILU0 && kind != VMS_PRECOND_BLOCK_JACOBI)
+    return fail(ctx, VMS_ERR_INVALID_ARG, "unknown preconditioner");
+  ctx->precond = kind;
   return VMS_OK;
 }
 
@@ -608,6 +617,7 @@ SolverWork& ctx_solver(vms_ctx* c) { return c->solver; }
 cudaStream_t ctx_stream(vms_ctx* c) { return c->stream; }
 int ctx_device(vms_ctx* c) { return c->device; }
 bool ctx_fp32(vms_ctx* c) { return fp32_mode(c); }
+int ctx_precond(vms_ctx* c) { return c->precond; }
 double* ctx_dscalar(vms_ctx* c) { return c->d_scalar; }
 double* ctx_hscalar(vms_ctx* c) { return c->h_scalar; }
 int ctx_fail(vms_ctx* c, int code, const char* msg) { return fail(c, code, msg); }

@@ -1,0 +1,543 @@
+// Block ILU(0) preconditioner of the condensed system (Section 6: Krylov solves with the solver
+// library's default preconditioner, which on one process is an incomplete LU factorisation that
+// keeps the sparsity pattern of the matrix).
+//
+// The matrix is viewed as 4x4 node blocks in natural node order. With no fill, the factorisation
+// of block row i is, for each lower block k < i in increasing order,
+//   L_ik = A_ik U_kk^-1,   A_ij -= L_ik U_kj   for every block j > k present in both rows,
+// after which U_ii = A_ii and its inverse is kept for the backward sweep.
+//
+// GPU mapping: one warp owns one node row at a time and claims rows in order from a counter, so a
+// row only ever waits for rows claimed earlier, by warps that are already running. A row publishes
+// itself by writing its epoch into a flag with release semantics; dependants poll the flag with
+// acquire loads (bounded: after ILU_SPIN_LIMIT polls the kernel records a timeout and returns),
+// and read data published in the same launch through L2 (ld.global.cg), never through L1.
+#include <algorithm>
+#include <vector>
+
+#include "precond.h"
+#include "solver.h"
+
+namespace vms {
+
+namespace {
+
+constexpr uint32_t ILU_SPIN_LIMIT = 1u << 22;
+constexpr int ILU_FWARPS = 4;    // warps per CTA of the factorisation
+constexpr int ILU_SWARPS = 8;    // warps per CTA of the sweeps
+constexpr unsigned ILU_SWEEP_CTAS = 152 * 2;  // sweep CTAs: 16 warps per SM claim rows in turn
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *f == epoch. Gives up (returns false) when another warp has recorded an error or
+// after ILU_SPIN_LIMIT polls, recording a timeout.
+__device__ __forceinline__ bool wait_ready(const uint32_t* f, uint32_t epoch, int* err) {
+  if (ld_acquire(f) == epoch) return true;
+  for (uint32_t it = 1; it <= ILU_SPIN_LIMIT; ++it) {
+    __nanosleep(32);
+    if (ld_acquire(f) == epoch) return true;
+    if ((it & 1023u) == 0 && *(volatile int*)err != 0) return false;
+  }
+  atomicCAS(err, 0, ILU_ERR_TIMEOUT);
+  return false;
+}
+
+template <typename T> struct V4;
+template <> struct V4<float> {
+  float v[4];
+  __device__ __forceinline__ static V4 ldg(const float* p) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    return {{t.x, t.y, t.z, t.w}};
+  }
+  __device__ __forceinline__ static V4 ldcg(const float* p) {
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+    return {{t.x, t.y, t.z, t.w}};
+  }
+};
+template <> struct V4<double> {
+  double v[4];
+  __device__ __forceinline__ static V4 ldg(const double* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return {{a.x, a.y, b.x, b.y}};
+  }
+  __device__ __forceinline__ static V4 ldcg(const double* p) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+    return {{a.x, a.y, b.x, b.y}};
+  }
+};
+
+// Claim the next row of this launch: 0 <= t < n_rows, or n_rows when none is left. A claim below
+// the launch's base (the counter was disturbed by a launch that stopped early) records an error
+// and also returns n_rows, so that no row index outside [0, n_rows) is ever formed.
+__device__ __forceinline__ int64_t claim_row(unsigned long long* ticket, unsigned long long base,
+                                             int64_t n_rows, int* err, int lane) {
+  unsigned long long t = 0;
+  if (lane == 0) t = atomicAdd(ticket, 1ull);
+  t = __shfl_sync(FULL, t, 0);
+  if (t < base) {
+    if (lane == 0) atomicCAS(err, 0, ILU_ERR_TIMEOUT);
+    return n_rows;
+  }
+  t -= base;
+  return t < (unsigned long long)n_rows ? (int64_t)t : n_rows;
+}
+
+// 4x4 inverse by Gauss-Jordan elimination with partial pivoting in FP64; false if a pivot vanishes.
+__device__ bool invert4(const double a[16], double inv[16]) {
+  double M[4][8];
+  double scale = 0.0;
+  for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 4; ++k) {
+      M[i][k] = a[4 * i + k];
+      M[i][4 + k] = i == k ? 1.0 : 0.0;
+      scale = fmax(scale, fabs(a[4 * i + k]));
+    }
+  if (!(scale > 0.0) || !isfinite(scale)) return false;
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    for (int i = c + 1; i < 4; ++i)
+      if (fabs(M[i][c]) > fabs(M[p][c])) p = i;
+    if (!(fabs(M[p][c]) > 1e-14 * scale)) return false;
+    if (p != c)
+      for (int k = 0; k < 8; ++k) { const double t = M[c][k]; M[c][k] = M[p][k]; M[p][k] = t; }
+    const double r = 1.0 / M[c][c];
+    for (int k = 0; k < 8; ++k) M[c][k] *= r;
+    for (int i = 0; i < 4; ++i) {
+      if (i == c) continue;
+      const double f = M[i][c];
+      for (int k = 0; k < 8; ++k) M[i][k] -= f * M[c][k];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 4; ++k) inv[4 * i + k] = M[i][4 + k];
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// factorisation: one warp per node row; the row is eliminated in shared memory
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(ILU_FWARPS * 32)
+    ilu_factor_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                      const T* __restrict__ A, T* F, T* Dinv, const int32_t* __restrict__ dpos,
+                      const int32_t* __restrict__ lptr, const int32_t* __restrict__ pptr,
+                      const uint16_t* __restrict__ pairs, int64_t n_nodes, uint32_t* flags,
+                      uint32_t epoch, unsigned long long* ticket, unsigned long long base, int* err) {
+  __shared__ T srow[ILU_FWARPS][ILU_MAX_DEG * 16];
+  const int lane = threadIdx.x & 31;
+  T* row = srow[threadIdx.x >> 5];
+  for (;;) {
+    const int64_t t = claim_row(ticket, base, n_nodes, err, lane);
+    if (t >= n_nodes) return;
+    const int64_t i = t;
+    const int32_t r0 = rowptr[4 * i];
+    const int deg = (rowptr[4 * i + 1] - r0) >> 2;
+    // row i into shared memory, block-major: row[16 kk + 4 q + c] = A(4i+q, 4 adj_kk + c)
+    for (int e = lane; e < deg * 16; e += 32)
+      row[e] = A[rowptr[4 * i + ((e >> 2) & 3)] + 4 * (e >> 4) + (e & 3)];
+    __syncwarp();
+    const int dp = dpos[i];
+    const int32_t l0 = lptr[i];
+    const int q = (lane >> 2) & 3, c = lane & 3, half = lane >> 4;
+    for (int kk = 0; kk < dp; ++kk) {
+      const int64_t k = colidx[r0 + 4 * kk] >> 2;
+      int ok = 1;
+      if (lane == 0) ok = wait_ready(flags + k, epoch, err);
+      if (!__shfl_sync(FULL, ok, 0)) return;
+      // L_ik = A_ik U_kk^-1 (lanes 0..15 hold entry (q, c))
+      T l = T(0);
+      if (lane < 16) {
+        const T* d = Dinv + 16 * k + c;
+        for (int m = 0; m < 4; ++m) l += row[16 * kk + 4 * q + m] * __ldcg(d + 4 * m);
+      }
+      __syncwarp();
+      if (lane < 16) row[16 * kk + lane] = l;
+      __syncwarp();
+      // A_ij -= L_ik U_kj over the pairs of this lower block, two pairs per step
+      int32_t rk[4];
+      for (int m = 0; m < 4; ++m) rk[m] = rowptr[4 * k + m];
+      const int32_t pe = pptr[l0 + kk + 1];
+      for (int32_t p = pptr[l0 + kk] + half; p < pe; p += 2) {
+        const uint32_t pr = pairs[p];
+        const int jj = pr & 255, jk = pr >> 8;
+        T s = T(0);
+        for (int m = 0; m < 4; ++m) s += row[16 * kk + 4 * q + m] * __ldcg(F + rk[m] + 4 * jk + c);
+        row[16 * jj + 4 * q + c] -= s;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      double a[16], inv[16];
+      for (int e = 0; e < 16; ++e) a[e] = (double)row[16 * dp + e];
+      if (!invert4(a, inv)) {
+        atomicCAS(err, 0, ILU_ERR_PIVOT);
+        for (int e = 0; e < 16; ++e) inv[e] = (e % 5 == 0) ? 1.0 : 0.0;
+      }
+      for (int e = 0; e < 16; ++e) Dinv[16 * i + e] = T(inv[e]);
+    }
+    for (int e = lane; e < deg * 16; e += 32)
+      F[rowptr[4 * i + ((e >> 2) & 3)] + 4 * (e >> 4) + (e & 3)] = row[e];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(flags + i, epoch);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// sweeps: y = L^-1 v (rows ascending), z = U^-1 y (rows descending)
+// One warp per node row, one lane per neighbour block of the row (a node has at most 32
+// neighbours): every lane waits for its own neighbour at the same time, so a row costs one
+// round trip to L2 once its last dependency is published.
+// ---------------------------------------------------------------------------------------------
+
+// FP32 sweeps publish every value in one 64-bit word together with the sweep's epoch (low half:
+// the float's bits, high half: the epoch). Naturally aligned 64-bit accesses are single-copy
+// atomic, so a reader that sees the current epoch in all four words of a node also holds their
+// values: one L2 round trip detects readiness and delivers the data, with no flag and no fence.
+__device__ __forceinline__ void st_packed(unsigned long long* p, float v, uint32_t ep) {
+  const unsigned long long w = ((unsigned long long)ep << 32) | __float_as_uint(v);
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ void ld_relaxed2(const unsigned long long* p, unsigned long long& a,
+                                            unsigned long long& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+// Wait until the four words of a node carry `ep`, then return their values.
+__device__ __forceinline__ bool wait_packed(const unsigned long long* p, uint32_t ep, float out[4],
+                                            int* err) {
+  for (uint32_t it = 0; it <= ILU_SPIN_LIMIT; ++it) {
+    unsigned long long a, b, c, d;
+    ld_relaxed2(p, a, b);
+    ld_relaxed2(p + 2, c, d);
+    if ((uint32_t)(a >> 32) == ep && (uint32_t)(b >> 32) == ep && (uint32_t)(c >> 32) == ep &&
+        (uint32_t)(d >> 32) == ep) {
+      out[0] = __uint_as_float((uint32_t)a);
+      out[1] = __uint_as_float((uint32_t)b);
+      out[2] = __uint_as_float((uint32_t)c);
+      out[3] = __uint_as_float((uint32_t)d);
+      return true;
+    }
+    if (it >= 64) __nanosleep(32);
+    if ((it & 1023u) == 1023u && *(volatile int*)err != 0) return false;
+  }
+  atomicCAS(err, 0, ILU_ERR_TIMEOUT);
+  return false;
+}
+
+// FP64 sweeps write into buffers filled with an all-ones bit pattern before the sweep (a NaN that
+// arithmetic never produces); a node is ready once none of its four words holds that pattern.
+constexpr unsigned long long UNSET64 = ~0ull;
+
+__device__ __forceinline__ bool wait_unset(const double* p, double out[4], int* err) {
+  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(p);
+  for (uint32_t it = 0; it <= ILU_SPIN_LIMIT; ++it) {
+    unsigned long long a, b, c, d;
+    ld_relaxed2(w, a, b);
+    ld_relaxed2(w + 2, c, d);
+    if (a != UNSET64 && b != UNSET64 && c != UNSET64 && d != UNSET64) {
+      out[0] = __longlong_as_double((long long)a);
+      out[1] = __longlong_as_double((long long)b);
+      out[2] = __longlong_as_double((long long)c);
+      out[3] = __longlong_as_double((long long)d);
+      return true;
+    }
+    if (it >= 64) __nanosleep(32);
+    if ((it & 1023u) == 1023u && *(volatile int*)err != 0) return false;
+  }
+  atomicCAS(err, 0, ILU_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
+}
+
+// Sum of the four per-lane partials over the warp; every lane receives all four sums.
+template <typename T>
+__device__ __forceinline__ void warp_sum4(T a[4]) {
+  for (int o = 16; o > 0; o >>= 1)
+    for (int q = 0; q < 4; ++q) a[q] += __shfl_xor_sync(FULL, a[q], o);
+}
+
+// T: element type of the factor (float: packed publication, double: sentinel publication).
+template <typename T, bool LOWER>
+__global__ void __launch_bounds__(ILU_SWARPS * 32)
+    ilu_sweep_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                     const T* __restrict__ F, const T* __restrict__ Dinv,
+                     const int32_t* __restrict__ dpos, const T* __restrict__ v,
+                     const unsigned long long* __restrict__ vp, void* pub, T* __restrict__ out,
+                     int64_t n_nodes, uint32_t ep, unsigned long long* ticket,
+                     unsigned long long base, int* err) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    const int64_t t = claim_row(ticket, base, n_nodes, err, lane);
+    if (t >= n_nodes) return;
+    const int64_t i = LOWER ? t : n_nodes - 1 - t;
+    int32_t rp[4];
+    for (int q = 0; q < 4; ++q) rp[q] = rowptr[4 * i + q];
+    const int deg = (rowptr[4 * i + 1] - rp[0]) >> 2;
+    const int dp = dpos[i];
+    const int kk = LOWER ? lane : dp + 1 + lane;
+    const bool mine = LOWER ? kk < dp : kk < deg;
+    // independent of any other row: the right-hand side and, for U, the row of U_ii^-1
+    T rhs = T(0), drow[4] = {T(0), T(0), T(0), T(0)};
+    if (lane < 4) {
+      if constexpr (LOWER) {
+        rhs = v[4 * i + lane];
+      } else if constexpr (sizeof(T) == 4) {
+        rhs = __uint_as_float((uint32_t)vp[4 * i + lane]);
+      } else {
+        rhs = v[4 * i + lane];
+      }
+      if constexpr (!LOWER) {
+        const V4<T> d = V4<T>::ldg(Dinv + 16 * i + 4 * lane);
+        for (int m = 0; m < 4; ++m) drow[m] = d.v[m];
+      }
+    }
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    bool ok = true;
+    if (mine) {
+      const int64_t k = colidx[rp[0] + 4 * kk] >> 2;
+      V4<T> f[4];
+      for (int q = 0; q < 4; ++q) f[q] = V4<T>::ldg(F + rp[q] + 4 * kk);
+      T xk[4];
+      if constexpr (sizeof(T) == 4)
+        ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err);
+      else
+        ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err);
+      if (ok)
+        for (int q = 0; q < 4; ++q)
+          for (int m = 0; m < 4; ++m) acc[q] += f[q].v[m] * xk[m];
+    }
+    if (!__all_sync(FULL, ok)) return;
+    warp_sum4(acc);
+    if (lane < 4) {
+      T w = rhs - acc[0];
+      for (int q = 1; q < 4; ++q) w = lane == q ? rhs - acc[q] : w;
+      T res = w;
+      if constexpr (!LOWER) {
+        T wq[4];
+        for (int m = 0; m < 4; ++m) wq[m] = __shfl_sync(0xfu, w, m);
+        res = drow[0] * wq[0] + drow[1] * wq[1] + drow[2] * wq[2] + drow[3] * wq[3];
+      }
+      if constexpr (sizeof(T) == 4)
+        st_packed(reinterpret_cast<unsigned long long*>(pub) + 4 * i + lane, res, ep);
+      else
+        st_relaxed_f64(reinterpret_cast<double*>(pub) + 4 * i + lane, res);
+      if (out) out[4 * i + lane] = res;
+    }
+  }
+}
+
+unsigned resident_ctas(int64_t rows, int warps_per_cta, unsigned cap) {
+  const int64_t b = (rows + warps_per_cta - 1) / warps_per_cta;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+uint32_t next_epoch(Ilu& p, cudaStream_t st) {
+  if (++p.epoch == 0) {  // wrapped: clear every flag so no stale epoch can match
+    cudaMemsetAsync(p.flags, 0, sizeof(uint32_t) * p.n_nodes, st);
+    cudaMemsetAsync(p.yp, 0, sizeof(unsigned long long) * 4 * p.n_nodes, st);
+    cudaMemsetAsync(p.xp, 0, sizeof(unsigned long long) * 4 * p.n_nodes, st);
+    p.epoch = 1;
+  }
+  return p.epoch;
+}
+
+// Host-side pattern of the factorisation from the CSR pattern: diagonal positions, lower blocks
+// and, for every lower block (i, k), the pairs (j in row i, j in row k) with j > k.
+int build_pattern(vms_ctx* ctx, Ilu& p, const Mesh& m) {
+  const int64_t N = m.n_nodes;
+  std::vector<int32_t> rowptr(4 * N + 1), colidx(m.nnz);
+  cudaError_t e = cudaMemcpy(rowptr.data(), m.rowptr, sizeof(int32_t) * rowptr.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(colidx.data(), m.colidx, sizeof(int32_t) * colidx.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  std::vector<int32_t> start(N + 1), adj, dpos(N), lptr(N + 1, 0), pptr(1, 0);
+  std::vector<uint16_t> pairs;
+  adj.reserve((size_t)m.nnz / 16);
+  for (int64_t i = 0; i < N; ++i) {
+    const int32_t r0 = rowptr[4 * i];
+    const int deg = (rowptr[4 * i + 1] - r0) / 4;
+    if (deg > ILU_MAX_DEG)
+      return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "ILU(0): a node has more than 32 neighbours");
+    start[i] = (int32_t)adj.size();
+    int d = -1;
+    for (int kk = 0; kk < deg; ++kk) {
+      const int32_t j = colidx[r0 + 4 * kk] / 4;
+      if (j == i) d = kk;
+      adj.push_back(j);
+    }
+    if (d < 0) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "ILU(0): a node belongs to no element");
+    dpos[i] = d;
+  }
+  start[N] = (int32_t)adj.size();
+  for (int64_t i = 0; i < N; ++i) {
+    const int32_t* ai = adj.data() + start[i];
+    const int degi = start[i + 1] - start[i];
+    for (int kk = 0; kk < dpos[i]; ++kk) {
+      const int32_t k = ai[kk];
+      const int32_t* ak = adj.data() + start[k];
+      const int degk = start[k + 1] - start[k];
+      int jj = kk + 1;
+      for (int jk = dpos[k] + 1; jk < degk; ++jk) {
+        const int32_t j = ak[jk];
+        while (jj < degi && ai[jj] < j) ++jj;
+        if (jj < degi && ai[jj] == j) pairs.push_back((uint16_t)(jj | (jk << 8)));
+      }
+      pptr.push_back((int32_t)pairs.size());
+    }
+    lptr[i + 1] = lptr[i] + dpos[i];
+  }
+  if (pairs.size() >= (size_t)INT32_MAX)
+    return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "ILU(0): too many update pairs");
+  p.n_nodes = N;
+  p.n_lower = lptr[N];
+  p.n_pairs = (int64_t)pairs.size();
+  e = cudaMalloc(&p.dpos, sizeof(int32_t) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&p.lptr, sizeof(int32_t) * (N + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p.pptr, sizeof(int32_t) * pptr.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p.pairs, sizeof(uint16_t) * std::max<size_t>(1, pairs.size()));
+  if (e == cudaSuccess) e = cudaMemcpy(p.dpos, dpos.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p.lptr, lptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p.pptr, pptr.data(), sizeof(int32_t) * pptr.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pairs.empty())
+    e = cudaMemcpy(p.pairs, pairs.data(), sizeof(uint16_t) * pairs.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess)
+    return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
+                    cudaGetErrorString(e));
+  return VMS_OK;
+}
+
+int ensure_work(vms_ctx* ctx, Ilu& p, const Mesh& m, size_t elem) {
+  if (p.F && p.elem == elem) return VMS_OK;
+  for (void* b : {p.F, p.Dinv, p.y}) if (b) cudaFree(b);
+  p.F = p.Dinv = p.y = nullptr;
+  cudaError_t e = cudaMalloc(&p.F, elem * m.nnz);
+  if (e == cudaSuccess) e = cudaMalloc(&p.Dinv, elem * 16 * m.n_nodes);
+  if (e == cudaSuccess) e = cudaMalloc(&p.y, elem * 4 * m.n_nodes);
+  if (e == cudaSuccess && !p.flags) {
+    e = cudaMalloc(&p.flags, sizeof(uint32_t) * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMemset(p.flags, 0, sizeof(uint32_t) * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&p.yp, sizeof(unsigned long long) * 4 * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMemset(p.yp, 0, sizeof(unsigned long long) * 4 * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&p.xp, sizeof(unsigned long long) * 4 * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMemset(p.xp, 0, sizeof(unsigned long long) * 4 * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&p.tickets, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(p.tickets, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&p.err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p.err, 0, sizeof(int));
+    p.epoch = 0;
+    p.base = 0;
+  }
+  if (e != cudaSuccess)
+    return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
+                    cudaGetErrorString(e));
+  p.elem = elem;
+  return VMS_OK;
+}
+
+}  // namespace
+
+void free_ilu(Ilu& p) {
+  void* bufs[] = {p.dpos, p.lptr, p.pptr, p.pairs, p.F, p.Dinv, p.y, p.flags, p.yp, p.xp,
+                  p.tickets, p.err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  p = Ilu();
+}
+
+int ilu_factor(vms_ctx* ctx, Ilu& p, const Mesh& m, bool fp32, const void* values, cudaStream_t st,
+               int* launches) {
+  *launches = 0;
+  if (p.dpos && p.n_nodes != m.n_nodes) free_ilu(p);
+  if (!p.dpos)
+    if (int rc = build_pattern(ctx, p, m)) return rc;
+  if (int rc = ensure_work(ctx, p, m, fp32 ? sizeof(float) : sizeof(double))) return rc;
+  const unsigned ctas = resident_ctas(m.n_nodes, ILU_FWARPS, 152 * 8);
+  const uint32_t ep = next_epoch(p, st);
+  if (fp32)
+    ilu_factor_kernel<float><<<ctas, ILU_FWARPS * 32, 0, st>>>(
+        m.rowptr, m.colidx, (const float*)values, (float*)p.F, (float*)p.Dinv, p.dpos, p.lptr,
+        p.pptr, p.pairs, m.n_nodes, p.flags, ep, p.tickets, p.base, p.err);
+  else
+    ilu_factor_kernel<double><<<ctas, ILU_FWARPS * 32, 0, st>>>(
+        m.rowptr, m.colidx, (const double*)values, (double*)p.F, (double*)p.Dinv, p.dpos, p.lptr,
+        p.pptr, p.pairs, m.n_nodes, p.flags, ep, p.tickets, p.base, p.err);
+  p.base += (unsigned long long)m.n_nodes + (unsigned long long)ctas * ILU_FWARPS;
+  p.factored = true;
+  *launches = 1;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+template <>
+int ilu_apply<float, float>(Ilu& p, const Mesh& m, const float* v, float* z, cudaStream_t st) {
+  const unsigned ctas = resident_ctas(m.n_nodes, ILU_SWARPS, ILU_SWEEP_CTAS);
+  const unsigned long long claims = (unsigned long long)m.n_nodes + (unsigned long long)ctas * ILU_SWARPS;
+  uint32_t ep = next_epoch(p, st);
+  ilu_sweep_kernel<float, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+      m.rowptr, m.colidx, (const float*)p.F, nullptr, p.dpos, v, nullptr, p.yp, nullptr,
+      m.n_nodes, ep, p.tickets, p.base, p.err);
+  p.base += claims;
+  ep = next_epoch(p, st);
+  ilu_sweep_kernel<float, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+      m.rowptr, m.colidx, (const float*)p.F, (const float*)p.Dinv, p.dpos, nullptr, p.yp, p.xp, z,
+      m.n_nodes, ep, p.tickets, p.base, p.err);
+  p.base += claims;
+  return 2;
+}
+
+template <>
+int ilu_apply<double, double>(Ilu& p, const Mesh& m, const double* v, double* z, cudaStream_t st) {
+  const unsigned ctas = resident_ctas(m.n_nodes, ILU_SWARPS, ILU_SWEEP_CTAS);
+  const unsigned long long claims = (unsigned long long)m.n_nodes + (unsigned long long)ctas * ILU_SWARPS;
+  double* y = reinterpret_cast<double*>(p.y);
+  cudaMemsetAsync(y, 0xff, sizeof(double) * 4 * m.n_nodes, st);
+  ilu_sweep_kernel<double, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+      m.rowptr, m.colidx, (const double*)p.F, nullptr, p.dpos, v, nullptr, y, nullptr,
+      m.n_nodes, 0, p.tickets, p.base, p.err);
+  p.base += claims;
+  cudaMemsetAsync(z, 0xff, sizeof(double) * 4 * m.n_nodes, st);
+  ilu_sweep_kernel<double, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+      m.rowptr, m.colidx, (const double*)p.F, (const double*)p.Dinv, p.dpos, y, nullptr, z, nullptr,
+      m.n_nodes, 0, p.tickets, p.base, p.err);
+  p.base += claims;
+  return 4;
+}
+
+int ilu_status(vms_ctx* ctx, Ilu& p, cudaStream_t st) {
+  if (!p.err) return VMS_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  if (h == 0) return VMS_OK;
+  // a launch stopped early: its claims and flags are unknown, so start both afresh
+  cudaMemsetAsync(p.err, 0, sizeof(int), st);
+  cudaMemsetAsync(p.tickets, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(p.flags, 0, sizeof(uint32_t) * p.n_nodes, st);
+  cudaMemsetAsync(p.yp, 0, sizeof(unsigned long long) * 4 * p.n_nodes, st);
+  cudaMemsetAsync(p.xp, 0, sizeof(unsigned long long) * 4 * p.n_nodes, st);
+  cudaStreamSynchronize(st);
+  p.base = 0;
+  p.epoch = 0;
+  p.factored = false;
+  return h == ILU_ERR_PIVOT
+             ? ctx_fail(ctx, VMS_ERR_ZERO_PIVOT, "ILU(0): zero pivot in a diagonal block")
+             : ctx_fail(ctx, VMS_ERR_TIMEOUT, "ILU(0): a row waited longer than its limit");
+}
+
+}  // namespace vms

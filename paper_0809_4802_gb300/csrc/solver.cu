@@ -17,6 +17,7 @@ void free_solver(SolverWork& s) {
   void* bufs[] = {s.x, s.r, s.V, s.Z, s.Dinv, s.h, s.rfull, s.bf, s.xf};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  free_ilu(s.ilu);
   s = SolverWork();
 }
 
@@ -239,6 +240,18 @@ struct Gmres {
   cudaStream_t st;
   int64_t n;
 
+  // z = M^-1 v with the preconditioner chosen for this solve
+  template <typename T, typename VT>
+  void precond(const VT* v, VT* z) {
+    KScope k(ctx, VMS_K_PRECOND);
+    if (w.use_ilu) {
+      k.add(ilu_apply<T, VT>(w.ilu, m, v, z, st));
+    } else {
+      block_apply_kernel<VT><<<grid_for(m.n_nodes), 256, 0, st>>>(w.Dinv, v, z, m.n_nodes);
+      k.add(1);
+    }
+  }
+
   int sync_host(void* dst, const void* src, size_t bytes) {
     cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -290,11 +303,7 @@ struct Gmres {
       for (; j < restart && it < maxit; ++j, ++it) {
         VT* vj = V + (int64_t)j * n;
         VT* vn = V + (int64_t)(j + 1) * n;
-        {
-          KScope k(ctx, VMS_K_KRYLOV);
-          block_apply_kernel<VT><<<grid_for(m.n_nodes), 256, 0, st>>>(w.Dinv, vj, z, m.n_nodes);
-          k.add(1);
-        }
+        precond<T, VT>(vj, z);
         { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, values, z, vn, st)); }
         // CGS2 against V_0..V_j: first pass coefficients into hd[0..j], second into hd[128..]
         const int kk = j + 1;
@@ -354,9 +363,13 @@ struct Gmres {
       {
         KScope k(ctx, VMS_K_KRYLOV);
         combine_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, n, hd + H_Y, j, z, n);
-        block_apply_kernel<VT><<<grid_for(m.n_nodes), 256, 0, st>>>(w.Dinv, z, V + n, m.n_nodes);
+        k.add(1);
+      }
+      precond<T, VT>(z, V + n);
+      {
+        KScope k(ctx, VMS_K_KRYLOV);
         axpby_kernel<VT, VT, VT><<<grid_for(n), 256, 0, st>>>(1.0, x, 1.0, V + n, x, n);
-        k.add(3);
+        k.add(1);
       }
       // restart: r = b - A x into V_0
       { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, values, x, z, st)); }
@@ -423,13 +436,21 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
   if (restart < 1 || restart > 120 || maxit < 1 || !(rtol > 0.0))
     return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid solver parameters");
   if (int rc = ensure_solver(ctx, restart)) return rc;
+  w.use_ilu = ctx_precond(ctx) == VMS_PRECOND_ILU0;
   {
-    KScope k(ctx, VMS_K_KRYLOV);
-    if (f32)
+    KScope k(ctx, VMS_K_PRECOND);
+    if (w.use_ilu) {
+      int launched = 0;
+      const int rc = ilu_factor(ctx, w.ilu, m, f32, wk.values, st, &launched);
+      k.add(launched);
+      if (rc) return rc;
+    } else if (f32) {
       block_diag_inv_kernel<float><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, m.n_nodes, w.Dinv);
-    else
+      k.add(1);
+    } else {
       block_diag_inv_kernel<double><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, m.n_nodes, w.Dinv);
-    k.add(1);
+      k.add(1);
+    }
   }
   // b = -rhs (FP64) in w.r
   {
@@ -459,6 +480,8 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
     int it = 0;
     double rel = 0.0;
     if (int rc = G.solve<double, double>(wk.values, w.r, w.x, bnorm, rtol, maxit, restart, &it, &rel)) return rc;
+    if (w.use_ilu)
+      if (int rc = ilu_status(ctx, w.ilu, st)) return rc;
     *iters_out = it;
     *rel_out = rel;
     return rel <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "GMRES reached maxit");
@@ -515,6 +538,8 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
     last_it = it;
   }
   if (rc) return rc;
+  if (w.use_ilu)
+    if (int rc2 = ilu_status(ctx, w.ilu, st)) return rc2;
   *iters_out = total;
   *rel_out = rel;
   return rel <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "refined GMRES reached maxit");

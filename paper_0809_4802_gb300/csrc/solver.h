@@ -1,6 +1,7 @@
 // Krylov solve, fine-scale recovery and Newton driver of the condensed system (Sections 4.2, 5, 6).
 #pragma once
 
+#include "precond.h"
 #include "vms_internal.h"
 
 namespace vms {
@@ -15,6 +16,8 @@ struct SolverWork {
   double* rfull = nullptr;   // n: FP64 refinement residual (mixed)
   float* bf = nullptr;       // n: FP32 right-hand side of the inner solve (mixed)
   float* xf = nullptr;       // n: FP32 inner correction (mixed)
+  Ilu ilu;                   // ILU(0) pattern, factor and sweep work
+  bool use_ilu = false;      // preconditioner of the current solve
   int restart = 0;
   int64_t n = 0;
 };
@@ -29,6 +32,7 @@ SolverWork& ctx_solver(vms_ctx* c);
 cudaStream_t ctx_stream(vms_ctx* c);
 int ctx_device(vms_ctx* c);
 bool ctx_fp32(vms_ctx* c);
+int ctx_precond(vms_ctx* c);
 double* ctx_dscalar(vms_ctx* c);
 double* ctx_hscalar(vms_ctx* c);
 int ctx_fail(vms_ctx* c, int code, const char* msg);

@@ -27,12 +27,16 @@ ERR_NEWTON_DIVERGED = -8
 ERR_STATE = -9
 ERR_UNSUPPORTED = -10
 ERR_TOO_LARGE = -11
+ERR_ZERO_PIVOT = -12
+ERR_TIMEOUT = -13
 NOALLOC_MAX_ENTRIES = 2097152
 
 PREC_FP64 = 0
 PREC_MIXED = 1
 SCATTER_ATOMIC = 0
 SCATTER_COLOUR = 1
+PRECOND_ILU0 = 0
+PRECOND_BLOCK_JACOBI = 1
 
 # every symbol include/vms.h declares
 EXPORTS = [
@@ -40,9 +44,9 @@ EXPORTS = [
     "vms_state_upload", "vms_state_download", "vms_assemble_newton_schur", "vms_get_csr",
     "vms_residual", "vms_element_matrices", "vms_apply", "vms_solve", "vms_newton_step",
     "vms_newton_solve", "vms_last_error", "vms_version", "vms_profile_enable", "vms_profile_read",
-    "vms_residual_norm_noalloc",
+    "vms_residual_norm_noalloc", "vms_set_preconditioner",
 ]
-K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov"]
+K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
 
 
 class VmsParams(ctypes.Structure):
@@ -95,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "vms_version": (c_char_p, []),
         "vms_profile_enable": (c_int, [p, c_int]),
         "vms_profile_read": (c_int, [p, c_int, p, p]),
+        "vms_set_preconditioner": (c_int, [p, c_int]),
         "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
                                               POINTER(VmsParams), p, p, p]),
     }
@@ -171,6 +176,9 @@ class Context:
     # -- setup -------------------------------------------------------------------------------
     def set_stream(self, stream_handle: int):
         self._check(self.lib.vms_set_stream(self.h, c_void_p(stream_handle)))
+
+    def set_preconditioner(self, kind: int):
+        self._check(self.lib.vms_set_preconditioner(self.h, int(kind)))
 
     def set_params(self, nu, visc_factor=2.0, dt=0.0, f=(0.0, 0.0, 0.0), bubble_scale=1.0,
                    quad_order=3, scatter_mode=SCATTER_ATOMIC):

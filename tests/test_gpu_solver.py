@@ -37,13 +37,16 @@ def distorted_problem(n, seed, frac=0.25):
     return mesh, bc, u, beta
 
 
+@pytest.mark.parametrize("precond", [0, 1], ids=["ilu0", "bjacobi"])
 @pytest.mark.parametrize("prec,restart", [(0, 110), (0, 50), (1, 110), (1, 50)])
-def test_solve_and_recovery_match_direct_solution(vms, prec, restart):
+def test_solve_and_recovery_match_direct_solution(vms, prec, restart, precond):
     """2^3 distorted traction-free problem (108 unknowns): unrestarted GMRES (restart 110) and
-    GMRES(50) with restarts both reach 1e-10; the solution matches a direct solve."""
+    GMRES(50) with restarts both reach 1e-10 with either preconditioner; the solution matches a
+    direct solve."""
     mesh, bc, u, beta = distorted_problem(2, 11)
     p = Params(nu=0.05)
     ctx = vms.Context(0, prec)
+    ctx.set_preconditioner(precond)
     ctx.mesh_upload(mesh.xyz, mesh.conn, bc.dofs, bc.vals)
     ctx.set_params(p.nu)
     ctx.state_upload(u, beta)
@@ -109,3 +112,87 @@ def test_newton_cavity8_matches_oracle(vms, prec, tol):
     R = oracle.residual_vector(wl.mesh.conn, wl.mesh.n_nodes, k, wl.bc.dofs)
     assert np.linalg.norm(R) <= 10 * tol * norms[0]
     ctx.close()
+
+
+def one_element_problem(constrained_face_z, seed=13):
+    """One distorted hexahedron with the velocity fixed on the face z = constrained_face_z."""
+    mesh = inputs.cavity_mesh(1)
+    rng = np.random.default_rng(seed)
+    mesh.xyz += rng.uniform(-0.25, 0.25, mesh.xyz.shape)
+    face = np.nonzero(mesh.node_ijk[:, 2] == constrained_face_z)[0]
+    dofs = np.sort(np.concatenate([4 * face + c for c in range(3)]))
+    bc = inputs.Dirichlet(dofs=dofs, vals=np.zeros(dofs.size))
+    u = rng.uniform(-0.5, 0.5, (mesh.n_nodes, 4))
+    u.reshape(-1)[dofs] = 0.0
+    beta = rng.uniform(-0.2, 0.2, (mesh.n_elems, 3))
+    return mesh, bc, u, beta
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ilu0_of_a_full_pattern_is_exact(vms, prec):
+    """On a one-element mesh every node neighbours every other, so the block pattern is full and
+    ILU(0) is the exact block LU factorisation: right-preconditioned GMRES converges at once.
+    (Velocity fixed on the top face, so the first nodes eliminated carry all four unknowns and
+    every pivot block is well conditioned: condition numbers 2 to 5e4.)"""
+    mesh, bc, u, beta = one_element_problem(1)
+    ctx = vms.Context(0, prec)
+    ctx.set_preconditioner(vms.PRECOND_ILU0)
+    ctx.mesh_upload(mesh.xyz, mesh.conn, bc.dofs, bc.vals)
+    ctx.set_params(0.05)
+    ctx.state_upload(u, beta)
+    ctx.assemble()
+    it, rel = ctx.solve(rtol=1e-10, maxit=20, restart=20, update=False)
+    # FP64: one iteration (a second at most, for rounding: the system's condition number is 4e5);
+    # mixed: each FP64 refinement pass of the FP32 inner solve takes one or two iterations
+    assert it <= (2 if prec == 0 else 10) and rel <= 1e-10, (it, rel)
+    ctx.close()
+
+
+def test_ilu0_zero_pivot_is_reported_and_context_stays_usable(vms):
+    """With the velocity fixed on the bottom face instead, the four bottom nodes come first in the
+    node order and only their pressures remain: the Schur complement of their pressure block is
+    singular, so block LU without pivoting meets a zero pivot at the fourth node. The solve
+    reports VMS_ERR_ZERO_PIVOT, leaves the state unchanged, and the same context then solves the
+    system with block-Jacobi preconditioning."""
+    mesh, bc, u, beta = one_element_problem(0)
+    ctx = vms.Context(0, 0)
+    ctx.set_preconditioner(vms.PRECOND_ILU0)
+    ctx.mesh_upload(mesh.xyz, mesh.conn, bc.dofs, bc.vals)
+    ctx.set_params(0.05)
+    ctx.state_upload(u, beta)
+    ctx.assemble()
+    with pytest.raises(vms.VmsError) as ei:
+        ctx.solve(rtol=1e-10, maxit=20, restart=20, update=True)
+    assert ei.value.code == vms.ERR_ZERO_PIVOT
+    u2, b2 = ctx.state_download()
+    np.testing.assert_array_equal(u2, u)
+    np.testing.assert_array_equal(b2, beta)
+    ctx.set_preconditioner(vms.PRECOND_BLOCK_JACOBI)
+    it, rel = ctx.solve(rtol=1e-10, maxit=200, restart=50, update=False)
+    assert rel <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ilu0_beats_block_jacobi_on_cavity(vms, prec):
+    """12^3 lid-driven cavity at Re 400 from the noisy start: both preconditioners give solutions
+    with the requested residual, and ILU(0) needs several times fewer GMRES(50) iterations."""
+    wl = inputs.cavity_workload(12, re=400.0, state="noise", seed=1001)
+    out = {}
+    for precond in (vms.PRECOND_ILU0, vms.PRECOND_BLOCK_JACOBI):
+        ctx = vms.Context(0, prec)
+        ctx.set_preconditioner(precond)
+        ctx.mesh_upload(wl.mesh.xyz, wl.mesh.conn, wl.bc.dofs, wl.bc.vals)
+        ctx.set_params(wl.nu)
+        ctx.state_upload(wl.u, wl.beta)
+        ctx.assemble()
+        rowptr, colidx, vals, rhs = ctx.csr_host()
+        G = sp.csr_matrix((vals.astype(np.float64), colidx, rowptr))
+        it, rel = ctx.solve(rtol=1e-6, maxit=5000, restart=50, update=True)
+        u2, _ = ctx.state_download()
+        du = (u2 - wl.u).reshape(-1)
+        du[wl.bc.dofs] = 0.0
+        assert np.linalg.norm(G @ du + rhs) <= 2e-6 * np.linalg.norm(rhs)
+        out[precond] = it
+        ctx.close()
+    assert 3 * out[vms.PRECOND_ILU0] <= out[vms.PRECOND_BLOCK_JACOBI], out
