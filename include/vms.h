@@ -170,8 +170,10 @@ int vms_apply(vms_ctx* ctx, const double* x, double* y);
 int vms_set_preconditioner(vms_ctx* ctx, int kind);
 
 /* Solve S du = -r with the last assembled system by restarted GMRES(restart), right-preconditioned
- * (vms_set_preconditioner), FP32 inner iterations and FP64 iterative refinement in VMS_PREC_MIXED
- * (FP64 throughout in VMS_PREC_FP64), to relative residual rtol within maxit iterations (the paper
+ * (vms_set_preconditioner; restart <= 240), FP32 inner iterations and FP64 iterative refinement in
+ * VMS_PREC_MIXED (a refinement pass that does not halve the FP64 residual hands the remaining
+ * correction to GMRES with FP64 vectors and the FP32 matrix and preconditioner), FP64 throughout
+ * in VMS_PREC_FP64, to relative residual rtol within maxit iterations in all (the paper
  * used a Krylov solver with tolerance 1e-12 and 50 iterations, Section 6). Then recovers the bubble
  * increments du' = K_ff^-1 (-R_f - K_fc du_e) per element (Section 5) and, if update != 0, adds
  * du and du' to the state. *iters (may be NULL) receives the Krylov iterations, *rel the final
@@ -180,12 +182,16 @@ int vms_set_preconditioner(vms_ctx* ctx, int kind);
 int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
               double* rel);
 
-/* One Newton-Schur iteration (Sections 4.2 and 5): assemble, solve, recover, update. *res_norm
- * receives the FP64 residual norm before the update. */
+/* One Newton-Schur iteration (Sections 4.2 and 5): assemble, solve (GMRES(150) to 1e-10 relative,
+ * at most 3000 iterations; a solve that stops above 1e-10 but below 0.1 is still applied),
+ * recover, update. *res_norm receives the FP64 residual norm before the update. */
 int vms_newton_step(vms_ctx* ctx, double* res_norm);
 
 /* Newton-Schur iteration until ||R|| <= rtol ||R^0|| or maxit iterations; hist (may be NULL,
- * maxit+1 doubles, host) receives the residual norms, *iters the iterations taken.
+ * maxit+1 doubles, host) receives the residual norms, *iters the iterations taken. Inexact
+ * Newton: each linear solve (GMRES(150), at most 3000 iterations) stops at the relative residual
+ * eta = max(min(1e-2, 0.1 ||R|| / ||R^0||), rtol ||R^0|| / (2 ||R||)), capped at 0.5, and a solve
+ * that stops above eta but below 0.1 is still applied.
  * Errors: VMS_ERR_NEWTON_DIVERGED, VMS_ERR_KRYLOV_MAXIT and those of the steps. */
 int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist);
 

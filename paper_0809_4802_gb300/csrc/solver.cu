@@ -6,7 +6,9 @@
 // classical Gram-Schmidt with one re-orthogonalisation pass (CGS2). In mixed precision the Krylov
 // vectors and the matrix are FP32 (dot products accumulate in FP64) and an outer FP64 iterative
 // refinement recomputes r = b - S x in FP64 until the tolerance is met.
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "solver.h"
@@ -14,7 +16,7 @@
 namespace vms {
 
 void free_solver(SolverWork& s) {
-  void* bufs[] = {s.x, s.r, s.V, s.Z, s.Dinv, s.h, s.rfull, s.bf, s.xf};
+  void* bufs[] = {s.x, s.r, s.V, s.Z, s.Dinv, s.h, s.rfull, s.bf, s.xf, s.cx, s.pv, s.pz};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free_ilu(s.ilu);
@@ -116,8 +118,9 @@ __global__ void block_apply_kernel(const double* __restrict__ Dinv, const VT* __
 constexpr int DOT_BLOCKS = 256, DOT_THREADS = 256;
 // device scratch layout (doubles): Gram-Schmidt coefficients of the two passes, a norm, the
 // least-squares solution, then per-block partial sums
-constexpr int H_PASS1 = 0, H_PASS2 = 128, H_NORM = 256, H_Y = 384, H_PART = 512;
-constexpr int H_SIZE = H_PART + 128 * DOT_BLOCKS;
+constexpr int MAX_RESTART = 240;
+constexpr int H_PASS1 = 0, H_PASS2 = 256, H_NORM = 512, H_Y = 768, H_PART = 1024;
+constexpr int H_SIZE = H_PART + 256 * DOT_BLOCKS;
 
 __device__ __forceinline__ double block_reduce(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(DOT_THREADS) reduce_partials_kernel(const doub
 template <typename VT>
 __global__ void gs_update_kernel(const VT* __restrict__ V, int64_t ld, const double* __restrict__ h,
                                  int m, VT* __restrict__ w, int64_t n) {
-  __shared__ double hs[128];
+  __shared__ double hs[MAX_RESTART + 1];
   for (int k = threadIdx.x; k < m; k += blockDim.x) hs[k] = h[k];
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -188,7 +191,7 @@ __global__ void scale_kernel(const VT* __restrict__ x, const double* __restrict_
 template <typename VT>
 __global__ void combine_kernel(const VT* __restrict__ V, int64_t ld, const double* __restrict__ y,
                                int m, VT* __restrict__ t, int64_t n) {
-  __shared__ double ys[128];
+  __shared__ double ys[MAX_RESTART + 1];
   for (int k = threadIdx.x; k < m; k += blockDim.x) ys[k] = y[k];
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -244,6 +247,15 @@ struct Gmres {
   template <typename T, typename VT>
   void precond(const VT* v, VT* z) {
     KScope k(ctx, VMS_K_PRECOND);
+    if constexpr (std::is_same<T, float>::value && std::is_same<VT, double>::value) {
+      if (w.use_ilu) {  // FP32 factor applied to FP64 vectors through FP32 copies
+        axpby_kernel<double, double, float><<<grid_for(n), 256, 0, st>>>(1.0, v, 0.0, (const double*)nullptr, w.pv, n);
+        k.add(1 + ilu_apply<float, float>(w.ilu, m, w.pv, w.pz, st));
+        axpby_kernel<float, float, double><<<grid_for(n), 256, 0, st>>>(1.0, w.pz, 0.0, (const float*)nullptr, z, n);
+        k.add(1);
+        return;
+      }
+    }
     if (w.use_ilu) {
       k.add(ilu_apply<T, VT>(w.ilu, m, v, z, st));
     } else {
@@ -305,7 +317,7 @@ struct Gmres {
         VT* vn = V + (int64_t)(j + 1) * n;
         precond<T, VT>(vj, z);
         { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, values, z, vn, st)); }
-        // CGS2 against V_0..V_j: first pass coefficients into hd[0..j], second into hd[128..]
+        // CGS2 against V_0..V_j: first pass coefficients into hd[H_PASS1..], second into hd[H_PASS2..]
         const int kk = j + 1;
         double* partial = hd + H_PART;
         for (int pass = 0; pass < 2; ++pass) {
@@ -414,6 +426,9 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
   if (e == cudaSuccess) e = cudaMalloc(&w.rfull, sizeof(double) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.bf, sizeof(float) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.xf, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.cx, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.pv, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.pz, sizeof(float) * n);
   if (e != cudaSuccess) {
     free_solver(w);
     return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
@@ -433,7 +448,7 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
   cudaStream_t st = ctx_stream(ctx);
   const int64_t n = 4 * m.n_nodes;
   const bool f32 = ctx_fp32(ctx);
-  if (restart < 1 || restart > 120 || maxit < 1 || !(rtol > 0.0))
+  if (restart < 1 || restart > MAX_RESTART || maxit < 1 || !(rtol > 0.0))
     return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid solver parameters");
   if (int rc = ensure_solver(ctx, restart)) return rc;
   w.use_ilu = ctx_precond(ctx) == VMS_PRECOND_ILU0;
@@ -498,8 +513,14 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
   float* xf = w.xf;
   int rc = VMS_OK;
   // The FP64 residual is recomputed after every correction, the last one included, so that the
-  // reported relative residual always belongs to the returned x.
+  // reported relative residual always belongs to the returned x. A pass that does not halve the
+  // residual ends the refinement: the FP32 inner solve cannot resolve directions whose singular
+  // values lie below FP32 resolution (the near-null pressure modes of distorted meshes), and the
+  // remaining correction is then solved with FP64 Krylov vectors (below).
   int last_it = -1;
+  double prev_rel = HUGE_VAL;
+  bool stalled = false;
+  double r2 = 0.0;
   for (int outer = 0;; ++outer) {
     // FP64 residual of the refinement
     { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, wk.values, w.x, rfull, st)); }
@@ -508,7 +529,6 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
       axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.r, -1.0, rfull, rfull, n);
       k.add(1);
     }
-    double r2 = 0.0;
     {
       KScope k(ctx, VMS_K_REDUCE);
       multidot_kernel<double><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(rfull, n, rfull, n, hd + H_PART);
@@ -518,6 +538,8 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
     if ((rc = G.sync_host(&r2, hd + H_NORM, sizeof(double)))) break;
     rel = std::sqrt(r2) / bnorm;
     if (rel <= rtol || !(rel == rel) || outer == 20 || total >= maxit || last_it == 0) break;
+    if (rel > 0.5 * prev_rel) { stalled = true; break; }
+    prev_rel = rel;
     {
       KScope k(ctx, VMS_K_KRYLOV);
       axpby_kernel<double, double, float><<<grid_for(n), 256, 0, st>>>(1.0, rfull, 0.0, (const double*)nullptr, bf, n);
@@ -536,6 +558,35 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
       k.add(1);
     }
     last_it = it;
+  }
+  if (rc == VMS_OK && stalled && total < maxit) {
+    // S c = b - S x with FP64 Krylov vectors, the FP32 matrix values and the FP32 preconditioner
+    int it = 0;
+    double irel = 0.0;
+    rc = G.solve<float, double>(wk.values, rfull, w.cx, std::sqrt(r2), rtol / rel, maxit - total,
+                                restart, &it, &irel);
+    if (rc == VMS_OK) {
+      total += it;
+      {
+        KScope k(ctx, VMS_K_KRYLOV);
+        axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.x, 1.0, w.cx, w.x, n);
+        k.add(1);
+      }
+      { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, wk.values, w.x, rfull, st)); }
+      {
+        KScope k(ctx, VMS_K_KRYLOV);
+        axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.r, -1.0, rfull, rfull, n);
+        k.add(1);
+      }
+      {
+        KScope k(ctx, VMS_K_REDUCE);
+        multidot_kernel<double><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(rfull, n, rfull, n, hd + H_PART);
+        reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+        k.add(2);
+      }
+      rc = G.sync_host(&r2, hd + H_NORM, sizeof(double));
+      rel = std::sqrt(r2) / bnorm;
+    }
   }
   if (rc) return rc;
   if (w.use_ilu)
@@ -588,6 +639,12 @@ int vms_apply(vms_ctx* ctx, const double* x, double* y) {
 
 namespace vms {
 
+// Krylov subspace of the Newton driver: the condensed systems of distorted meshes carry a few
+// near-null pressure modes (singular values down to 1e-9 of the largest), which restarted GMRES
+// resolves only when a cycle is long enough to keep them (GMRES(50) stagnates near 1e-5 on the
+// late Newton systems of a jittered 32^3 cavity, GMRES(100) too, GMRES(120) converges).
+constexpr int NEWTON_RESTART = 150;
+
 // Solve, then (if update) recover the bubble increments and update the state. A solve that stops
 // at maxit is still applied when its relative residual is below accept_below (inexact Newton).
 static int solve_impl(vms_ctx* ctx, double rtol, int maxit, int restart, int update,
@@ -627,7 +684,7 @@ int vms_newton_step(vms_ctx* ctx, double* res_norm) {
   if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
   int it = 0;
   double rel = 0.0;
-  return solve_impl(ctx, 1e-10, 2000, 50, 1, 0.1, &it, &rel);
+  return solve_impl(ctx, 1e-10, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel);
 }
 
 int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist) {
@@ -639,11 +696,13 @@ int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* h
   int k = 0;
   while (k < maxit && r > rtol * r0) {
     if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
-    // inexact Newton: forcing term proportional to the current relative residual
-    const double eta = std::max(std::min(1e-2, 0.1 * r / r0), 1e-12);
+    // inexact Newton: forcing term proportional to the current relative residual, but never
+    // tighter than the final target needs (a linear residual of eta * r <= rtol * r0 / 2)
+    const double eta = std::min(0.5, std::max({std::min(1e-2, 0.1 * r / r0),
+                                               0.5 * rtol * r0 / r, 1e-12}));
     int it = 0;
     double rel = 0.0;
-    if (int rc = solve_impl(ctx, eta, 2000, 50, 1, 0.1, &it, &rel)) return rc;
+    if (int rc = solve_impl(ctx, eta, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel)) return rc;
     ++k;
     if (int rc = vms_residual(ctx, &r, nullptr)) return rc;
     if (hist) hist[k] = r;

@@ -16,6 +16,9 @@ struct SolverWork {
   double* rfull = nullptr;   // n: FP64 refinement residual (mixed)
   float* bf = nullptr;       // n: FP32 right-hand side of the inner solve (mixed)
   float* xf = nullptr;       // n: FP32 inner correction (mixed)
+  double* cx = nullptr;      // n: FP64 correction of the final stage of the mixed solve
+  float* pv = nullptr;       // n: FP32 copy of a vector the FP32 factor is applied to
+  float* pz = nullptr;       // n: its FP32 result
   Ilu ilu;                   // ILU(0) pattern, factor and sweep work
   bool use_ilu = false;      // preconditioner of the current solve
   int restart = 0;
