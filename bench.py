@@ -25,7 +25,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "elements/s Newton-Schur tangent assembly"
+METRIC = "elements/s Newton-Schur tangent assembly"  # plus "newton": wall time per Newton solve
 UNIT = "elements/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -199,6 +199,18 @@ def reference_arm(args):
         rates.append(rate)
         t_total += t
     value = float(np.mean(rates))
+    newton = None
+    if args.newton != "off":
+        import oracle
+        small, _ = make_workload("cavity8_re100_fp64")
+        t0 = time.perf_counter()
+        _, _, norms = oracle.newton_solve(small.mesh.xyz, small.mesh.conn, small.u, small.beta,
+                                          small.bc.dofs, oracle.Params(nu=small.nu), tol=1e-10,
+                                          maxit=20)
+        newton = {"metric": "wall time per Newton solve to 1e-10 rel", "value": time.perf_counter() - t0,
+                  "unit": "s", "workload": "cavity8_re100_fp64", "newton_iterations": len(norms) - 1,
+                  "final_rel": norms[-1] / norms[0],
+                  "linear_solver": "scipy sparse direct solve (oracle)"}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -208,8 +220,43 @@ def reference_arm(args):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"first {per_step} elements of the mesh per step (numpy FP64 oracle)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "newton": newton,
     }
     print(json.dumps(line), flush=True)
+
+
+NEWTON_METRIC = "wall time per Newton solve to 1e-8 rel"
+
+
+def newton_timing(vms, wl, prec, device, stream, rtol=1e-8, repeats=2, maxit=30):
+    """Wall time of vms_newton_solve from the workload's initial state to ||R|| <= rtol ||R^0||:
+    host clock around the call with the device synchronised on both sides; the state is uploaded
+    again (outside the timed region) before each repeat; one untimed solve first builds the
+    ILU(0) pattern and the Krylov work space. Median over the repeats."""
+    import torch
+    ctx = vms.Context(device, prec)
+    ctx.set_stream(stream)
+    ctx.mesh_upload(wl.mesh.xyz, wl.mesh.conn, wl.bc.dofs, wl.bc.vals)
+    ctx.set_params(wl.nu, dt=wl.dt)
+    ctx.state_upload(wl.u, wl.beta, wl.u_prev)
+    ctx.newton_solve(rtol=rtol, maxit=maxit)
+    times, its, hist, stats = [], 0, None, (0, 0)
+    for _ in range(repeats):
+        ctx.state_upload(wl.u, wl.beta, wl.u_prev)
+        torch.cuda.synchronize(device)
+        ctx.solver_stats(reset=True)
+        t0 = time.perf_counter()
+        its, hist = ctx.newton_solve(rtol=rtol, maxit=maxit)
+        torch.cuda.synchronize(device)
+        times.append(time.perf_counter() - t0)
+        stats = ctx.solver_stats(reset=True)
+    ctx.close()
+    return {"metric": NEWTON_METRIC.replace("1e-8", f"{rtol:g}"), "value": float(np.median(times)),
+            "unit": "s", "higher_is_better": False, "precision": "mixed" if prec == 1 else "fp64",
+            "newton_iterations": int(its), "linear_solves": int(stats[0]),
+            "krylov_iterations": int(stats[1]), "final_rel": float(hist[-1] / hist[0]),
+            "krylov": "GMRES(150), block ILU(0) right preconditioner, inexact Newton",
+            "repeats": repeats, "times": [round(t, 4) for t in times]}
 
 
 def workload_config(name, wl, prec, scatter):
@@ -326,6 +373,20 @@ def ours(args):
                                      + (u_prev_host.numel() * 8 if u_prev_host is not None else 0)),
            "d2h_bytes_per_step": int(rhs_host.numel() * 8)}
 
+    # ---- wall time per Newton solve (same mesh and initial state; mixed and plain FP64) ----
+    newton = None
+    if args.newton == "on" or (args.newton == "auto" and args.workload.startswith("cavity")):
+        newton = newton_timing(vms, wl, prec, local, stream.cuda_stream)
+        other = newton_timing(vms, wl, 1 - prec, local, stream.cuda_stream)
+        newton["other_precision"] = {k: other[k] for k in ("precision", "value", "newton_iterations",
+                                                           "krylov_iterations", "final_rel")}
+        small, _ = make_workload("cavity8_re100_fp64")
+        newton["cavity8_re100_fp64_to_1e-10"] = {
+            k: v for k, v in newton_timing(vms, small, 0, local, stream.cuda_stream, rtol=1e-10,
+                                           repeats=3).items()
+            if k in ("value", "unit", "newton_iterations", "krylov_iterations", "final_rel")}
+        newton["value"] = max_over_ranks(newton["value"])
+
     cpu = None
     if rank == 0 and not args.skip_cpu_baseline:
         rate, n, t = oracle_assembly_rate(wl, target_s=args.cpu_seconds)
@@ -339,7 +400,7 @@ def ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
             "config": workload_config(args.workload, wl, prec, args.scatter),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "newton": newton,
             "gpu_launches": gpu_launches, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -360,6 +421,8 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=2048)
+    ap.add_argument("--newton", choices=["auto", "on", "off"], default="auto",
+                    help="also time Newton solves to 1e-8 (auto: on for the cavity workloads)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -215,6 +215,10 @@ int vms_profile_enable(vms_ctx* ctx, int timing);
  * reset; synchronises the stream. If reset != 0 the counters are cleared after reading. */
 int vms_profile_read(vms_ctx* ctx, int reset, double* ms, int64_t* launches);
 
+/* Linear solves (vms_solve and those of the Newton drivers) and their Krylov iterations since the
+ * last reset (either pointer may be NULL). Errors: VMS_ERR_INVALID_ARG. */
+int vms_solver_stats(vms_ctx* ctx, int reset, int64_t* solves, int64_t* krylov_iterations);
+
 /* ---- residual norm with caller-owned memory only ------------------------------------------
  * The paper has no counterpart to this call. It serves callers that cannot allocate device
  * memory: processes that hand all device memory to their own pool at start-up (a framework's

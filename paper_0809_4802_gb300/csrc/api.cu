@@ -31,6 +31,7 @@ struct vms_ctx {
   // kernel accounting
   bool timing = false;
   int64_t launches[VMS_K_COUNT] = {};
+  int64_t solver_stats[2] = {};  // linear solves, Krylov iterations
   double ms[VMS_K_COUNT] = {};
   struct Ev { int kind; cudaEvent_t a, b; };
   std::vector<Ev> events;
@@ -606,6 +607,14 @@ int vms_profile_read(vms_ctx* ctx, int reset, double* ms, int64_t* launches) {
   return VMS_OK;
 }
 
+int vms_solver_stats(vms_ctx* ctx, int reset, int64_t* solves, int64_t* krylov_iterations) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (solves) *solves = ctx->solver_stats[0];
+  if (krylov_iterations) *krylov_iterations = ctx->solver_stats[1];
+  if (reset) ctx->solver_stats[0] = ctx->solver_stats[1] = 0;
+  return VMS_OK;
+}
+
 }  // extern "C"
 
 // Accessors used by the solver translation unit.
@@ -618,6 +627,7 @@ cudaStream_t ctx_stream(vms_ctx* c) { return c->stream; }
 int ctx_device(vms_ctx* c) { return c->device; }
 bool ctx_fp32(vms_ctx* c) { return fp32_mode(c); }
 int ctx_precond(vms_ctx* c) { return c->precond; }
+int64_t* ctx_solver_stats(vms_ctx* c) { return c->solver_stats; }
 double* ctx_dscalar(vms_ctx* c) { return c->d_scalar; }
 double* ctx_hscalar(vms_ctx* c) { return c->h_scalar; }
 int ctx_fail(vms_ctx* c, int code, const char* msg) { return fail(c, code, msg); }

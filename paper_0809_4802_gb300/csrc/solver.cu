@@ -655,6 +655,8 @@ static int solve_impl(vms_ctx* ctx, double rtol, int maxit, int restart, int upd
   int it = 0;
   double r = 0.0;
   int rc = linear_solve(ctx, rtol, maxit, restart, &it, &r);
+  ctx_solver_stats(ctx)[0] += 1;
+  ctx_solver_stats(ctx)[1] += it;
   if (iters) *iters = it;
   if (rel) *rel = r;
   if (rc == VMS_ERR_KRYLOV_MAXIT && r < accept_below) rc = VMS_OK;

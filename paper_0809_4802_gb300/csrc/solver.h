@@ -36,6 +36,7 @@ cudaStream_t ctx_stream(vms_ctx* c);
 int ctx_device(vms_ctx* c);
 bool ctx_fp32(vms_ctx* c);
 int ctx_precond(vms_ctx* c);
+int64_t* ctx_solver_stats(vms_ctx* c);
 double* ctx_dscalar(vms_ctx* c);
 double* ctx_hscalar(vms_ctx* c);
 int ctx_fail(vms_ctx* c, int code, const char* msg);

@@ -44,7 +44,7 @@ EXPORTS = [
     "vms_state_upload", "vms_state_download", "vms_assemble_newton_schur", "vms_get_csr",
     "vms_residual", "vms_element_matrices", "vms_apply", "vms_solve", "vms_newton_step",
     "vms_newton_solve", "vms_last_error", "vms_version", "vms_profile_enable", "vms_profile_read",
-    "vms_residual_norm_noalloc", "vms_set_preconditioner",
+    "vms_residual_norm_noalloc", "vms_set_preconditioner", "vms_solver_stats",
 ]
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
 
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "vms_profile_enable": (c_int, [p, c_int]),
         "vms_profile_read": (c_int, [p, c_int, p, p]),
         "vms_set_preconditioner": (c_int, [p, c_int]),
+        "vms_solver_stats": (c_int, [p, c_int, POINTER(c_int64), POINTER(c_int64)]),
         "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
                                               POINTER(VmsParams), p, p, p]),
     }
@@ -269,6 +270,12 @@ class Context:
         hist = np.zeros(maxit + 1)
         self._check(self.lib.vms_newton_solve(self.h, rtol, maxit, byref(it), hist.ctypes.data))
         return it.value, hist[: it.value + 1]
+
+    def solver_stats(self, reset: bool = True):
+        """(linear solves, Krylov iterations) since the last reset."""
+        a, b = c_int64(), c_int64()
+        self._check(self.lib.vms_solver_stats(self.h, int(reset), byref(a), byref(b)))
+        return a.value, b.value
 
     # -- kernel accounting ----------------------------------------------------------------
     def profile_enable(self, timing: bool = True):
