@@ -161,6 +161,61 @@ int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, 
  * 4*n_nodes. Errors: VMS_ERR_STATE (nothing assembled), VMS_ERR_INVALID_ARG. */
 int vms_apply(vms_ctx* ctx, const double* x, double* y);
 
+/* ---- batches of independent problems (serving-style mixes) --------------------------------- */
+
+/* Per-element kinematic viscosity nu_e (n_elems doubles, host or device; copied), replacing
+ * params.nu element by element (weak-form coefficient visc_factor * nu_e): a batch of problems
+ * with different Reynolds numbers assembled as one mesh in one launch. NULL restores params.nu.
+ * Cleared by vms_mesh_upload. Errors: VMS_ERR_STATE (no mesh), VMS_ERR_INVALID_ARG (nu_e <= 0 or
+ * not finite). */
+int vms_set_element_viscosity(vms_ctx* ctx, const double* nu_e);
+
+/* Declare the uploaded mesh a batch of `count` independent problems: instance i owns nodes
+ * [node_offsets[i], node_offsets[i+1]) and elements [elem_offsets[i], elem_offsets[i+1]) (host
+ * arrays of count + 1 entries, starting at 0 and ending at n_nodes and n_elems). Every element of
+ * an instance must reference only nodes of that instance (checked), so each instance's rows form
+ * a diagonal block of the condensed matrix. Cleared by vms_mesh_upload.
+ * Errors: VMS_ERR_STATE (no mesh), VMS_ERR_INVALID_ARG. */
+int vms_set_instances(vms_ctx* ctx, int64_t count, const int64_t* node_offsets,
+                      const int64_t* elem_offsets);
+
+/* vms_solve restricted to instance `instance` (vms_set_instances): GMRES on its diagonal block of
+ * the last assembled system, then recovery of its bubble increments and, if update != 0, update of
+ * its part of the state only (the other instances keep theirs and their assembled blocks stay
+ * valid). The preconditioner is set up once per assembly for all instances. Same arguments,
+ * results and errors as vms_solve, plus VMS_ERR_INVALID_ARG for an unknown instance and
+ * VMS_ERR_STATE for an instance updated since the last assembly (vms_solve also returns
+ * VMS_ERR_STATE while any instance is). */
+int vms_solve_instance(vms_ctx* ctx, int64_t instance, double rtol, int maxit, int restart,
+                       int update, int* iters, double* rel);
+
+/* Launch shapes and scatter order of the assembly kernels. */
+typedef struct vms_tuning {
+  int32_t tangent_warps;    /* warps (elements) per tangent block: FP32 2, 4 or 8, FP64 1, 2 or 4; 0 = default (4 / 2) */
+  int32_t residual_threads; /* threads (elements) per residual block: 32 or 64; 0 = default (64) */
+  int32_t scatter_mode;     /* VMS_SCATTER_*, or -1 for params.scatter_mode */
+  int32_t reserved;         /* 0 */
+  double ms;                /* vms_autotune: median milliseconds of one assembly with these settings */
+} vms_tuning;
+
+/* Set or read the tuning of the context (defaults: {0, 0, -1}). Results do not depend on it except
+ * for the summation order of the atomic scatter. Errors: VMS_ERR_INVALID_ARG (value not offered). */
+int vms_set_tuning(vms_ctx* ctx, const vms_tuning* tuning);
+int vms_get_tuning(vms_ctx* ctx, vms_tuning* tuning);
+
+/* Autotuner: time `repeats` assemblies (CUDA events on the context's stream, after one warm-up)
+ * of the current mesh and state for every offered combination of tangent warps per block,
+ * residual threads per block and scatter mode, keep the fastest (median) as the context's tuning
+ * and return it in *best (may be NULL). The assembled system is discarded (assemble again).
+ * Errors: VMS_ERR_STATE (no state), those of vms_assemble_newton_schur. */
+int vms_autotune(vms_ctx* ctx, int repeats, vms_tuning* best);
+
+/* Record the kernels of one vms_assemble_newton_schur into a CUDA graph on first use and replay
+ * the graph afterwards (enable != 0); recaptured after vms_mesh_upload, vms_set_params,
+ * vms_set_element_viscosity or vms_set_tuning. Not used while kernel timing is enabled
+ * (vms_profile_enable). Results are those of the same calls without the graph. */
+int vms_set_graph(vms_ctx* ctx, int enable);
+
 /* Choose the right preconditioner of vms_solve / vms_newton_*: VMS_PRECOND_ILU0 (default) or
  * VMS_PRECOND_BLOCK_JACOBI. Section 6 solved every Newton system with a Krylov solver at its
  * library defaults; on one process that default preconditioner is an incomplete LU factorisation
@@ -172,7 +227,7 @@ int vms_set_preconditioner(vms_ctx* ctx, int kind);
 /* Solve S du = -r with the last assembled system by restarted GMRES(restart), right-preconditioned
  * (vms_set_preconditioner; restart <= 240), FP32 inner iterations and FP64 iterative refinement in
  * VMS_PREC_MIXED (a refinement pass that does not halve the FP64 residual hands the remaining
- * correction to GMRES with FP64 vectors and the FP32 matrix and preconditioner), FP64 throughout
+ * correction to flexible GMRES with FP64 vectors and the FP32 matrix and preconditioner), FP64 throughout
  * in VMS_PREC_FP64, to relative residual rtol within maxit iterations in all (the paper
  * used a Krylov solver with tolerance 1e-12 and 50 iterations, Section 6). Then recovers the bubble
  * increments du' = K_ff^-1 (-R_f - K_fc du_e) per element (Section 5) and, if update != 0, adds

@@ -1,5 +1,6 @@
 // C-ABI of libvms_gb300 (declared in include/vms.h): context, mesh and state upload, the
 // Newton-Schur assembly, residual evaluation and element-level outputs.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -36,6 +37,17 @@ struct vms_ctx {
   struct Ev { int kind; cudaEvent_t a, b; };
   std::vector<Ev> events;
   std::vector<cudaEvent_t> pool;
+  // independent problems in one mesh (vms_set_instances): offsets, count + 1 entries each
+  std::vector<int64_t> inst_nodes, inst_elems;
+  std::vector<uint8_t> inst_stale;  // instance updated since the last assembly
+  bool any_stale = false;
+  vms_tuning tune{0, 0, -1, 0, 0.0};  // launch shapes and scatter mode (vms_set_tuning)
+  // CUDA graph of one assembly (vms_set_graph)
+  bool use_graph = false;
+  bool graph_dirty = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_launches[VMS_K_COUNT] = {};
 };
 
 namespace vms {
@@ -96,7 +108,13 @@ void free_mesh(vms_ctx* c) {
   Mesh& m = c->mesh;
   dfree(m.xyz); dfree(m.conn); dfree(m.rowptr); dfree(m.colidx); dfree(m.blk); dfree(m.rowlen);
   dfree(m.dir_mask); dfree(m.dir_dof); dfree(m.dir_val); dfree(m.diag_pos); dfree(m.colour_order);
+  dfree(m.nu_e);
   m = Mesh();
+  c->inst_nodes.clear();
+  c->inst_elems.clear();
+  c->inst_stale.clear();
+  c->any_stale = false;
+  c->graph_dirty = true;
   State& s = c->state;
   dfree(s.u); dfree(s.u_prev); dfree(s.beta);
   s = State();
@@ -121,6 +139,11 @@ KParams kparams(const vms_ctx* c) {
   k.nq = c->nq;
   k.transient = c->params.dt > 0 ? 1 : 0;
   k.has_force = (k.f[0] != 0.0 || k.f[1] != 0.0 || k.f[2] != 0.0) ? 1 : 0;
+  k.nu_e = c->mesh.nu_e;
+  k.visc_factor = c->params.visc_factor;
+  k.tab64 = c->d_tab64;
+  k.tangent_warps = c->tune.tangent_warps;
+  k.residual_threads = c->tune.residual_threads;
   return k;
 }
 
@@ -268,6 +291,8 @@ int vms_destroy(vms_ctx* ctx) {
   for (auto& e : ctx->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_scalar);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->work.aux) { cudaStreamSynchronize(ctx->work.aux); cudaStreamDestroy(ctx->work.aux); }
   if (ctx->work.fork) cudaEventDestroy(ctx->work.fork);
   if (ctx->work.join) cudaEventDestroy(ctx->work.join);
@@ -303,6 +328,123 @@ int vms_set_params(vms_ctx* ctx, const vms_params* p) {
   ctx->params = *p;
   if (retab) TRY(upload_tables(ctx));
   ctx->work.assembled = false;
+  ctx->graph_dirty = true;
+  return VMS_OK;
+}
+
+int vms_set_element_viscosity(vms_ctx* ctx, const double* nu) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  const Mesh& m0 = ctx->mesh;
+  if (!m0.n_elems) return fail(ctx, VMS_ERR_STATE, "no mesh uploaded");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  Mesh& m = ctx->mesh;
+  ctx->graph_dirty = true;
+  ctx->work.assembled = false;
+  if (!nu) {
+    dfree(m.nu_e);
+    return VMS_OK;
+  }
+  std::vector<double> h(m.n_elems);
+  CK(cudaMemcpy(h.data(), nu, sizeof(double) * m.n_elems, cudaMemcpyDefault));
+  for (double v : h)
+    if (!(v > 0.0) || !std::isfinite(v)) return fail(ctx, VMS_ERR_INVALID_ARG, "viscosity must be positive and finite");
+  if (!m.nu_e) TRY(upload(ctx, m.nu_e, h.data(), m.n_elems));
+  else CK(cudaMemcpy(m.nu_e, h.data(), sizeof(double) * m.n_elems, cudaMemcpyHostToDevice));
+  return VMS_OK;
+}
+
+int vms_set_instances(vms_ctx* ctx, int64_t count, const int64_t* node_offsets,
+                      const int64_t* elem_offsets) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  const Mesh& m = ctx->mesh;
+  if (!m.n_elems) return fail(ctx, VMS_ERR_STATE, "no mesh uploaded");
+  if (count < 1 || !node_offsets || !elem_offsets) return fail(ctx, VMS_ERR_INVALID_ARG, "invalid instance arguments");
+  std::vector<int64_t> nodes(node_offsets, node_offsets + count + 1), elems(elem_offsets, elem_offsets + count + 1);
+  if (nodes[0] != 0 || elems[0] != 0 || nodes[count] != m.n_nodes || elems[count] != m.n_elems)
+    return fail(ctx, VMS_ERR_INVALID_ARG, "instance offsets must run from 0 to n_nodes and n_elems");
+  for (int64_t i = 0; i < count; ++i)
+    if (nodes[i + 1] <= nodes[i] || elems[i + 1] <= elems[i])
+      return fail(ctx, VMS_ERR_INVALID_ARG, "instance offsets must increase");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<int32_t> conn(8 * m.n_elems);
+  CK(cudaMemcpy(conn.data(), m.conn, sizeof(int32_t) * conn.size(), cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < count; ++i)
+    for (int64_t e = elems[i]; e < elems[i + 1]; ++e)
+      for (int a = 0; a < 8; ++a) {
+        const int64_t nd = conn[8 * e + a];
+        if (nd < nodes[i] || nd >= nodes[i + 1])
+          return fail(ctx, VMS_ERR_INVALID_ARG, "an element of an instance touches a node of another");
+      }
+  ctx->inst_nodes = std::move(nodes);
+  ctx->inst_elems = std::move(elems);
+  ctx->inst_stale.assign(count, 0);
+  ctx->any_stale = false;
+  return VMS_OK;
+}
+
+int vms_set_tuning(vms_ctx* ctx, const vms_tuning* t) {
+  if (!ctx || !t) return fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
+  const bool f32 = fp32_mode(ctx);
+  bool warps_ok = t->tangent_warps == 0;
+  for (int k = 0; k < 3; ++k) warps_ok = warps_ok || t->tangent_warps == tangent_warp_choice(f32, k);
+  if (!warps_ok || (t->residual_threads != 0 && t->residual_threads != 32 && t->residual_threads != 64) ||
+      t->scatter_mode < -1 || t->scatter_mode > VMS_SCATTER_COLOUR)
+    return fail(ctx, VMS_ERR_INVALID_ARG, "invalid tuning");
+  ctx->tune = *t;
+  ctx->graph_dirty = true;
+  return VMS_OK;
+}
+
+int vms_get_tuning(vms_ctx* ctx, vms_tuning* t) {
+  if (!ctx || !t) return fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
+  *t = ctx->tune;
+  return VMS_OK;
+}
+
+int vms_autotune(vms_ctx* ctx, int repeats, vms_tuning* best) {
+  if (!ctx || repeats < 1) return fail(ctx, VMS_ERR_INVALID_ARG, "invalid arguments");
+  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");
+  CK(cudaSetDevice(ctx->device));
+  const bool f32 = fp32_mode(ctx);
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  vms_tuning win{0, 0, -1, 0, HUGE_VAL};
+  int rc = VMS_OK;
+  for (int wk = 0; wk < 3 && rc == VMS_OK; ++wk)
+    for (int rt : {32, 64})
+      for (int sm = VMS_SCATTER_ATOMIC; sm <= VMS_SCATTER_COLOUR && rc == VMS_OK; ++sm) {
+        ctx->tune = vms_tuning{tangent_warp_choice(f32, wk), rt, sm, 0, 0.0};
+        ctx->graph_dirty = true;
+        if ((rc = vms_assemble_newton_schur(ctx, nullptr))) break;  // warm-up (and graph capture)
+        std::vector<float> t(repeats);
+        for (int r = 0; r < repeats && rc == VMS_OK; ++r) {
+          cudaEventRecord(a, ctx->stream);
+          rc = vms_assemble_newton_schur(ctx, nullptr);
+          cudaEventRecord(b, ctx->stream);
+          cudaEventSynchronize(b);
+          cudaEventElapsedTime(&t[r], a, b);
+        }
+        if (rc) break;
+        std::sort(t.begin(), t.end());
+        const double med = t[repeats / 2];
+        if (med < win.ms) win = vms_tuning{ctx->tune.tangent_warps, rt, sm, 0, med};
+      }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ctx->tune = rc == VMS_OK ? win : vms_tuning{0, 0, -1, 0, 0.0};
+  ctx->graph_dirty = true;
+  ctx->work.assembled = false;
+  if (rc) return rc;
+  if (best) *best = win;
+  return VMS_OK;
+}
+
+int vms_set_graph(vms_ctx* ctx, int enable) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  ctx->use_graph = enable != 0;
+  ctx->graph_dirty = true;
   return VMS_OK;
 }
 
@@ -424,36 +566,35 @@ static void fill_view(vms_ctx* ctx, vms_csr_view* out) {
   out->n_colours = ctx->mesh.n_colours;
 }
 
-int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out) {
-  if (!ctx) return VMS_ERR_INVALID_ARG;
-  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");
-  CK(cudaSetDevice(ctx->device));
+// Queue one assembly on `st` (no host synchronisation): fills, FP32 copies, the residual and the
+// tangent on two streams, the finish kernel and the Dirichlet rows.
+static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
   const Mesh& m = ctx->mesh;
   Work& w = ctx->work;
   const bool f32 = fp32_mode(ctx);
   const KParams kp = kparams(ctx);
-  cudaStream_t st = ctx->stream;
   {
-    KScope k(ctx, VMS_K_FILL);
+    KScope k(ctx, VMS_K_FILL, st);
     k.add(launch_fill_zero(w.values, (size_t)m.nnz * (f32 ? sizeof(float) : sizeof(double)), st));
     k.add(launch_fill_zero(w.rhs, sizeof(double) * 4 * m.n_nodes, st));
     k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st));
   }
   if (f32) {
-    KScope k(ctx, VMS_K_FILL);
+    KScope k(ctx, VMS_K_FILL, st);
     k.add(launch_to_fp32(m, ctx->state, w.f32, false, st));
   }
   TangentOut o;
   o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv;
   o.recY = w.recY;
   const void* tab = f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64;
-  const bool colour = ctx->params.scatter_mode == VMS_SCATTER_COLOUR;
+  const int scatter = ctx->tune.scatter_mode >= 0 ? ctx->tune.scatter_mode : ctx->params.scatter_mode;
+  const bool colour = scatter == VMS_SCATTER_COLOUR;
   // the FP64 residual kernel (this stream) and the tangent kernel (auxiliary stream, FP32 or FP64
   // pipe) are independent and run concurrently; the finish kernel joins them
   CK(cudaEventRecord(w.fork, st));
   CK(cudaStreamWaitEvent(w.aux, w.fork, 0));
   {
-    KScope k(ctx, VMS_K_RESIDUAL);
+    KScope k(ctx, VMS_K_RESIDUAL, st);
     k.add(launch_residual(m, ctx->state, kp, ctx->d_qp, w.elemR, nullptr, 0, m.n_elems, 0, w.flags, st));
   }
   {
@@ -472,7 +613,7 @@ int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out) {
   CK(cudaEventRecord(w.join, w.aux));
   CK(cudaStreamWaitEvent(st, w.join, 0));
   {
-    KScope k(ctx, VMS_K_DIRICHLET);
+    KScope k(ctx, VMS_K_DIRICHLET, st);
     if (colour) {
       for (int c = 0; c < m.n_colours; ++c) {
         const int64_t b = m.colour_start[c], n = m.colour_start[c + 1] - b;
@@ -482,10 +623,58 @@ int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out) {
       k.add(launch_finish(f32, m, w.elemR, o, 0, m.n_elems, nullptr, true, st));
     }
   }
-  { KScope k(ctx, VMS_K_DIRICHLET); k.add(launch_dirichlet_diag(m, w.values, f32, w.rhs, st)); }
+  { KScope k(ctx, VMS_K_DIRICHLET, st); k.add(launch_dirichlet_diag(m, w.values, f32, w.rhs, st)); }
   CK(cudaGetLastError());
+  return VMS_OK;
+}
+
+// Capture one assembly into a CUDA graph (on a private stream: the legacy default stream cannot
+// be captured) and keep its launch counts per kernel kind for the accounting of every replay.
+static int capture_assembly(vms_ctx* ctx) {
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  int64_t before[VMS_K_COUNT];
+  for (int k = 0; k < VMS_K_COUNT; ++k) before[k] = ctx->launches[k];
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+  const int rc = enqueue_assembly(ctx, ctx->cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  for (int k = 0; k < VMS_K_COUNT; ++k) {
+    ctx->graph_launches[k] = ctx->launches[k] - before[k];
+    ctx->launches[k] = before[k];
+  }
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) return fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e2));
+  ctx->graph_dirty = false;
+  return VMS_OK;
+}
+
+int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");
+  CK(cudaSetDevice(ctx->device));
+  Work& w = ctx->work;
+  if (ctx->use_graph && !ctx->timing) {
+    if (ctx->graph_dirty || !ctx->graph) TRY(capture_assembly(ctx));
+    CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+    for (int k = 0; k < VMS_K_COUNT; ++k) ctx->launches[k] += ctx->graph_launches[k];
+  } else {
+    TRY(enqueue_assembly(ctx, ctx->stream));
+  }
   TRY(check_flags(ctx));
   w.assembled = true;
+  ++w.assembly_id;
+  std::fill(ctx->inst_stale.begin(), ctx->inst_stale.end(), 0);
+  ctx->any_stale = false;
   if (out) fill_view(ctx, out);
   return VMS_OK;
 }
@@ -627,6 +816,17 @@ cudaStream_t ctx_stream(vms_ctx* c) { return c->stream; }
 int ctx_device(vms_ctx* c) { return c->device; }
 bool ctx_fp32(vms_ctx* c) { return fp32_mode(c); }
 int ctx_precond(vms_ctx* c) { return c->precond; }
+// The assembled block of instance i no longer matches its state (i < 0: the whole system).
+bool ctx_stale(vms_ctx* c, int64_t i) { return i < 0 ? c->any_stale : c->inst_stale[i] != 0; }
+void ctx_mark_stale(vms_ctx* c, int64_t i) {
+  c->inst_stale[i] = 1;
+  c->any_stale = true;
+}
+bool ctx_instance(vms_ctx* c, int64_t i, SysRange* out) {
+  if (c->inst_nodes.empty() || i < 0 || i + 1 >= (int64_t)c->inst_nodes.size()) return false;
+  *out = SysRange{c->inst_nodes[i], c->inst_nodes[i + 1], c->inst_elems[i], c->inst_elems[i + 1]};
+  return true;
+}
 int64_t* ctx_solver_stats(vms_ctx* c) { return c->solver_stats; }
 double* ctx_dscalar(vms_ctx* c) { return c->d_scalar; }
 double* ctx_hscalar(vms_ctx* c) { return c->h_scalar; }

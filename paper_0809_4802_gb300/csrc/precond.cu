@@ -273,19 +273,22 @@ __device__ __forceinline__ void warp_sum4(T a[4]) {
 }
 
 // T: element type of the factor (float: packed publication, double: sentinel publication).
+// Rows [n0, n0 + n_rows); `v` (forward sweep) and `out` are compact (index i - n0), the
+// publication buffer `pub`, the FP64 backward-sweep input `v` and the FP32 one `vp` are indexed by
+// node over the whole mesh.
 template <typename T, bool LOWER>
 __global__ void __launch_bounds__(ILU_SWARPS * 32)
     ilu_sweep_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                      const T* __restrict__ F, const T* __restrict__ Dinv,
                      const int32_t* __restrict__ dpos, const T* __restrict__ v,
                      const unsigned long long* __restrict__ vp, void* pub, T* __restrict__ out,
-                     int64_t n_nodes, uint32_t ep, unsigned long long* ticket,
+                     int64_t n0, int64_t n_rows, uint32_t ep, unsigned long long* ticket,
                      unsigned long long base, int* err) {
   const int lane = threadIdx.x & 31;
   for (;;) {
-    const int64_t t = claim_row(ticket, base, n_nodes, err, lane);
-    if (t >= n_nodes) return;
-    const int64_t i = LOWER ? t : n_nodes - 1 - t;
+    const int64_t t = claim_row(ticket, base, n_rows, err, lane);
+    if (t >= n_rows) return;
+    const int64_t i = LOWER ? n0 + t : n0 + n_rows - 1 - t;
     int32_t rp[4];
     for (int q = 0; q < 4; ++q) rp[q] = rowptr[4 * i + q];
     const int deg = (rowptr[4 * i + 1] - rp[0]) >> 2;
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(ILU_SWARPS * 32)
     T rhs = T(0), drow[4] = {T(0), T(0), T(0), T(0)};
     if (lane < 4) {
       if constexpr (LOWER) {
-        rhs = v[4 * i + lane];
+        rhs = v[4 * (i - n0) + lane];
       } else if constexpr (sizeof(T) == 4) {
         rhs = __uint_as_float((uint32_t)vp[4 * i + lane]);
       } else {
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(ILU_SWARPS * 32)
         st_packed(reinterpret_cast<unsigned long long*>(pub) + 4 * i + lane, res, ep);
       else
         st_relaxed_f64(reinterpret_cast<double*>(pub) + 4 * i + lane, res);
-      if (out) out[4 * i + lane] = res;
+      if (out) out[4 * (i - n0) + lane] = res;
     }
   }
 }
@@ -421,13 +424,19 @@ int build_pattern(vms_ctx* ctx, Ilu& p, const Mesh& m) {
   return VMS_OK;
 }
 
-int ensure_work(vms_ctx* ctx, Ilu& p, const Mesh& m, size_t elem) {
-  if (p.F && p.elem == elem) return VMS_OK;
-  for (void* b : {p.F, p.Dinv, p.y}) if (b) cudaFree(b);
-  p.F = p.Dinv = p.y = nullptr;
-  cudaError_t e = cudaMalloc(&p.F, elem * m.nnz);
-  if (e == cudaSuccess) e = cudaMalloc(&p.Dinv, elem * 16 * m.n_nodes);
-  if (e == cudaSuccess) e = cudaMalloc(&p.y, elem * 4 * m.n_nodes);
+int ensure_work(vms_ctx* ctx, Ilu& p, const Mesh& m, bool fp32) {
+  cudaError_t e = cudaSuccess;
+  if (!p.F) {
+    e = cudaMalloc(&p.F, sizeof(double) * m.nnz);
+    if (e == cudaSuccess) e = cudaMalloc(&p.Dinv, sizeof(double) * 16 * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&p.y, sizeof(double) * 4 * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&p.x64, sizeof(double) * 4 * m.n_nodes);
+  }
+  if (e == cudaSuccess && fp32 && !p.F32) {
+    e = cudaMalloc(&p.F32, sizeof(float) * m.nnz);
+    if (e == cudaSuccess) e = cudaMalloc(&p.Dinv32, sizeof(float) * 16 * m.n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&p.vals64, sizeof(double) * m.nnz);
+  }
   if (e == cudaSuccess && !p.flags) {
     e = cudaMalloc(&p.flags, sizeof(uint32_t) * m.n_nodes);
     if (e == cudaSuccess) e = cudaMemset(p.flags, 0, sizeof(uint32_t) * m.n_nodes);
@@ -445,15 +454,28 @@ int ensure_work(vms_ctx* ctx, Ilu& p, const Mesh& m, size_t elem) {
   if (e != cudaSuccess)
     return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
                     cudaGetErrorString(e));
-  p.elem = elem;
   return VMS_OK;
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ x, B* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = B(x[i]);
+}
+
+template <typename A, typename B>
+int convert(const A* x, B* y, int64_t n, cudaStream_t st) {
+  const int64_t b = (n + 255) / 256;
+  convert_kernel<A, B><<<(unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b)), 256, 0, st>>>(x, y, n);
+  return 1;
 }
 
 }  // namespace
 
 void free_ilu(Ilu& p) {
-  void* bufs[] = {p.dpos, p.lptr, p.pptr, p.pairs, p.F, p.Dinv, p.y, p.flags, p.yp, p.xp,
-                  p.tickets, p.err};
+  void* bufs[] = {p.dpos, p.lptr, p.pptr, p.pairs, p.F, p.Dinv, p.y, p.x64, p.F32, p.Dinv32,
+                  p.vals64, p.flags, p.yp, p.xp, p.tickets, p.err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   p = Ilu();
@@ -465,55 +487,68 @@ int ilu_factor(vms_ctx* ctx, Ilu& p, const Mesh& m, bool fp32, const void* value
   if (p.dpos && p.n_nodes != m.n_nodes) free_ilu(p);
   if (!p.dpos)
     if (int rc = build_pattern(ctx, p, m)) return rc;
-  if (int rc = ensure_work(ctx, p, m, fp32 ? sizeof(float) : sizeof(double))) return rc;
+  if (int rc = ensure_work(ctx, p, m, fp32)) return rc;
+  // The elimination always runs in FP64 (from the FP32 values in mixed precision): FP32
+  // elimination of the condensed systems of distorted meshes, whose condition numbers reach
+  // 1e9-1e10, gives factors too poor for GMRES to converge. Mixed precision then rounds the
+  // finished factor to FP32 for the FP32 sweeps.
+  const double* A = reinterpret_cast<const double*>(values);
+  if (fp32) {
+    *launches += convert<float, double>((const float*)values, p.vals64, m.nnz, st);
+    A = p.vals64;
+  }
   const unsigned ctas = resident_ctas(m.n_nodes, ILU_FWARPS, 152 * 8);
   const uint32_t ep = next_epoch(p, st);
-  if (fp32)
-    ilu_factor_kernel<float><<<ctas, ILU_FWARPS * 32, 0, st>>>(
-        m.rowptr, m.colidx, (const float*)values, (float*)p.F, (float*)p.Dinv, p.dpos, p.lptr,
-        p.pptr, p.pairs, m.n_nodes, p.flags, ep, p.tickets, p.base, p.err);
-  else
-    ilu_factor_kernel<double><<<ctas, ILU_FWARPS * 32, 0, st>>>(
-        m.rowptr, m.colidx, (const double*)values, (double*)p.F, (double*)p.Dinv, p.dpos, p.lptr,
-        p.pptr, p.pairs, m.n_nodes, p.flags, ep, p.tickets, p.base, p.err);
+  ilu_factor_kernel<double><<<ctas, ILU_FWARPS * 32, 0, st>>>(
+      m.rowptr, m.colidx, A, p.F, p.Dinv, p.dpos, p.lptr, p.pptr, p.pairs, m.n_nodes, p.flags, ep,
+      p.tickets, p.base, p.err);
   p.base += (unsigned long long)m.n_nodes + (unsigned long long)ctas * ILU_FWARPS;
+  *launches += 1;
+  if (fp32) {
+    *launches += convert<double, float>(p.F, p.F32, m.nnz, st);
+    *launches += convert<double, float>(p.Dinv, p.Dinv32, 16 * m.n_nodes, st);
+  }
   p.factored = true;
-  *launches = 1;
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
 }
 
 template <>
-int ilu_apply<float, float>(Ilu& p, const Mesh& m, const float* v, float* z, cudaStream_t st) {
-  const unsigned ctas = resident_ctas(m.n_nodes, ILU_SWARPS, ILU_SWEEP_CTAS);
-  const unsigned long long claims = (unsigned long long)m.n_nodes + (unsigned long long)ctas * ILU_SWARPS;
+int ilu_apply<float, float>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const float* v, float* z,
+                            cudaStream_t st) {
+  const int64_t rows = n1 - n0;
+  const unsigned ctas = resident_ctas(rows, ILU_SWARPS, ILU_SWEEP_CTAS);
+  const unsigned long long claims = (unsigned long long)rows + (unsigned long long)ctas * ILU_SWARPS;
   uint32_t ep = next_epoch(p, st);
   ilu_sweep_kernel<float, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, (const float*)p.F, nullptr, p.dpos, v, nullptr, p.yp, nullptr,
-      m.n_nodes, ep, p.tickets, p.base, p.err);
+      m.rowptr, m.colidx, p.F32, nullptr, p.dpos, v, nullptr, p.yp, nullptr, n0, rows,
+      ep, p.tickets, p.base, p.err);
   p.base += claims;
   ep = next_epoch(p, st);
   ilu_sweep_kernel<float, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, (const float*)p.F, (const float*)p.Dinv, p.dpos, nullptr, p.yp, p.xp, z,
-      m.n_nodes, ep, p.tickets, p.base, p.err);
+      m.rowptr, m.colidx, p.F32, p.Dinv32, p.dpos, nullptr, p.yp, p.xp, z,
+      n0, rows, ep, p.tickets, p.base, p.err);
   p.base += claims;
   return 2;
 }
 
 template <>
-int ilu_apply<double, double>(Ilu& p, const Mesh& m, const double* v, double* z, cudaStream_t st) {
-  const unsigned ctas = resident_ctas(m.n_nodes, ILU_SWARPS, ILU_SWEEP_CTAS);
-  const unsigned long long claims = (unsigned long long)m.n_nodes + (unsigned long long)ctas * ILU_SWARPS;
-  double* y = reinterpret_cast<double*>(p.y);
-  cudaMemsetAsync(y, 0xff, sizeof(double) * 4 * m.n_nodes, st);
+int ilu_apply<double, double>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const double* v,
+                              double* z, cudaStream_t st) {
+  const int64_t rows = n1 - n0;
+  const unsigned ctas = resident_ctas(rows, ILU_SWARPS, ILU_SWEEP_CTAS);
+  const unsigned long long claims = (unsigned long long)rows + (unsigned long long)ctas * ILU_SWARPS;
+  double* y = p.y;
+  double* x = p.x64;
+  cudaMemsetAsync(y + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
   ilu_sweep_kernel<double, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, (const double*)p.F, nullptr, p.dpos, v, nullptr, y, nullptr,
-      m.n_nodes, 0, p.tickets, p.base, p.err);
+      m.rowptr, m.colidx, p.F, nullptr, p.dpos, v, nullptr, y, nullptr, n0, rows, 0,
+      p.tickets, p.base, p.err);
   p.base += claims;
-  cudaMemsetAsync(z, 0xff, sizeof(double) * 4 * m.n_nodes, st);
+  cudaMemsetAsync(x + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
   ilu_sweep_kernel<double, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, (const double*)p.F, (const double*)p.Dinv, p.dpos, y, nullptr, z, nullptr,
-      m.n_nodes, 0, p.tickets, p.base, p.err);
+      m.rowptr, m.colidx, p.F, p.Dinv, p.dpos, y, nullptr, x, z, n0,
+      rows, 0, p.tickets, p.base, p.err);
   p.base += claims;
   return 4;
 }

@@ -16,11 +16,14 @@ struct Ilu {
   int32_t* pptr = nullptr;     // n_lower + 1: first update pair of each lower block
   uint16_t* pairs = nullptr;   // n_pairs: (jj | jk << 8) for A_ij -= L_ik U_kj
   int64_t n_nodes = 0, n_lower = 0, n_pairs = 0;
-  // factor and sweep work (element type of the matrix values)
-  void* F = nullptr;           // nnz: L (unit lower, strictly lower blocks) and U, CSR layout
-  void* Dinv = nullptr;        // n_nodes * 16: inverses of the diagonal blocks of U
-  void* y = nullptr;           // 4 n_nodes: forward-sweep result
-  size_t elem = 0;             // sizeof the element type F/Dinv/y were allocated for
+  // factor (always eliminated in FP64) and sweep work
+  double* F = nullptr;         // nnz: L (unit lower, strictly lower blocks) and U, CSR layout
+  double* Dinv = nullptr;      // n_nodes * 16: inverses of the diagonal blocks of U
+  float* F32 = nullptr;        // mixed precision: F rounded to FP32 (FP32 sweeps)
+  float* Dinv32 = nullptr;     // mixed precision: Dinv rounded to FP32
+  double* vals64 = nullptr;    // mixed precision: FP64 copy of the FP32 matrix values
+  double* y = nullptr;         // 4 n_nodes: FP64 forward-sweep publication
+  double* x64 = nullptr;       // 4 n_nodes: FP64 backward-sweep publication
   uint32_t* flags = nullptr;   // n_nodes: row-ready epochs (factorisation, FP64 sweeps)
   unsigned long long* yp = nullptr;  // 4 n_nodes: FP32 forward sweep, (epoch << 32 | value bits)
   unsigned long long* xp = nullptr;  // 4 n_nodes: FP32 backward sweep, same packing
@@ -44,12 +47,16 @@ int ilu_factor(vms_ctx* ctx, Ilu& p, const Mesh& m, bool fp32, const void* value
                int* launches);
 
 // z = (LU)^-1 v. T is the element type of the factor, VT the vector type. Returns the launches.
+// Rows of nodes [n0, n1) only (a block of the matrix with no couplings outside it); v and z are
+// compact: entry 4 (i - n0) + c belongs to node i.
 template <typename T, typename VT>
-int ilu_apply(Ilu& p, const Mesh& m, const VT* v, VT* z, cudaStream_t st);
+int ilu_apply(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const VT* v, VT* z, cudaStream_t st);
 template <>
-int ilu_apply<float, float>(Ilu& p, const Mesh& m, const float* v, float* z, cudaStream_t st);
+int ilu_apply<float, float>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const float* v, float* z,
+                            cudaStream_t st);
 template <>
-int ilu_apply<double, double>(Ilu& p, const Mesh& m, const double* v, double* z, cudaStream_t st);
+int ilu_apply<double, double>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const double* v,
+                              double* z, cudaStream_t st);
 
 // Read the device error word (synchronises `st`); on error, resets the claim counters and flags.
 int ilu_status(vms_ctx* ctx, Ilu& p, cudaStream_t st);

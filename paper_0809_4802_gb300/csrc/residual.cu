@@ -5,11 +5,13 @@
 
 namespace vms {
 
+// Threads per block: 64 by default; the autotuner (vms_autotune) may choose 32.
 constexpr int RES_THREADS = 64;
 
 // Monomial coefficients live in shared memory, one column per thread (conflict-free).
+template <int THREADS>
 struct SmemStore {
-  double (*sc)[RES_THREADS];
+  double (*sc)[THREADS];
   int tid;
   __device__ __forceinline__ double get(int k) const { return sc[k][tid]; }
   __device__ __forceinline__ void set(int k, double v) { sc[k][tid] = v; }
@@ -32,17 +34,17 @@ struct GlobalTable {
   __device__ __forceinline__ double w(int q) const { return __ldg(&t[q].w); }
 };
 
-template <bool TRANSIENT, bool FORCE>
-__global__ void __launch_bounds__(RES_THREADS) residual_kernel(
+template <bool TRANSIENT, bool FORCE, int THREADS>
+__global__ void __launch_bounds__(THREADS) residual_kernel(
     const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u,
     const double4_32a* __restrict__ uprev, const int32_t* __restrict__ conn,
     const double* __restrict__ beta, KParams kp, const QpRow* __restrict__ qp, int64_t first,
     int64_t count,
     double* __restrict__ elemR, double* __restrict__ resid, const uint32_t* __restrict__ dir_mask,
     int64_t n_nodes, int mode, unsigned int* __restrict__ flags) {
-  __shared__ double sc[RC_N][RES_THREADS];
+  __shared__ double sc[RC_N][THREADS];
   const int tid = threadIdx.x;
-  const int64_t t = (int64_t)blockIdx.x * RES_THREADS + tid;
+  const int64_t t = (int64_t)blockIdx.x * THREADS + tid;
   if (t >= count) return;
   const int64_t e = first + t;
 
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(
     nd[0] = c0.x; nd[1] = c0.y; nd[2] = c0.z; nd[3] = c0.w;
     nd[4] = c1.x; nd[5] = c1.y; nd[6] = c1.z; nd[7] = c1.w;
   }
-  SmemStore C{sc, tid};
+  SmemStore<THREADS> C{sc, tid};
   {
     double X[8][3], U[8][4], Up[8][3];
 #pragma unroll
@@ -71,7 +73,8 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(
   }
   const double bet[3] = {beta[3 * e + 0], beta[3 * e + 1], beta[3 * e + 2]};
   double Rcp[32], Rf[3];
-  const bool ok = residual_qp_loop<TRANSIENT, FORCE>(C, GlobalTable{qp}, kp.nq, bet, kp.nut, kp.tau,
+  const double nut = kp.nu_e ? kp.visc_factor * __ldg(kp.nu_e + e) : kp.nut;
+  const bool ok = residual_qp_loop<TRANSIENT, FORCE>(C, GlobalTable{qp}, kp.nq, bet, nut, kp.tau,
                                                      kp.f, Rcp, Rf);
   if (!ok) atomicOr(flags, FLAG_NEG_JACOBIAN);
   bool finite = isfinite(Rf[0]) && isfinite(Rf[1]) && isfinite(Rf[2]);
@@ -97,21 +100,31 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(
   }
 }
 
+template <int THREADS>
+static void launch_r(const Mesh& m, const State& s, const KParams& kp, const QpRow* qp,
+                     double* elemR, double* resid, int64_t first, int64_t count, int mode,
+                     unsigned int* flags, cudaStream_t st) {
+  const dim3 grid((unsigned)((count + THREADS - 1) / THREADS));
+#define VMS_RES_ARGS m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, first, count, elemR, resid, \
+                     m.dir_mask, m.n_nodes, mode, flags
+  if (kp.transient) {
+    if (kp.has_force) residual_kernel<true, true, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
+    else residual_kernel<true, false, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
+  } else {
+    if (kp.has_force) residual_kernel<false, true, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
+    else residual_kernel<false, false, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
+  }
+#undef VMS_RES_ARGS
+}
+
 int launch_residual(const Mesh& m, const State& s, const KParams& kp, const QpRow* qp,
                      double* elemR, double* resid, int64_t first, int64_t count, int mode,
                      unsigned int* flags, cudaStream_t st) {
   if (count <= 0) return 0;
-  const dim3 grid((unsigned)((count + RES_THREADS - 1) / RES_THREADS));
-#define VMS_RES_ARGS m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, first, count, elemR, resid, \
-                     m.dir_mask, m.n_nodes, mode, flags
-  if (kp.transient) {
-    if (kp.has_force) residual_kernel<true, true><<<grid, RES_THREADS, 0, st>>>(VMS_RES_ARGS);
-    else residual_kernel<true, false><<<grid, RES_THREADS, 0, st>>>(VMS_RES_ARGS);
-  } else {
-    if (kp.has_force) residual_kernel<false, true><<<grid, RES_THREADS, 0, st>>>(VMS_RES_ARGS);
-    else residual_kernel<false, false><<<grid, RES_THREADS, 0, st>>>(VMS_RES_ARGS);
-  }
-#undef VMS_RES_ARGS
+  if (kp.residual_threads == 32)
+    launch_r<32>(m, s, kp, qp, elemR, resid, first, count, mode, flags, st);
+  else
+    launch_r<RES_THREADS>(m, s, kp, qp, elemR, resid, first, count, mode, flags, st);
   return 1;
 }
 

@@ -16,7 +16,8 @@
 namespace vms {
 
 void free_solver(SolverWork& s) {
-  void* bufs[] = {s.x, s.r, s.V, s.Z, s.Dinv, s.h, s.rfull, s.bf, s.xf, s.cx, s.pv, s.pz};
+  void* bufs[] = {s.x, s.r, s.V, s.Z, s.Dinv, s.h, s.rfull, s.bf, s.xf, s.cx, s.pv, s.pz, s.Zf,
+                  s.xb, s.rb};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free_ilu(s.ilu);
@@ -26,33 +27,41 @@ void free_solver(SolverWork& s) {
 // ---------------------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------------------
+// y = A x over the rows of nodes [n0, n1) (row0 = 4 n0); x and y are compact (column c of the
+// block is x[c - row0]). One warp per scalar row; FP32 accumulation when matrix and vectors are
+// FP32 (the inner solve of the mixed mode), FP64 otherwise.
 template <typename T, typename VT>
 __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ colidx,
                                                    const T* __restrict__ val,
                                                    const VT* __restrict__ x, VT* __restrict__ y,
-                                                   int64_t n_rows) {
+                                                   int64_t row0, int64_t n_rows) {
+  using Acc = typename std::conditional<sizeof(T) == 4 && sizeof(VT) == 4, float, double>::type;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n_rows) return;
-  const int32_t b = rowptr[row], e = rowptr[row + 1];
-  double s = 0.0;
-  for (int32_t k = b + lane; k < e; k += 32) s = fma((double)val[k], (double)x[colidx[k]], s);
+  const int32_t b = rowptr[row0 + row], e = rowptr[row0 + row + 1];
+  Acc s = Acc(0);
+  for (int32_t k = b + lane; k < e; k += 32) s = fma((Acc)val[k], (Acc)x[colidx[k] - row0], s);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) y[row] = VT(s);
 }
 
 template <typename T, typename VT>
-static int spmv(const Mesh& m, const void* values, const VT* x, VT* y, cudaStream_t st) {
-  const int64_t n = 4 * m.n_nodes;
+static int spmv(const Mesh& m, const SysRange& R, const void* values, const VT* x, VT* y,
+                cudaStream_t st) {
+  const int64_t n = 4 * R.nodes();
   const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
-  spmv_kernel<T, VT><<<blocks, 256, 0, st>>>(m.rowptr, m.colidx, (const T*)values, x, y, n);
+  spmv_kernel<T, VT><<<blocks, 256, 0, st>>>(m.rowptr, m.colidx, (const T*)values, x, y,
+                                             4 * R.n0, n);
   return 1;
 }
 
 int launch_spmv(const Mesh& m, const void* values, bool fp32, const double* x, double* y,
                 cudaStream_t st) {
-  return fp32 ? spmv<float, double>(m, values, x, y, st) : spmv<double, double>(m, values, x, y, st);
+  const SysRange all{0, m.n_nodes, 0, m.n_elems};
+  return fp32 ? spmv<float, double>(m, all, values, x, y, st)
+              : spmv<double, double>(m, all, values, x, y, st);
 }
 
 // Inverse of each node's 4x4 diagonal block (Gauss-Jordan with partial pivoting, FP64); a block
@@ -211,15 +220,16 @@ __global__ void axpby_kernel(double a, const A* x, double b, const B* y, C* out,
 }
 
 // Fine-scale recovery (Section 5): dbeta_e = -(K_ff^-1 R_f + K_ff^-1 K_fc du_e); beta += dbeta.
+// Elements [e0, e1); du is compact over the nodes from n0 on.
 template <typename T>
 __global__ void recover_kernel(const int32_t* __restrict__ conn, const T* __restrict__ recX,
                                const double* __restrict__ recY, const double* __restrict__ du,
-                               double* __restrict__ beta, int64_t n_elems) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_elems) return;
+                               double* __restrict__ beta, int64_t e0, int64_t e1, int64_t n0) {
+  const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= e1) return;
   double s[3] = {recY[3 * e], recY[3 * e + 1], recY[3 * e + 2]};
   for (int a = 0; a < 8; ++a) {
-    const int64_t nd = conn[8 * e + a];
+    const int64_t nd = conn[8 * e + a] - n0;
     for (int c = 0; c < 4; ++c) {
       const double d = du[4 * nd + c];
       for (int m = 0; m < 3; ++m) s[m] += (double)recX[96 * e + 32 * m + 4 * a + c] * d;
@@ -241,25 +251,24 @@ struct Gmres {
   const Mesh& m;
   SolverWork& w;
   cudaStream_t st;
-  int64_t n;
+  int64_t n;      // 4 R.nodes(): length of every (compact) vector
+  SysRange R;
+  void* Zflex = nullptr;  // flexible GMRES: restart preconditioned vectors kept (else null)
 
   // z = M^-1 v with the preconditioner chosen for this solve
   template <typename T, typename VT>
   void precond(const VT* v, VT* z) {
     KScope k(ctx, VMS_K_PRECOND);
     if constexpr (std::is_same<T, float>::value && std::is_same<VT, double>::value) {
-      if (w.use_ilu) {  // FP32 factor applied to FP64 vectors through FP32 copies
-        axpby_kernel<double, double, float><<<grid_for(n), 256, 0, st>>>(1.0, v, 0.0, (const double*)nullptr, w.pv, n);
-        k.add(1 + ilu_apply<float, float>(w.ilu, m, w.pv, w.pz, st));
-        axpby_kernel<float, float, double><<<grid_for(n), 256, 0, st>>>(1.0, w.pz, 0.0, (const float*)nullptr, z, n);
-        k.add(1);
+      if (w.use_ilu) {  // FP64 vectors: the FP64 factor the FP32 one was rounded from
+        k.add(ilu_apply<double, double>(w.ilu, m, R.n0, R.n1, v, z, st));
         return;
       }
     }
     if (w.use_ilu) {
-      k.add(ilu_apply<T, VT>(w.ilu, m, v, z, st));
+      k.add(ilu_apply<T, VT>(w.ilu, m, R.n0, R.n1, v, z, st));
     } else {
-      block_apply_kernel<VT><<<grid_for(m.n_nodes), 256, 0, st>>>(w.Dinv, v, z, m.n_nodes);
+      block_apply_kernel<VT><<<grid_for(R.nodes()), 256, 0, st>>>(w.Dinv + 16 * R.n0, v, z, R.nodes());
       k.add(1);
     }
   }
@@ -315,8 +324,9 @@ struct Gmres {
       for (; j < restart && it < maxit; ++j, ++it) {
         VT* vj = V + (int64_t)j * n;
         VT* vn = V + (int64_t)(j + 1) * n;
-        precond<T, VT>(vj, z);
-        { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, values, z, vn, st)); }
+        VT* zj = Zflex ? reinterpret_cast<VT*>(Zflex) + (int64_t)j * n : z;
+        precond<T, VT>(vj, zj);
+        { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, R, values, zj, vn, st)); }
         // CGS2 against V_0..V_j: first pass coefficients into hd[H_PASS1..], second into hd[H_PASS2..]
         const int kk = j + 1;
         double* partial = hd + H_PART;
@@ -372,19 +382,25 @@ struct Gmres {
         y[i] = H[i * restart + i] != 0.0 ? s / H[i * restart + i] : 0.0;
       }
       cudaMemcpyAsync(hd + H_Y, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st);
-      {
+      if (Zflex) {  // x += Z y with the kept preconditioned vectors
         KScope k(ctx, VMS_K_KRYLOV);
-        combine_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, n, hd + H_Y, j, z, n);
+        combine_kernel<VT><<<grid_for(n), 256, 0, st>>>(reinterpret_cast<const VT*>(Zflex), n, hd + H_Y, j, V + n, n);
         k.add(1);
+      } else {      // x += M^-1 V y
+        {
+          KScope k(ctx, VMS_K_KRYLOV);
+          combine_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, n, hd + H_Y, j, z, n);
+          k.add(1);
+        }
+        precond<T, VT>(z, V + n);
       }
-      precond<T, VT>(z, V + n);
       {
         KScope k(ctx, VMS_K_KRYLOV);
         axpby_kernel<VT, VT, VT><<<grid_for(n), 256, 0, st>>>(1.0, x, 1.0, V + n, x, n);
         k.add(1);
       }
       // restart: r = b - A x into V_0
-      { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, values, x, z, st)); }
+      { KScope k(ctx, VMS_K_SPMV); k.add(spmv<T, VT>(m, R, values, x, z, st)); }
       {
         KScope k(ctx, VMS_K_KRYLOV);
         axpby_kernel<VT, VT, VT><<<grid_for(n), 256, 0, st>>>(1.0, b, -1.0, z, V, n);
@@ -427,6 +443,8 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
   if (e == cudaSuccess) e = cudaMalloc(&w.bf, sizeof(float) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.xf, sizeof(float) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.cx, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.xb, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.rb, sizeof(double) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.pv, sizeof(float) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.pz, sizeof(float) * n);
   if (e != cudaSuccess) {
@@ -440,25 +458,33 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
 }
 
 // Solve S du = -rhs into w.x (FP64). Mixed: FP32 GMRES inside FP64 iterative refinement.
-static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* iters_out,
-                        double* rel_out) {
+static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit, int restart,
+                        int* iters_out, double* rel_out) {
   const Mesh& m = ctx_mesh(ctx);
   Work& wk = ctx_work(ctx);
   SolverWork& w = ctx_solver(ctx);
   cudaStream_t st = ctx_stream(ctx);
-  const int64_t n = 4 * m.n_nodes;
+  const int64_t n = 4 * R.nodes();
   const bool f32 = ctx_fp32(ctx);
   if (restart < 1 || restart > MAX_RESTART || maxit < 1 || !(rtol > 0.0))
     return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid solver parameters");
   if (int rc = ensure_solver(ctx, restart)) return rc;
-  w.use_ilu = ctx_precond(ctx) == VMS_PRECOND_ILU0;
-  {
+  const int kind = ctx_precond(ctx);
+  w.use_ilu = kind == VMS_PRECOND_ILU0;
+  // the preconditioner covers the whole matrix (its blocks are independent) and is set up once
+  // per assembly and kind
+  if (w.precond_for != wk.assembly_id || w.precond_kind != kind || (w.use_ilu && !w.ilu.factored)) {
     KScope k(ctx, VMS_K_PRECOND);
+    w.precond_for = wk.assembly_id;
+    w.precond_kind = kind;
     if (w.use_ilu) {
       int launched = 0;
       const int rc = ilu_factor(ctx, w.ilu, m, f32, wk.values, st, &launched);
       k.add(launched);
-      if (rc) return rc;
+      if (rc) {
+        w.precond_for = 0;
+        return rc;
+      }
     } else if (f32) {
       block_diag_inv_kernel<float><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, m.n_nodes, w.Dinv);
       k.add(1);
@@ -470,7 +496,7 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
   // b = -rhs (FP64) in w.r
   {
     KScope k(ctx, VMS_K_KRYLOV);
-    axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(-1.0, wk.rhs, 0.0, (const double*)nullptr, w.r, n);
+    axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(-1.0, wk.rhs + 4 * R.n0, 0.0, (const double*)nullptr, w.r, n);
     k.add(1);
   }
   double* hd = w.h;
@@ -481,7 +507,7 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
     reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
     k.add(2);
   }
-  Gmres G{ctx, m, w, st, n};
+  Gmres G{ctx, m, w, st, n, R};
   if (int rc = G.sync_host(&bnorm2, hd + H_NORM, sizeof(double))) return rc;
   const double bnorm = std::sqrt(bnorm2);
   if (bnorm == 0.0) {
@@ -523,7 +549,7 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
   double r2 = 0.0;
   for (int outer = 0;; ++outer) {
     // FP64 residual of the refinement
-    { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, wk.values, w.x, rfull, st)); }
+    { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, R, wk.values, w.x, rfull, st)); }
     {
       KScope k(ctx, VMS_K_KRYLOV);
       axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.r, -1.0, rfull, rfull, n);
@@ -537,9 +563,20 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
     }
     if ((rc = G.sync_host(&r2, hd + H_NORM, sizeof(double)))) break;
     rel = std::sqrt(r2) / bnorm;
-    if (rel <= rtol || !(rel == rel) || outer == 20 || total >= maxit || last_it == 0) break;
+    if (!(rel <= prev_rel) && outer > 0) {
+      // the last FP32 correction made things worse (or not finite): return to the iterate before it
+      cudaMemcpyAsync(w.x, w.xb, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(rfull, w.rb, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+      rel = prev_rel;
+      r2 = (rel * bnorm) * (rel * bnorm);
+      stalled = true;
+      break;
+    }
+    if (rel <= rtol || outer == 20 || total >= maxit || last_it == 0) break;
     if (rel > 0.5 * prev_rel) { stalled = true; break; }
     prev_rel = rel;
+    cudaMemcpyAsync(w.xb, w.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(w.rb, rfull, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
     {
       KScope k(ctx, VMS_K_KRYLOV);
       axpby_kernel<double, double, float><<<grid_for(n), 256, 0, st>>>(1.0, rfull, 0.0, (const double*)nullptr, bf, n);
@@ -563,8 +600,17 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
     // S c = b - S x with FP64 Krylov vectors, the FP32 matrix values and the FP32 preconditioner
     int it = 0;
     double irel = 0.0;
+    // flexible GMRES: the FP32 factor applied through FP32 copies is not exactly linear
+    if (!w.Zf) {
+      const cudaError_t e = cudaMalloc(&w.Zf, sizeof(double) * (size_t)w.n * w.restart);
+      if (e != cudaSuccess)
+        return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
+                        cudaGetErrorString(e));
+    }
+    G.Zflex = w.Zf;
     rc = G.solve<float, double>(wk.values, rfull, w.cx, std::sqrt(r2), rtol / rel, maxit - total,
                                 restart, &it, &irel);
+    G.Zflex = nullptr;
     if (rc == VMS_OK) {
       total += it;
       {
@@ -572,7 +618,7 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
         axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.x, 1.0, w.cx, w.x, n);
         k.add(1);
       }
-      { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, wk.values, w.x, rfull, st)); }
+      { KScope k(ctx, VMS_K_SPMV); k.add(spmv<float, double>(m, R, wk.values, w.x, rfull, st)); }
       {
         KScope k(ctx, VMS_K_KRYLOV);
         axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.r, -1.0, rfull, rfull, n);
@@ -596,20 +642,21 @@ static int linear_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int* 
   return rel <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "refined GMRES reached maxit");
 }
 
-static int recover_and_update(vms_ctx* ctx) {
+static int recover_and_update(vms_ctx* ctx, const SysRange& R) {
   const Mesh& m = ctx_mesh(ctx);
   State& s = ctx_state(ctx);
   Work& wk = ctx_work(ctx);
   SolverWork& w = ctx_solver(ctx);
   cudaStream_t st = ctx_stream(ctx);
   KScope k(ctx, VMS_K_KRYLOV);
-  const unsigned eb = (unsigned)((m.n_elems + 127) / 128);
+  const int64_t ne = R.e1 - R.e0;
+  const unsigned eb = (unsigned)((ne + 127) / 128 > 0 ? (ne + 127) / 128 : 1);
   if (ctx_fp32(ctx))
-    recover_kernel<float><<<eb, 128, 0, st>>>(m.conn, (const float*)wk.recX, wk.recY, w.x, s.beta, m.n_elems);
+    recover_kernel<float><<<eb, 128, 0, st>>>(m.conn, (const float*)wk.recX, wk.recY, w.x, s.beta, R.e0, R.e1, R.n0);
   else
-    recover_kernel<double><<<eb, 128, 0, st>>>(m.conn, (const double*)wk.recX, wk.recY, w.x, s.beta, m.n_elems);
-  const int64_t n = 4 * m.n_nodes;
-  double* u = reinterpret_cast<double*>(s.u);
+    recover_kernel<double><<<eb, 128, 0, st>>>(m.conn, (const double*)wk.recX, wk.recY, w.x, s.beta, R.e0, R.e1, R.n0);
+  const int64_t n = 4 * R.nodes();
+  double* u = reinterpret_cast<double*>(s.u) + 4 * R.n0;
   axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, u, 1.0, w.x, u, n);
   k.add(2);
   const cudaError_t e = cudaGetLastError();
@@ -645,16 +692,25 @@ namespace vms {
 // late Newton systems of a jittered 32^3 cavity, GMRES(100) too, GMRES(120) converges).
 constexpr int NEWTON_RESTART = 150;
 
+static SysRange whole(vms_ctx* ctx) {
+  const Mesh& m = ctx_mesh(ctx);
+  return SysRange{0, m.n_nodes, 0, m.n_elems};
+}
+
 // Solve, then (if update) recover the bubble increments and update the state. A solve that stops
 // at maxit is still applied when its relative residual is below accept_below (inexact Newton).
-static int solve_impl(vms_ctx* ctx, double rtol, int maxit, int restart, int update,
-                      double accept_below, int* iters, double* rel) {
+// instance < 0: the whole system (its state changes invalidate the assembly); instance >= 0: one
+// diagonal block (its update leaves the other instances' blocks valid).
+static int solve_impl(vms_ctx* ctx, const SysRange& R, int64_t instance, double rtol, int maxit,
+                      int restart, int update, double accept_below, int* iters, double* rel) {
   if (!ctx) return VMS_ERR_INVALID_ARG;
   if (!ctx_work(ctx).assembled) return ctx_fail(ctx, VMS_ERR_STATE, "nothing assembled");
+  if (ctx_stale(ctx, instance))
+    return ctx_fail(ctx, VMS_ERR_STATE, "state updated since the last assembly");
   cudaSetDevice(ctx_device(ctx));
   int it = 0;
   double r = 0.0;
-  int rc = linear_solve(ctx, rtol, maxit, restart, &it, &r);
+  int rc = linear_solve(ctx, R, rtol, maxit, restart, &it, &r);
   ctx_solver_stats(ctx)[0] += 1;
   ctx_solver_stats(ctx)[1] += it;
   if (iters) *iters = it;
@@ -662,8 +718,9 @@ static int solve_impl(vms_ctx* ctx, double rtol, int maxit, int restart, int upd
   if (rc == VMS_ERR_KRYLOV_MAXIT && r < accept_below) rc = VMS_OK;
   if (rc != VMS_OK) return rc;
   if (update) {
-    if (int rc2 = recover_and_update(ctx)) return rc2;
-    ctx_work(ctx).assembled = false;  // the state changed
+    if (int rc2 = recover_and_update(ctx, R)) return rc2;
+    if (instance < 0) ctx_work(ctx).assembled = false;  // the state changed
+    else ctx_mark_stale(ctx, instance);
   }
   const cudaError_t e = cudaStreamSynchronize(ctx_stream(ctx));
   return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
@@ -675,7 +732,15 @@ extern "C" {
 
 int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
               double* rel) {
-  return solve_impl(ctx, rtol, maxit, restart, update, 0.0, iters, rel);
+  return solve_impl(ctx, whole(ctx), -1, rtol, maxit, restart, update, 0.0, iters, rel);
+}
+
+int vms_solve_instance(vms_ctx* ctx, int64_t instance, double rtol, int maxit, int restart,
+                       int update, int* iters, double* rel) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  SysRange R;
+  if (!ctx_instance(ctx, instance, &R)) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "no such instance");
+  return solve_impl(ctx, R, instance, rtol, maxit, restart, update, 0.0, iters, rel);
 }
 
 int vms_newton_step(vms_ctx* ctx, double* res_norm) {
@@ -686,7 +751,7 @@ int vms_newton_step(vms_ctx* ctx, double* res_norm) {
   if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
   int it = 0;
   double rel = 0.0;
-  return solve_impl(ctx, 1e-10, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel);
+  return solve_impl(ctx, whole(ctx), -1, 1e-10, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel);
 }
 
 int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist) {
@@ -704,7 +769,7 @@ int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* h
                                                0.5 * rtol * r0 / r, 1e-12}));
     int it = 0;
     double rel = 0.0;
-    if (int rc = solve_impl(ctx, eta, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel)) return rc;
+    if (int rc = solve_impl(ctx, whole(ctx), -1, eta, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel)) return rc;
     ++k;
     if (int rc = vms_residual(ctx, &r, nullptr)) return rc;
     if (hist) hist[k] = r;

@@ -6,6 +6,14 @@
 
 namespace vms {
 
+// A block of the condensed system: nodes [n0, n1) and elements [e0, e1), closed under the mesh
+// connectivity (no element couples it to other nodes), so the rows of its nodes have no columns
+// outside it. The whole mesh is one such block.
+struct SysRange {
+  int64_t n0 = 0, n1 = 0, e0 = 0, e1 = 0;
+  int64_t nodes() const { return n1 - n0; }
+};
+
 struct SolverWork {
   double* x = nullptr;       // n
   double* r = nullptr;       // n
@@ -19,8 +27,13 @@ struct SolverWork {
   double* cx = nullptr;      // n: FP64 correction of the final stage of the mixed solve
   float* pv = nullptr;       // n: FP32 copy of a vector the FP32 factor is applied to
   float* pz = nullptr;       // n: its FP32 result
+  double* Zf = nullptr;      // restart * n: preconditioned vectors of the flexible final stage
+  double* xb = nullptr;      // n: refinement iterate before the last FP32 correction
+  double* rb = nullptr;      // n: its FP64 residual
   Ilu ilu;                   // ILU(0) pattern, factor and sweep work
   bool use_ilu = false;      // preconditioner of the current solve
+  uint64_t precond_for = 0;  // assembly the preconditioner was set up for (0: none)
+  int precond_kind = -1;     // VMS_PRECOND_* it was set up as
   int restart = 0;
   int64_t n = 0;
 };
@@ -36,6 +49,9 @@ cudaStream_t ctx_stream(vms_ctx* c);
 int ctx_device(vms_ctx* c);
 bool ctx_fp32(vms_ctx* c);
 int ctx_precond(vms_ctx* c);
+bool ctx_instance(vms_ctx* c, int64_t i, SysRange* out);
+bool ctx_stale(vms_ctx* c, int64_t i);
+void ctx_mark_stale(vms_ctx* c, int64_t i);
 int64_t* ctx_solver_stats(vms_ctx* c);
 double* ctx_dscalar(vms_ctx* c);
 double* ctx_hscalar(vms_ctx* c);

@@ -10,8 +10,9 @@
 
 namespace vms {
 
-// warps per block: FP64 records are twice the size, so the FP64 kernel uses smaller blocks to keep
-// several blocks (and enough warps for the FP64 pipe) resident per SM
+// default warps per block: FP64 records are twice the size, so the FP64 kernel uses smaller
+// blocks to keep several blocks (and enough warps for the FP64 pipe) resident per SM. The
+// autotuner (vms_autotune) may choose another count from tan_warp_choices.
 template <typename T> constexpr int tan_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <typename T>
@@ -24,6 +25,76 @@ template <typename T>
 __host__ __device__ inline size_t tan_table_bytes(int nq) {
   return ((size_t)37 * nq * sizeof(T) + 15) & ~size_t(15);
 }
+
+// An FP32 K_ff is accurate to about 1e-7 of its largest entry (FP32 node data and quadrature
+// sums), which is 1e-7 * cond(K_ff) relative to its weakest direction; the condensation divides by
+// that direction, so elements whose K_ff is ill-conditioned (convection-dominated coarse elements)
+// get their K_ff again in FP64 before they are condensed. cond_inf above this value triggers it,
+// which bounds the K_ff part of the error of S_e near 1e-7 * 16.
+constexpr double KFF_FP64_COND = 16.0;
+
+#if defined(__CUDACC__)
+// K_ff in FP64 (Eq. NewtonUpdate2, fine-fine block: int b (b L + I v.d) + nut I d.d) from the FP64
+// node data of element e; lanes take quadrature points, the warp sums. Every lane returns K.
+__device__ void kff_fp64(int lane, int nq, const int nd[8], const double4_32a* __restrict__ xyz,
+                         const double4_32a* __restrict__ u, const double* __restrict__ beta,
+                         int64_t e, const double* __restrict__ tab, double nut, double K[9]) {
+  VMS_UNROLL
+  for (int j = 0; j < 9; ++j) K[j] = 0.0;
+  const double bt[3] = {beta[3 * e], beta[3 * e + 1], beta[3 * e + 2]};
+  for (int q = lane; q < nq; q += 32) {
+    const double* N = tab + 8 * q;
+    const double* dN = tab + 8 * nq + 24 * q;
+    const double bq = tab[32 * nq + q];
+    const double* db = tab + 33 * nq + 3 * q;
+    const double wq = tab[36 * nq + q];
+    double J[3][3] = {}, G[3][3] = {}, v[3] = {};
+    VMS_UNROLL
+    for (int a = 0; a < 8; ++a) {
+      const double4_32a x = xyz[nd[a]];
+      const double4_32a w = u[nd[a]];
+      const double xa[3] = {x.x, x.y, x.z}, va[3] = {w.x, w.y, w.z};
+      VMS_UNROLL
+      for (int i = 0; i < 3; ++i) {
+        v[i] += __ldg(N + a) * va[i];
+        VMS_UNROLL
+        for (int al = 0; al < 3; ++al) {
+          const double dn = __ldg(dN + 3 * a + al);
+          J[i][al] += xa[i] * dn;
+          G[i][al] += va[i] * dn;
+        }
+      }
+    }
+    double cof[3][3];
+    double det = cofactor3(J, cof);
+    if (!(det > 0.0)) det = 1.0;  // the FP32 pass has flagged the element already
+    const double r = 1.0 / det;
+    double d[3];
+    VMS_UNROLL
+    for (int j = 0; j < 3; ++j) d[j] = (__ldg(db) * cof[j][0] + __ldg(db + 1) * cof[j][1] + __ldg(db + 2) * cof[j][2]) * r;
+    VMS_UNROLL
+    for (int i = 0; i < 3; ++i) {
+      v[i] += bq * bt[i];
+      VMS_UNROLL
+      for (int al = 0; al < 3; ++al) G[i][al] += bt[i] * __ldg(db + al);
+    }
+    const double om = wq * det;
+    const double cd = v[0] * d[0] + v[1] * d[1] + v[2] * d[2];
+    const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    VMS_UNROLL
+    for (int i = 0; i < 3; ++i)
+      VMS_UNROLL
+      for (int k = 0; k < 3; ++k) {
+        // L_ik = sum_al G[i][al] (J^-1)[al][k], (J^-1)[al][k] = cof[k][al] / det
+        const double L = (G[i][0] * cof[k][0] + G[i][1] * cof[k][1] + G[i][2] * cof[k][2]) * r;
+        K[3 * i + k] += om * (bq * (bq * L + (i == k ? cd : 0.0)) + (i == k ? nut * dd : 0.0));
+      }
+  }
+  VMS_UNROLL
+  for (int j = 0; j < 9; ++j)
+    for (int o = 16; o > 0; o >>= 1) K[j] += __shfl_xor_sync(0xffffffffu, K[j], o);
+}
+#endif
 
 // Add four contiguous values (one row of a 4x4 node block; 16-byte aligned in FP32 because
 // every row offset and block offset is a multiple of 4). Constrained columns carry zeros.
@@ -49,14 +120,17 @@ template <typename T> struct NodeVec;
 template <> struct NodeVec<double> { using type = double4_32a; };
 template <> struct NodeVec<float> { using type = float4; };
 
-template <typename T, bool ELEM_OUT, bool ATOMIC>
-__global__ void __launch_bounds__(tan_warps<T>() * 32) tangent_kernel(
+template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
     const typename NodeVec<T>::type* __restrict__ xyz, const typename NodeVec<T>::type* __restrict__ u,
     const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
-    int nq, T nut, T tau, int64_t first, int64_t count, const int32_t* __restrict__ elem_list,
+    int nq, T nut, T tau, const double* __restrict__ nu_e, double visc_factor,
+    const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
+    const double* __restrict__ beta64, const double* __restrict__ tab64, int64_t first,
+    int64_t count, const int32_t* __restrict__ elem_list,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
-    T* __restrict__ recW, double* __restrict__ recKinv, double* __restrict__ oS,
+    double* __restrict__ recW, double* __restrict__ recKinv, double* __restrict__ oS,
     double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
     double* __restrict__ oKff, unsigned int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -67,7 +141,6 @@ __global__ void __launch_bounds__(tan_warps<T>() * 32) tangent_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpArea<T>& W = *reinterpret_cast<WarpArea<T>*>(smem + tan_table_bytes<T>(nq) +
                                                    warp * tan_warp_bytes<T>(nq));
-  constexpr int WARPS = tan_warps<T>();
   const int64_t total = (int64_t)gridDim.x * WARPS;
   for (int64_t it = (int64_t)blockIdx.x * WARPS + warp; it < count; it += total) {
     const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
@@ -85,12 +158,13 @@ __global__ void __launch_bounds__(tan_warps<T>() * 32) tangent_kernel(
       W.flag = 0u;
     }
     __syncwarp();
+    const T nut_e = nu_e ? T(visc_factor * __ldg(nu_e + e)) : nut;
     LaneAcc<T> A;
     tan_zero(A);
     for (int q0 = 0; q0 < nq; q0 += 32) {
-      tan_phase1(lane, q0, nq, W, tab, nut, tau, A);
+      tan_phase1(lane, q0, nq, W, tab, nut_e, tau, A);
       __syncwarp();
-      tan_phase2(lane, nq - q0 < 32 ? nq - q0 : 32, W, nut, A);
+      tan_phase2(lane, nq - q0 < 32 ? nq - q0 : 32, W, nut_e, A);
       __syncwarp();
     }
     const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
@@ -119,10 +193,28 @@ __global__ void __launch_bounds__(tan_warps<T>() * 32) tangent_kernel(
     __syncwarp();
     tan_phase3d(lane, W);
     __syncwarp();
-    T Wl[3];
-    tan_phase3f(lane, W, A, Wl);
+    bool accurate = false;
+    if constexpr (sizeof(T) == 4) {
+      int ill = 0;
+      if (lane == 0) ill = kff_cond_inf(W) > KFF_FP64_COND;
+      accurate = __shfl_sync(0xffffffffu, ill, 0) != 0;  // warp-uniform
+      if (accurate) {
+        double K[9];
+        const double nut64 = nu_e ? visc_factor * __ldg(nu_e + e) : (double)nut;
+        kff_fp64(lane, nq, W.nd, xyz64, u64, beta64, e, tab64, nut64, K);
+        __syncwarp();
+        if (lane < 9) W.Kff[lane] = K[lane];
+        __syncwarp();
+        tan_phase3c(lane, W);
+        __syncwarp();
+        tan_phase3d(lane, W);
+        __syncwarp();
+      }
+    }
+    double Wl[3];
+    tan_phase3f(lane, W, A, Wl, accurate);
     __syncwarp();
-    tan_phase3e(lane, W, A);
+    tan_phase3e(lane, W, A, accurate);
     // per-element data for the finish kernel and the fine-scale recovery
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -174,7 +266,7 @@ __global__ void __launch_bounds__(tan_warps<T>() * 32) tangent_kernel(
 // the recovery. One thread per (element, local dof); threads 32..34 of an element write y.
 template <typename T, bool ATOMIC>
 __global__ void __launch_bounds__(256) finish_kernel(
-    const int32_t* __restrict__ conn, const double* __restrict__ elemR, const T* __restrict__ recW,
+    const int32_t* __restrict__ conn, const double* __restrict__ elemR, const double* __restrict__ recW,
     const double* __restrict__ recKinv, const uint32_t* __restrict__ dir_mask, int64_t first,
     int64_t count, const int32_t* __restrict__ elem_list, double* __restrict__ rhs,
     double* __restrict__ recY, double* __restrict__ oR) {
@@ -185,7 +277,7 @@ __global__ void __launch_bounds__(256) finish_kernel(
   const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
   const double Rf[3] = {elemR[36 * e + 32], elemR[36 * e + 33], elemR[36 * e + 34]};
   if (t < 32) {
-    const T Wt[3] = {recW[96 * e + 3 * t], recW[96 * e + 3 * t + 1], recW[96 * e + 3 * t + 2]};
+    const double Wt[3] = {recW[96 * e + 3 * t], recW[96 * e + 3 * t + 1], recW[96 * e + 3 * t + 2]};
     const double r = condensed_residual(elemR[36 * e + t], Wt, Rf);
     if (oR) {
       oR[32 * it + t] = r;
@@ -227,14 +319,13 @@ int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, bool with_x
   return 1;
 }
 
-template <typename T, bool ELEM_OUT, bool ATOMIC>
-static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
+template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS>
+static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
                      const T* tab, const TangentOut& o, int64_t first, int64_t count,
                      const int32_t* elem_list, unsigned int* flags, cudaStream_t st) {
   const int nq = kp.nq;
-  constexpr int WARPS = tan_warps<T>();
   const size_t smem = tan_table_bytes<T>(nq) + WARPS * tan_warp_bytes<T>(nq);
-  auto kern = tangent_kernel<T, ELEM_OUT, ATOMIC>;
+  auto kern = tangent_kernel<T, ELEM_OUT, ATOMIC, WARPS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = (count + WARPS - 1) / WARPS;
   if (blocks > 152 * 128) blocks = 152 * 128;
@@ -248,9 +339,30 @@ static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const K
     xyz = m.xyz; u = s.u; beta = s.beta;
   }
   kern<<<(unsigned)blocks, WARPS * 32, smem, st>>>(
-      xyz, u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), first, count, elem_list, m.blk,
+      xyz, u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, s.u,
+      s.beta, kp.tab64, first, count, elem_list, m.blk,
       m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
-      reinterpret_cast<T*>(o.recW), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
+      reinterpret_cast<double*>(o.recW), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
+}
+
+// Warps per block: the default, or the tuned count when it is one of the compiled choices
+// (FP32: 2, 4, 8; FP64: 1, 2, 4). Element outputs always use the default.
+template <typename T, bool ELEM_OUT, bool ATOMIC>
+static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
+                     const T* tab, const TangentOut& o, int64_t first, int64_t count,
+                     const int32_t* elem_list, unsigned int* flags, cudaStream_t st) {
+  constexpr int D = tan_warps<T>();
+  const int w = ELEM_OUT ? D : (kp.tangent_warps ? kp.tangent_warps : D);
+  if constexpr (!ELEM_OUT) {
+    if (w == D / 2) return launch_w<T, false, ATOMIC, D / 2>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+    if (w == 2 * D) return launch_w<T, false, ATOMIC, 2 * D>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+  }
+  launch_w<T, ELEM_OUT, ATOMIC, D>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+}
+
+int tangent_warp_choice(bool fp32, int k) {
+  const int d = fp32 ? tan_warps<float>() : tan_warps<double>();
+  return k == 0 ? d / 2 : (k == 1 ? d : 2 * d);
 }
 
 int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32,
@@ -279,9 +391,9 @@ int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOu
   const unsigned blocks = (unsigned)((count * 36 + 255) / 256);
   if (fp32) {
     if (atomic)
-      finish_kernel<float, true><<<blocks, 256, 0, st>>>(m.conn, elemR, (const float*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
+      finish_kernel<float, true><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
     else
-      finish_kernel<float, false><<<blocks, 256, 0, st>>>(m.conn, elemR, (const float*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
+      finish_kernel<float, false><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
   } else {
     if (atomic)
       finish_kernel<double, true><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);

@@ -103,7 +103,8 @@ struct WarpArea {
   int nd[8];
   T kffp[32][9];
   T Kcf[32][3];
-  T Xs[3][32];
+  T Xs[3][32];     // X = K_ff^-1 K_fc rounded to T
+  T Xl[3][32];     // X - Xs (its low part in T; zero in FP64)
   double Kff[9];
   double cof[9];
   double Kinv[9];
@@ -321,29 +322,101 @@ VMS_HD void tan_phase3d(int lane, WarpArea<T>& W) {
   if (bad && lane == 0) W.flag |= 2u;
 }
 
-// Phase 3f: column L of X = K_ff^-1 K_fc and row L of K_cf to shared memory; row L of
-// W = K_cf K_ff^-1 (used later for r_e = R_cp - W R_f) into Wl.
+// Infinity-norm condition number of K_ff from its FP64 copy and inverse in shared memory (every
+// lane computes the same value).
 template <typename T>
-VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, T Wl[3]) {
+VMS_HD double kff_cond_inf(const WarpArea<T>& W) {
+  double nk = 0.0, ni = 0.0;
   VMS_UNROLL
-  for (int m = 0; m < 3; ++m) {
-    W.Xs[m][lane] = W.KinvT[3 * m] * A.kfc[0] + W.KinvT[3 * m + 1] * A.kfc[1] +
-                    W.KinvT[3 * m + 2] * A.kfc[2];
-    W.Kcf[lane][m] = A.kcf[m];
-    Wl[m] = A.kcf[0] * W.KinvT[m] + A.kcf[1] * W.KinvT[3 + m] + A.kcf[2] * W.KinvT[6 + m];
+  for (int i = 0; i < 3; ++i) {
+    nk = fmax(nk, fabs(W.Kff[3 * i]) + fabs(W.Kff[3 * i + 1]) + fabs(W.Kff[3 * i + 2]));
+    ni = fmax(ni, fabs(W.Kinv[3 * i]) + fabs(W.Kinv[3 * i + 1]) + fabs(W.Kinv[3 * i + 2]));
+  }
+  return nk * ni;
+}
+
+// Phase 3f: column L of X = K_ff^-1 K_fc and row L of W = K_cf K_ff^-1 (kept in FP64 as Wl for
+// r_e = R_cp - W R_f), and row L of K_cf, to shared memory. In FP32 with `accurate` (an
+// ill-conditioned K_ff) X and W are formed in FP64 from the FP64 inverse and X is kept as a high
+// and a low part in T; otherwise they are formed in T (Xl = 0).
+template <typename T>
+VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, double Wl[3], bool accurate) {
+  if (sizeof(T) == 8 || accurate) {
+    const double f0 = (double)A.kfc[0], f1 = (double)A.kfc[1], f2 = (double)A.kfc[2];
+    const double c0 = (double)A.kcf[0], c1 = (double)A.kcf[1], c2 = (double)A.kcf[2];
+    VMS_UNROLL
+    for (int m = 0; m < 3; ++m) {
+      const double x = W.Kinv[3 * m] * f0 + W.Kinv[3 * m + 1] * f1 + W.Kinv[3 * m + 2] * f2;
+      const T xh = T(x);
+      W.Xs[m][lane] = xh;
+      W.Xl[m][lane] = T(x - (double)xh);
+      W.Kcf[lane][m] = A.kcf[m];
+      Wl[m] = c0 * W.Kinv[m] + c1 * W.Kinv[3 + m] + c2 * W.Kinv[6 + m];
+    }
+  } else {
+    VMS_UNROLL
+    for (int m = 0; m < 3; ++m) {
+      W.Xs[m][lane] = W.KinvT[3 * m] * A.kfc[0] + W.KinvT[3 * m + 1] * A.kfc[1] +
+                      W.KinvT[3 * m + 2] * A.kfc[2];
+      W.Xl[m][lane] = T(0);
+      W.Kcf[lane][m] = A.kcf[m];
+      Wl[m] = (double)(A.kcf[0] * W.KinvT[m] + A.kcf[1] * W.KinvT[3 + m] + A.kcf[2] * W.KinvT[6 + m]);
+    }
   }
 }
 
 // Condensed residual entry (FP64): r_t = R_cp[t] - sum_m W[t][m] R_f[m].
-template <typename T>
-VMS_HD double condensed_residual(double Rcp_t, const T Wt[3], const double Rf[3]) {
-  return Rcp_t - ((double)Wt[0] * Rf[0] + (double)Wt[1] * Rf[1] + (double)Wt[2] * Rf[2]);
+VMS_HD double condensed_residual(double Rcp_t, const double Wt[3], const double Rf[3]) {
+  return Rcp_t - (Wt[0] * Rf[0] + Wt[1] * Rf[1] + Wt[2] * Rf[2]);
 }
 
-// Phase 3e: S blocks of the lane's two node pairs, in place: K -= K_cf X.
+#if defined(__CUDACC__)
+// s + sum_m c_m (xh_m + xl_m) in FP32 with the rounding error of every product (exact by FMA) and
+// of every addition (two-sum) carried in a compensation term (compensated dot product). The
+// condensation subtracts K_cf X from K_cc, and on convection-dominated elements the terms are up to
+// ~10^3 times larger than the result, so plain FP32 would lose three digits of S_e.
+__device__ __forceinline__ float comp_dot3(float s, const float c[3], const float xh[3],
+                                           const float xl[3]) {
+  float comp = 0.f;
+  VMS_UNROLL
+  for (int m = 0; m < 3; ++m) {
+    const float p = __fmul_rn(c[m], xh[m]);
+    const float e = __fmaf_rn(c[m], xh[m], -p);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    comp = __fadd_rn(comp, __fadd_rn(err, e));
+    comp = __fmaf_rn(c[m], xl[m], comp);
+    s = t;
+  }
+  return __fadd_rn(s, comp);
+}
+#endif
+
+// Phase 3e: S blocks of the lane's two node pairs, in place: K -= K_cf X (FP32 with `accurate`:
+// compensated, with X = Xs + Xl; otherwise plain FMA with X = Xs, and Xs + Xl in FP64).
 template <typename T>
-VMS_HD void tan_phase3e(int lane, const WarpArea<T>& W, LaneAcc<T>& A) {
+VMS_HD void tan_phase3e(int lane, const WarpArea<T>& W, LaneAcc<T>& A, bool accurate) {
   const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
+#if defined(__CUDA_ARCH__)
+  if (sizeof(T) == 4 && accurate) {
+    VMS_UNROLL
+    for (int i = 0; i < 4; ++i) {
+      const float ca[3] = {-W.Kcf[4 * a0 + i][0], -W.Kcf[4 * a0 + i][1], -W.Kcf[4 * a0 + i][2]};
+      const float cb[3] = {-W.Kcf[4 * a1 + i][0], -W.Kcf[4 * a1 + i][1], -W.Kcf[4 * a1 + i][2]};
+      VMS_UNROLL
+      for (int k = 0; k < 4; ++k) {
+        const float xh[3] = {W.Xs[0][4 * b + k], W.Xs[1][4 * b + k], W.Xs[2][4 * b + k]};
+        const float xl[3] = {W.Xl[0][4 * b + k], W.Xl[1][4 * b + k], W.Xl[2][4 * b + k]};
+        auto acc = A.K[4 * i + k];
+        acc.x = comp_dot3((float)acc.x, ca, xh, xl);
+        acc.y = comp_dot3((float)acc.y, cb, xh, xl);
+        A.K[4 * i + k] = acc;
+      }
+    }
+    return;
+  }
+#endif
   VMS_UNROLL
   for (int i = 0; i < 4; ++i) {
     const auto c0 = pk(-W.Kcf[4 * a0 + i][0], -W.Kcf[4 * a1 + i][0]);
@@ -351,7 +424,9 @@ VMS_HD void tan_phase3e(int lane, const WarpArea<T>& W, LaneAcc<T>& A) {
     const auto c2 = pk(-W.Kcf[4 * a0 + i][2], -W.Kcf[4 * a1 + i][2]);
     VMS_UNROLL
     for (int k = 0; k < 4; ++k) {
-      const T x0 = W.Xs[0][4 * b + k], x1 = W.Xs[1][4 * b + k], x2 = W.Xs[2][4 * b + k];
+      const T x0 = sizeof(T) == 8 ? W.Xs[0][4 * b + k] + W.Xl[0][4 * b + k] : W.Xs[0][4 * b + k];
+      const T x1 = sizeof(T) == 8 ? W.Xs[1][4 * b + k] + W.Xl[1][4 * b + k] : W.Xs[1][4 * b + k];
+      const T x2 = sizeof(T) == 8 ? W.Xs[2][4 * b + k] + W.Xl[2][4 * b + k] : W.Xs[2][4 * b + k];
       auto acc = A.K[4 * i + k];
       acc = pfma(c0, pk(x0, x0), acc);
       acc = pfma(c1, pk(x1, x1), acc);

@@ -39,6 +39,11 @@ struct KParams {
   int nq;        // number of quadrature points
   int transient; // tau != 0
   int has_force; // f != 0
+  const double* nu_e;  // per-element viscosity (device, n_elems) or null: nut = visc_factor * nu_e[e]
+  double visc_factor;
+  const double* tab64;   // FP64 reference table of the tangent kernel (37 nq), for FP64 K_ff
+  int tangent_warps;     // warps per tangent block (0: default)
+  int residual_threads;  // threads per residual block (0: default)
 };
 
 // The once-per-mesh pattern (host side, built by pattern.cpp).
@@ -75,6 +80,7 @@ struct Mesh {
   double* dir_val = nullptr;     // n_dir
   int64_t* diag_pos = nullptr;   // n_dir
   int32_t* colour_order = nullptr;
+  double* nu_e = nullptr;        // n_elems per-element viscosity, or null (vms_set_element_viscosity)
   std::vector<int32_t> colour_start;
   int n_colours = 0;
 };
@@ -97,7 +103,7 @@ struct Work {
   double* rhs = nullptr;      // 4 n_nodes
   double* elemR = nullptr;    // n_elems * 36: R_cp (32), R_f (3), pad
   void* recX = nullptr;       // n_elems * 96 (T): K_ff^-1 K_fc
-  void* recW = nullptr;       // n_elems * 96 (T): K_cf K_ff^-1
+  void* recW = nullptr;       // n_elems * 96 (FP64): K_cf K_ff^-1
   double* recKinv = nullptr;  // n_elems * 9: K_ff^-1 (FP64)
   double* recY = nullptr;     // n_elems * 3: K_ff^-1 R_f
   double* resid = nullptr;    // 4 n_nodes + 3 n_elems
@@ -107,6 +113,7 @@ struct Work {
   cudaStream_t aux = nullptr; // second stream for the tangent kernel
   cudaEvent_t fork = nullptr, join = nullptr;
   bool assembled = false;
+  uint64_t assembly_id = 0;   // incremented by every assembly (preconditioner caching)
 };
 
 // Element residual (FP64, modal evaluation). mode 0: write elemR[36*e + ...] (R_cp 32, R_f 3);
@@ -120,13 +127,15 @@ struct TangentOut {
   void* values = nullptr;      // CSR values (assembly)
   double* rhs = nullptr;       // condensed right-hand side (assembly, finish kernel)
   void* recX = nullptr;        // per element K_ff^-1 K_fc (T)
-  void* recW = nullptr;        // per element K_cf K_ff^-1 (T)
+  void* recW = nullptr;        // per element K_cf K_ff^-1 (FP64)
   double* recKinv = nullptr;   // per element K_ff^-1
   double* recY = nullptr;      // per element K_ff^-1 R_f (finish kernel)
   // element outputs (parity), FP64, may be null
   double *S = nullptr, *r = nullptr, *Kcc = nullptr, *Kcf = nullptr, *Kfc = nullptr,
          *Kff = nullptr;
 };
+// The three warps-per-block counts the tangent kernel is compiled for (k = 0, 1, 2; 1 = default).
+int tangent_warp_choice(bool fp32, int k);
 int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32,
                    const KParams& kp, const void* tab, const TangentOut& out, int64_t first,
                    int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,

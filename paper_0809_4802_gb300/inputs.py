@@ -317,9 +317,52 @@ def random_elements(n_elems: int, seed: int, distort: float = 0.15, h: float = 1
     return X, U, beta, Uprev
 
 
-def batched_cavities(count: int = 64, seed: int = 1004):
+def batched_cavities(count: int = 64, seed: int = 1004, edges=(8, 12, 16, 24, 32, 48)):
     """Edge counts and Reynolds numbers of a batch of independent cavity problems."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    ns = rng.choice(np.array([8, 12, 16, 24, 32, 48]), size=count)
+    ns = rng.choice(np.array(edges), size=count)
     res = rng.uniform(100.0, 1000.0, size=count)
     return [(int(n), float(r)) for n, r in zip(ns, res)]
+
+
+@dataclass
+class Batch:
+    """Independent problems merged into one mesh (instance i owns nodes node_offsets[i]:...[i+1]
+    and elements elem_offsets[i]:...[i+1]); nu_e is each element's viscosity."""
+    work: Workload
+    node_offsets: np.ndarray
+    elem_offsets: np.ndarray
+    nu_e: np.ndarray
+    members: list
+
+
+def merge_workloads(parts: list) -> Batch:
+    """Concatenate workloads into one mesh: node numbers, connectivity and constrained dofs are
+    shifted by each instance's node offset."""
+    n_off = np.concatenate([[0], np.cumsum([w.mesh.n_nodes for w in parts])]).astype(np.int64)
+    e_off = np.concatenate([[0], np.cumsum([w.mesh.n_elems for w in parts])]).astype(np.int64)
+    xyz = np.concatenate([w.mesh.xyz for w in parts])
+    conn = np.concatenate([w.mesh.conn.astype(np.int64) + n_off[i] for i, w in enumerate(parts)])
+    ijk = np.concatenate([w.mesh.node_ijk for w in parts])
+    eijk = np.concatenate([w.mesh.elem_ijk for w in parts])
+    mesh = Mesh(xyz=xyz, conn=conn.astype(np.int32), elem_ijk=eijk, node_ijk=ijk,
+                meta={"instances": len(parts)})
+    mesh.name = f"batch{len(parts)}"
+    dofs = np.concatenate([w.bc.dofs + 4 * n_off[i] for i, w in enumerate(parts)])
+    vals = np.concatenate([w.bc.vals for w in parts])
+    nu_e = np.concatenate([np.full(w.mesh.n_elems, w.nu) for w in parts])
+    work = Workload(mesh=mesh, bc=Dirichlet(dofs=dofs.astype(np.int64), vals=vals),
+                    u=np.concatenate([w.u for w in parts]),
+                    beta=np.concatenate([w.beta for w in parts]), nu=float(parts[0].nu),
+                    name=mesh.name)
+    return Batch(work=work, node_offsets=n_off, elem_offsets=e_off, nu_e=nu_e, members=parts)
+
+
+def batched_workload(count: int = 64, seed: int = 1004, edges=(8, 12, 16, 24, 32, 48),
+                     jitter_frac: float = 0.15) -> Batch:
+    """A serving-style mix: `count` lid-driven cavities with edge counts drawn from `edges` and
+    Re ~ U[100, 1000], each with its own seeded jittered mesh and random state (as the 32^3
+    cavity)."""
+    parts = [cavity_workload(n, re, jitter_frac=jitter_frac, state="random", seed=seed + 1 + i)
+             for i, (n, re) in enumerate(batched_cavities(count, seed, edges))]
+    return merge_workloads(parts)

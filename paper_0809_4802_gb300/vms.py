@@ -45,6 +45,8 @@ EXPORTS = [
     "vms_residual", "vms_element_matrices", "vms_apply", "vms_solve", "vms_newton_step",
     "vms_newton_solve", "vms_last_error", "vms_version", "vms_profile_enable", "vms_profile_read",
     "vms_residual_norm_noalloc", "vms_set_preconditioner", "vms_solver_stats",
+    "vms_set_element_viscosity", "vms_set_instances", "vms_solve_instance", "vms_set_graph",
+    "vms_set_tuning", "vms_get_tuning", "vms_autotune",
 ]
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
 
@@ -53,6 +55,15 @@ class VmsParams(ctypes.Structure):
     _fields_ = [("nu", c_double), ("visc_factor", c_double), ("dt", c_double),
                 ("f", c_double * 3), ("bubble_scale", c_double), ("quad_order", c_int32),
                 ("scatter_mode", c_int32)]
+
+
+class VmsTuning(ctypes.Structure):
+    _fields_ = [("tangent_warps", c_int32), ("residual_threads", c_int32),
+                ("scatter_mode", c_int32), ("reserved", c_int32), ("ms", c_double)]
+
+    def as_dict(self):
+        return {"tangent_warps": self.tangent_warps, "residual_threads": self.residual_threads,
+                "scatter_mode": self.scatter_mode, "ms": self.ms}
 
 
 class CsrView(ctypes.Structure):
@@ -100,6 +111,14 @@ def load_library(path: str = LIB_PATH):
         "vms_profile_enable": (c_int, [p, c_int]),
         "vms_profile_read": (c_int, [p, c_int, p, p]),
         "vms_set_preconditioner": (c_int, [p, c_int]),
+        "vms_set_element_viscosity": (c_int, [p, p]),
+        "vms_set_instances": (c_int, [p, c_int64, p, p]),
+        "vms_solve_instance": (c_int, [p, c_int64, c_double, c_int, c_int, c_int, POINTER(c_int),
+                                       POINTER(c_double)]),
+        "vms_set_graph": (c_int, [p, c_int]),
+        "vms_set_tuning": (c_int, [p, POINTER(VmsTuning)]),
+        "vms_get_tuning": (c_int, [p, POINTER(VmsTuning)]),
+        "vms_autotune": (c_int, [p, c_int, POINTER(VmsTuning)]),
         "vms_solver_stats": (c_int, [p, c_int, POINTER(c_int64), POINTER(c_int64)]),
         "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
                                               POINTER(VmsParams), p, p, p]),
@@ -252,6 +271,41 @@ class Context:
 
     def apply(self, x, y):
         self._check(self.lib.vms_apply(self.h, _ptr(x, np.float64), _ptr(y, np.float64)))
+
+    def set_element_viscosity(self, nu_e):
+        self._check(self.lib.vms_set_element_viscosity(
+            self.h, _ptr(nu_e, np.float64, self.n_elems) if nu_e is not None else None))
+
+    def set_instances(self, node_offsets, elem_offsets):
+        no = np.ascontiguousarray(node_offsets, dtype=np.int64)
+        eo = np.ascontiguousarray(elem_offsets, dtype=np.int64)
+        if no.shape != eo.shape or no.ndim != 1 or no.size < 2:
+            raise ValueError("offsets: two 1-D arrays of count + 1 entries")
+        self._check(self.lib.vms_set_instances(self.h, no.size - 1, no.ctypes.data, eo.ctypes.data))
+
+    def solve_instance(self, instance, rtol=1e-12, maxit=50, restart=50, update=True):
+        it = c_int()
+        rel = c_double()
+        self._check(self.lib.vms_solve_instance(self.h, int(instance), rtol, maxit, restart,
+                                                int(update), byref(it), byref(rel)))
+        return it.value, rel.value
+
+    def set_tuning(self, tangent_warps=0, residual_threads=0, scatter_mode=-1):
+        t = VmsTuning(tangent_warps, residual_threads, scatter_mode, 0, 0.0)
+        self._check(self.lib.vms_set_tuning(self.h, byref(t)))
+
+    def get_tuning(self):
+        t = VmsTuning()
+        self._check(self.lib.vms_get_tuning(self.h, byref(t)))
+        return t.as_dict()
+
+    def autotune(self, repeats=3):
+        t = VmsTuning()
+        self._check(self.lib.vms_autotune(self.h, int(repeats), byref(t)))
+        return t.as_dict()
+
+    def set_graph(self, enable: bool = True):
+        self._check(self.lib.vms_set_graph(self.h, int(enable)))
 
     def solve(self, rtol=1e-12, maxit=50, restart=50, update=True):
         it = c_int()
