@@ -250,6 +250,63 @@ int vms_newton_step(vms_ctx* ctx, double* res_norm);
  * Errors: VMS_ERR_NEWTON_DIVERGED, VMS_ERR_KRYLOV_MAXIT and those of the steps. */
 int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist);
 
+/* vms_newton_solve with an absolute target: iterate until ||R|| <= target (the same stopping
+ * rule whatever the starting point, e.g. a predicted one; the forcing term uses the ratio to the
+ * starting residual and is floored at target / (2 ||R||)). */
+int vms_newton_solve_to(vms_ctx* ctx, double target, int maxit, int* iters, double* hist);
+
+/* ---- learned warm start of the transient Newton iteration -------------------------------------
+ * Remark of Section 4.1 (backward-Euler steps) and Section 4.2 (Newton): a network predicts, for
+ * every node, the increment of (v, p) over the next time step from its state at the last two
+ * steps and the mean of its 1-ring, and Newton starts from the predicted state instead of the
+ * previous one. Newton still converges to the same tolerance, so the network only moves the
+ * starting point (the previous-step start is the fallback). The paper has no counterpart; it is
+ * an extension of the transient solver.
+ *
+ * Network: x (12) -> tanh(x W1 + b1) (128) -> tanh(. W2 + b2) (128) -> . W3 + b3 (4); weights
+ * stored in BF16, biases, activations and accumulation in FP32. Parameter vector (FP32, row-major):
+ * W1 [12][128], b1 [128], W2 [128][128], b2 [128], W3 [128][4], b3 [4]. */
+#define VMS_MLP_IN 12
+#define VMS_MLP_WIDTH 128
+#define VMS_MLP_OUT 4
+#define VMS_MLP_PARAMS 18692
+
+typedef struct vms_mlp vms_mlp;
+
+/* Create a network on `device` with all parameters zero. Errors: VMS_ERR_CUDA, OUT_OF_MEMORY. */
+int vms_mlp_create(vms_mlp** mlp, int device);
+int vms_mlp_destroy(vms_mlp* mlp);
+const char* vms_mlp_last_error(vms_mlp* mlp);
+/* Stream of every later call on this network (default: the legacy default stream). */
+int vms_mlp_set_stream(vms_mlp* mlp, void* stream);
+/* Set all VMS_MLP_PARAMS parameters (FP32, host or device; the weights are rounded to BF16 for
+ * use) and reset the optimiser. */
+int vms_mlp_set_params(vms_mlp* mlp, const float* params);
+/* Read the parameters: stored != 0 gives the values the kernels use (BF16 weights as FP32),
+ * stored == 0 the FP32 master copy the optimiser updates. */
+int vms_mlp_get_params(vms_mlp* mlp, float* params, int stored);
+/* Y (n x 4, device FP32) = network(X) for X (n x 12, device FP32), queued on the stream. */
+int vms_mlp_forward(vms_mlp* mlp, int64_t n, const float* X, float* Y);
+/* Gradient of the loss sum_r sum_c (y_rc - T_rc)^2 / (4 n) over n rows (rows: device int32
+ * indices into X and T, or NULL for the first n rows); kept for vms_mlp_adam. *loss (host, may be
+ * NULL) and grads (VMS_MLP_PARAMS, host or device, may be NULL) receive the loss and gradient
+ * (synchronises the stream when either is given). */
+int vms_mlp_grad(vms_mlp* mlp, int64_t n, const int32_t* rows, const float* X, const float* T,
+                 double* loss, float* grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) with the kept gradient. */
+int vms_mlp_adam(vms_mlp* mlp, float lr);
+
+/* Features of every node from the context's state u (step n) and u_prev (step n-1):
+ * X[i] = [u_i (4), u_prev_i (4), mean of u over the nodes sharing an element with i (4)] divided
+ * column-wise by scale_in (12 host floats, NULL = 1); X: n_nodes x 12 device FP32. */
+int vms_node_features(vms_ctx* ctx, const float* scale_in, float* X);
+/* D[i] = (u_i - u_prev_i) / scale_out (4 host floats, NULL = 1), n_nodes x 4 device FP32. */
+int vms_node_increment(vms_ctx* ctx, const float* scale_out, float* D);
+/* u_i += scale_out * D[i] (D device FP32, n_nodes x 4), then the Dirichlet values are imposed. */
+int vms_apply_increment(vms_ctx* ctx, const float* scale_out, const float* D);
+/* Start a new backward-Euler step: u_prev = u (on the device). */
+int vms_shift_time(vms_ctx* ctx);
+
 /* ---- kernel accounting (tracing) ----------------------------------------------------------- */
 #define VMS_K_RESIDUAL 0  /* element residual kernel (FP64) */
 #define VMS_K_TANGENT 1   /* element tangent + condensation + scatter kernel */

@@ -754,19 +754,18 @@ int vms_newton_step(vms_ctx* ctx, double* res_norm) {
   return solve_impl(ctx, whole(ctx), -1, 1e-10, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel);
 }
 
-int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist) {
-  if (!ctx || maxit < 0 || !(rtol > 0.0)) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid arguments");
+int vms_newton_solve_to(vms_ctx* ctx, double target, int maxit, int* iters, double* hist) {
+  if (!ctx || maxit < 0 || !(target > 0.0)) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid arguments");
   double r0 = 0.0, r = 0.0;
   if (int rc = vms_residual(ctx, &r0, nullptr)) return rc;
   if (hist) hist[0] = r0;
   r = r0;
   int k = 0;
-  while (k < maxit && r > rtol * r0) {
+  while (k < maxit && r > target) {
     if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
     // inexact Newton: forcing term proportional to the current relative residual, but never
-    // tighter than the final target needs (a linear residual of eta * r <= rtol * r0 / 2)
-    const double eta = std::min(0.5, std::max({std::min(1e-2, 0.1 * r / r0),
-                                               0.5 * rtol * r0 / r, 1e-12}));
+    // tighter than the target needs (a linear residual of eta * r <= target / 2)
+    const double eta = std::min(0.5, std::max({std::min(1e-2, 0.1 * r / r0), 0.5 * target / r, 1e-12}));
     int it = 0;
     double rel = 0.0;
     if (int rc = solve_impl(ctx, whole(ctx), -1, eta, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel)) return rc;
@@ -779,8 +778,20 @@ int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* h
     }
   }
   if (iters) *iters = k;
-  if (r > rtol * r0) return ctx_fail(ctx, VMS_ERR_NEWTON_DIVERGED, "Newton reached maxit");
+  if (r > target) return ctx_fail(ctx, VMS_ERR_NEWTON_DIVERGED, "Newton reached maxit");
   return VMS_OK;
+}
+
+int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist) {
+  if (!ctx || maxit < 0 || !(rtol > 0.0)) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid arguments");
+  double r0 = 0.0;
+  if (int rc = vms_residual(ctx, &r0, nullptr)) return rc;
+  if (r0 == 0.0) {
+    if (iters) *iters = 0;
+    if (hist) hist[0] = 0.0;
+    return VMS_OK;
+  }
+  return vms_newton_solve_to(ctx, rtol * r0, maxit, iters, hist);
 }
 
 }  // extern "C"

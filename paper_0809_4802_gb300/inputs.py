@@ -366,3 +366,46 @@ def batched_workload(count: int = 64, seed: int = 1004, edges=(8, 12, 16, 24, 32
     parts = [cavity_workload(n, re, jitter_frac=jitter_frac, state="random", seed=seed + 1 + i)
              for i, (n, re) in enumerate(batched_cavities(count, seed, edges))]
     return merge_workloads(parts)
+
+
+# ----------------------------------------------------------------------------------------------
+# initial parameters of the warm-start network (random numbers the method draws, passed in)
+# ----------------------------------------------------------------------------------------------
+
+def mlp_init(seed: int = 7, n_in: int = 12, width: int = 128, n_out: int = 4) -> np.ndarray:
+    """Flat FP32 parameter vector (W1, b1, W2, b2, W3, b3; row-major): weights uniform in
+    +-sqrt(6 / (fan_in + fan_out)) (Glorot), biases zero."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for fi, fo in ((n_in, width), (width, width), (width, n_out)):
+        a = np.sqrt(6.0 / (fi + fo))
+        parts += [rng.uniform(-a, a, fi * fo), np.zeros(fo)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------------------------
+# decaying vortex in a closed box (a smooth transient for the warm start): no-slip on every wall,
+# pressure pinned at the centre, initial velocity f(z) (d psi/dy, -d psi/dx, 0) with
+# psi = sin^2(pi x) sin^2(pi y) and f(z) = sin(pi z): divergence-free and zero on the walls
+# ----------------------------------------------------------------------------------------------
+
+def vortex_box_workload(n: int, re: float = 200.0, dt: float = 0.02, jitter_frac: float = 0.0,
+                        seed: int = 1006, amplitude: float = 1.0) -> Workload:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mesh = cavity_mesh(n)
+    if jitter_frac > 0:
+        jitter(mesh, jitter_frac, rng)
+    ijk = mesh.node_ijk
+    centre = np.nonzero((ijk[:, 0] == n // 2) & (ijk[:, 1] == n // 2) & (ijk[:, 2] == n // 2))[0]
+    bc = wall_bc(mesh, (0.0, 0.0, 0.0), pin_pressure_node=int(centre[0]))
+    x, y, z = mesh.xyz[:, 0], mesh.xyz[:, 1], mesh.xyz[:, 2]
+    pi = np.pi
+    dpsi_dy = np.sin(pi * x) ** 2 * 2 * pi * np.sin(pi * y) * np.cos(pi * y)
+    dpsi_dx = 2 * pi * np.sin(pi * x) * np.cos(pi * x) * np.sin(pi * y) ** 2
+    f = np.sin(pi * z)
+    u = np.zeros((mesh.n_nodes, 4))
+    u[:, 0] = amplitude * f * dpsi_dy
+    u[:, 1] = -amplitude * f * dpsi_dx
+    impose(u, bc)
+    return Workload(mesh=mesh, bc=bc, u=u, beta=np.zeros((mesh.n_elems, 3)), nu=1.0 / re, dt=dt,
+                    u_prev=u.copy(), name=f"vortex{n}_re{re:g}")

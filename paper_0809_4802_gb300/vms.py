@@ -47,7 +47,12 @@ EXPORTS = [
     "vms_residual_norm_noalloc", "vms_set_preconditioner", "vms_solver_stats",
     "vms_set_element_viscosity", "vms_set_instances", "vms_solve_instance", "vms_set_graph",
     "vms_set_tuning", "vms_get_tuning", "vms_autotune",
+    "vms_mlp_create", "vms_mlp_destroy", "vms_mlp_last_error", "vms_mlp_set_stream",
+    "vms_mlp_set_params", "vms_mlp_get_params", "vms_mlp_forward", "vms_mlp_grad", "vms_mlp_adam",
+    "vms_node_features", "vms_node_increment", "vms_apply_increment", "vms_shift_time",
+    "vms_newton_solve_to",
 ]
+MLP_IN, MLP_WIDTH, MLP_OUT, MLP_PARAMS = 12, 128, 4, 18692
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
 
 
@@ -119,6 +124,20 @@ def load_library(path: str = LIB_PATH):
         "vms_set_tuning": (c_int, [p, POINTER(VmsTuning)]),
         "vms_get_tuning": (c_int, [p, POINTER(VmsTuning)]),
         "vms_autotune": (c_int, [p, c_int, POINTER(VmsTuning)]),
+        "vms_mlp_create": (c_int, [POINTER(c_void_p), c_int]),
+        "vms_mlp_destroy": (c_int, [p]),
+        "vms_mlp_last_error": (c_char_p, [p]),
+        "vms_mlp_set_stream": (c_int, [p, p]),
+        "vms_mlp_set_params": (c_int, [p, p]),
+        "vms_mlp_get_params": (c_int, [p, p, c_int]),
+        "vms_mlp_forward": (c_int, [p, c_int64, p, p]),
+        "vms_mlp_grad": (c_int, [p, c_int64, p, p, p, POINTER(c_double), p]),
+        "vms_mlp_adam": (c_int, [p, ctypes.c_float]),
+        "vms_node_features": (c_int, [p, p, p]),
+        "vms_node_increment": (c_int, [p, p, p]),
+        "vms_apply_increment": (c_int, [p, p, p]),
+        "vms_shift_time": (c_int, [p]),
+        "vms_newton_solve_to": (c_int, [p, c_double, c_int, POINTER(c_int), p]),
         "vms_solver_stats": (c_int, [p, c_int, POINTER(c_int64), POINTER(c_int64)]),
         "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
                                               POINTER(VmsParams), p, p, p]),
@@ -331,6 +350,32 @@ class Context:
         self._check(self.lib.vms_solver_stats(self.h, int(reset), byref(a), byref(b)))
         return a.value, b.value
 
+    # -- transient driver -------------------------------------------------------------------
+    def node_features(self, X, scale_in=None):
+        """X: device float32 tensor (n_nodes, 12) receiving [u, u_prev, 1-ring mean of u]/scale."""
+        sc = None if scale_in is None else np.ascontiguousarray(scale_in, dtype=np.float32)
+        self._check(self.lib.vms_node_features(self.h, None if sc is None else sc.ctypes.data,
+                                               _ptr(X, np.float32, self.n_nodes * MLP_IN)))
+
+    def node_increment(self, D, scale_out=None):
+        sc = None if scale_out is None else np.ascontiguousarray(scale_out, dtype=np.float32)
+        self._check(self.lib.vms_node_increment(self.h, None if sc is None else sc.ctypes.data,
+                                                _ptr(D, np.float32, self.n_nodes * MLP_OUT)))
+
+    def apply_increment(self, D, scale_out=None):
+        sc = None if scale_out is None else np.ascontiguousarray(scale_out, dtype=np.float32)
+        self._check(self.lib.vms_apply_increment(self.h, None if sc is None else sc.ctypes.data,
+                                                 _ptr(D, np.float32, self.n_nodes * MLP_OUT)))
+
+    def shift_time(self):
+        self._check(self.lib.vms_shift_time(self.h))
+
+    def newton_solve_to(self, target, maxit=20):
+        it = c_int()
+        hist = np.zeros(maxit + 1)
+        self._check(self.lib.vms_newton_solve_to(self.h, target, maxit, byref(it), hist.ctypes.data))
+        return it.value, hist[: it.value + 1]
+
     # -- kernel accounting ----------------------------------------------------------------
     def profile_enable(self, timing: bool = True):
         self._check(self.lib.vms_profile_enable(self.h, int(timing)))
@@ -341,6 +386,66 @@ class Context:
         n = np.zeros(len(K_NAMES), np.int64)
         self._check(self.lib.vms_profile_read(self.h, int(reset), ms.ctypes.data, n.ctypes.data))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(K_NAMES)}
+
+
+class Mlp:
+    """The warm-start network (VMS_MLP_*): BF16 weights, FP32 activations, own kernels."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        h = c_void_p()
+        rc = self.lib.vms_mlp_create(byref(h), device)
+        if rc != OK:
+            raise VmsError(rc, "vms_mlp_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vms_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise VmsError(rc, self.lib.vms_mlp_last_error(self.h).decode())
+        return rc
+
+    def set_stream(self, stream_handle: int):
+        self._check(self.lib.vms_mlp_set_stream(self.h, c_void_p(stream_handle)))
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters")
+        self._check(self.lib.vms_mlp_set_params(self.h, a.ctypes.data))
+
+    def get_params(self, stored: bool = True):
+        out = np.empty(MLP_PARAMS, np.float32)
+        self._check(self.lib.vms_mlp_get_params(self.h, out.ctypes.data, int(stored)))
+        return out
+
+    def forward(self, X, Y):
+        n = int(X.shape[0])
+        self._check(self.lib.vms_mlp_forward(self.h, n, _ptr(X, np.float32, n * MLP_IN),
+                                             _ptr(Y, np.float32, n * MLP_OUT)))
+
+    def grad(self, X, T, rows=None, n=None, want=True):
+        """Loss and gradient over the rows (device int32 tensor) or the first n rows of X, T."""
+        n = int(rows.shape[0]) if rows is not None else int(n if n is not None else X.shape[0])
+        loss = c_double()
+        g = np.empty(MLP_PARAMS, np.float32) if want else None
+        self._check(self.lib.vms_mlp_grad(self.h, n, _ptr(rows, np.int32), _ptr(X, np.float32),
+                                          _ptr(T, np.float32), byref(loss) if want else None,
+                                          g.ctypes.data if want else None))
+        return (loss.value, g) if want else None
+
+    def adam(self, lr: float):
+        self._check(self.lib.vms_mlp_adam(self.h, ctypes.c_float(lr)))
 
 
 def version() -> str:
