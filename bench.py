@@ -65,8 +65,15 @@ WORKLOADS = {
     # serving-style mix: 64 jittered cavities, edges drawn from {8,12,16,24,32,48}, Re ~ U[100,1000],
     # random states, one merged mesh (1,677,504 elements) assembled per CUDA-graph launch, autotuned
     "batch64_mixed": dict(kind="batch", prec=1),
+    # transient runs with the learned warm start: a decaying vortex in a closed, jittered box
+    # (--ws-n cells per edge), and the channel past a cube (--ws-nx, --ws-nyz; its systems carry
+    # the nearly singular equal-order pressure modes of the hexahedral element, on which
+    # GMRES + ILU(0) stalls, see the design notes)
+    "vortex_warmstart_fp64": dict(kind="warmstart", flow="vortex", prec=0),
+    "channel_warmstart_mixed": dict(kind="warmstart", flow="channel", prec=1),
 }
 DEFAULT_WORKLOAD = "cavity32_re400_mixed"
+WS_SIZE = {"nx": 150, "nyz": 28, "n": 16}   # set from --ws-nx / --ws-nyz / --ws-n
 
 
 def make_workload(name, with_batch=False):
@@ -81,6 +88,10 @@ def make_workload(name, with_batch=False):
         wl = inputs.bfs_workload(13, re=800.0, jitter_frac=0.1, seed=1003)
     elif kind == "channel":
         wl = inputs.channel_workload(300, 56, re=1000.0, dt=0.01, seed=1005)
+    elif kind == "warmstart" and w["flow"] == "channel":
+        wl = inputs.channel_workload(WS_SIZE["nx"], WS_SIZE["nyz"], re=1000.0, dt=0.01, seed=1005)
+    elif kind == "warmstart":
+        wl = inputs.vortex_box_workload(WS_SIZE["n"], re=200.0, dt=0.02, jitter_frac=0.1)
     else:
         wl = inputs.cavity_workload(w["n"], re=w["re"], jitter_frac=w["jitter"], state=w["state"],
                                     seed=w["seed"])
@@ -268,6 +279,44 @@ def newton_timing(vms, wl, prec, device, stream, rtol=1e-8, repeats=2, maxit=30)
             "repeats": repeats, "times": [round(t, 4) for t in times]}
 
 
+def warmstart_study(vms, ctx, wl, args, dev):
+    """Backward-Euler steps from rest: record args.ws_train steps (previous-step start), train the
+    network, then run the next args.ws_eval steps twice from the same state: previous-step start
+    and learned start; Newton to the same absolute target (1e-8 of the previous-step start's
+    residual) in both."""
+    import torch
+    from paper_0809_4802_gb300 import transient as tr
+    ctx.set_graph(False)
+    ctx.state_upload(wl.u, wl.beta, wl.u_prev)
+    rec = tr.Recorder()
+    t0 = time.perf_counter()
+    tr.run_steps(vms, ctx, args.ws_train, rtol=1e-8, record=rec)
+    t_record = time.perf_counter() - t0
+    u, beta = ctx.state_download()
+    up = ctx.state_download_prev()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ws = tr.WarmStart(vms, dev.index or 0, seed=7)
+    loss = ws.fit(rec, epochs=args.ws_epochs, batch=4096, lr=2e-3)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    base = tr.run_steps(vms, ctx, args.ws_eval, rtol=1e-8, first_step=args.ws_train)
+    ctx.state_upload(u, beta, up)
+    learned = tr.run_steps(vms, ctx, args.ws_eval, rtol=1e-8, warm=ws, first_step=args.ws_train)
+    ws.mlp.close()
+
+    def summary(st):
+        return {"newton_iterations": int(sum(s.newton_iterations for s in st)),
+                "krylov_iterations": int(sum(s.krylov_iterations for s in st)),
+                "wall_s": float(sum(s.seconds for s in st)),
+                "start_residual_ratio_mean": float(np.mean([s.start_residual / s.reference_residual for s in st]))}
+    return {"steps_recorded": args.ws_train, "steps_evaluated": args.ws_eval,
+            "record_wall_s": t_record, "train_wall_s": t_train, "train_epochs": args.ws_epochs,
+            "final_loss": loss, "previous_step_start": summary(base), "learned_start": summary(learned),
+            "newton_iterations_saved": summary(base)["newton_iterations"] - summary(learned)["newton_iterations"],
+            "note": "warm start applied to the velocity; Newton to the same absolute target"}
+
+
 def workload_config(name, wl, prec, scatter, batch=None):
     c = {"workload": name, "elements": wl.mesh.n_elems, "nodes": wl.mesh.n_nodes,
          "reynolds": round(1.0 / wl.nu, 3), "dt": wl.dt, "precision": "mixed" if prec == 1 else "fp64",
@@ -408,6 +457,11 @@ def ours(args):
             if k in ("value", "unit", "newton_iterations", "krylov_iterations", "final_rel")}
         newton["value"] = max_over_ranks(newton["value"])
 
+    # ---- transient: learned warm start against the previous-step start ----
+    warm = None
+    if WORKLOADS[args.workload].get("kind") == "warmstart":
+        warm = warmstart_study(vms, ctx, wl, args, dev)
+
     # ---- batch: one linear solve per instance (the first inexact-Newton system, eta = 1e-2) ----
     per_instance = None
     if batch is not None:
@@ -447,7 +501,7 @@ def ours(args):
             "config": workload_config(args.workload, wl, prec, args.scatter, batch),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "newton": newton,
             "tuning": tuning, "graph": bool(batch is not None or args.graph),
-            "per_instance_solve": per_instance,
+            "per_instance_solve": per_instance, "warm_start": warm,
             "gpu_launches": gpu_launches, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -469,10 +523,17 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes first")
+    ap.add_argument("--ws-n", type=int, default=16)
+    ap.add_argument("--ws-nx", type=int, default=150)
+    ap.add_argument("--ws-nyz", type=int, default=28)
+    ap.add_argument("--ws-train", type=int, default=20)
+    ap.add_argument("--ws-eval", type=int, default=30)
+    ap.add_argument("--ws-epochs", type=int, default=60)
     ap.add_argument("--graph", action="store_true", help="replay the assembly as a CUDA graph")
     ap.add_argument("--newton", choices=["auto", "on", "off"], default="auto",
                     help="also time Newton solves to 1e-8 (auto: on for the cavity workloads)")
     args = ap.parse_args()
+    WS_SIZE.update(nx=args.ws_nx, nyz=args.ws_nyz, n=args.ws_n)
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -129,6 +129,10 @@ int vms_state_upload(vms_ctx* ctx, const double* u, const double* beta, const do
 /* Copy the current state to caller buffers (host or device); either pointer may be NULL. */
 int vms_state_download(vms_ctx* ctx, double* u, double* beta);
 
+/* Previous time-step velocity and pressure (n_nodes x 4 doubles, host or device; the u_prev of
+ * vms_state_upload, or u at the last vms_shift_time). Errors: VMS_ERR_STATE. */
+int vms_state_download_prev(vms_ctx* ctx, double* u_prev);
+
 /* One Newton-Schur tangent assembly: for every element, gather its nodes, evaluate geometry and
  * fields at every quadrature point, form R_c, R_p, R_f and the tangent blocks (Section 4),
  * condense the bubble unknowns (Section 5), scatter-add S_e and r_e into the CSR system, then

@@ -555,6 +555,15 @@ int vms_state_download(vms_ctx* ctx, double* u, double* beta) {
   return VMS_OK;
 }
 
+int vms_state_download_prev(vms_ctx* ctx, double* u_prev) {
+  if (!ctx || !u_prev) return fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
+  if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "no state uploaded");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(u_prev, ctx->state.u_prev, sizeof(double4_32a) * ctx->mesh.n_nodes, cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VMS_OK;
+}
+
 static void fill_view(vms_ctx* ctx, vms_csr_view* out) {
   out->n_rows = 4 * ctx->mesh.n_nodes;
   out->nnz = ctx->mesh.nnz;

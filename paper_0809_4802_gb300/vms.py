@@ -50,7 +50,7 @@ EXPORTS = [
     "vms_mlp_create", "vms_mlp_destroy", "vms_mlp_last_error", "vms_mlp_set_stream",
     "vms_mlp_set_params", "vms_mlp_get_params", "vms_mlp_forward", "vms_mlp_grad", "vms_mlp_adam",
     "vms_node_features", "vms_node_increment", "vms_apply_increment", "vms_shift_time",
-    "vms_newton_solve_to",
+    "vms_newton_solve_to", "vms_state_download_prev",
 ]
 MLP_IN, MLP_WIDTH, MLP_OUT, MLP_PARAMS = 12, 128, 4, 18692
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
@@ -138,6 +138,7 @@ def load_library(path: str = LIB_PATH):
         "vms_apply_increment": (c_int, [p, p, p]),
         "vms_shift_time": (c_int, [p]),
         "vms_newton_solve_to": (c_int, [p, c_double, c_int, POINTER(c_int), p]),
+        "vms_state_download_prev": (c_int, [p, p]),
         "vms_solver_stats": (c_int, [p, c_int, POINTER(c_int64), POINTER(c_int64)]),
         "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
                                               POINTER(VmsParams), p, p, p]),
@@ -246,6 +247,11 @@ class Context:
         beta = np.empty((self.n_elems, 3))
         self._check(self.lib.vms_state_download(self.h, u.ctypes.data, beta.ctypes.data))
         return u, beta
+
+    def state_download_prev(self):
+        up = np.empty((self.n_nodes, 4))
+        self._check(self.lib.vms_state_download_prev(self.h, up.ctypes.data))
+        return up
 
     # -- the hot path ---------------------------------------------------------------------
     def assemble(self) -> CsrView:
