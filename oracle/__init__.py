@@ -20,4 +20,5 @@ from .vms import (  # noqa: F401
     assemble, apply_dirichlet, residual_vector, newton_solve, uncondensed_system,
     fine_recovery, element_residual_only, elementary_integrals, assemble_vector,
     element_dofs, gather, pack_residual, NegativeJacobian, CORNERS,
+    tet_rule, p1_basis, tet_bubble, element_basis, TET_CORNERS,
 )

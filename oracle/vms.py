@@ -37,7 +37,8 @@ class Params:
     dt: float = 0.0             # backward-Euler step; 0 = steady
     f: tuple = (0.0, 0.0, 0.0)  # body force b (constant)
     quad_order: int = 3         # Gauss points per direction
-    bubble_scale: float = 1.0   # b = bubble_scale * (1-xi^2)(1-eta^2)(1-zeta^2)
+    bubble_scale: float = 1.0   # b = bubble_scale * (1-xi^2)(1-eta^2)(1-zeta^2) (hexahedron)
+    element: str = "hex"        # "hex": Q1 + one bubble; "tet": P1 + one bubble (MINI-type)
 
     @property
     def nut(self) -> float:
@@ -96,6 +97,69 @@ def bubble(xi: np.ndarray, scale: float = 1.0):
 
 
 # ----------------------------------------------------------------------------------------------
+# reference tetrahedron: vertices (0,0,0), (1,0,0), (0,1,0), (0,0,1); barycentric coordinates
+# lambda = (1 - xi - eta - zeta, xi, eta, zeta); P1 shape functions N_a = lambda_a; the bubble
+# b = 256 lambda_0 lambda_1 lambda_2 lambda_3 (zero on every face, 1 at the centroid)
+# ----------------------------------------------------------------------------------------------
+
+TET_CORNERS = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+TET_DLAMBDA = np.array([[-1, -1, -1], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+
+
+def tet_rule(n: int):
+    """Conical-product (collapsed Gauss) rule on the reference tetrahedron with n points per
+    direction: xi = u, eta = v (1 - u), zeta = w (1 - u)(1 - v) with Gauss-Jacobi points in u
+    (weight (1-u)^2), v (weight (1-v)) and Gauss-Legendre points in w, all on [0, 1]; exact for
+    polynomials of total degree 2n - 1. Returns points (n^3, 3) and weights (sum 1/6)."""
+    from scipy.special import roots_jacobi
+    def on01(x, w, a):   # Gauss-Jacobi on [-1,1] with weight (1-x)^a -> [0,1] with (1-u)^a
+        return (x + 1.0) / 2.0, w / 2.0 ** (a + 1)
+    ux, uw = on01(*roots_jacobi(n, 2.0, 0.0), 2)
+    vx, vw = on01(*roots_jacobi(n, 1.0, 0.0), 1)
+    wx, ww = on01(*roots_jacobi(n, 0.0, 0.0), 0)
+    pts, wts = [], []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                u, v, w = ux[i], vx[j], wx[k]
+                pts.append((u, v * (1.0 - u), w * (1.0 - u) * (1.0 - v)))
+                wts.append(uw[i] * vw[j] * ww[k])
+    return np.array(pts), np.array(wts)
+
+
+def p1_basis(xi: np.ndarray):
+    """N_a = lambda_a and the constant reference gradients. Returns N (nq,4), dN (nq,4,3)."""
+    xi = np.atleast_2d(xi)
+    lam = np.stack([1.0 - xi.sum(axis=1), xi[:, 0], xi[:, 1], xi[:, 2]], axis=1)
+    dN = np.broadcast_to(TET_DLAMBDA, (xi.shape[0], 4, 3)).copy()
+    return lam, dN
+
+
+def tet_bubble(xi: np.ndarray, scale: float = 1.0):
+    """b = scale * 256 prod_a lambda_a and its reference gradient. Returns b (nq,), db (nq,3)."""
+    lam, _ = p1_basis(xi)
+    b = scale * 256.0 * lam.prod(axis=1)
+    db = np.zeros((lam.shape[0], 3))
+    for a in range(4):
+        others = np.prod(lam[:, [c for c in range(4) if c != a]], axis=1)
+        db += scale * 256.0 * others[:, None] * TET_DLAMBDA[a][None, :]
+    return b, db
+
+
+def element_basis(params):
+    """Quadrature points, weights, shape functions and bubble of the element kind in params."""
+    if params.element == "tet":
+        pts, wts = tet_rule(params.quad_order)
+        N, dN = p1_basis(pts)
+        b, db = tet_bubble(pts, params.bubble_scale)
+    else:
+        pts, wts = gauss_rule(params.quad_order)
+        N, dN = q1_basis(pts)
+        b, db = bubble(pts, params.bubble_scale)
+    return pts, wts, N, dN, b, db
+
+
+# ----------------------------------------------------------------------------------------------
 # element residual and consistent tangent (Section 4.1 Eqs. SC_Coarse_Resid_Vec, _Vec_2,
 # SC_Fine_Resid_Vec and the transient Remark; Section 4.2 Eq. NewtonUpdate2)
 # ----------------------------------------------------------------------------------------------
@@ -151,16 +215,15 @@ def element_kernel(X, U, beta, params: Params, Uprev=None, with_tangent=True):
         if Uprev is None:
             raise ValueError("transient step needs the previous velocity")
         dV = V - np.asarray(Uprev, np.float64)[:, :, :3]
-    pts, wts = gauss_rule(params.quad_order)
-    Nq, dNq = q1_basis(pts)
-    bq, dbq = bubble(pts, params.bubble_scale)
+    pts, wts, Nq, dNq, bq, dbq = element_basis(params)
     I3 = np.eye(3)
+    na = X.shape[1]   # nodes per element: 8 (hexahedron) or 4 (tetrahedron)
 
-    Rc = np.zeros((E, 8, 3)); Rp = np.zeros((E, 8)); Rf = np.zeros((E, 3))
+    Rc = np.zeros((E, na, 3)); Rp = np.zeros((E, na)); Rf = np.zeros((E, 3))
     if with_tangent:
-        Kvv = np.zeros((E, 8, 3, 8, 3)); Kvp = np.zeros((E, 8, 3, 8)); Kpv = np.zeros((E, 8, 8, 3))
-        Kvf = np.zeros((E, 8, 3, 3)); Kpf = np.zeros((E, 8, 3))
-        Kfv = np.zeros((E, 3, 8, 3)); Kfp = np.zeros((E, 3, 8)); Kff = np.zeros((E, 3, 3))
+        Kvv = np.zeros((E, na, 3, na, 3)); Kvp = np.zeros((E, na, 3, na)); Kpv = np.zeros((E, na, na, 3))
+        Kvf = np.zeros((E, na, 3, 3)); Kpf = np.zeros((E, na, 3))
+        Kfv = np.zeros((E, 3, na, 3)); Kfp = np.zeros((E, 3, na)); Kff = np.zeros((E, 3, 3))
 
     for q in range(pts.shape[0]):
         N, dN, b, db = Nq[q], dNq[q], bq[q], dbq[q]
@@ -245,38 +308,40 @@ def elementary_integrals(X, quad_order=3, bubble_scale=1.0):
 
 
 def pack_element(k):
-    """Pack the blocks in node-major coarse order (dof 4a+c, c=3 pressure).
+    """Pack the blocks in node-major coarse order (dof 4a+c, c=3 pressure); n = 4 * nodes per
+    element (32 for the hexahedron, 16 for the tetrahedron).
 
-    Returns Kcc (E,32,32), Kcf (E,32,3), Kfc (E,3,32), Kff (E,3,3), Rcp (E,32), Rf (E,3)."""
-    E = k["Rc"].shape[0]
-    Kcc = np.zeros((E, 8, 4, 8, 4))
+    Returns Kcc (E,n,n), Kcf (E,n,3), Kfc (E,3,n), Kff (E,3,3), Rcp (E,n), Rf (E,3)."""
+    E, na = k["Rc"].shape[0], k["Rc"].shape[1]
+    nc = 4 * na
+    Kcc = np.zeros((E, na, 4, na, 4))
     Kcc[:, :, :3, :, :3] = k["Kvv"]
     Kcc[:, :, :3, :, 3] = k["Kvp"]
     Kcc[:, :, 3, :, :3] = k["Kpv"]
-    Kcf = np.zeros((E, 8, 4, 3))
+    Kcf = np.zeros((E, na, 4, 3))
     Kcf[:, :, :3, :] = k["Kvf"]
     Kcf[:, :, 3, :] = k["Kpf"]
-    Kfc = np.zeros((E, 3, 8, 4))
+    Kfc = np.zeros((E, 3, na, 4))
     Kfc[:, :, :, :3] = k["Kfv"]
     Kfc[:, :, :, 3] = k["Kfp"]
-    Rcp = np.zeros((E, 8, 4))
+    Rcp = np.zeros((E, na, 4))
     Rcp[:, :, :3] = k["Rc"]
     Rcp[:, :, 3] = k["Rp"]
-    return (Kcc.reshape(E, 32, 32), Kcf.reshape(E, 32, 3), Kfc.reshape(E, 3, 32),
-            k["Kff"].copy(), Rcp.reshape(E, 32), k["Rf"].copy())
+    return (Kcc.reshape(E, nc, nc), Kcf.reshape(E, nc, 3), Kfc.reshape(E, 3, nc),
+            k["Kff"].copy(), Rcp.reshape(E, nc), k["Rf"].copy())
 
 
 def pack_residual(k):
-    """Residuals in node-major coarse order: Rcp (E,32) with dof 4a+c, and Rf (E,3)."""
-    E = k["Rc"].shape[0]
-    Rcp = np.concatenate([k["Rc"], k["Rp"][:, :, None]], axis=2).reshape(E, 32)
+    """Residuals in node-major coarse order: Rcp (E,4 na) with dof 4a+c, and Rf (E,3)."""
+    E, na = k["Rc"].shape[0], k["Rc"].shape[1]
+    Rcp = np.concatenate([k["Rc"], k["Rp"][:, :, None]], axis=2).reshape(E, 4 * na)
     return Rcp, k["Rf"].copy()
 
 
 def condense(Kcc, Kcf, Kfc, Kff, Rcp, Rf):
     """Block Gauss elimination of the three bubble unknowns (Section 5, Eq. SchurUpdate):
       S_e = K_cc - K_cf K_ff^-1 K_fc,     r_e = R_cp - K_cf K_ff^-1 R_f.
-    Returns S (E,32,32), r (E,32), KffinvKfc (E,3,32), KffinvRf (E,3)."""
+    Returns S (E,n,n), r (E,n), KffinvKfc (E,3,n), KffinvRf (E,3)."""
     X = np.linalg.solve(Kff, Kfc)                    # K_ff^-1 K_fc
     y = np.linalg.solve(Kff, Rf[:, :, None])[:, :, 0]
     S = Kcc - Kcf @ X
@@ -290,7 +355,7 @@ def condense(Kcc, Kcf, Kfc, Kff, Rcp, Rf):
 
 def element_dofs(conn):
     conn = np.asarray(conn, np.int64)
-    return (4 * conn[:, :, None] + np.arange(4)[None, None, :]).reshape(conn.shape[0], 32)
+    return (4 * conn[:, :, None] + np.arange(4)[None, None, :]).reshape(conn.shape[0], 4 * conn.shape[1])
 
 
 def gather(conn, xyz, u, beta, u_prev=None):
@@ -304,8 +369,9 @@ def assemble(conn, n_nodes, S, r):
     """Sum element matrices and vectors into the global coarse system (CSR, duplicates summed)."""
     dofs = element_dofs(conn)
     E = dofs.shape[0]
-    rows = np.repeat(dofs, 32, axis=1).reshape(-1)
-    cols = np.tile(dofs, (1, 32)).reshape(-1)
+    nc = dofs.shape[1]
+    rows = np.repeat(dofs, nc, axis=1).reshape(-1)
+    cols = np.tile(dofs, (1, nc)).reshape(-1)
     n = 4 * n_nodes
     A = sp.coo_matrix((S.reshape(-1), (rows, cols)), shape=(n, n)).tocsr()
     A.sum_duplicates()
@@ -340,7 +406,7 @@ def residual_vector(conn, n_nodes, k, dir_dofs):
     dofs = element_dofs(conn)
     Rcp = np.zeros(4 * n_nodes)
     E = conn.shape[0]
-    rc = np.concatenate([k["Rc"], k["Rp"][:, :, None]], axis=2).reshape(E, 32)
+    rc = np.concatenate([k["Rc"], k["Rp"][:, :, None]], axis=2).reshape(E, dofs.shape[1])
     np.add.at(Rcp, dofs.reshape(-1), rc.reshape(-1))
     Rcp[np.asarray(dir_dofs, np.int64)] = 0.0
     return np.concatenate([Rcp, k["Rf"].reshape(-1)])
@@ -348,7 +414,7 @@ def residual_vector(conn, n_nodes, k, dir_dofs):
 
 def fine_recovery(conn, du, X_kfc, y_rf):
     """Delta beta_e = K_ff^-1 (-R_f - K_fc Delta u_e)  (Section 5, after Eq. SchurUpdate)."""
-    due = du[element_dofs(conn)]                     # (E,32)
+    due = du[element_dofs(conn)]                     # (E,4 na)
     return -y_rf - np.einsum("eic,ec->ei", X_kfc, due)
 
 

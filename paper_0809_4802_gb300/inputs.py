@@ -409,3 +409,58 @@ def vortex_box_workload(n: int, re: float = 200.0, dt: float = 0.02, jitter_frac
     impose(u, bc)
     return Workload(mesh=mesh, bc=bc, u=u, beta=np.zeros((mesh.n_elems, 3)), nu=1.0 / re, dt=dt,
                     u_prev=u.copy(), name=f"vortex{n}_re{re:g}")
+
+
+# ----------------------------------------------------------------------------------------------
+# tetrahedral meshes: every lattice hexahedron split into the 6 tetrahedra along its main diagonal
+# (Kuhn subdivision: the paths 000 -> 111 along the three axes in every order), which is
+# conforming across neighbouring cubes
+# ----------------------------------------------------------------------------------------------
+
+def tet_mesh_from_lattice(hexm: Mesh) -> Mesh:
+    """Split a lattice hexahedral mesh into tetrahedra (6 per hexahedron), positively oriented."""
+    # local hex corner of offset (dx, dy, dz) in the order of HEX_CORNERS
+    off = HEX_CORNERS.clip(0, 1).astype(int)
+    local = {tuple(o): a for a, o in enumerate(off)}
+    paths = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        p = np.zeros(3, int)
+        verts = [local[tuple(p)]]
+        for ax in perm:
+            p = p.copy()
+            p[ax] = 1
+            verts.append(local[tuple(p)])
+        paths.append(verts)
+    conn = np.concatenate([hexm.conn[:, v] for v in paths], axis=0)
+    x = hexm.xyz[conn]
+    vol = np.einsum("ei,ei->e", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))
+    neg = vol < 0
+    conn[neg] = conn[neg][:, [0, 2, 1, 3]]
+    m = Mesh(xyz=hexm.xyz.copy(), conn=conn.astype(np.int32), node_ijk=hexm.node_ijk,
+             meta=dict(hexm.meta, element="tet"))
+    m.name = hexm.name + "_tet"
+    return m
+
+
+def tet_cavity_workload(n: int, re: float, *, jitter_frac: float = 0.0, state: str = "noise",
+                        seed: int = 1001) -> Workload:
+    """The lid-driven cavity of cavity_workload on the Kuhn tetrahedral mesh of the n^3 lattice
+    (6 n^3 tetrahedra, (n+1)^3 nodes): same boundary conditions, pressure pin and states."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hexm = cavity_mesh(n)
+    if jitter_frac > 0:
+        jitter(hexm, jitter_frac, rng)
+    bc = cavity_bc(hexm)
+    u = np.zeros((hexm.n_nodes, 4))
+    if state == "noise":
+        inner = ~boundary_nodes(hexm)
+        u[inner, :3] = rng.uniform(-0.05, 0.05, size=(int(inner.sum()), 3))
+    elif state == "random":
+        u[:, :3] = rng.uniform(-0.5, 0.5, size=(hexm.n_nodes, 3))
+        u[:, 3] = rng.normal(0.0, 0.1, size=hexm.n_nodes)
+    elif state != "zero":
+        raise ValueError(state)
+    impose(u, bc)
+    mesh = tet_mesh_from_lattice(hexm)
+    return Workload(mesh=mesh, bc=bc, u=u, beta=np.zeros((mesh.n_elems, 3)), nu=1.0 / re,
+                    name=f"tetcavity{n}_re{re:g}")
