@@ -116,6 +116,22 @@ int vms_mesh_upload(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_
                     const int32_t* conn, int64_t n_dir, const int64_t* dir_dof,
                     const double* dir_val);
 
+/* vms_mesh_upload for a mesh of 4-node tetrahedra (P1 velocity and pressure plus one vector bubble
+ * b = 256 lambda_0 lambda_1 lambda_2 lambda_3 per element: the MINI-type element the paper cites,
+ * Section 3.3). conn: n_elems x 4 int32, positively oriented (reference vertices (0,0,0), (1,0,0),
+ * (0,1,0), (0,0,1)). Element blocks have 16 coarse dofs (vms_element_matrices returns 16 x 16
+ * S_e). Quadrature: the conical-product rule with params.quad_order points per direction (exact to
+ * degree 2 quad_order - 1; vms_tet_rule). The tetrahedral kernels compute in FP64 in both
+ * precision modes; VMS_PREC_MIXED stores the CSR values in FP32 for the mixed-precision solve.
+ * Errors: as vms_mesh_upload. */
+int vms_mesh_upload_tet(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_elems,
+                        const int32_t* conn, int64_t n_dir, const int64_t* dir_dof,
+                        const double* dir_val);
+
+/* The tetrahedral quadrature rule (host only, no GPU needed): n^3 points (pts, 3 n^3 doubles,
+ * reference coordinates) and weights (wts, n^3 doubles summing to 1/6), 1 <= n <= 8. */
+int vms_tet_rule(int n, double* pts, double* wts);
+
 /* Set nu, visc_factor, dt, body force, bubble scale, quadrature order and scatter mode.
  * Errors: VMS_ERR_INVALID_ARG (nu <= 0, quad_order not in {2,3,4}, dt < 0, bad mode). */
 int vms_set_params(vms_ctx* ctx, const vms_params* params);

@@ -21,6 +21,8 @@ struct vms_ctx {
   QpRow* d_qp = nullptr;     // nq rows (residual kernel)
   double* d_tab64 = nullptr; // 37 nq (tangent kernel, FP64)
   float* d_tab32 = nullptr;  // 37 nq (tangent kernel, FP32)
+  double* d_tettab = nullptr; // TET_ROW nq_tet (tetrahedral kernel)
+  int nq_tet = 0;
   Mesh mesh;
   State state;
   Work work;
@@ -213,6 +215,12 @@ int upload_tables(vms_ctx* ctx) {
   CK(cudaMemcpy(ctx->d_tab64, t64.data(), sizeof(double) * 37 * nq, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_tab32, t32.data(), sizeof(float) * 37 * nq, cudaMemcpyHostToDevice));
   ctx->nq = nq;
+  std::vector<double> tt;
+  tet_table(n1, bs, tt);
+  dfree(ctx->d_tettab);
+  CK(cudaMalloc(&ctx->d_tettab, sizeof(double) * tt.size()));
+  CK(cudaMemcpy(ctx->d_tettab, tt.data(), sizeof(double) * tt.size(), cudaMemcpyHostToDevice));
+  ctx->nq_tet = (int)(tt.size() / TET_ROW);
   return VMS_OK;
 }
 
@@ -291,6 +299,7 @@ int vms_destroy(vms_ctx* ctx) {
   for (auto& e : ctx->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_scalar);
+  dfree(ctx->d_tettab);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->work.aux) { cudaStreamSynchronize(ctx->work.aux); cudaStreamDestroy(ctx->work.aux); }
@@ -448,9 +457,25 @@ int vms_set_graph(vms_ctx* ctx, int enable) {
   return VMS_OK;
 }
 
+static int mesh_upload_impl(vms_ctx* ctx, int npe, int64_t n_nodes, const double* xyz,
+                            int64_t n_elems, const int32_t* conn, int64_t n_dir,
+                            const int64_t* dir_dof, const double* dir_val);
+
 int vms_mesh_upload(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_elems,
                     const int32_t* conn, int64_t n_dir, const int64_t* dir_dof,
                     const double* dir_val) {
+  return mesh_upload_impl(ctx, 8, n_nodes, xyz, n_elems, conn, n_dir, dir_dof, dir_val);
+}
+
+int vms_mesh_upload_tet(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_elems,
+                        const int32_t* conn, int64_t n_dir, const int64_t* dir_dof,
+                        const double* dir_val) {
+  return mesh_upload_impl(ctx, 4, n_nodes, xyz, n_elems, conn, n_dir, dir_dof, dir_val);
+}
+
+static int mesh_upload_impl(vms_ctx* ctx, int npe, int64_t n_nodes, const double* xyz,
+                            int64_t n_elems, const int32_t* conn, int64_t n_dir,
+                            const int64_t* dir_dof, const double* dir_val) {
   if (!ctx) return VMS_ERR_INVALID_ARG;
   if (n_nodes <= 0 || n_elems <= 0 || !xyz || !conn || n_dir < 0 || (n_dir > 0 && (!dir_dof || !dir_val)))
     return fail(ctx, VMS_ERR_INVALID_ARG, "invalid mesh arguments");
@@ -461,28 +486,29 @@ int vms_mesh_upload(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_
   free_mesh(ctx);
   // bring inputs to the host (they may be device pointers)
   std::vector<double> hx(3 * n_nodes);
-  std::vector<int32_t> hc(8 * n_elems);
+  std::vector<int32_t> hc((size_t)npe * n_elems);
   std::vector<int64_t> hd(n_dir);
   std::vector<double> hv(n_dir);
   CK(cudaMemcpy(hx.data(), xyz, sizeof(double) * 3 * n_nodes, cudaMemcpyDefault));
-  CK(cudaMemcpy(hc.data(), conn, sizeof(int32_t) * 8 * n_elems, cudaMemcpyDefault));
+  CK(cudaMemcpy(hc.data(), conn, sizeof(int32_t) * npe * n_elems, cudaMemcpyDefault));
   if (n_dir) {
     CK(cudaMemcpy(hd.data(), dir_dof, sizeof(int64_t) * n_dir, cudaMemcpyDefault));
     CK(cudaMemcpy(hv.data(), dir_val, sizeof(double) * n_dir, cudaMemcpyDefault));
   }
   HostPattern pat;
-  const std::string perr = build_pattern(n_nodes, n_elems, hc.data(), n_dir, hd.data(), pat);
+  const std::string perr = build_pattern(n_nodes, n_elems, hc.data(), n_dir, hd.data(), pat, npe);
   if (!perr.empty()) return fail(ctx, VMS_ERR_INVALID_ARG, perr);
 
   Mesh& m = ctx->mesh;
   m.n_nodes = n_nodes;
   m.n_elems = n_elems;
+  m.npe = npe;
   m.nnz = pat.rowptr.back();
   m.n_dir = n_dir;
   std::vector<double4_32a> x4(n_nodes);
   for (int64_t i = 0; i < n_nodes; ++i) x4[i] = make_double4_32a(hx[3 * i], hx[3 * i + 1], hx[3 * i + 2], 0.0);
   TRY(upload(ctx, m.xyz, x4.data(), n_nodes));
-  TRY(upload(ctx, m.conn, hc.data(), 8 * n_elems));
+  TRY(upload(ctx, m.conn, hc.data(), (size_t)npe * n_elems));
   TRY(upload(ctx, m.rowptr, pat.rowptr.data(), pat.rowptr.size()));
   TRY(upload(ctx, m.colidx, pat.colidx.data(), pat.colidx.size()));
   TRY(upload(ctx, m.blk, pat.blk.data(), pat.blk.size()));
@@ -587,6 +613,28 @@ static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
     k.add(launch_fill_zero(w.values, (size_t)m.nnz * (f32 ? sizeof(float) : sizeof(double)), st));
     k.add(launch_fill_zero(w.rhs, sizeof(double) * 4 * m.n_nodes, st));
     k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st));
+  }
+  if (m.npe == 4) {  // tetrahedra: one kernel does residual, tangent, condensation and scatter
+    TangentOut o;
+    o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv;
+    o.recY = w.recY;
+    const int scatter = ctx->tune.scatter_mode >= 0 ? ctx->tune.scatter_mode : ctx->params.scatter_mode;
+    {
+      KScope k(ctx, VMS_K_TANGENT, st);
+      if (scatter == VMS_SCATTER_COLOUR) {
+        for (int c = 0; c < m.n_colours; ++c) {
+          const int64_t b = m.colour_start[c], n = m.colour_start[c + 1] - b;
+          k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, o, b, n,
+                                    m.colour_order, false, false, w.flags, st));
+        }
+      } else {
+        k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, o, 0,
+                                  m.n_elems, nullptr, false, true, w.flags, st));
+      }
+    }
+    { KScope k(ctx, VMS_K_DIRICHLET, st); k.add(launch_dirichlet_diag(m, w.values, f32, w.rhs, st)); }
+    CK(cudaGetLastError());
+    return VMS_OK;
   }
   if (f32) {
     KScope k(ctx, VMS_K_FILL, st);
@@ -710,8 +758,12 @@ int vms_residual(vms_ctx* ctx, double* norm, double* R) {
   }
   {
     KScope k(ctx, VMS_K_RESIDUAL);
-    k.add(launch_residual(m, ctx->state, kparams(ctx), ctx->d_qp, nullptr, w.resid, 0, m.n_elems, 1,
-                          w.flags, st));
+    if (m.npe == 4)
+      k.add(launch_tet_residual(m, ctx->state, kparams(ctx), ctx->d_tettab, ctx->nq_tet, nullptr,
+                                w.resid, 0, m.n_elems, 1, w.flags, st));
+    else
+      k.add(launch_residual(m, ctx->state, kparams(ctx), ctx->d_qp, nullptr, w.resid, 0, m.n_elems, 1,
+                            w.flags, st));
   }
   { KScope k(ctx, VMS_K_REDUCE); k.add(launch_norm2(w.resid, n, w.partial, ctx->d_scalar, st)); }
   CK(cudaGetLastError());
@@ -720,6 +772,50 @@ int vms_residual(vms_ctx* ctx, double* norm, double* R) {
   TRY(check_flags(ctx));
   *norm = std::sqrt(ctx->h_scalar[0]);
   return VMS_OK;
+}
+
+// Element outputs of the tetrahedral kernel: blocks of 16 coarse dofs.
+static int element_matrices_tet(vms_ctx* ctx, int64_t first, int64_t count, double* S, double* r,
+                                double* Kcc, double* Kcf, double* Kfc, double* Kff, double* Rcp,
+                                double* Rf) {
+  const Mesh& m = ctx->mesh;
+  Work& w = ctx->work;
+  cudaStream_t st = ctx->stream;
+  const KParams kp = kparams(ctx);
+  const bool f32 = fp32_mode(ctx);
+  {
+    KScope k(ctx, VMS_K_RESIDUAL);
+    k.add(launch_tet_residual(m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, w.elemR, nullptr,
+                              first, count, 0, w.flags, st));
+  }
+  double* buf = nullptr;
+  const size_t per = 256 + 16 + 256 + 48 + 48 + 9;
+  CK(cudaMalloc(&buf, sizeof(double) * per * count));
+  TangentOut o;
+  o.S = buf; o.r = buf + 256 * count; o.Kcc = buf + 272 * count; o.Kcf = buf + 528 * count;
+  o.Kfc = buf + 576 * count; o.Kff = buf + 624 * count;
+  o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv; o.recY = w.recY;
+  {
+    KScope k(ctx, VMS_K_TANGENT);
+    k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, o, first, count,
+                              nullptr, true, true, w.flags, st));
+  }
+  cudaError_t e = cudaGetLastError();
+  struct Out { double* dst; double* src; size_t n; } outs[6] = {
+      {S, o.S, 256}, {r, o.r, 16}, {Kcc, o.Kcc, 256}, {Kcf, o.Kcf, 48}, {Kfc, o.Kfc, 48}, {Kff, o.Kff, 9}};
+  for (auto& x : outs)
+    if (e == cudaSuccess && x.dst)
+      e = cudaMemcpyAsync(x.dst, x.src, sizeof(double) * x.n * count, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && Rcp)
+    e = cudaMemcpy2DAsync(Rcp, 16 * sizeof(double), w.elemR + 36 * first, 36 * sizeof(double),
+                          16 * sizeof(double), count, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && Rf)
+    e = cudaMemcpy2DAsync(Rf, 3 * sizeof(double), w.elemR + 36 * first + 32, 36 * sizeof(double),
+                          3 * sizeof(double), count, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  return check_flags(ctx);
 }
 
 int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, double* r,
@@ -737,6 +833,7 @@ int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, 
   const KParams kp = kparams(ctx);
   const bool f32 = fp32_mode(ctx);
   { KScope k(ctx, VMS_K_FILL); k.add(launch_fill_zero(w.flags, sizeof(unsigned int), st)); }
+  if (m.npe == 4) return element_matrices_tet(ctx, first, count, S, r, Kcc, Kcf, Kfc, Kff, Rcp, Rf);
   if (f32) {
     KScope k(ctx, VMS_K_FILL);
     k.add(launch_to_fp32(m, ctx->state, w.f32, false, st));

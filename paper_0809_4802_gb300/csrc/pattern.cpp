@@ -1,7 +1,8 @@
 // Once-per-mesh host work: CSR pattern of the condensed coarse system, element -> CSR block map,
 // element colouring and Dirichlet bookkeeping. The assembly operator of Section 5 (Eq.
-// SchurUpdate) sums 32x32 element matrices over elements; this file fixes where each element's
-// 8x8 node blocks of 4x4 values land, so the device scatter is a plain indexed add.
+// SchurUpdate) sums element matrices (32x32 for the hexahedron, 16x16 for the tetrahedron) over
+// elements; this file fixes where each element's npe x npe node blocks of 4x4 values land, so the
+// device scatter is a plain indexed add.
 //
 // Layout: node-major dofs 4*node+c. Row 4n+i holds, for every neighbour m of node n in increasing
 // order, the four columns 4m..4m+3, so the 4x4 block (n,m) occupies four runs of four contiguous
@@ -16,24 +17,25 @@
 namespace vms {
 
 std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn, int64_t n_dir,
-                          const int64_t* dir_dof, HostPattern& out) {
+                          const int64_t* dir_dof, HostPattern& out, int npe) {
   if (n_nodes <= 0 || n_elems <= 0) return "mesh must have nodes and elements";
-  for (int64_t i = 0; i < n_elems * 8; ++i)
+  if (npe != 4 && npe != 8) return "elements must have 4 or 8 nodes";
+  for (int64_t i = 0; i < n_elems * npe; ++i)
     if (conn[i] < 0 || conn[i] >= n_nodes) return "connectivity index out of range";
   for (int64_t e = 0; e < n_elems; ++e)
-    for (int a = 0; a < 8; ++a)
-      for (int b = a + 1; b < 8; ++b)
-        if (conn[e * 8 + a] == conn[e * 8 + b]) return "element with a repeated node";
+    for (int a = 0; a < npe; ++a)
+      for (int b = a + 1; b < npe; ++b)
+        if (conn[e * npe + a] == conn[e * npe + b]) return "element with a repeated node";
 
   // node -> element incidence (counting sort)
   std::vector<int64_t> nstart(n_nodes + 1, 0);
-  for (int64_t i = 0; i < n_elems * 8; ++i) nstart[conn[i] + 1]++;
+  for (int64_t i = 0; i < n_elems * npe; ++i) nstart[conn[i] + 1]++;
   for (int64_t n = 0; n < n_nodes; ++n) nstart[n + 1] += nstart[n];
   std::vector<int32_t> nelem(nstart[n_nodes]);
   {
     std::vector<int64_t> fill(nstart.begin(), nstart.end() - 1);
     for (int64_t e = 0; e < n_elems; ++e)
-      for (int a = 0; a < 8; ++a) nelem[fill[conn[e * 8 + a]]++] = (int32_t)e;
+      for (int a = 0; a < npe; ++a) nelem[fill[conn[e * npe + a]]++] = (int32_t)e;
   }
 
   // sorted neighbour lists
@@ -45,8 +47,8 @@ std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn,
   for (int64_t n = 0; n < n_nodes; ++n) {
     cand.clear();
     for (int64_t k = nstart[n]; k < nstart[n + 1]; ++k) {
-      const int32_t* c = conn + (int64_t)nelem[k] * 8;
-      cand.insert(cand.end(), c, c + 8);
+      const int32_t* c = conn + (int64_t)nelem[k] * npe;
+      cand.insert(cand.end(), c, c + npe);
     }
     std::sort(cand.begin(), cand.end());
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
@@ -79,30 +81,32 @@ std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn,
     return (int64_t)(it - b);
   };
 
-  // element block map
-  out.blk.resize((size_t)n_elems * 64);
+  // element block map: npe x npe blocks per element
+  const int nb = npe * npe;
+  out.blk.resize((size_t)n_elems * nb);
   for (int64_t e = 0; e < n_elems; ++e) {
-    const int32_t* c = conn + e * 8;
-    for (int a = 0; a < 8; ++a)
-      for (int b = 0; b < 8; ++b)
-        out.blk[e * 64 + a * 8 + b] = out.rowptr[4 * c[a]] + (int32_t)(4 * find_pos(c[a], c[b]));
+    const int32_t* c = conn + e * npe;
+    for (int a = 0; a < npe; ++a)
+      for (int b = 0; b < npe; ++b)
+        out.blk[e * nb + a * npe + b] = out.rowptr[4 * c[a]] + (int32_t)(4 * find_pos(c[a], c[b]));
   }
 
-  // greedy colouring: no two elements of one colour share a node
+  // greedy colouring: no two elements of one colour share a node (at most 128 colours)
+  constexpr int MAXC = 128;
   out.colour.assign(n_elems, -1);
   int n_col = 0;
   for (int64_t e = 0; e < n_elems; ++e) {
-    uint64_t used = 0;
-    for (int a = 0; a < 8; ++a) {
-      int32_t n = conn[e * 8 + a];
+    uint64_t used[MAXC / 64] = {0, 0};
+    for (int a = 0; a < npe; ++a) {
+      int32_t n = conn[e * npe + a];
       for (int64_t k = nstart[n]; k < nstart[n + 1]; ++k) {
         int32_t o = out.colour[nelem[k]];
-        if (o >= 0 && o < 64) used |= (1ull << o);
+        if (o >= 0) used[o >> 6] |= (1ull << (o & 63));
       }
     }
     int col = 0;
-    while (col < 64 && (used >> col & 1ull)) ++col;
-    if (col >= 64) return "element colouring needs more than 64 colours";
+    while (col < MAXC && (used[col >> 6] >> (col & 63) & 1ull)) ++col;
+    if (col >= MAXC) return "element colouring needs more than 128 colours";
     out.colour[e] = col;
     n_col = std::max(n_col, col + 1);
   }
@@ -130,9 +134,9 @@ std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn,
   out.dir_mask.assign(n_elems, 0u);
   for (int64_t e = 0; e < n_elems; ++e) {
     uint32_t m = 0;
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < npe; ++a)
       for (int c = 0; c < 4; ++c)
-        if (constrained[4 * (int64_t)conn[e * 8 + a] + c]) m |= 1u << (4 * a + c);
+        if (constrained[4 * (int64_t)conn[e * npe + a] + c]) m |= 1u << (4 * a + c);
     out.dir_mask[e] = m;
   }
   return "";

@@ -222,14 +222,14 @@ __global__ void axpby_kernel(double a, const A* x, double b, const B* y, C* out,
 // Fine-scale recovery (Section 5): dbeta_e = -(K_ff^-1 R_f + K_ff^-1 K_fc du_e); beta += dbeta.
 // Elements [e0, e1); du is compact over the nodes from n0 on.
 template <typename T>
-__global__ void recover_kernel(const int32_t* __restrict__ conn, const T* __restrict__ recX,
+__global__ void recover_kernel(const int32_t* __restrict__ conn, int npe, const T* __restrict__ recX,
                                const double* __restrict__ recY, const double* __restrict__ du,
                                double* __restrict__ beta, int64_t e0, int64_t e1, int64_t n0) {
   const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= e1) return;
   double s[3] = {recY[3 * e], recY[3 * e + 1], recY[3 * e + 2]};
-  for (int a = 0; a < 8; ++a) {
-    const int64_t nd = conn[8 * e + a] - n0;
+  for (int a = 0; a < npe; ++a) {
+    const int64_t nd = conn[npe * e + a] - n0;
     for (int c = 0; c < 4; ++c) {
       const double d = du[4 * nd + c];
       for (int m = 0; m < 3; ++m) s[m] += (double)recX[96 * e + 32 * m + 4 * a + c] * d;
@@ -652,9 +652,9 @@ static int recover_and_update(vms_ctx* ctx, const SysRange& R) {
   const int64_t ne = R.e1 - R.e0;
   const unsigned eb = (unsigned)((ne + 127) / 128 > 0 ? (ne + 127) / 128 : 1);
   if (ctx_fp32(ctx))
-    recover_kernel<float><<<eb, 128, 0, st>>>(m.conn, (const float*)wk.recX, wk.recY, w.x, s.beta, R.e0, R.e1, R.n0);
+    recover_kernel<float><<<eb, 128, 0, st>>>(m.conn, m.npe, (const float*)wk.recX, wk.recY, w.x, s.beta, R.e0, R.e1, R.n0);
   else
-    recover_kernel<double><<<eb, 128, 0, st>>>(m.conn, (const double*)wk.recX, wk.recY, w.x, s.beta, R.e0, R.e1, R.n0);
+    recover_kernel<double><<<eb, 128, 0, st>>>(m.conn, m.npe, (const double*)wk.recX, wk.recY, w.x, s.beta, R.e0, R.e1, R.n0);
   const int64_t n = 4 * R.nodes();
   double* u = reinterpret_cast<double*>(s.u) + 4 * R.n0;
   axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, u, 1.0, w.x, u, n);

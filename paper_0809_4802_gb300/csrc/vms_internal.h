@@ -50,7 +50,7 @@ struct KParams {
 struct HostPattern {
   std::vector<int32_t> rowptr;    // 4*n_nodes + 1
   std::vector<int32_t> colidx;    // nnz
-  std::vector<int32_t> blk;       // n_elems * 64: value offset of block (a,b), row 4*na, col 4*nb
+  std::vector<int32_t> blk;       // n_elems * npe^2: value offset of block (a,b), row 4*na, col 4*nb
   std::vector<int32_t> rowlen;    // n_nodes: entries per row of node n (4 * neighbours)
   std::vector<int32_t> colour;    // n_elems
   std::vector<int32_t> colour_order;  // elements sorted by colour
@@ -62,17 +62,18 @@ struct HostPattern {
 
 // Builds the CSR pattern, block map, colouring and Dirichlet masks. Returns "" or an error text.
 std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn, int64_t n_dir,
-                          const int64_t* dir_dof, HostPattern& out);
+                          const int64_t* dir_dof, HostPattern& out, int npe);
 
 // ---- device data and kernel launchers ----------------------------------------------------------
 
 struct Mesh {
   int64_t n_nodes = 0, n_elems = 0, nnz = 0;
+  int npe = 8;                   // nodes per element: 8 (hexahedron) or 4 (tetrahedron)
   double4_32a* xyz = nullptr;        // n_nodes (x, y, z, 0)
-  int32_t* conn = nullptr;       // n_elems * 8
+  int32_t* conn = nullptr;       // n_elems * npe
   int32_t* rowptr = nullptr;     // 4 n_nodes + 1
   int32_t* colidx = nullptr;     // nnz
-  int32_t* blk = nullptr;        // n_elems * 64
+  int32_t* blk = nullptr;        // n_elems * npe^2
   int32_t* rowlen = nullptr;     // n_nodes
   uint32_t* dir_mask = nullptr;  // n_elems
   int64_t n_dir = 0;
@@ -134,6 +135,20 @@ struct TangentOut {
   double *S = nullptr, *r = nullptr, *Kcc = nullptr, *Kcf = nullptr, *Kfc = nullptr,
          *Kff = nullptr;
 };
+// Tetrahedral element (tet.cu): table row per quadrature point (lambda_0..3, b, db/dxi_0..2, w)
+constexpr int TET_ROW = 9;
+void tet_table(int n, double bubble_scale, std::vector<double>& tab);
+// The whole assembly of a tetrahedral mesh (residual, tangent, condensation, scatter, r_e and the
+// recovery data) in one kernel; FP64 arithmetic, values stored in FP32 when fp32.
+int launch_tet_assembly(bool fp32, const Mesh& m, const State& s, const KParams& kp,
+                        const double* tab, int nq, const TangentOut& o, int64_t first, int64_t count,
+                        const int32_t* elem_list, bool elem_outputs, bool atomic,
+                        unsigned int* flags, cudaStream_t st);
+// Tetrahedral residual: mode 0 per element into elemR (stride 36), mode 1 assembled into resid.
+int launch_tet_residual(const Mesh& m, const State& s, const KParams& kp, const double* tab, int nq,
+                        double* elemR, double* resid, int64_t first, int64_t count, int mode,
+                        unsigned int* flags, cudaStream_t st);
+
 // The three warps-per-block counts the tangent kernel is compiled for (k = 0, 1, 2; 1 = default).
 int tangent_warp_choice(bool fp32, int k);
 int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32,

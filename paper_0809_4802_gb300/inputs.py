@@ -436,7 +436,7 @@ def tet_mesh_from_lattice(hexm: Mesh) -> Mesh:
     vol = np.einsum("ei,ei->e", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))
     neg = vol < 0
     conn[neg] = conn[neg][:, [0, 2, 1, 3]]
-    m = Mesh(xyz=hexm.xyz.copy(), conn=conn.astype(np.int32), node_ijk=hexm.node_ijk,
+    m = Mesh(xyz=hexm.xyz.copy(), conn=np.ascontiguousarray(conn, dtype=np.int32), node_ijk=hexm.node_ijk,
              meta=dict(hexm.meta, element="tet"))
     m.name = hexm.name + "_tet"
     return m

@@ -50,7 +50,7 @@ EXPORTS = [
     "vms_mlp_create", "vms_mlp_destroy", "vms_mlp_last_error", "vms_mlp_set_stream",
     "vms_mlp_set_params", "vms_mlp_get_params", "vms_mlp_forward", "vms_mlp_grad", "vms_mlp_adam",
     "vms_node_features", "vms_node_increment", "vms_apply_increment", "vms_shift_time",
-    "vms_newton_solve_to", "vms_state_download_prev",
+    "vms_newton_solve_to", "vms_state_download_prev", "vms_mesh_upload_tet", "vms_tet_rule",
 ]
 MLP_IN, MLP_WIDTH, MLP_OUT, MLP_PARAMS = 12, 128, 4, 18692
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
@@ -139,6 +139,8 @@ def load_library(path: str = LIB_PATH):
         "vms_shift_time": (c_int, [p]),
         "vms_newton_solve_to": (c_int, [p, c_double, c_int, POINTER(c_int), p]),
         "vms_state_download_prev": (c_int, [p, p]),
+        "vms_mesh_upload_tet": (c_int, [p, c_int64, p, c_int64, p, c_int64, p, p]),
+        "vms_tet_rule": (c_int, [c_int, p, p]),
         "vms_solver_stats": (c_int, [p, c_int, POINTER(c_int64), POINTER(c_int64)]),
         "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
                                               POINTER(VmsParams), p, p, p]),
@@ -227,15 +229,20 @@ class Context:
         self._check(self.lib.vms_set_params(self.h, byref(p)))
 
     def mesh_upload(self, xyz, conn, dir_dofs, dir_vals):
+        """Upload a mesh: conn (n_elems, 8) hexahedra or (n_elems, 4) tetrahedra."""
         n_nodes = int(xyz.shape[0])
         n_elems = int(conn.shape[0])
+        npe = int(conn.shape[1])
+        if npe not in (4, 8):
+            raise ValueError("elements must have 4 or 8 nodes")
         n_dir = int(dir_dofs.shape[0]) if dir_dofs is not None else 0
-        self._check(self.lib.vms_mesh_upload(
+        fn = self.lib.vms_mesh_upload if npe == 8 else self.lib.vms_mesh_upload_tet
+        self._check(fn(
             self.h, n_nodes, _ptr(xyz, np.float64, 3 * n_nodes), n_elems,
-            _ptr(conn, np.int32, 8 * n_elems), n_dir,
+            _ptr(conn, np.int32, npe * n_elems), n_dir,
             _ptr(dir_dofs, np.int64, n_dir) if n_dir else None,
             _ptr(dir_vals, np.float64, n_dir) if n_dir else None))
-        self.n_nodes, self.n_elems = n_nodes, n_elems
+        self.n_nodes, self.n_elems, self.npe = n_nodes, n_elems, npe
 
     def state_upload(self, u, beta=None, u_prev=None):
         self._check(self.lib.vms_state_upload(
@@ -284,11 +291,12 @@ class Context:
         return (norm.value, R) if want_vector else norm.value
 
     def element_matrices(self, first, count, blocks=True):
-        out = {"S": np.empty((count, 32, 32)), "r": np.empty((count, 32))}
+        nc = 4 * getattr(self, "npe", 8)
+        out = {"S": np.empty((count, nc, nc)), "r": np.empty((count, nc))}
         if blocks:
-            out.update(Kcc=np.empty((count, 32, 32)), Kcf=np.empty((count, 32, 3)),
-                       Kfc=np.empty((count, 3, 32)), Kff=np.empty((count, 3, 3)),
-                       Rcp=np.empty((count, 32)), Rf=np.empty((count, 3)))
+            out.update(Kcc=np.empty((count, nc, nc)), Kcf=np.empty((count, nc, 3)),
+                       Kfc=np.empty((count, 3, nc)), Kff=np.empty((count, 3, 3)),
+                       Rcp=np.empty((count, nc)), Rf=np.empty((count, 3)))
         g = lambda k: out[k].ctypes.data if k in out else None  # noqa: E731
         self._check(self.lib.vms_element_matrices(self.h, first, count, g("S"), g("r"), g("Kcc"),
                                                   g("Kcf"), g("Kfc"), g("Kff"), g("Rcp"), g("Rf")))
@@ -452,6 +460,16 @@ class Mlp:
 
     def adam(self, lr: float):
         self._check(self.lib.vms_mlp_adam(self.h, ctypes.c_float(lr)))
+
+
+def tet_rule(n: int):
+    """The library's tetrahedral quadrature rule (host code): points (n^3, 3), weights (n^3)."""
+    pts = np.empty((n ** 3, 3))
+    wts = np.empty(n ** 3)
+    rc = load_library().vms_tet_rule(n, pts.ctypes.data, wts.ctypes.data)
+    if rc != OK:
+        raise VmsError(rc, "vms_tet_rule failed")
+    return pts, wts
 
 
 def version() -> str:

@@ -4,6 +4,7 @@ import os
 import re
 import ctypes
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -55,3 +56,17 @@ def test_bad_arguments_return_codes_without_a_device(lib):
 def test_library_is_built_for_sm_103a_only():
     from paper_0809_4802_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6])
+def test_library_tet_rule_matches_the_oracle(n):
+    """The library's conical-product rule (Gauss-Jacobi points by Golub-Welsch in C++) against the
+    oracle's (scipy's Gauss-Jacobi roots): same points and weights (host code, no GPU)."""
+    import oracle
+    from paper_0809_4802_gb300 import vms
+    pts, wts = vms.tet_rule(n)
+    opts, owts = oracle.tet_rule(n)
+    order = np.lexsort(pts.T[::-1])
+    oorder = np.lexsort(opts.T[::-1])
+    np.testing.assert_allclose(pts[order], opts[oorder], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(wts[order], owts[oorder], rtol=1e-13, atol=1e-17)
