@@ -37,10 +37,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Executed FP64 flops per element (FMA = 2, add/mul = 1) of each kernel as implemented, 27-point
 # rule, from ncu's per-opcode counts on the 32^3 cavity (sass__thread_inst_executed_true_per_opcode
 # divided by the 32,768 elements): residual 5,967 DFMA + 1,759 DMUL + 1,098 DADD; FP64 tangent
-# 51,034 DFMA + 15,673 DMUL + 11,956 DADD.
+# 51,034 DFMA + 15,673 DMUL + 11,956 DADD; tetrahedral kernel below.
 FP64_FLOPS_PER_ELEM = {
     "residual": 14_791,
     "tangent_fp64": 129_697,
+    # tetrahedral assembly kernel (one kernel: residual, tangent, condensation, scatter), 27-point
+    # conical rule: 19,408 DFMA + 18,972 DMUL + 3,900 DADD per element (ncu, 21^3 Kuhn cavity)
+    "tet": 61_688,
 }
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
@@ -65,6 +68,12 @@ WORKLOADS = {
     # serving-style mix: 64 jittered cavities, edges drawn from {8,12,16,24,32,48}, Re ~ U[100,1000],
     # random states, one merged mesh (1,677,504 elements) assembled per CUDA-graph launch, autotuned
     "batch64_mixed": dict(kind="batch", prec=1),
+    # tetrahedral P1 + bubble cavities sized like the paper's Table 1 meshes (fine DOF = 3 x
+    # elements): 39^3 Kuhn lattice, 355,914 elements (mesh E: 353,719); 21^3, 55,566 (mesh A:
+    # 55,763); jittered 0.15 h, Re 400, random state
+    "tetcavity39_re400_mixed": dict(kind="tet", n=39, re=400.0, jitter=0.15, state="random", seed=1002, prec=1),
+    "tetcavity39_re400_fp64": dict(kind="tet", n=39, re=400.0, jitter=0.15, state="random", seed=1002, prec=0),
+    "tetcavity21_re400_mixed": dict(kind="tet", n=21, re=400.0, jitter=0.15, state="random", seed=1002, prec=1),
     # transient runs with the learned warm start: a decaying vortex in a closed, jittered box
     # (--ws-n cells per edge), and the channel past a cube (--ws-nx, --ws-nyz; its systems carry
     # the nearly singular equal-order pressure modes of the hexahedral element, on which
@@ -88,6 +97,9 @@ def make_workload(name, with_batch=False):
         wl = inputs.bfs_workload(13, re=800.0, jitter_frac=0.1, seed=1003)
     elif kind == "channel":
         wl = inputs.channel_workload(300, 56, re=1000.0, dt=0.01, seed=1005)
+    elif kind == "tet":
+        wl = inputs.tet_cavity_workload(w["n"], re=w["re"], jitter_frac=w["jitter"], state=w["state"],
+                                        seed=w["seed"])
     elif kind == "warmstart" and w["flow"] == "channel":
         wl = inputs.channel_workload(WS_SIZE["nx"], WS_SIZE["nyz"], re=1000.0, dt=0.01, seed=1005)
     elif kind == "warmstart":
@@ -163,7 +175,7 @@ def oracle_assembly_rate(wl, target_s=10.0, max_elems=None):
     import oracle
     from oracle import Params
     mesh = wl.mesh
-    p = Params(nu=wl.nu, dt=wl.dt)
+    p = Params(nu=wl.nu, dt=wl.dt, element="tet" if mesh.conn.shape[1] == 4 else "hex")
     beta = wl.beta
 
     def run(n):
@@ -259,7 +271,12 @@ def newton_timing(vms, wl, prec, device, stream, rtol=1e-8, repeats=2, maxit=30)
     ctx.mesh_upload(wl.mesh.xyz, wl.mesh.conn, wl.bc.dofs, wl.bc.vals)
     ctx.set_params(wl.nu, dt=wl.dt)
     ctx.state_upload(wl.u, wl.beta, wl.u_prev)
-    ctx.newton_solve(rtol=rtol, maxit=maxit)
+    try:
+        ctx.newton_solve(rtol=rtol, maxit=maxit)
+    except vms.VmsError as e:
+        ctx.close()
+        return {"metric": NEWTON_METRIC.replace("1e-8", f"{rtol:g}"), "value": None, "unit": "s",
+                "precision": "mixed" if prec == 1 else "fp64", "failed": str(e)}
     times, its, hist, stats = [], 0, None, (0, 0)
     for _ in range(repeats):
         ctx.state_upload(wl.u, wl.beta, wl.u_prev)
@@ -409,16 +426,18 @@ def ours(args):
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     # the kernel on the FP64 critical path: the residual in mixed precision (the FP32 tangent runs
     # beside it on a second stream), the tangent in FP64 mode
-    dom = "residual" if prec == 1 else "tangent"
+    tet = mesh.conn.shape[1] == 4
+    dom = "tangent" if (tet or prec == 0) else "residual"
     dom_ms = kern[dom][0] / kern[dom][1]
-    key = "residual" if dom == "residual" else "tangent_fp64"
-    flops = FP64_FLOPS_PER_ELEM[key] * E
-    achieved = flops / (dom_ms / 1000.0) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+    key = "tet" if tet else ("residual" if dom == "residual" else "tangent_fp64")
+    fpe = FP64_FLOPS_PER_ELEM.get(key)
+    achieved = fpe * E / (dom_ms / 1000.0) / 1e12 if fpe else None
+    roofline = {"bound": "alu", "kernel": "tet_assembly" if tet else dom, "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
                 "traffic": NCU_TRAFFIC_BYTES.get((dom, args.workload)),
                 "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
-                "flops_per_element": FP64_FLOPS_PER_ELEM[key],
+                "flops_per_element": fpe,
                 "concurrent": "residual (stream 1) and tangent (stream 2) overlap; times are in situ",
                 "kernel_ms": {k: round(v[0] / v[1], 4) for k, v in kern.items()}}
 
@@ -445,17 +464,19 @@ def ours(args):
 
     # ---- wall time per Newton solve (same mesh and initial state; mixed and plain FP64) ----
     newton = None
-    if args.newton == "on" or (args.newton == "auto" and args.workload.startswith("cavity")):
+    if args.newton == "on" or (args.newton == "auto" and (args.workload.startswith("cavity")
+                                                          or args.workload.startswith("tetcavity"))):
         newton = newton_timing(vms, wl, prec, local, stream.cuda_stream)
         other = newton_timing(vms, wl, 1 - prec, local, stream.cuda_stream)
-        newton["other_precision"] = {k: other[k] for k in ("precision", "value", "newton_iterations",
-                                                           "krylov_iterations", "final_rel")}
+        newton["other_precision"] = {k: other.get(k) for k in ("precision", "value", "newton_iterations",
+                                                               "krylov_iterations", "final_rel", "failed")}
         small, _ = make_workload("cavity8_re100_fp64")
         newton["cavity8_re100_fp64_to_1e-10"] = {
             k: v for k, v in newton_timing(vms, small, 0, local, stream.cuda_stream, rtol=1e-10,
                                            repeats=3).items()
             if k in ("value", "unit", "newton_iterations", "krylov_iterations", "final_rel")}
-        newton["value"] = max_over_ranks(newton["value"])
+        if newton["value"] is not None:
+            newton["value"] = max_over_ranks(newton["value"])
 
     # ---- transient: learned warm start against the previous-step start ----
     warm = None
