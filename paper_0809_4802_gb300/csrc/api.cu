@@ -21,8 +21,7 @@ struct vms_ctx {
   QpRow* d_qp = nullptr;     // nq rows (residual kernel)
   double* d_tab64 = nullptr; // 37 nq (tangent kernel, FP64)
   float* d_tab32 = nullptr;  // 37 nq (tangent kernel, FP32)
-  double* d_tettab = nullptr; // TET_ROW nq_tet (tetrahedral kernel)
-  int nq_tet = 0;
+  vms::TetMoments tet_mom{};  // reference moments of the tetrahedral rule (kernel parameter)
   Mesh mesh;
   State state;
   Work work;
@@ -215,12 +214,7 @@ int upload_tables(vms_ctx* ctx) {
   CK(cudaMemcpy(ctx->d_tab64, t64.data(), sizeof(double) * 37 * nq, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_tab32, t32.data(), sizeof(float) * 37 * nq, cudaMemcpyHostToDevice));
   ctx->nq = nq;
-  std::vector<double> tt;
-  tet_table(n1, bs, tt);
-  dfree(ctx->d_tettab);
-  CK(cudaMalloc(&ctx->d_tettab, sizeof(double) * tt.size()));
-  CK(cudaMemcpy(ctx->d_tettab, tt.data(), sizeof(double) * tt.size(), cudaMemcpyHostToDevice));
-  ctx->nq_tet = (int)(tt.size() / TET_ROW);
+  tet_moments(n1, bs, ctx->tet_mom);
   return VMS_OK;
 }
 
@@ -299,7 +293,6 @@ int vms_destroy(vms_ctx* ctx) {
   for (auto& e : ctx->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_scalar);
-  dfree(ctx->d_tettab);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->work.aux) { cudaStreamSynchronize(ctx->work.aux); cudaStreamDestroy(ctx->work.aux); }
@@ -624,11 +617,11 @@ static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
       if (scatter == VMS_SCATTER_COLOUR) {
         for (int c = 0; c < m.n_colours; ++c) {
           const int64_t b = m.colour_start[c], n = m.colour_start[c + 1] - b;
-          k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, o, b, n,
+          k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->tet_mom, o, b, n,
                                     m.colour_order, false, false, w.flags, st));
         }
       } else {
-        k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, o, 0,
+        k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->tet_mom, o, 0,
                                   m.n_elems, nullptr, false, true, w.flags, st));
       }
     }
@@ -759,7 +752,7 @@ int vms_residual(vms_ctx* ctx, double* norm, double* R) {
   {
     KScope k(ctx, VMS_K_RESIDUAL);
     if (m.npe == 4)
-      k.add(launch_tet_residual(m, ctx->state, kparams(ctx), ctx->d_tettab, ctx->nq_tet, nullptr,
+      k.add(launch_tet_residual(m, ctx->state, kparams(ctx), ctx->tet_mom, nullptr,
                                 w.resid, 0, m.n_elems, 1, w.flags, st));
     else
       k.add(launch_residual(m, ctx->state, kparams(ctx), ctx->d_qp, nullptr, w.resid, 0, m.n_elems, 1,
@@ -785,7 +778,7 @@ static int element_matrices_tet(vms_ctx* ctx, int64_t first, int64_t count, doub
   const bool f32 = fp32_mode(ctx);
   {
     KScope k(ctx, VMS_K_RESIDUAL);
-    k.add(launch_tet_residual(m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, w.elemR, nullptr,
+    k.add(launch_tet_residual(m, ctx->state, kp, ctx->tet_mom, w.elemR, nullptr,
                               first, count, 0, w.flags, st));
   }
   double* buf = nullptr;
@@ -797,7 +790,7 @@ static int element_matrices_tet(vms_ctx* ctx, int64_t first, int64_t count, doub
   o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv; o.recY = w.recY;
   {
     KScope k(ctx, VMS_K_TANGENT);
-    k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->d_tettab, ctx->nq_tet, o, first, count,
+    k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->tet_mom, o, first, count,
                               nullptr, true, true, w.flags, st));
   }
   cudaError_t e = cudaGetLastError();

@@ -11,7 +11,9 @@
 // row only ever waits for rows claimed earlier, by warps that are already running. A row publishes
 // itself by writing its epoch into a flag with release semantics; dependants poll the flag with
 // acquire loads (bounded: after ILU_SPIN_LIMIT polls the kernel records a timeout and returns),
-// and read data published in the same launch through L2 (ld.global.cg), never through L1.
+// and read data published in the same launch through L2 (ld.global.cg), never through L1. The
+// triangular sweeps take rows in chunks per CTA, so that most dependencies (the previous rows of
+// the same chunk) are resolved through shared memory instead of L2.
 #include <algorithm>
 #include <vector>
 
@@ -24,8 +26,8 @@ namespace {
 
 constexpr uint32_t ILU_SPIN_LIMIT = 1u << 22;
 constexpr int ILU_FWARPS = 4;    // warps per CTA of the factorisation
-constexpr int ILU_SWARPS = 8;    // warps per CTA of the sweeps
-constexpr unsigned ILU_SWEEP_CTAS = 152 * 2;  // sweep CTAs: 16 warps per SM claim rows in turn
+constexpr int ILU_SWARPS = 16;   // warps per CTA of the sweeps (one segment each)
+constexpr unsigned ILU_SWEEP_CTAS = 152 * 2;  // at most two sweep CTAs per SM
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
@@ -265,83 +267,195 @@ __device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
 }
 
-// Sum of the four per-lane partials over the warp; every lane receives all four sums.
+// Sum of the four per-lane partials over the warp, reduce-scatter style (7 shuffles): on return
+// lane L holds the full sum of component (L >> 3) & 3.
 template <typename T>
-__device__ __forceinline__ void warp_sum4(T a[4]) {
-  for (int o = 16; o > 0; o >>= 1)
-    for (int q = 0; q < 4; ++q) a[q] += __shfl_xor_sync(FULL, a[q], o);
+__device__ __forceinline__ T warp_sum4_scatter(const T a[4], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const T s0 = h16 ? a[0] : a[2], s1 = h16 ? a[1] : a[3];
+  const T b0 = (h16 ? a[2] : a[0]) + __shfl_xor_sync(FULL, s0, 16);
+  const T b1 = (h16 ? a[3] : a[1]) + __shfl_xor_sync(FULL, s1, 16);
+  T c = (h8 ? b1 : b0) + __shfl_xor_sync(FULL, h8 ? b0 : b1, 8);
+  c += __shfl_xor_sync(FULL, c, 4);
+  c += __shfl_xor_sync(FULL, c, 2);
+  c += __shfl_xor_sync(FULL, c, 1);
+  return c;
+}
+
+// Wait for a row of the CTA's own chunk (shared-memory flag), bounded like the global waits.
+__device__ __forceinline__ bool wait_shared(const volatile uint32_t* f, int* err) {
+  for (uint32_t it = 0; it <= ILU_SPIN_LIMIT; ++it) {
+    if (*f) {
+      __threadfence_block();
+      return true;
+    }
+    if (it >= 32) __nanosleep(8);
+    if ((it & 1023u) == 1023u && *(volatile int*)err != 0) return false;
+  }
+  atomicCAS(err, 0, ILU_ERR_TIMEOUT);
+  return false;
+}
+
+// One row of a sweep with everything that does not depend on other rows: its neighbour block
+// (one per lane), the factor blocks, the right-hand side and, for U, the row of U_ii^-1.
+template <typename T>
+struct SweepRow {
+  int64_t k;     // the lane's neighbour node
+  bool mine;     // the lane has a neighbour block on the sweep's side of the diagonal
+  V4<T> f[4];
+  T rhs;
+  T drow[4];
+};
+
+template <typename T, bool LOWER>
+__device__ __forceinline__ void load_row(SweepRow<T>& R, int64_t i, int lane, int q, bool writer,
+                                         const int32_t* __restrict__ rowptr,
+                                         const int32_t* __restrict__ colidx, const T* __restrict__ F,
+                                         const T* __restrict__ Dinv, const int32_t* __restrict__ dpos,
+                                         const T* __restrict__ v, const unsigned long long* __restrict__ vp,
+                                         int64_t n0) {
+  int32_t rp[4];
+  for (int m = 0; m < 4; ++m) rp[m] = rowptr[4 * i + m];
+  const int deg = (rowptr[4 * i + 1] - rp[0]) >> 2;
+  const int dp = dpos[i];
+  const int kk = LOWER ? lane : dp + 1 + lane;
+  R.mine = LOWER ? kk < dp : kk < deg;
+  R.k = 0;
+  if (R.mine) {
+    R.k = colidx[rp[0] + 4 * kk] >> 2;
+    for (int m = 0; m < 4; ++m) R.f[m] = V4<T>::ldg(F + rp[m] + 4 * kk);
+  }
+  R.rhs = T(0);
+  for (int m = 0; m < 4; ++m) R.drow[m] = T(0);
+  if (writer) {
+    if constexpr (LOWER) {
+      R.rhs = v[4 * (i - n0) + q];
+    } else if constexpr (sizeof(T) == 4) {
+      R.rhs = __uint_as_float((uint32_t)vp[4 * i + q]);
+    } else {
+      R.rhs = v[4 * i + q];
+    }
+    if constexpr (!LOWER) {
+      const V4<T> d = V4<T>::ldg(Dinv + 16 * i + 4 * q);
+      for (int m = 0; m < 4; ++m) R.drow[m] = d.v[m];
+    }
+  }
 }
 
 // T: element type of the factor (float: packed publication, double: sentinel publication).
 // Rows [n0, n0 + n_rows); `v` (forward sweep) and `out` are compact (index i - n0), the
 // publication buffer `pub`, the FP64 backward-sweep input `v` and the FP32 one `vp` are indexed by
 // node over the whole mesh.
+//
+// The rows are cut into segments (seg[s] .. seg[s+1]): maximal runs of consecutive nodes in which
+// every node is coupled to the one before it (a grid line in a lattice numbering), at most
+// ILU_SEG_MAX long. A CTA claims the next chunk of ILU_SWARPS segments in sweep order from the
+// global counter and each of its warps takes one segment and does its rows in order, loading the
+// next row while the current one waits. A row's dependency in the same chunk is read from shared
+// memory once its flag is set (no L2 round trip; in the warp's own segment it is already there);
+// a dependency in an earlier chunk is read from the L2 publication. Chunks are claimed in order by
+// running CTAs, so every wait is for work that is already in progress.
 template <typename T, bool LOWER>
 __global__ void __launch_bounds__(ILU_SWARPS * 32)
     ilu_sweep_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                      const T* __restrict__ F, const T* __restrict__ Dinv,
-                     const int32_t* __restrict__ dpos, const T* __restrict__ v,
+                     const int32_t* __restrict__ dpos, const int32_t* __restrict__ seg, int64_t s0,
+                     int64_t n_segs, const T* __restrict__ v,
                      const unsigned long long* __restrict__ vp, void* pub, T* __restrict__ out,
                      int64_t n0, int64_t n_rows, uint32_t ep, unsigned long long* ticket,
                      unsigned long long base, int* err) {
-  const int lane = threadIdx.x & 31;
+  constexpr int SLOTS = ILU_SWARPS * ILU_SEG_MAX;
+  __shared__ __align__(16) T sx[SLOTS * 4];
+  __shared__ uint32_t sready[SLOTS];
+  __shared__ int64_t s_chunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q = (lane >> 3) & 3;          // the component this lane's reduction ends with
+  const bool writer = (lane & 7) == 0;    // lanes 0, 8, 16, 24 finish components 0..3
+  const int64_t n1 = n0 + n_rows;
+  const int64_t n_chunks = (n_segs + ILU_SWARPS - 1) / ILU_SWARPS;
   for (;;) {
-    const int64_t t = claim_row(ticket, base, n_rows, err, lane);
-    if (t >= n_rows) return;
-    const int64_t i = LOWER ? n0 + t : n0 + n_rows - 1 - t;
-    int32_t rp[4];
-    for (int q = 0; q < 4; ++q) rp[q] = rowptr[4 * i + q];
-    const int deg = (rowptr[4 * i + 1] - rp[0]) >> 2;
-    const int dp = dpos[i];
-    const int kk = LOWER ? lane : dp + 1 + lane;
-    const bool mine = LOWER ? kk < dp : kk < deg;
-    // independent of any other row: the right-hand side and, for U, the row of U_ii^-1
-    T rhs = T(0), drow[4] = {T(0), T(0), T(0), T(0)};
-    if (lane < 4) {
-      if constexpr (LOWER) {
-        rhs = v[4 * (i - n0) + lane];
-      } else if constexpr (sizeof(T) == 4) {
-        rhs = __uint_as_float((uint32_t)vp[4 * i + lane]);
-      } else {
-        rhs = v[4 * i + lane];
+    if (threadIdx.x == 0) {
+      int64_t c = n_chunks;
+      if (*(volatile int*)err == 0) {
+        const unsigned long long t = atomicAdd(ticket, 1ull);
+        if (t < base) atomicCAS(err, 0, ILU_ERR_TIMEOUT);  // the counter was disturbed
+        else if (t - base < (unsigned long long)n_chunks) c = (int64_t)(t - base);
       }
-      if constexpr (!LOWER) {
-        const V4<T> d = V4<T>::ldg(Dinv + 16 * i + 4 * lane);
-        for (int m = 0; m < 4; ++m) drow[m] = d.v[m];
+      s_chunk = c;
+    }
+    for (int l = threadIdx.x; l < SLOTS; l += blockDim.x) sready[l] = 0u;
+    __syncthreads();
+    const int64_t c = s_chunk;
+    if (c >= n_chunks) return;
+    // segments jlo .. jhi - 1 in sweep order; their nodes form the range [a, b)
+    const int64_t jlo = c * ILU_SWARPS;
+    const int64_t jhi = jlo + ILU_SWARPS < n_segs ? jlo + ILU_SWARPS : n_segs;
+    int64_t a = LOWER ? seg[s0 + jlo] : seg[s0 + n_segs - jhi];
+    int64_t b = LOWER ? seg[s0 + jhi] : seg[s0 + n_segs - jlo];
+    a = a > n0 ? a : n0;
+    b = b < n1 ? b : n1;
+    const int64_t j = jlo + warp;
+    if (j < jhi) {
+      const int64_t s = LOWER ? s0 + j : s0 + n_segs - 1 - j;
+      int64_t r_lo = seg[s], r_hi = seg[s + 1];
+      r_lo = r_lo > n0 ? r_lo : n0;
+      r_hi = r_hi < n1 ? r_hi : n1;
+      const int len = (int)(r_hi - r_lo);
+      SweepRow<T> nxt;
+      if (len > 0)
+        load_row<T, LOWER>(nxt, LOWER ? r_lo : r_hi - 1, lane, q, writer, rowptr, colidx, F, Dinv,
+                           dpos, v, vp, n0);
+      for (int r = 0; r < len; ++r) {
+        const int64_t i = LOWER ? r_lo + r : r_hi - 1 - r;
+        const SweepRow<T> cur = nxt;
+        if (r + 1 < len)
+          load_row<T, LOWER>(nxt, LOWER ? i + 1 : i - 1, lane, q, writer, rowptr, colidx, F, Dinv,
+                             dpos, v, vp, n0);
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        bool ok = true;
+        if (cur.mine) {
+          const int64_t k = cur.k;
+          T xk[4];
+          if (k >= a && k < b) {  // a row of this chunk: shared memory
+            const int64_t sk = LOWER ? k - a : b - 1 - k;
+            ok = wait_shared(sready + sk, err);
+            if (ok)
+              for (int m = 0; m < 4; ++m) xk[m] = sx[4 * sk + m];
+          } else if constexpr (sizeof(T) == 4) {
+            ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err);
+          } else {
+            ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err);
+          }
+          if (ok)
+            for (int rr = 0; rr < 4; ++rr)
+              for (int m = 0; m < 4; ++m) acc[rr] += cur.f[rr].v[m] * xk[m];
+        }
+        if (!__all_sync(FULL, ok)) break;  // an error was recorded; the CTA stops after this chunk
+        const T sum = warp_sum4_scatter(acc, lane);
+        const T w = writer ? cur.rhs - sum : T(0);
+        T res = w;
+        if constexpr (!LOWER) {
+          T wq[4];
+          for (int m = 0; m < 4; ++m) wq[m] = __shfl_sync(FULL, w, 8 * m);
+          res = cur.drow[0] * wq[0] + cur.drow[1] * wq[1] + cur.drow[2] * wq[2] + cur.drow[3] * wq[3];
+        }
+        const int64_t si = LOWER ? i - a : b - 1 - i;
+        if (writer) {
+          sx[4 * si + q] = res;
+          if constexpr (sizeof(T) == 4)
+            st_packed(reinterpret_cast<unsigned long long*>(pub) + 4 * i + q, res, ep);
+          else
+            st_relaxed_f64(reinterpret_cast<double*>(pub) + 4 * i + q, res);
+          if (out) out[4 * (i - n0) + q] = res;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          *(volatile uint32_t*)(sready + si) = 1u;
+        }
       }
     }
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    bool ok = true;
-    if (mine) {
-      const int64_t k = colidx[rp[0] + 4 * kk] >> 2;
-      V4<T> f[4];
-      for (int q = 0; q < 4; ++q) f[q] = V4<T>::ldg(F + rp[q] + 4 * kk);
-      T xk[4];
-      if constexpr (sizeof(T) == 4)
-        ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err);
-      else
-        ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err);
-      if (ok)
-        for (int q = 0; q < 4; ++q)
-          for (int m = 0; m < 4; ++m) acc[q] += f[q].v[m] * xk[m];
-    }
-    if (!__all_sync(FULL, ok)) return;
-    warp_sum4(acc);
-    if (lane < 4) {
-      T w = rhs - acc[0];
-      for (int q = 1; q < 4; ++q) w = lane == q ? rhs - acc[q] : w;
-      T res = w;
-      if constexpr (!LOWER) {
-        T wq[4];
-        for (int m = 0; m < 4; ++m) wq[m] = __shfl_sync(0xfu, w, m);
-        res = drow[0] * wq[0] + drow[1] * wq[1] + drow[2] * wq[2] + drow[3] * wq[3];
-      }
-      if constexpr (sizeof(T) == 4)
-        st_packed(reinterpret_cast<unsigned long long*>(pub) + 4 * i + lane, res, ep);
-      else
-        st_relaxed_f64(reinterpret_cast<double*>(pub) + 4 * i + lane, res);
-      if (out) out[4 * (i - n0) + lane] = res;
-    }
+    __syncthreads();
   }
 }
 
@@ -406,10 +520,29 @@ int build_pattern(vms_ctx* ctx, Ilu& p, const Mesh& m) {
   }
   if (pairs.size() >= (size_t)INT32_MAX)
     return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "ILU(0): too many update pairs");
+  // sweep segments: node i continues the segment of i - 1 when the two are coupled (adjacency
+  // lists are sorted, so i - 1 is the entry just before the diagonal)
+  std::vector<int32_t> seg;
+  seg.reserve((size_t)N / 8 + 2);
+  int run = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const bool coupled = i > 0 && dpos[i] > 0 && adj[start[i] + dpos[i] - 1] == i - 1;
+    if (coupled && run < ILU_SEG_MAX) {
+      ++run;
+    } else {
+      seg.push_back((int32_t)i);
+      run = 1;
+    }
+  }
+  seg.push_back((int32_t)N);
   p.n_nodes = N;
   p.n_lower = lptr[N];
   p.n_pairs = (int64_t)pairs.size();
+  p.n_segs = (int64_t)seg.size() - 1;
   e = cudaMalloc(&p.dpos, sizeof(int32_t) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&p.seg, sizeof(int32_t) * seg.size());
+  if (e == cudaSuccess) e = cudaMemcpy(p.seg, seg.data(), sizeof(int32_t) * seg.size(), cudaMemcpyHostToDevice);
+  p.seg_host = std::move(seg);
   if (e == cudaSuccess) e = cudaMalloc(&p.lptr, sizeof(int32_t) * (N + 1));
   if (e == cudaSuccess) e = cudaMalloc(&p.pptr, sizeof(int32_t) * pptr.size());
   if (e == cudaSuccess) e = cudaMalloc(&p.pairs, sizeof(uint16_t) * std::max<size_t>(1, pairs.size()));
@@ -475,7 +608,7 @@ int convert(const A* x, B* y, int64_t n, cudaStream_t st) {
 
 void free_ilu(Ilu& p) {
   void* bufs[] = {p.dpos, p.lptr, p.pptr, p.pairs, p.F, p.Dinv, p.y, p.x64, p.F32, p.Dinv32,
-                  p.vals64, p.flags, p.yp, p.xp, p.tickets, p.err};
+                  p.vals64, p.flags, p.yp, p.xp, p.tickets, p.err, p.seg};
   for (void* b : bufs)
     if (b) cudaFree(b);
   p = Ilu();
@@ -513,21 +646,34 @@ int ilu_factor(vms_ctx* ctx, Ilu& p, const Mesh& m, bool fp32, const void* value
   return e == cudaSuccess ? VMS_OK : ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
 }
 
+// Segments covering nodes [n0, n1): [s0, s0 + count). Rows outside [n0, n1) are clamped away in
+// the kernel (a block solve has no couplings outside its rows, so n0 and n1 are segment starts).
+static void segment_range(const Ilu& p, int64_t n0, int64_t n1, int64_t& s0, int64_t& count) {
+  const std::vector<int32_t>& sg = p.seg_host;
+  const int64_t a = (int64_t)(std::upper_bound(sg.begin(), sg.end() - 1, (int32_t)n0) - sg.begin()) - 1;
+  const int64_t b = (int64_t)(std::lower_bound(sg.begin(), sg.end() - 1, (int32_t)n1) - sg.begin());
+  s0 = a < 0 ? 0 : a;
+  count = b - s0;
+}
+
 template <>
 int ilu_apply<float, float>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const float* v, float* z,
                             cudaStream_t st) {
   const int64_t rows = n1 - n0;
-  const unsigned ctas = resident_ctas(rows, ILU_SWARPS, ILU_SWEEP_CTAS);
-  const unsigned long long claims = (unsigned long long)rows + (unsigned long long)ctas * ILU_SWARPS;
+  int64_t s0 = 0, ns = 0;
+  segment_range(p, n0, n1, s0, ns);
+  const int64_t chunks = (ns + ILU_SWARPS - 1) / ILU_SWARPS;
+  const unsigned ctas = resident_ctas(chunks, 1, ILU_SWEEP_CTAS);
+  const unsigned long long claims = (unsigned long long)chunks + ctas;  // + each CTA's last claim
   uint32_t ep = next_epoch(p, st);
   ilu_sweep_kernel<float, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, p.F32, nullptr, p.dpos, v, nullptr, p.yp, nullptr, n0, rows,
-      ep, p.tickets, p.base, p.err);
+      m.rowptr, m.colidx, p.F32, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, p.yp, nullptr, n0,
+      rows, ep, p.tickets, p.base, p.err);
   p.base += claims;
   ep = next_epoch(p, st);
   ilu_sweep_kernel<float, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, p.F32, p.Dinv32, p.dpos, nullptr, p.yp, p.xp, z,
-      n0, rows, ep, p.tickets, p.base, p.err);
+      m.rowptr, m.colidx, p.F32, p.Dinv32, p.dpos, p.seg, s0, ns, nullptr, p.yp, p.xp, z, n0,
+      rows, ep, p.tickets, p.base, p.err);
   p.base += claims;
   return 2;
 }
@@ -536,19 +682,22 @@ template <>
 int ilu_apply<double, double>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const double* v,
                               double* z, cudaStream_t st) {
   const int64_t rows = n1 - n0;
-  const unsigned ctas = resident_ctas(rows, ILU_SWARPS, ILU_SWEEP_CTAS);
-  const unsigned long long claims = (unsigned long long)rows + (unsigned long long)ctas * ILU_SWARPS;
+  int64_t s0 = 0, ns = 0;
+  segment_range(p, n0, n1, s0, ns);
+  const int64_t chunks = (ns + ILU_SWARPS - 1) / ILU_SWARPS;
+  const unsigned ctas = resident_ctas(chunks, 1, ILU_SWEEP_CTAS);
+  const unsigned long long claims = (unsigned long long)chunks + ctas;  // + each CTA's last claim
   double* y = p.y;
   double* x = p.x64;
   cudaMemsetAsync(y + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
   ilu_sweep_kernel<double, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, p.F, nullptr, p.dpos, v, nullptr, y, nullptr, n0, rows, 0,
+      m.rowptr, m.colidx, p.F, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, y, nullptr, n0, rows, 0,
       p.tickets, p.base, p.err);
   p.base += claims;
   cudaMemsetAsync(x + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
   ilu_sweep_kernel<double, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
-      m.rowptr, m.colidx, p.F, p.Dinv, p.dpos, y, nullptr, x, z, n0,
-      rows, 0, p.tickets, p.base, p.err);
+      m.rowptr, m.colidx, p.F, p.Dinv, p.dpos, p.seg, s0, ns, y, nullptr, x, z, n0, rows, 0,
+      p.tickets, p.base, p.err);
   p.base += claims;
   return 4;
 }

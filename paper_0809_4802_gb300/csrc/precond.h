@@ -16,6 +16,11 @@ struct Ilu {
   int32_t* pptr = nullptr;     // n_lower + 1: first update pair of each lower block
   uint16_t* pairs = nullptr;   // n_pairs: (jj | jk << 8) for A_ij -= L_ik U_kj
   int64_t n_nodes = 0, n_lower = 0, n_pairs = 0;
+  // sweep segments: maximal runs of consecutive nodes each coupled to the one before (at most
+  // ILU_SEG_MAX long); segment s is nodes seg[s] .. seg[s+1] - 1
+  int32_t* seg = nullptr;           // device, n_segs + 1
+  std::vector<int32_t> seg_host;    // host copy (segment ranges of node blocks)
+  int64_t n_segs = 0;
   // factor (always eliminated in FP64) and sweep work
   double* F = nullptr;         // nnz: L (unit lower, strictly lower blocks) and U, CSR layout
   double* Dinv = nullptr;      // n_nodes * 16: inverses of the diagonal blocks of U
@@ -37,6 +42,7 @@ struct Ilu {
 constexpr int ILU_ERR_TIMEOUT = 1;
 constexpr int ILU_ERR_PIVOT = 2;
 constexpr int ILU_MAX_DEG = 32;
+constexpr int ILU_SEG_MAX = 64;
 
 void free_ilu(Ilu& p);
 

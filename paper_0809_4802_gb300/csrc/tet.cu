@@ -5,11 +5,12 @@
 // Reference tetrahedron (0,0,0), (1,0,0), (0,1,0), (0,0,1); N_a = lambda_a with lambda = (1 - xi -
 // eta - zeta, xi, eta, zeta); bubble b = 256 lambda_0 lambda_1 lambda_2 lambda_3. The geometry is
 // affine, so det J and the P1 gradients g_a are constant on the element; only the bubble gradient
-// and the fields vary between quadrature points.
+// and the fields vary between quadrature points, as reference polynomials. Each integral is
+// therefore a combination of reference moments of the quadrature rule (computed once per rule on
+// the host) with element constants: the quadrature sums, regrouped.
 //
-// One warp per element, FP64 arithmetic in both precision modes (the values are stored in the
-// mode's type): lanes take quadrature points and write their point records to shared memory, then
-// lanes take matrix entries and sum them over the points, then the warp condenses and scatters.
+// FP64 arithmetic in both precision modes (the values are stored in the mode's type); four lanes
+// per element, no shared memory.
 #include <cmath>
 #include <vector>
 
@@ -99,19 +100,20 @@ void tet_rule(int n, std::vector<double>& pts, std::vector<double>& wts) {
       }
 }
 
-// Table row per point: lambda_0..3, b, db/dxi_0..2, weight.
-void tet_table(int n, double bubble_scale, std::vector<double>& tab) {
+// Reference moments of the rule with n points per direction (layout of TetMoments): the sums of
+// w_q times products of lambda_a, b = 256 s lambda_0 lambda_1 lambda_2 lambda_3 (s the bubble
+// scale) and db/dxi at the rule's points.
+void tet_moments(int n, double bubble_scale, TetMoments& mom) {
   std::vector<double> pts, wts;
   tet_rule(n, pts, wts);
-  const int nq = (int)wts.size();
-  tab.assign((size_t)TET_ROW * nq, 0.0);
+  double* M = mom.m;
+  for (int i = 0; i < TM_COUNT; ++i) M[i] = 0.0;
   static const double dl[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-  for (int q = 0; q < nq; ++q) {
+  for (size_t q = 0; q < wts.size(); ++q) {
     const double xi = pts[3 * q], eta = pts[3 * q + 1], zeta = pts[3 * q + 2];
     const double lam[4] = {1.0 - xi - eta - zeta, xi, eta, zeta};
-    double* r = tab.data() + (size_t)TET_ROW * q;
-    for (int a = 0; a < 4; ++a) r[a] = lam[a];
-    r[4] = bubble_scale * 256.0 * lam[0] * lam[1] * lam[2] * lam[3];
+    const double b = bubble_scale * 256.0 * lam[0] * lam[1] * lam[2] * lam[3];
+    double db[3];
     for (int al = 0; al < 3; ++al) {
       double s = 0.0;
       for (int a = 0; a < 4; ++a) {
@@ -120,263 +122,251 @@ void tet_table(int n, double bubble_scale, std::vector<double>& tab) {
           if (c != a) prod *= lam[c];
         s += prod * dl[a][al];
       }
-      r[5 + al] = bubble_scale * 256.0 * s;
+      db[al] = bubble_scale * 256.0 * s;
     }
-    r[8] = wts[q];
+    const double w = wts[q];
+    M[TM_M0] += w;
+    M[TM_MB] += w * b;
+    M[TM_MBB] += w * b * b;
+    for (int al = 0; al < 3; ++al) {
+      M[TM_MD + al] += w * db[al];
+      M[TM_MBBD + al] += w * b * b * db[al];
+      for (int be = 0; be < 3; ++be) M[TM_MDD + 3 * al + be] += w * db[al] * db[be];
+    }
+    for (int a = 0; a < 4; ++a) {
+      M[TM_M1 + a] += w * lam[a];
+      M[TM_M1B + a] += w * lam[a] * b;
+      for (int al = 0; al < 3; ++al) {
+        M[TM_M1D + 3 * a + al] += w * lam[a] * db[al];
+        M[TM_M1BD + 3 * a + al] += w * lam[a] * b * db[al];
+      }
+      for (int c = 0; c < 4; ++c) {
+        M[TM_M2 + 4 * a + c] += w * lam[a] * lam[c];
+        for (int al = 0; al < 3; ++al)
+          M[TM_M2D + 12 * a + 3 * c + al] += w * lam[a] * lam[c] * db[al];
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
 // device
+//
+// Four lanes per tetrahedron, eight tetrahedra per warp: lane a of a group owns node a (the rows
+// 4a..4a+3 of R_cp, K_cc, K_cf and S_e) and the column block a of K_fc. With v = sum_c lambda_c V_c
+// + b beta, L = G + beta (x) d (G the constant coarse gradient, d = grad b = J^-T db/dxi) and
+// p = sum_c lambda_c P_c, each term of Section 4.1 and Eq. NewtonUpdate2 integrates to element
+// constants times reference moments, e.g. int lambda_a lambda_b L_ik = det (G_ik M2[a][b] +
+// beta_i sum_al M2d[a][b][al] Jinv[al][k]). Every value is formed in FP64; no lane loops over
+// quadrature points.
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-constexpr int TET_WARPS = 2;
-constexpr int QREC = 36;  // doubles per point record
+constexpr int TET_WARPS = 2;     // warps per block
+constexpr int TET_PER_WARP = 8;  // tetrahedra per warp
 
-// point record layout
-constexpr int Q_LAM = 0, Q_B = 4, Q_D = 5, Q_V = 8, Q_L = 11, Q_P = 20, Q_CONV = 21, Q_DV = 24,
-              Q_OM = 27, Q_CD = 28, Q_DD = 29, Q_TRL = 30, Q_CB = 31;  // c_b = v . g_b (4)
-
-struct TetWarp {
-  double X[4][3];
-  double V[4][3];
-  double P[4];
-  double Vp[4][3];
-  double beta[3];
+// What every lane of an element's group holds (a = the lane's node).
+struct TetElem {
   int nd[4];
-  double g[4][3];   // P1 gradients (constant)
-  double vol;       // sum of the point weights times det J
-  double Kcc[16][16];
-  double Kcf[16][3];
-  double Kfc[3][16];
-  double Kff[9];
-  double Rcp[16];
-  double Rf[3];
-  double cof[9];
-  double Kinv[9];
-  double Xs[3][16];
-  unsigned int flag;
+  int nda;           // node a
+  bool ok;           // det J > 0
+  double det;
+  double Ji[3][3];   // J^-1: Ji[al][j] = d xi_al / d x_j
+  double g[4][3];    // P1 gradients g_c = grad lambda_c
+  double G[3][3];    // coarse velocity gradient G[i][j] = sum_c V_c[i] g_c[j]
+  double beta[3];
+  double Ua[3];      // int lambda_a v       (all integrals divided by det)
+  double Ub[3];      // int b v
+  double Aa;         // int lambda_a v.d
+  double Ab;         // int b v.d
+  double Bd;         // int lambda_a beta.d
+  double Dint[3];    // int d
+  double DD;         // int d.d
+  double Pbar;       // int p
+  double PdJ[3];     // int p d
+  double dVa[3];     // int lambda_a (v - v_prev)
+  double dVb[3];     // int b (v - v_prev)
+  double ga[3];      // g_a
+  // the moment rows of node a (selected without dynamic indexing)
+  double m1a, m1ba, m2a[4], m1da[3], m1bda[3], m2da[12];
 };
 
-__host__ __device__ size_t tet_warp_bytes(int nq) {
-  return ((sizeof(TetWarp) + 15) & ~size_t(15)) + sizeof(double) * QREC * nq;
+__device__ __forceinline__ double sel4(int a, double x0, double x1, double x2, double x3) {
+  return a == 0 ? x0 : a == 1 ? x1 : a == 2 ? x2 : x3;
 }
 
-template <typename T>
-__device__ __forceinline__ void add_row(T* p, const double v[4], bool atomic) {
+// Gather the element (every lane loads all four nodes; the group's lanes hit the same lines) and
+// form the element constants and the integrals the residual and the tangent share.
+__device__ __forceinline__ void tet_element(int a, int64_t e, const double4_32a* __restrict__ xyz,
+                                            const double4_32a* __restrict__ u,
+                                            const double4_32a* __restrict__ up,
+                                            const int32_t* __restrict__ conn,
+                                            const double* __restrict__ beta, bool transient,
+                                            const double* __restrict__ M, TetElem& E) {
+  double X[4][3], V[4][3], P[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (v[k] == 0.0) continue;
-    if (atomic) atomicAdd(p + k, T(v[k])); else p[k] += T(v[k]);
-  }
-}
-
-// Phase A: gather, geometry (every lane, same values), point records (lanes = points).
-__device__ bool tet_points(int lane, int64_t e, int nq, const double4_32a* __restrict__ xyz,
-                           const double4_32a* __restrict__ u, const double4_32a* __restrict__ up,
-                           const int32_t* __restrict__ conn, const double* __restrict__ beta,
-                           const double* __restrict__ tab, double tau, bool transient,
-                           TetWarp& W, double* __restrict__ rec) {
-  if (lane < 4) {
-    const int nd = conn[4 * e + lane];
-    W.nd[lane] = nd;
+  for (int c = 0; c < 4; ++c) {
+    const int nd = conn[4 * e + c];
+    E.nd[c] = nd;
     const double4_32a x = xyz[nd], w = u[nd];
-    W.X[lane][0] = x.x; W.X[lane][1] = x.y; W.X[lane][2] = x.z;
-    W.V[lane][0] = w.x; W.V[lane][1] = w.y; W.V[lane][2] = w.z; W.P[lane] = w.w;
-    if (transient) {
-      const double4_32a o = up[nd];
-      W.Vp[lane][0] = o.x; W.Vp[lane][1] = o.y; W.Vp[lane][2] = o.z;
-    } else {
-      W.Vp[lane][0] = W.Vp[lane][1] = W.Vp[lane][2] = 0.0;
-    }
-  } else if (lane < 7) {
-    W.beta[lane - 4] = beta[3 * e + lane - 4];
-  } else if (lane == 7) {
-    W.flag = 0u;
+    X[c][0] = x.x; X[c][1] = x.y; X[c][2] = x.z;
+    V[c][0] = w.x; V[c][1] = w.y; V[c][2] = w.z; P[c] = w.w;
   }
-  __syncwarp();
-  // J[i][al] = x_{al+1,i} - x_{0,i}; cof; g_a[j] = sum_al dlambda_a[al] (J^-1)[al][j]
+#pragma unroll
+  for (int i = 0; i < 3; ++i) E.beta[i] = beta[3 * e + i];
+  E.nda = a == 0 ? E.nd[0] : a == 1 ? E.nd[1] : a == 2 ? E.nd[2] : E.nd[3];
+  E.m1a = sel4(a, M[TM_M1], M[TM_M1 + 1], M[TM_M1 + 2], M[TM_M1 + 3]);
+  E.m1ba = sel4(a, M[TM_M1B], M[TM_M1B + 1], M[TM_M1B + 2], M[TM_M1B + 3]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) E.m2a[c] = sel4(a, M[TM_M2 + c], M[TM_M2 + 4 + c], M[TM_M2 + 8 + c], M[TM_M2 + 12 + c]);
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    E.m1da[al] = sel4(a, M[TM_M1D + al], M[TM_M1D + 3 + al], M[TM_M1D + 6 + al], M[TM_M1D + 9 + al]);
+    E.m1bda[al] = sel4(a, M[TM_M1BD + al], M[TM_M1BD + 3 + al], M[TM_M1BD + 6 + al], M[TM_M1BD + 9 + al]);
+  }
+#pragma unroll
+  for (int l = 0; l < 12; ++l)
+    E.m2da[l] = sel4(a, M[TM_M2D + l], M[TM_M2D + 12 + l], M[TM_M2D + 24 + l], M[TM_M2D + 36 + l]);
+  // J[i][al] = x_{al+1,i} - x_{0,i}; Jinv[al][j] = cof[j][al] / det
   double J[3][3], cof[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int al = 0; al < 3; ++al) J[i][al] = W.X[al + 1][i] - W.X[0][i];
+    for (int al = 0; al < 3; ++al) J[i][al] = X[al + 1][i] - X[0][i];
   double det = cofactor3(J, cof);
-  const bool ok = det > 0.0;
-  if (!ok) det = 1.0;
+  E.ok = det > 0.0;
+  if (!E.ok) det = 1.0;
+  E.det = det;
   const double r = 1.0 / det;
-  double g[4][3];
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) E.Ji[al][j] = cof[j][al] * r;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    // (J^-1)[al][j] = cof[j][al] / det; dlambda_0 = -(1,1,1), dlambda_{a} = e_{a-1}
-    g[1][j] = cof[j][0] * r;
-    g[2][j] = cof[j][1] * r;
-    g[3][j] = cof[j][2] * r;
-    g[0][j] = -(g[1][j] + g[2][j] + g[3][j]);
+    E.g[1][j] = E.Ji[0][j];
+    E.g[2][j] = E.Ji[1][j];
+    E.g[3][j] = E.Ji[2][j];
+    E.g[0][j] = -(E.Ji[0][j] + E.Ji[1][j] + E.Ji[2][j]);
+    E.ga[j] = sel4(a, E.g[0][j], E.g[1][j], E.g[2][j], E.g[3][j]);
   }
-  if (lane < 12) W.g[lane / 3][lane % 3] = g[lane / 3][lane % 3];
-  for (int q = lane; q < nq; q += 32) {
-    const double* t = tab + TET_ROW * q;
-    double* R = rec + QREC * q;
-    const double lam[4] = {t[0], t[1], t[2], t[3]};
-    const double bq = t[4];
-    double d[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) d[j] = (t[5] * cof[j][0] + t[6] * cof[j][1] + t[7] * cof[j][2]) * r;
-    double v[3], L[3][3], dv[3];
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      E.G[i][j] = V[0][i] * E.g[0][j] + V[1][i] * E.g[1][j] + V[2][i] * E.g[2][j] + V[3][i] * E.g[3][j];
+  // reference-frame components Vr_c = Jinv V_c, br = Jinv beta
+  double Vr[4][3], br[3];
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Vr[c][al] = E.Ji[al][0] * V[c][0] + E.Ji[al][1] * V[c][1] + E.Ji[al][2] * V[c][2];
+    br[al] = E.Ji[al][0] * E.beta[0] + E.Ji[al][1] * E.beta[1] + E.Ji[al][2] * E.beta[2];
+  }
+  const double* M2a = E.m2a;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    E.Ua[j] = M2a[0] * V[0][j] + M2a[1] * V[1][j] + M2a[2] * V[2][j] + M2a[3] * V[3][j] + E.m1ba * E.beta[j];
+    E.Ub[j] = M[TM_M1B] * V[0][j] + M[TM_M1B + 1] * V[1][j] + M[TM_M1B + 2] * V[2][j] +
+              M[TM_M1B + 3] * V[3][j] + M[TM_MBB] * E.beta[j];
+  }
+  double Aa = 0.0, Ab = 0.0, Bd = 0.0;
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Aa += E.m2da[3 * c + al] * Vr[c][al];
+      Ab += M[TM_M1BD + 3 * c + al] * Vr[c][al];
+    }
+    Aa += E.m1bda[al] * br[al];
+    Ab += M[TM_MBBD + al] * br[al];
+    Bd += E.m1da[al] * br[al];
+  }
+  E.Aa = Aa;
+  E.Ab = Ab;
+  E.Bd = Bd;
+  E.Pbar = M[TM_M1] * P[0] + M[TM_M1 + 1] * P[1] + M[TM_M1 + 2] * P[2] + M[TM_M1 + 3] * P[3];
+  double Pd[3];
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+    Pd[al] = M[TM_M1D + al] * P[0] + M[TM_M1D + 3 + al] * P[1] + M[TM_M1D + 6 + al] * P[2] + M[TM_M1D + 9 + al] * P[3];
+  double JJ[3][3];  // Jinv Jinv^T
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int be = 0; be < 3; ++be)
+      JJ[al][be] = E.Ji[al][0] * E.Ji[be][0] + E.Ji[al][1] * E.Ji[be][1] + E.Ji[al][2] * E.Ji[be][2];
+  double DD = 0.0;
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int be = 0; be < 3; ++be) DD += M[TM_MDD + 3 * al + be] * JJ[al][be];
+  E.DD = DD;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    E.Dint[j] = M[TM_MD] * E.Ji[0][j] + M[TM_MD + 1] * E.Ji[1][j] + M[TM_MD + 2] * E.Ji[2][j];
+    E.PdJ[j] = Pd[0] * E.Ji[0][j] + Pd[1] * E.Ji[1][j] + Pd[2] * E.Ji[2][j];
+  }
+  if (transient) {
+    double dV[4][3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double4_32a o = up[E.nd[c]];
+      dV[c][0] = V[c][0] - o.x; dV[c][1] = V[c][1] - o.y; dV[c][2] = V[c][2] - o.z;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      double s = bq * W.beta[i], sp = 0.0;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        s += lam[a] * W.V[a][i];
-        sp += lam[a] * (W.V[a][i] - W.Vp[a][i]);
-      }
-      v[i] = s;
-      dv[i] = sp;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        double l = W.beta[i] * d[j];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) l += W.V[a][i] * g[a][j];
-        L[i][j] = l;
-      }
+      E.dVa[i] = M2a[0] * dV[0][i] + M2a[1] * dV[1][i] + M2a[2] * dV[2][i] + M2a[3] * dV[3][i];
+      E.dVb[i] = M[TM_M1B] * dV[0][i] + M[TM_M1B + 1] * dV[1][i] + M[TM_M1B + 2] * dV[2][i] + M[TM_M1B + 3] * dV[3][i];
     }
-    double p = 0.0;
+  } else {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) p += lam[a] * W.P[a];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) R[Q_LAM + a] = lam[a];
-    R[Q_B] = bq;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) { R[Q_D + j] = d[j]; R[Q_V + j] = v[j]; R[Q_DV + j] = dv[j]; }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) R[Q_L + 3 * i + j] = L[i][j];
-      R[Q_CONV + i] = L[i][0] * v[0] + L[i][1] * v[1] + L[i][2] * v[2];
-    }
-    R[Q_P] = p;
-    R[Q_OM] = t[8] * det;
-    R[Q_CD] = v[0] * d[0] + v[1] * d[1] + v[2] * d[2];
-    R[Q_DD] = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    R[Q_TRL] = L[0][0] + L[1][1] + L[2][2];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) R[Q_CB + b] = v[0] * g[b][0] + v[1] * g[b][1] + v[2] * g[b][2];
-  }
-  if (lane == 0 && !ok) W.flag |= 1u;
-  __syncwarp();
-  if (lane == 0) {
-    double vol = 0.0;
-    for (int q = 0; q < nq; ++q) vol += rec[QREC * q + Q_OM];
-    W.vol = vol;
-  }
-  __syncwarp();
-  return ok;
-}
-
-// Residual entries (lanes 0..15: R_cp, lanes 16..18: R_f) summed over the points.
-__device__ void tet_residual_entries(int lane, int nq, const TetWarp& W, const double* rec,
-                                     double nut, double tau, const double f[3], double& out) {
-  out = 0.0;
-  if (lane < 16) {
-    const int a = lane >> 2, i = lane & 3;
-    for (int q = 0; q < nq; ++q) {
-      const double* R = rec + QREC * q;
-      const double om = R[Q_OM], la = R[Q_LAM + a];
-      if (i < 3) {
-        double s = la * (R[Q_CONV + i] - f[i] + tau * R[Q_DV + i]) - W.g[a][i] * R[Q_P];
-        s += nut * (W.g[a][0] * R[Q_L + 3 * i] + W.g[a][1] * R[Q_L + 3 * i + 1] + W.g[a][2] * R[Q_L + 3 * i + 2]);
-        out += om * s;
-      } else {
-        out -= om * la * R[Q_TRL];
-      }
-    }
-  } else if (lane < 19) {
-    const int i = lane - 16;
-    for (int q = 0; q < nq; ++q) {
-      const double* R = rec + QREC * q;
-      const double b = R[Q_B];
-      double s = b * (R[Q_CONV + i] - f[i] + tau * R[Q_DV + i]) - R[Q_D + i] * R[Q_P];
-      s += nut * (R[Q_D] * R[Q_L + 3 * i] + R[Q_D + 1] * R[Q_L + 3 * i + 1] + R[Q_D + 2] * R[Q_L + 3 * i + 2]);
-      out += R[Q_OM] * s;
-    }
+    for (int i = 0; i < 3; ++i) E.dVa[i] = E.dVb[i] = 0.0;
   }
 }
 
-// Tangent blocks (lanes take entries; formulas of Eq. NewtonUpdate2 with the P1 basis).
-__device__ void tet_tangent_entries(int lane, int nq, TetWarp& W, const double* rec, double nut,
-                                    double tau) {
-  for (int ent = lane; ent < 256; ent += 32) {
-    const int r = ent >> 4, c = ent & 15;
-    const int a = r >> 2, i = r & 3, b = c >> 2, k = c & 3;
-    double s = 0.0;
-    if (i < 3 && k < 3) {
-      for (int q = 0; q < nq; ++q) {
-        const double* R = rec + QREC * q;
-        const double lab = R[Q_LAM + a] * R[Q_LAM + b];
-        double t = lab * R[Q_L + 3 * i + k];
-        if (i == k) t += R[Q_LAM + a] * R[Q_CB + b] + tau * lab;
-        s += R[Q_OM] * t;
-      }
-      if (i == k) s += nut * W.vol * (W.g[a][0] * W.g[b][0] + W.g[a][1] * W.g[b][1] + W.g[a][2] * W.g[b][2]);
-    } else if (i < 3 && k == 3) {
-      for (int q = 0; q < nq; ++q) s += rec[QREC * q + Q_OM] * rec[QREC * q + Q_LAM + b];
-      s *= -W.g[a][i];
-    } else if (i == 3 && k < 3) {
-      for (int q = 0; q < nq; ++q) s += rec[QREC * q + Q_OM] * rec[QREC * q + Q_LAM + a];
-      s *= -W.g[b][k];
-    }
-    W.Kcc[r][c] = s;
+__device__ __forceinline__ double dot3(const double x[3], const double y[3]) {
+  return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
+}
+
+// R_cp rows of node a (Eqs. SC_Coarse_Resid_Vec, SC_Coarse_Resid_Vec_2) and R_f (Eq.
+// SC_Fine_Resid_Vec), every lane of the group holding the same R_f.
+__device__ __forceinline__ void tet_residual(int a, const TetElem& E, const double* __restrict__ M,
+                                             double nut, double tau, const double f[3],
+                                             double Rcp[4], double Rf[3]) {
+  const double gD = dot3(E.ga, E.Dint);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double s = dot3(E.G[i], E.Ua) + E.beta[i] * E.Aa - f[i] * E.m1a + tau * E.dVa[i] -
+                     E.ga[i] * E.Pbar + nut * (M[TM_M0] * dot3(E.ga, E.G[i]) + E.beta[i] * gD);
+    Rcp[i] = E.det * s;
+    const double t = dot3(E.G[i], E.Ub) + E.beta[i] * E.Ab - f[i] * M[TM_MB] + tau * E.dVb[i] -
+                     E.PdJ[i] + nut * (dot3(E.G[i], E.Dint) + E.beta[i] * E.DD);
+    Rf[i] = E.det * t;
   }
-  for (int ent = lane; ent < 48; ent += 32) {
-    const int r = ent / 3, m = ent % 3;   // K_cf[r][m]
-    const int a = r >> 2, i = r & 3;
-    double s = 0.0;
-    for (int q = 0; q < nq; ++q) {
-      const double* R = rec + QREC * q;
-      const double om = R[Q_OM], la = R[Q_LAM + a];
-      if (i < 3) {
-        double t = la * R[Q_B] * R[Q_L + 3 * i + m];
-        if (i == m) t += la * R[Q_CD] + nut * (W.g[a][0] * R[Q_D] + W.g[a][1] * R[Q_D + 1] + W.g[a][2] * R[Q_D + 2]);
-        s += om * t;
-      } else {
-        s -= om * la * R[Q_D + m];
-      }
-    }
-    W.Kcf[r][m] = s;
+  Rcp[3] = -E.det * (E.m1a * (E.G[0][0] + E.G[1][1] + E.G[2][2]) + E.Bd);
+}
+
+template <typename T>
+__device__ __forceinline__ void tet_scatter_row(T* p, const double v[4], bool atomic);
+template <>
+__device__ __forceinline__ void tet_scatter_row<float>(float* p, const double v[4], bool atomic) {
+  // one row of a 4x4 node block: four contiguous values, 16-byte aligned (offsets are multiples of 4)
+  const float4 w = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  if (atomic) {
+    atomicAdd(reinterpret_cast<float4*>(p), w);
+  } else {
+    float4 o = *reinterpret_cast<float4*>(p);
+    o.x += w.x; o.y += w.y; o.z += w.z; o.w += w.w;
+    *reinterpret_cast<float4*>(p) = o;
   }
-  for (int ent = lane; ent < 48; ent += 32) {
-    const int m = ent / 16, c = ent % 16;   // K_fc[m][c]
-    const int b = c >> 2, k = c & 3;
-    double s = 0.0;
-    for (int q = 0; q < nq; ++q) {
-      const double* R = rec + QREC * q;
-      const double om = R[Q_OM], lb = R[Q_LAM + b], bq = R[Q_B];
-      if (k < 3) {
-        double t = bq * lb * R[Q_L + 3 * m + k];
-        if (m == k)
-          t += bq * R[Q_CB + b] + nut * (R[Q_D] * W.g[b][0] + R[Q_D + 1] * W.g[b][1] + R[Q_D + 2] * W.g[b][2]) +
-               tau * bq * lb;
-        s += om * t;
-      } else {
-        s -= om * R[Q_D + m] * lb;
-      }
-    }
-    W.Kfc[m][c] = s;
-  }
-  if (lane < 9) {
-    const int i = lane / 3, k = lane % 3;
-    double s = 0.0;
-    for (int q = 0; q < nq; ++q) {
-      const double* R = rec + QREC * q;
-      const double bq = R[Q_B];
-      double t = bq * bq * R[Q_L + 3 * i + k];
-      if (i == k) t += bq * R[Q_CD] + nut * R[Q_DD];
-      s += R[Q_OM] * t;
-    }
-    W.Kff[lane] = s;
+}
+template <>
+__device__ __forceinline__ void tet_scatter_row<double>(double* p, const double v[4], bool atomic) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (v[k] == 0.0) continue;
+    if (atomic) atomicAdd(p + k, v[k]); else p[k] += v[k];
   }
 }
 
@@ -384,7 +374,7 @@ template <typename T, bool ELEM_OUT, bool ATOMIC>
 __global__ void __launch_bounds__(TET_WARPS * 32) tet_assembly_kernel(
     const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u,
     const double4_32a* __restrict__ up, const int32_t* __restrict__ conn,
-    const double* __restrict__ beta, const double* __restrict__ tab, int nq, KParams kp,
+    const double* __restrict__ beta, const TetMoments mom, KParams kp,
     int64_t first, int64_t count, const int32_t* __restrict__ elem_list,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, double* __restrict__ rhs,
@@ -392,98 +382,183 @@ __global__ void __launch_bounds__(TET_WARPS * 32) tet_assembly_kernel(
     double* __restrict__ recY, double* __restrict__ oS, double* __restrict__ oR,
     double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
     double* __restrict__ oKff, unsigned int* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  const double* M = mom.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* base = smem + warp * tet_warp_bytes(nq);
-  TetWarp& W = *reinterpret_cast<TetWarp*>(base);
-  double* rec = reinterpret_cast<double*>(base + ((sizeof(TetWarp) + 15) & ~size_t(15)));
-  const int64_t total = (int64_t)gridDim.x * TET_WARPS;
-  for (int64_t it = (int64_t)blockIdx.x * TET_WARPS + warp; it < count; it += total) {
+  const int a = lane & 3, src0 = lane & ~3;
+  const int64_t stride = (int64_t)gridDim.x * TET_WARPS * TET_PER_WARP;
+  for (int64_t base = ((int64_t)blockIdx.x * TET_WARPS + warp) * TET_PER_WARP; base < count; base += stride) {
+    // the loop is uniform over the warp (shuffles below); groups past the end redo element `base`
+    // and store nothing
+    const int64_t it0 = base + (lane >> 2);
+    const bool valid = it0 < count;
+    const int64_t it = valid ? it0 : base;
     const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
     const double nut = kp.nu_e ? kp.visc_factor * kp.nu_e[e] : kp.nut;
-    tet_points(lane, e, nq, xyz, u, up, conn, beta, tab, kp.tau, kp.transient != 0, W, rec);
-    double res;
-    tet_residual_entries(lane, nq, W, rec, nut, kp.tau, kp.f, res);
-    if (lane < 16) W.Rcp[lane] = res;
-    else if (lane < 19) W.Rf[lane - 16] = res;
-    tet_tangent_entries(lane, nq, W, rec, nut, kp.tau);
-    __syncwarp();
-    // K_ff^-1 (FP64, cofactors on lanes 0..8)
-    if (lane < 9) {
-      const int i = lane / 3, j = lane % 3;
-      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-      W.cof[lane] = W.Kff[3 * i1 + j1] * W.Kff[3 * i2 + j2] - W.Kff[3 * i1 + j2] * W.Kff[3 * i2 + j1];
-    }
-    __syncwarp();
-    const double det = W.Kff[0] * W.cof[0] + W.Kff[1] * W.cof[1] + W.Kff[2] * W.cof[2];
-    const bool bad = !(det != 0.0) || !isfinite(det);
-    if (lane < 9) W.Kinv[lane] = bad ? 0.0 : W.cof[3 * (lane % 3) + lane / 3] / det;
-    if (bad && lane == 0) W.flag |= 2u;
-    __syncwarp();
-    // X = K_ff^-1 K_fc (3 x 16), W_row = K_cf K_ff^-1 (16 x 3)
-    for (int ent = lane; ent < 48; ent += 32) {
-      const int m = ent / 16, c = ent % 16;
-      W.Xs[m][c] = W.Kinv[3 * m] * W.Kfc[0][c] + W.Kinv[3 * m + 1] * W.Kfc[1][c] + W.Kinv[3 * m + 2] * W.Kfc[2][c];
-    }
-    __syncwarp();
-    const uint32_t msk = dir_mask[e];
-    // recovery data and the condensed residual r = R_cp - K_cf K_ff^-1 R_f
-    double y[3];
+    const double tau = kp.tau;
+    TetElem E;
+    tet_element(a, e, xyz, u, up, conn, beta, kp.transient != 0, M, E);
+    double Rcp[4], Rf[3];
+    tet_residual(a, E, M, nut, tau, kp.f, Rcp, Rf);
+    const double det = E.det;
+
+    // K_ff and its inverse (every lane)
+    double Q[3], Kff[9];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) y[m] = W.Kinv[3 * m] * W.Rf[0] + W.Kinv[3 * m + 1] * W.Rf[1] + W.Kinv[3 * m + 2] * W.Rf[2];
-    for (int ent = lane; ent < 48; ent += 32) recX[96 * e + 32 * (ent / 16) + (ent % 16)] = T(W.Xs[ent / 16][ent % 16]);
-    if (lane < 16) {
-      double wr[3];
+    for (int k = 0; k < 3; ++k) Q[k] = M[TM_MBBD] * E.Ji[0][k] + M[TM_MBBD + 1] * E.Ji[1][k] + M[TM_MBBD + 2] * E.Ji[2][k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        Kff[3 * i + k] = det * (M[TM_MBB] * E.G[i][k] + E.beta[i] * Q[k] + (i == k ? E.Ab + nut * E.DD : 0.0));
+    double Kc[9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      const int i = l / 3, j = l % 3;
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      Kc[l] = Kff[3 * i1 + j1] * Kff[3 * i2 + j2] - Kff[3 * i1 + j2] * Kff[3 * i2 + j1];
+    }
+    const double kdet = Kff[0] * Kc[0] + Kff[1] * Kc[1] + Kff[2] * Kc[2];
+    const bool bad = !(kdet != 0.0) || !isfinite(kdet);
+    const double kr = bad ? 0.0 : 1.0 / kdet;
+    double Kinv[9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) Kinv[l] = Kc[3 * (l % 3) + l / 3] * kr;
+
+    // F_a = int lambda_a b d, H_a = int lambda_a d (divided by det)
+    double F[3], H[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      F[m] = E.m1bda[0] * E.Ji[0][m] + E.m1bda[1] * E.Ji[1][m] + E.m1bda[2] * E.Ji[2][m];
+      H[m] = E.m1da[0] * E.Ji[0][m] + E.m1da[1] * E.Ji[1][m] + E.m1da[2] * E.Ji[2][m];
+    }
+    const double gD = dot3(E.ga, E.Dint);
+    const double m1b = E.m1ba;
+    // K_fc column block a (3 x 4) and X_a = K_ff^-1 K_fc[:, block a]
+    double Kfc[3][4], Xa[3][4];
+    {
+      const double gUb = dot3(E.ga, E.Ub);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          Kfc[m][k] = det * (m1b * E.G[m][k] + E.beta[m] * F[k] + (m == k ? gUb + nut * gD + tau * m1b : 0.0));
+        Kfc[m][3] = -det * H[m];
+      }
 #pragma unroll
       for (int m = 0; m < 3; ++m)
-        wr[m] = W.Kcf[lane][0] * W.Kinv[m] + W.Kcf[lane][1] * W.Kinv[3 + m] + W.Kcf[lane][2] * W.Kinv[6 + m];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) recW[96 * e + 3 * lane + m] = wr[m];
-      const double rr = W.Rcp[lane] - (wr[0] * W.Rf[0] + wr[1] * W.Rf[1] + wr[2] * W.Rf[2]);
-      if (!isfinite(rr)) atomicOr(flags, FLAG_NAN);
-      if (ELEM_OUT) {
-        if (oR) oR[16 * it + lane] = rr;
-      } else if (!(msk >> lane & 1u)) {
-        double* dst = rhs + 4 * (int64_t)W.nd[lane >> 2] + (lane & 3);
-        if (ATOMIC) atomicAdd(dst, rr); else *dst += rr;
-      }
-    }
-    if (lane < 9) recKinv[9 * e + lane] = W.Kinv[lane];
-    if (lane < 3) recY[3 * e + lane] = y[lane];
-    // S = K_cc - K_cf X: lane -> block (a, b) = ((lane >> 1) >> 2, (lane >> 1) & 3), rows 2h, 2h+1
-    const int blkid = lane >> 1, a = blkid >> 2, b = blkid & 3, h = lane & 1;
-    for (int ii = 0; ii < 2; ++ii) {
-      const int i = 2 * h + ii, r = 4 * a + i;
-      double v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int c = 4 * b + k;
-        v[k] = W.Kcc[r][c] - (W.Kcf[r][0] * W.Xs[0][c] + W.Kcf[r][1] * W.Xs[1][c] + W.Kcf[r][2] * W.Xs[2][c]);
-      }
-      if (ELEM_OUT) {
-        if (oS)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) oS[256 * it + 16 * r + 4 * b + k] = v[k];
-      } else if (!(msk >> r & 1u)) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (msk >> (4 * b + k) & 1u) v[k] = 0.0;
-        const int32_t off = blk[16 * e + 4 * a + b] + i * rowlen[W.nd[a]];
-        add_row(values + off, v, ATOMIC);
+          Xa[m][k] = Kinv[3 * m] * Kfc[0][k] + Kinv[3 * m + 1] * Kfc[1][k] + Kinv[3 * m + 2] * Kfc[2][k];
+    }
+    // K_cf rows of node a (4 x 3), W_a = K_cf K_ff^-1, condensed residual r = R_cp - W_a R_f
+    double Kcf[4][3], rr[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+        Kcf[i][m] = det * (m1b * E.G[i][m] + E.beta[i] * F[m] + (i == m ? E.Aa + nut * gD : 0.0));
+#pragma unroll
+    for (int m = 0; m < 3; ++m) Kcf[3][m] = -det * H[m];
+    double Wa[4][3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) Wa[i][m] = Kcf[i][0] * Kinv[m] + Kcf[i][1] * Kinv[3 + m] + Kcf[i][2] * Kinv[6 + m];
+      rr[i] = Rcp[i] - (Wa[i][0] * Rf[0] + Wa[i][1] * Rf[1] + Wa[i][2] * Rf[2]);
+    }
+    const uint32_t msk = dir_mask[e];
+    if (valid) {
+      if (!(isfinite(rr[0]) && isfinite(rr[1]) && isfinite(rr[2]) && isfinite(rr[3])))
+        atomicOr(flags, FLAG_NAN);
+      if (a == 0 && (!E.ok || bad)) atomicOr(flags, (E.ok ? 0u : FLAG_NEG_JACOBIAN) | (bad ? FLAG_SINGULAR_KFF : 0u));
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) recX[96 * e + 32 * m + 4 * a + k] = T(Xa[m][k]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) recW[96 * e + 3 * (4 * a + i) + m] = Wa[i][m];
+      if (a < 3) {
+        double kr3[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) kr3[k] = a == 0 ? Kinv[k] : a == 1 ? Kinv[3 + k] : Kinv[6 + k];
+        recY[3 * e + a] = kr3[0] * Rf[0] + kr3[1] * Rf[1] + kr3[2] * Rf[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) recKinv[9 * e + 3 * a + k] = kr3[k];
+      }
+      if (ELEM_OUT) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (oR) oR[16 * it + 4 * a + i] = rr[i];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            if (oKcf) oKcf[48 * it + 3 * (4 * a + i) + m] = Kcf[i][m];
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (oKfc) oKfc[48 * it + 16 * m + 4 * a + k] = Kfc[m][k];
+        if (oKff && a < 3)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) oKff[9 * it + 3 * a + k] = a == 0 ? Kff[k] : a == 1 ? Kff[3 + k] : Kff[6 + k];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (!(msk >> (4 * a + i) & 1u)) {
+            double* dst = rhs + 4 * (int64_t)E.nda + i;
+            if (ATOMIC) atomicAdd(dst, rr[i]); else *dst += rr[i];
+          }
       }
     }
-    if (ELEM_OUT) {
-      if (oKcc)
-        for (int ent = lane; ent < 256; ent += 32) oKcc[256 * it + ent] = W.Kcc[ent >> 4][ent & 15];
-      if (oKcf)
-        for (int ent = lane; ent < 48; ent += 32) oKcf[48 * it + ent] = W.Kcf[ent / 3][ent % 3];
-      if (oKfc)
-        for (int ent = lane; ent < 48; ent += 32) oKfc[48 * it + ent] = W.Kfc[ent / 16][ent % 16];
-      if (oKff && lane < 9) oKff[9 * it + lane] = W.Kff[lane];
+    // S_e blocks (a, b) = K_cc(a, b) - K_cf(a rows) X_b, X_b from lane b of the group
+    const int rl = valid && !ELEM_OUT ? rowlen[E.nda] : 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      double Xb[3][4];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Xb[m][k] = __shfl_sync(0xffffffffu, Xa[m][k], src0 | b);
+      const double m2 = E.m2a[b];
+      double Eab[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        Eab[k] = E.m2da[3 * b] * E.Ji[0][k] + E.m2da[3 * b + 1] * E.Ji[1][k] + E.m2da[3 * b + 2] * E.Ji[2][k];
+      const double sd = dot3(E.g[b], E.Ua) + tau * m2 + nut * M[TM_M0] * dot3(E.ga, E.g[b]);
+      double K[4][4];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) K[i][k] = det * (E.G[i][k] * m2 + E.beta[i] * Eab[k] + (i == k ? sd : 0.0));
+        K[i][3] = -det * E.ga[i] * M[TM_M1 + b];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) K[3][k] = -det * E.g[b][k] * E.m1a;
+      K[3][3] = 0.0;
+      if (!valid) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        double v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = K[i][k] - (Kcf[i][0] * Xb[0][k] + Kcf[i][1] * Xb[1][k] + Kcf[i][2] * Xb[2][k]);
+        const int r = 4 * a + i;
+        if (ELEM_OUT) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (oS) oS[256 * it + 16 * r + 4 * b + k] = v[k];
+            if (oKcc) oKcc[256 * it + 16 * r + 4 * b + k] = K[i][k];
+          }
+        } else if (!(msk >> r & 1u)) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (msk >> (4 * b + k) & 1u) v[k] = 0.0;
+          tet_scatter_row<T>(values + blk[16 * e + 4 * a + b] + i * rl, v, ATOMIC);
+        }
+      }
     }
-    __syncwarp();
-    if (lane == 0 && W.flag) atomicOr(flags, W.flag);
-    __syncwarp();
   }
 }
 
@@ -492,52 +567,52 @@ __global__ void __launch_bounds__(TET_WARPS * 32) tet_assembly_kernel(
 __global__ void __launch_bounds__(TET_WARPS * 32) tet_residual_kernel(
     const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u,
     const double4_32a* __restrict__ up, const int32_t* __restrict__ conn,
-    const double* __restrict__ beta, const double* __restrict__ tab, int nq, KParams kp,
-    int64_t first, int64_t count, double* __restrict__ elemR, double* __restrict__ resid,
+    const double* __restrict__ beta, const TetMoments mom, KParams kp, int64_t first,
+    int64_t count, double* __restrict__ elemR, double* __restrict__ resid,
     const uint32_t* __restrict__ dir_mask, int64_t n_nodes, int mode, unsigned int* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  const double* M = mom.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* base = smem + warp * tet_warp_bytes(nq);
-  TetWarp& W = *reinterpret_cast<TetWarp*>(base);
-  double* rec = reinterpret_cast<double*>(base + ((sizeof(TetWarp) + 15) & ~size_t(15)));
-  const int64_t total = (int64_t)gridDim.x * TET_WARPS;
-  for (int64_t it = (int64_t)blockIdx.x * TET_WARPS + warp; it < count; it += total) {
+  const int a = lane & 3;
+  const int64_t stride = (int64_t)gridDim.x * TET_WARPS * TET_PER_WARP;
+  for (int64_t base = ((int64_t)blockIdx.x * TET_WARPS + warp) * TET_PER_WARP; base < count; base += stride) {
+    const int64_t it = base + (lane >> 2);
+    if (it >= count) continue;  // no shuffles here: groups past the end just skip
     const int64_t e = first + it;
     const double nut = kp.nu_e ? kp.visc_factor * kp.nu_e[e] : kp.nut;
-    tet_points(lane, e, nq, xyz, u, up, conn, beta, tab, kp.tau, kp.transient != 0, W, rec);
-    double res;
-    tet_residual_entries(lane, nq, W, rec, nut, kp.tau, kp.f, res);
-    if (lane < 19 && !isfinite(res)) atomicOr(flags, FLAG_NAN);
+    TetElem E;
+    tet_element(a, e, xyz, u, up, conn, beta, kp.transient != 0, M, E);
+    double Rcp[4], Rf[3];
+    tet_residual(a, E, M, nut, kp.tau, kp.f, Rcp, Rf);
+    if (!(isfinite(Rcp[0]) && isfinite(Rcp[1]) && isfinite(Rcp[2]) && isfinite(Rcp[3]) &&
+          isfinite(Rf[0]) && isfinite(Rf[1]) && isfinite(Rf[2])))
+      atomicOr(flags, FLAG_NAN);
+    if (a == 0 && !E.ok) atomicOr(flags, FLAG_NEG_JACOBIAN);
     if (mode == 0) {
-      if (lane < 16) elemR[36 * e + lane] = res;
-      else if (lane < 19) elemR[36 * e + 32 + lane - 16] = res;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) elemR[36 * e + 4 * a + i] = Rcp[i];
+      if (a < 3) elemR[36 * e + 32 + a] = a == 0 ? Rf[0] : a == 1 ? Rf[1] : Rf[2];
     } else {
-      if (lane < 16) {
-        if (!(dir_mask[e] >> lane & 1u)) atomicAdd(resid + 4 * (int64_t)W.nd[lane >> 2] + (lane & 3), res);
-      } else if (lane < 19) {
-        resid[4 * n_nodes + 3 * e + lane - 16] = res;
-      }
+      const uint32_t msk = dir_mask[e];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (!(msk >> (4 * a + i) & 1u)) atomicAdd(resid + 4 * (int64_t)E.nda + i, Rcp[i]);
+      if (a < 3) resid[4 * n_nodes + 3 * e + a] = a == 0 ? Rf[0] : a == 1 ? Rf[1] : Rf[2];
     }
-    __syncwarp();
-    if (lane == 0 && W.flag) atomicOr(flags, W.flag);
-    __syncwarp();
   }
 }
 
 unsigned tet_blocks(int64_t count) {
-  int64_t b = (count + TET_WARPS - 1) / TET_WARPS;
-  return (unsigned)(b < 1 ? 1 : (b > 152 * 64 ? 152 * 64 : b));
+  const int64_t per = TET_WARPS * TET_PER_WARP;
+  int64_t b = (count + per - 1) / per;
+  return (unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
 }
 
 template <typename T, bool ELEM_OUT, bool ATOMIC>
-void launch_ta(const Mesh& m, const State& s, const KParams& kp, const double* tab, int nq,
+void launch_ta(const Mesh& m, const State& s, const KParams& kp, const TetMoments& mom,
                const TangentOut& o, int64_t first, int64_t count, const int32_t* elem_list,
                unsigned int* flags, cudaStream_t st) {
-  const size_t smem = TET_WARPS * tet_warp_bytes(nq);
-  auto kern = tet_assembly_kernel<T, ELEM_OUT, ATOMIC>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<tet_blocks(count), TET_WARPS * 32, smem, st>>>(
-      m.xyz, s.u, s.u_prev, m.conn, s.beta, tab, nq, kp, first, count, elem_list, m.blk, m.rowlen,
+  tet_assembly_kernel<T, ELEM_OUT, ATOMIC><<<tet_blocks(count), TET_WARPS * 32, 0, st>>>(
+      m.xyz, s.u, s.u_prev, m.conn, s.beta, mom, kp, first, count, elem_list, m.blk, m.rowlen,
       m.dir_mask, reinterpret_cast<T*>(o.values), o.rhs, reinterpret_cast<T*>(o.recX),
       reinterpret_cast<double*>(o.recW), o.recKinv, o.recY, o.S,
       o.r, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
@@ -546,27 +621,25 @@ void launch_ta(const Mesh& m, const State& s, const KParams& kp, const double* t
 }  // namespace
 
 int launch_tet_assembly(bool fp32, const Mesh& m, const State& s, const KParams& kp,
-                        const double* tab, int nq, const TangentOut& o, int64_t first, int64_t count,
+                        const TetMoments& mom, const TangentOut& o, int64_t first, int64_t count,
                         const int32_t* elem_list, bool elem_outputs, bool atomic,
                         unsigned int* flags, cudaStream_t st) {
   if (count <= 0) return 0;
-  if (elem_outputs && fp32) launch_ta<float, true, true>(m, s, kp, tab, nq, o, first, count, elem_list, flags, st);
-  else if (elem_outputs) launch_ta<double, true, true>(m, s, kp, tab, nq, o, first, count, elem_list, flags, st);
-  else if (fp32 && atomic) launch_ta<float, false, true>(m, s, kp, tab, nq, o, first, count, elem_list, flags, st);
-  else if (fp32) launch_ta<float, false, false>(m, s, kp, tab, nq, o, first, count, elem_list, flags, st);
-  else if (atomic) launch_ta<double, false, true>(m, s, kp, tab, nq, o, first, count, elem_list, flags, st);
-  else launch_ta<double, false, false>(m, s, kp, tab, nq, o, first, count, elem_list, flags, st);
+  if (elem_outputs && fp32) launch_ta<float, true, true>(m, s, kp, mom, o, first, count, elem_list, flags, st);
+  else if (elem_outputs) launch_ta<double, true, true>(m, s, kp, mom, o, first, count, elem_list, flags, st);
+  else if (fp32 && atomic) launch_ta<float, false, true>(m, s, kp, mom, o, first, count, elem_list, flags, st);
+  else if (fp32) launch_ta<float, false, false>(m, s, kp, mom, o, first, count, elem_list, flags, st);
+  else if (atomic) launch_ta<double, false, true>(m, s, kp, mom, o, first, count, elem_list, flags, st);
+  else launch_ta<double, false, false>(m, s, kp, mom, o, first, count, elem_list, flags, st);
   return 1;
 }
 
-int launch_tet_residual(const Mesh& m, const State& s, const KParams& kp, const double* tab, int nq,
+int launch_tet_residual(const Mesh& m, const State& s, const KParams& kp, const TetMoments& mom,
                         double* elemR, double* resid, int64_t first, int64_t count, int mode,
                         unsigned int* flags, cudaStream_t st) {
   if (count <= 0) return 0;
-  const size_t smem = TET_WARPS * tet_warp_bytes(nq);
-  cudaFuncSetAttribute(tet_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  tet_residual_kernel<<<tet_blocks(count), TET_WARPS * 32, smem, st>>>(
-      m.xyz, s.u, s.u_prev, m.conn, s.beta, tab, nq, kp, first, count, elemR, resid, m.dir_mask,
+  tet_residual_kernel<<<tet_blocks(count), TET_WARPS * 32, 0, st>>>(
+      m.xyz, s.u, s.u_prev, m.conn, s.beta, mom, kp, first, count, elemR, resid, m.dir_mask,
       m.n_nodes, mode, flags);
   return 1;
 }

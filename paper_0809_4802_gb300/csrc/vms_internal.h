@@ -135,17 +135,38 @@ struct TangentOut {
   double *S = nullptr, *r = nullptr, *Kcc = nullptr, *Kcf = nullptr, *Kfc = nullptr,
          *Kff = nullptr;
 };
-// Tetrahedral element (tet.cu): table row per quadrature point (lambda_0..3, b, db/dxi_0..2, w)
-constexpr int TET_ROW = 9;
-void tet_table(int n, double bubble_scale, std::vector<double>& tab);
+// Tetrahedral element (tet.cu). On an affine tetrahedron every integrand of the residual and the
+// tangent is a reference polynomial (products of lambda_a, b and db/dxi) times element constants,
+// so the element needs only the reference moments below, summed once per quadrature rule with the
+// rule's own points and weights (sum_q w_q f(xi_q)): the results equal the point-by-point sums up
+// to the order of rounding.
+enum : int {
+  TM_M0 = 0,      // sum w
+  TM_M1 = 1,      // [a]        lambda_a
+  TM_M2 = 5,      // [a][c]     lambda_a lambda_c
+  TM_M1B = 21,    // [a]        lambda_a b
+  TM_MB = 25,     //            b
+  TM_MBB = 26,    //            b^2
+  TM_MD = 27,     // [al]       db_al
+  TM_M1D = 30,    // [a][al]    lambda_a db_al
+  TM_M2D = 42,    // [a][c][al] lambda_a lambda_c db_al
+  TM_M1BD = 90,   // [a][al]    lambda_a b db_al
+  TM_MBBD = 102,  // [al]       b^2 db_al
+  TM_MDD = 105,   // [al][be]   db_al db_be
+  TM_COUNT = 114,
+};
+struct TetMoments {
+  double m[TM_COUNT];
+};
+void tet_moments(int n, double bubble_scale, TetMoments& mom);
 // The whole assembly of a tetrahedral mesh (residual, tangent, condensation, scatter, r_e and the
 // recovery data) in one kernel; FP64 arithmetic, values stored in FP32 when fp32.
 int launch_tet_assembly(bool fp32, const Mesh& m, const State& s, const KParams& kp,
-                        const double* tab, int nq, const TangentOut& o, int64_t first, int64_t count,
+                        const TetMoments& mom, const TangentOut& o, int64_t first, int64_t count,
                         const int32_t* elem_list, bool elem_outputs, bool atomic,
                         unsigned int* flags, cudaStream_t st);
 // Tetrahedral residual: mode 0 per element into elemR (stride 36), mode 1 assembled into resid.
-int launch_tet_residual(const Mesh& m, const State& s, const KParams& kp, const double* tab, int nq,
+int launch_tet_residual(const Mesh& m, const State& s, const KParams& kp, const TetMoments& mom,
                         double* elemR, double* resid, int64_t first, int64_t count, int mode,
                         unsigned int* flags, cudaStream_t st);
 
