@@ -41,16 +41,20 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_FLOPS_PER_ELEM = {
     "residual": 14_791,
     "tangent_fp64": 129_697,
-    # tetrahedral assembly kernel (one kernel: residual, tangent, condensation, scatter), 27-point
-    # conical rule: 19,408 DFMA + 18,972 DMUL + 3,900 DADD per element (ncu, 21^3 Kuhn cavity)
-    "tet": 61_688,
+    # tetrahedral assembly kernel (one kernel: residual, tangent, condensation, scatter from the
+    # reference moments, four lanes per element): 2,316 DFMA + 1,432 DMUL + 534 DADD per element
+    # (ncu thread-instruction counts on the 21^3 Kuhn cavity, 55,566 elements)
+    "tet": 6_598,
 }
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# same workload (profiles/residual_kernel_cavity32_re400.md); None where not captured for the
-# current kernel.
+# same workload (profiles/residual_kernel_cavity32_re400.md,
+# profiles/tet_assembly_kernel_tetcavity21_re400.md); None where not captured for the current
+# kernel.
 NCU_TRAFFIC_BYTES = {("residual", "cavity32_re400_mixed"): 4_203_776,
-                     ("residual", "cavity32_re400_fp64"): 4_203_776}
+                     ("residual", "cavity32_re400_fp64"): 4_203_776,
+                     # profiles/tet_assembly_kernel_tetcavity21_re400.md
+                     ("tangent", "tetcavity21_re400_mixed"): 21_358_592}
 
 WORKLOADS = {
     # the 32^3 jittered lid-driven cavity at Re 400, random state (mixed precision by default)

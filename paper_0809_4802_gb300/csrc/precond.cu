@@ -26,8 +26,10 @@ namespace {
 
 constexpr uint32_t ILU_SPIN_LIMIT = 1u << 22;
 constexpr int ILU_FWARPS = 4;    // warps per CTA of the factorisation
-constexpr int ILU_SWARPS = 16;   // warps per CTA of the sweeps (one segment each)
-constexpr unsigned ILU_SWEEP_CTAS = 152 * 2;  // at most two sweep CTAs per SM
+// warps per CTA of the sweeps (one segment each): FP64 rows keep the FP64 pipe of their SM
+// partition busy for ~1000 cycles, so FP64 sweeps spread over more SMs
+template <typename T> constexpr int sweep_warps() { return sizeof(T) == 4 ? 8 : 4; }
+constexpr unsigned ILU_SWEEP_CTAS = 152 * 4;  // at most four sweep CTAs per SM
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
@@ -296,8 +298,16 @@ __device__ __forceinline__ bool wait_shared(const volatile uint32_t* f, int* err
   return false;
 }
 
-// One row of a sweep with everything that does not depend on other rows: its neighbour block
-// (one per lane), the factor blocks, the right-hand side and, for U, the row of U_ii^-1.
+// One row of a sweep with everything that does not depend on other rows, loaded in two stages so
+// that no load waits on another inside the row chain: first the row's offsets (SweepIdx), then,
+// one row later, the lane's neighbour block, the factor blocks, the right-hand side and, for U,
+// the row of U_ii^-1 (SweepRow).
+struct SweepIdx {
+  int32_t rp[4];
+  int32_t rp1;   // start of the row's second scalar row (degree = (rp1 - rp[0]) / 4)
+  int32_t dp;
+};
+
 template <typename T>
 struct SweepRow {
   int64_t k;     // the lane's neighbour node
@@ -307,23 +317,26 @@ struct SweepRow {
   T drow[4];
 };
 
+__device__ __forceinline__ void load_idx(SweepIdx& X, int64_t i, const int32_t* __restrict__ rowptr,
+                                         const int32_t* __restrict__ dpos) {
+  for (int m = 0; m < 4; ++m) X.rp[m] = rowptr[4 * i + m];
+  X.rp1 = X.rp[1];
+  X.dp = dpos[i];
+}
+
 template <typename T, bool LOWER>
-__device__ __forceinline__ void load_row(SweepRow<T>& R, int64_t i, int lane, int q, bool writer,
-                                         const int32_t* __restrict__ rowptr,
-                                         const int32_t* __restrict__ colidx, const T* __restrict__ F,
-                                         const T* __restrict__ Dinv, const int32_t* __restrict__ dpos,
-                                         const T* __restrict__ v, const unsigned long long* __restrict__ vp,
-                                         int64_t n0) {
-  int32_t rp[4];
-  for (int m = 0; m < 4; ++m) rp[m] = rowptr[4 * i + m];
-  const int deg = (rowptr[4 * i + 1] - rp[0]) >> 2;
-  const int dp = dpos[i];
-  const int kk = LOWER ? lane : dp + 1 + lane;
-  R.mine = LOWER ? kk < dp : kk < deg;
+__device__ __forceinline__ void load_row(SweepRow<T>& R, const SweepIdx& X, int64_t i, int lane,
+                                         int q, bool writer, const int32_t* __restrict__ colidx,
+                                         const T* __restrict__ F, const T* __restrict__ Dinv,
+                                         const T* __restrict__ v,
+                                         const unsigned long long* __restrict__ vp, int64_t n0) {
+  const int deg = (X.rp1 - X.rp[0]) >> 2;
+  const int kk = LOWER ? lane : X.dp + 1 + lane;
+  R.mine = LOWER ? kk < X.dp : kk < deg;
   R.k = 0;
   if (R.mine) {
-    R.k = colidx[rp[0] + 4 * kk] >> 2;
-    for (int m = 0; m < 4; ++m) R.f[m] = V4<T>::ldg(F + rp[m] + 4 * kk);
+    R.k = colidx[X.rp[0] + 4 * kk] >> 2;
+    for (int m = 0; m < 4; ++m) R.f[m] = V4<T>::ldg(F + X.rp[m] + 4 * kk);
   }
   R.rhs = T(0);
   for (int m = 0; m < 4; ++m) R.drow[m] = T(0);
@@ -349,14 +362,14 @@ __device__ __forceinline__ void load_row(SweepRow<T>& R, int64_t i, int lane, in
 //
 // The rows are cut into segments (seg[s] .. seg[s+1]): maximal runs of consecutive nodes in which
 // every node is coupled to the one before it (a grid line in a lattice numbering), at most
-// ILU_SEG_MAX long. A CTA claims the next chunk of ILU_SWARPS segments in sweep order from the
+// ILU_SEG_MAX long. A CTA claims the next chunk of W segments in sweep order from the
 // global counter and each of its warps takes one segment and does its rows in order, loading the
 // next row while the current one waits. A row's dependency in the same chunk is read from shared
 // memory once its flag is set (no L2 round trip; in the warp's own segment it is already there);
 // a dependency in an earlier chunk is read from the L2 publication. Chunks are claimed in order by
 // running CTAs, so every wait is for work that is already in progress.
-template <typename T, bool LOWER>
-__global__ void __launch_bounds__(ILU_SWARPS * 32)
+template <typename T, bool LOWER, int W = sweep_warps<T>()>
+__global__ void __launch_bounds__(W * 32)
     ilu_sweep_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                      const T* __restrict__ F, const T* __restrict__ Dinv,
                      const int32_t* __restrict__ dpos, const int32_t* __restrict__ seg, int64_t s0,
@@ -364,7 +377,7 @@ __global__ void __launch_bounds__(ILU_SWARPS * 32)
                      const unsigned long long* __restrict__ vp, void* pub, T* __restrict__ out,
                      int64_t n0, int64_t n_rows, uint32_t ep, unsigned long long* ticket,
                      unsigned long long base, int* err) {
-  constexpr int SLOTS = ILU_SWARPS * ILU_SEG_MAX;
+  constexpr int SLOTS = W * ILU_SEG_MAX;
   __shared__ __align__(16) T sx[SLOTS * 4];
   __shared__ uint32_t sready[SLOTS];
   __shared__ int64_t s_chunk;
@@ -372,7 +385,7 @@ __global__ void __launch_bounds__(ILU_SWARPS * 32)
   const int q = (lane >> 3) & 3;          // the component this lane's reduction ends with
   const bool writer = (lane & 7) == 0;    // lanes 0, 8, 16, 24 finish components 0..3
   const int64_t n1 = n0 + n_rows;
-  const int64_t n_chunks = (n_segs + ILU_SWARPS - 1) / ILU_SWARPS;
+  const int64_t n_chunks = (n_segs + W - 1) / W;
   for (;;) {
     if (threadIdx.x == 0) {
       int64_t c = n_chunks;
@@ -388,8 +401,8 @@ __global__ void __launch_bounds__(ILU_SWARPS * 32)
     const int64_t c = s_chunk;
     if (c >= n_chunks) return;
     // segments jlo .. jhi - 1 in sweep order; their nodes form the range [a, b)
-    const int64_t jlo = c * ILU_SWARPS;
-    const int64_t jhi = jlo + ILU_SWARPS < n_segs ? jlo + ILU_SWARPS : n_segs;
+    const int64_t jlo = c * W;
+    const int64_t jhi = jlo + W < n_segs ? jlo + W : n_segs;
     int64_t a = LOWER ? seg[s0 + jlo] : seg[s0 + n_segs - jhi];
     int64_t b = LOWER ? seg[s0 + jhi] : seg[s0 + n_segs - jlo];
     a = a > n0 ? a : n0;
@@ -401,16 +414,23 @@ __global__ void __launch_bounds__(ILU_SWARPS * 32)
       r_lo = r_lo > n0 ? r_lo : n0;
       r_hi = r_hi < n1 ? r_hi : n1;
       const int len = (int)(r_hi - r_lo);
+      // rows r of the segment in sweep order: node LOWER ? r_lo + r : r_hi - 1 - r. Pipeline:
+      // offsets two rows ahead, data one row ahead of the row being solved.
       SweepRow<T> nxt;
-      if (len > 0)
-        load_row<T, LOWER>(nxt, LOWER ? r_lo : r_hi - 1, lane, q, writer, rowptr, colidx, F, Dinv,
-                           dpos, v, vp, n0);
+      SweepIdx idx;
+      if (len > 0) {
+        load_idx(idx, LOWER ? r_lo : r_hi - 1, rowptr, dpos);
+        load_row<T, LOWER>(nxt, idx, LOWER ? r_lo : r_hi - 1, lane, q, writer, colidx, F, Dinv, v,
+                           vp, n0);
+      }
+      if (len > 1) load_idx(idx, LOWER ? r_lo + 1 : r_hi - 2, rowptr, dpos);
       for (int r = 0; r < len; ++r) {
         const int64_t i = LOWER ? r_lo + r : r_hi - 1 - r;
         const SweepRow<T> cur = nxt;
         if (r + 1 < len)
-          load_row<T, LOWER>(nxt, LOWER ? i + 1 : i - 1, lane, q, writer, rowptr, colidx, F, Dinv,
-                             dpos, v, vp, n0);
+          load_row<T, LOWER>(nxt, idx, LOWER ? i + 1 : i - 1, lane, q, writer, colidx, F, Dinv, v,
+                             vp, n0);
+        if (r + 2 < len) load_idx(idx, LOWER ? i + 2 : i - 2, rowptr, dpos);
         T acc[4] = {T(0), T(0), T(0), T(0)};
         bool ok = true;
         if (cur.mine) {
@@ -662,16 +682,17 @@ int ilu_apply<float, float>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const
   const int64_t rows = n1 - n0;
   int64_t s0 = 0, ns = 0;
   segment_range(p, n0, n1, s0, ns);
-  const int64_t chunks = (ns + ILU_SWARPS - 1) / ILU_SWARPS;
+  constexpr int W = sweep_warps<float>();
+  const int64_t chunks = (ns + W - 1) / W;
   const unsigned ctas = resident_ctas(chunks, 1, ILU_SWEEP_CTAS);
   const unsigned long long claims = (unsigned long long)chunks + ctas;  // + each CTA's last claim
   uint32_t ep = next_epoch(p, st);
-  ilu_sweep_kernel<float, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+  ilu_sweep_kernel<float, true><<<ctas, W * 32, 0, st>>>(
       m.rowptr, m.colidx, p.F32, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, p.yp, nullptr, n0,
       rows, ep, p.tickets, p.base, p.err);
   p.base += claims;
   ep = next_epoch(p, st);
-  ilu_sweep_kernel<float, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+  ilu_sweep_kernel<float, false><<<ctas, W * 32, 0, st>>>(
       m.rowptr, m.colidx, p.F32, p.Dinv32, p.dpos, p.seg, s0, ns, nullptr, p.yp, p.xp, z, n0,
       rows, ep, p.tickets, p.base, p.err);
   p.base += claims;
@@ -684,18 +705,19 @@ int ilu_apply<double, double>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, con
   const int64_t rows = n1 - n0;
   int64_t s0 = 0, ns = 0;
   segment_range(p, n0, n1, s0, ns);
-  const int64_t chunks = (ns + ILU_SWARPS - 1) / ILU_SWARPS;
+  constexpr int W = sweep_warps<double>();
+  const int64_t chunks = (ns + W - 1) / W;
   const unsigned ctas = resident_ctas(chunks, 1, ILU_SWEEP_CTAS);
   const unsigned long long claims = (unsigned long long)chunks + ctas;  // + each CTA's last claim
   double* y = p.y;
   double* x = p.x64;
   cudaMemsetAsync(y + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
-  ilu_sweep_kernel<double, true><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+  ilu_sweep_kernel<double, true><<<ctas, W * 32, 0, st>>>(
       m.rowptr, m.colidx, p.F, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, y, nullptr, n0, rows, 0,
       p.tickets, p.base, p.err);
   p.base += claims;
   cudaMemsetAsync(x + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
-  ilu_sweep_kernel<double, false><<<ctas, ILU_SWARPS * 32, 0, st>>>(
+  ilu_sweep_kernel<double, false><<<ctas, W * 32, 0, st>>>(
       m.rowptr, m.colidx, p.F, p.Dinv, p.dpos, p.seg, s0, ns, y, nullptr, x, z, n0, rows, 0,
       p.tickets, p.base, p.err);
   p.base += claims;
