@@ -55,32 +55,6 @@ __device__ __forceinline__ bool wait_ready(const uint32_t* f, uint32_t epoch, in
   return false;
 }
 
-template <typename T> struct V4;
-template <> struct V4<float> {
-  float v[4];
-  __device__ __forceinline__ static V4 ldg(const float* p) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    return {{t.x, t.y, t.z, t.w}};
-  }
-  __device__ __forceinline__ static V4 ldcg(const float* p) {
-    const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
-    return {{t.x, t.y, t.z, t.w}};
-  }
-};
-template <> struct V4<double> {
-  double v[4];
-  __device__ __forceinline__ static V4 ldg(const double* p) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    return {{a.x, a.y, b.x, b.y}};
-  }
-  __device__ __forceinline__ static V4 ldcg(const double* p) {
-    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
-    return {{a.x, a.y, b.x, b.y}};
-  }
-};
-
 // Claim the next row of this launch: 0 <= t < n_rows, or n_rows when none is left. A claim below
 // the launch's base (the counter was disturbed by a launch that stopped early) records an error
 // and also returns n_rows, so that no row index outside [0, n_rows) is ever formed.
@@ -284,11 +258,26 @@ __device__ __forceinline__ T warp_sum4_scatter(const T a[4], int lane) {
   return c;
 }
 
-// Wait for a row of the CTA's own chunk (shared-memory flag), bounded like the global waits.
-__device__ __forceinline__ bool wait_shared(const volatile uint32_t* f, int* err) {
+// Shared-memory publication inside a chunk: the CTA fills the chunk's value slots with an all-ones
+// bit pattern (a NaN that arithmetic never produces) when it takes the chunk, each writer lane then
+// stores its value directly, and a reader polls until none of the node's four words holds the
+// pattern. Every word is written once by one lane, so no flag and no fence is needed.
+template <typename T> struct Bits;
+template <> struct Bits<float> { using U = uint32_t; static constexpr U unset = 0xffffffffu; };
+template <> struct Bits<double> { using U = unsigned long long; static constexpr U unset = ~0ull; };
+
+template <typename T>
+__device__ __forceinline__ bool wait_shared(const T* p, T out[4], int* err) {
+  using U = typename Bits<T>::U;
+  const volatile U* w = reinterpret_cast<const volatile U*>(p);
   for (uint32_t it = 0; it <= ILU_SPIN_LIMIT; ++it) {
-    if (*f) {
-      __threadfence_block();
+    const U a = w[0], b = w[1], c = w[2], d = w[3];
+    if (a != Bits<T>::unset && b != Bits<T>::unset && c != Bits<T>::unset && d != Bits<T>::unset) {
+      const U u[4] = {a, b, c, d};
+      for (int m = 0; m < 4; ++m) {
+        if constexpr (sizeof(T) == 4) out[m] = __uint_as_float(u[m]);
+        else out[m] = __longlong_as_double((long long)u[m]);
+      }
       return true;
     }
     if (it >= 32) __nanosleep(8);
@@ -298,61 +287,33 @@ __device__ __forceinline__ bool wait_shared(const volatile uint32_t* f, int* err
   return false;
 }
 
-// One row of a sweep with everything that does not depend on other rows, loaded in two stages so
-// that no load waits on another inside the row chain: first the row's offsets (SweepIdx), then,
-// one row later, the lane's neighbour block, the factor blocks, the right-hand side and, for U,
-// the row of U_ii^-1 (SweepRow).
-struct SweepIdx {
-  int32_t rp[4];
-  int32_t rp1;   // start of the row's second scalar row (degree = (rp1 - rp[0]) / 4)
-  int32_t dp;
-};
-
-template <typename T>
-struct SweepRow {
-  int64_t k;     // the lane's neighbour node
-  bool mine;     // the lane has a neighbour block on the sweep's side of the diagonal
-  V4<T> f[4];
-  T rhs;
-  T drow[4];
-};
-
-__device__ __forceinline__ void load_idx(SweepIdx& X, int64_t i, const int32_t* __restrict__ rowptr,
-                                         const int32_t* __restrict__ dpos) {
-  for (int m = 0; m < 4; ++m) X.rp[m] = rowptr[4 * i + m];
-  X.rp1 = X.rp[1];
-  X.dp = dpos[i];
+// Asynchronous global -> shared copies (per thread; completion tracked per thread by groups, so a
+// thread only ever reads what it copied itself and no flag or barrier is involved).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <typename T, bool LOWER>
-__device__ __forceinline__ void load_row(SweepRow<T>& R, const SweepIdx& X, int64_t i, int lane,
-                                         int q, bool writer, const int32_t* __restrict__ colidx,
-                                         const T* __restrict__ F, const T* __restrict__ Dinv,
-                                         const T* __restrict__ v,
-                                         const unsigned long long* __restrict__ vp, int64_t n0) {
-  const int deg = (X.rp1 - X.rp[0]) >> 2;
-  const int kk = LOWER ? lane : X.dp + 1 + lane;
-  R.mine = LOWER ? kk < X.dp : kk < deg;
-  R.k = 0;
-  if (R.mine) {
-    R.k = colidx[X.rp[0] + 4 * kk] >> 2;
-    for (int m = 0; m < 4; ++m) R.f[m] = V4<T>::ldg(F + X.rp[m] + 4 * kk);
-  }
-  R.rhs = T(0);
-  for (int m = 0; m < 4; ++m) R.drow[m] = T(0);
-  if (writer) {
-    if constexpr (LOWER) {
-      R.rhs = v[4 * (i - n0) + q];
-    } else if constexpr (sizeof(T) == 4) {
-      R.rhs = __uint_as_float((uint32_t)vp[4 * i + q]);
-    } else {
-      R.rhs = v[4 * i + q];
-    }
-    if constexpr (!LOWER) {
-      const V4<T> d = V4<T>::ldg(Dinv + 16 * i + 4 * q);
-      for (int m = 0; m < 4; ++m) R.drow[m] = d.v[m];
-    }
-  }
+// Rows of a segment in flight ahead of the row being solved, and the per-warp ring they land in:
+// for each slot, every lane's 4x4 factor block, every lane's column index and the four rows of
+// U_ii^-1 (backward sweep).
+constexpr int ILU_PF = 4;
+template <typename T>
+struct SweepSlot {
+  T f[32][16];
+  int32_t col[32];
+  T dinv[4][4];
+};
+template <typename T>
+constexpr size_t sweep_ring_bytes(int warps) {
+  return (size_t)warps * ILU_PF * sizeof(SweepSlot<T>);
 }
 
 // T: element type of the factor (float: packed publication, double: sentinel publication).
@@ -379,9 +340,10 @@ __global__ void __launch_bounds__(W * 32)
                      unsigned long long base, int* err) {
   constexpr int SLOTS = W * ILU_SEG_MAX;
   __shared__ __align__(16) T sx[SLOTS * 4];
-  __shared__ uint32_t sready[SLOTS];
   __shared__ int64_t s_chunk;
+  extern __shared__ __align__(16) unsigned char sring[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  SweepSlot<T>* ring = reinterpret_cast<SweepSlot<T>*>(sring) + warp * ILU_PF;
   const int q = (lane >> 3) & 3;          // the component this lane's reduction ends with
   const bool writer = (lane & 7) == 0;    // lanes 0, 8, 16, 24 finish components 0..3
   const int64_t n1 = n0 + n_rows;
@@ -396,7 +358,8 @@ __global__ void __launch_bounds__(W * 32)
       }
       s_chunk = c;
     }
-    for (int l = threadIdx.x; l < SLOTS; l += blockDim.x) sready[l] = 0u;
+    for (int l = threadIdx.x; l < 4 * SLOTS; l += blockDim.x)
+      reinterpret_cast<typename Bits<T>::U*>(sx)[l] = Bits<T>::unset;
     __syncthreads();
     const int64_t c = s_chunk;
     if (c >= n_chunks) return;
@@ -414,33 +377,90 @@ __global__ void __launch_bounds__(W * 32)
       r_lo = r_lo > n0 ? r_lo : n0;
       r_hi = r_hi < n1 ? r_hi : n1;
       const int len = (int)(r_hi - r_lo);
-      // rows r of the segment in sweep order: node LOWER ? r_lo + r : r_hi - 1 - r. Pipeline:
-      // offsets two rows ahead, data one row ahead of the row being solved.
-      SweepRow<T> nxt;
-      SweepIdx idx;
-      if (len > 0) {
-        load_idx(idx, LOWER ? r_lo : r_hi - 1, rowptr, dpos);
-        load_row<T, LOWER>(nxt, idx, LOWER ? r_lo : r_hi - 1, lane, q, writer, colidx, F, Dinv, v,
-                           vp, n0);
+      // rows r of the segment in sweep order: node LOWER ? r_lo + r : r_hi - 1 - r. All rows'
+      // offsets and right-hand sides are loaded at once (row r on lane r % 32, register set r / 32);
+      // factor blocks, column indices and U_ii^-1 rows stream through the ring ILU_PF - 1 rows
+      // ahead of the row being solved.
+      int32_t o_rp[2][4], o_dp[2];
+      T o_rhs[2][4];
+      for (int h = 0; h < 2; ++h) {
+        const int l = lane + 32 * h;
+        o_dp[h] = 0;
+        for (int m = 0; m < 4; ++m) { o_rp[h][m] = 0; o_rhs[h][m] = T(0); }
+        if (l < len) {
+          const int64_t il = LOWER ? r_lo + l : r_hi - 1 - l;
+          for (int m = 0; m < 4; ++m) o_rp[h][m] = rowptr[4 * il + m];
+          o_dp[h] = dpos[il];
+          for (int m = 0; m < 4; ++m) {
+            if constexpr (LOWER) {
+              o_rhs[h][m] = v[4 * (il - n0) + m];
+            } else if constexpr (sizeof(T) == 4) {
+              o_rhs[h][m] = __uint_as_float((uint32_t)vp[4 * il + m]);
+            } else {
+              o_rhs[h][m] = v[4 * il + m];
+            }
+          }
+        }
       }
-      if (len > 1) load_idx(idx, LOWER ? r_lo + 1 : r_hi - 2, rowptr, dpos);
+      // offsets of row r (uniform r): broadcast from the lane that loaded them
+      auto row_offsets = [&](int r, int32_t rp[4], int& dp) {
+        const int src = r & 31;
+        const bool hi = r >= 32;
+        for (int m = 0; m < 4; ++m) rp[m] = __shfl_sync(FULL, hi ? o_rp[1][m] : o_rp[0][m], src);
+        dp = __shfl_sync(FULL, hi ? o_dp[1] : o_dp[0], src);
+      };
+      auto issue = [&](int r) {  // start the copies of row r (every lane commits one group)
+        if (r < len) {
+          int32_t rp[4], dp;
+          row_offsets(r, rp, dp);
+          const int deg = (rp[1] - rp[0]) >> 2;
+          const int kk = LOWER ? lane : dp + 1 + lane;
+          const bool mine = LOWER ? kk < dp : kk < deg;
+          SweepSlot<T>& sl = ring[r % ILU_PF];
+          constexpr int CH = (int)(4 * sizeof(T)) / 16;  // 16-byte pieces of a 4-value block row
+          constexpr int EPC = 16 / (int)sizeof(T);        // values per piece
+          if (mine) {
+            for (int m = 0; m < 4; ++m)
+              for (int c = 0; c < CH; ++c)
+                cp_async16(&sl.f[lane][4 * m + c * EPC], F + rp[m] + 4 * kk + c * EPC);
+            cp_async4(&sl.col[lane], colidx + rp[0] + 4 * kk);
+          }
+          if (!LOWER && writer) {
+            const int64_t ir = r_hi - 1 - r;
+            for (int c = 0; c < CH; ++c)
+              cp_async16(&sl.dinv[q][c * EPC], Dinv + 16 * ir + 4 * q + c * EPC);
+          }
+        }
+        cp_commit();
+      };
+      for (int r = 0; r < ILU_PF - 1; ++r) issue(r);
       for (int r = 0; r < len; ++r) {
         const int64_t i = LOWER ? r_lo + r : r_hi - 1 - r;
-        const SweepRow<T> cur = nxt;
-        if (r + 1 < len)
-          load_row<T, LOWER>(nxt, idx, LOWER ? i + 1 : i - 1, lane, q, writer, colidx, F, Dinv, v,
-                             vp, n0);
-        if (r + 2 < len) load_idx(idx, LOWER ? i + 2 : i - 2, rowptr, dpos);
+        issue(r + ILU_PF - 1);
+        cp_wait<ILU_PF - 1>();  // this thread's copies of row r have landed
+        const SweepSlot<T>& sl = ring[r % ILU_PF];
+        int32_t rp[4], dp;
+        row_offsets(r, rp, dp);
+        const int deg = (rp[1] - rp[0]) >> 2;
+        const int kk = LOWER ? lane : dp + 1 + lane;
+        const bool mine = LOWER ? kk < dp : kk < deg;
+        T rhs = T(0);
+        {
+          const int src = r & 31;
+          const bool hi = r >= 32;
+          for (int m = 0; m < 4; ++m) {
+            const T t = __shfl_sync(FULL, hi ? o_rhs[1][m] : o_rhs[0][m], src);
+            if (m == q) rhs = t;
+          }
+        }
         T acc[4] = {T(0), T(0), T(0), T(0)};
         bool ok = true;
-        if (cur.mine) {
-          const int64_t k = cur.k;
+        if (mine) {
+          const int64_t k = sl.col[lane] >> 2;
           T xk[4];
           if (k >= a && k < b) {  // a row of this chunk: shared memory
             const int64_t sk = LOWER ? k - a : b - 1 - k;
-            ok = wait_shared(sready + sk, err);
-            if (ok)
-              for (int m = 0; m < 4; ++m) xk[m] = sx[4 * sk + m];
+            ok = wait_shared<T>(sx + 4 * sk, xk, err);
           } else if constexpr (sizeof(T) == 4) {
             ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err);
           } else {
@@ -448,32 +468,30 @@ __global__ void __launch_bounds__(W * 32)
           }
           if (ok)
             for (int rr = 0; rr < 4; ++rr)
-              for (int m = 0; m < 4; ++m) acc[rr] += cur.f[rr].v[m] * xk[m];
+              for (int m = 0; m < 4; ++m) acc[rr] += sl.f[lane][4 * rr + m] * xk[m];
         }
         if (!__all_sync(FULL, ok)) break;  // an error was recorded; the CTA stops after this chunk
         const T sum = warp_sum4_scatter(acc, lane);
-        const T w = writer ? cur.rhs - sum : T(0);
+        const T w = writer ? rhs - sum : T(0);
         T res = w;
         if constexpr (!LOWER) {
           T wq[4];
           for (int m = 0; m < 4; ++m) wq[m] = __shfl_sync(FULL, w, 8 * m);
-          res = cur.drow[0] * wq[0] + cur.drow[1] * wq[1] + cur.drow[2] * wq[2] + cur.drow[3] * wq[3];
+          res = writer ? sl.dinv[q][0] * wq[0] + sl.dinv[q][1] * wq[1] + sl.dinv[q][2] * wq[2] +
+                             sl.dinv[q][3] * wq[3]
+                       : T(0);
         }
         const int64_t si = LOWER ? i - a : b - 1 - i;
         if (writer) {
-          sx[4 * si + q] = res;
+          *reinterpret_cast<volatile T*>(sx + 4 * si + q) = res;
           if constexpr (sizeof(T) == 4)
             st_packed(reinterpret_cast<unsigned long long*>(pub) + 4 * i + q, res, ep);
           else
             st_relaxed_f64(reinterpret_cast<double*>(pub) + 4 * i + q, res);
           if (out) out[4 * (i - n0) + q] = res;
         }
-        __syncwarp();
-        if (lane == 0) {
-          __threadfence_block();
-          *(volatile uint32_t*)(sready + si) = 1u;
-        }
       }
+      cp_wait<0>();  // no copy of this segment may land in the ring after the warp has moved on
     }
     __syncthreads();
   }
@@ -687,12 +705,16 @@ int ilu_apply<float, float>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const
   const unsigned ctas = resident_ctas(chunks, 1, ILU_SWEEP_CTAS);
   const unsigned long long claims = (unsigned long long)chunks + ctas;  // + each CTA's last claim
   uint32_t ep = next_epoch(p, st);
-  ilu_sweep_kernel<float, true><<<ctas, W * 32, 0, st>>>(
+  const size_t ring = sweep_ring_bytes<float>(W);
+  // the ring needs more than the default 48 KB of dynamic shared memory (set for the current device)
+  cudaFuncSetAttribute(ilu_sweep_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+  cudaFuncSetAttribute(ilu_sweep_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+  ilu_sweep_kernel<float, true><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F32, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, p.yp, nullptr, n0,
       rows, ep, p.tickets, p.base, p.err);
   p.base += claims;
   ep = next_epoch(p, st);
-  ilu_sweep_kernel<float, false><<<ctas, W * 32, 0, st>>>(
+  ilu_sweep_kernel<float, false><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F32, p.Dinv32, p.dpos, p.seg, s0, ns, nullptr, p.yp, p.xp, z, n0,
       rows, ep, p.tickets, p.base, p.err);
   p.base += claims;
@@ -712,12 +734,16 @@ int ilu_apply<double, double>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, con
   double* y = p.y;
   double* x = p.x64;
   cudaMemsetAsync(y + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
-  ilu_sweep_kernel<double, true><<<ctas, W * 32, 0, st>>>(
+  const size_t ring = sweep_ring_bytes<double>(W);
+  // the ring needs more than the default 48 KB of dynamic shared memory (set for the current device)
+  cudaFuncSetAttribute(ilu_sweep_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+  cudaFuncSetAttribute(ilu_sweep_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+  ilu_sweep_kernel<double, true><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, y, nullptr, n0, rows, 0,
       p.tickets, p.base, p.err);
   p.base += claims;
   cudaMemsetAsync(x + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
-  ilu_sweep_kernel<double, false><<<ctas, W * 32, 0, st>>>(
+  ilu_sweep_kernel<double, false><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F, p.Dinv, p.dpos, p.seg, s0, ns, y, nullptr, x, z, n0, rows, 0,
       p.tickets, p.base, p.err);
   p.base += claims;

@@ -143,46 +143,131 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
   return v;
 }
 
-// partial[k][bx] = sum over this block's chunk of V_k . w, for k = blockIdx.y (FP64 accumulation)
+// Four consecutive entries of a vector as doubles (16-byte loads for FP32, two for FP64).
+template <typename VT> struct Quad;
+template <> struct Quad<float> {
+  __device__ __forceinline__ static void ld(const float* p, double o[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
+  __device__ __forceinline__ static void st(float* p, const double v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  }
+};
+template <> struct Quad<double> {
+  __device__ __forceinline__ static void ld(const double* p, double o[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  __device__ __forceinline__ static void st(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+constexpr int MD_K = 8;          // vectors per block of the multi-dot and per step of the combine
+constexpr int MD_THREADS = 256;
+constexpr int MD_MAX_BLOCKS = 256;
+
+// partial[k * nb + bx] = this block's share of V_k . w for k in [MD_K by, MD_K by + MD_K) and
+// k < m (FP64 accumulation). Rows are taken four at a time (quad) when every vector allows it.
 template <typename VT>
-__global__ void __launch_bounds__(DOT_THREADS) multidot_kernel(const VT* __restrict__ V, int64_t ld,
-                                                               const VT* __restrict__ w, int64_t n,
-                                                               double* __restrict__ partial) {
-  __shared__ double sh[DOT_THREADS / 32];
-  const int k = blockIdx.y;
-  const VT* v = V + (int64_t)k * ld;
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; i < n;
-       i += (int64_t)DOT_BLOCKS * DOT_THREADS)
-    s = fma((double)v[i], (double)w[i], s);
-  s = block_reduce(s, sh);
-  if (threadIdx.x == 0) partial[k * DOT_BLOCKS + blockIdx.x] = s;
+__global__ void __launch_bounds__(MD_THREADS) mdot_kernel(const VT* __restrict__ V, int64_t ld, int m,
+                                                          const VT* __restrict__ w, int64_t n,
+                                                          bool quad, double* __restrict__ partial) {
+  __shared__ double sh[MD_K][MD_THREADS / 32];
+  const int k0 = blockIdx.y * MD_K;
+  const int nb = gridDim.x;
+  double acc[MD_K];
+#pragma unroll
+  for (int t = 0; t < MD_K; ++t) acc[t] = 0.0;
+  if (quad) {
+    const int64_t n4 = n >> 2;
+    for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n4; i += (int64_t)nb * MD_THREADS) {
+      double wv[4], vv[MD_K][4];
+      Quad<VT>::ld(w + 4 * i, wv);
+#pragma unroll
+      for (int t = 0; t < MD_K; ++t)
+        if (k0 + t < m) Quad<VT>::ld(V + (int64_t)(k0 + t) * ld + 4 * i, vv[t]);
+#pragma unroll
+      for (int t = 0; t < MD_K; ++t)
+        if (k0 + t < m)
+          acc[t] = fma(vv[t][3], wv[3], fma(vv[t][2], wv[2], fma(vv[t][1], wv[1], fma(vv[t][0], wv[0], acc[t]))));
+    }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n; i += (int64_t)nb * MD_THREADS) {
+      const double wi = (double)w[i];
+#pragma unroll
+      for (int t = 0; t < MD_K; ++t)
+        if (k0 + t < m) acc[t] = fma((double)V[(int64_t)(k0 + t) * ld + i], wi, acc[t]);
+    }
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < MD_K; ++t) {
+    double v = acc[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[t][wp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < MD_K && k0 + (int)threadIdx.x < m) {
+    double v = 0.0;
+    for (int q = 0; q < MD_THREADS / 32; ++q) v += sh[threadIdx.x][q];
+    partial[(int64_t)(k0 + threadIdx.x) * nb + blockIdx.x] = v;
+  }
 }
 
-// out[k] = (accumulate ? out[k] : 0) + sum_b partial[k][b]
+// out[k] = sum_b partial[k * nb + b], one block per k
 __global__ void __launch_bounds__(DOT_THREADS) reduce_partials_kernel(const double* __restrict__ partial,
-                                                                      double* __restrict__ out,
-                                                                      int accumulate) {
+                                                                      int nb, double* __restrict__ out) {
   __shared__ double sh[DOT_THREADS / 32];
   const int k = blockIdx.x;
   double s = 0.0;
-  for (int b = threadIdx.x; b < DOT_BLOCKS; b += DOT_THREADS) s += partial[k * DOT_BLOCKS + b];
+  for (int b = threadIdx.x; b < nb; b += DOT_THREADS) s += partial[(int64_t)k * nb + b];
   s = block_reduce(s, sh);
-  if (threadIdx.x == 0) out[k] = (accumulate ? out[k] : 0.0) + s;
+  if (threadIdx.x == 0) out[k] = s;
 }
 
-// w -= sum_{k < m} h[k] V_k
+// out = (base ? base : 0) + sign * sum_{k < m} c[k] V_k, rows four at a time when aligned, with
+// MD_K vector loads in flight per thread
 template <typename VT>
-__global__ void gs_update_kernel(const VT* __restrict__ V, int64_t ld, const double* __restrict__ h,
-                                 int m, VT* __restrict__ w, int64_t n) {
-  __shared__ double hs[MAX_RESTART + 1];
-  for (int k = threadIdx.x; k < m; k += blockDim.x) hs[k] = h[k];
+__global__ void __launch_bounds__(256) vcomb_kernel(const VT* __restrict__ V, int64_t ld,
+                                                    const double* __restrict__ c, int m, double sign,
+                                                    const VT* base, VT* out, int64_t n, bool quad) {
+  __shared__ double cs[MAX_RESTART + 1];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) cs[k] = sign * c[k];
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = (double)w[i];
-    for (int k = 0; k < m; ++k) s -= hs[k] * (double)V[(int64_t)k * ld + i];
-    w[i] = VT(s);
+  if (quad) {
+    const int64_t n4 = n >> 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+      if (base) Quad<VT>::ld(base + 4 * i, s);
+      int k = 0;
+      for (; k + MD_K <= m; k += MD_K) {
+        double vv[MD_K][4];
+#pragma unroll
+        for (int t = 0; t < MD_K; ++t) Quad<VT>::ld(V + (int64_t)(k + t) * ld + 4 * i, vv[t]);
+#pragma unroll
+        for (int t = 0; t < MD_K; ++t)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) s[e] = fma(cs[k + t], vv[t][e], s[e]);
+      }
+      for (; k < m; ++k) {
+        double vv[4];
+        Quad<VT>::ld(V + (int64_t)k * ld + 4 * i, vv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s[e] = fma(cs[k], vv[e], s[e]);
+      }
+      Quad<VT>::st(out + 4 * i, s);
+    }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      double s = base ? (double)base[i] : 0.0;
+      for (int k = 0; k < m; ++k) s = fma(cs[k], (double)V[(int64_t)k * ld + i], s);
+      out[i] = VT(s);
+    }
   }
 }
 
@@ -194,21 +279,6 @@ __global__ void scale_kernel(const VT* __restrict__ x, const double* __restrict_
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = VT((double)x[i] * s);
-}
-
-// t = sum_k y[k] V_k  (y on the device)
-template <typename VT>
-__global__ void combine_kernel(const VT* __restrict__ V, int64_t ld, const double* __restrict__ y,
-                               int m, VT* __restrict__ t, int64_t n) {
-  __shared__ double ys[MAX_RESTART + 1];
-  for (int k = threadIdx.x; k < m; k += blockDim.x) ys[k] = y[k];
-  __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < m; ++k) s += ys[k] * (double)V[(int64_t)k * ld + i];
-    t[i] = VT(s);
-  }
 }
 
 // out = a * x + b * y (mixed vector types)
@@ -244,6 +314,40 @@ __global__ void recover_kernel(const int32_t* __restrict__ conn, int npe, const 
 static unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b));
+}
+
+// Rows can be taken four at a time when the length, the stride and every pointer allow 16-byte
+// (FP32) or 32-byte (FP64) accesses.
+static bool quad_ok(int64_t n, int64_t ld, size_t elem, std::initializer_list<const void*> ptrs) {
+  if ((n & 3) || (ld & 3)) return false;
+  for (const void* q : ptrs)
+    if (q && ((uintptr_t)q % (4 * elem))) return false;
+  return true;
+}
+
+// out[k] = V_k . w for k < m (m <= MAX_RESTART + 1), FP64 accumulation; `partial` holds
+// m * MD_MAX_BLOCKS doubles. Returns the launches.
+template <typename VT>
+static int dots(const VT* V, int64_t ld, int m, const VT* w, int64_t n, double* partial,
+                double* out, cudaStream_t st) {
+  const bool quad = quad_ok(n, ld, sizeof(VT), {V, w});
+  const int groups = (m + MD_K - 1) / MD_K;
+  const int64_t units = quad ? n / 4 : n;
+  int64_t nb = (4 * 152 + groups - 1) / groups;  // about four blocks per SM in all
+  nb = std::min<int64_t>(nb, (units + MD_THREADS - 1) / MD_THREADS);
+  nb = std::max<int64_t>(1, std::min<int64_t>(nb, MD_MAX_BLOCKS));
+  mdot_kernel<VT><<<dim3((unsigned)nb, (unsigned)groups), MD_THREADS, 0, st>>>(V, ld, m, w, n, quad, partial);
+  reduce_partials_kernel<<<m, DOT_THREADS, 0, st>>>(partial, (int)nb, out);
+  return 2;
+}
+
+// out = (base ? base : 0) + sign * sum_{k < m} c[k] V_k (c on the device). Returns the launches.
+template <typename VT>
+static int vcomb(const VT* V, int64_t ld, const double* c, int m, double sign, const VT* base,
+                 VT* out, int64_t n, cudaStream_t st) {
+  const bool quad = quad_ok(n, ld, sizeof(VT), {V, base, out});
+  vcomb_kernel<VT><<<grid_for(quad ? n / 4 : n), 256, 0, st>>>(V, ld, c, m, sign, base, out, n, quad);
+  return 1;
 }
 
 struct Gmres {
@@ -305,9 +409,7 @@ struct Gmres {
       // V_0 = r / |r|
       {
         KScope k(ctx, VMS_K_REDUCE);
-        multidot_kernel<VT><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(V, n, V, n, hd + H_PART);
-        reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
-        k.add(2);
+        k.add(dots<VT>(V, n, 1, V, n, hd + H_PART, hd + H_NORM, st));
       }
       int rc = sync_host(&res, hd + H_NORM, sizeof(double));
       if (rc) return rc;
@@ -333,19 +435,14 @@ struct Gmres {
         for (int pass = 0; pass < 2; ++pass) {
           {
             KScope k(ctx, VMS_K_REDUCE);
-            multidot_kernel<VT><<<dim3(DOT_BLOCKS, kk), DOT_THREADS, 0, st>>>(V, n, vn, n, partial);
-            reduce_partials_kernel<<<kk, DOT_THREADS, 0, st>>>(partial, hd + (pass ? H_PASS2 : H_PASS1), 0);
-            k.add(2);
+            k.add(dots<VT>(V, n, kk, vn, n, partial, hd + (pass ? H_PASS2 : H_PASS1), st));
           }
           KScope k(ctx, VMS_K_KRYLOV);
-          gs_update_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, n, hd + (pass ? H_PASS2 : H_PASS1), kk, vn, n);
-          k.add(1);
+          k.add(vcomb<VT>(V, n, hd + (pass ? H_PASS2 : H_PASS1), kk, -1.0, vn, vn, n, st));
         }
         {
           KScope k(ctx, VMS_K_REDUCE);
-          multidot_kernel<VT><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(vn, n, vn, n, partial);
-          reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(partial, hd + H_NORM, 0);
-          k.add(2);
+          k.add(dots<VT>(vn, n, 1, vn, n, partial, hd + H_NORM, st));
         }
         {
           KScope k(ctx, VMS_K_KRYLOV);
@@ -384,13 +481,11 @@ struct Gmres {
       cudaMemcpyAsync(hd + H_Y, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st);
       if (Zflex) {  // x += Z y with the kept preconditioned vectors
         KScope k(ctx, VMS_K_KRYLOV);
-        combine_kernel<VT><<<grid_for(n), 256, 0, st>>>(reinterpret_cast<const VT*>(Zflex), n, hd + H_Y, j, V + n, n);
-        k.add(1);
+        k.add(vcomb<VT>(reinterpret_cast<const VT*>(Zflex), n, hd + H_Y, j, 1.0, nullptr, V + n, n, st));
       } else {      // x += M^-1 V y
         {
           KScope k(ctx, VMS_K_KRYLOV);
-          combine_kernel<VT><<<grid_for(n), 256, 0, st>>>(V, n, hd + H_Y, j, z, n);
-          k.add(1);
+          k.add(vcomb<VT>(V, n, hd + H_Y, j, 1.0, nullptr, z, n, st));
         }
         precond<T, VT>(z, V + n);
       }
@@ -411,9 +506,7 @@ struct Gmres {
       // true residual norm for the next cycle's test is computed at the top of the loop
       if (!(res > rtol * bnorm)) {
         KScope k(ctx, VMS_K_REDUCE);
-        multidot_kernel<VT><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(V, n, V, n, hd + H_PART);
-        reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
-        k.add(2);
+        k.add(dots<VT>(V, n, 1, V, n, hd + H_PART, hd + H_NORM, st));
         double r2 = 0.0;
         if (int rc2 = sync_host(&r2, hd + H_NORM, sizeof(double))) return rc2;
         res = std::sqrt(r2);
@@ -503,8 +596,7 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
   double bnorm2 = 0.0;
   {
     KScope k(ctx, VMS_K_REDUCE);
-    multidot_kernel<double><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(w.r, n, w.r, n, hd + H_PART);
-    reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+    dots<double>(w.r, n, 1, w.r, n, hd + H_PART, hd + H_NORM, st);
     k.add(2);
   }
   Gmres G{ctx, m, w, st, n, R};
@@ -557,8 +649,7 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
     }
     {
       KScope k(ctx, VMS_K_REDUCE);
-      multidot_kernel<double><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(rfull, n, rfull, n, hd + H_PART);
-      reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+      dots<double>(rfull, n, 1, rfull, n, hd + H_PART, hd + H_NORM, st);
       k.add(2);
     }
     if ((rc = G.sync_host(&r2, hd + H_NORM, sizeof(double)))) break;
@@ -626,8 +717,7 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
       }
       {
         KScope k(ctx, VMS_K_REDUCE);
-        multidot_kernel<double><<<dim3(DOT_BLOCKS, 1), DOT_THREADS, 0, st>>>(rfull, n, rfull, n, hd + H_PART);
-        reduce_partials_kernel<<<1, DOT_THREADS, 0, st>>>(hd + H_PART, hd + H_NORM, 0);
+        dots<double>(rfull, n, 1, rfull, n, hd + H_PART, hd + H_NORM, st);
         k.add(2);
       }
       rc = G.sync_host(&r2, hd + H_NORM, sizeof(double));
