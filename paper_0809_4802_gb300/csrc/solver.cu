@@ -181,7 +181,24 @@ __global__ void __launch_bounds__(MD_THREADS) mdot_kernel(const VT* __restrict__
   double acc[MD_K];
 #pragma unroll
   for (int t = 0; t < MD_K; ++t) acc[t] = 0.0;
-  if (quad) {
+  if (quad && sizeof(VT) == 4) {
+    // FP32 vectors: the four products of a quad are summed in FP32 and the quad's partial is
+    // accumulated in FP64 (one conversion and one FP64 add per quad and vector: the FP64 pipe,
+    // 1/64 of FP32, would otherwise bound the kernel)
+    const int64_t n4 = n >> 2;
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n4; i += (int64_t)nb * MD_THREADS) {
+      const float4 wv = w4[i];
+      float4 vv[MD_K];
+#pragma unroll
+      for (int t = 0; t < MD_K; ++t)
+        if (k0 + t < m) vv[t] = reinterpret_cast<const float4*>(V + (int64_t)(k0 + t) * ld)[i];
+#pragma unroll
+      for (int t = 0; t < MD_K; ++t)
+        if (k0 + t < m)
+          acc[t] += (double)fmaf(vv[t].w, wv.w, fmaf(vv[t].z, wv.z, fmaf(vv[t].y, wv.y, vv[t].x * wv.x)));
+    }
+  } else if (quad) {
     const int64_t n4 = n >> 2;
     for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n4; i += (int64_t)nb * MD_THREADS) {
       double wv[4], vv[MD_K][4];
@@ -235,9 +252,39 @@ __global__ void __launch_bounds__(256) vcomb_kernel(const VT* __restrict__ V, in
                                                     const double* __restrict__ c, int m, double sign,
                                                     const VT* base, VT* out, int64_t n, bool quad) {
   __shared__ double cs[MAX_RESTART + 1];
-  for (int k = threadIdx.x; k < m; k += blockDim.x) cs[k] = sign * c[k];
+  __shared__ float cs32[MAX_RESTART + 1];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    cs[k] = sign * c[k];
+    cs32[k] = (float)(sign * c[k]);
+  }
   __syncthreads();
-  if (quad) {
+  if (quad && sizeof(VT) == 4) {
+    // FP32 vectors are combined in FP32 (the inner solve's working precision)
+    const int64_t n4 = n >> 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      float4 s = base ? reinterpret_cast<const float4*>(base)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      int k = 0;
+      for (; k + MD_K <= m; k += MD_K) {
+        float4 vv[MD_K];
+#pragma unroll
+        for (int t = 0; t < MD_K; ++t) vv[t] = reinterpret_cast<const float4*>(V + (int64_t)(k + t) * ld)[i];
+#pragma unroll
+        for (int t = 0; t < MD_K; ++t) {
+          const float ct = cs32[k + t];
+          s.x = fmaf(ct, vv[t].x, s.x); s.y = fmaf(ct, vv[t].y, s.y);
+          s.z = fmaf(ct, vv[t].z, s.z); s.w = fmaf(ct, vv[t].w, s.w);
+        }
+      }
+      for (; k < m; ++k) {
+        const float4 vv = reinterpret_cast<const float4*>(V + (int64_t)k * ld)[i];
+        const float ct = cs32[k];
+        s.x = fmaf(ct, vv.x, s.x); s.y = fmaf(ct, vv.y, s.y);
+        s.z = fmaf(ct, vv.z, s.z); s.w = fmaf(ct, vv.w, s.w);
+      }
+      reinterpret_cast<float4*>(out)[i] = s;
+    }
+  } else if (quad) {
     const int64_t n4 = n >> 2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
