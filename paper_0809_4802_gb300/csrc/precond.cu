@@ -71,37 +71,6 @@ __device__ __forceinline__ int64_t claim_row(unsigned long long* ticket, unsigne
   return t < (unsigned long long)n_rows ? (int64_t)t : n_rows;
 }
 
-// 4x4 inverse by Gauss-Jordan elimination with partial pivoting in FP64; false if a pivot vanishes.
-__device__ bool invert4(const double a[16], double inv[16]) {
-  double M[4][8];
-  double scale = 0.0;
-  for (int i = 0; i < 4; ++i)
-    for (int k = 0; k < 4; ++k) {
-      M[i][k] = a[4 * i + k];
-      M[i][4 + k] = i == k ? 1.0 : 0.0;
-      scale = fmax(scale, fabs(a[4 * i + k]));
-    }
-  if (!(scale > 0.0) || !isfinite(scale)) return false;
-  for (int c = 0; c < 4; ++c) {
-    int p = c;
-    for (int i = c + 1; i < 4; ++i)
-      if (fabs(M[i][c]) > fabs(M[p][c])) p = i;
-    if (!(fabs(M[p][c]) > 1e-14 * scale)) return false;
-    if (p != c)
-      for (int k = 0; k < 8; ++k) { const double t = M[c][k]; M[c][k] = M[p][k]; M[p][k] = t; }
-    const double r = 1.0 / M[c][c];
-    for (int k = 0; k < 8; ++k) M[c][k] *= r;
-    for (int i = 0; i < 4; ++i) {
-      if (i == c) continue;
-      const double f = M[i][c];
-      for (int k = 0; k < 8; ++k) M[i][k] -= f * M[c][k];
-    }
-  }
-  for (int i = 0; i < 4; ++i)
-    for (int k = 0; k < 4; ++k) inv[4 * i + k] = M[i][4 + k];
-  return true;
-}
-
 // ---------------------------------------------------------------------------------------------
 // factorisation: one warp per node row; the row is eliminated in shared memory
 // ---------------------------------------------------------------------------------------------
@@ -155,14 +124,36 @@ __global__ void __launch_bounds__(ILU_FWARPS * 32)
       }
       __syncwarp();
     }
-    if (lane == 0) {
-      double a[16], inv[16];
-      for (int e = 0; e < 16; ++e) a[e] = (double)row[16 * dp + e];
-      if (!invert4(a, inv)) {
-        atomicCAS(err, 0, ILU_ERR_PIVOT);
-        for (int e = 0; e < 16; ++e) inv[e] = (e % 5 == 0) ? 1.0 : 0.0;
-      }
-      for (int e = 0; e < 16; ++e) Dinv[16 * i + e] = T(inv[e]);
+    // U_ii^-1 = adj(U_ii) / det on lanes 0..15 (lane 4r + c forms the cofactor of entry (r, c)):
+    // a handful of FP64 instructions per lane instead of a serial elimination on one lane
+    {
+      const T* D = row + 16 * dp;
+      const int r = (lane >> 2) & 3, c = lane & 3;
+      double mnr[3][3];  // the minor: rows other than r, columns other than c
+#pragma unroll
+      for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2)
+          mnr[a2][b2] = (double)D[4 * (a2 + (a2 >= r)) + b2 + (b2 >= c)];
+      const double m3 = mnr[0][0] * (mnr[1][1] * mnr[2][2] - mnr[1][2] * mnr[2][1]) -
+                        mnr[0][1] * (mnr[1][0] * mnr[2][2] - mnr[1][2] * mnr[2][0]) +
+                        mnr[0][2] * (mnr[1][0] * mnr[2][1] - mnr[1][1] * mnr[2][0]);
+      const double cf = ((r + c) & 1) ? -m3 : m3;
+      const double dv = lane < 16 ? (double)D[lane] : 0.0;
+      double dt = lane < 4 ? dv * cf : 0.0;  // det by the first row
+      dt += __shfl_xor_sync(FULL, dt, 1);
+      dt += __shfl_xor_sync(FULL, dt, 2);
+      const double det = __shfl_sync(FULL, dt, 0);
+      // singular unless |det| is a fair fraction of the product of the row norms (Hadamard's
+      // bound; independent of the rows' scales)
+      double rn = dv * dv;
+      rn += __shfl_xor_sync(FULL, rn, 1);
+      rn += __shfl_xor_sync(FULL, rn, 2);
+      const double hb = sqrt(__shfl_sync(FULL, rn, 0)) * sqrt(__shfl_sync(FULL, rn, 4)) *
+                        sqrt(__shfl_sync(FULL, rn, 8)) * sqrt(__shfl_sync(FULL, rn, 12));
+      const bool good = isfinite(det) && hb > 0.0 && fabs(det) > 1e-14 * hb;
+      if (!good && lane == 0) atomicCAS(err, 0, ILU_ERR_PIVOT);
+      if (lane < 16) Dinv[16 * i + 4 * c + r] = good ? T(cf / det) : T(r == c ? 1.0 : 0.0);
     }
     for (int e = lane; e < deg * 16; e += 32)
       F[rowptr[4 * i + ((e >> 2) & 3)] + 4 * (e >> 4) + (e & 3)] = row[e];
