@@ -245,7 +245,7 @@ int vms_set_graph(vms_ctx* ctx, int enable);
 int vms_set_preconditioner(vms_ctx* ctx, int kind);
 
 /* Solve S du = -r with the last assembled system by restarted GMRES(restart), right-preconditioned
- * (vms_set_preconditioner; restart <= 240), FP32 inner iterations and FP64 iterative refinement in
+ * (vms_set_preconditioner; restart <= 480), FP32 inner iterations and FP64 iterative refinement in
  * VMS_PREC_MIXED (a refinement pass that does not halve the FP64 residual hands the remaining
  * correction to flexible GMRES with FP64 vectors and the FP32 matrix and preconditioner), FP64 throughout
  * in VMS_PREC_FP64, to relative residual rtol within maxit iterations in all (the paper
@@ -258,13 +258,15 @@ int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int
               double* rel);
 
 /* One Newton-Schur iteration (Sections 4.2 and 5): assemble, solve (GMRES(150) to 1e-10 relative,
- * at most 3000 iterations; a solve that stops above 1e-10 but below 0.1 is still applied),
+ * the cycle doubled up to 480 whenever one does not halve the residual, at most 3000 iterations;
+ * a solve that stops above 1e-10 but below 0.1 is still applied),
  * recover, update. *res_norm receives the FP64 residual norm before the update. */
 int vms_newton_step(vms_ctx* ctx, double* res_norm);
 
 /* Newton-Schur iteration until ||R|| <= rtol ||R^0|| or maxit iterations; hist (may be NULL,
  * maxit+1 doubles, host) receives the residual norms, *iters the iterations taken. Inexact
- * Newton: each linear solve (GMRES(150), at most 3000 iterations) stops at the relative residual
+ * Newton: each linear solve (GMRES(150), the cycle doubled up to 480 whenever one does not halve
+ * the residual, at most 3000 iterations) stops at the relative residual
  * eta = max(min(1e-2, 0.1 ||R|| / ||R^0||), rtol ||R^0|| / (2 ||R||)), capped at 0.5, and a solve
  * that stops above eta but below 0.1 is still applied.
  * Errors: VMS_ERR_NEWTON_DIVERGED, VMS_ERR_KRYLOV_MAXIT and those of the steps. */

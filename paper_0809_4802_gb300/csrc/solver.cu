@@ -127,9 +127,8 @@ __global__ void block_apply_kernel(const double* __restrict__ Dinv, const VT* __
 constexpr int DOT_BLOCKS = 256, DOT_THREADS = 256;
 // device scratch layout (doubles): Gram-Schmidt coefficients of the two passes, a norm, the
 // least-squares solution, then per-block partial sums
-constexpr int MAX_RESTART = 240;
-constexpr int H_PASS1 = 0, H_PASS2 = 256, H_NORM = 512, H_Y = 768, H_PART = 1024;
-constexpr int H_SIZE = H_PART + 256 * DOT_BLOCKS;
+constexpr int MAX_RESTART = 480;
+constexpr int H_PASS1 = 0, H_PASS2 = 512, H_NORM = 1024, H_Y = 1025, H_PART = 1536;
 
 __device__ __forceinline__ double block_reduce(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -168,6 +167,7 @@ template <> struct Quad<double> {
 constexpr int MD_K = 8;          // vectors per block of the multi-dot and per step of the combine
 constexpr int MD_THREADS = 256;
 constexpr int MD_MAX_BLOCKS = 256;
+constexpr int H_SIZE = H_PART + (MAX_RESTART + 1) * MD_MAX_BLOCKS;
 
 // partial[k * nb + bx] = this block's share of V_k . w for k in [MD_K by, MD_K by + MD_K) and
 // k < m (FP64 accumulation). Rows are taken four at a time (quad) when every vector allows it.
@@ -405,6 +405,8 @@ struct Gmres {
   int64_t n;      // 4 R.nodes(): length of every (compact) vector
   SysRange R;
   void* Zflex = nullptr;  // flexible GMRES: restart preconditioned vectors kept (else null)
+  int restart_cap = 0;    // > restart: a cycle that does not halve the residual doubles the
+                          // restart length (up to this), the basis growing with it
 
   // z = M^-1 v with the preconditioner chosen for this solve
   template <typename T, typename VT>
@@ -432,9 +434,37 @@ struct Gmres {
 
   // One restarted GMRES solve of A x = b from x = 0 in vector type VT; matrix values type T.
   // Returns VMS_OK with *iters and *relres; x receives the solution.
+  // Grow the Krylov basis (and the kept preconditioned vectors) to `restart` vectors, keeping V_0.
+  template <typename VT>
+  int grow_basis(int restart) {
+    double* nv = nullptr;
+    cudaError_t e = cudaMalloc(&nv, sizeof(double) * (size_t)n * (restart + 1));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(nv, w.V, sizeof(VT) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && Zflex) {
+      double* nz = nullptr;
+      e = cudaMalloc(&nz, sizeof(double) * (size_t)n * restart);
+      if (e == cudaSuccess) {
+        cudaFree(w.Zf);
+        w.Zf = nz;
+        w.zf_restart = restart;
+        Zflex = nz;
+      }
+    }
+    if (e != cudaSuccess) {
+      if (nv) cudaFree(nv);
+      return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
+                      cudaGetErrorString(e));
+    }
+    cudaFree(w.V);  // waits for the work queued on it
+    w.V = nv;
+    w.restart = restart;
+    return VMS_OK;
+  }
+
   template <typename T, typename VT>
   int solve(const void* values, const VT* b, VT* x, double bnorm, double rtol, int maxit,
-            int restart, int* iters, double* relres) {
+            int& restart, int* iters, double* relres) {
     VT* V = reinterpret_cast<VT*>(w.V);
     VT* z = reinterpret_cast<VT*>(w.Z);
     double* hd = w.h;
@@ -452,6 +482,7 @@ struct Gmres {
       axpby_kernel<VT, VT, VT><<<grid_for(n), 256, 0, st>>>(1.0, b, 0.0, (const VT*)nullptr, V, n);
       k.add(1);
     }
+    double cycle_res0 = res;
     while (it < maxit && res > rtol * bnorm) {
       // V_0 = r / |r|
       {
@@ -469,6 +500,7 @@ struct Gmres {
       }
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = res;
+      cycle_res0 = res;
       int j = 0;
       for (; j < restart && it < maxit; ++j, ++it) {
         VT* vj = V + (int64_t)j * n;
@@ -550,6 +582,20 @@ struct Gmres {
       }
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+      // a full cycle that did not halve the residual: the cycle is too short to keep the slow
+      // directions (coarse modes of large meshes); continue with a longer one
+      if (j == restart && it < maxit && res > rtol * bnorm && res > 0.5 * cycle_res0 &&
+          restart < restart_cap) {
+        const int nr = std::min(2 * restart, restart_cap);
+        if (int rc2 = grow_basis<VT>(nr)) return rc2;
+        V = reinterpret_cast<VT*>(w.V);
+        restart = nr;
+        H.assign((size_t)(restart + 1) * restart, 0.0);
+        cs.assign(restart, 0.0);
+        sn.assign(restart, 0.0);
+        g.assign(restart + 1, 0.0);
+        hh.assign(restart + 2, 0.0);
+      }
       // true residual norm for the next cycle's test is computed at the top of the loop
       if (!(res > rtol * bnorm)) {
         KScope k(ctx, VMS_K_REDUCE);
@@ -599,7 +645,7 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
 
 // Solve S du = -rhs into w.x (FP64). Mixed: FP32 GMRES inside FP64 iterative refinement.
 static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit, int restart,
-                        int* iters_out, double* rel_out) {
+                        int restart_cap, int* iters_out, double* rel_out) {
   const Mesh& m = ctx_mesh(ctx);
   Work& wk = ctx_work(ctx);
   SolverWork& w = ctx_solver(ctx);
@@ -647,6 +693,7 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
     k.add(2);
   }
   Gmres G{ctx, m, w, st, n, R};
+  G.restart_cap = std::min(std::max(restart_cap, restart), MAX_RESTART);
   if (int rc = G.sync_host(&bnorm2, hd + H_NORM, sizeof(double))) return rc;
   const double bnorm = std::sqrt(bnorm2);
   if (bnorm == 0.0) {
@@ -739,11 +786,14 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
     int it = 0;
     double irel = 0.0;
     // flexible GMRES: the FP32 factor applied through FP32 copies is not exactly linear
-    if (!w.Zf) {
-      const cudaError_t e = cudaMalloc(&w.Zf, sizeof(double) * (size_t)w.n * w.restart);
+    if (!w.Zf || w.zf_restart < restart) {
+      if (w.Zf) cudaFree(w.Zf);
+      w.Zf = nullptr;
+      const cudaError_t e = cudaMalloc(&w.Zf, sizeof(double) * (size_t)w.n * restart);
       if (e != cudaSuccess)
         return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
                         cudaGetErrorString(e));
+      w.zf_restart = restart;
     }
     G.Zflex = w.Zf;
     rc = G.solve<float, double>(wk.values, rfull, w.cx, std::sqrt(r2), rtol / rel, maxit - total,
@@ -826,7 +876,10 @@ namespace vms {
 // Krylov subspace of the Newton driver: the condensed systems of distorted meshes carry a few
 // near-null pressure modes (singular values down to 1e-9 of the largest), which restarted GMRES
 // resolves only when a cycle is long enough to keep them (GMRES(50) stagnates near 1e-5 on the
-// late Newton systems of a jittered 32^3 cavity, GMRES(100) too, GMRES(120) converges).
+// late Newton systems of a jittered 32^3 cavity, GMRES(100) too, GMRES(120) converges). Larger
+// meshes need longer cycles still (ILU(0)-preconditioned GMRES(150) stalls near 1e-2 on the first
+// Newton system of the 39^3 tetrahedral cavity, GMRES(400) converges): the Newton driver starts at
+// 150 and doubles the cycle whenever one does not halve the residual, up to MAX_RESTART.
 constexpr int NEWTON_RESTART = 150;
 
 static SysRange whole(vms_ctx* ctx) {
@@ -839,7 +892,8 @@ static SysRange whole(vms_ctx* ctx) {
 // instance < 0: the whole system (its state changes invalidate the assembly); instance >= 0: one
 // diagonal block (its update leaves the other instances' blocks valid).
 static int solve_impl(vms_ctx* ctx, const SysRange& R, int64_t instance, double rtol, int maxit,
-                      int restart, int update, double accept_below, int* iters, double* rel) {
+                      int restart, int restart_cap, int update, double accept_below, int* iters,
+                      double* rel) {
   if (!ctx) return VMS_ERR_INVALID_ARG;
   if (!ctx_work(ctx).assembled) return ctx_fail(ctx, VMS_ERR_STATE, "nothing assembled");
   if (ctx_stale(ctx, instance))
@@ -847,7 +901,7 @@ static int solve_impl(vms_ctx* ctx, const SysRange& R, int64_t instance, double 
   cudaSetDevice(ctx_device(ctx));
   int it = 0;
   double r = 0.0;
-  int rc = linear_solve(ctx, R, rtol, maxit, restart, &it, &r);
+  int rc = linear_solve(ctx, R, rtol, maxit, restart, restart_cap, &it, &r);
   ctx_solver_stats(ctx)[0] += 1;
   ctx_solver_stats(ctx)[1] += it;
   if (iters) *iters = it;
@@ -869,7 +923,7 @@ extern "C" {
 
 int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
               double* rel) {
-  return solve_impl(ctx, whole(ctx), -1, rtol, maxit, restart, update, 0.0, iters, rel);
+  return solve_impl(ctx, whole(ctx), -1, rtol, maxit, restart, restart, update, 0.0, iters, rel);
 }
 
 int vms_solve_instance(vms_ctx* ctx, int64_t instance, double rtol, int maxit, int restart,
@@ -877,7 +931,7 @@ int vms_solve_instance(vms_ctx* ctx, int64_t instance, double rtol, int maxit, i
   if (!ctx) return VMS_ERR_INVALID_ARG;
   SysRange R;
   if (!ctx_instance(ctx, instance, &R)) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "no such instance");
-  return solve_impl(ctx, R, instance, rtol, maxit, restart, update, 0.0, iters, rel);
+  return solve_impl(ctx, R, instance, rtol, maxit, restart, restart, update, 0.0, iters, rel);
 }
 
 int vms_newton_step(vms_ctx* ctx, double* res_norm) {
@@ -888,7 +942,7 @@ int vms_newton_step(vms_ctx* ctx, double* res_norm) {
   if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
   int it = 0;
   double rel = 0.0;
-  return solve_impl(ctx, whole(ctx), -1, 1e-10, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel);
+  return solve_impl(ctx, whole(ctx), -1, 1e-10, 3000, NEWTON_RESTART, MAX_RESTART, 1, 0.1, &it, &rel);
 }
 
 int vms_newton_solve_to(vms_ctx* ctx, double target, int maxit, int* iters, double* hist) {
@@ -905,7 +959,7 @@ int vms_newton_solve_to(vms_ctx* ctx, double target, int maxit, int* iters, doub
     const double eta = std::min(0.5, std::max({std::min(1e-2, 0.1 * r / r0), 0.5 * target / r, 1e-12}));
     int it = 0;
     double rel = 0.0;
-    if (int rc = solve_impl(ctx, whole(ctx), -1, eta, 3000, NEWTON_RESTART, 1, 0.1, &it, &rel)) return rc;
+    if (int rc = solve_impl(ctx, whole(ctx), -1, eta, 3000, NEWTON_RESTART, MAX_RESTART, 1, 0.1, &it, &rel)) return rc;
     ++k;
     if (int rc = vms_residual(ctx, &r, nullptr)) return rc;
     if (hist) hist[k] = r;

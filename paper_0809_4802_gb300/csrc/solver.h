@@ -27,7 +27,8 @@ struct SolverWork {
   double* cx = nullptr;      // n: FP64 correction of the final stage of the mixed solve
   float* pv = nullptr;       // n: FP32 copy of a vector the FP32 factor is applied to
   float* pz = nullptr;       // n: its FP32 result
-  double* Zf = nullptr;      // restart * n: preconditioned vectors of the flexible final stage
+  double* Zf = nullptr;      // zf_restart * n: preconditioned vectors of the flexible final stage
+  int zf_restart = 0;
   double* xb = nullptr;      // n: refinement iterate before the last FP32 correction
   double* rb = nullptr;      // n: its FP64 residual
   Ilu ilu;                   // ILU(0) pattern, factor and sweep work
