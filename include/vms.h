@@ -318,9 +318,9 @@ int vms_mlp_grad(vms_mlp* mlp, int64_t n, const int32_t* rows, const float* X, c
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) with the kept gradient. */
 int vms_mlp_adam(vms_mlp* mlp, float lr);
 
-/* Features of every node from the context's state u (step n) and u_prev (step n-1):
- * X[i] = [u_i (4), u_prev_i (4), mean of u over the nodes sharing an element with i (4)] divided
- * column-wise by scale_in (12 host floats, NULL = 1); X: n_nodes x 12 device FP32. */
+/* Features of every node from the context's state u (step n) and u_prev (step n-1), with
+ * d = u - u_prev: X[i] = [u_i (4), d_i (4), mean of d over the nodes sharing an element with i (4)]
+ * divided column-wise by scale_in (12 host floats, NULL = 1); X: n_nodes x 12 device FP32. */
 int vms_node_features(vms_ctx* ctx, const float* scale_in, float* X);
 /* D[i] = (u_i - u_prev_i) / scale_out (4 host floats, NULL = 1), n_nodes x 4 device FP32. */
 int vms_node_increment(vms_ctx* ctx, const float* scale_out, float* D);

@@ -6,7 +6,7 @@ starts from u^n + increment instead of u^n; Newton then converges to the same to
 network only changes the starting point.
 
 Network (plain definition, written out here):
-  features  x = [u^n (4), u^{n-1} (4), mean of u^n over the node's 1-ring (4)]     (12)
+  features  x = [u^n (4), d = u^n - u^{n-1} (4), mean of d over the node's 1-ring (4)] (12)
   H1 = tanh(x W1 + b1)          W1 (12 x 128)
   H2 = tanh(H1 W2 + b2)         W2 (128 x 128)
   y  = H2 W3 + b3               W3 (128 x 4)
@@ -112,10 +112,11 @@ def ring_mean(conn, n_nodes, u):
 
 
 def features(conn, u_n, u_nm1, scale_in=None):
-    """x = [u^n, u^{n-1}, ring mean of u^n], each column divided by scale_in (12) if given."""
+    """x = [u^n, d, ring mean of d] with d = u^n - u^{n-1}, each column divided by scale_in (12)
+    if given."""
     u_n = np.asarray(u_n, np.float64)
-    x = np.concatenate([u_n, np.asarray(u_nm1, np.float64), ring_mean(conn, u_n.shape[0], u_n)],
-                       axis=1)
+    d = u_n - np.asarray(u_nm1, np.float64)
+    x = np.concatenate([u_n, d, ring_mean(conn, u_n.shape[0], d)], axis=1)
     if scale_in is not None:
         x = x / np.asarray(scale_in, np.float64)[None, :]
     return x

@@ -343,13 +343,15 @@ __global__ void node_features_kernel(const int32_t* __restrict__ rowptr,
   for (int k = 0; k < deg; ++k) {
     const int64_t j = colidx[r0 + 4 * k] >> 2;
     if (j == i) continue;
-    const double4_32a w = u[j];
-    s[0] += w.x; s[1] += w.y; s[2] += w.z; s[3] += w.w;
+    const double4_32a w = u[j], wp = up[j];
+    s[0] += w.x - wp.x; s[1] += w.y - wp.y; s[2] += w.z - wp.z; s[3] += w.w - wp.w;
     ++cnt;
   }
   const double inv = cnt ? 1.0 / cnt : 0.0;
   const double4_32a a = u[i], b = up[i];
-  const double f[NI] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w,
+  // the last step's increment is given directly: a network with BF16 weights cannot form it from
+  // u^n and u^(n-1), which agree in their leading digits
+  const double f[NI] = {a.x, a.y, a.z, a.w, a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w,
                         s[0] * inv, s[1] * inv, s[2] * inv, s[3] * inv};
 #pragma unroll
   for (int c = 0; c < NI; ++c) X[i * NI + c] = (float)(f[c] / (double)sc.in[c]);

@@ -2,8 +2,8 @@
 term; Section 4.2: Newton) and the learned warm start.
 
 Step n -> n+1 on a context whose state holds u^n and u^{n-1}:
-  1. features of u^n, u^{n-1} and the 1-ring mean of u^n (vms_node_features), if a network is used
-     or the step is recorded for training;
+  1. features of u^n, d = u^n - u^{n-1} and the 1-ring mean of d (vms_node_features), if a
+     network is used or the step is recorded for training;
   2. u_prev <- u^n (vms_shift_time); the reference residual r_ref is the residual at u^n;
   3. start: u^n (previous-step start) or u^n + network(features) (vms_apply_increment);
   4. Newton until ||R|| <= rtol * r_ref (vms_newton_solve_to): the same target for every start;

@@ -366,7 +366,8 @@ class Context:
 
     # -- transient driver -------------------------------------------------------------------
     def node_features(self, X, scale_in=None):
-        """X: device float32 tensor (n_nodes, 12) receiving [u, u_prev, 1-ring mean of u]/scale."""
+        """X: device float32 tensor (n_nodes, 12) receiving [u, d, 1-ring mean of d] / scale with
+        d = u - u_prev."""
         sc = None if scale_in is None else np.ascontiguousarray(scale_in, dtype=np.float32)
         self._check(self.lib.vms_node_features(self.h, None if sc is None else sc.ctypes.data,
                                                _ptr(X, np.float32, self.n_nodes * MLP_IN)))

@@ -95,5 +95,5 @@ def test_features_layout_and_scaling():
     s = np.arange(1, 13, dtype=np.float64)
     x = ws.features(mesh.conn, un, um, s)
     np.testing.assert_allclose(x[:, :4] * s[:4], un)
-    np.testing.assert_allclose(x[:, 4:8] * s[4:8], um)
-    np.testing.assert_allclose(x[:, 8:] * s[8:], ws.ring_mean(mesh.conn, mesh.n_nodes, un))
+    np.testing.assert_allclose(x[:, 4:8] * s[4:8], un - um)
+    np.testing.assert_allclose(x[:, 8:] * s[8:], ws.ring_mean(mesh.conn, mesh.n_nodes, un - um))
