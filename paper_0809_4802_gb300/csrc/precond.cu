@@ -307,6 +307,80 @@ constexpr size_t sweep_ring_bytes(int warps) {
   return (size_t)warps * ILU_PF * sizeof(SweepSlot<T>);
 }
 
+// FP64 rows with at most 16 blocks on the sweep's side take two lanes per block (two block rows
+// each): 8 DFMA instructions per row instead of 16 (the FP64 unit of an SM partition spends a
+// full warp slot on every FP64 instruction, however many lanes are active).
+template <typename T>
+__device__ __forceinline__ bool split_rows_t(int side) { return sizeof(T) == 8 && side <= 16; }
+
+// One row of the two-lanes-per-block mapping (lane 2 bl + h: rows 2h, 2h + 1 of block bl). The
+// sums end on lanes 0, 16, 1, 17 for components 0..3. Returns false if a wait gave up.
+template <typename T, bool LOWER>
+__device__ __forceinline__ bool split_row(const SweepSlot<T>& sl, int r, int64_t i, int dp, int deg,
+                                          int lane, const T (&o_rhs)[2][4], T* sx, int64_t a,
+                                          int64_t b, void* pub, T* out, int64_t n0, uint32_t ep,
+                                          int* err) {
+  const int bl = lane >> 1, h = lane & 1;
+  const int kk = LOWER ? bl : dp + 1 + bl;
+  const bool mine = LOWER ? kk < dp : kk < deg;
+  const int qw = 2 * h + ((lane >> 4) & 1);      // the component this lane's reduction ends with
+  const bool wr = (lane & 14) == 0;              // lanes 0, 1, 16, 17
+  T rhs = T(0);
+  {
+    const int src = r & 31;
+    const bool hi = r >= 32;
+    for (int m = 0; m < 4; ++m) {
+      const T t = __shfl_sync(FULL, hi ? o_rhs[1][m] : o_rhs[0][m], src);
+      if (m == qw) rhs = t;
+    }
+  }
+  T acc0 = T(0), acc1 = T(0);
+  bool ok = true;
+  if (mine) {
+    const int64_t k = sl.col[lane] >> 2;
+    T xk[4];
+    if (k >= a && k < b) {
+      const int64_t sk = LOWER ? k - a : b - 1 - k;
+      ok = wait_shared<T>(sx + 4 * sk, xk, err);
+    } else if constexpr (sizeof(T) == 4) {
+      ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err);
+    } else {
+      ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err);
+    }
+    if (ok)
+      for (int m = 0; m < 4; ++m) {
+        acc0 += sl.f[lane][m] * xk[m];
+        acc1 += sl.f[lane][4 + m] * xk[m];
+      }
+  }
+  if (!__all_sync(FULL, ok)) return false;
+  // sum over the 16 blocks (lane bits 1..4), rows 2h (lane bit 4 clear) or 2h + 1 (set)
+  const bool b4 = lane & 16;
+  T sm = (b4 ? acc1 : acc0) + __shfl_xor_sync(FULL, b4 ? acc0 : acc1, 16);
+  sm += __shfl_xor_sync(FULL, sm, 8);
+  sm += __shfl_xor_sync(FULL, sm, 4);
+  sm += __shfl_xor_sync(FULL, sm, 2);
+  const T w = wr ? rhs - sm : T(0);
+  T res = w;
+  if constexpr (!LOWER) {
+    // components 0..3 sit on lanes 0, 16, 1, 17
+    const T w0 = __shfl_sync(FULL, w, 0), w1 = __shfl_sync(FULL, w, 16);
+    const T w2 = __shfl_sync(FULL, w, 1), w3 = __shfl_sync(FULL, w, 17);
+    res = wr ? sl.dinv[qw][0] * w0 + sl.dinv[qw][1] * w1 + sl.dinv[qw][2] * w2 + sl.dinv[qw][3] * w3
+             : T(0);
+  }
+  const int64_t si = LOWER ? i - a : b - 1 - i;
+  if (wr) {
+    *reinterpret_cast<volatile T*>(sx + 4 * si + qw) = res;
+    if constexpr (sizeof(T) == 4)
+      st_packed(reinterpret_cast<unsigned long long*>(pub) + 4 * i + qw, res, ep);
+    else
+      st_relaxed_f64(reinterpret_cast<double*>(pub) + 4 * i + qw, res);
+    if (out) out[4 * (i - n0) + qw] = res;
+  }
+  return true;
+}
+
 // T: element type of the factor (float: packed publication, double: sentinel publication).
 // Rows [n0, n0 + n_rows); `v` (forward sweep) and `out` are compact (index i - n0), the
 // publication buffer `pub`, the FP64 backward-sweep input `v` and the FP32 one `vp` are indexed by
@@ -400,21 +474,35 @@ __global__ void __launch_bounds__(W * 32)
         for (int m = 0; m < 4; ++m) rp[m] = __shfl_sync(FULL, hi ? o_rp[1][m] : o_rp[0][m], src);
         dp = __shfl_sync(FULL, hi ? o_dp[1] : o_dp[0], src);
       };
+      auto split_rows = [&](int dp, int deg) { return split_rows_t<T>(LOWER ? dp : deg - dp - 1); };
       auto issue = [&](int r) {  // start the copies of row r (every lane commits one group)
         if (r < len) {
           int32_t rp[4], dp;
           row_offsets(r, rp, dp);
           const int deg = (rp[1] - rp[0]) >> 2;
-          const int kk = LOWER ? lane : dp + 1 + lane;
-          const bool mine = LOWER ? kk < dp : kk < deg;
           SweepSlot<T>& sl = ring[r % ILU_PF];
           constexpr int CH = (int)(4 * sizeof(T)) / 16;  // 16-byte pieces of a 4-value block row
           constexpr int EPC = 16 / (int)sizeof(T);        // values per piece
-          if (mine) {
-            for (int m = 0; m < 4; ++m)
-              for (int c = 0; c < CH; ++c)
-                cp_async16(&sl.f[lane][4 * m + c * EPC], F + rp[m] + 4 * kk + c * EPC);
-            cp_async4(&sl.col[lane], colidx + rp[0] + 4 * kk);
+          if (split_rows(dp, deg)) {
+            // two lanes per block: lane 2 bl + h copies rows 2h, 2h + 1 of block bl
+            const int bl = lane >> 1, h = lane & 1;
+            const int kk = LOWER ? bl : dp + 1 + bl;
+            if (LOWER ? kk < dp : kk < deg) {
+              const int32_t ra = h ? rp[2] : rp[0], rb = h ? rp[3] : rp[1];
+              for (int c = 0; c < CH; ++c) {
+                cp_async16(&sl.f[lane][c * EPC], F + ra + 4 * kk + c * EPC);
+                cp_async16(&sl.f[lane][4 + c * EPC], F + rb + 4 * kk + c * EPC);
+              }
+              cp_async4(&sl.col[lane], colidx + rp[0] + 4 * kk);
+            }
+          } else {
+            const int kk = LOWER ? lane : dp + 1 + lane;
+            if (LOWER ? kk < dp : kk < deg) {
+              for (int m = 0; m < 4; ++m)
+                for (int c = 0; c < CH; ++c)
+                  cp_async16(&sl.f[lane][4 * m + c * EPC], F + rp[m] + 4 * kk + c * EPC);
+              cp_async4(&sl.col[lane], colidx + rp[0] + 4 * kk);
+            }
           }
           if (!LOWER && writer) {
             const int64_t ir = r_hi - 1 - r;
@@ -429,10 +517,16 @@ __global__ void __launch_bounds__(W * 32)
         const int64_t i = LOWER ? r_lo + r : r_hi - 1 - r;
         issue(r + ILU_PF - 1);
         cp_wait<ILU_PF - 1>();  // this thread's copies of row r have landed
+        __syncwarp();           // ... and every lane's (U_ii^-1 rows are read across lanes)
         const SweepSlot<T>& sl = ring[r % ILU_PF];
         int32_t rp[4], dp;
         row_offsets(r, rp, dp);
         const int deg = (rp[1] - rp[0]) >> 2;
+        if (split_rows(dp, deg)) {
+          if (!split_row<T, LOWER>(sl, r, i, dp, deg, lane, o_rhs, sx, a, b, pub, out, n0, ep, err))
+            break;  // an error was recorded; the CTA stops after this chunk
+          continue;
+        }
         const int kk = LOWER ? lane : dp + 1 + lane;
         const bool mine = LOWER ? kk < dp : kk < deg;
         T rhs = T(0);
