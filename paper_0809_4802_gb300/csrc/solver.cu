@@ -27,33 +27,70 @@ void free_solver(SolverWork& s) {
 // ---------------------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------------------
-// y = A x over the rows of nodes [n0, n1) (row0 = 4 n0); x and y are compact (column c of the
-// block is x[c - row0]). One warp per scalar row; FP32 accumulation when matrix and vectors are
-// FP32 (the inner solve of the mixed mode), FP64 otherwise.
+// y = S x on the rows of nodes [node0, node0 + n_nodes): one warp per node (its four scalar rows
+// share one column pattern of 4x4 blocks), one lane per block, so a column index is read once per
+// block instead of once per value. x and y are compact (x[c - 4 node0], y[4 (node - node0) + q]).
+// FP32 accumulation when matrix and vectors are FP32 (the inner solve of the mixed mode), FP64
+// otherwise.
+template <typename T> struct Row4;
+template <> struct Row4<float> {
+  __device__ __forceinline__ static void ld(const float* p, float o[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
+};
+template <> struct Row4<double> {
+  __device__ __forceinline__ static void ld(const double* p, double o[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+};
+
 template <typename T, typename VT>
 __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ colidx,
                                                    const T* __restrict__ val,
                                                    const VT* __restrict__ x, VT* __restrict__ y,
-                                                   int64_t row0, int64_t n_rows) {
+                                                   int64_t node0, int64_t n_nodes) {
   using Acc = typename std::conditional<sizeof(T) == 4 && sizeof(VT) == 4, float, double>::type;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nd = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (row >= n_rows) return;
-  const int32_t b = rowptr[row0 + row], e = rowptr[row0 + row + 1];
-  Acc s = Acc(0);
-  for (int32_t k = b + lane; k < e; k += 32) s = fma((Acc)val[k], (Acc)x[colidx[k] - row0], s);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = VT(s);
+  if (nd >= n_nodes) return;  // uniform over the warp
+  const int64_t g = node0 + nd;
+  int32_t rp[4];
+  for (int m = 0; m < 4; ++m) rp[m] = rowptr[4 * g + m];
+  const int deg = (rp[1] - rp[0]) >> 2;
+  Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+  for (int kk = lane; kk < deg; kk += 32) {
+    const int64_t c = (int64_t)colidx[rp[0] + 4 * kk] - 4 * node0;
+    Acc xv[4];
+    for (int m = 0; m < 4; ++m) xv[m] = (Acc)x[c + m];
+    for (int r = 0; r < 4; ++r) {
+      T v[4];
+      Row4<T>::ld(val + rp[r] + 4 * kk, v);
+      for (int m = 0; m < 4; ++m) acc[r] = fma((Acc)v[m], xv[m], acc[r]);
+    }
+  }
+  // reduce-scatter of the four sums over the warp: lane L ends with component (L >> 3) & 3
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const Acc s0 = h16 ? acc[0] : acc[2], s1 = h16 ? acc[1] : acc[3];
+  const Acc b0 = (h16 ? acc[2] : acc[0]) + __shfl_xor_sync(0xffffffffu, s0, 16);
+  const Acc b1 = (h16 ? acc[3] : acc[1]) + __shfl_xor_sync(0xffffffffu, s1, 16);
+  Acc t = (h8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h8 ? b0 : b1, 8);
+  t += __shfl_xor_sync(0xffffffffu, t, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  if ((lane & 7) == 0) y[4 * nd + (lane >> 3)] = VT(t);
 }
 
 template <typename T, typename VT>
 static int spmv(const Mesh& m, const SysRange& R, const void* values, const VT* x, VT* y,
                 cudaStream_t st) {
-  const int64_t n = 4 * R.nodes();
-  const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
-  spmv_kernel<T, VT><<<blocks, 256, 0, st>>>(m.rowptr, m.colidx, (const T*)values, x, y,
-                                             4 * R.n0, n);
+  const int64_t nodes = R.nodes();
+  const unsigned blocks = (unsigned)((nodes * 32 + 255) / 256);
+  spmv_kernel<T, VT><<<blocks, 256, 0, st>>>(m.rowptr, m.colidx, (const T*)values, x, y, R.n0,
+                                             nodes);
   return 1;
 }
 
@@ -124,7 +161,7 @@ __global__ void block_apply_kernel(const double* __restrict__ Dinv, const VT* __
   }
 }
 
-constexpr int DOT_BLOCKS = 256, DOT_THREADS = 256;
+constexpr int DOT_THREADS = 256;
 // device scratch layout (doubles): Gram-Schmidt coefficients of the two passes, a norm, the
 // least-squares solution, then per-block partial sums
 constexpr int MAX_RESTART = 480;
