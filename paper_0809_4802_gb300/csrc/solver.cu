@@ -218,10 +218,14 @@ __global__ void __launch_bounds__(MD_THREADS) mdot_kernel(const VT* __restrict__
   double acc[MD_K];
 #pragma unroll
   for (int t = 0; t < MD_K; ++t) acc[t] = 0.0;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   if (quad && sizeof(VT) == 4) {
-    // FP32 vectors: the four products of a quad are summed in FP32 and the quad's partial is
-    // accumulated in FP64 (one conversion and one FP64 add per quad and vector: the FP64 pipe,
-    // 1/64 of FP32, would otherwise bound the kernel)
+    // FP32 vectors: each thread's products and the warp's sum (at most 128 products per warp in
+    // the usual one quad per thread) are formed in FP32, the warps' and blocks' sums in FP64: the
+    // FP64 pipe, 1/64 of FP32, would otherwise bound the kernel
+    float accf[MD_K];
+#pragma unroll
+    for (int t = 0; t < MD_K; ++t) accf[t] = 0.f;
     const int64_t n4 = n >> 2;
     const float4* w4 = reinterpret_cast<const float4*>(w);
     for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n4; i += (int64_t)nb * MD_THREADS) {
@@ -233,35 +237,42 @@ __global__ void __launch_bounds__(MD_THREADS) mdot_kernel(const VT* __restrict__
 #pragma unroll
       for (int t = 0; t < MD_K; ++t)
         if (k0 + t < m)
-          acc[t] += (double)fmaf(vv[t].w, wv.w, fmaf(vv[t].z, wv.z, fmaf(vv[t].y, wv.y, vv[t].x * wv.x)));
+          accf[t] = fmaf(vv[t].w, wv.w, fmaf(vv[t].z, wv.z, fmaf(vv[t].y, wv.y, fmaf(vv[t].x, wv.x, accf[t]))));
     }
-  } else if (quad) {
-    const int64_t n4 = n >> 2;
-    for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n4; i += (int64_t)nb * MD_THREADS) {
-      double wv[4], vv[MD_K][4];
-      Quad<VT>::ld(w + 4 * i, wv);
 #pragma unroll
-      for (int t = 0; t < MD_K; ++t)
-        if (k0 + t < m) Quad<VT>::ld(V + (int64_t)(k0 + t) * ld + 4 * i, vv[t]);
-#pragma unroll
-      for (int t = 0; t < MD_K; ++t)
-        if (k0 + t < m)
-          acc[t] = fma(vv[t][3], wv[3], fma(vv[t][2], wv[2], fma(vv[t][1], wv[1], fma(vv[t][0], wv[0], acc[t]))));
+    for (int t = 0; t < MD_K; ++t) {
+      float v = accf[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[t][wp] = (double)v;
     }
   } else {
-    for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n; i += (int64_t)nb * MD_THREADS) {
-      const double wi = (double)w[i];
+    if (quad) {
+      const int64_t n4 = n >> 2;
+      for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n4; i += (int64_t)nb * MD_THREADS) {
+        double wv[4], vv[MD_K][4];
+        Quad<VT>::ld(w + 4 * i, wv);
 #pragma unroll
-      for (int t = 0; t < MD_K; ++t)
-        if (k0 + t < m) acc[t] = fma((double)V[(int64_t)(k0 + t) * ld + i], wi, acc[t]);
+        for (int t = 0; t < MD_K; ++t)
+          if (k0 + t < m) Quad<VT>::ld(V + (int64_t)(k0 + t) * ld + 4 * i, vv[t]);
+#pragma unroll
+        for (int t = 0; t < MD_K; ++t)
+          if (k0 + t < m)
+            acc[t] = fma(vv[t][3], wv[3], fma(vv[t][2], wv[2], fma(vv[t][1], wv[1], fma(vv[t][0], wv[0], acc[t]))));
+      }
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n; i += (int64_t)nb * MD_THREADS) {
+        const double wi = (double)w[i];
+#pragma unroll
+        for (int t = 0; t < MD_K; ++t)
+          if (k0 + t < m) acc[t] = fma((double)V[(int64_t)(k0 + t) * ld + i], wi, acc[t]);
+      }
     }
-  }
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-  for (int t = 0; t < MD_K; ++t) {
-    double v = acc[t];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[t][wp] = v;
+    for (int t = 0; t < MD_K; ++t) {
+      double v = acc[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[t][wp] = v;
+    }
   }
   __syncthreads();
   if (threadIdx.x < MD_K && k0 + (int)threadIdx.x < m) {
