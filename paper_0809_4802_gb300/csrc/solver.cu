@@ -1000,11 +1000,31 @@ int vms_newton_solve_to(vms_ctx* ctx, double target, int maxit, int* iters, doub
   if (hist) hist[0] = r0;
   r = r0;
   int k = 0;
+  double r_prev = 0.0, eta_prev = 0.0;
+  const bool fp64 = !ctx_fp32(ctx);
   while (k < maxit && r > target) {
     if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
-    // inexact Newton: forcing term proportional to the current relative residual, but never
-    // tighter than the target needs (a linear residual of eta * r <= target / 2)
-    const double eta = std::min(0.5, std::max({std::min(1e-2, 0.1 * r / r0), 0.5 * target / r, 1e-12}));
+    // inexact Newton, never tighter than the target needs (a linear residual of eta r <= target/2).
+    // FP64: Eisenstat and Walker's choice 2 (gamma 0.5, exponent 2, eta_0 0.05, safeguarded by
+    // gamma eta_prev^2 when that exceeds 0.1). Mixed: a forcing term proportional to the relative
+    // residual, capped at 1e-2 - the looser late solves of the former leave near-null pressure
+    // components that the FP32 inner solve cannot resolve, and the last Newton system then does not
+    // converge within the iteration limit.
+    double eta;
+    if (fp64) {
+      if (k == 0) {
+        eta = 0.05;
+      } else {
+        eta = 0.5 * (r / r_prev) * (r / r_prev);
+        const double guard = 0.5 * eta_prev * eta_prev;
+        if (guard > 0.1) eta = std::max(eta, guard);
+      }
+    } else {
+      eta = std::min(1e-2, 0.1 * r / r0);
+    }
+    eta = std::min(0.5, std::max({eta, 0.5 * target / r, 1e-12}));
+    r_prev = r;
+    eta_prev = eta;
     int it = 0;
     double rel = 0.0;
     if (int rc = solve_impl(ctx, whole(ctx), -1, eta, 3000, NEWTON_RESTART, MAX_RESTART, 1, 0.1, &it, &rel)) return rc;
