@@ -267,9 +267,10 @@ int vms_newton_step(vms_ctx* ctx, double* res_norm);
  * maxit+1 doubles, host) receives the residual norms, *iters the iterations taken. Inexact
  * Newton: each linear solve (GMRES(150), the cycle doubled up to 480 whenever one does not halve
  * the residual, at most 3000 iterations) stops at the relative residual eta, capped at 0.5 and
- * at least rtol ||R^0|| / (2 ||R||): in FP64 mode Eisenstat and Walker's choice 2 (eta_0 = 0.05,
- * eta_k = 0.5 (||R^k|| / ||R^{k-1}||)^2, or 0.5 eta_{k-1}^2 when that exceeds 0.1); in mixed mode
- * min(1e-2, 0.1 ||R|| / ||R^0||). A solve that stops above eta but below 0.1 is still applied.
+ * at least rtol ||R^0|| / (2 ||R||): Eisenstat and Walker's choice 2 (eta_0 = 0.05,
+ * eta_k = 0.5 (||R^k|| / ||R^{k-1}||)^2, or 0.5 eta_{k-1}^2 when that exceeds 0.1), in mixed mode
+ * only while ||R|| > 1e-3 ||R^0|| and min(1e-2, 0.1 ||R|| / ||R^0||) after. A solve that stops
+ * above eta but below 0.1 is still applied.
  * Errors: VMS_ERR_NEWTON_DIVERGED, VMS_ERR_KRYLOV_MAXIT and those of the steps. */
 int vms_newton_solve(vms_ctx* ctx, double rtol, int maxit, int* iters, double* hist);
 

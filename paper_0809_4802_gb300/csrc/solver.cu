@@ -1004,14 +1004,14 @@ int vms_newton_solve_to(vms_ctx* ctx, double target, int maxit, int* iters, doub
   const bool fp64 = !ctx_fp32(ctx);
   while (k < maxit && r > target) {
     if (int rc = vms_assemble_newton_schur(ctx, nullptr)) return rc;
-    // inexact Newton, never tighter than the target needs (a linear residual of eta r <= target/2).
-    // FP64: Eisenstat and Walker's choice 2 (gamma 0.5, exponent 2, eta_0 0.05, safeguarded by
-    // gamma eta_prev^2 when that exceeds 0.1). Mixed: a forcing term proportional to the relative
-    // residual, capped at 1e-2 - the looser late solves of the former leave near-null pressure
-    // components that the FP32 inner solve cannot resolve, and the last Newton system then does not
-    // converge within the iteration limit.
+    // inexact Newton, never tighter than the target needs (a linear residual of eta r <= target/2):
+    // Eisenstat and Walker's choice 2 (gamma 0.5, exponent 2, eta_0 0.05, safeguarded by
+    // gamma eta_prev^2 when that exceeds 0.1). In mixed precision only while ||R|| > 1e-3 ||R^0||,
+    // then a forcing term proportional to the relative residual, capped at 1e-2: the looser late
+    // solves of the former leave near-null pressure components that the FP32 inner solve cannot
+    // resolve, and the last Newton system then does not converge within the iteration limit.
     double eta;
-    if (fp64) {
+    if (fp64 || r > 1e-3 * r0) {
       if (k == 0) {
         eta = 0.05;
       } else {
