@@ -7,13 +7,14 @@
 //   L_ik = A_ik U_kk^-1,   A_ij -= L_ik U_kj   for every block j > k present in both rows,
 // after which U_ii = A_ii and its inverse is kept for the backward sweep.
 //
-// GPU mapping: one warp owns one node row at a time and claims rows in order from a counter, so a
-// row only ever waits for rows claimed earlier, by warps that are already running. A row publishes
-// itself by writing its epoch into a flag with release semantics; dependants poll the flag with
-// acquire loads (bounded: after ILU_SPIN_LIMIT polls the kernel records a timeout and returns),
-// and read data published in the same launch through L2 (ld.global.cg), never through L1. The
-// triangular sweeps take rows in chunks per CTA, so that most dependencies (the previous rows of
-// the same chunk) are resolved through shared memory instead of L2.
+// GPU mapping of the factorisation: one warp owns one node row at a time and claims rows in order
+// from a counter, so a row only ever waits for rows claimed earlier, by warps that are already
+// running. A row publishes itself by writing its epoch into a flag with release semantics;
+// dependants poll the flag with acquire loads (bounded: after ILU_SPIN_LIMIT polls the kernel
+// records a timeout and returns), and read data published in the same launch through L2
+// (ld.global.cg), never through L1. The triangular sweeps claim chunks of grid-line segments per
+// CTA, one segment per warp (see ilu_sweep_kernel), so that most dependencies are resolved in
+// registers and shared memory instead of L2.
 #include <algorithm>
 #include <vector>
 
@@ -165,9 +166,9 @@ __global__ void __launch_bounds__(ILU_FWARPS * 32)
 
 // ---------------------------------------------------------------------------------------------
 // sweeps: y = L^-1 v (rows ascending), z = U^-1 y (rows descending)
-// One warp per node row, one lane per neighbour block of the row (a node has at most 32
-// neighbours): every lane waits for its own neighbour at the same time, so a row costs one
-// round trip to L2 once its last dependency is published.
+// A warp solves the rows of one grid-line segment in order, one lane per neighbour block of the
+// row (a node has at most 32 neighbours; FP64 rows with at most 16 blocks on the sweep's side take
+// two lanes per block): every lane waits for its own neighbour at the same time.
 // ---------------------------------------------------------------------------------------------
 
 // FP32 sweeps publish every value in one 64-bit word together with the sweep's epoch (low half:

@@ -2,10 +2,11 @@
 // Newton-Schur driver (Sections 4.2 and 5; the paper used a Krylov solver with tolerance 1e-12 and
 // at most 50 iterations, Section 6).
 //
-// Solver: restarted GMRES(m), right-preconditioned by the inverses of the 4x4 diagonal node blocks,
-// classical Gram-Schmidt with one re-orthogonalisation pass (CGS2). In mixed precision the Krylov
-// vectors and the matrix are FP32 (dot products accumulate in FP64) and an outer FP64 iterative
-// refinement recomputes r = b - S x in FP64 until the tolerance is met.
+// Solver: restarted GMRES(m), right-preconditioned by block ILU(0) (precond.cu) or the inverses of
+// the 4x4 diagonal node blocks, classical Gram-Schmidt with one re-orthogonalisation pass (CGS2).
+// In mixed precision the Krylov vectors and the matrix are FP32 (dot products summed in FP32 within
+// a warp and in FP64 across warps) and an outer FP64 iterative refinement recomputes r = b - S x
+// in FP64 until the tolerance is met.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
