@@ -196,3 +196,38 @@ def test_ilu0_beats_block_jacobi_on_cavity(vms, prec):
         out[precond] = it
         ctx.close()
     assert 3 * out[vms.PRECOND_ILU0] <= out[vms.PRECOND_BLOCK_JACOBI], out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ilu0_row_with_more_than_16_lower_blocks(vms, prec):
+    """The 2^3 distorted problem renumbered so that the centre node comes last: its row has 26
+    lower neighbour blocks, more than the two-lanes-per-block layout of the FP64 sweeps takes, so
+    that row is solved with one lane per block. The solve still matches a direct solution."""
+    mesh, bc, u, beta = distorted_problem(2, 11)
+    order = np.arange(mesh.n_nodes)
+    centre = int(np.nonzero(np.all(mesh.node_ijk == 1, axis=1))[0][0])
+    order[[centre, mesh.n_nodes - 1]] = order[[mesh.n_nodes - 1, centre]]
+    new_of_old = np.empty_like(order)
+    new_of_old[order] = np.arange(mesh.n_nodes)
+    xyz = np.ascontiguousarray(mesh.xyz[order])
+    conn = np.ascontiguousarray(new_of_old[mesh.conn].astype(np.int32))
+    dofs = np.sort(4 * new_of_old[bc.dofs // 4] + bc.dofs % 4)
+    u2 = np.ascontiguousarray(u[order])
+    ctx = vms.Context(0, prec)
+    ctx.set_preconditioner(vms.PRECOND_ILU0)
+    ctx.mesh_upload(xyz, conn, dofs, np.zeros(dofs.size))
+    ctx.set_params(0.05)
+    ctx.state_upload(u2, beta)
+    ctx.assemble()
+    rowptr, colidx, vals, rhs = ctx.csr_host()
+    last = 4 * (mesh.n_nodes - 1)
+    assert np.all(colidx[rowptr[last]:rowptr[last + 1]] // 4 <= mesh.n_nodes - 1)
+    assert (rowptr[last + 1] - rowptr[last]) // 4 == 27   # 26 lower blocks and the diagonal
+    G = sp.csr_matrix((vals.astype(np.float64), colidx, rowptr))
+    du_ref = spla.spsolve(G.tocsc(), -rhs)
+    it, rel = ctx.solve(rtol=1e-10, maxit=3000, restart=110, update=True)
+    assert rel <= 1e-10 and it > 0
+    du = (ctx.state_download()[0] - u2).reshape(-1)
+    assert np.linalg.norm(G @ du + rhs) <= 2e-10 * np.linalg.norm(rhs)
+    assert np.abs(du - du_ref).max() <= 1e-5 * np.abs(du_ref).max()
+    ctx.close()
