@@ -551,8 +551,8 @@ def main():
     ap.add_argument("--ws-n", type=int, default=16)
     ap.add_argument("--ws-nx", type=int, default=150)
     ap.add_argument("--ws-nyz", type=int, default=28)
-    ap.add_argument("--ws-train", type=int, default=20)
-    ap.add_argument("--ws-eval", type=int, default=30)
+    ap.add_argument("--ws-train", type=int, default=100)
+    ap.add_argument("--ws-eval", type=int, default=200)
     ap.add_argument("--ws-epochs", type=int, default=60)
     ap.add_argument("--graph", action="store_true", help="replay the assembly as a CUDA graph")
     ap.add_argument("--newton", choices=["auto", "on", "off"], default="auto",
