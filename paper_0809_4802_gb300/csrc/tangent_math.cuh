@@ -402,12 +402,16 @@ VMS_HD void tan_phase3e(int lane, const WarpArea<T>& W, LaneAcc<T>& A, bool accu
   if (sizeof(T) == 4 && accurate) {
     VMS_UNROLL
     for (int i = 0; i < 4; ++i) {
-      const float ca[3] = {-W.Kcf[4 * a0 + i][0], -W.Kcf[4 * a0 + i][1], -W.Kcf[4 * a0 + i][2]};
-      const float cb[3] = {-W.Kcf[4 * a1 + i][0], -W.Kcf[4 * a1 + i][1], -W.Kcf[4 * a1 + i][2]};
+      const float ca[3] = {(float)-W.Kcf[4 * a0 + i][0], (float)-W.Kcf[4 * a0 + i][1],
+                           (float)-W.Kcf[4 * a0 + i][2]};
+      const float cb[3] = {(float)-W.Kcf[4 * a1 + i][0], (float)-W.Kcf[4 * a1 + i][1],
+                           (float)-W.Kcf[4 * a1 + i][2]};
       VMS_UNROLL
       for (int k = 0; k < 4; ++k) {
-        const float xh[3] = {W.Xs[0][4 * b + k], W.Xs[1][4 * b + k], W.Xs[2][4 * b + k]};
-        const float xl[3] = {W.Xl[0][4 * b + k], W.Xl[1][4 * b + k], W.Xl[2][4 * b + k]};
+        const float xh[3] = {(float)W.Xs[0][4 * b + k], (float)W.Xs[1][4 * b + k],
+                             (float)W.Xs[2][4 * b + k]};
+        const float xl[3] = {(float)W.Xl[0][4 * b + k], (float)W.Xl[1][4 * b + k],
+                             (float)W.Xl[2][4 * b + k]};
         auto acc = A.K[4 * i + k];
         acc.x = comp_dot3((float)acc.x, ca, xh, xl);
         acc.y = comp_dot3((float)acc.y, cb, xh, xl);
