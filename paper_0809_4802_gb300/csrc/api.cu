@@ -122,7 +122,7 @@ void free_mesh(vms_ctx* c) {
   Work& w = c->work;
   dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recW); dfree(w.recKinv);
   dfree(w.recY); dfree(w.resid); dfree(w.partial); dfree(w.flags);
-  dfree(w.f32.xyz); dfree(w.f32.u); dfree(w.f32.beta);
+  dfree(w.f32.u); dfree(w.f32.beta);
   cudaStream_t aux = w.aux;
   cudaEvent_t fork = w.fork, join = w.join;
   w = Work();
@@ -526,14 +526,8 @@ static int mesh_upload_impl(vms_ctx* ctx, int npe, int64_t n_nodes, const double
   CK(cudaMalloc(&w.recW, sizeof(double) * 96 * n_elems));
   CK(cudaMalloc(&w.recKinv, sizeof(double) * 9 * n_elems));
   CK(cudaMalloc(&w.recY, sizeof(double) * 3 * n_elems));
-  CK(cudaMalloc(&w.f32.xyz, sizeof(float4) * n_nodes));
   CK(cudaMalloc(&w.f32.u, sizeof(float4) * n_nodes));
   CK(cudaMalloc(&w.f32.beta, sizeof(float) * 3 * n_elems));
-  {
-    // FP32 coordinates once per mesh (the mixed-precision tangent reads them)
-    KScope k(ctx, VMS_K_FILL);
-    k.add(launch_to_fp32(m, s, w.f32, true, ctx->stream));
-  }
   CK(cudaGetLastError());
   CK(cudaMalloc(&w.resid, sizeof(double) * (4 * n_nodes + 3 * n_elems)));
   CK(cudaMalloc(&w.partial, sizeof(double) * 1024));
@@ -631,7 +625,7 @@ static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
   }
   if (f32) {
     KScope k(ctx, VMS_K_FILL, st);
-    k.add(launch_to_fp32(m, ctx->state, w.f32, false, st));
+    k.add(launch_to_fp32(m, ctx->state, w.f32, st));
   }
   TangentOut o;
   o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv;
@@ -829,7 +823,7 @@ int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, 
   if (m.npe == 4) return element_matrices_tet(ctx, first, count, S, r, Kcc, Kcf, Kfc, Kff, Rcp, Rf);
   if (f32) {
     KScope k(ctx, VMS_K_FILL);
-    k.add(launch_to_fp32(m, ctx->state, w.f32, false, st));
+    k.add(launch_to_fp32(m, ctx->state, w.f32, st));
   }
   {
     KScope k(ctx, VMS_K_RESIDUAL);

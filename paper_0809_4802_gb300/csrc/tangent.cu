@@ -122,8 +122,7 @@ template <> struct NodeVec<float> { using type = float4; };
 
 template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
-    const typename NodeVec<T>::type* __restrict__ xyz, const typename NodeVec<T>::type* __restrict__ u,
-    const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
+    const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
     int nq, T nut, T tau, const double* __restrict__ nu_e, double visc_factor,
     const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
     const double* __restrict__ beta64, const double* __restrict__ tab64, int64_t first,
@@ -148,9 +147,19 @@ __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
     if (lane < 8) {
       const int nd = conn[8 * e + lane];
       W.nd[lane] = nd;
-      const auto x = xyz[nd];
+      const double4_32a x = xyz64[nd];
       const auto w = u[nd];
-      W.X[lane][0] = x.x; W.X[lane][1] = x.y; W.X[lane][2] = x.z;
+      if constexpr (sizeof(T) == 4) {
+        // FP32 geometry from the coordinates relative to the element's first node, taken in
+        // FP64: J is unchanged (the basis gradients sum to zero), while FP32 copies of absolute
+        // coordinates far from the origin would resolve the element's extent only to
+        // |x| * 6e-8 / h (2e-5 at x = 30 with h = 1/13)
+        W.X[lane][0] = (float)(x.x - __shfl_sync(0xffu, x.x, 0));
+        W.X[lane][1] = (float)(x.y - __shfl_sync(0xffu, x.y, 0));
+        W.X[lane][2] = (float)(x.z - __shfl_sync(0xffu, x.z, 0));
+      } else {
+        W.X[lane][0] = x.x; W.X[lane][1] = x.y; W.X[lane][2] = x.z;
+      }
       W.V[lane][0] = w.x; W.V[lane][1] = w.y; W.V[lane][2] = w.z;
     } else if (lane < 11) {
       W.beta[lane - 8] = beta[3 * e + lane - 8];
@@ -292,30 +301,26 @@ __global__ void __launch_bounds__(256) finish_kernel(
   }
 }
 
-// FP32 copies of the node records and bubble coefficients for the mixed-precision tangent.
-__global__ void to_fp32_kernel(const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u,
-                               const double* __restrict__ beta, float4* __restrict__ xyz32,
+// FP32 copies of the nodal state and bubble coefficients for the mixed-precision tangent (its
+// geometry comes from the FP64 coordinates).
+__global__ void to_fp32_kernel(const double4_32a* __restrict__ u, const double* __restrict__ beta,
                                float4* __restrict__ u32, float* __restrict__ beta32,
-                               int64_t n_nodes, int64_t n_elems, int with_xyz) {
+                               int64_t n_nodes, int64_t n_elems) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += stride) {
     const double4_32a w = u[i];
     u32[i] = make_float4((float)w.x, (float)w.y, (float)w.z, (float)w.w);
-    if (with_xyz) {
-      const double4_32a x = xyz[i];
-      xyz32[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
-    }
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_elems; i += stride)
     beta32[i] = (float)beta[i];
 }
 
-int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, bool with_xyz, cudaStream_t st) {
+int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, cudaStream_t st) {
   const int64_t n = m.n_nodes > 3 * m.n_elems ? m.n_nodes : 3 * m.n_elems;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  to_fp32_kernel<<<(unsigned)blocks, 256, 0, st>>>(m.xyz, s.u, s.beta, c.xyz, c.u, c.beta,
-                                                   m.n_nodes, m.n_elems, with_xyz ? 1 : 0);
+  to_fp32_kernel<<<(unsigned)blocks, 256, 0, st>>>(s.u, s.beta, c.u, c.beta, m.n_nodes,
+                                                   m.n_elems);
   return 1;
 }
 
@@ -330,16 +335,15 @@ static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const K
   int64_t blocks = (count + WARPS - 1) / WARPS;
   if (blocks > 152 * 128) blocks = 152 * 128;
   using NV = typename NodeVec<T>::type;
-  const NV* xyz;
   const NV* u;
   const T* beta;
   if constexpr (sizeof(T) == 4) {
-    xyz = c32.xyz; u = c32.u; beta = c32.beta;
+    u = c32.u; beta = c32.beta;
   } else {
-    xyz = m.xyz; u = s.u; beta = s.beta;
+    u = s.u; beta = s.beta;
   }
   kern<<<(unsigned)blocks, WARPS * 32, smem, st>>>(
-      xyz, u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, s.u,
+      u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, s.u,
       s.beta, kp.tab64, first, count, elem_list, m.blk,
       m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
       reinterpret_cast<double*>(o.recW), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);

@@ -94,7 +94,6 @@ struct State {
 };
 
 struct Fp32Copy {
-  float4* xyz = nullptr;      // n_nodes (x, y, z, 0) in FP32
   float4* u = nullptr;        // n_nodes (v, p) in FP32
   float* beta = nullptr;      // n_elems * 3
 };
@@ -180,9 +179,8 @@ int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32
 int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOut& out,
                   int64_t first, int64_t count, const int32_t* elem_list, bool atomic,
                   cudaStream_t st);
-// FP32 copies of the node records (xyz only when with_xyz) and of beta.
-int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, bool with_xyz,
-                   cudaStream_t st);
+// FP32 copies of the nodal state and of beta.
+int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, cudaStream_t st);
 
 int launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
 int launch_dirichlet_diag(const Mesh& m, void* values, bool fp32, double* rhs, cudaStream_t st);
