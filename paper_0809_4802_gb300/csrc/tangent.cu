@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
     bool accurate = false;
     if constexpr (sizeof(T) == 4) {
       int ill = 0;
-      if (lane == 0) ill = kff_cond_inf(W) > KFF_FP64_COND;
+      if (lane == 0) ill = kff_cond_inf(W) > T(KFF_FP64_COND);
       accurate = __shfl_sync(0xffffffffu, ill, 0) != 0;  // warp-uniform
       if (accurate) {
         double K[9];

@@ -25,6 +25,7 @@
 #pragma once
 
 #include <cmath>
+#include <cstring>
 
 #include <vector_functions.h>
 #include <vector_types.h>
@@ -108,6 +109,7 @@ struct WarpArea {
   double Kff[9];
   double cof[9];
   double Kinv[9];
+  T KffT[9];       // K_ff summed in T (before widening)
   T KinvT[9];
   unsigned int flag;
   QpRec<T> qp[1];
@@ -293,6 +295,7 @@ VMS_HD void tan_phase3b(int lane, WarpArea<T>& W) {
   if (lane < 9) {
     T s = T(0);
     for (int l = 0; l < 32; ++l) s += W.kffp[l][lane];
+    W.KffT[lane] = s;
     W.Kff[lane] = (double)s;
   }
 }
@@ -312,7 +315,10 @@ VMS_HD void tan_phase3c(int lane, WarpArea<T>& W) {
 template <typename T>
 VMS_HD void tan_phase3d(int lane, WarpArea<T>& W) {
   const double det = W.Kff[0] * W.cof[0] + W.Kff[1] * W.cof[1] + W.Kff[2] * W.cof[2];
-  const bool bad = !(det != 0.0) || !(det - det == 0.0);
+  // zero or not finite, tested on the bits (an FP64 compare takes a whole FP64 issue slot)
+  uint64_t db;
+  memcpy(&db, &det, sizeof db);
+  const bool bad = (db << 1) == 0 || ((db >> 52) & 0x7ffu) == 0x7ffu;
   const double r = bad ? 0.0 : 1.0 / det;
   if (lane < 9) {
     const double v = W.cof[3 * (lane % 3) + lane / 3] * r;
@@ -322,15 +328,17 @@ VMS_HD void tan_phase3d(int lane, WarpArea<T>& W) {
   if (bad && lane == 0) W.flag |= 2u;
 }
 
-// Infinity-norm condition number of K_ff from its FP64 copy and inverse in shared memory (every
-// lane computes the same value).
+// Infinity-norm condition number of K_ff, in T, from the sums before widening and the inverse
+// rounded to T. It only chooses between two correct condensation paths (in FP32 the choice may
+// differ from an FP64 estimate only within rounding of the threshold), and in FP32 it takes no
+// FP64 issue slot.
 template <typename T>
-VMS_HD double kff_cond_inf(const WarpArea<T>& W) {
-  double nk = 0.0, ni = 0.0;
+VMS_HD T kff_cond_inf(const WarpArea<T>& W) {
+  T nk = T(0), ni = T(0);
   VMS_UNROLL
   for (int i = 0; i < 3; ++i) {
-    nk = fmax(nk, fabs(W.Kff[3 * i]) + fabs(W.Kff[3 * i + 1]) + fabs(W.Kff[3 * i + 2]));
-    ni = fmax(ni, fabs(W.Kinv[3 * i]) + fabs(W.Kinv[3 * i + 1]) + fabs(W.Kinv[3 * i + 2]));
+    nk = fmax(nk, fabs(W.KffT[3 * i]) + fabs(W.KffT[3 * i + 1]) + fabs(W.KffT[3 * i + 2]));
+    ni = fmax(ni, fabs(W.KinvT[3 * i]) + fabs(W.KinvT[3 * i + 1]) + fabs(W.KinvT[3 * i + 2]));
   }
   return nk * ni;
 }
