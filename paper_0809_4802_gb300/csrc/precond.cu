@@ -112,16 +112,17 @@ __global__ void __launch_bounds__(ILU_FWARPS * 32)
       __syncwarp();
       if (lane < 16) row[16 * kk + lane] = l;
       __syncwarp();
-      // A_ij -= L_ik U_kj over the pairs of this lower block, two pairs per step
+      // A_ij -= L_ik U_kj over the pairs of this lower block, two pairs per step (the products
+      // are subtracted one by one, so that each is a fused multiply-add)
       int32_t rk[4];
       for (int m = 0; m < 4; ++m) rk[m] = rowptr[4 * k + m];
       const int32_t pe = pptr[l0 + kk + 1];
       for (int32_t p = pptr[l0 + kk] + half; p < pe; p += 2) {
         const uint32_t pr = pairs[p];
         const int jj = pr & 255, jk = pr >> 8;
-        T s = T(0);
-        for (int m = 0; m < 4; ++m) s += row[16 * kk + 4 * q + m] * __ldcg(F + rk[m] + 4 * jk + c);
-        row[16 * jj + 4 * q + c] -= s;
+        T s = row[16 * jj + 4 * q + c];
+        for (int m = 0; m < 4; ++m) s -= row[16 * kk + 4 * q + m] * __ldcg(F + rk[m] + 4 * jk + c);
+        row[16 * jj + 4 * q + c] = s;
       }
       __syncwarp();
     }
@@ -146,13 +147,13 @@ __global__ void __launch_bounds__(ILU_FWARPS * 32)
       dt += __shfl_xor_sync(FULL, dt, 2);
       const double det = __shfl_sync(FULL, dt, 0);
       // singular unless |det| is a fair fraction of the product of the row norms (Hadamard's
-      // bound; independent of the rows' scales)
+      // bound; independent of the rows' scales), compared squared: det^2 > 1e-28 prod |row|^2
       double rn = dv * dv;
       rn += __shfl_xor_sync(FULL, rn, 1);
       rn += __shfl_xor_sync(FULL, rn, 2);
-      const double hb = sqrt(__shfl_sync(FULL, rn, 0)) * sqrt(__shfl_sync(FULL, rn, 4)) *
-                        sqrt(__shfl_sync(FULL, rn, 8)) * sqrt(__shfl_sync(FULL, rn, 12));
-      const bool good = isfinite(det) && hb > 0.0 && fabs(det) > 1e-14 * hb;
+      const double hb2 = __shfl_sync(FULL, rn, 0) * __shfl_sync(FULL, rn, 4) *
+                         __shfl_sync(FULL, rn, 8) * __shfl_sync(FULL, rn, 12);
+      const bool good = isfinite(det) && hb2 > 0.0 && det * det > 1e-28 * hb2;
       if (!good && lane == 0) atomicCAS(err, 0, ILU_ERR_PIVOT);
       if (lane < 16) Dinv[16 * i + 4 * c + r] = good ? T(cf / det) : T(r == c ? 1.0 : 0.0);
     }
