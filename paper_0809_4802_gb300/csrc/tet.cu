@@ -250,62 +250,111 @@ __device__ __forceinline__ void tet_element(int a, int64_t e, const double4_32a*
     E.g[0][j] = -(E.Ji[0][j] + E.Ji[1][j] + E.Ji[2][j]);
     E.ga[j] = sel4(a, E.g[0][j], E.g[1][j], E.g[2][j], E.g[3][j]);
   }
+  // The element constants below are the same on the group's four lanes. Each lane forms one part
+  // of each (its own node's, or row / column a), in the same instruction stream as the others,
+  // and the parts are exchanged by shuffles within the group: the FP64 pipe, which takes a whole
+  // issue slot per warp instruction, then does each constant once per element instead of on all
+  // four lanes.
+  const int gb = threadIdx.x & 28;  // first lane of the group
+  auto from = [gb](double v, int src) { return __shfl_sync(0xffffffffu, v, gb | src); };
+  auto gsum = [](double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v + __shfl_xor_sync(0xffffffffu, v, 2);
+  };
+  // w_c: component a of node c's velocity (a < 3) or its pressure (a = 3)
+  double w[4];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int c = 0; c < 4; ++c) w[c] = sel4(a, V[c][0], V[c][1], V[c][2], P[c]);
+  // G[i][j] = sum_c V_c[i] g_c[j]: row a on lane a (lane 3 forms the pressure gradient, unused)
+  {
+    double Ga[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      E.G[i][j] = V[0][i] * E.g[0][j] + V[1][i] * E.g[1][j] + V[2][i] * E.g[2][j] + V[3][i] * E.g[3][j];
-  // reference-frame components Vr_c = Jinv V_c, br = Jinv beta
-  double Vr[4][3], br[3];
+      Ga[j] = w[0] * E.g[0][j] + w[1] * E.g[1][j] + w[2] * E.g[2][j] + w[3] * E.g[3][j];
 #pragma unroll
-  for (int al = 0; al < 3; ++al) {
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) Vr[c][al] = E.Ji[al][0] * V[c][0] + E.Ji[al][1] * V[c][1] + E.Ji[al][2] * V[c][2];
-    br[al] = E.Ji[al][0] * E.beta[0] + E.Ji[al][1] * E.beta[1] + E.Ji[al][2] * E.beta[2];
+      for (int j = 0; j < 3; ++j) E.G[i][j] = from(Ga[j], i);
+  }
+  // Ub[j] = int b v_j: component a on lane a
+  {
+    const double ba = sel4(a, E.beta[0], E.beta[1], E.beta[2], 0.0);
+    const double ub = M[TM_M1B] * w[0] + M[TM_M1B + 1] * w[1] + M[TM_M1B + 2] * w[2] +
+                      M[TM_M1B + 3] * w[3] + M[TM_MBB] * ba;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) E.Ub[j] = from(ub, j);
   }
   const double* M2a = E.m2a;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
+  for (int j = 0; j < 3; ++j)
     E.Ua[j] = M2a[0] * V[0][j] + M2a[1] * V[1][j] + M2a[2] * V[2][j] + M2a[3] * V[3][j] + E.m1ba * E.beta[j];
-    E.Ub[j] = M[TM_M1B] * V[0][j] + M[TM_M1B + 1] * V[1][j] + M[TM_M1B + 2] * V[2][j] +
-              M[TM_M1B + 3] * V[3][j] + M[TM_MBB] * E.beta[j];
+  // reference-frame components Vr_c = Jinv V_c (node c's on lane c) and br = Jinv beta
+  double Vra[3], Vr[4][3], br[3];
+  {
+    double Va[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Va[j] = sel4(a, V[0][j], V[1][j], V[2][j], V[3][j]);
+#pragma unroll
+    for (int al = 0; al < 3; ++al) {
+      Vra[al] = E.Ji[al][0] * Va[0] + E.Ji[al][1] * Va[1] + E.Ji[al][2] * Va[2];
+      br[al] = E.Ji[al][0] * E.beta[0] + E.Ji[al][1] * E.beta[1] + E.Ji[al][2] * E.beta[2];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int al = 0; al < 3; ++al) Vr[c][al] = from(Vra[al], c);
   }
-  double Aa = 0.0, Ab = 0.0, Bd = 0.0;
+  double Aa = 0.0, Bd = 0.0;
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      Aa += E.m2da[3 * c + al] * Vr[c][al];
-      Ab += M[TM_M1BD + 3 * c + al] * Vr[c][al];
-    }
+    for (int c = 0; c < 4; ++c) Aa += E.m2da[3 * c + al] * Vr[c][al];
     Aa += E.m1bda[al] * br[al];
-    Ab += M[TM_MBBD + al] * br[al];
     Bd += E.m1da[al] * br[al];
   }
   E.Aa = Aa;
-  E.Ab = Ab;
   E.Bd = Bd;
+  // Ab = int b v.d: node a's terms on lane a, summed over the group
+  {
+    double ab = 0.0;
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+      ab += sel4(a, M[TM_M1BD + al], M[TM_M1BD + 3 + al], M[TM_M1BD + 6 + al], M[TM_M1BD + 9 + al]) * Vra[al];
+    E.Ab = gsum(ab) + M[TM_MBBD] * br[0] + M[TM_MBBD + 1] * br[1] + M[TM_MBBD + 2] * br[2];
+  }
   E.Pbar = M[TM_M1] * P[0] + M[TM_M1 + 1] * P[1] + M[TM_M1 + 2] * P[2] + M[TM_M1 + 3] * P[3];
-  double Pd[3];
+  // column a of Jinv (lane 3: zero)
+  double Jc[3];
 #pragma unroll
-  for (int al = 0; al < 3; ++al)
-    Pd[al] = M[TM_M1D + al] * P[0] + M[TM_M1D + 3 + al] * P[1] + M[TM_M1D + 6 + al] * P[2] + M[TM_M1D + 9 + al] * P[3];
-  double JJ[3][3];  // Jinv Jinv^T
+  for (int al = 0; al < 3; ++al) Jc[al] = sel4(a, E.Ji[al][0], E.Ji[al][1], E.Ji[al][2], 0.0);
+  // DD = int d.d = sum_{al,be} Mdd[al][be] (Jinv Jinv^T)[al][be]: row a of Jinv Jinv^T on lane a
+  {
+    double Jr[3];  // row a of Jinv (lane 3: zero)
 #pragma unroll
-  for (int al = 0; al < 3; ++al)
+    for (int j = 0; j < 3; ++j) Jr[j] = sel4(a, E.Ji[0][j], E.Ji[1][j], E.Ji[2][j], 0.0);
+    double dd = 0.0;
 #pragma unroll
-    for (int be = 0; be < 3; ++be)
-      JJ[al][be] = E.Ji[al][0] * E.Ji[be][0] + E.Ji[al][1] * E.Ji[be][1] + E.Ji[al][2] * E.Ji[be][2];
-  double DD = 0.0;
+    for (int be = 0; be < 3; ++be) {
+      const double jj = Jr[0] * E.Ji[be][0] + Jr[1] * E.Ji[be][1] + Jr[2] * E.Ji[be][2];
+      dd += sel4(a, M[TM_MDD + be], M[TM_MDD + 3 + be], M[TM_MDD + 6 + be], 0.0) * jj;
+    }
+    E.DD = gsum(dd);
+  }
+  // Pd[al] = int p d_al (reference): component a on lane a; then PdJ = Jinv^T Pd and
+  // Dint = Jinv^T Md, component a on lane a
+  {
+    const double pda = sel4(a, M[TM_M1D], M[TM_M1D + 1], M[TM_M1D + 2], 0.0) * P[0] +
+                       sel4(a, M[TM_M1D + 3], M[TM_M1D + 4], M[TM_M1D + 5], 0.0) * P[1] +
+                       sel4(a, M[TM_M1D + 6], M[TM_M1D + 7], M[TM_M1D + 8], 0.0) * P[2] +
+                       sel4(a, M[TM_M1D + 9], M[TM_M1D + 10], M[TM_M1D + 11], 0.0) * P[3];
+    const double Pd[3] = {from(pda, 0), from(pda, 1), from(pda, 2)};
+    const double pdj = Pd[0] * Jc[0] + Pd[1] * Jc[1] + Pd[2] * Jc[2];
+    const double din = M[TM_MD] * Jc[0] + M[TM_MD + 1] * Jc[1] + M[TM_MD + 2] * Jc[2];
 #pragma unroll
-  for (int al = 0; al < 3; ++al)
-#pragma unroll
-    for (int be = 0; be < 3; ++be) DD += M[TM_MDD + 3 * al + be] * JJ[al][be];
-  E.DD = DD;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    E.Dint[j] = M[TM_MD] * E.Ji[0][j] + M[TM_MD + 1] * E.Ji[1][j] + M[TM_MD + 2] * E.Ji[2][j];
-    E.PdJ[j] = Pd[0] * E.Ji[0][j] + Pd[1] * E.Ji[1][j] + Pd[2] * E.Ji[2][j];
+    for (int j = 0; j < 3; ++j) {
+      E.PdJ[j] = from(pdj, j);
+      E.Dint[j] = from(din, j);
+    }
   }
   if (transient) {
     double dV[4][3];
@@ -315,10 +364,14 @@ __device__ __forceinline__ void tet_element(int a, int64_t e, const double4_32a*
       dV[c][0] = V[c][0] - o.x; dV[c][1] = V[c][1] - o.y; dV[c][2] = V[c][2] - o.z;
     }
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 3; ++i)
       E.dVa[i] = M2a[0] * dV[0][i] + M2a[1] * dV[1][i] + M2a[2] * dV[2][i] + M2a[3] * dV[3][i];
-      E.dVb[i] = M[TM_M1B] * dV[0][i] + M[TM_M1B + 1] * dV[1][i] + M[TM_M1B + 2] * dV[2][i] + M[TM_M1B + 3] * dV[3][i];
-    }
+    // dVb[i] = int b (v - v_prev)_i: component a on lane a
+    double dvb = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dvb += M[TM_M1B + c] * sel4(a, dV[c][0], dV[c][1], dV[c][2], 0.0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) E.dVb[i] = from(dvb, i);
   } else {
 #pragma unroll
     for (int i = 0; i < 3; ++i) E.dVa[i] = E.dVb[i] = 0.0;
@@ -575,14 +628,18 @@ __global__ void __launch_bounds__(TET_WARPS * 32) tet_residual_kernel(
   const int a = lane & 3;
   const int64_t stride = (int64_t)gridDim.x * TET_WARPS * TET_PER_WARP;
   for (int64_t base = ((int64_t)blockIdx.x * TET_WARPS + warp) * TET_PER_WARP; base < count; base += stride) {
-    const int64_t it = base + (lane >> 2);
-    if (it >= count) continue;  // no shuffles here: groups past the end just skip
+    // the loop is uniform over the warp (tet_element exchanges values by shuffles); groups past
+    // the end redo element `base` and store nothing
+    const int64_t it0 = base + (lane >> 2);
+    const bool valid = it0 < count;
+    const int64_t it = valid ? it0 : base;
     const int64_t e = first + it;
     const double nut = kp.nu_e ? kp.visc_factor * kp.nu_e[e] : kp.nut;
     TetElem E;
     tet_element(a, e, xyz, u, up, conn, beta, kp.transient != 0, M, E);
     double Rcp[4], Rf[3];
     tet_residual(a, E, M, nut, kp.tau, kp.f, Rcp, Rf);
+    if (!valid) continue;
     if (!(isfinite(Rcp[0]) && isfinite(Rcp[1]) && isfinite(Rcp[2]) && isfinite(Rcp[3]) &&
           isfinite(Rf[0]) && isfinite(Rf[1]) && isfinite(Rf[2])))
       atomicOr(flags, FLAG_NAN);
