@@ -247,7 +247,8 @@ int vms_set_preconditioner(vms_ctx* ctx, int kind);
 /* Solve S du = -r with the last assembled system by restarted GMRES(restart), right-preconditioned
  * (vms_set_preconditioner; restart <= 480), FP32 inner iterations and FP64 iterative refinement in
  * VMS_PREC_MIXED (a refinement pass that does not halve the FP64 residual hands the remaining
- * correction to flexible GMRES with FP64 vectors and the FP32 matrix and preconditioner), FP64 throughout
+ * correction to GMRES with FP64 vectors, the FP32 matrix and the FP64 preconditioner, keeping its
+ * preconditioned vectors), FP64 throughout
  * in VMS_PREC_FP64, to relative residual rtol within maxit iterations in all (the paper
  * used a Krylov solver with tolerance 1e-12 and 50 iterations, Section 6). Then recovers the bubble
  * increments du' = K_ff^-1 (-R_f - K_fc du_e) per element (Section 5) and, if update != 0, adds

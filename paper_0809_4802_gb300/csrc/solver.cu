@@ -831,10 +831,12 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
     last_it = it;
   }
   if (rc == VMS_OK && stalled && total < maxit) {
-    // S c = b - S x with FP64 Krylov vectors, the FP32 matrix values and the FP32 preconditioner
+    // S c = b - S x with FP64 Krylov vectors, the FP32 matrix values and the FP64 preconditioner
+    // (the ILU(0) factor the FP32 sweeps' copy is rounded from)
     int it = 0;
     double irel = 0.0;
-    // flexible GMRES: the FP32 factor applied through FP32 copies is not exactly linear
+    // the preconditioned vectors are kept (flexible form), so that the update x += Z y needs no
+    // further preconditioner application
     if (!w.Zf || w.zf_restart < restart) {
       if (w.Zf) cudaFree(w.Zf);
       w.Zf = nullptr;
