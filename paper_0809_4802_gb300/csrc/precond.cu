@@ -395,8 +395,8 @@ __device__ __forceinline__ bool split_row(const SweepSlot<T>& sl, int r, int64_t
 // next row while the current one waits. A row's dependency in the same chunk is read from shared
 // memory once its value slots no longer hold the all-ones pattern (no L2 round trip; in the warp's
 // own segment it is already there); a dependency in an earlier chunk is read from the L2
-// publication. Chunks are claimed in order by
-// running CTAs, so every wait is for work that is already in progress.
+// publication. Chunks are claimed in order by running CTAs, so every wait is for work that is
+// already in progress.
 template <typename T, bool LOWER, int W = sweep_warps<T>()>
 __global__ void __launch_bounds__(W * 32)
     ilu_sweep_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
