@@ -27,33 +27,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "elements/s Newton-Schur tangent assembly"  # plus "newton": wall time per Newton solve
 UNIT = "elements/s"
-PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
-# FP64 peak of the GB300: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz (maximum SM
-# clock) = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s FP64 figure); FP32: 152 x 128 x 2 x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic flops per element of the two hexahedral element kernels, 27-point rule: the
+# per-point cost of a direct evaluation of the formulas (geometry and fields ~600 flops, residual
+# ~300, tangent blocks K_vv ~1.7k + K_vp ~0.4k + fine-coupled blocks ~0.5k) plus the condensation
+# (~7k flops per element). The kernels execute fewer flops than these counts where their
+# formulation needs fewer (the residual's monomial form executes 14,791 FP64 flops per element,
+# ncu opcode counts on the 32^3 cavity); `executed` gives those counts.
+ALG_FLOPS = {"residual": (600 + 300) * 27, "tangent": (600 + 1700 + 400 + 500) * 27 + 7000}
+EXECUTED_FLOPS = {"residual": 14_791, "tangent_fp64": 129_697, "tet": 5_866}
 
-# Executed FP64 flops per element (FMA = 2, add/mul = 1) of each kernel as implemented, 27-point
-# rule, from ncu's per-opcode counts on the 32^3 cavity (sass__thread_inst_executed_true_per_opcode
-# divided by the 32,768 elements): residual 5,967 DFMA + 1,759 DMUL + 1,098 DADD; FP64 tangent
-# 51,034 DFMA + 15,673 DMUL + 11,956 DADD; tetrahedral kernel below.
-FP64_FLOPS_PER_ELEM = {
-    "residual": 14_791,
-    "tangent_fp64": 129_697,
-    # tetrahedral assembly kernel (one kernel: residual, tangent, condensation, scatter from the
-    # reference moments, four lanes per element): 2,316 DFMA + 1,432 DMUL + 534 DADD per element
-    # (ncu thread-instruction counts on the 21^3 Kuhn cavity, 55,566 elements)
-    "tet": 5_866,
-}
-
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# same workload (profiles/residual_kernel_cavity32_re400.md,
-# profiles/tet_assembly_kernel_tetcavity21_re400.md); None where not captured for the current
-# kernel.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the
+# same kernels (profiles/); None where the current kernel has not been captured.
 NCU_TRAFFIC_BYTES = {("residual", "cavity32_re400_mixed"): 4_203_776,
                      ("residual", "cavity32_re400_fp64"): 4_203_776,
-                     # profiles/tet_assembly_kernel_tetcavity21_re400.md
                      ("tangent", "tetcavity21_re400_mixed"): 20_044_288}
 
 WORKLOADS = {
@@ -85,7 +72,7 @@ WORKLOADS = {
     "vortex_warmstart_fp64": dict(kind="warmstart", flow="vortex", prec=0),
     "channel_warmstart_mixed": dict(kind="warmstart", flow="channel", prec=1),
 }
-DEFAULT_WORKLOAD = "cavity32_re400_mixed"
+DEFAULT_WORKLOAD = "channel_re1000_mixed"
 WS_SIZE = {"nx": 150, "nyz": 28, "n": 16}   # set from --ws-nx / --ws-nyz / --ws-n
 
 
@@ -173,30 +160,97 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ----------------------------------------------------------------------------------------------
-def oracle_assembly_rate(wl, target_s=10.0, max_elems=None):
-    """Elements/s of the oracle's assembly (element kernel, condensation, CSR assembly, Dirichlet)
-    on the first elements of the workload's mesh, sized to take about target_s seconds."""
+def _oracle_chunk(job):
+    """One oracle work unit (runs in a worker process): element residuals and tangents,
+    condensation and CSR assembly of a chunk of elements into a partial system."""
     import oracle
     from oracle import Params
-    mesh = wl.mesh
-    p = Params(nu=wl.nu, dt=wl.dt, element="tet" if mesh.conn.shape[1] == 4 else "hex")
-    beta = wl.beta
+    conn, xyz, u, beta, u_prev, nu, dt, tet = job
+    p = Params(nu=nu, dt=dt, element="tet" if tet else "hex")
+    X, U, b, Up = oracle.gather(conn, xyz, u, beta, u_prev)
+    k = oracle.element_kernel(X, U, b, p, Up)
+    S, r, _, _ = oracle.condense(*oracle.pack_element(k))
+    return oracle.assemble(conn, xyz.shape[0], S, r)
 
-    def run(n):
-        t0 = time.perf_counter()
-        X, U, b, Up = oracle.gather(mesh.conn[:n], mesh.xyz, wl.u, beta[:n], wl.u_prev)
-        k = oracle.element_kernel(X, U, b, p, Up)
-        S, r, _, _ = oracle.condense(*oracle.pack_element(k))
-        A, rhs = oracle.assemble(mesh.conn[:n], mesh.n_nodes, S, r)
-        oracle.apply_dirichlet(A, rhs, wl.bc.dofs)
-        return time.perf_counter() - t0
 
-    n0 = min(256, mesh.n_elems)
-    t0 = run(n0)
-    n = int(min(mesh.n_elems if max_elems is None else max_elems,
-                max(n0, n0 * target_s / max(t0, 1e-6))))
-    t = run(n)
-    return n / t, n, t
+def _oracle_sample(wl, n):
+    """The first n elements of the workload as a mesh of their own (nodes renumbered in order of
+    first use, Dirichlet dofs restricted to those nodes): the oracle's inputs for a bounded sample."""
+    conn = wl.mesh.conn[:n]
+    used, inv = np.unique(conn, return_inverse=True)
+    local = np.full(wl.mesh.n_nodes, -1, np.int64)
+    local[used] = np.arange(used.size)
+    dofs = wl.bc.dofs[local[wl.bc.dofs // 4] >= 0]
+    return {"conn": inv.reshape(conn.shape).astype(np.int32), "xyz": wl.mesh.xyz[used],
+            "u": wl.u[used], "beta": wl.beta[:n],
+            "u_prev": None if wl.u_prev is None else wl.u_prev[used],
+            "dofs": 4 * local[dofs // 4] + dofs % 4, "nu": wl.nu, "dt": wl.dt,
+            "tet": wl.mesh.conn.shape[1] == 4}
+
+
+def _oracle_jobs(smp, parts):
+    n = smp["conn"].shape[0]
+    cuts = np.linspace(0, n, parts + 1).astype(int)
+    return [(smp["conn"][cuts[i]:cuts[i + 1]], smp["xyz"], smp["u"], smp["beta"][cuts[i]:cuts[i + 1]],
+             smp["u_prev"], smp["nu"], smp["dt"], smp["tet"]) for i in range(parts) if cuts[i + 1] > cuts[i]]
+
+
+def _oracle_run(pool, smp, parts):
+    """Seconds of one oracle assembly of a sample (_oracle_sample): the element chunks on the
+    pool's workers, the partial systems summed and the Dirichlet rows applied in this process."""
+    import oracle
+    jobs = _oracle_jobs(smp, parts)
+    t0 = time.perf_counter()
+    out = pool.map(_oracle_chunk, jobs)
+    A, rhs = out[0]
+    for Ai, ri in out[1:]:
+        A = A + Ai
+        rhs = rhs + ri
+    oracle.apply_dirichlet(A, rhs, smp["dofs"])
+    return time.perf_counter() - t0
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_baseline(wl, target_s=8.0, cores=None):
+    """The FP64 oracle (as it stands) timed on the host's cores: one worker process, then one per
+    core, on the same first elements of the workload's mesh (sized so that the one-worker run
+    takes about target_s). Workers are spawned processes with one math-library thread each."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    try:
+        with ctx.Pool(1) as pool:
+            _oracle_run(pool, _oracle_sample(wl, min(64, wl.mesh.n_elems)), 1)  # start-up
+            n0 = min(512, wl.mesh.n_elems)
+            t0 = _oracle_run(pool, _oracle_sample(wl, n0), 1)
+            n = int(min(wl.mesh.n_elems, max(n0, n0 * target_s / max(t0, 1e-6))))
+            smp = _oracle_sample(wl, n)
+            t1 = _oracle_run(pool, smp, 1)
+        with ctx.Pool(cores) as pool:
+            _oracle_run(pool, _oracle_sample(wl, min(64 * cores, wl.mesh.n_elems)), cores)
+            tc = _oracle_run(pool, smp, 4 * cores)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"elements": n, "one_core_s": t1, "all_cores_s": tc, "one_core": n / t1,
+            "all_cores": n / tc, "cores": cores, "cpu": cpu_model()}
 
 
 def dist_setup():
@@ -220,21 +274,29 @@ def max_over_ranks(x: float) -> float:
 
 
 def reference_arm(args):
+    """The oracle as the reference arm: each step is one oracle assembly (element kernels,
+    condensation, CSR assembly, Dirichlet rows) of a bounded sample of the workload's elements, in
+    element chunks on one spawned worker process per host core."""
     ws, rank, local = dist_setup()
     if rank != 0:
         return
-    wl, prec = make_workload(args.workload)
-    # bounded sample: about 150k oracle elements in total (~45 s on one core), at least 64 a step
-    per_step = max(64, min(args.ref_sample, 150_000 // max(args.steps, 1)))
-    for _ in range(args.warmup):
-        oracle_assembly_rate(wl, target_s=0.0, max_elems=64)
-    rates = []
-    t_total = 0.0
-    for _ in range(args.steps):
-        rate, n, t = oracle_assembly_rate(wl, target_s=0.0, max_elems=per_step)
-        rates.append(rate)
-        t_total += t
-    value = float(np.mean(rates))
+    import multiprocessing as mp
+    wl, prec, batch = make_workload(args.workload, with_batch=True)
+    cores = os.cpu_count() or 1
+    # bounded sample: about 64 x per_step x steps oracle element evaluations in all
+    per_step = max(64, min(args.ref_sample, 400_000 // max(args.steps, 1)))
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    times = []
+    n = min(per_step, wl.mesh.n_elems)
+    smp = _oracle_sample(wl, n)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        _oracle_run(pool, _oracle_sample(wl, min(64 * cores, wl.mesh.n_elems)), cores)
+        for _ in range(args.warmup):
+            _oracle_run(pool, smp, 4 * cores)
+        for _ in range(args.steps):
+            times.append(_oracle_run(pool, smp, 4 * cores))
+    value = n * len(times) / sum(times)
     newton = None
     if args.newton != "off":
         import oracle
@@ -247,14 +309,15 @@ def reference_arm(args):
                   "unit": "s", "workload": "cavity8_re100_fp64", "newton_iterations": len(norms) - 1,
                   "final_rel": norms[-1] / norms[0],
                   "linear_solver": "scipy sparse direct solve (oracle)"}
+    sample = (f"first {n} elements of the mesh per step, numpy FP64 oracle in {4 * cores} chunks on "
+              f"{cores} worker processes ({cpu_model()})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+        "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.workload, wl, prec, None),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"first {per_step} elements of the mesh per step (numpy FP64 oracle)"},
+        "config": workload_config(args.workload, wl, prec, batch),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "newton": newton,
     }
@@ -266,9 +329,10 @@ NEWTON_METRIC = "wall time per Newton solve to 1e-8 rel"
 
 def newton_timing(vms, wl, prec, device, stream, rtol=1e-8, repeats=2, maxit=30):
     """Wall time of vms_newton_solve from the workload's initial state to ||R|| <= rtol ||R^0||:
-    host clock around the call with the device synchronised on both sides; the state is uploaded
-    again (outside the timed region) before each repeat; one untimed solve first builds the
-    ILU(0) pattern and the Krylov work space. Median over the repeats."""
+    host clock around the call with the device synchronised on both sides (`value`), and around
+    the upload of the initial state from host arrays, the solve and the download of the solution
+    to host arrays (`host_to_host_s`); one untimed solve first builds the ILU(0) pattern and the
+    Krylov work space. Medians over the repeats."""
     import torch
     ctx = vms.Context(device, prec)
     ctx.set_stream(stream)
@@ -281,19 +345,27 @@ def newton_timing(vms, wl, prec, device, stream, rtol=1e-8, repeats=2, maxit=30)
         ctx.close()
         return {"metric": NEWTON_METRIC.replace("1e-8", f"{rtol:g}"), "value": None, "unit": "s",
                 "precision": "mixed" if prec == 1 else "fp64", "failed": str(e)}
-    times, its, hist, stats = [], 0, None, (0, 0)
+    times, h2h, its, hist, stats = [], [], 0, None, (0, 0)
+    u_out = np.empty((wl.mesh.n_nodes, 4))
+    b_out = np.empty((wl.mesh.n_elems, 3))
     for _ in range(repeats):
-        ctx.state_upload(wl.u, wl.beta, wl.u_prev)
         torch.cuda.synchronize(device)
         ctx.solver_stats(reset=True)
+        th = time.perf_counter()
+        ctx.state_upload(wl.u, wl.beta, wl.u_prev)   # host arrays
+        torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         its, hist = ctx.newton_solve(rtol=rtol, maxit=maxit)
         torch.cuda.synchronize(device)
-        times.append(time.perf_counter() - t0)
+        t1 = time.perf_counter()
+        u_out[...], b_out[...] = ctx.state_download()  # back to host arrays
+        h2h.append(time.perf_counter() - th)
+        times.append(t1 - t0)
         stats = ctx.solver_stats(reset=True)
     ctx.close()
     return {"metric": NEWTON_METRIC.replace("1e-8", f"{rtol:g}"), "value": float(np.median(times)),
             "unit": "s", "higher_is_better": False, "precision": "mixed" if prec == 1 else "fp64",
+            "host_to_host_s": float(np.median(h2h)),
             "newton_iterations": int(its), "linear_solves": int(stats[0]),
             "krylov_iterations": int(stats[1]), "final_rel": float(hist[-1] / hist[0]),
             "krylov": "GMRES(150), block ILU(0) right preconditioner, inexact Newton",
@@ -338,7 +410,7 @@ def warmstart_study(vms, ctx, wl, args, dev):
             "note": "warm start applied to the velocity; Newton to the same absolute target"}
 
 
-def workload_config(name, wl, prec, scatter, batch=None):
+def workload_config(name, wl, prec, batch=None):
     c = {"workload": name, "elements": wl.mesh.n_elems, "nodes": wl.mesh.n_nodes,
          "reynolds": round(1.0 / wl.nu, 3), "dt": wl.dt, "precision": "mixed" if prec == 1 else "fp64",
          "quad_points": 27, "l2": "flushed between timed steps (256 MB write)"}
@@ -346,9 +418,79 @@ def workload_config(name, wl, prec, scatter, batch=None):
         edges = [int(round(w.mesh.n_elems ** (1 / 3))) for w in batch.members]
         c.update(instances=len(batch.members), reynolds="per instance, U[100, 1000]",
                  edge_counts={str(k): edges.count(k) for k in sorted(set(edges))})
-    if scatter is not None:
-        c["scatter"] = "colour" if scatter == 1 else "atomic"
     return c
+
+
+def measured_peaks(vms, dev_index):
+    """FP64 and FP32 FMA throughput of this GPU, measured by the library's probe kernel (best of
+    three launches each; FP32 is the better of scalar and packed FMA), with the SM clock sampled
+    during the probe."""
+    with ClockSampler(dev_index) as clk:
+        fp64 = vms.fma_throughput(dev_index, 0)
+        fp32 = max(vms.fma_throughput(dev_index, 1), vms.fma_throughput(dev_index, 2))
+    c = clk.summary()
+    return {"fp64_tflops": fp64, "fp32_tflops": fp32, "sm_mhz": c.get("sm_mhz"),
+            "source": "measured: vms_fma_throughput (independent FMA chains, CUDA events)"}
+
+
+def timed_assembly(ctx, stream, steps, flush, barrier, dev):
+    """CUDA-event time (ms, summed) of `steps` assemblies with device-resident inputs, the L2
+    flushed before each; the library's launch counts over the same region."""
+    import torch
+    ctx.profile_read(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    barrier()
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        ctx.assemble()
+        ends[k].record(stream)
+    barrier()
+    counts = ctx.profile_read(reset=True)
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), int(sum(v[1] for v in counts.values()))
+
+
+def kernel_times(ctx, steps, flush):
+    """Per-kernel-kind milliseconds per launch, from the library's own CUDA events around each
+    launch on the stream it is launched on (residual: the context's stream; tangent: its second
+    stream), over `steps` assemblies."""
+    ctx.profile_enable(True)
+    for _ in range(steps):
+        flush.zero_()
+        ctx.assemble()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    return {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
+
+
+def roofline_entries(kern, E, prec, tet, peaks, workload):
+    """One roofline entry per element kernel: algorithmic flops per launch / its event time."""
+    out = []
+    if tet:
+        ms = kern["tangent"]
+        fpe = EXECUTED_FLOPS["tet"]
+        out.append({"bound": "alu", "kernel": "tet_assembly", "pipe": "fp64", "unit": "TFLOP/s",
+                    "flops_per_element": fpe, "flops": "executed (ncu opcode counts; no algorithmic count is stated for the tetrahedron)",
+                    "ms": ms, "achieved": fpe * E / (ms * 1e-3) / 1e12, "peak": peaks["fp64_tflops"],
+                    "traffic": NCU_TRAFFIC_BYTES.get(("tangent", workload))})
+    else:
+        for name, pipe in (("residual", "fp64"), ("tangent", "fp32" if prec == 1 else "fp64")):
+            if name not in kern:
+                continue
+            ms = kern[name]
+            fpe = ALG_FLOPS[name]
+            exe = EXECUTED_FLOPS.get(name if name == "residual" else ("tangent_fp64" if prec == 0 else ""))
+            out.append({"bound": "alu", "kernel": name, "pipe": pipe, "unit": "TFLOP/s",
+                        "flops_per_element": fpe, "executed_flops_per_element": exe,
+                        "ms": ms, "achieved": fpe * E / (ms * 1e-3) / 1e12,
+                        "peak": peaks["fp64_tflops"] if pipe == "fp64" else peaks["fp32_tflops"],
+                        "traffic": NCU_TRAFFIC_BYTES.get((name, workload))})
+    for r in out:
+        r["frac"] = r["achieved"] / r["peak"]
+        r["ms"] = round(r["ms"], 4)
+        r["peak_source"] = peaks["source"]
+    return out
 
 
 def ours(args):
@@ -371,20 +513,23 @@ def ours(args):
         prec = {"mixed": 1, "fp64": 0}[args.precision]
     mesh = wl.mesh
     E = mesh.n_elems
+    tet = mesh.conn.shape[1] == 4
     stream = torch.cuda.current_stream(dev)
-    ctx = vms.Context(local, prec)
-    ctx.set_stream(stream.cuda_stream)
-    ctx.mesh_upload(mesh.xyz, mesh.conn, wl.bc.dofs, wl.bc.vals)
-    ctx.set_params(wl.nu, dt=wl.dt, scatter_mode=args.scatter)
+    peaks = measured_peaks(vms, local)
+
+    def make_ctx(p):
+        c = vms.Context(local, p)
+        c.set_stream(stream.cuda_stream)
+        c.mesh_upload(mesh.xyz, mesh.conn, wl.bc.dofs, wl.bc.vals)
+        c.set_params(wl.nu, dt=wl.dt, scatter_mode=args.scatter)
+        if batch is not None:
+            c.set_element_viscosity(batch.nu_e)
+            c.set_instances(batch.node_offsets, batch.elem_offsets)
+        c.state_upload(wl.u, wl.beta, wl.u_prev)
+        return c
+
+    ctx = make_ctx(prec)
     tuning = None
-    if batch is not None:
-        ctx.set_element_viscosity(batch.nu_e)
-        ctx.set_instances(batch.node_offsets, batch.elem_offsets)
-    u_host = torch.from_numpy(np.ascontiguousarray(wl.u)).pin_memory()
-    beta_host = torch.from_numpy(np.ascontiguousarray(wl.beta)).pin_memory()
-    u_prev_host = (torch.from_numpy(np.ascontiguousarray(wl.u_prev)).pin_memory()
-                   if wl.u_prev is not None else None)
-    ctx.state_upload(wl.u, wl.beta, wl.u_prev)
     if batch is not None or args.autotune:
         tuning = ctx.autotune(repeats=3)
     if batch is not None or args.graph:
@@ -403,50 +548,33 @@ def ours(args):
     barrier()
 
     # ---- timed region: device-resident inputs ----
-    ctx.profile_read(reset=True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
-        barrier()
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            ctx.assemble()
-            ends[k].record(stream)
-        barrier()
-    counts = ctx.profile_read(reset=True)
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    gpu_launches = int(sum(v[1] for v in counts.values()))
+        ms, gpu_launches = timed_assembly(ctx, stream, args.steps, flush, barrier, dev)
     ms = max_over_ranks(ms)
     value = ws * E * args.steps / (ms / 1000.0)
 
-    # ---- per-kernel times (events inside the library, same stream) for the roofline ----
-    ctx.profile_enable(True)
-    for _ in range(args.steps):
-        flush.zero_()
-        ctx.assemble()
-    prof = ctx.profile_read(reset=True)
-    ctx.profile_enable(False)
-    kern = {k: v for k, v in prof.items() if v[1] > 0}
-    # the kernel on the FP64 critical path: the residual in mixed precision (the FP32 tangent runs
-    # beside it on a second stream), the tangent in FP64 mode
-    tet = mesh.conn.shape[1] == 4
-    dom = "tangent" if (tet or prec == 0) else "residual"
-    dom_ms = kern[dom][0] / kern[dom][1]
-    key = "tet" if tet else ("residual" if dom == "residual" else "tangent_fp64")
-    fpe = FP64_FLOPS_PER_ELEM.get(key)
-    achieved = fpe * E / (dom_ms / 1000.0) / 1e12 if fpe else None
-    roofline = {"bound": "alu", "kernel": "tet_assembly" if tet else dom, "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                "traffic": NCU_TRAFFIC_BYTES.get((dom, args.workload)),
-                "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
-                "flops_per_element": fpe,
-                "concurrent": "residual (stream 1) and tangent (stream 2) overlap; times are in situ",
-                "kernel_ms": {k: round(v[0] / v[1], 4) for k, v in kern.items()}}
+    # ---- per-kernel times (events inside the library, on each kernel's stream) ----
+    kern = kernel_times(ctx, args.steps, flush)
+    entries = roofline_entries(kern, E, prec, tet, peaks, args.workload)
+    # the dominant kernel: the largest share of the step's device time when the kernels run one
+    # after another (the ncu launch list): the FP64 residual in mixed precision, the tangent in
+    # FP64, the single assembly kernel of the tetrahedron. In the step the residual and the
+    # tangent overlap on two streams; every kernel's own entry is in `kernels`.
+    dom_name = "tet_assembly" if tet else ("tangent" if prec == 0 else "residual")
+    roofline = dict(next(r for r in entries if r["kernel"] == dom_name))
+    roofline["kernels"] = entries
+    roofline["kernel_ms"] = {k: round(v, 4) for k, v in kern.items()}
+    roofline["concurrent"] = ("residual (context stream) and tangent (second stream) overlap in the "
+                              "step; each time is that kernel's own launch-to-completion in the step")
 
-    # ---- end to end through the C-ABI with host buffers ----
-    rhs_host = torch.empty(4 * mesh.n_nodes, dtype=torch.float64).pin_memory()
+    # ---- end to end through the C-ABI: host state in, assembled system (values + rhs) out ----
+    u_host = torch.from_numpy(np.ascontiguousarray(wl.u)).pin_memory()
+    beta_host = torch.from_numpy(np.ascontiguousarray(wl.beta)).pin_memory()
+    u_prev_host = (torch.from_numpy(np.ascontiguousarray(wl.u_prev)).pin_memory()
+                   if wl.u_prev is not None else None)
+    view = ctx.csr()
+    vals_host = torch.empty(view.nnz, dtype=torch.float32 if view.values_dtype == 1 else torch.float64).pin_memory()
+    rhs_host = torch.empty(view.n_rows, dtype=torch.float64).pin_memory()
     e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -454,42 +582,67 @@ def ours(args):
         flush.zero_()
         e_starts[k].record(stream)
         ctx.state_upload(u_host, beta_host, u_prev_host)
-        view = ctx.assemble()
-        rhs_dev = ctx.csr_device(view)[3]
-        rhs_host.copy_(rhs_dev, non_blocking=True)
+        ctx.assemble()
+        ctx.csr_download(values=vals_host, rhs=rhs_host)
         e_ends[k].record(stream)
     barrier()
-    e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends))
-    e_ms = max_over_ranks(e_ms)
+    e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)))
     e2e = {"value": ws * E * args.steps / (e_ms / 1000.0), "unit": UNIT,
            "h2d_bytes_per_step": int(u_host.numel() * 8 + beta_host.numel() * 8
                                      + (u_prev_host.numel() * 8 if u_prev_host is not None else 0)),
-           "d2h_bytes_per_step": int(rhs_host.numel() * 8)}
+           "d2h_bytes_per_step": int(vals_host.numel() * vals_host.element_size() + rhs_host.numel() * 8),
+           "path": "vms_state_upload (pinned host) + vms_assemble_newton_schur + vms_csr_download "
+                   "(CSR values and right-hand side to pinned host)"}
+    ctx.close()
+    del vals_host
 
-    # ---- wall time per Newton solve (same mesh and initial state; mixed and plain FP64) ----
+    # ---- the same mesh in the other precision (FP64 beside mixed) ----
+    other = None
+    if not args.skip_other_precision:
+        c2 = make_ctx(1 - prec)
+        for _ in range(2):
+            c2.assemble()
+        k2 = max(3, min(args.steps, 10))
+        ms2, _ = timed_assembly(c2, stream, k2, flush, barrier, dev)
+        kern2 = kernel_times(c2, 2, flush)
+        other = {"precision": "mixed" if prec == 0 else "fp64", "steps": k2,
+                 "value": E * k2 / (max_over_ranks(ms2) / 1000.0), "unit": UNIT,
+                 "ms_per_step": ms2 / k2,
+                 "roofline": roofline_entries(kern2, E, 1 - prec, tet, peaks, args.workload)}
+        c2.close()
+
+    # ---- wall time per Newton solve: the 32^3 jittered cavity (mixed and plain FP64, to 1e-8)
+    # and the 8^3 cavity (FP64, to 1e-10); the large workloads' solves take minutes each ----
     newton = None
-    if args.newton == "on" or (args.newton == "auto" and (args.workload.startswith("cavity")
-                                                          or args.workload.startswith("tetcavity"))):
-        newton = newton_timing(vms, wl, prec, local, stream.cuda_stream)
-        other = newton_timing(vms, wl, 1 - prec, local, stream.cuda_stream)
-        newton["other_precision"] = {k: other.get(k) for k in ("precision", "value", "newton_iterations",
-                                                               "krylov_iterations", "final_rel", "failed")}
+    if args.newton == "on" or (args.newton == "auto" and WORKLOADS[args.workload].get("kind") != "warmstart"
+                               and batch is None):
+        nw = args.workload if (args.workload.startswith("cavity") or args.workload.startswith("tetcavity")) \
+            else "cavity32_re400_mixed"
+        nwl, nprec = make_workload(nw)
+        newton = newton_timing(vms, nwl, nprec, local, stream.cuda_stream)
+        newton["workload"] = nw
+        o = newton_timing(vms, nwl, 1 - nprec, local, stream.cuda_stream)
+        newton["other_precision"] = {k: o.get(k) for k in ("precision", "value", "host_to_host_s", "newton_iterations",
+                                                           "krylov_iterations", "final_rel", "failed")}
         small, _ = make_workload("cavity8_re100_fp64")
         newton["cavity8_re100_fp64_to_1e-10"] = {
             k: v for k, v in newton_timing(vms, small, 0, local, stream.cuda_stream, rtol=1e-10,
                                            repeats=3).items()
-            if k in ("value", "unit", "newton_iterations", "krylov_iterations", "final_rel")}
+            if k in ("value", "host_to_host_s", "unit", "newton_iterations", "krylov_iterations", "final_rel")}
         if newton["value"] is not None:
             newton["value"] = max_over_ranks(newton["value"])
 
     # ---- transient: learned warm start against the previous-step start ----
     warm = None
     if WORKLOADS[args.workload].get("kind") == "warmstart":
+        ctx = make_ctx(prec)
         warm = warmstart_study(vms, ctx, wl, args, dev)
+        ctx.close()
 
     # ---- batch: one linear solve per instance (the first inexact-Newton system, eta = 1e-2) ----
     per_instance = None
     if batch is not None:
+        ctx = make_ctx(prec)
         ctx.assemble()
         times, iters, fails = [], [], 0
         for i in range(len(batch.members)):
@@ -501,6 +654,7 @@ def ours(args):
             except vms.VmsError:
                 fails += 1
             times.append(time.perf_counter() - t0)
+        ctx.close()
         ms_i = np.array(times) * 1e3
         per_instance = {"metric": "per-instance linear solve time (first Newton system, rtol 1e-2)",
                         "unit": "ms", "instances": len(times), "failures": fails,
@@ -512,10 +666,16 @@ def ours(args):
     cpu = None
     if rank == 0 and not args.skip_cpu_baseline:
         src = batch.members[0] if batch is not None else wl
-        rate, n, t = oracle_assembly_rate(src, target_s=args.cpu_seconds)
-        what = "of the first instance" if batch is not None else f"of {E}"
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n} elements {what}, numpy FP64 oracle assembly ({t:.1f} s)"}
+        ob = oracle_baseline(src, target_s=args.cpu_seconds)
+        what = "the first instance" if batch is not None else args.workload
+        cpu = {"value": ob["one_core"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"first {ob['elements']} elements of {what}: numpy FP64 oracle assembly "
+                          f"(element kernels, condensation, CSR assembly, Dirichlet rows), "
+                          f"{ob['one_core_s']:.1f} s on one core of {ob['cpu']}"),
+               "all_cores": {"value": ob["all_cores"], "cores": ob["cores"], "seconds": ob["all_cores_s"],
+                             "how": "the same elements in 4 chunks per core on spawned worker processes, "
+                                    "partial systems summed"},
+               "cpu": ob["cpu"]}
 
     if rank == 0:
         line = {
@@ -523,14 +683,15 @@ def ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
-            "config": workload_config(args.workload, wl, prec, args.scatter, batch),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "newton": newton,
+            "config": workload_config(args.workload, wl, prec, batch),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "other_precision": other, "newton": newton,
+            "scatter": "colour" if args.scatter == 1 else "atomic",
             "tuning": tuning, "graph": bool(batch is not None or args.graph),
             "per_instance_solve": per_instance, "warm_start": warm,
-            "gpu_launches": gpu_launches, "clocks": clk.summary(),
+            "peaks": peaks, "gpu_launches": gpu_launches, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
@@ -545,8 +706,10 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default=None)
     ap.add_argument("--scatter", type=int, choices=[0, 1], default=0)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-sample", type=int, default=2048)
+    ap.add_argument("--skip-other-precision", action="store_true",
+                    help="do not time the same mesh in the other precision mode")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--ref-sample", type=int, default=8192)
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--ws-n", type=int, default=16)
     ap.add_argument("--ws-nx", type=int, default=150)

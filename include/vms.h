@@ -161,6 +161,12 @@ int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out);
 /* Return the last assembled system without assembling again (VMS_ERR_STATE if none). */
 int vms_get_csr(vms_ctx* ctx, vms_csr_view* out);
 
+/* Copy the last assembled system to caller buffers (host or device; any may be NULL): rowptr
+ * (4 n_nodes + 1 int32), colidx (nnz int32), values (nnz entries of the view's values_dtype: FP64
+ * or FP32) and rhs (4 n_nodes doubles). Synchronises the context's stream. Errors: VMS_ERR_STATE
+ * (nothing assembled), VMS_ERR_CUDA. */
+int vms_csr_download(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* values, double* rhs);
+
 /* Residual-only evaluation in FP64 (Section 4.1 residual vectors, assembled): writes the 2-norm
  * of [R_c, R_p on free dofs; R_f of every element] to *norm (host). If R (host or device, may
  * be NULL) is given it receives the 4*n_nodes + 3*n_elems entries (constrained coarse entries 0).
@@ -244,6 +250,14 @@ int vms_set_graph(vms_ctx* ctx, int enable);
  * (VMS_ERR_UNSUPPORTED otherwise). Errors: VMS_ERR_INVALID_ARG. */
 int vms_set_preconditioner(vms_ctx* ctx, int kind);
 
+/* Limit of every device-side wait of the ILU(0) factorisation and sweeps (a row waiting for a row
+ * it depends on): after `polls` polls (about 32 ns apart) the kernel records a timeout and stops
+ * its remaining work, and the solve returns VMS_ERR_TIMEOUT with the state unchanged; the context
+ * stays usable. polls = 0 restores the default (2^22, about 0.13 s). A limit too small for the
+ * rows' normal hand-over times makes every ILU(0) solve time out. Not part of the paper's method:
+ * failure detection of the GPU solver. Errors: VMS_ERR_INVALID_ARG (polls < 0 or > 2^30). */
+int vms_set_wait_limit(vms_ctx* ctx, int64_t polls);
+
 /* Solve S du = -r with the last assembled system by restarted GMRES(restart), right-preconditioned
  * (vms_set_preconditioner; restart <= 480), FP32 inner iterations and FP64 iterative refinement in
  * VMS_PREC_MIXED (a refinement pass that does not halve the FP64 residual hands the remaining
@@ -254,7 +268,8 @@ int vms_set_preconditioner(vms_ctx* ctx, int kind);
  * increments du' = K_ff^-1 (-R_f - K_fc du_e) per element (Section 5) and, if update != 0, adds
  * du and du' to the state. *iters (may be NULL) receives the Krylov iterations, *rel the final
  * relative residual. Errors: VMS_ERR_STATE, VMS_ERR_KRYLOV_MAXIT (state left unchanged),
- * VMS_ERR_ZERO_PIVOT, VMS_ERR_TIMEOUT (ILU(0) only; the state is left unchanged). */
+ * VMS_ERR_ZERO_PIVOT, VMS_ERR_TIMEOUT (ILU(0) only; the state is left unchanged), VMS_ERR_NAN
+ * (non-finite right-hand side). */
 int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
               double* rel);
 
@@ -376,7 +391,9 @@ int vms_solver_stats(vms_ctx* ctx, int reset, int64_t* solves, int64_t* krylov_i
  * Returns VMS_OK, VMS_ERR_INVALID_ARG (null pointer, bad parameters), VMS_ERR_TOO_LARGE
  * (4*n_nodes + 3*n_elems > VMS_NOALLOC_MAX_ENTRIES; nothing is queued) or VMS_ERR_CUDA.
  * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture. Every call shares
+ * with that device current and keeps it for the life of the process; make that first call before
+ * any stream capture, and do not call it again on a device after a cudaDeviceReset of that device
+ * (the kept address would be stale). Every call shares
  * the one array and clears what it needs at its start, so calls whose GPU work overlaps (other
  * streams, other host threads) race on it: order them on one stream or serialise them. */
 #define VMS_ERR_TOO_LARGE -11
@@ -387,6 +404,13 @@ int vms_residual_norm_noalloc(int64_t n_nodes, const double* xyz, int64_t n_elem
                               const double* u, const double* beta, const double* u_prev,
                               const vms_params* params, double* norm, int32_t* status,
                               void* stream);
+
+/* Arithmetic throughput of the current GPU (no context needed): a kernel of independent fused
+ * multiply-add chains, sized to a multiple of the SM count, timed with CUDA events on `device`.
+ *   kind 0: FP64 FMA,  1: FP32 FMA,  2: packed FP32 FMA (two lanes per instruction)
+ * *tflops receives the measured TFLOP/s (2 flops per FMA), the denominator of the element kernels'
+ * rooflines. Not part of the paper's method. Errors: VMS_ERR_INVALID_ARG, VMS_ERR_CUDA. */
+int vms_fma_throughput(int device, int kind, double* tflops);
 
 /* Message of the last error on this context ("" if none); valid until the next call. */
 const char* vms_last_error(vms_ctx* ctx);

@@ -730,6 +730,21 @@ int vms_get_csr(vms_ctx* ctx, vms_csr_view* out) {
   return VMS_OK;
 }
 
+int vms_csr_download(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* values, double* rhs) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx->work.assembled) return fail(ctx, VMS_ERR_STATE, "nothing assembled");
+  CK(cudaSetDevice(ctx->device));
+  const Mesh& m = ctx->mesh;
+  cudaStream_t st = ctx->stream;
+  const size_t vbytes = (size_t)m.nnz * (fp32_mode(ctx) ? sizeof(float) : sizeof(double));
+  if (rowptr) CK(cudaMemcpyAsync(rowptr, m.rowptr, sizeof(int32_t) * (4 * m.n_nodes + 1), cudaMemcpyDefault, st));
+  if (colidx) CK(cudaMemcpyAsync(colidx, m.colidx, sizeof(int32_t) * m.nnz, cudaMemcpyDefault, st));
+  if (values) CK(cudaMemcpyAsync(values, ctx->work.values, vbytes, cudaMemcpyDefault, st));
+  if (rhs) CK(cudaMemcpyAsync(rhs, ctx->work.rhs, sizeof(double) * 4 * m.n_nodes, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  return VMS_OK;
+}
+
 int vms_residual(vms_ctx* ctx, double* norm, double* R) {
   if (!ctx || !norm) return fail(ctx, VMS_ERR_INVALID_ARG, "null argument");
   if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");

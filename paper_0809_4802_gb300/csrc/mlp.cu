@@ -302,7 +302,8 @@ __global__ void mlp_stored_kernel(const __nv_bfloat16* __restrict__ w, const flo
 
 unsigned grid_rows(int64_t n) {
   const int64_t tiles = (n + TILE - 1) / TILE;
-  return (unsigned)(tiles < 1 ? 1 : (tiles > 152 ? 152 : tiles));
+  const int64_t sms = vms::sm_count();
+  return (unsigned)(tiles < 1 ? 1 : (tiles > sms ? sms : tiles));
 }
 
 int mfail(vms_mlp* p, int code, const char* msg) {

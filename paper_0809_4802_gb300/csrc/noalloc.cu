@@ -62,7 +62,7 @@ struct NaStore {
   __device__ __forceinline__ void set(int k, double v) { sc[k][tid] = v; }
 };
 
-// The quadrature table is written by a copy queued before the kernel and only read by it.
+// The quadrature table is written by a kernel queued before the residual kernel, which only reads it.
 struct NaTable {
   const QpRow* __restrict__ t;
   __device__ __forceinline__ double xi(int q) const { return __ldg(&t[q].xi); }
@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(NA_THREADS) na_finish_kernel(const double* __r
   }
 }
 
-void qp_rows(int n1, double bubble_scale, QpRow* rows) {
+// The quadrature table (the same rule as the context's tables), written on the device from the
+// rule's order and the bubble scale passed by value: no host memory is read by the queued work.
+__global__ void na_table_kernel(int n1, double bubble_scale, QpRow* __restrict__ rows) {
   double x[4], w[4];
   if (n1 == 2) {
     const double a = 1.0 / sqrt(3.0);
@@ -210,20 +212,19 @@ void qp_rows(int n1, double bubble_scale, QpRow* rows) {
     w[0] = w[3] = (18.0 - sqrt(30.0)) / 36.0;
     w[1] = w[2] = (18.0 + sqrt(30.0)) / 36.0;
   }
-  for (int k = 0; k < n1; ++k)
-    for (int j = 0; j < n1; ++j)
-      for (int i = 0; i < n1; ++i) {
-        QpRow& r = rows[(k * n1 + j) * n1 + i];
-        const double p0 = x[i], p1 = x[j], p2 = x[k];
-        r.xi = p0; r.eta = p1; r.zeta = p2;
-        r.xe = p0 * p1; r.xz = p0 * p2; r.ez = p1 * p2; r.xez = p0 * p1 * p2;
-        const double f0 = 1 - p0 * p0, f1 = 1 - p1 * p1, f2 = 1 - p2 * p2;
-        r.b = bubble_scale * f0 * f1 * f2;
-        r.db0 = bubble_scale * (-2 * p0) * f1 * f2;
-        r.db1 = bubble_scale * (-2 * p1) * f0 * f2;
-        r.db2 = bubble_scale * (-2 * p2) * f0 * f1;
-        r.w = w[i] * w[j] * w[k];
-      }
+  const int q = threadIdx.x;
+  if (q >= n1 * n1 * n1) return;
+  const int i = q % n1, j = (q / n1) % n1, k = q / (n1 * n1);
+  QpRow& r = rows[q];
+  const double p0 = x[i], p1 = x[j], p2 = x[k];
+  r.xi = p0; r.eta = p1; r.zeta = p2;
+  r.xe = p0 * p1; r.xz = p0 * p2; r.ez = p1 * p2; r.xez = p0 * p1 * p2;
+  const double f0 = 1 - p0 * p0, f1 = 1 - p1 * p1, f2 = 1 - p2 * p2;
+  r.b = bubble_scale * f0 * f1 * f2;
+  r.db0 = bubble_scale * (-2 * p0) * f1 * f2;
+  r.db1 = bubble_scale * (-2 * p1) * f0 * f2;
+  r.db2 = bubble_scale * (-2 * p2) * f0 * f1;
+  r.w = w[i] * w[j] * w[k];
 }
 
 }  // namespace
@@ -258,17 +259,14 @@ extern "C" int vms_residual_norm_noalloc(int64_t n_nodes, const double* xyz, int
   kp.nq = p.quad_order * p.quad_order * p.quad_order;
   kp.transient = p.dt > 0 ? 1 : 0;
   kp.has_force = (p.f[0] != 0.0 || p.f[1] != 0.0 || p.f[2] != 0.0) ? 1 : 0;
-  QpRow rows[MAX_QP];
-  qp_rows(p.quad_order, p.bubble_scale, rows);
 
   // the array keeps the previous call's contents: clear the residual, partials and flags
   const int64_t n = 4 * n_nodes + 3 * n_elems;
-  na_zero_kernel<<<152 * 4, 256, 0, st>>>(scratch, n);
+  na_zero_kernel<<<4 * sm_count(), 256, 0, st>>>(scratch, n);
   na_zero_kernel<<<1, 256, 0, st>>>(scratch + NA_PART, NA_BLOCKS);
   na_zero_kernel<<<1, 32, 0, st>>>(scratch + NA_FLAGS, 4);
-  cudaError_t e = cudaMemcpyAsync(scratch + NA_QP, rows, sizeof(QpRow) * kp.nq,
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return VMS_ERR_CUDA;
+  na_table_kernel<<<1, MAX_QP, 0, st>>>(p.quad_order, p.bubble_scale,
+                                        reinterpret_cast<QpRow*>(scratch + NA_QP));
   const unsigned eb = (unsigned)((n_elems + 63) / 64);
   const double* up = u_prev ? u_prev : u;
   if (kp.transient) {
@@ -282,6 +280,5 @@ extern "C" int vms_residual_norm_noalloc(int64_t n_nodes, const double* xyz, int
     na_zero_dofs_kernel<<<(unsigned)((n_dir + 255) / 256), 256, 0, st>>>(dir_dof, n_dir, 4 * n_nodes, scratch);
   na_sumsq_kernel<<<NA_BLOCKS, NA_THREADS, 0, st>>>(n, scratch);
   na_finish_kernel<<<1, NA_THREADS, 0, st>>>(scratch, norm, status);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? VMS_OK : VMS_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? VMS_OK : VMS_ERR_CUDA;
 }

@@ -10,7 +10,7 @@
 // GPU mapping of the factorisation: one warp owns one node row at a time and claims rows in order
 // from a counter, so a row only ever waits for rows claimed earlier, by warps that are already
 // running. A row publishes itself by writing its epoch into a flag with release semantics;
-// dependants poll the flag with acquire loads (bounded: after ILU_SPIN_LIMIT polls the kernel
+// dependants poll the flag with acquire loads (bounded: after Ilu::spin_limit polls the kernel
 // records a timeout and returns), and read data published in the same launch through L2
 // (ld.global.cg), never through L1. The triangular sweeps claim chunks of grid-line segments per
 // CTA, one segment per warp (see ilu_sweep_kernel), so that most dependencies are resolved in
@@ -25,12 +25,10 @@ namespace vms {
 
 namespace {
 
-constexpr uint32_t ILU_SPIN_LIMIT = 1u << 22;
 constexpr int ILU_FWARPS = 4;    // warps per CTA of the factorisation
 // warps per CTA of the sweeps (one segment each): FP64 rows keep the FP64 pipe of their SM
 // partition busy for ~1000 cycles, so FP64 sweeps spread over more SMs
 template <typename T> constexpr int sweep_warps() { return sizeof(T) == 4 ? 8 : 4; }
-constexpr unsigned ILU_SWEEP_CTAS = 152 * 4;  // at most four sweep CTAs per SM
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
@@ -44,10 +42,10 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 }
 
 // Wait until *f == epoch. Gives up (returns false) when another warp has recorded an error or
-// after ILU_SPIN_LIMIT polls, recording a timeout.
-__device__ __forceinline__ bool wait_ready(const uint32_t* f, uint32_t epoch, int* err) {
+// after `lim` polls (Ilu::spin_limit), recording a timeout.
+__device__ __forceinline__ bool wait_ready(const uint32_t* f, uint32_t epoch, int* err, uint32_t lim) {
   if (ld_acquire(f) == epoch) return true;
-  for (uint32_t it = 1; it <= ILU_SPIN_LIMIT; ++it) {
+  for (uint32_t it = 1; it <= lim; ++it) {
     __nanosleep(32);
     if (ld_acquire(f) == epoch) return true;
     if ((it & 1023u) == 0 && *(volatile int*)err != 0) return false;
@@ -81,7 +79,8 @@ __global__ void __launch_bounds__(ILU_FWARPS * 32)
                       const T* __restrict__ A, T* F, T* Dinv, const int32_t* __restrict__ dpos,
                       const int32_t* __restrict__ lptr, const int32_t* __restrict__ pptr,
                       const uint16_t* __restrict__ pairs, int64_t n_nodes, uint32_t* flags,
-                      uint32_t epoch, unsigned long long* ticket, unsigned long long base, int* err) {
+                      uint32_t epoch, unsigned long long* ticket, unsigned long long base, int* err,
+                      uint32_t lim) {
   __shared__ T srow[ILU_FWARPS][ILU_MAX_DEG * 16];
   const int lane = threadIdx.x & 31;
   T* row = srow[threadIdx.x >> 5];
@@ -101,7 +100,7 @@ __global__ void __launch_bounds__(ILU_FWARPS * 32)
     for (int kk = 0; kk < dp; ++kk) {
       const int64_t k = colidx[r0 + 4 * kk] >> 2;
       int ok = 1;
-      if (lane == 0) ok = wait_ready(flags + k, epoch, err);
+      if (lane == 0) ok = wait_ready(flags + k, epoch, err, lim);
       if (!__shfl_sync(FULL, ok, 0)) return;
       // L_ik = A_ik U_kk^-1 (lanes 0..15 hold entry (q, c))
       T l = T(0);
@@ -188,8 +187,8 @@ __device__ __forceinline__ void ld_relaxed2(const unsigned long long* p, unsigne
 
 // Wait until the four words of a node carry `ep`, then return their values.
 __device__ __forceinline__ bool wait_packed(const unsigned long long* p, uint32_t ep, float out[4],
-                                            int* err) {
-  for (uint32_t it = 0; it <= ILU_SPIN_LIMIT; ++it) {
+                                            int* err, uint32_t lim) {
+  for (uint32_t it = 0; it <= lim; ++it) {
     unsigned long long a, b, c, d;
     ld_relaxed2(p, a, b);
     ld_relaxed2(p + 2, c, d);
@@ -212,9 +211,9 @@ __device__ __forceinline__ bool wait_packed(const unsigned long long* p, uint32_
 // arithmetic never produces); a node is ready once none of its four words holds that pattern.
 constexpr unsigned long long UNSET64 = ~0ull;
 
-__device__ __forceinline__ bool wait_unset(const double* p, double out[4], int* err) {
+__device__ __forceinline__ bool wait_unset(const double* p, double out[4], int* err, uint32_t lim) {
   const unsigned long long* w = reinterpret_cast<const unsigned long long*>(p);
-  for (uint32_t it = 0; it <= ILU_SPIN_LIMIT; ++it) {
+  for (uint32_t it = 0; it <= lim; ++it) {
     unsigned long long a, b, c, d;
     ld_relaxed2(w, a, b);
     ld_relaxed2(w + 2, c, d);
@@ -260,10 +259,10 @@ template <> struct Bits<float> { using U = uint32_t; static constexpr U unset = 
 template <> struct Bits<double> { using U = unsigned long long; static constexpr U unset = ~0ull; };
 
 template <typename T>
-__device__ __forceinline__ bool wait_shared(const T* p, T out[4], int* err) {
+__device__ __forceinline__ bool wait_shared(const T* p, T out[4], int* err, uint32_t lim) {
   using U = typename Bits<T>::U;
   const volatile U* w = reinterpret_cast<const volatile U*>(p);
-  for (uint32_t it = 0; it <= ILU_SPIN_LIMIT; ++it) {
+  for (uint32_t it = 0; it <= lim; ++it) {
     const U a = w[0], b = w[1], c = w[2], d = w[3];
     if (a != Bits<T>::unset && b != Bits<T>::unset && c != Bits<T>::unset && d != Bits<T>::unset) {
       const U u[4] = {a, b, c, d};
@@ -321,7 +320,7 @@ template <typename T, bool LOWER>
 __device__ __forceinline__ bool split_row(const SweepSlot<T>& sl, int r, int64_t i, int dp, int deg,
                                           int lane, const T (&o_rhs)[2][4], T* sx, int64_t a,
                                           int64_t b, void* pub, T* out, int64_t n0, uint32_t ep,
-                                          int* err) {
+                                          int* err, uint32_t lim) {
   const int bl = lane >> 1, h = lane & 1;
   const int kk = LOWER ? bl : dp + 1 + bl;
   const bool mine = LOWER ? kk < dp : kk < deg;
@@ -343,11 +342,11 @@ __device__ __forceinline__ bool split_row(const SweepSlot<T>& sl, int r, int64_t
     T xk[4];
     if (k >= a && k < b) {
       const int64_t sk = LOWER ? k - a : b - 1 - k;
-      ok = wait_shared<T>(sx + 4 * sk, xk, err);
+      ok = wait_shared<T>(sx + 4 * sk, xk, err, lim);
     } else if constexpr (sizeof(T) == 4) {
-      ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err);
+      ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err, lim);
     } else {
-      ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err);
+      ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err, lim);
     }
     if (ok)
       for (int m = 0; m < 4; ++m) {
@@ -405,7 +404,7 @@ __global__ void __launch_bounds__(W * 32)
                      int64_t n_segs, const T* __restrict__ v,
                      const unsigned long long* __restrict__ vp, void* pub, T* __restrict__ out,
                      int64_t n0, int64_t n_rows, uint32_t ep, unsigned long long* ticket,
-                     unsigned long long base, int* err) {
+                     unsigned long long base, int* err, uint32_t lim) {
   constexpr int SLOTS = W * ILU_SEG_MAX;
   __shared__ __align__(16) T sx[SLOTS * 4];
   __shared__ int64_t s_chunk;
@@ -526,7 +525,7 @@ __global__ void __launch_bounds__(W * 32)
         row_offsets(r, rp, dp);
         const int deg = (rp[1] - rp[0]) >> 2;
         if (split_rows(dp, deg)) {
-          if (!split_row<T, LOWER>(sl, r, i, dp, deg, lane, o_rhs, sx, a, b, pub, out, n0, ep, err))
+          if (!split_row<T, LOWER>(sl, r, i, dp, deg, lane, o_rhs, sx, a, b, pub, out, n0, ep, err, lim))
             break;  // an error was recorded; the CTA stops after this chunk
           continue;
         }
@@ -548,11 +547,11 @@ __global__ void __launch_bounds__(W * 32)
           T xk[4];
           if (k >= a && k < b) {  // a row of this chunk: shared memory
             const int64_t sk = LOWER ? k - a : b - 1 - k;
-            ok = wait_shared<T>(sx + 4 * sk, xk, err);
+            ok = wait_shared<T>(sx + 4 * sk, xk, err, lim);
           } else if constexpr (sizeof(T) == 4) {
-            ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err);
+            ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err, lim);
           } else {
-            ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err);
+            ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err, lim);
           }
           if (ok)
             for (int rr = 0; rr < 4; ++rr)
@@ -726,18 +725,21 @@ __global__ void convert_kernel(const A* __restrict__ x, B* __restrict__ y, int64
 template <typename A, typename B>
 int convert(const A* x, B* y, int64_t n, cudaStream_t st) {
   const int64_t b = (n + 255) / 256;
-  convert_kernel<A, B><<<(unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b)), 256, 0, st>>>(x, y, n);
+  const int64_t cap = (int64_t)sm_count() * 8;
+  convert_kernel<A, B><<<(unsigned)(b > cap ? cap : (b < 1 ? 1 : b)), 256, 0, st>>>(x, y, n);
   return 1;
 }
 
 }  // namespace
 
 void free_ilu(Ilu& p) {
+  const uint32_t lim = p.spin_limit;  // a setting of the context, kept across meshes
   void* bufs[] = {p.dpos, p.lptr, p.pptr, p.pairs, p.F, p.Dinv, p.y, p.x64, p.F32, p.Dinv32,
                   p.vals64, p.flags, p.yp, p.xp, p.tickets, p.err, p.seg};
   for (void* b : bufs)
     if (b) cudaFree(b);
   p = Ilu();
+  p.spin_limit = lim;
 }
 
 int ilu_factor(vms_ctx* ctx, Ilu& p, const Mesh& m, bool fp32, const void* values, cudaStream_t st,
@@ -756,11 +758,11 @@ int ilu_factor(vms_ctx* ctx, Ilu& p, const Mesh& m, bool fp32, const void* value
     *launches += convert<float, double>((const float*)values, p.vals64, m.nnz, st);
     A = p.vals64;
   }
-  const unsigned ctas = resident_ctas(m.n_nodes, ILU_FWARPS, 152 * 8);
+  const unsigned ctas = resident_ctas(m.n_nodes, ILU_FWARPS, 8 * sm_count());
   const uint32_t ep = next_epoch(p, st);
   ilu_factor_kernel<double><<<ctas, ILU_FWARPS * 32, 0, st>>>(
       m.rowptr, m.colidx, A, p.F, p.Dinv, p.dpos, p.lptr, p.pptr, p.pairs, m.n_nodes, p.flags, ep,
-      p.tickets, p.base, p.err);
+      p.tickets, p.base, p.err, p.spin_limit);
   p.base += (unsigned long long)m.n_nodes + (unsigned long long)ctas * ILU_FWARPS;
   *launches += 1;
   if (fp32) {
@@ -790,7 +792,7 @@ int ilu_apply<float, float>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const
   segment_range(p, n0, n1, s0, ns);
   constexpr int W = sweep_warps<float>();
   const int64_t chunks = (ns + W - 1) / W;
-  const unsigned ctas = resident_ctas(chunks, 1, ILU_SWEEP_CTAS);
+  const unsigned ctas = resident_ctas(chunks, 1, 4 * sm_count());  // at most four CTAs per SM
   const unsigned long long claims = (unsigned long long)chunks + ctas;  // + each CTA's last claim
   uint32_t ep = next_epoch(p, st);
   const size_t ring = sweep_ring_bytes<float>(W);
@@ -799,12 +801,12 @@ int ilu_apply<float, float>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, const
   cudaFuncSetAttribute(ilu_sweep_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
   ilu_sweep_kernel<float, true><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F32, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, p.yp, nullptr, n0,
-      rows, ep, p.tickets, p.base, p.err);
+      rows, ep, p.tickets, p.base, p.err, p.spin_limit);
   p.base += claims;
   ep = next_epoch(p, st);
   ilu_sweep_kernel<float, false><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F32, p.Dinv32, p.dpos, p.seg, s0, ns, nullptr, p.yp, p.xp, z, n0,
-      rows, ep, p.tickets, p.base, p.err);
+      rows, ep, p.tickets, p.base, p.err, p.spin_limit);
   p.base += claims;
   return 2;
 }
@@ -817,7 +819,7 @@ int ilu_apply<double, double>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, con
   segment_range(p, n0, n1, s0, ns);
   constexpr int W = sweep_warps<double>();
   const int64_t chunks = (ns + W - 1) / W;
-  const unsigned ctas = resident_ctas(chunks, 1, ILU_SWEEP_CTAS);
+  const unsigned ctas = resident_ctas(chunks, 1, 4 * sm_count());  // at most four CTAs per SM
   const unsigned long long claims = (unsigned long long)chunks + ctas;  // + each CTA's last claim
   double* y = p.y;
   double* x = p.x64;
@@ -828,12 +830,12 @@ int ilu_apply<double, double>(Ilu& p, const Mesh& m, int64_t n0, int64_t n1, con
   cudaFuncSetAttribute(ilu_sweep_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
   ilu_sweep_kernel<double, true><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F, nullptr, p.dpos, p.seg, s0, ns, v, nullptr, y, nullptr, n0, rows, 0,
-      p.tickets, p.base, p.err);
+      p.tickets, p.base, p.err, p.spin_limit);
   p.base += claims;
   cudaMemsetAsync(x + 4 * n0, 0xff, sizeof(double) * 4 * rows, st);
   ilu_sweep_kernel<double, false><<<ctas, W * 32, ring, st>>>(
       m.rowptr, m.colidx, p.F, p.Dinv, p.dpos, p.seg, s0, ns, y, nullptr, x, z, n0, rows, 0,
-      p.tickets, p.base, p.err);
+      p.tickets, p.base, p.err, p.spin_limit);
   p.base += claims;
   return 4;
 }

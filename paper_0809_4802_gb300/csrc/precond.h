@@ -7,6 +7,12 @@
 
 namespace vms {
 
+constexpr int ILU_ERR_TIMEOUT = 1;
+constexpr uint32_t ILU_SPIN_DEFAULT = 1u << 22;  // with a 32 ns sleep per poll: about 0.13 s
+constexpr int ILU_ERR_PIVOT = 2;
+constexpr int ILU_MAX_DEG = 32;
+constexpr int ILU_SEG_MAX = 64;
+
 // Block ILU(0) of the node-block matrix (4x4 blocks, natural node order), factored and applied on
 // the device by warps that each own one node row and wait for the rows their row depends on.
 struct Ilu {
@@ -36,13 +42,10 @@ struct Ilu {
   int* err = nullptr;          // device error word: 0, ILU_ERR_TIMEOUT or ILU_ERR_PIVOT
   uint32_t epoch = 0;
   unsigned long long base = 0; // claims made on `tickets` by earlier launches
+  uint32_t spin_limit = ILU_SPIN_DEFAULT;  // polls of one device-side wait before it gives up
   bool factored = false;
 };
 
-constexpr int ILU_ERR_TIMEOUT = 1;
-constexpr int ILU_ERR_PIVOT = 2;
-constexpr int ILU_MAX_DEG = 32;
-constexpr int ILU_SEG_MAX = 64;
 
 void free_ilu(Ilu& p);
 

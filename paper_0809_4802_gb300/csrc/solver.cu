@@ -408,8 +408,8 @@ __global__ void recover_kernel(const int32_t* __restrict__ conn, int npe, const 
 // host side
 // ---------------------------------------------------------------------------------------------
 static unsigned grid_for(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b));
+  const int64_t b = (n + 255) / 256, cap = (int64_t)sm_count() * 8;
+  return (unsigned)(b > cap ? cap : (b < 1 ? 1 : b));
 }
 
 // Rows can be taken four at a time when the length, the stride and every pointer allow 16-byte
@@ -429,7 +429,7 @@ static int dots(const VT* V, int64_t ld, int m, const VT* w, int64_t n, double* 
   const bool quad = quad_ok(n, ld, sizeof(VT), {V, w});
   const int groups = (m + MD_K - 1) / MD_K;
   const int64_t units = quad ? n / 4 : n;
-  int64_t nb = (4 * 152 + groups - 1) / groups;  // about four blocks per SM in all
+  int64_t nb = (4 * (int64_t)sm_count() + groups - 1) / groups;  // about four blocks per SM in all
   nb = std::min<int64_t>(nb, (units + MD_THREADS - 1) / MD_THREADS);
   nb = std::max<int64_t>(1, std::min<int64_t>(nb, MD_MAX_BLOCKS));
   mdot_kernel<VT><<<dim3((unsigned)nb, (unsigned)groups), MD_THREADS, 0, st>>>(V, ld, m, w, n, quad, partial);
@@ -745,6 +745,8 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
   G.restart_cap = std::min(std::max(restart_cap, restart), MAX_RESTART);
   if (int rc = G.sync_host(&bnorm2, hd + H_NORM, sizeof(double))) return rc;
   const double bnorm = std::sqrt(bnorm2);
+  // a non-finite right-hand side is reported as such before any preconditioner sweep runs
+  if (!std::isfinite(bnorm)) return ctx_fail(ctx, VMS_ERR_NAN, "non-finite right-hand side");
   if (bnorm == 0.0) {
     KScope k(ctx, VMS_K_FILL);
     k.add(launch_fill_zero(w.x, sizeof(double) * n, st));
@@ -975,6 +977,13 @@ extern "C" {
 int vms_solve(vms_ctx* ctx, double rtol, int maxit, int restart, int update, int* iters,
               double* rel) {
   return solve_impl(ctx, whole(ctx), -1, rtol, maxit, restart, restart, update, 0.0, iters, rel);
+}
+
+int vms_set_wait_limit(vms_ctx* ctx, int64_t polls) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (polls < 0 || polls > ((int64_t)1 << 30)) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "wait limit out of range");
+  ctx_solver(ctx).ilu.spin_limit = polls == 0 ? ILU_SPIN_DEFAULT : (uint32_t)polls;
+  return VMS_OK;
 }
 
 int vms_solve_instance(vms_ctx* ctx, int64_t instance, double rtol, int maxit, int restart,

@@ -318,7 +318,7 @@ __global__ void to_fp32_kernel(const double4_32a* __restrict__ u, const double* 
 int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, cudaStream_t st) {
   const int64_t n = m.n_nodes > 3 * m.n_elems ? m.n_nodes : 3 * m.n_elems;
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
   to_fp32_kernel<<<(unsigned)blocks, 256, 0, st>>>(s.u, s.beta, c.u, c.beta, m.n_nodes,
                                                    m.n_elems);
   return 1;
@@ -333,7 +333,7 @@ static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const K
   auto kern = tangent_kernel<T, ELEM_OUT, ATOMIC, WARPS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = (count + WARPS - 1) / WARPS;
-  if (blocks > 152 * 128) blocks = 152 * 128;
+  if (blocks > (int64_t)sm_count() * 128) blocks = (int64_t)sm_count() * 128;
   using NV = typename NodeVec<T>::type;
   const NV* u;
   const T* beta;

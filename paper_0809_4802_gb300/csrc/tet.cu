@@ -660,8 +660,8 @@ __global__ void __launch_bounds__(TET_WARPS * 32) tet_residual_kernel(
 
 unsigned tet_blocks(int64_t count) {
   const int64_t per = TET_WARPS * TET_PER_WARP;
-  int64_t b = (count + per - 1) / per;
-  return (unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+  const int64_t b = (count + per - 1) / per, cap = (int64_t)sm_count() * 32;
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 template <typename T, bool ELEM_OUT, bool ATOMIC>

@@ -182,6 +182,10 @@ int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOu
 // FP32 copies of the nodal state and of beta.
 int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, cudaStream_t st);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, looked up once
+// per device). Grid sizes are multiples of it.
+int sm_count();
+
 int launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
 int launch_dirichlet_diag(const Mesh& m, void* values, bool fp32, double* rhs, cudaStream_t st);
 int launch_zero_dofs(const int64_t* dofs, int64_t n, double* v, cudaStream_t st);

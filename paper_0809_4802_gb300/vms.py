@@ -51,6 +51,7 @@ EXPORTS = [
     "vms_mlp_set_params", "vms_mlp_get_params", "vms_mlp_forward", "vms_mlp_grad", "vms_mlp_adam",
     "vms_node_features", "vms_node_increment", "vms_apply_increment", "vms_shift_time",
     "vms_newton_solve_to", "vms_state_download_prev", "vms_mesh_upload_tet", "vms_tet_rule",
+    "vms_set_wait_limit", "vms_csr_download", "vms_fma_throughput",
 ]
 MLP_IN, MLP_WIDTH, MLP_OUT, MLP_PARAMS = 12, 128, 4, 18692
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
@@ -144,6 +145,9 @@ def load_library(path: str = LIB_PATH):
         "vms_solver_stats": (c_int, [p, c_int, POINTER(c_int64), POINTER(c_int64)]),
         "vms_residual_norm_noalloc": (c_int, [c_int64, p, c_int64, p, c_int64, p, p, p, p,
                                               POINTER(VmsParams), p, p, p]),
+        "vms_set_wait_limit": (c_int, [p, c_int64]),
+        "vms_csr_download": (c_int, [p, p, p, p, p]),
+        "vms_fma_throughput": (c_int, [c_int, c_int, POINTER(c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -283,6 +287,18 @@ class Context:
     def csr_host(self):
         rowptr, colidx, vals, rhs = self.csr_device()
         return (rowptr.cpu().numpy(), colidx.cpu().numpy(), vals.cpu().numpy(), rhs.cpu().numpy())
+
+    def csr_download(self, rowptr=None, colidx=None, values=None, rhs=None):
+        """Copy the last assembled system into caller buffers (numpy arrays or torch tensors, host
+        or device; values FP32 in mixed precision, FP64 otherwise)."""
+        vdt = np.float32 if self.precision != PREC_FP64 else np.float64
+        self._check(self.lib.vms_csr_download(self.h, _ptr(rowptr, np.int32), _ptr(colidx, np.int32),
+                                              _ptr(values, vdt), _ptr(rhs, np.float64)))
+
+    def set_wait_limit(self, polls: int):
+        """Polls of one device-side wait of the ILU(0) kernels before the solve gives up
+        (VMS_ERR_TIMEOUT); 0 restores the default."""
+        self._check(self.lib.vms_set_wait_limit(self.h, int(polls)))
 
     def residual(self, want_vector=False):
         norm = c_double()
@@ -471,6 +487,15 @@ def tet_rule(n: int):
     if rc != OK:
         raise VmsError(rc, "vms_tet_rule failed")
     return pts, wts
+
+
+def fma_throughput(device: int, kind: int) -> float:
+    """Measured TFLOP/s of the GPU's FMA pipe: kind 0 FP64, 1 FP32, 2 packed FP32."""
+    t = c_double()
+    rc = load_library().vms_fma_throughput(int(device), int(kind), byref(t))
+    if rc != OK:
+        raise VmsError(rc, "vms_fma_throughput failed")
+    return t.value
 
 
 def version() -> str:
