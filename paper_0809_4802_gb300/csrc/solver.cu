@@ -21,8 +21,10 @@ void free_solver(SolverWork& s) {
                   s.xb, s.rb};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  const uint32_t lim = s.ilu.spin_limit;  // a setting of the context, kept across re-allocations
   free_ilu(s.ilu);
   s = SolverWork();
+  s.ilu.spin_limit = lim;
 }
 
 // ---------------------------------------------------------------------------------------------
