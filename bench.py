@@ -475,6 +475,19 @@ def roofline_entries(kern, E, prec, tet, peaks, workload):
                     "ms": ms, "achieved": fpe * E / (ms * 1e-3) / 1e12, "peak": peaks["fp64_tflops"],
                     "traffic": NCU_TRAFFIC_BYTES.get(("tangent", workload))})
     else:
+        if "fused" in kern:
+            # one launch holds both element kernels: its FP64 (residual) and FP32 (tangent) work
+            # are each set against their own pipe's peak over the launch's duration
+            ms = kern["fused"]
+            for name, pipe, part in (("residual", "fp64", "FP64 residual work"),
+                                     ("tangent", "fp32", "FP32 tangent work")):
+                fpe = ALG_FLOPS[name]
+                out.append({"bound": "alu", "kernel": "fused_assembly", "pipe": pipe, "unit": "TFLOP/s",
+                            "part": part, "flops_per_element": fpe,
+                            "executed_flops_per_element": EXECUTED_FLOPS["residual"] if pipe == "fp64" else None,
+                            "ms": ms, "achieved": fpe * E / (ms * 1e-3) / 1e12,
+                            "peak": peaks["fp64_tflops"] if pipe == "fp64" else peaks["fp32_tflops"],
+                            "traffic": NCU_TRAFFIC_BYTES.get(("fused", workload))})
         for name, pipe in (("residual", "fp64"), ("tangent", "fp32" if prec == 1 else "fp64")):
             if name not in kern:
                 continue
@@ -553,14 +566,27 @@ def ours(args):
     ms = max_over_ranks(ms)
     value = ws * E * args.steps / (ms / 1000.0)
 
+    # ---- the other kernel schedule of the mixed step (two kernels on two streams), for reference ----
+    schedules = None
+    if prec == 1 and not tet and batch is None and args.scatter == 0:
+        ctx.set_tuning(schedule=vms.SCHEDULE_TWO_STREAMS)
+        for _ in range(2):
+            ctx.assemble()
+        ms_two, _ = timed_assembly(ctx, stream, args.steps, flush, barrier, dev)
+        ctx.set_tuning(schedule=vms.SCHEDULE_FUSED)
+        ctx.assemble()
+        schedules = {"fused_ms_per_step": ms / args.steps, "two_streams_ms_per_step": ms_two / args.steps}
+
     # ---- per-kernel times (events inside the library, on each kernel's stream) ----
     kern = kernel_times(ctx, args.steps, flush)
     entries = roofline_entries(kern, E, prec, tet, peaks, args.workload)
-    # the dominant kernel: the largest share of the step's device time when the kernels run one
-    # after another (the ncu launch list): the FP64 residual in mixed precision, the tangent in
-    # FP64, the single assembly kernel of the tetrahedron. In the step the residual and the
-    # tangent overlap on two streams; every kernel's own entry is in `kernels`.
-    dom_name = "tet_assembly" if tet else ("tangent" if prec == 0 else "residual")
+    # the dominant kernel: the largest share of the step's device time (the ncu launch list): the
+    # fused residual + tangent kernel in mixed precision (its FP64 part, the binding pipe; with two
+    # kernels on two streams the FP64 residual), the tangent in FP64, the single assembly kernel of
+    # the tetrahedron. Every kernel's own entry is in `kernels`.
+    kinds = [r["kernel"] for r in entries]
+    dom_name = ("tet_assembly" if tet else "tangent" if prec == 0 else
+                "fused_assembly" if "fused_assembly" in kinds else "residual")
     roofline = dict(next(r for r in entries if r["kernel"] == dom_name))
     roofline["kernels"] = entries
     roofline["kernel_ms"] = {k: round(v, 4) for k, v in kern.items()}
@@ -685,7 +711,7 @@ def ours(args):
             "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
             "config": workload_config(args.workload, wl, prec, batch),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "other_precision": other, "newton": newton,
+            "other_precision": other, "schedules": schedules, "newton": newton,
             "scatter": "colour" if args.scatter == 1 else "atomic",
             "tuning": tuning, "graph": bool(batch is not None or args.graph),
             "per_instance_solve": per_instance, "warm_start": warm,

@@ -215,24 +215,32 @@ int vms_set_instances(vms_ctx* ctx, int64_t count, const int64_t* node_offsets,
 int vms_solve_instance(vms_ctx* ctx, int64_t instance, double rtol, int maxit, int restart,
                        int update, int* iters, double* rel);
 
-/* Launch shapes and scatter order of the assembly kernels. */
+/* Kernel schedules of a mixed-precision assembly with the atomic scatter (vms_tuning.schedule). */
+#define VMS_SCHEDULE_FUSED 0        /* one persistent launch: FP64 residual warps and FP32 tangent
+                                       warps share every SM (default) */
+#define VMS_SCHEDULE_TWO_STREAMS 1  /* residual and tangent kernels launched on two streams */
+
+/* Launch shapes, kernel schedule and scatter order of the assembly kernels. */
 typedef struct vms_tuning {
   int32_t tangent_warps;    /* warps (elements) per tangent block: FP32 2, 4 or 8, FP64 1, 2 or 4; 0 = default (4 / 2) */
   int32_t residual_threads; /* threads (elements) per residual block: 32 or 64; 0 = default (64) */
   int32_t scatter_mode;     /* VMS_SCATTER_*, or -1 for params.scatter_mode */
-  int32_t reserved;         /* 0 */
+  int32_t schedule;         /* VMS_SCHEDULE_*: used in VMS_PREC_MIXED with the atomic scatter (the
+                               fused kernel takes no block shape); the other cases run two kernels */
   double ms;                /* vms_autotune: median milliseconds of one assembly with these settings */
 } vms_tuning;
 
-/* Set or read the tuning of the context (defaults: {0, 0, -1}). Results do not depend on it except
- * for the summation order of the atomic scatter. Errors: VMS_ERR_INVALID_ARG (value not offered). */
+/* Set or read the tuning of the context (defaults: {0, 0, -1, VMS_SCHEDULE_FUSED}). Results do not
+ * depend on it except for the summation order of the atomic scatter. Errors: VMS_ERR_INVALID_ARG
+ * (value not offered). */
 int vms_set_tuning(vms_ctx* ctx, const vms_tuning* tuning);
 int vms_get_tuning(vms_ctx* ctx, vms_tuning* tuning);
 
 /* Autotuner: time `repeats` assemblies (CUDA events on the context's stream, after one warm-up)
- * of the current mesh and state for every offered combination of tangent warps per block,
- * residual threads per block and scatter mode, keep the fastest (median) as the context's tuning
- * and return it in *best (may be NULL). The assembled system is discarded (assemble again).
+ * of the current mesh and state for every offered tuning (in VMS_PREC_MIXED the fused schedule,
+ * and every combination of tangent warps per block, residual threads per block and scatter mode
+ * with two kernels), keep the fastest (median) as the context's tuning and return it in *best
+ * (may be NULL). The assembled system is discarded (assemble again).
  * Errors: VMS_ERR_STATE (no state), those of vms_assemble_newton_schur. */
 int vms_autotune(vms_ctx* ctx, int repeats, vms_tuning* best);
 
@@ -356,7 +364,8 @@ int vms_shift_time(vms_ctx* ctx);
 #define VMS_K_SPMV 5      /* CSR matrix-vector products */
 #define VMS_K_KRYLOV 6    /* other Krylov / recovery / update kernels */
 #define VMS_K_PRECOND 7   /* preconditioner set-up and application (ILU(0) factor and sweeps) */
-#define VMS_K_COUNT 8
+#define VMS_K_FUSED 8     /* fused residual + tangent kernel (VMS_SCHEDULE_FUSED) */
+#define VMS_K_COUNT 9
 
 /* Count every kernel launch of the context (always on) and, if `timing` != 0, bracket each launch
  * with CUDA events on the context's stream to accumulate its GPU time per kernel kind. */

@@ -42,7 +42,7 @@ struct vms_ctx {
   std::vector<int64_t> inst_nodes, inst_elems;
   std::vector<uint8_t> inst_stale;  // instance updated since the last assembly
   bool any_stale = false;
-  vms_tuning tune{0, 0, -1, 0, 0.0};  // launch shapes and scatter mode (vms_set_tuning)
+  vms_tuning tune{0, 0, -1, VMS_SCHEDULE_FUSED, 0.0};  // launch shapes, schedule, scatter (vms_set_tuning)
   // CUDA graph of one assembly (vms_set_graph)
   bool use_graph = false;
   bool graph_dirty = true;
@@ -121,7 +121,7 @@ void free_mesh(vms_ctx* c) {
   s = State();
   Work& w = c->work;
   dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recW); dfree(w.recKinv);
-  dfree(w.recY); dfree(w.resid); dfree(w.partial); dfree(w.flags);
+  dfree(w.recY); dfree(w.resid); dfree(w.partial); dfree(w.flags); dfree(w.queues);
   dfree(w.f32.u); dfree(w.f32.beta);
   cudaStream_t aux = w.aux;
   cudaEvent_t fork = w.fork, join = w.join;
@@ -391,7 +391,8 @@ int vms_set_tuning(vms_ctx* ctx, const vms_tuning* t) {
   bool warps_ok = t->tangent_warps == 0;
   for (int k = 0; k < 3; ++k) warps_ok = warps_ok || t->tangent_warps == tangent_warp_choice(f32, k);
   if (!warps_ok || (t->residual_threads != 0 && t->residual_threads != 32 && t->residual_threads != 64) ||
-      t->scatter_mode < -1 || t->scatter_mode > VMS_SCATTER_COLOUR)
+      t->scatter_mode < -1 || t->scatter_mode > VMS_SCATTER_COLOUR ||
+      (t->schedule != VMS_SCHEDULE_FUSED && t->schedule != VMS_SCHEDULE_TWO_STREAMS))
     return fail(ctx, VMS_ERR_INVALID_ARG, "invalid tuning");
   ctx->tune = *t;
   ctx->graph_dirty = true;
@@ -412,30 +413,34 @@ int vms_autotune(vms_ctx* ctx, int repeats, vms_tuning* best) {
   cudaEvent_t a = nullptr, b = nullptr;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
-  vms_tuning win{0, 0, -1, 0, HUGE_VAL};
-  int rc = VMS_OK;
-  for (int wk = 0; wk < 3 && rc == VMS_OK; ++wk)
+  vms_tuning win{0, 0, -1, VMS_SCHEDULE_FUSED, HUGE_VAL};
+  std::vector<vms_tuning> cands;
+  if (f32) cands.push_back(vms_tuning{0, 0, VMS_SCATTER_ATOMIC, VMS_SCHEDULE_FUSED, 0.0});
+  for (int wk = 0; wk < 3; ++wk)
     for (int rt : {32, 64})
-      for (int sm = VMS_SCATTER_ATOMIC; sm <= VMS_SCATTER_COLOUR && rc == VMS_OK; ++sm) {
-        ctx->tune = vms_tuning{tangent_warp_choice(f32, wk), rt, sm, 0, 0.0};
-        ctx->graph_dirty = true;
-        if ((rc = vms_assemble_newton_schur(ctx, nullptr))) break;  // warm-up (and graph capture)
-        std::vector<float> t(repeats);
-        for (int r = 0; r < repeats && rc == VMS_OK; ++r) {
-          cudaEventRecord(a, ctx->stream);
-          rc = vms_assemble_newton_schur(ctx, nullptr);
-          cudaEventRecord(b, ctx->stream);
-          cudaEventSynchronize(b);
-          cudaEventElapsedTime(&t[r], a, b);
-        }
-        if (rc) break;
-        std::sort(t.begin(), t.end());
-        const double med = t[repeats / 2];
-        if (med < win.ms) win = vms_tuning{ctx->tune.tangent_warps, rt, sm, 0, med};
-      }
+      for (int sm = VMS_SCATTER_ATOMIC; sm <= VMS_SCATTER_COLOUR; ++sm)
+        cands.push_back(vms_tuning{tangent_warp_choice(f32, wk), rt, sm, VMS_SCHEDULE_TWO_STREAMS, 0.0});
+  int rc = VMS_OK;
+  for (const vms_tuning& cand : cands) {
+    ctx->tune = cand;
+    ctx->graph_dirty = true;
+    if ((rc = vms_assemble_newton_schur(ctx, nullptr))) break;  // warm-up (and graph capture)
+    std::vector<float> t(repeats);
+    for (int r = 0; r < repeats && rc == VMS_OK; ++r) {
+      cudaEventRecord(a, ctx->stream);
+      rc = vms_assemble_newton_schur(ctx, nullptr);
+      cudaEventRecord(b, ctx->stream);
+      cudaEventSynchronize(b);
+      cudaEventElapsedTime(&t[r], a, b);
+    }
+    if (rc) break;
+    std::sort(t.begin(), t.end());
+    const double med = t[repeats / 2];
+    if (med < win.ms) { win = cand; win.ms = med; }
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  ctx->tune = rc == VMS_OK ? win : vms_tuning{0, 0, -1, 0, 0.0};
+  ctx->tune = rc == VMS_OK ? win : vms_tuning{0, 0, -1, VMS_SCHEDULE_FUSED, 0.0};
   ctx->graph_dirty = true;
   ctx->work.assembled = false;
   if (rc) return rc;
@@ -532,6 +537,7 @@ static int mesh_upload_impl(vms_ctx* ctx, int npe, int64_t n_nodes, const double
   CK(cudaMalloc(&w.resid, sizeof(double) * (4 * n_nodes + 3 * n_elems)));
   CK(cudaMalloc(&w.partial, sizeof(double) * 1024));
   CK(cudaMalloc(&w.flags, sizeof(unsigned int)));
+  CK(cudaMalloc(&w.queues, 2 * sizeof(unsigned long long)));
   return VMS_OK;
 }
 
@@ -633,6 +639,25 @@ static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
   const void* tab = f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64;
   const int scatter = ctx->tune.scatter_mode >= 0 ? ctx->tune.scatter_mode : ctx->params.scatter_mode;
   const bool colour = scatter == VMS_SCATTER_COLOUR;
+  if (f32 && !colour && ctx->tune.schedule == VMS_SCHEDULE_FUSED) {
+    // residual and tangent in one persistent launch, then r_e and the Dirichlet rows
+    {
+      KScope k(ctx, VMS_K_FILL, st);
+      k.add(launch_fill_zero(w.queues, 2 * sizeof(unsigned long long), st));
+    }
+    {
+      KScope k(ctx, VMS_K_FUSED, st);
+      k.add(launch_fused_assembly(m, ctx->state, w.f32, kp, ctx->d_qp, ctx->d_tab32, w.elemR, o,
+                                  w.queues, w.flags, st));
+    }
+    {
+      KScope k(ctx, VMS_K_DIRICHLET, st);
+      k.add(launch_finish(f32, m, w.elemR, o, 0, m.n_elems, nullptr, true, st));
+    }
+    { KScope k(ctx, VMS_K_DIRICHLET, st); k.add(launch_dirichlet_diag(m, w.values, f32, w.rhs, st)); }
+    CK(cudaGetLastError());
+    return VMS_OK;
+  }
   // the FP64 residual kernel (this stream) and the tangent kernel (auxiliary stream, FP32 or FP64
   // pipe) are independent and run concurrently; the finish kernel joins them
   CK(cudaEventRecord(w.fork, st));

@@ -59,7 +59,7 @@ struct NaStore {
   double (*sc)[64];
   int tid;
   __device__ __forceinline__ double get(int k) const { return sc[k][tid]; }
-  __device__ __forceinline__ void set(int k, double v) { sc[k][tid] = v; }
+  __device__ __forceinline__ void set(int k, double v) const { sc[k][tid] = v; }
 };
 
 // The quadrature table is written by a kernel queued before the residual kernel, which only reads it.
@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(64) na_residual_kernel(
     const double* __restrict__ xyz, const double* __restrict__ u, const double* __restrict__ uprev,
     const int32_t* __restrict__ conn, const double* __restrict__ beta, KParams kp,
     int64_t n_nodes, int64_t n_elems, double* __restrict__ scratch) {
-  __shared__ double sc[RC_N][64];
+  extern __shared__ __align__(16) unsigned char na_smem[];
+  double (*sc)[64] = reinterpret_cast<double (*)[64]>(na_smem);
   const int tid = threadIdx.x;
   const int64_t e = (int64_t)blockIdx.x * 64 + tid;
   if (e >= n_elems) return;
@@ -269,12 +270,17 @@ extern "C" int vms_residual_norm_noalloc(int64_t n_nodes, const double* xyz, int
                                         reinterpret_cast<QpRow*>(scratch + NA_QP));
   const unsigned eb = (unsigned)((n_elems + 63) / 64);
   const double* up = u_prev ? u_prev : u;
+  const size_t smem = sizeof(double) * RC_N * 64;  // the coefficient store (above 48 KB)
+  auto launch = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<eb, 64, smem, st>>>(xyz, u, up, conn, beta, kp, n_nodes, n_elems, scratch);
+  };
   if (kp.transient) {
-    if (kp.has_force) na_residual_kernel<true, true><<<eb, 64, 0, st>>>(xyz, u, up, conn, beta, kp, n_nodes, n_elems, scratch);
-    else na_residual_kernel<true, false><<<eb, 64, 0, st>>>(xyz, u, up, conn, beta, kp, n_nodes, n_elems, scratch);
+    if (kp.has_force) launch(na_residual_kernel<true, true>);
+    else launch(na_residual_kernel<true, false>);
   } else {
-    if (kp.has_force) na_residual_kernel<false, true><<<eb, 64, 0, st>>>(xyz, u, up, conn, beta, kp, n_nodes, n_elems, scratch);
-    else na_residual_kernel<false, false><<<eb, 64, 0, st>>>(xyz, u, up, conn, beta, kp, n_nodes, n_elems, scratch);
+    if (kp.has_force) launch(na_residual_kernel<false, true>);
+    else launch(na_residual_kernel<false, false>);
   }
   if (n_dir > 0)
     na_zero_dofs_kernel<<<(unsigned)((n_dir + 255) / 256), 256, 0, st>>>(dir_dof, n_dir, 4 * n_nodes, scratch);

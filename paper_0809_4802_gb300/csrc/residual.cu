@@ -1,38 +1,14 @@
 // FP64 element residual kernel (Section 4.1), one thread per element; arithmetic in
 // residual_math.cuh.
 #include "residual_math.cuh"
+#include "residual_table.cuh"
 #include "vms_internal.h"
 
 namespace vms {
 
 // Threads per block: 64 by default; the autotuner (vms_autotune) may choose 32.
 constexpr int RES_THREADS = 64;
-
-// Monomial coefficients live in shared memory, one column per thread (conflict-free).
-template <int THREADS>
-struct SmemStore {
-  double (*sc)[THREADS];
-  int tid;
-  __device__ __forceinline__ double get(int k) const { return sc[k][tid]; }
-  __device__ __forceinline__ void set(int k, double v) { sc[k][tid] = v; }
-};
-
-// Per-point table in global memory; every thread of a warp reads the same row (broadcast).
-struct GlobalTable {
-  const QpRow* __restrict__ t;
-  __device__ __forceinline__ double xi(int q) const { return __ldg(&t[q].xi); }
-  __device__ __forceinline__ double eta(int q) const { return __ldg(&t[q].eta); }
-  __device__ __forceinline__ double zeta(int q) const { return __ldg(&t[q].zeta); }
-  __device__ __forceinline__ double xe(int q) const { return __ldg(&t[q].xe); }
-  __device__ __forceinline__ double xz(int q) const { return __ldg(&t[q].xz); }
-  __device__ __forceinline__ double ez(int q) const { return __ldg(&t[q].ez); }
-  __device__ __forceinline__ double xez(int q) const { return __ldg(&t[q].xez); }
-  __device__ __forceinline__ double b(int q) const { return __ldg(&t[q].b); }
-  __device__ __forceinline__ double db(int q, int al) const {
-    return al == 0 ? __ldg(&t[q].db0) : (al == 1 ? __ldg(&t[q].db1) : __ldg(&t[q].db2));
-  }
-  __device__ __forceinline__ double w(int q) const { return __ldg(&t[q].w); }
-};
+static_assert(FLAG_NEG_JACOBIAN == 1u && FLAG_NAN == 4u, "residual_element error bits");
 
 template <bool TRANSIENT, bool FORCE, int THREADS>
 __global__ void __launch_bounds__(THREADS) residual_kernel(
@@ -42,52 +18,21 @@ __global__ void __launch_bounds__(THREADS) residual_kernel(
     int64_t count,
     double* __restrict__ elemR, double* __restrict__ resid, const uint32_t* __restrict__ dir_mask,
     int64_t n_nodes, int mode, unsigned int* __restrict__ flags) {
-  __shared__ double sc[RC_N][THREADS];
+  extern __shared__ __align__(16) unsigned char res_smem[];
+  double (*sc)[THREADS] = reinterpret_cast<double (*)[THREADS]>(res_smem);
   const int tid = threadIdx.x;
   const int64_t t = (int64_t)blockIdx.x * THREADS + tid;
   if (t >= count) return;
   const int64_t e = first + t;
 
   int nd[8];
-  {
-    const int4* cp = reinterpret_cast<const int4*>(conn + 8 * e);
-    const int4 c0 = cp[0], c1 = cp[1];
-    nd[0] = c0.x; nd[1] = c0.y; nd[2] = c0.z; nd[3] = c0.w;
-    nd[4] = c1.x; nd[5] = c1.y; nd[6] = c1.z; nd[7] = c1.w;
-  }
   SmemStore<THREADS> C{sc, tid};
-  {
-    double X[8][3], U[8][4], Up[8][3];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const double4_32a x = xyz[nd[a]];
-      const double4_32a w = u[nd[a]];
-      X[a][0] = x.x; X[a][1] = x.y; X[a][2] = x.z;
-      U[a][0] = w.x; U[a][1] = w.y; U[a][2] = w.z; U[a][3] = w.w;
-      if (TRANSIENT) {
-        const double4_32a o = uprev[nd[a]];
-        Up[a][0] = o.x; Up[a][1] = o.y; Up[a][2] = o.z;
-      }
-    }
-    residual_load(C, X, U, Up, TRANSIENT);
-  }
-  const double bet[3] = {beta[3 * e + 0], beta[3 * e + 1], beta[3 * e + 2]};
   double Rcp[32], Rf[3];
-  const double nut = kp.nu_e ? kp.visc_factor * __ldg(kp.nu_e + e) : kp.nut;
-  const bool ok = residual_qp_loop<TRANSIENT, FORCE>(C, GlobalTable{qp}, kp.nq, bet, nut, kp.tau,
-                                                     kp.f, Rcp, Rf);
-  if (!ok) atomicOr(flags, FLAG_NEG_JACOBIAN);
-  bool finite = isfinite(Rf[0]) && isfinite(Rf[1]) && isfinite(Rf[2]);
-#pragma unroll
-  for (int k = 0; k < 32; ++k) finite = finite && isfinite(Rcp[k]);
-  if (!finite) atomicOr(flags, FLAG_NAN);
-
+  const unsigned bad = residual_element<TRANSIENT, FORCE>(e, C, GlobalTable{qp}, kp, xyz, u, uprev,
+                                                          conn, beta, nd, Rcp, Rf);
+  if (bad) atomicOr(flags, bad);  // bits 1 and 4: FLAG_NEG_JACOBIAN, FLAG_NAN
   if (mode == 0) {
-    double2* out = reinterpret_cast<double2*>(elemR + 36 * e);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) out[k] = make_double2(Rcp[2 * k], Rcp[2 * k + 1]);
-    out[16] = make_double2(Rf[0], Rf[1]);
-    out[17] = make_double2(Rf[2], 0.0);
+    store_elem_residual(elemR + 36 * e, Rcp, Rf);
   } else {
     const uint32_t msk = dir_mask[e];
 #pragma unroll
@@ -105,16 +50,19 @@ static void launch_r(const Mesh& m, const State& s, const KParams& kp, const QpR
                      double* elemR, double* resid, int64_t first, int64_t count, int mode,
                      unsigned int* flags, cudaStream_t st) {
   const dim3 grid((unsigned)((count + THREADS - 1) / THREADS));
-#define VMS_RES_ARGS m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, first, count, elemR, resid, \
-                     m.dir_mask, m.n_nodes, mode, flags
+  const size_t smem = sizeof(double) * RC_N * THREADS;  // the coefficient store: above 48 KB at 64
+  auto launch = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, THREADS, smem, st>>>(m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, first, count,
+                                      elemR, resid, m.dir_mask, m.n_nodes, mode, flags);
+  };
   if (kp.transient) {
-    if (kp.has_force) residual_kernel<true, true, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
-    else residual_kernel<true, false, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
+    if (kp.has_force) launch(residual_kernel<true, true, THREADS>);
+    else launch(residual_kernel<true, false, THREADS>);
   } else {
-    if (kp.has_force) residual_kernel<false, true, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
-    else residual_kernel<false, false, THREADS><<<grid, THREADS, 0, st>>>(VMS_RES_ARGS);
+    if (kp.has_force) launch(residual_kernel<false, true, THREADS>);
+    else launch(residual_kernel<false, false, THREADS>);
   }
-#undef VMS_RES_ARGS
 }
 
 int launch_residual(const Mesh& m, const State& s, const KParams& kp, const QpRow* qp,

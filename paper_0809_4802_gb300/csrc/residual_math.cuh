@@ -20,11 +20,12 @@
 
 namespace vms {
 
-// Coefficient slots: x-gradient coefficients (3 x 7), v (3 x 8), p (8), vbar - vbar_n (3 x 8).
-constexpr int RC_X = 0, RC_V = 21, RC_P = 45, RC_DV = 53, RC_N = 77;
+// Store slots: x-gradient coefficients (3 x 7), v (3 x 8), p (8), vbar - vbar_n (3 x 8), then the
+// monomial sums of the momentum (3 x 8) and continuity (8) test functions.
+constexpr int RC_X = 0, RC_V = 21, RC_P = 45, RC_DV = 53, RC_RM = 77, RC_RP = 101, RC_N = 109;
 
 template <class Store>
-VMS_HD void residual_load(Store& C, const double X[8][3], const double U[8][4],
+VMS_HD void residual_load(const Store& C, const double X[8][3], const double U[8][4],
                           const double Uprev[8][3], bool transient) {
   double f[8], c[8];
   VMS_UNROLL
@@ -62,128 +63,223 @@ VMS_HD void residual_load(Store& C, const double X[8][3], const double U[8][4],
 
 // Quadrature loop. Rcp[32] (node-major 4a+c) and Rf[3] receive the element residual; returns
 // false if det J <= 0 at some point (the offending point then uses det J = 1).
+//
+// The tensor Gauss rule is walked line by line (xi fastest; the table's point order). Along a
+// line eta and zeta are fixed, so every trilinear field is a + xi b with a, b formed once per line:
+// J[.][0] and the polynomial part of G[.][0] (which is also the xi-slope b of v), v's a, p's a and
+// b, and (transient) those of vbar - vbar_n. The test-function sums are factored the same way: a
+// monomial xi^a eta^b zeta^c (or its derivative) is xi^a times a line constant, so each line keeps
+// seven sums per component (src, xi src, P0, P1, xi P1, P2, xi P2) and two for the continuity term,
+// and adds them into the eight monomial sums, which live in the store, once per line.
 template <bool TRANSIENT, bool FORCE, class Store, class Table>
 VMS_HD bool residual_qp_loop(const Store& C, const Table& tab, int nq, const double bet[3],
                              double nut, double tau, const double f[3], double Rcp[32],
                              double Rf[3]) {
-  double rm[3][8], rp[8];
+  const int n1 = nq == 8 ? 2 : (nq == 27 ? 3 : 4);
   VMS_UNROLL
-  for (int m = 0; m < 8; ++m) { rm[0][m] = rm[1][m] = rm[2][m] = 0.0; rp[m] = 0.0; }
+  for (int m = 0; m < 32; ++m) C.set(RC_RM + m, 0.0);
   Rf[0] = Rf[1] = Rf[2] = 0.0;
   bool ok = true;
-  for (int q = 0; q < nq; ++q) {
-    const double xi = tab.xi(q), eta = tab.eta(q), zeta = tab.zeta(q);
-    const double xe = tab.xe(q), xz = tab.xz(q), ez = tab.ez(q), xez = tab.xez(q);
-    const double bq = tab.b(q), db0 = tab.db(q, 0), db1 = tab.db(q, 1), db2 = tab.db(q, 2);
-    const double wq = tab.w(q);
-
-    double J[3][3];
-    VMS_UNROLL
-    for (int i = 0; i < 3; ++i) {
-      const double c1 = C.get(RC_X + 7 * i + 0), c2 = C.get(RC_X + 7 * i + 1);
-      const double c3 = C.get(RC_X + 7 * i + 2), c4 = C.get(RC_X + 7 * i + 3);
-      const double c5 = C.get(RC_X + 7 * i + 4), c6 = C.get(RC_X + 7 * i + 5);
-      const double c7 = C.get(RC_X + 7 * i + 6);
-      J[i][0] = c1 + c4 * eta + c5 * zeta + c7 * ez;
-      J[i][1] = c2 + c4 * xi + c6 * zeta + c7 * xz;
-      J[i][2] = c3 + c5 * xi + c6 * eta + c7 * xe;
-    }
-    double cof[3][3];
-    double det = cofactor3(J, cof);
-    if (!(det > 0.0)) { ok = false; det = 1.0; }
-    const double om = wq * det;
-
-    const double bet0 = bet[0], bet1 = bet[1], bet2 = bet[2];
-    const double betv[3] = {bet0, bet1, bet2};
-    double v[3], G[3][3];
-    VMS_UNROLL
-    for (int i = 0; i < 3; ++i) {
-      const double c0 = C.get(RC_V + 8 * i + 0), c1 = C.get(RC_V + 8 * i + 1);
-      const double c2 = C.get(RC_V + 8 * i + 2), c3 = C.get(RC_V + 8 * i + 3);
-      const double c4 = C.get(RC_V + 8 * i + 4), c5 = C.get(RC_V + 8 * i + 5);
-      const double c6 = C.get(RC_V + 8 * i + 6), c7 = C.get(RC_V + 8 * i + 7);
-      v[i] = c0 + c1 * xi + c2 * eta + c3 * zeta + c4 * xe + c5 * xz + c6 * ez + c7 * xez + bq * betv[i];
-      G[i][0] = c1 + c4 * eta + c5 * zeta + c7 * ez + betv[i] * db0;
-      G[i][1] = c2 + c4 * xi + c6 * zeta + c7 * xz + betv[i] * db1;
-      G[i][2] = c3 + c5 * xi + c6 * eta + c7 * xe + betv[i] * db2;
-    }
-    const double p = C.get(RC_P + 0) + C.get(RC_P + 1) * xi + C.get(RC_P + 2) * eta +
-                     C.get(RC_P + 3) * zeta + C.get(RC_P + 4) * xe + C.get(RC_P + 5) * xz +
-                     C.get(RC_P + 6) * ez + C.get(RC_P + 7) * xez;
-
-    double wv[3];
-    VMS_UNROLL
-    for (int al = 0; al < 3; ++al)
-      wv[al] = wq * (cof[0][al] * v[0] + cof[1][al] * v[1] + cof[2][al] * v[2]);
-    double src[3];
-    VMS_UNROLL
-    for (int i = 0; i < 3; ++i) src[i] = G[i][0] * wv[0] + G[i][1] * wv[1] + G[i][2] * wv[2];
-    if (FORCE) {
-      VMS_UNROLL
-      for (int i = 0; i < 3; ++i) src[i] -= om * f[i];
-    }
-    if (TRANSIENT) {
-      const double tom = tau * om;
+  for (int k = 0; k < n1; ++k) {
+    for (int j = 0; j < n1; ++j) {
+      const int q0 = (k * n1 + j) * n1;
+      const double eta = tab.eta(q0), zeta = tab.zeta(q0), ez = tab.ez(q0);
+      // line constants
+      double J0[3], vb[3], va[3], dva[3], dvb[3];
       VMS_UNROLL
       for (int i = 0; i < 3; ++i) {
-        const double dv = C.get(RC_DV + 8 * i + 0) + C.get(RC_DV + 8 * i + 1) * xi +
-                          C.get(RC_DV + 8 * i + 2) * eta + C.get(RC_DV + 8 * i + 3) * zeta +
-                          C.get(RC_DV + 8 * i + 4) * xe + C.get(RC_DV + 8 * i + 5) * xz +
-                          C.get(RC_DV + 8 * i + 6) * ez + C.get(RC_DV + 8 * i + 7) * xez;
-        src[i] += tom * dv;
+        J0[i] = C.get(RC_X + 7 * i + 0) + C.get(RC_X + 7 * i + 3) * eta +
+                C.get(RC_X + 7 * i + 4) * zeta + C.get(RC_X + 7 * i + 6) * ez;
+        vb[i] = C.get(RC_V + 8 * i + 1) + C.get(RC_V + 8 * i + 4) * eta +
+                C.get(RC_V + 8 * i + 5) * zeta + C.get(RC_V + 8 * i + 7) * ez;
+        va[i] = C.get(RC_V + 8 * i + 0) + C.get(RC_V + 8 * i + 2) * eta +
+                C.get(RC_V + 8 * i + 3) * zeta + C.get(RC_V + 8 * i + 6) * ez;
+        if (TRANSIENT) {
+          dva[i] = C.get(RC_DV + 8 * i + 0) + C.get(RC_DV + 8 * i + 2) * eta +
+                   C.get(RC_DV + 8 * i + 3) * zeta + C.get(RC_DV + 8 * i + 6) * ez;
+          dvb[i] = C.get(RC_DV + 8 * i + 1) + C.get(RC_DV + 8 * i + 4) * eta +
+                   C.get(RC_DV + 8 * i + 5) * zeta + C.get(RC_DV + 8 * i + 7) * ez;
+        }
       }
-    }
-    const double s = wq * nut / det;
-    const double A00 = s * (cof[0][0] * cof[0][0] + cof[1][0] * cof[1][0] + cof[2][0] * cof[2][0]);
-    const double A11 = s * (cof[0][1] * cof[0][1] + cof[1][1] * cof[1][1] + cof[2][1] * cof[2][1]);
-    const double A22 = s * (cof[0][2] * cof[0][2] + cof[1][2] * cof[1][2] + cof[2][2] * cof[2][2]);
-    const double A01 = s * (cof[0][0] * cof[0][1] + cof[1][0] * cof[1][1] + cof[2][0] * cof[2][1]);
-    const double A02 = s * (cof[0][0] * cof[0][2] + cof[1][0] * cof[1][2] + cof[2][0] * cof[2][2]);
-    const double A12 = s * (cof[0][1] * cof[0][2] + cof[1][1] * cof[1][2] + cof[2][1] * cof[2][2]);
-    const double wp = wq * p;
-    double P[3][3];
-    double trw = 0.0;
-    VMS_UNROLL
-    for (int i = 0; i < 3; ++i) {
-      P[i][0] = G[i][0] * A00 + G[i][1] * A01 + G[i][2] * A02 - wp * cof[i][0];
-      P[i][1] = G[i][0] * A01 + G[i][1] * A11 + G[i][2] * A12 - wp * cof[i][1];
-      P[i][2] = G[i][0] * A02 + G[i][1] * A12 + G[i][2] * A22 - wp * cof[i][2];
-      trw += G[i][0] * cof[i][0] + G[i][1] * cof[i][1] + G[i][2] * cof[i][2];
-    }
-    const double Tp = -wq * trw;
+      const double pa = C.get(RC_P + 0) + C.get(RC_P + 2) * eta + C.get(RC_P + 3) * zeta +
+                        C.get(RC_P + 6) * ez;
+      const double pb = C.get(RC_P + 1) + C.get(RC_P + 4) * eta + C.get(RC_P + 5) * zeta +
+                        C.get(RC_P + 7) * ez;
+      // line sums: src, xi src, P0, P1, xi P1, P2, xi P2 (per component), Tp, xi Tp
+      double s0[3] = {0.0, 0.0, 0.0}, s1[3] = {0.0, 0.0, 0.0}, b0[3] = {0.0, 0.0, 0.0};
+      double c0[3] = {0.0, 0.0, 0.0}, c1[3] = {0.0, 0.0, 0.0};
+      double d0[3] = {0.0, 0.0, 0.0}, d1[3] = {0.0, 0.0, 0.0};
+      double t0 = 0.0, t1 = 0.0;
+      for (int ii = 0; ii < n1; ++ii) {
+        const int q = q0 + ii;
+        const double xi = tab.xi(q), xz = tab.xz(q), xe = tab.xe(q);
+        const double bq = tab.b(q), db0 = tab.db(q, 0), db1 = tab.db(q, 1), db2 = tab.db(q, 2);
+        const double wq = tab.w(q);
 
-    VMS_UNROLL
-    for (int i = 0; i < 3; ++i) {
-      Rf[i] += bq * src[i] + db0 * P[i][0] + db1 * P[i][1] + db2 * P[i][2];
-      rm[i][0] += src[i];
-      rm[i][1] += xi * src[i] + P[i][0];
-      rm[i][2] += eta * src[i] + P[i][1];
-      rm[i][3] += zeta * src[i] + P[i][2];
-      rm[i][4] += xe * src[i] + eta * P[i][0] + xi * P[i][1];
-      rm[i][5] += xz * src[i] + zeta * P[i][0] + xi * P[i][2];
-      rm[i][6] += ez * src[i] + zeta * P[i][1] + eta * P[i][2];
-      rm[i][7] += xez * src[i] + ez * P[i][0] + xz * P[i][1] + xe * P[i][2];
+        double J[3][3];
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i) {
+          const double c2 = C.get(RC_X + 7 * i + 1), c3 = C.get(RC_X + 7 * i + 2);
+          const double c4 = C.get(RC_X + 7 * i + 3), c5 = C.get(RC_X + 7 * i + 4);
+          const double c6 = C.get(RC_X + 7 * i + 5), c7 = C.get(RC_X + 7 * i + 6);
+          J[i][0] = J0[i];
+          J[i][1] = c2 + c4 * xi + c6 * zeta + c7 * xz;
+          J[i][2] = c3 + c5 * xi + c6 * eta + c7 * xe;
+        }
+        double cof[3][3];
+        double det = cofactor3(J, cof);
+        if (!(det > 0.0)) { ok = false; det = 1.0; }
+        const double om = wq * det;
+
+        double v[3], G[3][3];
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i) {
+          const double c2 = C.get(RC_V + 8 * i + 2), c3 = C.get(RC_V + 8 * i + 3);
+          const double c4 = C.get(RC_V + 8 * i + 4), c5 = C.get(RC_V + 8 * i + 5);
+          const double c6 = C.get(RC_V + 8 * i + 6), c7 = C.get(RC_V + 8 * i + 7);
+          v[i] = va[i] + xi * vb[i] + bq * bet[i];
+          G[i][0] = vb[i] + bet[i] * db0;
+          G[i][1] = c2 + c4 * xi + c6 * zeta + c7 * xz + bet[i] * db1;
+          G[i][2] = c3 + c5 * xi + c6 * eta + c7 * xe + bet[i] * db2;
+        }
+        const double p = pa + xi * pb;
+
+        double wv[3];
+        VMS_UNROLL
+        for (int al = 0; al < 3; ++al)
+          wv[al] = wq * (cof[0][al] * v[0] + cof[1][al] * v[1] + cof[2][al] * v[2]);
+        double src[3];
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i) src[i] = G[i][0] * wv[0] + G[i][1] * wv[1] + G[i][2] * wv[2];
+        if (FORCE) {
+          VMS_UNROLL
+          for (int i = 0; i < 3; ++i) src[i] -= om * f[i];
+        }
+        if (TRANSIENT) {
+          const double tom = tau * om;
+          VMS_UNROLL
+          for (int i = 0; i < 3; ++i) src[i] += tom * (dva[i] + xi * dvb[i]);
+        }
+        const double s = wq * nut / det;
+        const double A00 = s * (cof[0][0] * cof[0][0] + cof[1][0] * cof[1][0] + cof[2][0] * cof[2][0]);
+        const double A11 = s * (cof[0][1] * cof[0][1] + cof[1][1] * cof[1][1] + cof[2][1] * cof[2][1]);
+        const double A22 = s * (cof[0][2] * cof[0][2] + cof[1][2] * cof[1][2] + cof[2][2] * cof[2][2]);
+        const double A01 = s * (cof[0][0] * cof[0][1] + cof[1][0] * cof[1][1] + cof[2][0] * cof[2][1]);
+        const double A02 = s * (cof[0][0] * cof[0][2] + cof[1][0] * cof[1][2] + cof[2][0] * cof[2][2]);
+        const double A12 = s * (cof[0][1] * cof[0][2] + cof[1][1] * cof[1][2] + cof[2][1] * cof[2][2]);
+        const double wp = wq * p;
+        double trw = 0.0;
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i) {
+          const double P0 = G[i][0] * A00 + G[i][1] * A01 + G[i][2] * A02 - wp * cof[i][0];
+          const double P1 = G[i][0] * A01 + G[i][1] * A11 + G[i][2] * A12 - wp * cof[i][1];
+          const double P2 = G[i][0] * A02 + G[i][1] * A12 + G[i][2] * A22 - wp * cof[i][2];
+          trw += G[i][0] * cof[i][0] + G[i][1] * cof[i][1] + G[i][2] * cof[i][2];
+          Rf[i] += bq * src[i] + db0 * P0 + db1 * P1 + db2 * P2;
+          s0[i] += src[i];
+          s1[i] += xi * src[i];
+          b0[i] += P0;
+          c0[i] += P1;
+          c1[i] += xi * P1;
+          d0[i] += P2;
+          d1[i] += xi * P2;
+        }
+        const double Tp = -wq * trw;
+        t0 += Tp;
+        t1 += xi * Tp;
+      }
+      // the line's contributions to the monomial sums: xi^a eta^b zeta^c src_i and the
+      // derivatives d/dxi (P0), d/deta (P1), d/dzeta (P2) of the same monomials
+      VMS_UNROLL
+      for (int i = 0; i < 3; ++i) {
+        const double sb = s1[i] + b0[i];
+        const int r = RC_RM + 8 * i;
+        C.set(r + 0, C.get(r + 0) + s0[i]);
+        C.set(r + 1, C.get(r + 1) + sb);
+        C.set(r + 2, C.get(r + 2) + (eta * s0[i] + c0[i]));
+        C.set(r + 3, C.get(r + 3) + (zeta * s0[i] + d0[i]));
+        C.set(r + 4, C.get(r + 4) + (eta * sb + c1[i]));
+        C.set(r + 5, C.get(r + 5) + (zeta * sb + d1[i]));
+        C.set(r + 6, C.get(r + 6) + (ez * s0[i] + zeta * c0[i] + eta * d0[i]));
+        C.set(r + 7, C.get(r + 7) + (ez * sb + zeta * c1[i] + eta * d1[i]));
+      }
+      C.set(RC_RP + 0, C.get(RC_RP + 0) + t0);
+      C.set(RC_RP + 1, C.get(RC_RP + 1) + t1);
+      C.set(RC_RP + 2, C.get(RC_RP + 2) + eta * t0);
+      C.set(RC_RP + 3, C.get(RC_RP + 3) + zeta * t0);
+      C.set(RC_RP + 4, C.get(RC_RP + 4) + eta * t1);
+      C.set(RC_RP + 5, C.get(RC_RP + 5) + zeta * t1);
+      C.set(RC_RP + 6, C.get(RC_RP + 6) + ez * t0);
+      C.set(RC_RP + 7, C.get(RC_RP + 7) + ez * t1);
     }
-    rp[0] += Tp;
-    rp[1] += xi * Tp;
-    rp[2] += eta * Tp;
-    rp[3] += zeta * Tp;
-    rp[4] += xe * Tp;
-    rp[5] += xz * Tp;
-    rp[6] += ez * Tp;
-    rp[7] += xez * Tp;
   }
-  double r[8];
+  double r[8], mm[8];
   VMS_UNROLL
   for (int i = 0; i < 3; ++i) {
-    nodal8(rm[i], r);
+    VMS_UNROLL
+    for (int m = 0; m < 8; ++m) mm[m] = C.get(RC_RM + 8 * i + m);
+    nodal8(mm, r);
     VMS_UNROLL
     for (int a = 0; a < 8; ++a) Rcp[4 * a + i] = 0.125 * r[a];
   }
-  nodal8(rp, r);
+  VMS_UNROLL
+  for (int m = 0; m < 8; ++m) mm[m] = C.get(RC_RP + m);
+  nodal8(mm, r);
   VMS_UNROLL
   for (int a = 0; a < 8; ++a) Rcp[4 * a + 3] = 0.125 * r[a];
   return ok;
 }
+
+#if defined(__CUDACC__)
+// One element's residual on one thread: gather the 8 nodes (and the previous step's velocities),
+// map them to monomial coefficients in `C`, run the quadrature loop. Returns the element's error
+// bits: 1 if det J <= 0 at some point, 4 if a residual entry is not finite (the values of
+// FLAG_NEG_JACOBIAN and FLAG_NAN). P provides nut, visc_factor, nu_e, nq, tau and f.
+template <bool TRANSIENT, bool FORCE, class Store, class Table, class P>
+__device__ __forceinline__ unsigned residual_element(
+    int64_t e, const Store& C, const Table& tab, const P& kp,
+    const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u,
+    const double4_32a* __restrict__ uprev, const int32_t* __restrict__ conn,
+    const double* __restrict__ beta, int nd[8], double Rcp[32], double Rf[3]) {
+  {
+    const int4* cp = reinterpret_cast<const int4*>(conn + 8 * e);
+    const int4 c0 = cp[0], c1 = cp[1];
+    nd[0] = c0.x; nd[1] = c0.y; nd[2] = c0.z; nd[3] = c0.w;
+    nd[4] = c1.x; nd[5] = c1.y; nd[6] = c1.z; nd[7] = c1.w;
+  }
+  {
+    double X[8][3], U[8][4], Up[8][3];
+    VMS_UNROLL
+    for (int a = 0; a < 8; ++a) {
+      const double4_32a x = xyz[nd[a]];
+      const double4_32a w = u[nd[a]];
+      X[a][0] = x.x; X[a][1] = x.y; X[a][2] = x.z;
+      U[a][0] = w.x; U[a][1] = w.y; U[a][2] = w.z; U[a][3] = w.w;
+      if (TRANSIENT) {
+        const double4_32a o = uprev[nd[a]];
+        Up[a][0] = o.x; Up[a][1] = o.y; Up[a][2] = o.z;
+      }
+    }
+    residual_load(C, X, U, Up, TRANSIENT);
+  }
+  const double bet[3] = {beta[3 * e + 0], beta[3 * e + 1], beta[3 * e + 2]};
+  const double nut = kp.nu_e ? kp.visc_factor * __ldg(kp.nu_e + e) : kp.nut;
+  const bool ok = residual_qp_loop<TRANSIENT, FORCE>(C, tab, kp.nq, bet, nut, kp.tau, kp.f, Rcp, Rf);
+  bool finite = isfinite(Rf[0]) && isfinite(Rf[1]) && isfinite(Rf[2]);
+  VMS_UNROLL
+  for (int k = 0; k < 32; ++k) finite = finite && isfinite(Rcp[k]);
+  return (ok ? 0u : 1u) | (finite ? 0u : 4u);
+}
+
+// Store the element residual in its 36-double record: R_cp (32, node-major), R_f (3), pad.
+__device__ __forceinline__ void store_elem_residual(double* __restrict__ rec, const double Rcp[32],
+                                                    const double Rf[3]) {
+  double2* out = reinterpret_cast<double2*>(rec);
+  VMS_UNROLL
+  for (int k = 0; k < 16; ++k) out[k] = make_double2(Rcp[2 * k], Rcp[2 * k + 1]);
+  out[16] = make_double2(Rf[0], Rf[1]);
+  out[17] = make_double2(Rf[2], 0.0);
+}
+#endif
 
 }  // namespace vms

@@ -5,6 +5,8 @@
 // W = K_cf K_ff^-1 and K_ff^-1, and the FP64 finish kernel forms r_e = R_cp - W R_f and
 // y = K_ff^-1 R_f once both the residual and the tangent kernels are done. The two element
 // kernels are therefore independent and run concurrently (FP64 pipe and FP32 pipe).
+#include "residual_math.cuh"
+#include "residual_table.cuh"
 #include "tangent_math.cuh"
 #include "vms_internal.h"
 
@@ -15,9 +17,11 @@ namespace vms {
 // autotuner (vms_autotune) may choose another count from tan_warp_choices.
 template <typename T> constexpr int tan_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
-template <typename T>
+// Shared memory of one warp: the fixed part and the records of at most QCH quadrature points
+// (points are processed in chunks of QCH).
+template <typename T, int QCH = 32>
 __host__ __device__ inline size_t tan_warp_bytes(int nq) {
-  int qc = nq < 32 ? nq : 32;
+  int qc = nq < QCH ? nq : QCH;
   size_t b = offsetof(WarpArea<T>, qp) + (size_t)qc * sizeof(QpRec<T>);
   return (b + 15) & ~size_t(15);
 }
@@ -120,6 +124,148 @@ template <typename T> struct NodeVec;
 template <> struct NodeVec<double> { using type = double4_32a; };
 template <> struct NodeVec<float> { using type = float4; };
 
+// One element (a1-a8) for one warp: gather, quadrature-point coefficients, tangent blocks,
+// condensation, recovery data and the scatter (or the element outputs). `it` is the element's
+// position in the launch (element outputs), `e` its index in the mesh.
+template <typename T, bool ELEM_OUT, bool ATOMIC, int QCH = 32>
+__device__ __forceinline__ void tangent_element(
+    int lane, int64_t it, int64_t e, WarpArea<T>& W, const RefTab<T>& tab,
+    const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn,
+    const T* __restrict__ beta, int nq, T nut, T tau, const double* __restrict__ nu_e,
+    double visc_factor, const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
+    const double* __restrict__ beta64, const double* __restrict__ tab64,
+    const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
+    const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
+    double* __restrict__ recW, double* __restrict__ recKinv, double* __restrict__ oS,
+    double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
+    double* __restrict__ oKff, unsigned int* __restrict__ flags) {
+  // gather (a1): 8 nodes and the bubble coefficients
+  if (lane < 8) {
+    const int nd = conn[8 * e + lane];
+    W.nd[lane] = nd;
+    const double4_32a x = xyz64[nd];
+    const auto w = u[nd];
+    if constexpr (sizeof(T) == 4) {
+      // FP32 geometry from the coordinates relative to the element's first node, taken in
+      // FP64: J is unchanged (the basis gradients sum to zero), while FP32 copies of absolute
+      // coordinates far from the origin would resolve the element's extent only to
+      // |x| * 6e-8 / h (2e-5 at x = 30 with h = 1/13)
+      W.X[lane][0] = (float)(x.x - __shfl_sync(0xffu, x.x, 0));
+      W.X[lane][1] = (float)(x.y - __shfl_sync(0xffu, x.y, 0));
+      W.X[lane][2] = (float)(x.z - __shfl_sync(0xffu, x.z, 0));
+    } else {
+      W.X[lane][0] = x.x; W.X[lane][1] = x.y; W.X[lane][2] = x.z;
+    }
+    W.V[lane][0] = w.x; W.V[lane][1] = w.y; W.V[lane][2] = w.z;
+  } else if (lane < 11) {
+    W.beta[lane - 8] = beta[3 * e + lane - 8];
+  } else if (lane == 11) {
+    W.flag = 0u;
+  }
+  __syncwarp();
+  const T nut_e = nu_e ? T(visc_factor * __ldg(nu_e + e)) : nut;
+  LaneAcc<T> A;
+  tan_zero(A);
+  for (int q0 = 0; q0 < nq; q0 += QCH) {
+    if (QCH == 32 || lane < QCH) tan_phase1(lane, q0, nq, W, tab, nut_e, tau, A);
+    __syncwarp();
+    tan_phase2(lane, nq - q0 < QCH ? nq - q0 : QCH, W, nut_e, A);
+    __syncwarp();
+  }
+  const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
+  if (ELEM_OUT) {
+    if (oKcc) {
+      double* K = oKcc + 1024 * it;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          K[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].x;
+          K[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].y;
+        }
+    }
+    if (oKcf)
+      for (int k = 0; k < 3; ++k) oKcf[96 * it + 3 * lane + k] = (double)A.kcf[k];
+    if (oKfc)
+      for (int k = 0; k < 3; ++k) oKfc[96 * it + 32 * k + lane] = (double)A.kfc[k];
+  }
+  // condensation (a6)
+  tan_phase3a(lane, W, A);
+  __syncwarp();
+  tan_phase3b(lane, W);
+  __syncwarp();
+  tan_phase3c(lane, W);
+  __syncwarp();
+  tan_phase3d(lane, W);
+  __syncwarp();
+  bool accurate = false;
+  if constexpr (sizeof(T) == 4) {
+    int ill = 0;
+    if (lane == 0) ill = kff_cond_inf(W) > T(KFF_FP64_COND);
+    accurate = __shfl_sync(0xffffffffu, ill, 0) != 0;  // warp-uniform
+    if (accurate) {
+      double K[9];
+      const double nut64 = nu_e ? visc_factor * __ldg(nu_e + e) : (double)nut;
+      kff_fp64(lane, nq, W.nd, xyz64, u64, beta64, e, tab64, nut64, K);
+      __syncwarp();
+      if (lane < 9) W.Kff[lane] = K[lane];
+      __syncwarp();
+      tan_phase3c(lane, W);
+      __syncwarp();
+      tan_phase3d(lane, W);
+      __syncwarp();
+    }
+  }
+  double Wl[3];
+  tan_phase3f(lane, W, A, Wl, accurate);
+  __syncwarp();
+  tan_phase3e(lane, W, A, accurate);
+  // per-element data for the finish kernel and the fine-scale recovery
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    recX[96 * e + 32 * m + lane] = W.Xs[m][lane];
+    recW[96 * e + 3 * lane + m] = Wl[m];
+  }
+  if (lane < 9) recKinv[9 * e + lane] = W.Kinv[lane];
+  if (ELEM_OUT) {
+    if (oS) {
+      double* S = oS + 1024 * it;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          S[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].x;
+          S[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].y;
+        }
+    }
+    if (oKff && lane < 9) oKff[9 * it + lane] = W.Kff[lane];
+  } else {
+    // scatter-add (a7), skipping constrained rows and columns (a8 is completed by the
+    // diagonal kernel)
+    const uint32_t msk = dir_mask[e];
+    const int32_t* bk = blk + 64 * e;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int a = p ? a1 : a0;
+      const int32_t off = bk[8 * a + b];
+      const int32_t rl = rowlen[W.nd[a]];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (msk >> (4 * a + i) & 1u) continue;
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          v[k] = (msk >> (4 * b + k) & 1u) ? T(0) : (p ? A.K[4 * i + k].y : A.K[4 * i + k].x);
+        scatter_row(values + off + (int64_t)i * rl, v, ATOMIC);
+      }
+    }
+  }
+  __syncwarp();
+  // flag bits 1 (det J <= 0) and 2 (singular K_ff) coincide with FLAG_NEG_JACOBIAN/SINGULAR_KFF
+  if (lane == 0 && W.flag) atomicOr(flags, W.flag);
+  __syncwarp();
+}
+
 template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
@@ -143,132 +289,111 @@ __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
   const int64_t total = (int64_t)gridDim.x * WARPS;
   for (int64_t it = (int64_t)blockIdx.x * WARPS + warp; it < count; it += total) {
     const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
-    // gather (a1): 8 nodes and the bubble coefficients
-    if (lane < 8) {
-      const int nd = conn[8 * e + lane];
-      W.nd[lane] = nd;
-      const double4_32a x = xyz64[nd];
-      const auto w = u[nd];
-      if constexpr (sizeof(T) == 4) {
-        // FP32 geometry from the coordinates relative to the element's first node, taken in
-        // FP64: J is unchanged (the basis gradients sum to zero), while FP32 copies of absolute
-        // coordinates far from the origin would resolve the element's extent only to
-        // |x| * 6e-8 / h (2e-5 at x = 30 with h = 1/13)
-        W.X[lane][0] = (float)(x.x - __shfl_sync(0xffu, x.x, 0));
-        W.X[lane][1] = (float)(x.y - __shfl_sync(0xffu, x.y, 0));
-        W.X[lane][2] = (float)(x.z - __shfl_sync(0xffu, x.z, 0));
-      } else {
-        W.X[lane][0] = x.x; W.X[lane][1] = x.y; W.X[lane][2] = x.z;
-      }
-      W.V[lane][0] = w.x; W.V[lane][1] = w.y; W.V[lane][2] = w.z;
-    } else if (lane < 11) {
-      W.beta[lane - 8] = beta[3 * e + lane - 8];
-    } else if (lane == 11) {
-      W.flag = 0u;
-    }
-    __syncwarp();
-    const T nut_e = nu_e ? T(visc_factor * __ldg(nu_e + e)) : nut;
-    LaneAcc<T> A;
-    tan_zero(A);
-    for (int q0 = 0; q0 < nq; q0 += 32) {
-      tan_phase1(lane, q0, nq, W, tab, nut_e, tau, A);
-      __syncwarp();
-      tan_phase2(lane, nq - q0 < 32 ? nq - q0 : 32, W, nut_e, A);
-      __syncwarp();
-    }
-    const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
-    if (ELEM_OUT) {
-      if (oKcc) {
-        double* K = oKcc + 1024 * it;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            K[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].x;
-            K[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].y;
-          }
-      }
-      if (oKcf)
-        for (int k = 0; k < 3; ++k) oKcf[96 * it + 3 * lane + k] = (double)A.kcf[k];
-      if (oKfc)
-        for (int k = 0; k < 3; ++k) oKfc[96 * it + 32 * k + lane] = (double)A.kfc[k];
-    }
-    // condensation (a6)
-    tan_phase3a(lane, W, A);
-    __syncwarp();
-    tan_phase3b(lane, W);
-    __syncwarp();
-    tan_phase3c(lane, W);
-    __syncwarp();
-    tan_phase3d(lane, W);
-    __syncwarp();
-    bool accurate = false;
-    if constexpr (sizeof(T) == 4) {
-      int ill = 0;
-      if (lane == 0) ill = kff_cond_inf(W) > T(KFF_FP64_COND);
-      accurate = __shfl_sync(0xffffffffu, ill, 0) != 0;  // warp-uniform
-      if (accurate) {
-        double K[9];
-        const double nut64 = nu_e ? visc_factor * __ldg(nu_e + e) : (double)nut;
-        kff_fp64(lane, nq, W.nd, xyz64, u64, beta64, e, tab64, nut64, K);
-        __syncwarp();
-        if (lane < 9) W.Kff[lane] = K[lane];
-        __syncwarp();
-        tan_phase3c(lane, W);
-        __syncwarp();
-        tan_phase3d(lane, W);
-        __syncwarp();
-      }
-    }
-    double Wl[3];
-    tan_phase3f(lane, W, A, Wl, accurate);
-    __syncwarp();
-    tan_phase3e(lane, W, A, accurate);
-    // per-element data for the finish kernel and the fine-scale recovery
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      recX[96 * e + 32 * m + lane] = W.Xs[m][lane];
-      recW[96 * e + 3 * lane + m] = Wl[m];
-    }
-    if (lane < 9) recKinv[9 * e + lane] = W.Kinv[lane];
-    if (ELEM_OUT) {
-      if (oS) {
-        double* S = oS + 1024 * it;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            S[(4 * a0 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].x;
-            S[(4 * a1 + i) * 32 + 4 * b + k] = (double)A.K[4 * i + k].y;
-          }
-      }
-      if (oKff && lane < 9) oKff[9 * it + lane] = W.Kff[lane];
-    } else {
-      // scatter-add (a7), skipping constrained rows and columns (a8 is completed by the
-      // diagonal kernel)
-      const uint32_t msk = dir_mask[e];
-      const int32_t* bk = blk + 64 * e;
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const int a = p ? a1 : a0;
-        const int32_t off = bk[8 * a + b];
-        const int32_t rl = rowlen[W.nd[a]];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (msk >> (4 * a + i) & 1u) continue;
-          T v[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            v[k] = (msk >> (4 * b + k) & 1u) ? T(0) : (p ? A.K[4 * i + k].y : A.K[4 * i + k].x);
-          scatter_row(values + off + (int64_t)i * rl, v, ATOMIC);
-        }
-      }
-    }
-    __syncwarp();
-    // flag bits 1 (det J <= 0) and 2 (singular K_ff) coincide with FLAG_NEG_JACOBIAN/SINGULAR_KFF
-    if (lane == 0 && W.flag) atomicOr(flags, W.flag);
-    __syncwarp();
+    tangent_element<T, ELEM_OUT, ATOMIC>(lane, it, e, W, tab, u, conn, beta, nq, nut, tau, nu_e,
+                                         visc_factor, xyz64, u64, beta64, tab64, blk, rowlen,
+                                         dir_mask, values, recX, recW, recKinv, oS, oKcc, oKcf,
+                                         oKfc, oKff, flags);
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mixed precision, atomic scatter: the FP64 residual and the FP32 tangent in one persistent launch
+// ---------------------------------------------------------------------------------------------
+// The residual is bound by the FP64 pipe (a warp instruction occupies an SM partition's FP64 unit
+// for many cycles, so one warp per partition keeps it busy) and the FP32 tangent by the latency of
+// its warps. Launched as two kernels, the residual's blocks (226 registers per thread) take every
+// SM and the tangent runs mostly after them. Here one CTA per SM holds both: warps 0-3 (one per
+// partition) evaluate residuals, one element per thread, 32 elements per claim; warps 4-7 form
+// tangents, one element per warp, FUSED_TCLAIM elements per claim. A residual warp whose queue is
+// empty joins the tangent queue. The queues are two counters (zeroed before the launch); no warp
+// ever waits for another.
+// The tangent warps take quadrature points 16 at a time (two passes of 16 lanes for the 27-point
+// rule), which halves their point records and lets the residual's store and eight warp areas fit
+// in one SM's shared memory.
+constexpr int FUSED_WARPS = 8, FUSED_RES_WARPS = 4, FUSED_TCLAIM = 4, FUSED_QCH = 16;
+constexpr int FUSED_RES_THREADS = FUSED_RES_WARPS * 32;
+
+__host__ __device__ inline size_t fused_res_bytes() {
+  return sizeof(double) * RC_N * FUSED_RES_THREADS;
+}
+size_t fused_smem_bytes(int nq) {
+  return fused_res_bytes() + tan_table_bytes<float>(nq) + FUSED_WARPS * tan_warp_bytes<float, FUSED_QCH>(nq);
+}
+
+template <bool TRANSIENT, bool FORCE>
+__global__ void __launch_bounds__(FUSED_WARPS * 32, 1) fused_assembly_kernel(
+    const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u64,
+    const double4_32a* __restrict__ uprev, const int32_t* __restrict__ conn,
+    const double* __restrict__ beta64, KParams kp, const QpRow* __restrict__ qp,
+    double* __restrict__ elemR, const float4* __restrict__ u32, const float* __restrict__ beta32,
+    const float* __restrict__ gtab, float nut, float tau, const int32_t* __restrict__ blk,
+    const int32_t* __restrict__ rowlen, const uint32_t* __restrict__ dir_mask,
+    float* __restrict__ values, float* __restrict__ recX, double* __restrict__ recW,
+    double* __restrict__ recKinv, int64_t n_elems, unsigned long long* __restrict__ queues,
+    unsigned int* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nq = kp.nq;
+  float* st = reinterpret_cast<float*>(smem + fused_res_bytes());
+  for (int i = threadIdx.x; i < 37 * nq; i += blockDim.x) st[i] = gtab[i];
+  __syncthreads();
+  const RefTab<float> tab{st, st + 8 * nq, st + 32 * nq, st + 33 * nq, st + 36 * nq};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < FUSED_RES_WARPS) {
+    SmemStore<FUSED_RES_THREADS> C{reinterpret_cast<double (*)[FUSED_RES_THREADS]>(smem),
+                                   (int)threadIdx.x};
+    for (;;) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(queues, 32ull);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= (unsigned long long)n_elems) break;
+      const int64_t e = (int64_t)base + lane;
+      if (e < n_elems) {
+        int nd[8];
+        double Rcp[32], Rf[3];
+        const unsigned bad = residual_element<TRANSIENT, FORCE>(e, C, GlobalTable{qp}, kp, xyz, u64,
+                                                                uprev, conn, beta64, nd, Rcp, Rf);
+        if (bad) atomicOr(flags, bad);
+        store_elem_residual(elemR + 36 * e, Rcp, Rf);
+      }
+    }
+  }
+  WarpArea<float>& W = *reinterpret_cast<WarpArea<float>*>(
+      smem + fused_res_bytes() + tan_table_bytes<float>(nq) + warp * tan_warp_bytes<float, FUSED_QCH>(nq));
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(queues + 1, (unsigned long long)FUSED_TCLAIM);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= (unsigned long long)n_elems) break;
+    const int64_t end = (int64_t)base + FUSED_TCLAIM < n_elems ? (int64_t)base + FUSED_TCLAIM : n_elems;
+    for (int64_t e = (int64_t)base; e < end; ++e)
+      tangent_element<float, false, true, FUSED_QCH>(lane, e, e, W, tab, u32, conn, beta32, nq, nut, tau,
+                                          kp.nu_e, kp.visc_factor, xyz, u64, beta64, kp.tab64, blk,
+                                          rowlen, dir_mask, values, recX, recW, recKinv, nullptr,
+                                          nullptr, nullptr, nullptr, nullptr, flags);
+  }
+}
+
+int launch_fused_assembly(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
+                          const QpRow* qp, const float* tab32, double* elemR, const TangentOut& o,
+                          unsigned long long* queues, unsigned int* flags, cudaStream_t st) {
+  if (m.n_elems <= 0) return 0;
+  const size_t smem = fused_smem_bytes(kp.nq);
+  auto launch = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(unsigned)sm_count(), FUSED_WARPS * 32, smem, st>>>(
+        m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, elemR, c32.u, c32.beta, tab32,
+        (float)kp.nut, (float)kp.tau, m.blk, m.rowlen, m.dir_mask, reinterpret_cast<float*>(o.values),
+        reinterpret_cast<float*>(o.recX), reinterpret_cast<double*>(o.recW), o.recKinv, m.n_elems,
+        queues, flags);
+  };
+  if (kp.transient) {
+    if (kp.has_force) launch(fused_assembly_kernel<true, true>);
+    else launch(fused_assembly_kernel<true, false>);
+  } else {
+    if (kp.has_force) launch(fused_assembly_kernel<false, true>);
+    else launch(fused_assembly_kernel<false, false>);
+  }
+  return 1;
 }
 
 // r_e = R_cp - W R_f (FP64) scattered into the right-hand side, and y = K_ff^-1 R_f stored for

@@ -109,6 +109,7 @@ struct Work {
   double* resid = nullptr;    // 4 n_nodes + 3 n_elems
   double* partial = nullptr;  // reduction partials
   unsigned int* flags = nullptr;
+  unsigned long long* queues = nullptr;  // 2 work counters of the fused assembly kernel
   Fp32Copy f32;               // mixed precision only
   cudaStream_t aux = nullptr; // second stream for the tangent kernel
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -175,6 +176,11 @@ int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32
                    const KParams& kp, const void* tab, const TangentOut& out, int64_t first,
                    int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
                    unsigned int* flags, cudaStream_t st);
+// Mixed precision with the atomic scatter: the residual (into elemR) and the FP32 tangent (into
+// out) in one persistent launch; `queues` holds two zeroed counters.
+int launch_fused_assembly(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
+                          const QpRow* qp, const float* tab32, double* elemR, const TangentOut& o,
+                          unsigned long long* queues, unsigned int* flags, cudaStream_t st);
 // r_e = R_cp - K_cf K_ff^-1 R_f (FP64) into rhs (or into out.r), and K_ff^-1 R_f into recY.
 int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOut& out,
                   int64_t first, int64_t count, const int32_t* elem_list, bool atomic,

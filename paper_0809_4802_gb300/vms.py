@@ -54,7 +54,9 @@ EXPORTS = [
     "vms_set_wait_limit", "vms_csr_download", "vms_fma_throughput",
 ]
 MLP_IN, MLP_WIDTH, MLP_OUT, MLP_PARAMS = 12, 128, 4, 18692
-K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond"]
+K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond", "fused"]
+SCHEDULE_FUSED = 0
+SCHEDULE_TWO_STREAMS = 1
 
 
 class VmsParams(ctypes.Structure):
@@ -65,11 +67,11 @@ class VmsParams(ctypes.Structure):
 
 class VmsTuning(ctypes.Structure):
     _fields_ = [("tangent_warps", c_int32), ("residual_threads", c_int32),
-                ("scatter_mode", c_int32), ("reserved", c_int32), ("ms", c_double)]
+                ("scatter_mode", c_int32), ("schedule", c_int32), ("ms", c_double)]
 
     def as_dict(self):
         return {"tangent_warps": self.tangent_warps, "residual_threads": self.residual_threads,
-                "scatter_mode": self.scatter_mode, "ms": self.ms}
+                "scatter_mode": self.scatter_mode, "schedule": self.schedule, "ms": self.ms}
 
 
 class CsrView(ctypes.Structure):
@@ -339,8 +341,8 @@ class Context:
                                                 int(update), byref(it), byref(rel)))
         return it.value, rel.value
 
-    def set_tuning(self, tangent_warps=0, residual_threads=0, scatter_mode=-1):
-        t = VmsTuning(tangent_warps, residual_threads, scatter_mode, 0, 0.0)
+    def set_tuning(self, tangent_warps=0, residual_threads=0, scatter_mode=-1, schedule=SCHEDULE_FUSED):
+        t = VmsTuning(tangent_warps, residual_threads, scatter_mode, schedule, 0.0)
         self._check(self.lib.vms_set_tuning(self.h, byref(t)))
 
     def get_tuning(self):

@@ -179,25 +179,30 @@ def test_autotune_picks_an_offered_tuning_and_keeps_results(vms, small_batch):
     ctx.assemble()
     ref = [a.copy() for a in ctx.csr_host()[2:]]
     best = ctx.autotune(repeats=2)
-    assert best["tangent_warps"] in (2, 4, 8)
-    assert best["residual_threads"] in (32, 64)
-    assert best["scatter_mode"] in (0, 1)
+    if best["schedule"] == vms.SCHEDULE_FUSED:   # one persistent launch, atomic scatter
+        assert (best["tangent_warps"], best["residual_threads"], best["scatter_mode"]) == (0, 0, 0)
+    else:
+        assert best["schedule"] == vms.SCHEDULE_TWO_STREAMS
+        assert best["tangent_warps"] in (2, 4, 8)
+        assert best["residual_threads"] in (32, 64)
+        assert best["scatter_mode"] in (0, 1)
     assert best["ms"] > 0.0
-    assert ctx.get_tuning()["tangent_warps"] == best["tangent_warps"]
+    assert ctx.get_tuning() == {**best, "ms": ctx.get_tuning()["ms"]}
     ctx.assemble()
     vals, rhs = ctx.csr_host()[2:]
     assert relerr(vals, ref[0]) <= 1e-6 and relerr(rhs, ref[1]) <= 1e-6
     # every offered tuning with the colour scatter reproduces the default bits
     for tw in (2, 4, 8):
         for rt in (32, 64):
-            ctx.set_tuning(tw, rt, 1)
+            ctx.set_tuning(tw, rt, 1, vms.SCHEDULE_TWO_STREAMS)
             ctx.assemble()
             vals, rhs = ctx.csr_host()[2:]
             np.testing.assert_array_equal(vals, ref[0])
             np.testing.assert_array_equal(rhs, ref[1])
-    with pytest.raises(vms.VmsError) as ei:
-        ctx.set_tuning(3, 64, 1)
-    assert ei.value.code == vms.ERR_INVALID_ARG
+    for bad in ((3, 64, 1, 0), (4, 64, 1, 2)):
+        with pytest.raises(vms.VmsError) as ei:
+            ctx.set_tuning(*bad)
+        assert ei.value.code == vms.ERR_INVALID_ARG
     ctx.close()
 
 

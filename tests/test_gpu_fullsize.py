@@ -147,9 +147,11 @@ def test_channel_past_cube_full_size_sampled(vms):
     ctx.close()
 
 
-def test_batch64_full_size_sampled(vms):
+@pytest.mark.parametrize("schedule", [0, 1], ids=["fused", "two_streams"])
+def test_batch64_full_size_sampled(vms, schedule):
     """The 64-cavity batch (edges 8-48, Re 100-1000 per instance) in the benchmark's launch
-    configuration: CUDA-graph replay with 4 tangent warps per block and 64 residual threads."""
+    configurations: CUDA-graph replay of the fused kernel, and of the two kernels with 4 tangent
+    warps per block and 64 residual threads."""
     b = inputs.batched_workload(64, seed=1004)
     w = b.work
     ctx = vms.Context(0, MIXED)
@@ -158,7 +160,7 @@ def test_batch64_full_size_sampled(vms):
     ctx.set_element_viscosity(b.nu_e)
     ctx.set_instances(b.node_offsets, b.elem_offsets)
     ctx.state_upload(w.u, w.beta)
-    ctx.set_tuning(tangent_warps=4, residual_threads=64)
+    ctx.set_tuning(tangent_warps=4, residual_threads=64, schedule=schedule)
     ctx.set_graph(True)
     ctx.assemble()
     ctx.assemble()  # the second call replays the captured graph
