@@ -73,6 +73,8 @@ WORKLOADS = {
     "channel_warmstart_mixed": dict(kind="warmstart", flow="channel", prec=1),
 }
 DEFAULT_WORKLOAD = "channel_re1000_mixed"
+# the library's precision modes (VMS_PREC_*)
+PREC_NAMES = {0: "fp64", 1: "mixed", 2: "tc_bf16", 3: "tc_tf32"}
 WS_SIZE = {"nx": 150, "nyz": 28, "n": 16}   # set from --ws-nx / --ws-nyz / --ws-n
 
 
@@ -344,7 +346,7 @@ def newton_timing(vms, wl, prec, device, stream, rtol=1e-8, repeats=2, maxit=30)
     except vms.VmsError as e:
         ctx.close()
         return {"metric": NEWTON_METRIC.replace("1e-8", f"{rtol:g}"), "value": None, "unit": "s",
-                "precision": "mixed" if prec == 1 else "fp64", "failed": str(e)}
+                "precision": PREC_NAMES[prec], "failed": str(e)}
     times, h2h, its, hist, stats = [], [], 0, None, (0, 0)
     u_out = np.empty((wl.mesh.n_nodes, 4))
     b_out = np.empty((wl.mesh.n_elems, 3))
@@ -364,7 +366,7 @@ def newton_timing(vms, wl, prec, device, stream, rtol=1e-8, repeats=2, maxit=30)
         stats = ctx.solver_stats(reset=True)
     ctx.close()
     return {"metric": NEWTON_METRIC.replace("1e-8", f"{rtol:g}"), "value": float(np.median(times)),
-            "unit": "s", "higher_is_better": False, "precision": "mixed" if prec == 1 else "fp64",
+            "unit": "s", "higher_is_better": False, "precision": PREC_NAMES[prec],
             "host_to_host_s": float(np.median(h2h)),
             "newton_iterations": int(its), "linear_solves": int(stats[0]),
             "krylov_iterations": int(stats[1]), "final_rel": float(hist[-1] / hist[0]),
@@ -412,7 +414,7 @@ def warmstart_study(vms, ctx, wl, args, dev):
 
 def workload_config(name, wl, prec, batch=None):
     c = {"workload": name, "elements": wl.mesh.n_elems, "nodes": wl.mesh.n_nodes,
-         "reynolds": round(1.0 / wl.nu, 3), "dt": wl.dt, "precision": "mixed" if prec == 1 else "fp64",
+         "reynolds": round(1.0 / wl.nu, 3), "dt": wl.dt, "precision": PREC_NAMES[prec],
          "quad_points": 27, "l2": "flushed between timed steps (256 MB write)"}
     if batch is not None:
         edges = [int(round(w.mesh.n_elems ** (1 / 3))) for w in batch.members]
@@ -488,7 +490,7 @@ def roofline_entries(kern, E, prec, tet, peaks, workload):
                             "ms": ms, "achieved": fpe * E / (ms * 1e-3) / 1e12,
                             "peak": peaks["fp64_tflops"] if pipe == "fp64" else peaks["fp32_tflops"],
                             "traffic": NCU_TRAFFIC_BYTES.get(("fused", workload))})
-        for name, pipe in (("residual", "fp64"), ("tangent", "fp32" if prec == 1 else "fp64")):
+        for name, pipe in (("residual", "fp64"), ("tangent", "fp32" if prec != 0 else "fp64")):
             if name not in kern:
                 continue
             ms = kern[name]
@@ -523,7 +525,7 @@ def ours(args):
 
     wl, prec, batch = make_workload(args.workload, with_batch=True)
     if args.precision is not None:
-        prec = {"mixed": 1, "fp64": 0}[args.precision]
+        prec = {"mixed": 1, "fp64": 0, "tc_bf16": 2, "tc_tf32": 3}[args.precision]
     mesh = wl.mesh
     E = mesh.n_elems
     tet = mesh.conn.shape[1] == 4
@@ -625,17 +627,36 @@ def ours(args):
     # ---- the same mesh in the other precision (FP64 beside mixed) ----
     other = None
     if not args.skip_other_precision:
-        c2 = make_ctx(1 - prec)
+        oprec = 1 if prec == 0 else 0
+        c2 = make_ctx(oprec)
         for _ in range(2):
             c2.assemble()
         k2 = max(3, min(args.steps, 10))
         ms2, _ = timed_assembly(c2, stream, k2, flush, barrier, dev)
         kern2 = kernel_times(c2, 2, flush)
-        other = {"precision": "mixed" if prec == 0 else "fp64", "steps": k2,
+        other = {"precision": PREC_NAMES[oprec], "steps": k2,
                  "value": E * k2 / (max_over_ranks(ms2) / 1000.0), "unit": UNIT,
                  "ms_per_step": ms2 / k2,
-                 "roofline": roofline_entries(kern2, E, 1 - prec, tet, peaks, args.workload)}
+                 "roofline": roofline_entries(kern2, E, oprec, tet, peaks, args.workload)}
         c2.close()
+
+    # ---- the tensor-core modes of the tangent's contractions on the same mesh (hexahedra) ----
+    tensor_core = None
+    if prec == 1 and not tet and batch is None and not args.skip_other_precision:
+        tensor_core = {}
+        for tp in (2, 3):
+            c3 = make_ctx(tp)
+            for _ in range(2):
+                c3.assemble()
+            k3 = max(3, min(args.steps, 10))
+            ms3, _ = timed_assembly(c3, stream, k3, flush, barrier, dev)
+            kern3 = kernel_times(c3, 2, flush)
+            tensor_core[PREC_NAMES[tp]] = {
+                "value": E * k3 / (max_over_ranks(ms3) / 1000.0), "unit": UNIT, "steps": k3,
+                "ms_per_step": ms3 / k3, "tangent_ms": round(kern3.get("tangent", 0.0), 4),
+                "residual_ms": round(kern3.get("residual", 0.0), 4),
+                "schedule": "residual and tensor-core tangent kernels on two streams"}
+            c3.close()
 
     # ---- wall time per Newton solve: the 32^3 jittered cavity (mixed and plain FP64, to 1e-8)
     # and the 8^3 cavity (FP64, to 1e-10); the large workloads' solves take minutes each ----
@@ -708,10 +729,11 @@ def ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+            "dtype": "f32+f64" if prec != 0 else "f64", "data": "synthetic",
             "config": workload_config(args.workload, wl, prec, batch),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "other_precision": other, "schedules": schedules, "newton": newton,
+            "other_precision": other, "schedules": schedules, "tensor_core": tensor_core,
+            "newton": newton,
             "scatter": "colour" if args.scatter == 1 else "atomic",
             "tuning": tuning, "graph": bool(batch is not None or args.graph),
             "per_instance_solve": per_instance, "warm_start": warm,
@@ -729,7 +751,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default=None)
+    ap.add_argument("--precision", choices=["mixed", "fp64", "tc_bf16", "tc_tf32"], default=None)
     ap.add_argument("--scatter", type=int, choices=[0, 1], default=0)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-other-precision", action="store_true",

@@ -58,6 +58,14 @@ extern "C" {
 /* ---- precision modes (vms_create) ---------------------------------------------------------- */
 #define VMS_PREC_FP64 0   /* all element arithmetic, matrix values and residuals in FP64 */
 #define VMS_PREC_MIXED 1  /* tangent blocks and S_e in FP32; residual R, K_ff^-1, r_e in FP64 */
+/* VMS_PREC_MIXED with the tangent's basis contractions (every coarse block and the coarse-fine
+ * couplings: per element two small GEMMs against the reference basis at the quadrature points,
+ * Eq. NewtonUpdate2) on the tensor cores (mma.sync), FP32 accumulation; K_ff, its FP64 inverse,
+ * the condensation, the FP64 residual and r_e as in VMS_PREC_MIXED. Hexahedra, quad_order <= 3
+ * (tetrahedral meshes assemble as in VMS_PREC_MIXED). */
+#define VMS_PREC_MIXED_TC_BF16 2  /* BF16 operands, one product: blocks to ~1e-2 relative */
+#define VMS_PREC_MIXED_TC_TF32 3  /* TF32 operands split into high and low parts, three products
+                                     (the corrections accumulated apart): blocks to ~1e-6 */
 
 /* ---- preconditioners of the Krylov solve (vms_set_preconditioner) ---------------------------- */
 #define VMS_PRECOND_ILU0 0          /* block ILU(0), 4x4 node blocks, natural node order (default) */
@@ -94,7 +102,8 @@ typedef struct {
 } vms_csr_view;
 
 /* Create a context on CUDA device `device` in precision mode `precision` (VMS_PREC_*).
- * *ctx receives the new context. Errors: VMS_ERR_INVALID_ARG, VMS_ERR_CUDA. */
+ * *ctx receives the new context. Errors: VMS_ERR_INVALID_ARG, VMS_ERR_CUDA. The CSR values are
+ * FP32 in every mode but VMS_PREC_FP64. */
 int vms_create(vms_ctx** ctx, int device, int precision);
 
 /* Release every device buffer of the context and the context itself. NULL is accepted. */
@@ -133,7 +142,8 @@ int vms_mesh_upload_tet(vms_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
 int vms_tet_rule(int n, double* pts, double* wts);
 
 /* Set nu, visc_factor, dt, body force, bubble scale, quadrature order and scatter mode.
- * Errors: VMS_ERR_INVALID_ARG (nu <= 0, quad_order not in {2,3,4}, dt < 0, bad mode). */
+ * Errors: VMS_ERR_INVALID_ARG (nu <= 0, quad_order not in {2,3,4}, dt < 0, bad mode),
+ * VMS_ERR_UNSUPPORTED (quad_order 4 in a tensor-core mode). */
 int vms_set_params(vms_ctx* ctx, const vms_params* params);
 
 /* Upload the state: nodal (v, p) u [n_nodes x 4], bubble coefficients beta [n_elems x 3] (NULL =

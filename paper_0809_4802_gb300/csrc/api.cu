@@ -120,7 +120,7 @@ void free_mesh(vms_ctx* c) {
   dfree(s.u); dfree(s.u_prev); dfree(s.beta);
   s = State();
   Work& w = c->work;
-  dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recW); dfree(w.recKinv);
+  dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recKcf); dfree(w.recKinv);
   dfree(w.recY); dfree(w.resid); dfree(w.partial); dfree(w.flags); dfree(w.queues);
   dfree(w.f32.u); dfree(w.f32.beta);
   cudaStream_t aux = w.aux;
@@ -130,7 +130,13 @@ void free_mesh(vms_ctx* c) {
   free_solver(c->solver);
 }
 
-bool fp32_mode(const vms_ctx* c) { return c->precision == VMS_PREC_MIXED; }
+// FP32 tangent and CSR values (every mode but FP64)
+bool fp32_mode(const vms_ctx* c) { return c->precision != VMS_PREC_FP64; }
+
+// contractions of the FP32 tangent: 0 CUDA cores, TC_BF16 or TC_TF32X3 tensor cores
+int engine(const vms_ctx* c) {
+  return c->precision == VMS_PREC_MIXED_TC_BF16 ? 1 : (c->precision == VMS_PREC_MIXED_TC_TF32 ? 2 : 0);
+}
 
 KParams kparams(const vms_ctx* c) {
   KParams k{};
@@ -257,7 +263,7 @@ const char* vms_last_error(vms_ctx* ctx) { return ctx ? ctx->err.c_str() : "null
 int vms_create(vms_ctx** out, int device, int precision) {
   if (!out) return VMS_ERR_INVALID_ARG;
   *out = nullptr;
-  if (precision != VMS_PREC_FP64 && precision != VMS_PREC_MIXED) return VMS_ERR_INVALID_ARG;
+  if (precision < VMS_PREC_FP64 || precision > VMS_PREC_MIXED_TC_TF32) return VMS_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return VMS_ERR_CUDA;
@@ -324,6 +330,8 @@ int vms_set_params(vms_ctx* ctx, const vms_params* p) {
       p->quad_order < 2 || p->quad_order > 4 ||
       (p->scatter_mode != VMS_SCATTER_ATOMIC && p->scatter_mode != VMS_SCATTER_COLOUR))
     return fail(ctx, VMS_ERR_INVALID_ARG, "invalid parameters");
+  if (engine(ctx) != 0 && p->quad_order > 3)
+    return fail(ctx, VMS_ERR_UNSUPPORTED, "the tensor-core tangent takes at most 27 points (quad_order <= 3)");
   CK(cudaSetDevice(ctx->device));
   CK(cudaStreamSynchronize(ctx->stream));
   const bool retab = p->quad_order != ctx->params.quad_order || p->bubble_scale != ctx->params.bubble_scale;
@@ -415,7 +423,7 @@ int vms_autotune(vms_ctx* ctx, int repeats, vms_tuning* best) {
   CK(cudaEventCreate(&b));
   vms_tuning win{0, 0, -1, VMS_SCHEDULE_FUSED, HUGE_VAL};
   std::vector<vms_tuning> cands;
-  if (f32) cands.push_back(vms_tuning{0, 0, VMS_SCATTER_ATOMIC, VMS_SCHEDULE_FUSED, 0.0});
+  if (f32 && engine(ctx) == 0) cands.push_back(vms_tuning{0, 0, VMS_SCATTER_ATOMIC, VMS_SCHEDULE_FUSED, 0.0});
   for (int wk = 0; wk < 3; ++wk)
     for (int rt : {32, 64})
       for (int sm = VMS_SCATTER_ATOMIC; sm <= VMS_SCATTER_COLOUR; ++sm)
@@ -528,7 +536,7 @@ static int mesh_upload_impl(vms_ctx* ctx, int npe, int64_t n_nodes, const double
   CK(cudaMalloc(&w.rhs, sizeof(double) * 4 * n_nodes));
   CK(cudaMalloc(&w.elemR, sizeof(double) * 36 * n_elems));
   CK(cudaMalloc(&w.recX, sizeof(double) * 96 * n_elems));
-  CK(cudaMalloc(&w.recW, sizeof(double) * 96 * n_elems));
+  CK(cudaMalloc(&w.recKcf, sizeof(double) * 96 * n_elems));
   CK(cudaMalloc(&w.recKinv, sizeof(double) * 9 * n_elems));
   CK(cudaMalloc(&w.recY, sizeof(double) * 3 * n_elems));
   CK(cudaMalloc(&w.f32.u, sizeof(float4) * n_nodes));
@@ -609,7 +617,7 @@ static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
   }
   if (m.npe == 4) {  // tetrahedra: one kernel does residual, tangent, condensation and scatter
     TangentOut o;
-    o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv;
+    o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recKcf = w.recKcf; o.recKinv = w.recKinv;
     o.recY = w.recY;
     const int scatter = ctx->tune.scatter_mode >= 0 ? ctx->tune.scatter_mode : ctx->params.scatter_mode;
     {
@@ -634,12 +642,12 @@ static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
     k.add(launch_to_fp32(m, ctx->state, w.f32, st));
   }
   TangentOut o;
-  o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv;
+  o.values = w.values; o.rhs = w.rhs; o.recX = w.recX; o.recKcf = w.recKcf; o.recKinv = w.recKinv;
   o.recY = w.recY;
   const void* tab = f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64;
   const int scatter = ctx->tune.scatter_mode >= 0 ? ctx->tune.scatter_mode : ctx->params.scatter_mode;
   const bool colour = scatter == VMS_SCATTER_COLOUR;
-  if (f32 && !colour && ctx->tune.schedule == VMS_SCHEDULE_FUSED) {
+  if (f32 && engine(ctx) == 0 && !colour && ctx->tune.schedule == VMS_SCHEDULE_FUSED) {
     // residual and tangent in one persistent launch, then r_e and the Dirichlet rows
     {
       KScope k(ctx, VMS_K_FILL, st);
@@ -671,11 +679,11 @@ static int enqueue_assembly(vms_ctx* ctx, cudaStream_t st) {
     if (colour) {
       for (int c = 0; c < m.n_colours; ++c) {
         const int64_t b = m.colour_start[c], n = m.colour_start[c + 1] - b;
-        k.add(launch_tangent(f32, m, ctx->state, w.f32, kp, tab, o, b, n, m.colour_order, false,
+        k.add(launch_tangent(f32, engine(ctx), m, ctx->state, w.f32, kp, tab, o, b, n, m.colour_order, false,
                              false, w.flags, w.aux));
       }
     } else {
-      k.add(launch_tangent(f32, m, ctx->state, w.f32, kp, tab, o, 0, m.n_elems, nullptr, false,
+      k.add(launch_tangent(f32, engine(ctx), m, ctx->state, w.f32, kp, tab, o, 0, m.n_elems, nullptr, false,
                            true, w.flags, w.aux));
     }
   }
@@ -821,7 +829,7 @@ static int element_matrices_tet(vms_ctx* ctx, int64_t first, int64_t count, doub
   TangentOut o;
   o.S = buf; o.r = buf + 256 * count; o.Kcc = buf + 272 * count; o.Kcf = buf + 528 * count;
   o.Kfc = buf + 576 * count; o.Kff = buf + 624 * count;
-  o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv; o.recY = w.recY;
+  o.recX = w.recX; o.recKcf = w.recKcf; o.recKinv = w.recKinv; o.recY = w.recY;
   {
     KScope k(ctx, VMS_K_TANGENT);
     k.add(launch_tet_assembly(f32, m, ctx->state, kp, ctx->tet_mom, o, first, count,
@@ -875,10 +883,10 @@ int vms_element_matrices(vms_ctx* ctx, int64_t first, int64_t count, double* S, 
   TangentOut o;
   o.S = buf; o.r = buf + 1024 * count; o.Kcc = buf + 1056 * count; o.Kcf = buf + 2080 * count;
   o.Kfc = buf + 2176 * count; o.Kff = buf + 2272 * count;
-  o.recX = w.recX; o.recW = w.recW; o.recKinv = w.recKinv; o.recY = w.recY;
+  o.recX = w.recX; o.recKcf = w.recKcf; o.recKinv = w.recKinv; o.recY = w.recY;
   {
     KScope k(ctx, VMS_K_TANGENT);
-    k.add(launch_tangent(f32, m, ctx->state, w.f32, kp,
+    k.add(launch_tangent(f32, engine(ctx), m, ctx->state, w.f32, kp,
                          f32 ? (const void*)ctx->d_tab32 : (const void*)ctx->d_tab64, o, first,
                          count, nullptr, true, true, w.flags, st));
   }

@@ -71,11 +71,10 @@ VMS_HD void residual_load(const Store& C, const double X[8][3], const double U[8
 // monomial xi^a eta^b zeta^c (or its derivative) is xi^a times a line constant, so each line keeps
 // seven sums per component (src, xi src, P0, P1, xi P1, P2, xi P2) and two for the continuity term,
 // and adds them into the eight monomial sums, which live in the store, once per line.
-template <bool TRANSIENT, bool FORCE, class Store, class Table>
-VMS_HD bool residual_qp_loop(const Store& C, const Table& tab, int nq, const double bet[3],
-                             double nut, double tau, const double f[3], double Rcp[32],
-                             double Rf[3]) {
-  const int n1 = nq == 8 ? 2 : (nq == 27 ? 3 : 4);
+template <bool TRANSIENT, bool FORCE, int N1, class Store, class Table>
+VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double bet[3], double nut,
+                               double tau, const double f[3], double Rcp[32], double Rf[3]) {
+  constexpr int n1 = N1;
   VMS_UNROLL
   for (int m = 0; m < 32; ++m) C.set(RC_RM + m, 0.0);
   Rf[0] = Rf[1] = Rf[2] = 0.0;
@@ -110,6 +109,7 @@ VMS_HD bool residual_qp_loop(const Store& C, const Table& tab, int nq, const dou
       double c0[3] = {0.0, 0.0, 0.0}, c1[3] = {0.0, 0.0, 0.0};
       double d0[3] = {0.0, 0.0, 0.0}, d1[3] = {0.0, 0.0, 0.0};
       double t0 = 0.0, t1 = 0.0;
+      VMS_UNROLL
       for (int ii = 0; ii < n1; ++ii) {
         const int q = q0 + ii;
         const double xi = tab.xi(q), xz = tab.xz(q), xe = tab.xe(q);
@@ -230,6 +230,16 @@ VMS_HD bool residual_qp_loop(const Store& C, const Table& tab, int nq, const dou
   return ok;
 }
 
+// The quadrature loop for the Gauss rule of nq = 8, 27 or 64 points (the line loop unrolled).
+template <bool TRANSIENT, bool FORCE, class Store, class Table>
+VMS_HD bool residual_qp_loop(const Store& C, const Table& tab, int nq, const double bet[3],
+                             double nut, double tau, const double f[3], double Rcp[32],
+                             double Rf[3]) {
+  if (nq == 27) return residual_qp_loop_n<TRANSIENT, FORCE, 3>(C, tab, bet, nut, tau, f, Rcp, Rf);
+  if (nq == 8) return residual_qp_loop_n<TRANSIENT, FORCE, 2>(C, tab, bet, nut, tau, f, Rcp, Rf);
+  return residual_qp_loop_n<TRANSIENT, FORCE, 4>(C, tab, bet, nut, tau, f, Rcp, Rf);
+}
+
 #if defined(__CUDACC__)
 // One element's residual on one thread: gather the 8 nodes (and the previous step's velocities),
 // map them to monomial coefficients in `C`, run the quadrature loop. Returns the element's error
@@ -248,19 +258,59 @@ __device__ __forceinline__ unsigned residual_element(
     nd[4] = c1.x; nd[5] = c1.y; nd[6] = c1.z; nd[7] = c1.w;
   }
   {
-    double X[8][3], U[8][4], Up[8][3];
-    VMS_UNROLL
-    for (int a = 0; a < 8; ++a) {
-      const double4_32a x = xyz[nd[a]];
-      const double4_32a w = u[nd[a]];
-      X[a][0] = x.x; X[a][1] = x.y; X[a][2] = x.z;
-      U[a][0] = w.x; U[a][1] = w.y; U[a][2] = w.z; U[a][3] = w.w;
-      if (TRANSIENT) {
-        const double4_32a o = uprev[nd[a]];
-        Up[a][0] = o.x; Up[a][1] = o.y; Up[a][2] = o.z;
+    // one record type at a time, each mapped to its monomial coefficients before the next is
+    // loaded (fewer values live at once than gathering all node data first)
+    double f[8], c[8], U[8][3];
+    {
+      double X[8][3];
+      VMS_UNROLL
+      for (int a = 0; a < 8; ++a) {
+        const double4_32a x = xyz[nd[a]];
+        X[a][0] = x.x; X[a][1] = x.y; X[a][2] = x.z;
+      }
+      VMS_UNROLL
+      for (int i = 0; i < 3; ++i) {
+        VMS_UNROLL
+        for (int a = 0; a < 8; ++a) f[a] = X[a][i];
+        modal8(f, c);
+        VMS_UNROLL
+        for (int m = 1; m < 8; ++m) C.set(RC_X + 7 * i + m - 1, 0.125 * c[m]);
       }
     }
-    residual_load(C, X, U, Up, TRANSIENT);
+    {
+      double P[8];
+      VMS_UNROLL
+      for (int a = 0; a < 8; ++a) {
+        const double4_32a w = u[nd[a]];
+        U[a][0] = w.x; U[a][1] = w.y; U[a][2] = w.z; P[a] = w.w;
+      }
+      modal8(P, c);
+      VMS_UNROLL
+      for (int m = 0; m < 8; ++m) C.set(RC_P + m, 0.125 * c[m]);
+    }
+    VMS_UNROLL
+    for (int i = 0; i < 3; ++i) {
+      VMS_UNROLL
+      for (int a = 0; a < 8; ++a) f[a] = U[a][i];
+      modal8(f, c);
+      VMS_UNROLL
+      for (int m = 0; m < 8; ++m) C.set(RC_V + 8 * i + m, 0.125 * c[m]);
+    }
+    if (TRANSIENT) {
+      VMS_UNROLL
+      for (int a = 0; a < 8; ++a) {
+        const double4_32a o = uprev[nd[a]];
+        U[a][0] -= o.x; U[a][1] -= o.y; U[a][2] -= o.z;
+      }
+      VMS_UNROLL
+      for (int i = 0; i < 3; ++i) {
+        VMS_UNROLL
+        for (int a = 0; a < 8; ++a) f[a] = U[a][i];
+        modal8(f, c);
+        VMS_UNROLL
+        for (int m = 0; m < 8; ++m) C.set(RC_DV + 8 * i + m, 0.125 * c[m]);
+      }
+    }
   }
   const double bet[3] = {beta[3 * e + 0], beta[3 * e + 1], beta[3 * e + 2]};
   const double nut = kp.nu_e ? kp.visc_factor * __ldg(kp.nu_e + e) : kp.nut;

@@ -8,6 +8,7 @@
 #include "residual_math.cuh"
 #include "residual_table.cuh"
 #include "tangent_math.cuh"
+#include "tangent_tc.cuh"
 #include "vms_internal.h"
 
 namespace vms {
@@ -127,16 +128,17 @@ template <> struct NodeVec<float> { using type = float4; };
 // One element (a1-a8) for one warp: gather, quadrature-point coefficients, tangent blocks,
 // condensation, recovery data and the scatter (or the element outputs). `it` is the element's
 // position in the launch (element outputs), `e` its index in the mesh.
-template <typename T, bool ELEM_OUT, bool ATOMIC, int QCH = 32>
+template <typename T, bool ELEM_OUT, bool ATOMIC, int QCH = 32, int ENG = 0>
 __device__ __forceinline__ void tangent_element(
-    int lane, int64_t it, int64_t e, WarpArea<T>& W, const RefTab<T>& tab,
+    int lane, int64_t it, int64_t e, WarpArea<T>& W, const RefTab<T>& tab, void* tcw,
+    const uint32_t* __restrict__ bfrag,
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn,
     const T* __restrict__ beta, int nq, T nut, T tau, const double* __restrict__ nu_e,
     double visc_factor, const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
     const double* __restrict__ beta64, const double* __restrict__ tab64,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
-    double* __restrict__ recW, double* __restrict__ recKinv, double* __restrict__ oS,
+    T* __restrict__ recKcf, double* __restrict__ recKinv, double* __restrict__ oS,
     double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
     double* __restrict__ oKff, unsigned int* __restrict__ flags) {
   // gather (a1): 8 nodes and the bubble coefficients
@@ -166,10 +168,21 @@ __device__ __forceinline__ void tangent_element(
   const T nut_e = nu_e ? T(visc_factor * __ldg(nu_e + e)) : nut;
   LaneAcc<T> A;
   tan_zero(A);
-  for (int q0 = 0; q0 < nq; q0 += QCH) {
-    if (QCH == 32 || lane < QCH) tan_phase1(lane, q0, nq, W, tab, nut_e, tau, A);
+  if constexpr (ENG == 0) {
+    for (int q0 = 0; q0 < nq; q0 += QCH) {
+      if (QCH == 32 || lane < QCH) tan_phase1(lane, q0, nq, W, tab, nut_e, tau, A);
+      __syncwarp();
+      tan_phase2(lane, nq - q0 < QCH ? nq - q0 : QCH, W, nut_e, A);
+      __syncwarp();
+    }
+  } else {
+    // tensor-core contractions (FP32 only; nq <= 32, checked on the host)
+    TcArea<ENG>& C = *reinterpret_cast<TcArea<ENG>*>(tcw);
+    tc_phase1<ENG>(lane, nq, W, C, tab, nut_e, tau, A);
     __syncwarp();
-    tan_phase2(lane, nq - q0 < QCH ? nq - q0 : QCH, W, nut_e, A);
+    tc_contract<ENG>(lane, C, bfrag);
+    __syncwarp();
+    tc_gather<ENG>(lane, C, A);
     __syncwarp();
   }
   const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
@@ -216,15 +229,14 @@ __device__ __forceinline__ void tangent_element(
       __syncwarp();
     }
   }
-  double Wl[3];
-  tan_phase3f(lane, W, A, Wl, accurate);
+  tan_phase3f(lane, W, A, accurate);
   __syncwarp();
   tan_phase3e(lane, W, A, accurate);
-  // per-element data for the finish kernel and the fine-scale recovery
+  // per-element data for the finish kernel (K_cf, K_ff^-1) and the fine-scale recovery (X)
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     recX[96 * e + 32 * m + lane] = W.Xs[m][lane];
-    recW[96 * e + 3 * lane + m] = Wl[m];
+    recKcf[96 * e + 3 * lane + m] = A.kcf[m];
   }
   if (lane < 9) recKinv[9 * e + lane] = W.Kinv[lane];
   if (ELEM_OUT) {
@@ -266,7 +278,21 @@ __device__ __forceinline__ void tangent_element(
   __syncwarp();
 }
 
-template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS>
+// Shared memory of the tangent kernel: the reference table, the tensor-core right operands (ENG
+// != 0), then per warp its WarpArea (point records only for the CUDA-core contractions) and its
+// TcArea (tensor-core contractions).
+template <typename T, int ENG>
+__host__ __device__ inline size_t tan_bfrag_bytes() {
+  if constexpr (ENG == 0) return 0;
+  else return (size_t)tc_bsteps<ENG>() * 32 * tc_bwords<ENG>() * 4;
+}
+template <typename T, int ENG>
+__host__ __device__ inline size_t tan_warp_total(int nq) {
+  if constexpr (ENG == 0) return tan_warp_bytes<T>(nq);
+  else return tan_warp_bytes<T, 0>(nq) + ((sizeof(TcArea<ENG>) + 15) & ~size_t(15));
+}
+
+template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS, int ENG = 0>
 __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
     int nq, T nut, T tau, const double* __restrict__ nu_e, double visc_factor,
@@ -275,7 +301,7 @@ __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
     int64_t count, const int32_t* __restrict__ elem_list,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
-    double* __restrict__ recW, double* __restrict__ recKinv, double* __restrict__ oS,
+    T* __restrict__ recKcf, double* __restrict__ recKinv, double* __restrict__ oS,
     double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
     double* __restrict__ oKff, unsigned int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -284,14 +310,24 @@ __global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
   __syncthreads();
   const RefTab<T> tab{st, st + 8 * nq, st + 32 * nq, st + 33 * nq, st + 36 * nq};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpArea<T>& W = *reinterpret_cast<WarpArea<T>*>(smem + tan_table_bytes<T>(nq) +
-                                                   warp * tan_warp_bytes<T>(nq));
+  uint32_t* bfrag = reinterpret_cast<uint32_t*>(smem + tan_table_bytes<T>(nq));
+  unsigned char* wbase = smem + tan_table_bytes<T>(nq) + tan_bfrag_bytes<T, ENG>() +
+                         (size_t)warp * tan_warp_total<T, ENG>(nq);
+  WarpArea<T>& W = *reinterpret_cast<WarpArea<T>*>(wbase);
+  void* tcw = nullptr;
+  if constexpr (ENG != 0) {
+    tc_build_b<ENG>(tab.N, tab.dN, nq, bfrag);
+    tcw = wbase + tan_warp_bytes<T, 0>(nq);
+    TcArea<ENG>& C = *reinterpret_cast<TcArea<ENG>*>(tcw);
+    for (int i = lane; i < (TC_ROWS_D - 10) * tc_sd<ENG>(); i += 32) (&C.AD[10][0])[i] = 0.f;
+    __syncthreads();
+  }
   const int64_t total = (int64_t)gridDim.x * WARPS;
   for (int64_t it = (int64_t)blockIdx.x * WARPS + warp; it < count; it += total) {
     const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
-    tangent_element<T, ELEM_OUT, ATOMIC>(lane, it, e, W, tab, u, conn, beta, nq, nut, tau, nu_e,
+    tangent_element<T, ELEM_OUT, ATOMIC, 32, ENG>(lane, it, e, W, tab, tcw, bfrag, u, conn, beta, nq, nut, tau, nu_e,
                                          visc_factor, xyz64, u64, beta64, tab64, blk, rowlen,
-                                         dir_mask, values, recX, recW, recKinv, oS, oKcc, oKcf,
+                                         dir_mask, values, recX, recKcf, recKinv, oS, oKcc, oKcf,
                                          oKfc, oKff, flags);
   }
 }
@@ -328,7 +364,7 @@ __global__ void __launch_bounds__(FUSED_WARPS * 32, 1) fused_assembly_kernel(
     double* __restrict__ elemR, const float4* __restrict__ u32, const float* __restrict__ beta32,
     const float* __restrict__ gtab, float nut, float tau, const int32_t* __restrict__ blk,
     const int32_t* __restrict__ rowlen, const uint32_t* __restrict__ dir_mask,
-    float* __restrict__ values, float* __restrict__ recX, double* __restrict__ recW,
+    float* __restrict__ values, float* __restrict__ recX, float* __restrict__ recKcf,
     double* __restrict__ recKinv, int64_t n_elems, unsigned long long* __restrict__ queues,
     unsigned int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -366,9 +402,9 @@ __global__ void __launch_bounds__(FUSED_WARPS * 32, 1) fused_assembly_kernel(
     if (base >= (unsigned long long)n_elems) break;
     const int64_t end = (int64_t)base + FUSED_TCLAIM < n_elems ? (int64_t)base + FUSED_TCLAIM : n_elems;
     for (int64_t e = (int64_t)base; e < end; ++e)
-      tangent_element<float, false, true, FUSED_QCH>(lane, e, e, W, tab, u32, conn, beta32, nq, nut, tau,
+      tangent_element<float, false, true, FUSED_QCH>(lane, e, e, W, tab, nullptr, nullptr, u32, conn, beta32, nq, nut, tau,
                                           kp.nu_e, kp.visc_factor, xyz, u64, beta64, kp.tab64, blk,
-                                          rowlen, dir_mask, values, recX, recW, recKinv, nullptr,
+                                          rowlen, dir_mask, values, recX, recKcf, recKinv, nullptr,
                                           nullptr, nullptr, nullptr, nullptr, flags);
   }
 }
@@ -383,7 +419,7 @@ int launch_fused_assembly(const Mesh& m, const State& s, const Fp32Copy& c32, co
     kern<<<(unsigned)sm_count(), FUSED_WARPS * 32, smem, st>>>(
         m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, elemR, c32.u, c32.beta, tab32,
         (float)kp.nut, (float)kp.tau, m.blk, m.rowlen, m.dir_mask, reinterpret_cast<float*>(o.values),
-        reinterpret_cast<float*>(o.recX), reinterpret_cast<double*>(o.recW), o.recKinv, m.n_elems,
+        reinterpret_cast<float*>(o.recX), reinterpret_cast<float*>(o.recKcf), o.recKinv, m.n_elems,
         queues, flags);
   };
   if (kp.transient) {
@@ -396,33 +432,38 @@ int launch_fused_assembly(const Mesh& m, const State& s, const Fp32Copy& c32, co
   return 1;
 }
 
-// r_e = R_cp - W R_f (FP64) scattered into the right-hand side, and y = K_ff^-1 R_f stored for
-// the recovery. One thread per (element, local dof); threads 32..34 of an element write y.
+// y = K_ff^-1 R_f (FP64, kept for the recovery) and r_e = R_cp - K_cf y (FP64 arithmetic on the
+// stored K_cf, FP32 in mixed precision) scattered into the right-hand side. One thread per element.
 template <typename T, bool ATOMIC>
-__global__ void __launch_bounds__(256) finish_kernel(
-    const int32_t* __restrict__ conn, const double* __restrict__ elemR, const double* __restrict__ recW,
+__global__ void __launch_bounds__(128) finish_kernel(
+    const int32_t* __restrict__ conn, const double* __restrict__ elemR, const T* __restrict__ recKcf,
     const double* __restrict__ recKinv, const uint32_t* __restrict__ dir_mask, int64_t first,
     int64_t count, const int32_t* __restrict__ elem_list, double* __restrict__ rhs,
     double* __restrict__ recY, double* __restrict__ oR) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t it = g / 36;
-  const int t = (int)(g % 36);
-  if (it >= count || t >= 35) return;
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= count) return;
   const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
-  const double Rf[3] = {elemR[36 * e + 32], elemR[36 * e + 33], elemR[36 * e + 34]};
-  if (t < 32) {
-    const double Wt[3] = {recW[96 * e + 3 * t], recW[96 * e + 3 * t + 1], recW[96 * e + 3 * t + 2]};
-    const double r = condensed_residual(elemR[36 * e + t], Wt, Rf);
+  const double* R = elemR + 36 * e;
+  const double Rf[3] = {R[32], R[33], R[34]};
+  double y[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const double* K = recKinv + 9 * e + 3 * m;
+    y[m] = K[0] * Rf[0] + K[1] * Rf[1] + K[2] * Rf[2];
+    recY[3 * e + m] = y[m];
+  }
+  const uint32_t msk = oR ? 0u : dir_mask[e];
+  const T* kc = recKcf + 96 * e;
+#pragma unroll 4
+  for (int t = 0; t < 32; ++t) {
+    const double r = R[t] - ((double)kc[3 * t] * y[0] + (double)kc[3 * t + 1] * y[1] +
+                             (double)kc[3 * t + 2] * y[2]);
     if (oR) {
       oR[32 * it + t] = r;
-    } else if (!(dir_mask[e] >> t & 1u)) {
+    } else if (!(msk >> t & 1u)) {
       double* dst = rhs + 4 * (int64_t)conn[8 * e + (t >> 2)] + (t & 3);
       if (ATOMIC) atomicAdd(dst, r); else *dst += r;
     }
-  } else {
-    const int m = t - 32;
-    const double* K = recKinv + 9 * e + 3 * m;
-    recY[3 * e + m] = K[0] * Rf[0] + K[1] * Rf[1] + K[2] * Rf[2];
   }
 }
 
@@ -449,13 +490,13 @@ int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, cudaStream_
   return 1;
 }
 
-template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS>
+template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS, int ENG>
 static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
                      const T* tab, const TangentOut& o, int64_t first, int64_t count,
                      const int32_t* elem_list, unsigned int* flags, cudaStream_t st) {
   const int nq = kp.nq;
-  const size_t smem = tan_table_bytes<T>(nq) + WARPS * tan_warp_bytes<T>(nq);
-  auto kern = tangent_kernel<T, ELEM_OUT, ATOMIC, WARPS>;
+  const size_t smem = tan_table_bytes<T>(nq) + tan_bfrag_bytes<T, ENG>() + WARPS * tan_warp_total<T, ENG>(nq);
+  auto kern = tangent_kernel<T, ELEM_OUT, ATOMIC, WARPS, ENG>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = (count + WARPS - 1) / WARPS;
   if (blocks > (int64_t)sm_count() * 128) blocks = (int64_t)sm_count() * 128;
@@ -471,22 +512,29 @@ static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const K
       u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, s.u,
       s.beta, kp.tab64, first, count, elem_list, m.blk,
       m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
-      reinterpret_cast<double*>(o.recW), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
+      reinterpret_cast<T*>(o.recKcf), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
 }
 
 // Warps per block: the default, or the tuned count when it is one of the compiled choices
-// (FP32: 2, 4, 8; FP64: 1, 2, 4). Element outputs always use the default.
+// (FP32: 2, 4, 8; FP64: 1, 2, 4). Element outputs always use the default. The tensor-core
+// engines (FP32 only) run two warps per block (their per-warp operand storage is ~33 KB).
 template <typename T, bool ELEM_OUT, bool ATOMIC>
 static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
                      const T* tab, const TangentOut& o, int64_t first, int64_t count,
-                     const int32_t* elem_list, unsigned int* flags, cudaStream_t st) {
+                     const int32_t* elem_list, int engine, unsigned int* flags, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (engine == TC_BF16)
+      return launch_w<T, ELEM_OUT, ATOMIC, 2, TC_BF16>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+    if (engine == TC_TF32X3)
+      return launch_w<T, ELEM_OUT, ATOMIC, 2, TC_TF32X3>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+  }
   constexpr int D = tan_warps<T>();
   const int w = ELEM_OUT ? D : (kp.tangent_warps ? kp.tangent_warps : D);
   if constexpr (!ELEM_OUT) {
-    if (w == D / 2) return launch_w<T, false, ATOMIC, D / 2>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
-    if (w == 2 * D) return launch_w<T, false, ATOMIC, 2 * D>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+    if (w == D / 2) return launch_w<T, false, ATOMIC, D / 2, 0>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+    if (w == 2 * D) return launch_w<T, false, ATOMIC, 2 * D, 0>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
   }
-  launch_w<T, ELEM_OUT, ATOMIC, D>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+  launch_w<T, ELEM_OUT, ATOMIC, D, 0>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
 }
 
 int tangent_warp_choice(bool fp32, int k) {
@@ -494,21 +542,21 @@ int tangent_warp_choice(bool fp32, int k) {
   return k == 0 ? d / 2 : (k == 1 ? d : 2 * d);
 }
 
-int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32,
+int launch_tangent(bool fp32, int engine, const Mesh& m, const State& s, const Fp32Copy& c32,
                    const KParams& kp, const void* tab, const TangentOut& out, int64_t first,
                    int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
                    unsigned int* flags, cudaStream_t st) {
   if (count <= 0) return 0;
   if (fp32) {
     const float* t = reinterpret_cast<const float*>(tab);
-    if (elem_outputs) launch_t<float, true, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
-    else if (atomic) launch_t<float, false, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
-    else launch_t<float, false, false>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
+    if (elem_outputs) launch_t<float, true, true>(m, s, c32, kp, t, out, first, count, elem_list, engine, flags, st);
+    else if (atomic) launch_t<float, false, true>(m, s, c32, kp, t, out, first, count, elem_list, engine, flags, st);
+    else launch_t<float, false, false>(m, s, c32, kp, t, out, first, count, elem_list, engine, flags, st);
   } else {
     const double* t = reinterpret_cast<const double*>(tab);
-    if (elem_outputs) launch_t<double, true, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
-    else if (atomic) launch_t<double, false, true>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
-    else launch_t<double, false, false>(m, s, c32, kp, t, out, first, count, elem_list, flags, st);
+    if (elem_outputs) launch_t<double, true, true>(m, s, c32, kp, t, out, first, count, elem_list, 0, flags, st);
+    else if (atomic) launch_t<double, false, true>(m, s, c32, kp, t, out, first, count, elem_list, 0, flags, st);
+    else launch_t<double, false, false>(m, s, c32, kp, t, out, first, count, elem_list, 0, flags, st);
   }
   return 1;
 }
@@ -517,17 +565,17 @@ int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOu
                   int64_t first, int64_t count, const int32_t* elem_list, bool atomic,
                   cudaStream_t st) {
   if (count <= 0) return 0;
-  const unsigned blocks = (unsigned)((count * 36 + 255) / 256);
+  const unsigned blocks = (unsigned)((count + 127) / 128);
+  auto go = [&](auto kern, auto* kcf) {
+    kern<<<blocks, 128, 0, st>>>(m.conn, elemR, kcf, o.recKinv, m.dir_mask, first, count,
+                                 elem_list, o.rhs, o.recY, o.r);
+  };
   if (fp32) {
-    if (atomic)
-      finish_kernel<float, true><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
-    else
-      finish_kernel<float, false><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
+    const float* k = reinterpret_cast<const float*>(o.recKcf);
+    if (atomic) go(finish_kernel<float, true>, k); else go(finish_kernel<float, false>, k);
   } else {
-    if (atomic)
-      finish_kernel<double, true><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
-    else
-      finish_kernel<double, false><<<blocks, 256, 0, st>>>(m.conn, elemR, (const double*)o.recW, o.recKinv, m.dir_mask, first, count, elem_list, o.rhs, o.recY, o.r);
+    const double* k = reinterpret_cast<const double*>(o.recKcf);
+    if (atomic) go(finish_kernel<double, true>, k); else go(finish_kernel<double, false>, k);
   }
   return 1;
 }

@@ -343,15 +343,13 @@ VMS_HD T kff_cond_inf(const WarpArea<T>& W) {
   return nk * ni;
 }
 
-// Phase 3f: column L of X = K_ff^-1 K_fc and row L of W = K_cf K_ff^-1 (kept in FP64 as Wl for
-// r_e = R_cp - W R_f), and row L of K_cf, to shared memory. In FP32 with `accurate` (an
-// ill-conditioned K_ff) X and W are formed in FP64 from the FP64 inverse and X is kept as a high
-// and a low part in T; otherwise they are formed in T (Xl = 0).
+// Phase 3f: column L of X = K_ff^-1 K_fc and row L of K_cf, to shared memory. In FP32 with
+// `accurate` (an ill-conditioned K_ff) X is formed in FP64 from the FP64 inverse and kept as a high
+// and a low part in T; otherwise it is formed in T (Xl = 0).
 template <typename T>
-VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, double Wl[3], bool accurate) {
+VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, bool accurate) {
   if (sizeof(T) == 8 || accurate) {
     const double f0 = (double)A.kfc[0], f1 = (double)A.kfc[1], f2 = (double)A.kfc[2];
-    const double c0 = (double)A.kcf[0], c1 = (double)A.kcf[1], c2 = (double)A.kcf[2];
     VMS_UNROLL
     for (int m = 0; m < 3; ++m) {
       const double x = W.Kinv[3 * m] * f0 + W.Kinv[3 * m + 1] * f1 + W.Kinv[3 * m + 2] * f2;
@@ -359,7 +357,6 @@ VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, double Wl
       W.Xs[m][lane] = xh;
       W.Xl[m][lane] = T(x - (double)xh);
       W.Kcf[lane][m] = A.kcf[m];
-      Wl[m] = c0 * W.Kinv[m] + c1 * W.Kinv[3 + m] + c2 * W.Kinv[6 + m];
     }
   } else {
     VMS_UNROLL
@@ -368,14 +365,8 @@ VMS_HD void tan_phase3f(int lane, WarpArea<T>& W, const LaneAcc<T>& A, double Wl
                       W.KinvT[3 * m + 2] * A.kfc[2];
       W.Xl[m][lane] = T(0);
       W.Kcf[lane][m] = A.kcf[m];
-      Wl[m] = (double)(A.kcf[0] * W.KinvT[m] + A.kcf[1] * W.KinvT[3 + m] + A.kcf[2] * W.KinvT[6 + m]);
     }
   }
-}
-
-// Condensed residual entry (FP64): r_t = R_cp[t] - sum_m W[t][m] R_f[m].
-VMS_HD double condensed_residual(double Rcp_t, const double Wt[3], const double Rf[3]) {
-  return Rcp_t - (Wt[0] * Rf[0] + Wt[1] * Rf[1] + Wt[2] * Rf[2]);
 }
 
 #if defined(__CUDACC__)

@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(TET_WARPS * 32) tet_assembly_kernel(
     int64_t first, int64_t count, const int32_t* __restrict__ elem_list,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, double* __restrict__ rhs,
-    T* __restrict__ recX, double* __restrict__ recW, double* __restrict__ recKinv,
+    T* __restrict__ recX, double* __restrict__ recKinv,
     double* __restrict__ recY, double* __restrict__ oS, double* __restrict__ oR,
     double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
     double* __restrict__ oKff, unsigned int* __restrict__ flags) {
@@ -528,10 +528,6 @@ __global__ void __launch_bounds__(TET_WARPS * 32) tet_assembly_kernel(
       for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int k = 0; k < 4; ++k) recX[96 * e + 32 * m + 4 * a + k] = T(Xa[m][k]);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) recW[96 * e + 3 * (4 * a + i) + m] = Wa[i][m];
       if (a < 3) {
         double kr3[3];
 #pragma unroll
@@ -671,7 +667,7 @@ void launch_ta(const Mesh& m, const State& s, const KParams& kp, const TetMoment
   tet_assembly_kernel<T, ELEM_OUT, ATOMIC><<<tet_blocks(count), TET_WARPS * 32, 0, st>>>(
       m.xyz, s.u, s.u_prev, m.conn, s.beta, mom, kp, first, count, elem_list, m.blk, m.rowlen,
       m.dir_mask, reinterpret_cast<T*>(o.values), o.rhs, reinterpret_cast<T*>(o.recX),
-      reinterpret_cast<double*>(o.recW), o.recKinv, o.recY, o.S,
+      o.recKinv, o.recY, o.S,
       o.r, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
 }
 

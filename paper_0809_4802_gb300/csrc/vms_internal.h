@@ -103,7 +103,7 @@ struct Work {
   double* rhs = nullptr;      // 4 n_nodes
   double* elemR = nullptr;    // n_elems * 36: R_cp (32), R_f (3), pad
   void* recX = nullptr;       // n_elems * 96 (T): K_ff^-1 K_fc
-  void* recW = nullptr;       // n_elems * 96 (FP64): K_cf K_ff^-1
+  void* recKcf = nullptr;     // n_elems * 96 (T): K_cf, row-major [32][3] (hexahedra)
   double* recKinv = nullptr;  // n_elems * 9: K_ff^-1 (FP64)
   double* recY = nullptr;     // n_elems * 3: K_ff^-1 R_f
   double* resid = nullptr;    // 4 n_nodes + 3 n_elems
@@ -128,7 +128,7 @@ struct TangentOut {
   void* values = nullptr;      // CSR values (assembly)
   double* rhs = nullptr;       // condensed right-hand side (assembly, finish kernel)
   void* recX = nullptr;        // per element K_ff^-1 K_fc (T)
-  void* recW = nullptr;        // per element K_cf K_ff^-1 (FP64)
+  void* recKcf = nullptr;      // per element K_cf (T), row-major [32][3] (finish kernel)
   double* recKinv = nullptr;   // per element K_ff^-1
   double* recY = nullptr;      // per element K_ff^-1 R_f (finish kernel)
   // element outputs (parity), FP64, may be null
@@ -172,7 +172,8 @@ int launch_tet_residual(const Mesh& m, const State& s, const KParams& kp, const 
 
 // The three warps-per-block counts the tangent kernel is compiled for (k = 0, 1, 2; 1 = default).
 int tangent_warp_choice(bool fp32, int k);
-int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32,
+// engine (FP32 only): 0 CUDA-core contractions, 1 BF16 tensor cores, 2 split-TF32 tensor cores.
+int launch_tangent(bool fp32, int engine, const Mesh& m, const State& s, const Fp32Copy& c32,
                    const KParams& kp, const void* tab, const TangentOut& out, int64_t first,
                    int64_t count, const int32_t* elem_list, bool elem_outputs, bool atomic,
                    unsigned int* flags, cudaStream_t st);
@@ -181,7 +182,7 @@ int launch_tangent(bool fp32, const Mesh& m, const State& s, const Fp32Copy& c32
 int launch_fused_assembly(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
                           const QpRow* qp, const float* tab32, double* elemR, const TangentOut& o,
                           unsigned long long* queues, unsigned int* flags, cudaStream_t st);
-// r_e = R_cp - K_cf K_ff^-1 R_f (FP64) into rhs (or into out.r), and K_ff^-1 R_f into recY.
+// y = K_ff^-1 R_f into recY and r_e = R_cp - K_cf y (FP64) into rhs (or into out.r).
 int launch_finish(bool fp32, const Mesh& m, const double* elemR, const TangentOut& out,
                   int64_t first, int64_t count, const int32_t* elem_list, bool atomic,
                   cudaStream_t st);

@@ -33,6 +33,8 @@ NOALLOC_MAX_ENTRIES = 2097152
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_MIXED_TC_BF16 = 2
+PREC_MIXED_TC_TF32 = 3
 SCATTER_ATOMIC = 0
 SCATTER_COLOUR = 1
 PRECOND_ILU0 = 0
