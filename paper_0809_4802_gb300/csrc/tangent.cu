@@ -292,8 +292,10 @@ __host__ __device__ inline size_t tan_warp_total(int nq) {
   else return tan_warp_bytes<T, 0>(nq) + ((sizeof(TcArea<ENG>) + 15) & ~size_t(15));
 }
 
+constexpr int TC_WARPS = 2;
+
 template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS, int ENG = 0>
-__global__ void __launch_bounds__(WARPS * 32) tangent_kernel(
+__global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : 4) tangent_kernel(
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
     int nq, T nut, T tau, const double* __restrict__ nu_e, double visc_factor,
     const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
@@ -517,16 +519,16 @@ static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const K
 
 // Warps per block: the default, or the tuned count when it is one of the compiled choices
 // (FP32: 2, 4, 8; FP64: 1, 2, 4). Element outputs always use the default. The tensor-core
-// engines (FP32 only) run two warps per block (their per-warp operand storage is ~33 KB).
+// engines (FP32 only) run TC_WARPS warps per block (their per-warp operand storage is ~28 KB).
 template <typename T, bool ELEM_OUT, bool ATOMIC>
 static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const KParams& kp,
                      const T* tab, const TangentOut& o, int64_t first, int64_t count,
                      const int32_t* elem_list, int engine, unsigned int* flags, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (engine == TC_BF16)
-      return launch_w<T, ELEM_OUT, ATOMIC, 2, TC_BF16>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+      return launch_w<T, ELEM_OUT, ATOMIC, TC_WARPS, TC_BF16>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
     if (engine == TC_TF32X3)
-      return launch_w<T, ELEM_OUT, ATOMIC, 2, TC_TF32X3>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+      return launch_w<T, ELEM_OUT, ATOMIC, TC_WARPS, TC_TF32X3>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
   }
   constexpr int D = tan_warps<T>();
   const int w = ELEM_OUT ? D : (kp.tangent_warps ? kp.tangent_warps : D);

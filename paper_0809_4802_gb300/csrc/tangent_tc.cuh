@@ -43,12 +43,17 @@ template <int ENG> constexpr int tc_bwords() { return ENG == TC_BF16 ? 2 : 4; }
 template <int ENG> constexpr int tc_bsteps() { return TC_KN / tc_kstep<ENG>() + TC_KD / tc_kstep<ENG>(); }
 
 // Per-warp operand and result storage of the tensor-core contractions.
+// The results (Out, 144 x 8) overwrite the left operand AN: tile mt's results go to floats
+// [128 mt, 128 mt + 128), which lie in AN tiles < mt (already consumed) or, for mt = 0, in tile 0
+// itself after its loads; the D results (rows 128..143) are stored last, into AN tiles 1 and 2.
 template <int ENG>
 struct TcArea {
   float AN[TC_ROWS_N][tc_sn<ENG>()];
   float AD[TC_ROWS_D][tc_sd<ENG>()];
-  float Out[TC_ROWS_N + TC_ROWS_D][8];
+  __device__ float (*out())[8] { return reinterpret_cast<float (*)[8]>(&AN[0][0]); }
+  __device__ const float (*out() const)[8] { return reinterpret_cast<const float (*)[8]>(&AN[0][0]); }
 };
+static_assert(TC_ROWS_N * (TC_KN + 4) >= 8 * (TC_ROWS_N + TC_ROWS_D), "results fit in AN");
 
 #if defined(__CUDACC__)
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
@@ -60,10 +65,17 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return r;
 }
-// x = hi + lo with hi, lo in TF32 (|x - hi - lo| <= 2^-22 |x|)
+// x = hi + lo with hi, lo in TF32 (|x - hi - lo| <= 2^-22 |x|): the constant operands
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
   hi = tf32_rna(x);
   lo = tf32_rna(x - __uint_as_float(hi));
+}
+// The per-element operands, with two instructions per value: hi = x with the 13 low mantissa bits
+// cleared (a TF32 value), lo = x - hi (exact in FP32, |lo| < 2^-10 |x|), whose own low bits the
+// TF32 multiply ignores: |x - hi - tf32(lo)| < 2^-20 |x|.
+__device__ __forceinline__ void tf32_split_fast(float x, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(x) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
 }
 __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -242,10 +254,10 @@ __device__ __forceinline__ void tc_tile(int lane, const float* __restrict__ Arow
     } else {
       const float* p = Arow + s * 8 + t;
       uint32_t ah[4], al[4];
-      tf32_split(p[g * LD], ah[0], al[0]);
-      tf32_split(p[(g + 8) * LD], ah[1], al[1]);
-      tf32_split(p[g * LD + 4], ah[2], al[2]);
-      tf32_split(p[(g + 8) * LD + 4], ah[3], al[3]);
+      tf32_split_fast(p[g * LD], ah[0], al[0]);
+      tf32_split_fast(p[(g + 8) * LD], ah[1], al[1]);
+      tf32_split_fast(p[g * LD + 4], ah[2], al[2]);
+      tf32_split_fast(p[(g + 8) * LD + 4], ah[3], al[3]);
       const uint4 b = *reinterpret_cast<const uint4*>(w);  // high b0, b1, low b0, b1
       mma_tf32(acc, ah, b.x, b.y);
       mma_tf32(cor, ah, b.z, b.w);
@@ -256,6 +268,7 @@ __device__ __forceinline__ void tc_tile(int lane, const float* __restrict__ Arow
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] += cor[j];
   }
+  __syncwarp();  // every lane's loads of this tile are done before the results overwrite it
   *reinterpret_cast<float2*>(&Out[g][2 * t]) = make_float2(acc[0], acc[1]);
   *reinterpret_cast<float2*>(&Out[g + 8][2 * t]) = make_float2(acc[2], acc[3]);
 }
@@ -264,10 +277,11 @@ __device__ __forceinline__ void tc_tile(int lane, const float* __restrict__ Arow
 template <int ENG>
 __device__ __forceinline__ void tc_contract(int lane, TcArea<ENG>& C, const uint32_t* __restrict__ bf) {
   constexpr int KS = tc_kstep<ENG>(), SN = TC_KN / KS, SD = TC_KD / KS;
+  float (*Out)[8] = C.out();
 #pragma unroll 1
   for (int mt = 0; mt < TC_ROWS_N / 16; ++mt)
-    tc_tile<ENG, tc_sn<ENG>()>(lane, &C.AN[16 * mt][0], SN, bf, 0, &C.Out[16 * mt]);
-  tc_tile<ENG, tc_sd<ENG>()>(lane, &C.AD[0][0], SD, bf, SN, &C.Out[TC_ROWS_N]);
+    tc_tile<ENG, tc_sn<ENG>()>(lane, &C.AN[16 * mt][0], SN, bf, 0, &Out[16 * mt]);
+  tc_tile<ENG, tc_sd<ENG>()>(lane, &C.AD[0][0], SD, bf, SN, &Out[TC_ROWS_N]);
 }
 
 // The lane's accumulators from the contraction results (the layout of LaneAcc: blocks (a0, b) and
@@ -276,8 +290,8 @@ __device__ __forceinline__ void tc_contract(int lane, TcArea<ENG>& C, const uint
 template <int ENG>
 __device__ __forceinline__ void tc_gather(int lane, const TcArea<ENG>& C, LaneAcc<float>& A) {
   const int a0 = lane >> 3, a1 = a0 + 4, b = lane & 7;
-  const float (*O)[8] = C.Out;
-  const float* OD = &C.Out[TC_ROWS_N][0];
+  const float (*O)[8] = C.out();
+  const float* OD = &C.out()[TC_ROWS_N][0];
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     const int a = p ? a1 : a0;
