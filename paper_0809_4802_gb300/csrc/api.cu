@@ -20,6 +20,8 @@ struct vms_ctx {
   int nq = 27;
   QpRow* d_qp = nullptr;     // nq rows (residual kernel)
   double* d_tab64 = nullptr; // 37 nq (tangent kernel, FP64)
+  double* d_tsw = nullptr;   // FP64 tangent weighted sums: weights (quad_order <= 3)
+  uint16_t* d_tsjobs = nullptr;  // and jobs
   float* d_tab32 = nullptr;  // 37 nq (tangent kernel, FP32)
   vms::TetMoments tet_mom{};  // reference moments of the tetrahedral rule (kernel parameter)
   Mesh mesh;
@@ -151,6 +153,8 @@ KParams kparams(const vms_ctx* c) {
   k.tab64 = c->d_tab64;
   k.tangent_warps = c->tune.tangent_warps;
   k.residual_threads = c->tune.residual_threads;
+  k.ts_w = c->d_tsw;
+  k.ts_jobs = c->d_tsjobs;
   return k;
 }
 
@@ -212,7 +216,16 @@ int upload_tables(vms_ctx* ctx) {
         t64[36 * nq + q] = r.w;
       }
   std::vector<float> t32(t64.begin(), t64.end());
-  dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32);
+  dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_tsw); dfree(ctx->d_tsjobs);
+  if (n1 <= 3) {
+    std::vector<double> tw;
+    std::vector<uint16_t> tj;
+    ts_tables(n1, x, tw, tj);
+    CK(cudaMalloc(&ctx->d_tsw, sizeof(double) * tw.size()));
+    CK(cudaMalloc(&ctx->d_tsjobs, sizeof(uint16_t) * tj.size()));
+    CK(cudaMemcpy(ctx->d_tsw, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tsjobs, tj.data(), sizeof(uint16_t) * tj.size(), cudaMemcpyHostToDevice));
+  }
   CK(cudaMalloc(&ctx->d_qp, sizeof(QpRow) * nq));
   CK(cudaMalloc(&ctx->d_tab64, sizeof(double) * 37 * nq));
   CK(cudaMalloc(&ctx->d_tab32, sizeof(float) * 37 * nq));
@@ -299,6 +312,7 @@ int vms_destroy(vms_ctx* ctx) {
   for (auto& e : ctx->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_scalar);
+  dfree(ctx->d_tsw); dfree(ctx->d_tsjobs);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->work.aux) { cudaStreamSynchronize(ctx->work.aux); cudaStreamDestroy(ctx->work.aux); }

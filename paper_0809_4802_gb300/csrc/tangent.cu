@@ -9,6 +9,7 @@
 #include "residual_table.cuh"
 #include "tangent_math.cuh"
 #include "tangent_tc.cuh"
+#include "tangent_ts.cuh"
 #include "vms_internal.h"
 
 namespace vms {
@@ -131,7 +132,7 @@ template <> struct NodeVec<float> { using type = float4; };
 template <typename T, bool ELEM_OUT, bool ATOMIC, int QCH = 32, int ENG = 0>
 __device__ __forceinline__ void tangent_element(
     int lane, int64_t it, int64_t e, WarpArea<T>& W, const RefTab<T>& tab, void* tcw,
-    const uint32_t* __restrict__ bfrag,
+    const void* __restrict__ ext0, const void* __restrict__ ext1,
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn,
     const T* __restrict__ beta, int nq, T nut, T tau, const double* __restrict__ nu_e,
     double visc_factor, const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
@@ -175,12 +176,22 @@ __device__ __forceinline__ void tangent_element(
       tan_phase2(lane, nq - q0 < QCH ? nq - q0 : QCH, W, nut_e, A);
       __syncwarp();
     }
+  } else if constexpr (ENG == TS_ENGINE) {
+    // FP64 weighted point sums (nq <= 27, checked on the host): ext0 = weight table (global),
+    // ext1 = job table (shared)
+    TsArea& C = *reinterpret_cast<TsArea*>(tcw);
+    ts_phase1(lane, nq, W, C, tab, nut_e, tau, A);
+    __syncwarp();
+    ts_sums(lane, nq, C, reinterpret_cast<const double*>(ext0), reinterpret_cast<const uint16_t*>(ext1));
+    __syncwarp();
+    ts_gather(lane, C, A);
+    __syncwarp();
   } else {
-    // tensor-core contractions (FP32 only; nq <= 32, checked on the host)
+    // tensor-core contractions (FP32 only; nq <= 32, checked on the host); ext0 = B fragments
     TcArea<ENG>& C = *reinterpret_cast<TcArea<ENG>*>(tcw);
     tc_phase1<ENG>(lane, nq, W, C, tab, nut_e, tau, A);
     __syncwarp();
-    tc_contract<ENG>(lane, C, bfrag);
+    tc_contract<ENG>(lane, C, reinterpret_cast<const uint32_t*>(ext0));
     __syncwarp();
     tc_gather<ENG>(lane, C, A);
     __syncwarp();
@@ -284,18 +295,21 @@ __device__ __forceinline__ void tangent_element(
 template <typename T, int ENG>
 __host__ __device__ inline size_t tan_bfrag_bytes() {
   if constexpr (ENG == 0) return 0;
+  else if constexpr (ENG == TS_ENGINE) return ((size_t)TS_JOBS * sizeof(uint16_t) + 15) & ~size_t(15);
   else return (size_t)tc_bsteps<ENG>() * 32 * tc_bwords<ENG>() * 4;
 }
 template <typename T, int ENG>
 __host__ __device__ inline size_t tan_warp_total(int nq) {
   if constexpr (ENG == 0) return tan_warp_bytes<T>(nq);
+  else if constexpr (ENG == TS_ENGINE) return tan_warp_bytes<T, 0>(nq) + ts_area_bytes(nq);
   else return tan_warp_bytes<T, 0>(nq) + ((sizeof(TcArea<ENG>) + 15) & ~size_t(15));
 }
 
 constexpr int TC_WARPS = 2;
+constexpr int TS_WARPS = 4;  // FP64 weighted sums: ~24 KB of point fields and sums per warp
 
 template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS, int ENG = 0>
-__global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : 4) tangent_kernel(
+__global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : (ENG == TS_ENGINE ? 2 : 4)) tangent_kernel(
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
     int nq, T nut, T tau, const double* __restrict__ nu_e, double visc_factor,
     const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
@@ -305,7 +319,8 @@ __global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : 4) tangent_kernel(
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
     T* __restrict__ recKcf, double* __restrict__ recKinv, double* __restrict__ oS,
     double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
-    double* __restrict__ oKff, unsigned int* __restrict__ flags) {
+    double* __restrict__ oKff, unsigned int* __restrict__ flags, const double* __restrict__ tsw,
+    const uint16_t* __restrict__ tsjobs) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* st = reinterpret_cast<T*>(smem);
   for (int i = threadIdx.x; i < 37 * nq; i += blockDim.x) st[i] = gtab[i];
@@ -317,7 +332,16 @@ __global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : 4) tangent_kernel(
                          (size_t)warp * tan_warp_total<T, ENG>(nq);
   WarpArea<T>& W = *reinterpret_cast<WarpArea<T>*>(wbase);
   void* tcw = nullptr;
-  if constexpr (ENG != 0) {
+  const void* ext0 = bfrag;
+  const void* ext1 = nullptr;
+  if constexpr (ENG == TS_ENGINE) {
+    uint16_t* jobs = reinterpret_cast<uint16_t*>(bfrag);
+    for (int i = threadIdx.x; i < TS_JOBS; i += blockDim.x) jobs[i] = tsjobs[i];
+    tcw = wbase + tan_warp_bytes<T, 0>(nq);
+    ext0 = tsw;
+    ext1 = jobs;
+    __syncthreads();
+  } else if constexpr (ENG != 0) {
     tc_build_b<ENG>(tab.N, tab.dN, nq, bfrag);
     tcw = wbase + tan_warp_bytes<T, 0>(nq);
     TcArea<ENG>& C = *reinterpret_cast<TcArea<ENG>*>(tcw);
@@ -327,7 +351,7 @@ __global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : 4) tangent_kernel(
   const int64_t total = (int64_t)gridDim.x * WARPS;
   for (int64_t it = (int64_t)blockIdx.x * WARPS + warp; it < count; it += total) {
     const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
-    tangent_element<T, ELEM_OUT, ATOMIC, 32, ENG>(lane, it, e, W, tab, tcw, bfrag, u, conn, beta, nq, nut, tau, nu_e,
+    tangent_element<T, ELEM_OUT, ATOMIC, 32, ENG>(lane, it, e, W, tab, tcw, ext0, ext1, u, conn, beta, nq, nut, tau, nu_e,
                                          visc_factor, xyz64, u64, beta64, tab64, blk, rowlen,
                                          dir_mask, values, recX, recKcf, recKinv, oS, oKcc, oKcf,
                                          oKfc, oKff, flags);
@@ -404,7 +428,7 @@ __global__ void __launch_bounds__(FUSED_WARPS * 32, 1) fused_assembly_kernel(
     if (base >= (unsigned long long)n_elems) break;
     const int64_t end = (int64_t)base + FUSED_TCLAIM < n_elems ? (int64_t)base + FUSED_TCLAIM : n_elems;
     for (int64_t e = (int64_t)base; e < end; ++e)
-      tangent_element<float, false, true, FUSED_QCH>(lane, e, e, W, tab, nullptr, nullptr, u32, conn, beta32, nq, nut, tau,
+      tangent_element<float, false, true, FUSED_QCH>(lane, e, e, W, tab, nullptr, nullptr, nullptr, u32, conn, beta32, nq, nut, tau,
                                           kp.nu_e, kp.visc_factor, xyz, u64, beta64, kp.tab64, blk,
                                           rowlen, dir_mask, values, recX, recKcf, recKinv, nullptr,
                                           nullptr, nullptr, nullptr, nullptr, flags);
@@ -514,7 +538,8 @@ static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const K
       u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, s.u,
       s.beta, kp.tab64, first, count, elem_list, m.blk,
       m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
-      reinterpret_cast<T*>(o.recKcf), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags);
+      reinterpret_cast<T*>(o.recKcf), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags, kp.ts_w,
+      kp.ts_jobs);
 }
 
 // Warps per block: the default, or the tuned count when it is one of the compiled choices
@@ -530,6 +555,11 @@ static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const K
     if (engine == TC_TF32X3)
       return launch_w<T, ELEM_OUT, ATOMIC, TC_WARPS, TC_TF32X3>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
   }
+  if constexpr (sizeof(T) == 8) {
+    // FP64: weighted point sums for the 8- and 27-point rules (the tables exist), TS_WARPS per CTA
+    if (kp.ts_w && kp.nq <= 27)
+      return launch_w<T, ELEM_OUT, ATOMIC, TS_WARPS, TS_ENGINE>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+  }
   constexpr int D = tan_warps<T>();
   const int w = ELEM_OUT ? D : (kp.tangent_warps ? kp.tangent_warps : D);
   if constexpr (!ELEM_OUT) {
@@ -537,6 +567,59 @@ static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const K
     if (w == 2 * D) return launch_w<T, false, ATOMIC, 2 * D, 0>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
   }
   launch_w<T, ELEM_OUT, ATOMIC, D, 0>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
+}
+
+void ts_tables(int n1, const double* x, std::vector<double>& w, std::vector<uint16_t>& jobs) {
+  const int nq = n1 * n1 * n1;
+  auto phi = [](int b, double t) { return b ? 0.5 * (1.0 + t) : 0.5 * (1.0 - t); };
+  auto psi = [&](int sm, double t) { return sm == 0 ? phi(0, t) * phi(0, t) : sm == 1 ? phi(0, t) * phi(1, t) : phi(1, t) * phi(1, t); };
+  auto bit = [](int a, int d) { return d == 0 ? ((a + 1) >> 1) & 1 : (d == 1 ? (a >> 1) & 1 : (a >> 2) & 1); };
+  w.assign((size_t)TS_WEIGHTS * nq, 0.0);
+  auto W = [&](int k, int q) -> double& { return w[(size_t)q * TS_WEIGHTS + k]; };  // point-major
+  for (int q = 0; q < nq; ++q) {
+    const double xi[3] = {x[q % n1], x[(q / n1) % n1], x[q / (n1 * n1)]};
+    for (int t = 0; t < 27; ++t)
+      W(TW_PSI3 + t, q) = psi(t % 3, xi[0]) * psi((t / 3) % 3, xi[1]) * psi(t / 9, xi[2]);
+    for (int al = 0; al < 3; ++al) {
+      const int d1 = ts_d1(al), d2 = ts_d2(al);
+      for (int ty = 0; ty < 18; ++ty) {
+        const int xb = ty & 1, ps = ty >> 1;
+        W(TW_PHIPSI + 18 * al + ty, q) = phi(xb, xi[al]) * psi(ps % 3, xi[d1]) * psi(ps / 3, xi[d2]);
+      }
+      for (int ty = 0; ty < 9; ++ty)
+        W(TW_PSI2 + 9 * al + ty, q) = psi(ty % 3, xi[d1]) * psi(ty / 3, xi[d2]);
+      for (int ty = 0; ty < 4; ++ty)
+        W(TW_PHI2 + 4 * al + ty, q) = phi(ty & 1, xi[d1]) * phi(ty >> 1, xi[d2]);
+    }
+    for (int pp = 0; pp < 3; ++pp) {
+      const int al = pp == 2 ? 1 : 0, be = pp == 0 ? 1 : 2, ga = 2 - pp;
+      for (int ty = 0; ty < 12; ++ty)
+        W(TW_PHI2PSI + 12 * pp + ty, q) = phi(ty & 1, xi[al]) * phi((ty >> 1) & 1, xi[be]) * psi(ty >> 2, xi[ga]);
+    }
+    for (int a = 0; a < 8; ++a)
+      W(TW_N + a, q) = phi(bit(a, 0), xi[0]) * phi(bit(a, 1), xi[1]) * phi(bit(a, 2), xi[2]);
+  }
+  jobs.assign(TS_JOBS, 0);
+  auto job = [&](int j, int field, int weight) { jobs[j] = (uint16_t)(field | (weight << 8)); };
+  for (int ik = 0; ik < 9; ++ik)
+    for (int t = 0; t < 27; ++t) job(TJ_L + 27 * ik + t, TF_L + ik, TW_PSI3 + t);
+  for (int al = 0; al < 3; ++al) {
+    for (int fl = 0; fl < 4; ++fl)
+      for (int ty = 0; ty < 18; ++ty)
+        job(TJ_VP + 72 * al + 18 * fl + ty, fl == 0 ? TF_ADV + al : TF_VP + 3 * al + fl - 1, TW_PHIPSI + 18 * al + ty);
+    for (int ty = 0; ty < 9; ++ty) job(TJ_DD + 9 * al + ty, TF_G + al, TW_PSI2 + 9 * al + ty);
+    for (int ty = 0; ty < 4; ++ty) {
+      job(TJ_CFD + 4 * al + ty, TF_ZCF + al, TW_PHI2 + 4 * al + ty);
+      job(TJ_FCD + 4 * al + ty, TF_ZFC + al, TW_PHI2 + 4 * al + ty);
+    }
+  }
+  for (int pp = 0; pp < 3; ++pp)
+    for (int ty = 0; ty < 12; ++ty) job(TJ_OD + 12 * pp + ty, TF_G + 3 + pp, TW_PHI2PSI + 12 * pp + ty);
+  for (int cf = 0; cf < 12; ++cf)
+    for (int a = 0; a < 8; ++a) {
+      job(TJ_CFN + 8 * cf + a, TF_YCF + cf, TW_N + a);
+      job(TJ_FCN + 8 * cf + a, TF_YFC + cf, TW_N + a);
+    }
 }
 
 int tangent_warp_choice(bool fp32, int k) {

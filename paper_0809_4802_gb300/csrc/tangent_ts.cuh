@@ -1,0 +1,242 @@
+// FP64 tangent blocks by weighted point sums (Section 4.2, Eq. NewtonUpdate2).
+//
+// Every entry of the coarse blocks and of the coarse-fine couplings is a sum over the quadrature
+// points of a per-element field times a product of one-dimensional factors of the reference
+// basis. With phi_0 = (1 - x)/2, phi_1 = (1 + x)/2 (so that N_a = prod_d phi_{a_d}(xi_d) for the
+// corner bits a_d of node a), psi_s = phi_x phi_y for x + y = s, and dphi_x/dx = +-1/2:
+//   N_a N_b                = prod_d psi_{a_d + b_d}                      (27 weights)
+//   N_a dN_b/dxi_al        = +-1/2 phi_{a_al}(xi_al) prod_{d != al} psi   (18 per al)
+//   dN_a/dxi_al dN_b/dxi_al = +-1/4 prod_{d != al} psi                    (9 per al)
+//   dN_a/dxi_al dN_b/dxi_be = +-1/4 phi(xi_al) phi(xi_be) psi(xi_ga)      (12 per pair al < be)
+//   N_a, dN_a/dxi_al       = prod phi, +-1/2 prod_{d != al} phi            (8, 4 per al)
+// so only 164 distinct weights exist. Per element the warp forms 738 sums
+//   T_j = sum_q W[w_j][q] F[f_j][q]
+// over 57 per-point fields F (omega L_ik + tau omega delta_ik; omega (J^-1 v)_al; omega J^-1[al][i];
+// nut omega (J^-1 J^-T)_albe; the K_cf / K_fc coefficients Ycf, Yfc of tangent_math.cuh;
+// nut omega (J^-1 d)_al and (J^-1 (omega b v + nut omega d))_al), one sum per lane per round, and
+// every block entry is then a signed combination of a few T_j: about 20 k FMA per element instead
+// of the ~51 k of the pair loop. Used for the 8- and 27-point rules in FP64 mode.
+#pragma once
+
+#include "tangent_math.cuh"
+
+namespace vms {
+
+constexpr int TS_FIELDS = 57, TS_WEIGHTS = 164, TS_JOBS = 738;
+constexpr int TS_ENGINE = 3;
+// field slots
+constexpr int TF_L = 0, TF_ADV = 9, TF_VP = 12, TF_G = 21, TF_YCF = 27, TF_YFC = 39, TF_ZCF = 51,
+              TF_ZFC = 54;
+// job ranges
+constexpr int TJ_L = 0, TJ_VP = 243, TJ_DD = 459, TJ_OD = 486, TJ_CFN = 522, TJ_FCN = 618,
+              TJ_CFD = 714, TJ_FCD = 726;
+// weight ranges
+constexpr int TW_PSI3 = 0, TW_PHIPSI = 27, TW_PSI2 = 81, TW_PHI2PSI = 108, TW_N = 144, TW_PHI2 = 152;
+
+// point-field stride (odd: conflict-free column reads across lanes)
+__host__ __device__ constexpr int ts_ld(int nq) { return nq | 1; }
+
+// Per-warp storage: the point fields and the 738 sums.
+struct TsArea {
+  double T[TS_JOBS];
+  double F[1];  // TS_FIELDS x ts_ld(nq), sized at launch
+};
+__host__ __device__ inline size_t ts_area_bytes(int nq) {
+  return (offsetof(TsArea, F) + sizeof(double) * TS_FIELDS * ts_ld(nq) + 15) & ~size_t(15);
+}
+
+// the two directions other than al, in increasing order
+__host__ __device__ inline int ts_d1(int al) { return al == 0 ? 1 : 0; }
+__host__ __device__ inline int ts_d2(int al) { return al == 2 ? 1 : 2; }
+
+#if defined(__CUDACC__)
+// Lane q = quadrature point (< nq): geometry, fields at q into F[.][q], and the lane's K_ff part.
+__device__ __forceinline__ void ts_phase1(int lane, int nq, WarpArea<double>& W, TsArea& C,
+                                          const RefTab<double>& tab, double nut, double tau,
+                                          LaneAcc<double>& A) {
+  const int q = lane;
+  if (q >= nq) return;
+  const int ld = ts_ld(nq);
+  double* F = C.F;
+  const double* dN = tab.dN + 24 * q;
+  const double* N = tab.N + 8 * q;
+  const double bq = tab.b[q];
+  const double db[3] = {tab.db[3 * q], tab.db[3 * q + 1], tab.db[3 * q + 2]};
+  double J[3][3], G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) {
+      double s = 0.0, g = 0.0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        s += W.X[a][i] * dN[3 * a + al];
+        g += W.V[a][i] * dN[3 * a + al];
+      }
+      J[i][al] = s;
+      G[i][al] = g;  // reference gradient of the coarse velocity
+    }
+  double cof[3][3];
+  double det = cofactor3(J, cof);
+  if (!(det > 0.0)) { W.flag = 1u; det = 1.0; }
+  const double rdet = 1.0 / det;
+  double Ji[3][3];  // (J^-1)[al][j] = cof[j][al] / det
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Ji[al][j] = cof[j][al] * rdet;
+  const double om = tab.w[q] * det;
+  double d[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) d[j] = db[0] * Ji[0][j] + db[1] * Ji[1][j] + db[2] * Ji[2][j];
+  double v[3], L[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) s += N[a] * W.V[a][i];
+    v[i] = s + bq * W.beta[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      L[i][k] = G[i][0] * Ji[0][k] + G[i][1] * Ji[1][k] + G[i][2] * Ji[2][k] + W.beta[i] * d[k];
+  }
+  const double cd = v[0] * d[0] + v[1] * d[1] + v[2] * d[2];
+  const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double omb = om * bq, nom = nut * om, tom = tau * om;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F[(TF_L + 3 * i + k) * ld + q] = om * L[i][k] + (i == k ? tom : 0.0);
+  const double Wv[3] = {omb * v[0] + nom * d[0], omb * v[1] + nom * d[1], omb * v[2] + nom * d[2]};
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    F[(TF_ADV + al) * ld + q] = om * (Ji[al][0] * v[0] + Ji[al][1] * v[1] + Ji[al][2] * v[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[(TF_VP + 3 * al + i) * ld + q] = om * Ji[al][i];
+    F[(TF_ZCF + al) * ld + q] = nom * (Ji[al][0] * d[0] + Ji[al][1] * d[1] + Ji[al][2] * d[2]);
+    F[(TF_ZFC + al) * ld + q] = Ji[al][0] * Wv[0] + Ji[al][1] * Wv[1] + Ji[al][2] * Wv[2];
+  }
+  // nut omega (J^-1 J^-T): diagonal 00, 11, 22, then 01, 02, 12
+  const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int m = 0; m < 6; ++m)
+    F[(TF_G + m) * ld + q] = nom * (Ji[pa[m]][0] * Ji[pb[m]][0] + Ji[pa[m]][1] * Ji[pb[m]][1] +
+                                    Ji[pa[m]][2] * Ji[pb[m]][2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      F[(TF_YCF + 3 * c + k) * ld + q] = omb * L[c][k] + (c == k ? om * cd : 0.0);
+      F[(TF_YFC + 3 * c + k) * ld + q] = omb * (L[k][c] + (c == k ? tau : 0.0));
+    }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    F[(TF_YCF + 9 + k) * ld + q] = -om * d[k];
+    F[(TF_YFC + 9 + k) * ld + q] = -om * d[k];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      A.kff[3 * i + k] += om * (bq * (bq * L[i][k] + (i == k ? cd : 0.0)) + (i == k ? nut * dd : 0.0));
+}
+
+// The 738 sums: lane `lane` takes jobs lane, lane + 32, ...; job j reads field jobs[j] & 255 and
+// weight jobs[j] >> 8. The weight table Wt (global, read through L1) is point-major, nq rows of
+// TS_WEIGHTS, so that the lanes of a round, whose jobs mostly use consecutive weights, read
+// consecutive words.
+__device__ __forceinline__ void ts_sums(int lane, int nq, TsArea& C, const double* __restrict__ Wt,
+                                        const uint16_t* __restrict__ jobs) {
+  const int ld = ts_ld(nq);
+  for (int j = lane; j < TS_JOBS; j += 32) {
+    const uint16_t jb = jobs[j];
+    const double* f = C.F + (jb & 255) * ld;
+    const double* w = Wt + (jb >> 8);
+    double s0 = 0.0, s1 = 0.0;
+    int q = 0;
+    for (; q + 1 < nq; q += 2) {
+      s0 += __ldg(w + q * TS_WEIGHTS) * f[q];
+      s1 += __ldg(w + (q + 1) * TS_WEIGHTS) * f[q + 1];
+    }
+    if (q < nq) s0 += __ldg(w + q * TS_WEIGHTS) * f[q];
+    C.T[j] = s0 + s1;
+  }
+}
+
+__device__ __forceinline__ int ts_bit(int a, int d) {
+  // corner bits of the local node order (-,-,-) (+,-,-) (+,+,-) (-,+,-) (-,-,+) (+,-,+) (+,+,+) (-,+,+)
+  return d == 0 ? ((a + 1) >> 1) & 1 : (d == 1 ? (a >> 1) & 1 : (a >> 2) & 1);
+}
+__device__ __forceinline__ double ts_sgn(int bit) { return bit ? 1.0 : -1.0; }
+
+// The lane's accumulators (blocks (a0, b), (a1, b) of K_cc; row lane of K_cf; column lane of K_fc)
+// from the sums.
+__device__ __forceinline__ void ts_gather(int lane, const TsArea& C, LaneAcc<double>& A) {
+  const double* T = C.T;
+  const int a0 = lane >> 3, b = lane & 7;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int a = a0 + 4 * p;
+    int ab[3], bb[3], s[3];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      ab[dd] = ts_bit(a, dd);
+      bb[dd] = ts_bit(b, dd);
+      s[dd] = ab[dd] + bb[dd];
+    }
+    const int tL = s[0] + 3 * s[1] + 9 * s[2];
+    double diag = 0.0, vp[3] = {0.0, 0.0, 0.0}, pv[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int al = 0; al < 3; ++al) {
+      const int d1 = ts_d1(al), d2 = ts_d2(al);
+      const int psi = s[d1] + 3 * s[d2];
+      const int base = TJ_VP + 72 * al;
+      diag += 0.5 * ts_sgn(bb[al]) * T[base + ab[al] + 2 * psi];                          // advection
+      diag += (ab[al] == bb[al] ? 0.25 : -0.25) * T[TJ_DD + 9 * al + psi];                 // diffusion
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        vp[i] -= 0.5 * ts_sgn(ab[al]) * T[base + 18 * (1 + i) + bb[al] + 2 * psi];        // K_vp
+        pv[i] -= 0.5 * ts_sgn(bb[al]) * T[base + 18 * (1 + i) + ab[al] + 2 * psi];        // K_pv
+      }
+    }
+    // off-diagonal diffusion: pairs (al, be) = (0,1), (0,2), (1,2), third direction ga
+#pragma unroll
+    for (int pp = 0; pp < 3; ++pp) {
+      const int al = pp == 2 ? 1 : 0, be = pp == 0 ? 1 : 2, ga = 2 - pp;
+      const double* Tp = T + TJ_OD + 12 * pp;
+      diag += 0.25 * ts_sgn(ab[al]) * ts_sgn(bb[be]) * Tp[bb[al] + 2 * ab[be] + 4 * s[ga]];
+      diag += 0.25 * ts_sgn(ab[be]) * ts_sgn(bb[al]) * Tp[ab[al] + 2 * bb[be] + 4 * s[ga]];
+    }
+    double k[16];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) k[4 * i + kk] = T[TJ_L + 27 * (3 * i + kk) + tL] + (i == kk ? diag : 0.0);
+      k[4 * i + 3] = vp[i];
+      k[12 + i] = pv[i];
+    }
+    k[15] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (p) A.K[j].y = k[j];
+      else A.K[j].x = k[j];
+    }
+  }
+  const int at = lane >> 2, ct = lane & 3;
+  double dcf = 0.0, dfc = 0.0;
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    const int u = ts_bit(at, ts_d1(al)), w = ts_bit(at, ts_d2(al));
+    const double sg = 0.5 * ts_sgn(ts_bit(at, al));
+    dcf += sg * T[TJ_CFD + 4 * al + u + 2 * w];
+    dfc += sg * T[TJ_FCD + 4 * al + u + 2 * w];
+  }
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    A.kcf[kk] = T[TJ_CFN + 8 * (3 * ct + kk) + at] + (ct == kk ? dcf : 0.0);
+    A.kfc[kk] = T[TJ_FCN + 8 * (3 * ct + kk) + at] + (ct == kk ? dfc : 0.0);
+  }
+}
+#endif
+
+}  // namespace vms

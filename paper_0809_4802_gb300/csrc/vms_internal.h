@@ -44,6 +44,8 @@ struct KParams {
   const double* tab64;   // FP64 reference table of the tangent kernel (37 nq), for FP64 K_ff
   int tangent_warps;     // warps per tangent block (0: default)
   int residual_threads;  // threads per residual block (0: default)
+  const double* ts_w = nullptr;      // FP64 tangent: weight table (nq x 164, point-major), nq <= 27
+  const uint16_t* ts_jobs = nullptr; // FP64 tangent: 738 jobs (field | weight << 8)
 };
 
 // The once-per-mesh pattern (host side, built by pattern.cpp).
@@ -59,6 +61,10 @@ struct HostPattern {
   std::vector<uint32_t> dir_mask; // per element: bit 4a+c set if that coarse dof is constrained
   int n_colours = 0;
 };
+
+// Weight table (nq x 164 doubles, point-major) and job table (738 entries: field | weight << 8)
+// of the FP64 tangent's weighted point sums for the n1^3-point Gauss rule with points x (n1 <= 3).
+void ts_tables(int n1, const double* x, std::vector<double>& w, std::vector<uint16_t>& jobs);
 
 // Builds the CSR pattern, block map, colouring and Dirichlet masks. Returns "" or an error text.
 std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn, int64_t n_dir,
