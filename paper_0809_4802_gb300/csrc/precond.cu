@@ -515,41 +515,15 @@ __global__ void __launch_bounds__(W * 32)
         cp_commit();
       };
       for (int r = 0; r < ILU_PF - 1; ++r) issue(r);
-      // FP32: the lane's dependency of the next row in an earlier chunk is loaded while the
-      // current row is solved (one L2 round trip hidden per row); it is used if it already
-      // carries this sweep's epoch, and polled as before otherwise
-      int64_t pf_k = -1;
-      unsigned long long pf[4] = {0ull, 0ull, 0ull, 0ull};
       for (int r = 0; r < len; ++r) {
         const int64_t i = LOWER ? r_lo + r : r_hi - 1 - r;
         issue(r + ILU_PF - 1);
-        // this thread's copies of row r (FP32: and of row r + 1, for its prefetch) have landed
-        if constexpr (sizeof(T) == 4) cp_wait<ILU_PF - 2>();
-        else cp_wait<ILU_PF - 1>();
-        __syncwarp();  // ... and every lane's (U_ii^-1 rows are read across lanes)
+        cp_wait<ILU_PF - 1>();  // this thread's copies of row r have landed
+        __syncwarp();           // ... and every lane's (U_ii^-1 rows are read across lanes)
         const SweepSlot<T>& sl = ring[r % ILU_PF];
         int32_t rp[4], dp;
         row_offsets(r, rp, dp);
         const int deg = (rp[1] - rp[0]) >> 2;
-        int64_t nk = -1;
-        unsigned long long nf[4] = {0ull, 0ull, 0ull, 0ull};
-        if constexpr (sizeof(T) == 4) {
-          if (r + 1 < len) {
-            int32_t rp1[4], dp1;
-            row_offsets(r + 1, rp1, dp1);
-            const int deg1 = (rp1[1] - rp1[0]) >> 2;
-            const int kk1 = LOWER ? lane : dp1 + 1 + lane;
-            if (LOWER ? kk1 < dp1 : kk1 < deg1) {
-              const int64_t k1 = ring[(r + 1) % ILU_PF].col[lane] >> 2;
-              if (!(k1 >= a && k1 < b)) {
-                const unsigned long long* p1 = reinterpret_cast<const unsigned long long*>(pub) + 4 * k1;
-                ld_relaxed2(p1, nf[0], nf[1]);
-                ld_relaxed2(p1 + 2, nf[2], nf[3]);
-                nk = k1;
-              }
-            }
-          }
-        }
         if (split_rows(dp, deg)) {
           if (!split_row<T, LOWER>(sl, r, i, dp, deg, lane, o_rhs, sx, a, b, pub, out, n0, ep, err, lim))
             break;  // an error was recorded; the CTA stops after this chunk
@@ -575,12 +549,7 @@ __global__ void __launch_bounds__(W * 32)
             const int64_t sk = LOWER ? k - a : b - 1 - k;
             ok = wait_shared<T>(sx + 4 * sk, xk, err, lim);
           } else if constexpr (sizeof(T) == 4) {
-            if (k == pf_k && (uint32_t)(pf[0] >> 32) == ep && (uint32_t)(pf[1] >> 32) == ep &&
-                (uint32_t)(pf[2] >> 32) == ep && (uint32_t)(pf[3] >> 32) == ep) {
-              for (int m = 0; m < 4; ++m) xk[m] = __uint_as_float((uint32_t)pf[m]);
-            } else {
-              ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err, lim);
-            }
+            ok = wait_packed(reinterpret_cast<const unsigned long long*>(pub) + 4 * k, ep, xk, err, lim);
           } else {
             ok = wait_unset(reinterpret_cast<const double*>(pub) + 4 * k, xk, err, lim);
           }
@@ -588,8 +557,6 @@ __global__ void __launch_bounds__(W * 32)
             for (int rr = 0; rr < 4; ++rr)
               for (int m = 0; m < 4; ++m) acc[rr] += sl.f[lane][4 * rr + m] * xk[m];
         }
-        pf_k = nk;
-        for (int m = 0; m < 4; ++m) pf[m] = nf[m];
         if (!__all_sync(FULL, ok)) break;  // an error was recorded; the CTA stops after this chunk
         const T sum = warp_sum4_scatter(acc, lane);
         const T w = writer ? rhs - sum : T(0);
