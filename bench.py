@@ -592,8 +592,12 @@ def ours(args):
     roofline = dict(next(r for r in entries if r["kernel"] == dom_name))
     roofline["kernels"] = entries
     roofline["kernel_ms"] = {k: round(v, 4) for k, v in kern.items()}
-    roofline["concurrent"] = ("residual (context stream) and tangent (second stream) overlap in the "
-                              "step; each time is that kernel's own launch-to-completion in the step")
+    roofline["concurrent"] = (
+        "one persistent kernel runs the residual (FP64) and the tangent (FP32) warps side by side; "
+        "its time is its own launch-to-completion in the step" if "fused" in kern else
+        "one kernel per element pass" if tet else
+        "residual (context stream) and tangent (second stream) overlap in the step; each time is "
+        "that kernel's own launch-to-completion in the step")
 
     # ---- end to end through the C-ABI: host state in, assembled system (values + rhs) out ----
     u_host = torch.from_numpy(np.ascontiguousarray(wl.u)).pin_memory()

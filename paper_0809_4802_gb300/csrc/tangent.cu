@@ -574,7 +574,9 @@ void ts_tables(int n1, const double* x, std::vector<double>& w, std::vector<uint
   auto phi = [](int b, double t) { return b ? 0.5 * (1.0 + t) : 0.5 * (1.0 - t); };
   auto psi = [&](int sm, double t) { return sm == 0 ? phi(0, t) * phi(0, t) : sm == 1 ? phi(0, t) * phi(1, t) : phi(1, t) * phi(1, t); };
   auto bit = [](int a, int d) { return d == 0 ? ((a + 1) >> 1) & 1 : (d == 1 ? (a >> 1) & 1 : (a >> 2) & 1); };
-  w.assign((size_t)TS_WEIGHTS * nq, 0.0);
+  w.assign((size_t)TS_WEIGHTS * nq + 12, 0.0);
+  for (int sm = 0; sm < 3; ++sm)
+    for (int i = 0; i < n1; ++i) w[(size_t)TS_WEIGHTS * nq + 4 * sm + i] = psi(sm, x[i]);
   auto W = [&](int k, int q) -> double& { return w[(size_t)q * TS_WEIGHTS + k]; };  // point-major
   for (int q = 0; q < nq; ++q) {
     const double xi[3] = {x[q % n1], x[(q / n1) % n1], x[q / (n1 * n1)]};

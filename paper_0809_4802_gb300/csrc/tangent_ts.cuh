@@ -145,10 +145,45 @@ __device__ __forceinline__ void ts_phase1(int lane, int nq, WarpArea<double>& W,
 // weight jobs[j] >> 8. The weight table Wt (global, read through L1) is point-major, nq rows of
 // TS_WEIGHTS, so that the lanes of a round, whose jobs mostly use consecutive weights, read
 // consecutive words.
+//
+// The 243 sums of the N_a N_b family (9 fields x 27 weights prod_d psi_{s_d}(xi_d)) are formed by
+// sum factorisation instead, one direction at a time (3 x 243 x n1 FMA for n1 points per
+// direction instead of 243 x n1^3), the intermediate sums parked in T[243..728] before the other
+// jobs overwrite them. psi[s][i] = psi_s(x_i) follows the weight table (TS_WEIGHTS * nq + 4 s + i).
 __device__ __forceinline__ void ts_sums(int lane, int nq, TsArea& C, const double* __restrict__ Wt,
                                         const uint16_t* __restrict__ jobs) {
   const int ld = ts_ld(nq);
-  for (int j = lane; j < TS_JOBS; j += 32) {
+  const int n1 = nq == 8 ? 2 : 3;
+  const double* psi = Wt + TS_WEIGHTS * nq;
+  {
+    double* s1 = C.T + TJ_VP;          // [f][s0][i1 + n1 i2]
+    double* s2 = C.T + TJ_VP + 243;    // [f][s0][s1][i2]
+    const int n_1 = 27 * n1 * n1, n_2 = 81 * n1;
+    for (int o = lane; o < n_1; o += 32) {
+      const int i12 = o % (n1 * n1), fs = o / (n1 * n1), f = fs / 3, s0 = fs % 3;
+      const double* fr = C.F + (TF_L + f) * ld + n1 * i12;
+      double acc = 0.0;
+      for (int i0 = 0; i0 < n1; ++i0) acc += __ldg(psi + 4 * s0 + i0) * fr[i0];
+      s1[o] = acc;
+    }
+    __syncwarp();
+    for (int o = lane; o < n_2; o += 32) {
+      const int i2 = o % n1, fss = o / n1, s1i = fss % 3, fs0 = fss / 3;
+      double acc = 0.0;
+      for (int i1 = 0; i1 < n1; ++i1) acc += __ldg(psi + 4 * s1i + i1) * s1[fs0 * n1 * n1 + i1 + n1 * i2];
+      s2[o] = acc;
+    }
+    __syncwarp();
+    for (int o = lane; o < 243; o += 32) {
+      const int f = o / 27, t = o % 27, s0 = t % 3, s1i = (t / 3) % 3, s2i = t / 9;
+      const double* r = s2 + ((f * 3 + s0) * 3 + s1i) * n1;
+      double acc = 0.0;
+      for (int i2 = 0; i2 < n1; ++i2) acc += __ldg(psi + 4 * s2i + i2) * r[i2];
+      C.T[TJ_L + o] = acc;
+    }
+    __syncwarp();
+  }
+  for (int j = TJ_VP + lane; j < TS_JOBS; j += 32) {
     const uint16_t jb = jobs[j];
     const double* f = C.F + (jb & 255) * ld;
     const double* w = Wt + (jb >> 8);

@@ -62,8 +62,9 @@ struct HostPattern {
   int n_colours = 0;
 };
 
-// Weight table (nq x 164 doubles, point-major) and job table (738 entries: field | weight << 8)
-// of the FP64 tangent's weighted point sums for the n1^3-point Gauss rule with points x (n1 <= 3).
+// Weight table (nq x 164 doubles, point-major, then psi_s(x_i) at 164 nq + 4 s + i) and job
+// table (738 entries: field | weight << 8) of the FP64 tangent's weighted point sums for the
+// n1^3-point Gauss rule with points x (n1 <= 3).
 void ts_tables(int n1, const double* x, std::vector<double>& w, std::vector<uint16_t>& jobs);
 
 // Builds the CSR pattern, block map, colouring and Dirichlet masks. Returns "" or an error text.
