@@ -20,8 +20,8 @@ struct vms_ctx {
   int nq = 27;
   QpRow* d_qp = nullptr;     // nq rows (residual kernel)
   double* d_tab64 = nullptr; // 37 nq (tangent kernel, FP64)
-  double* d_tsw = nullptr;   // FP64 tangent weighted sums: weights (quad_order <= 3)
-  uint16_t* d_tsjobs = nullptr;  // and jobs
+  double* d_tsbasis = nullptr;   // FP64 tangent factorised sums: basis rows (quad_order 2, 3)
+  uint32_t* d_tsplan = nullptr;  // and their plan
   float* d_tab32 = nullptr;  // 37 nq (tangent kernel, FP32)
   vms::TetMoments tet_mom{};  // reference moments of the tetrahedral rule (kernel parameter)
   Mesh mesh;
@@ -153,8 +153,8 @@ KParams kparams(const vms_ctx* c) {
   k.tab64 = c->d_tab64;
   k.tangent_warps = c->tune.tangent_warps;
   k.residual_threads = c->tune.residual_threads;
-  k.ts_w = c->d_tsw;
-  k.ts_jobs = c->d_tsjobs;
+  k.ts_basis = c->d_tsbasis;
+  k.ts_plan = c->d_tsplan;
   return k;
 }
 
@@ -216,15 +216,14 @@ int upload_tables(vms_ctx* ctx) {
         t64[36 * nq + q] = r.w;
       }
   std::vector<float> t32(t64.begin(), t64.end());
-  dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_tsw); dfree(ctx->d_tsjobs);
-  if (n1 <= 3) {
-    std::vector<double> tw;
-    std::vector<uint16_t> tj;
-    ts_tables(n1, x, tw, tj);
-    CK(cudaMalloc(&ctx->d_tsw, sizeof(double) * tw.size()));
-    CK(cudaMalloc(&ctx->d_tsjobs, sizeof(uint16_t) * tj.size()));
-    CK(cudaMemcpy(ctx->d_tsw, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_tsjobs, tj.data(), sizeof(uint16_t) * tj.size(), cudaMemcpyHostToDevice));
+  dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_tsbasis); dfree(ctx->d_tsplan);
+  std::vector<double> tsb;
+  std::vector<uint32_t> tsp;
+  if ((n1 == 2 || n1 == 3) && ts_tables(n1, x, tsb, tsp)) {
+    CK(cudaMalloc(&ctx->d_tsbasis, sizeof(double) * tsb.size()));
+    CK(cudaMalloc(&ctx->d_tsplan, sizeof(uint32_t) * tsp.size()));
+    CK(cudaMemcpy(ctx->d_tsbasis, tsb.data(), sizeof(double) * tsb.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tsplan, tsp.data(), sizeof(uint32_t) * tsp.size(), cudaMemcpyHostToDevice));
   }
   CK(cudaMalloc(&ctx->d_qp, sizeof(QpRow) * nq));
   CK(cudaMalloc(&ctx->d_tab64, sizeof(double) * 37 * nq));
@@ -312,7 +311,7 @@ int vms_destroy(vms_ctx* ctx) {
   for (auto& e : ctx->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   dfree(ctx->d_qp); dfree(ctx->d_tab64); dfree(ctx->d_tab32); dfree(ctx->d_scalar);
-  dfree(ctx->d_tsw); dfree(ctx->d_tsjobs);
+  dfree(ctx->d_tsbasis); dfree(ctx->d_tsplan);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->work.aux) { cudaStreamSynchronize(ctx->work.aux); cudaStreamDestroy(ctx->work.aux); }

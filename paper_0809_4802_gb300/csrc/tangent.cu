@@ -5,6 +5,8 @@
 // W = K_cf K_ff^-1 and K_ff^-1, and the FP64 finish kernel forms r_e = R_cp - W R_f and
 // y = K_ff^-1 R_f once both the residual and the tangent kernels are done. The two element
 // kernels are therefore independent and run concurrently (FP64 pipe and FP32 pipe).
+#include <algorithm>
+
 #include "residual_math.cuh"
 #include "residual_table.cuh"
 #include "tangent_math.cuh"
@@ -177,12 +179,12 @@ __device__ __forceinline__ void tangent_element(
       __syncwarp();
     }
   } else if constexpr (ENG == TS_ENGINE) {
-    // FP64 weighted point sums (nq <= 27, checked on the host): ext0 = weight table (global),
-    // ext1 = job table (shared)
+    // FP64 factorised sums (nq = 8 or 27, checked on the host): ext0 = one-dimensional basis
+    // (shared), ext1 = plan of the partial sums (global)
     TsArea& C = *reinterpret_cast<TsArea*>(tcw);
     ts_phase1(lane, nq, W, C, tab, nut_e, tau, A);
     __syncwarp();
-    ts_sums(lane, nq, C, reinterpret_cast<const double*>(ext0), reinterpret_cast<const uint16_t*>(ext1));
+    ts_sums(lane, nq, C, reinterpret_cast<const double*>(ext0), reinterpret_cast<const uint32_t*>(ext1));
     __syncwarp();
     ts_gather(lane, C, A);
     __syncwarp();
@@ -295,7 +297,7 @@ __device__ __forceinline__ void tangent_element(
 template <typename T, int ENG>
 __host__ __device__ inline size_t tan_bfrag_bytes() {
   if constexpr (ENG == 0) return 0;
-  else if constexpr (ENG == TS_ENGINE) return ((size_t)TS_JOBS * sizeof(uint16_t) + 15) & ~size_t(15);
+  else if constexpr (ENG == TS_ENGINE) return sizeof(double) * 4 * TS_BASIS_ROWS;
   else return (size_t)tc_bsteps<ENG>() * 32 * tc_bwords<ENG>() * 4;
 }
 template <typename T, int ENG>
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : (ENG == TS_ENGINE ?
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
     T* __restrict__ recKcf, double* __restrict__ recKinv, double* __restrict__ oS,
     double* __restrict__ oKcc, double* __restrict__ oKcf, double* __restrict__ oKfc,
-    double* __restrict__ oKff, unsigned int* __restrict__ flags, const double* __restrict__ tsw,
-    const uint16_t* __restrict__ tsjobs) {
+    double* __restrict__ oKff, unsigned int* __restrict__ flags, const double* __restrict__ tsbasis,
+    const uint32_t* __restrict__ tsplan) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* st = reinterpret_cast<T*>(smem);
   for (int i = threadIdx.x; i < 37 * nq; i += blockDim.x) st[i] = gtab[i];
@@ -335,11 +337,11 @@ __global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : (ENG == TS_ENGINE ?
   const void* ext0 = bfrag;
   const void* ext1 = nullptr;
   if constexpr (ENG == TS_ENGINE) {
-    uint16_t* jobs = reinterpret_cast<uint16_t*>(bfrag);
-    for (int i = threadIdx.x; i < TS_JOBS; i += blockDim.x) jobs[i] = tsjobs[i];
+    double* basis = reinterpret_cast<double*>(bfrag);
+    for (int i = threadIdx.x; i < 4 * TS_BASIS_ROWS; i += blockDim.x) basis[i] = tsbasis[i];
     tcw = wbase + tan_warp_bytes<T, 0>(nq);
-    ext0 = tsw;
-    ext1 = jobs;
+    ext0 = basis;
+    ext1 = tsplan;
     __syncthreads();
   } else if constexpr (ENG != 0) {
     tc_build_b<ENG>(tab.N, tab.dN, nq, bfrag);
@@ -538,8 +540,8 @@ static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const K
       u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, s.u,
       s.beta, kp.tab64, first, count, elem_list, m.blk,
       m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
-      reinterpret_cast<T*>(o.recKcf), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags, kp.ts_w,
-      kp.ts_jobs);
+      reinterpret_cast<T*>(o.recKcf), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags, kp.ts_basis,
+      kp.ts_plan);
 }
 
 // Warps per block: the default, or the tuned count when it is one of the compiled choices
@@ -557,7 +559,7 @@ static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const K
   }
   if constexpr (sizeof(T) == 8) {
     // FP64: weighted point sums for the 8- and 27-point rules (the tables exist), TS_WARPS per CTA
-    if (kp.ts_w && kp.nq <= 27)
+    if (kp.ts_plan && kp.nq <= 27)
       return launch_w<T, ELEM_OUT, ATOMIC, TS_WARPS, TS_ENGINE>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
   }
   constexpr int D = tan_warps<T>();
@@ -569,59 +571,107 @@ static void launch_t(const Mesh& m, const State& s, const Fp32Copy& c32, const K
   launch_w<T, ELEM_OUT, ATOMIC, D, 0>(m, s, c32, kp, tab, o, first, count, elem_list, flags, st);
 }
 
-void ts_tables(int n1, const double* x, std::vector<double>& w, std::vector<uint16_t>& jobs) {
-  const int nq = n1 * n1 * n1;
+bool ts_tables(int n1, const double* x, std::vector<double>& basis, std::vector<uint32_t>& plan) {
+  const int nq = n1 * n1 * n1, ld = ts_ld(nq), fbase = TS_SUMS, total = TS_SUMS + TS_FIELDS * ld;
   auto phi = [](int b, double t) { return b ? 0.5 * (1.0 + t) : 0.5 * (1.0 - t); };
-  auto psi = [&](int sm, double t) { return sm == 0 ? phi(0, t) * phi(0, t) : sm == 1 ? phi(0, t) * phi(1, t) : phi(1, t) * phi(1, t); };
-  auto bit = [](int a, int d) { return d == 0 ? ((a + 1) >> 1) & 1 : (d == 1 ? (a >> 1) & 1 : (a >> 2) & 1); };
-  w.assign((size_t)TS_WEIGHTS * nq + 12, 0.0);
-  for (int sm = 0; sm < 3; ++sm)
-    for (int i = 0; i < n1; ++i) w[(size_t)TS_WEIGHTS * nq + 4 * sm + i] = psi(sm, x[i]);
-  auto W = [&](int k, int q) -> double& { return w[(size_t)q * TS_WEIGHTS + k]; };  // point-major
-  for (int q = 0; q < nq; ++q) {
-    const double xi[3] = {x[q % n1], x[(q / n1) % n1], x[q / (n1 * n1)]};
-    for (int t = 0; t < 27; ++t)
-      W(TW_PSI3 + t, q) = psi(t % 3, xi[0]) * psi((t / 3) % 3, xi[1]) * psi(t / 9, xi[2]);
-    for (int al = 0; al < 3; ++al) {
-      const int d1 = ts_d1(al), d2 = ts_d2(al);
-      for (int ty = 0; ty < 18; ++ty) {
-        const int xb = ty & 1, ps = ty >> 1;
-        W(TW_PHIPSI + 18 * al + ty, q) = phi(xb, xi[al]) * psi(ps % 3, xi[d1]) * psi(ps / 3, xi[d2]);
-      }
-      for (int ty = 0; ty < 9; ++ty)
-        W(TW_PSI2 + 9 * al + ty, q) = psi(ty % 3, xi[d1]) * psi(ty / 3, xi[d2]);
-      for (int ty = 0; ty < 4; ++ty)
-        W(TW_PHI2 + 4 * al + ty, q) = phi(ty & 1, xi[d1]) * phi(ty >> 1, xi[d2]);
-    }
-    for (int pp = 0; pp < 3; ++pp) {
-      const int al = pp == 2 ? 1 : 0, be = pp == 0 ? 1 : 2, ga = 2 - pp;
-      for (int ty = 0; ty < 12; ++ty)
-        W(TW_PHI2PSI + 12 * pp + ty, q) = phi(ty & 1, xi[al]) * phi((ty >> 1) & 1, xi[be]) * psi(ty >> 2, xi[ga]);
-    }
-    for (int a = 0; a < 8; ++a)
-      W(TW_N + a, q) = phi(bit(a, 0), xi[0]) * phi(bit(a, 1), xi[1]) * phi(bit(a, 2), xi[2]);
+  basis.assign(4 * TS_BASIS_ROWS, 0.0);
+  for (int i = 0; i < n1; ++i) {
+    for (int sm = 0; sm < 3; ++sm)
+      basis[4 * (TS_ROW_PSI + sm) + i] = phi(sm == 2, x[i]) * phi(sm >= 1, x[i]);
+    for (int b = 0; b < 2; ++b) basis[4 * (TS_ROW_PHI + b) + i] = phi(b, x[i]);
+    basis[4 * TS_ROW_ONE + i] = 1.0;
   }
-  jobs.assign(TS_JOBS, 0);
-  auto job = [&](int j, int field, int weight) { jobs[j] = (uint16_t)(field | (weight << 8)); };
-  for (int ik = 0; ik < 9; ++ik)
-    for (int t = 0; t < 27; ++t) job(TJ_L + 27 * ik + t, TF_L + ik, TW_PSI3 + t);
-  for (int al = 0; al < 3; ++al) {
+  // one factorised sum family: a field, per direction the first basis row, the row count and the
+  // stride of that direction's index in the sums, and where the sums start
+  struct Task { int field, out, row[3], m[3], st[3]; };
+  struct Dir { int row, m, st; };
+  const Dir PSI{TS_ROW_PSI, 3, 0}, PHI{TS_ROW_PHI, 2, 0}, ONE{TS_ROW_ONE, 1, 0};
+  auto task = [](int field, int out, Dir d0, Dir d1, Dir d2, int s0, int s1, int s2) {
+    return Task{field, out, {d0.row, d1.row, d2.row}, {d0.m, d1.m, d2.m}, {s0, s1, s2}};
+  };
+  // direction al gets (da, sa), the two others in increasing order (db, sb) and (dc, sc)
+  auto by_dir = [&](int field, int out, int al, Dir da, int sa, Dir db, int sb, Dir dc, int sc) {
+    Dir d[3]; int st[3];
+    d[al] = da; st[al] = sa;
+    d[ts_d1(al)] = db; st[ts_d1(al)] = sb;
+    d[ts_d2(al)] = dc; st[ts_d2(al)] = sc;
+    return task(field, out, d[0], d[1], d[2], st[0], st[1], st[2]);
+  };
+  std::vector<Task> ga, gb;  // fields 0..26 (coarse blocks) and 27..56 (couplings)
+  for (int f = 0; f < 9; ++f) ga.push_back(task(TF_L + f, TJ_L + 27 * f, PSI, PSI, PSI, 1, 3, 9));
+  for (int al = 0; al < 3; ++al)
     for (int fl = 0; fl < 4; ++fl)
-      for (int ty = 0; ty < 18; ++ty)
-        job(TJ_VP + 72 * al + 18 * fl + ty, fl == 0 ? TF_ADV + al : TF_VP + 3 * al + fl - 1, TW_PHIPSI + 18 * al + ty);
-    for (int ty = 0; ty < 9; ++ty) job(TJ_DD + 9 * al + ty, TF_G + al, TW_PSI2 + 9 * al + ty);
-    for (int ty = 0; ty < 4; ++ty) {
-      job(TJ_CFD + 4 * al + ty, TF_ZCF + al, TW_PHI2 + 4 * al + ty);
-      job(TJ_FCD + 4 * al + ty, TF_ZFC + al, TW_PHI2 + 4 * al + ty);
-    }
+      ga.push_back(by_dir(fl == 0 ? TF_ADV + al : TF_VP + 3 * al + fl - 1, TJ_VP + 72 * al + 18 * fl,
+                          al, PHI, 1, PSI, 2, PSI, 6));
+  for (int al = 0; al < 3; ++al) ga.push_back(by_dir(TF_G + al, TJ_DD + 9 * al, al, ONE, 0, PSI, 1, PSI, 3));
+  for (int pp = 0; pp < 3; ++pp) {
+    const int al = pp == 2 ? 1 : 0, be = pp == 0 ? 1 : 2, gm = 2 - pp;
+    Dir d[3]; int st[3];
+    d[al] = PHI; st[al] = 1;
+    d[be] = PHI; st[be] = 2;
+    d[gm] = PSI; st[gm] = 4;
+    ga.push_back(task(TF_G + 3 + pp, TJ_OD + 12 * pp, d[0], d[1], d[2], st[0], st[1], st[2]));
   }
-  for (int pp = 0; pp < 3; ++pp)
-    for (int ty = 0; ty < 12; ++ty) job(TJ_OD + 12 * pp + ty, TF_G + 3 + pp, TW_PHI2PSI + 12 * pp + ty);
-  for (int cf = 0; cf < 12; ++cf)
-    for (int a = 0; a < 8; ++a) {
-      job(TJ_CFN + 8 * cf + a, TF_YCF + cf, TW_N + a);
-      job(TJ_FCN + 8 * cf + a, TF_YFC + cf, TW_N + a);
+  for (int f = 0; f < 12; ++f) {
+    gb.push_back(task(TF_YCF + f, TJ_CFN + 8 * f, PHI, PHI, PHI, 1, 2, 4));
+    gb.push_back(task(TF_YFC + f, TJ_FCN + 8 * f, PHI, PHI, PHI, 1, 2, 4));
+  }
+  for (int al = 0; al < 3; ++al) {
+    gb.push_back(by_dir(TF_ZCF + al, TJ_CFD + 4 * al, al, ONE, 0, PHI, 1, PHI, 2));
+    gb.push_back(by_dir(TF_ZFC + al, TJ_FCD + 4 * al, al, ONE, 0, PHI, 1, PHI, 2));
+  }
+  // first fit of `size` doubles avoiding the busy intervals [a, b)
+  auto place = [&](int size, std::vector<std::pair<int, int>> busy) {
+    std::sort(busy.begin(), busy.end());
+    int at = 0;
+    for (auto& iv : busy) {
+      if (iv.first - at >= size) break;
+      at = std::max(at, iv.second);
     }
+    return at + size <= total ? at : -1;
+  };
+  plan.assign(TS_PLAN_HEAD, 0u);
+  auto entry = [&](int in, int out, int row) {
+    plan.push_back((uint32_t)in | (uint32_t)out << 12 | (uint32_t)row << 24);
+  };
+  const std::vector<Task>* groups[2] = {&ga, &gb};
+  const int f_hi[2] = {27, TS_FIELDS}, t_lo[2] = {0, TJ_CFN}, t_hi[2] = {TJ_CFN, TS_SUMS};
+  if (total > 4096) return false;
+  int step = 0;
+  for (int g = 0; g < 2; ++g) {
+    const auto& ts = *groups[g];
+    const std::pair<int, int> later{fbase + f_hi[g] * ld, total}, done{0, t_lo[g]};
+    int n1sz = 0, n2sz = 0;
+    for (auto& t : ts) { n1sz += t.m[0] * n1 * n1; n2sz += t.m[0] * t.m[1] * n1; }
+    const int s1 = place(n1sz, {{fbase + (g ? 27 : 0) * ld, total}, done});
+    if (s1 < 0) return false;
+    const int s2 = place(n2sz, {{s1, s1 + n1sz}, later, done, {t_lo[g], t_hi[g]}});
+    if (s2 < 0) return false;
+    // step 1: direction 0 of the point fields into s1 (per task and t0: n1^2 partial sums)
+    plan[step++] = (uint32_t)plan.size();
+    int p1 = s1;
+    for (auto& t : ts)
+      for (int t0 = 0; t0 < t.m[0]; ++t0)
+        for (int i12 = 0; i12 < n1 * n1; ++i12) entry(fbase + t.field * ld + n1 * i12, p1++, t.row[0] + t0);
+    // step 2: direction 1 (per task, t0, t1: n1 partial sums)
+    plan[step++] = (uint32_t)plan.size();
+    p1 = s1;
+    int p2 = s2;
+    for (auto& t : ts)
+      for (int t0 = 0; t0 < t.m[0]; ++t0, p1 += n1 * n1)
+        for (int t1 = 0; t1 < t.m[1]; ++t1)
+          for (int i2 = 0; i2 < n1; ++i2) entry(p1 + n1 * i2, p2++, t.row[1] + t1);
+    // step 3: direction 2 into the sums
+    plan[step++] = (uint32_t)plan.size();
+    p2 = s2;
+    for (auto& t : ts)
+      for (int t0 = 0; t0 < t.m[0]; ++t0)
+        for (int t1 = 0; t1 < t.m[1]; ++t1, p2 += n1)
+          for (int t2 = 0; t2 < t.m[2]; ++t2)
+            entry(p2, t.out + t0 * t.st[0] + t1 * t.st[1] + t2 * t.st[2], t.row[2] + t2);
+  }
+  plan[step] = (uint32_t)plan.size();
+  return true;
 }
 
 int tangent_warp_choice(bool fp32, int k) {

@@ -1,4 +1,5 @@
-// FP64 tangent blocks by weighted point sums (Section 4.2, Eq. NewtonUpdate2).
+// FP64 tangent blocks from sums of point fields against the reference basis (Section 4.2,
+// Eq. NewtonUpdate2).
 //
 // Every entry of the coarse blocks and of the coarse-fine couplings is a sum over the quadrature
 // points of a per-element field times a product of one-dimensional factors of the reference
@@ -10,35 +11,37 @@
 //   dN_a/dxi_al dN_b/dxi_be = +-1/4 phi(xi_al) phi(xi_be) psi(xi_ga)      (12 per pair al < be)
 //   N_a, dN_a/dxi_al       = prod phi, +-1/2 prod_{d != al} phi            (8, 4 per al)
 // so only 164 distinct weights exist. Per element the warp forms 738 sums
-//   T_j = sum_q W[w_j][q] F[f_j][q]
+//   T_j = sum_q W_j(xi_q) F[f_j][q]
 // over 57 per-point fields F (omega L_ik + tau omega delta_ik; omega (J^-1 v)_al; omega J^-1[al][i];
 // nut omega (J^-1 J^-T)_albe; the K_cf / K_fc coefficients Ycf, Yfc of tangent_math.cuh;
-// nut omega (J^-1 d)_al and (J^-1 (omega b v + nut omega d))_al), one sum per lane per round, and
-// every block entry is then a signed combination of a few T_j: about 20 k FMA per element instead
-// of the ~51 k of the pair loop. Used for the 8- and 27-point rules in FP64 mode.
+// nut omega (J^-1 d)_al and (J^-1 (omega b v + nut omega d))_al). The weights being products over
+// the directions, each sum is taken one direction at a time on the tensor Gauss rule (ts_sums), and
+// every block entry is then a signed combination of a few T_j: about 8 k FMA per element for 27
+// points, where the node-pair loop takes ~51 k. Used for the 8- and 27-point rules in FP64 mode.
 #pragma once
 
 #include "tangent_math.cuh"
 
 namespace vms {
 
-constexpr int TS_FIELDS = 57, TS_WEIGHTS = 164, TS_JOBS = 738;
+constexpr int TS_FIELDS = 57, TS_SUMS = 738;
 constexpr int TS_ENGINE = 3;
+constexpr int TS_STEPS = 6, TS_PLAN_HEAD = 8;
+// rows of the one-dimensional basis table: psi_0..2, phi_0..1, the constant 1
+constexpr int TS_ROW_PSI = 0, TS_ROW_PHI = 3, TS_ROW_ONE = 5, TS_BASIS_ROWS = 8;
 // field slots
 constexpr int TF_L = 0, TF_ADV = 9, TF_VP = 12, TF_G = 21, TF_YCF = 27, TF_YFC = 39, TF_ZCF = 51,
               TF_ZFC = 54;
-// job ranges
+// ranges of the sums
 constexpr int TJ_L = 0, TJ_VP = 243, TJ_DD = 459, TJ_OD = 486, TJ_CFN = 522, TJ_FCN = 618,
               TJ_CFD = 714, TJ_FCD = 726;
-// weight ranges
-constexpr int TW_PSI3 = 0, TW_PHIPSI = 27, TW_PSI2 = 81, TW_PHI2PSI = 108, TW_N = 144, TW_PHI2 = 152;
 
 // point-field stride (odd: conflict-free column reads across lanes)
 __host__ __device__ constexpr int ts_ld(int nq) { return nq | 1; }
 
-// Per-warp storage: the point fields and the 738 sums.
+// Per-warp storage: the 738 sums and the point fields (one array: the sums' plan addresses both).
 struct TsArea {
-  double T[TS_JOBS];
+  double T[TS_SUMS];
   double F[1];  // TS_FIELDS x ts_ld(nq), sized at launch
 };
 __host__ __device__ inline size_t ts_area_bytes(int nq) {
@@ -141,60 +144,37 @@ __device__ __forceinline__ void ts_phase1(int lane, int nq, WarpArea<double>& W,
       A.kff[3 * i + k] += om * (bq * (bq * L[i][k] + (i == k ? cd : 0.0)) + (i == k ? nut * dd : 0.0));
 }
 
-// The 738 sums: lane `lane` takes jobs lane, lane + 32, ...; job j reads field jobs[j] & 255 and
-// weight jobs[j] >> 8. The weight table Wt (global, read through L1) is point-major, nq rows of
-// TS_WEIGHTS, so that the lanes of a round, whose jobs mostly use consecutive weights, read
-// consecutive words.
-//
-// The 243 sums of the N_a N_b family (9 fields x 27 weights prod_d psi_{s_d}(xi_d)) are formed by
-// sum factorisation instead, one direction at a time (3 x 243 x n1 FMA for n1 points per
-// direction instead of 243 x n1^3), the intermediate sums parked in T[243..728] before the other
-// jobs overwrite them. psi[s][i] = psi_s(x_i) follows the weight table (TS_WEIGHTS * nq + 4 s + i).
-__device__ __forceinline__ void ts_sums(int lane, int nq, TsArea& C, const double* __restrict__ Wt,
-                                        const uint16_t* __restrict__ jobs) {
-  const int ld = ts_ld(nq);
-  const int n1 = nq == 8 ? 2 : 3;
-  const double* psi = Wt + TS_WEIGHTS * nq;
-  {
-    double* s1 = C.T + TJ_VP;          // [f][s0][i1 + n1 i2]
-    double* s2 = C.T + TJ_VP + 243;    // [f][s0][s1][i2]
-    const int n_1 = 27 * n1 * n1, n_2 = 81 * n1;
-    for (int o = lane; o < n_1; o += 32) {
-      const int i12 = o % (n1 * n1), fs = o / (n1 * n1), f = fs / 3, s0 = fs % 3;
-      const double* fr = C.F + (TF_L + f) * ld + n1 * i12;
-      double acc = 0.0;
-      for (int i0 = 0; i0 < n1; ++i0) acc += __ldg(psi + 4 * s0 + i0) * fr[i0];
-      s1[o] = acc;
+// The 738 sums, by sum factorisation: a sum over the n1^3 points of a field times a product of
+// one-dimensional factors prod_d B_d(xi_d) is taken one direction at a time (xi_0 first), each
+// partial sum an n1-term dot product with one row of the one-dimensional basis table B (psi_0..2,
+// phi_0..1, 1 at the n1 Gauss points; `basis`, 8 x 4 doubles). The host-built plan lists every
+// partial sum of the six steps (three directions for the fields 0..26 of the coarse blocks, then
+// three for the fields 27..56 of the couplings) as in | out << 12 | row << 24, in and out being
+// offsets into the warp's TsArea taken as one array (the sums T, then the fields F); scratch of
+// one step is placed where neither its own inputs, the fields still to come nor the sums already
+// formed lie. plan[0..6] are the steps' first and last entries. About 8 k FMA per element for
+// 27 points, where point sums take 20 k.
+__device__ __forceinline__ void ts_sums(int lane, int nq, TsArea& C, const double* __restrict__ B,
+                                        const uint32_t* __restrict__ plan) {
+  double* A = C.T;
+  for (int st = 0; st < TS_STEPS; ++st) {
+    const int end = (int)__ldg(plan + st + 1);
+    if (nq == 27) {
+      for (int j = (int)__ldg(plan + st) + lane; j < end; j += 32) {
+        const uint32_t en = __ldg(plan + j);
+        const double* a = A + (en & 4095u);
+        const double* b = B + 4 * (en >> 24);
+        A[(en >> 12) & 4095u] = fma(b[2], a[2], fma(b[1], a[1], b[0] * a[0]));
+      }
+    } else {
+      for (int j = (int)__ldg(plan + st) + lane; j < end; j += 32) {
+        const uint32_t en = __ldg(plan + j);
+        const double* a = A + (en & 4095u);
+        const double* b = B + 4 * (en >> 24);
+        A[(en >> 12) & 4095u] = fma(b[1], a[1], b[0] * a[0]);
+      }
     }
     __syncwarp();
-    for (int o = lane; o < n_2; o += 32) {
-      const int i2 = o % n1, fss = o / n1, s1i = fss % 3, fs0 = fss / 3;
-      double acc = 0.0;
-      for (int i1 = 0; i1 < n1; ++i1) acc += __ldg(psi + 4 * s1i + i1) * s1[fs0 * n1 * n1 + i1 + n1 * i2];
-      s2[o] = acc;
-    }
-    __syncwarp();
-    for (int o = lane; o < 243; o += 32) {
-      const int f = o / 27, t = o % 27, s0 = t % 3, s1i = (t / 3) % 3, s2i = t / 9;
-      const double* r = s2 + ((f * 3 + s0) * 3 + s1i) * n1;
-      double acc = 0.0;
-      for (int i2 = 0; i2 < n1; ++i2) acc += __ldg(psi + 4 * s2i + i2) * r[i2];
-      C.T[TJ_L + o] = acc;
-    }
-    __syncwarp();
-  }
-  for (int j = TJ_VP + lane; j < TS_JOBS; j += 32) {
-    const uint16_t jb = jobs[j];
-    const double* f = C.F + (jb & 255) * ld;
-    const double* w = Wt + (jb >> 8);
-    double s0 = 0.0, s1 = 0.0;
-    int q = 0;
-    for (; q + 1 < nq; q += 2) {
-      s0 += __ldg(w + q * TS_WEIGHTS) * f[q];
-      s1 += __ldg(w + (q + 1) * TS_WEIGHTS) * f[q + 1];
-    }
-    if (q < nq) s0 += __ldg(w + q * TS_WEIGHTS) * f[q];
-    C.T[j] = s0 + s1;
   }
 }
 
@@ -258,6 +238,7 @@ __device__ __forceinline__ void ts_gather(int lane, const TsArea& C, LaneAcc<dou
     }
   }
   const int at = lane >> 2, ct = lane & 3;
+  const int tb = ts_bit(at, 0) + 2 * ts_bit(at, 1) + 4 * ts_bit(at, 2);  // tensor order of node at
   double dcf = 0.0, dfc = 0.0;
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
@@ -268,8 +249,8 @@ __device__ __forceinline__ void ts_gather(int lane, const TsArea& C, LaneAcc<dou
   }
 #pragma unroll
   for (int kk = 0; kk < 3; ++kk) {
-    A.kcf[kk] = T[TJ_CFN + 8 * (3 * ct + kk) + at] + (ct == kk ? dcf : 0.0);
-    A.kfc[kk] = T[TJ_FCN + 8 * (3 * ct + kk) + at] + (ct == kk ? dfc : 0.0);
+    A.kcf[kk] = T[TJ_CFN + 8 * (3 * ct + kk) + tb] + (ct == kk ? dcf : 0.0);
+    A.kfc[kk] = T[TJ_FCN + 8 * (3 * ct + kk) + tb] + (ct == kk ? dfc : 0.0);
   }
 }
 #endif

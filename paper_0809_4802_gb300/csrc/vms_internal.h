@@ -44,8 +44,8 @@ struct KParams {
   const double* tab64;   // FP64 reference table of the tangent kernel (37 nq), for FP64 K_ff
   int tangent_warps;     // warps per tangent block (0: default)
   int residual_threads;  // threads per residual block (0: default)
-  const double* ts_w = nullptr;      // FP64 tangent: weight table (nq x 164, point-major), nq <= 27
-  const uint16_t* ts_jobs = nullptr; // FP64 tangent: 738 jobs (field | weight << 8)
+  const double* ts_basis = nullptr;  // FP64 tangent: one-dimensional basis (8 x 4), nq = 8 or 27
+  const uint32_t* ts_plan = nullptr;  // FP64 tangent: plan of the factorised sums
 };
 
 // The once-per-mesh pattern (host side, built by pattern.cpp).
@@ -62,10 +62,10 @@ struct HostPattern {
   int n_colours = 0;
 };
 
-// Weight table (nq x 164 doubles, point-major, then psi_s(x_i) at 164 nq + 4 s + i) and job
-// table (738 entries: field | weight << 8) of the FP64 tangent's weighted point sums for the
-// n1^3-point Gauss rule with points x (n1 <= 3).
-void ts_tables(int n1, const double* x, std::vector<double>& w, std::vector<uint16_t>& jobs);
+// One-dimensional basis rows (psi_0..2, phi_0..1, 1 at the n1 Gauss points x, 8 x 4 doubles) and
+// the plan of the FP64 tangent's factorised sums for the n1^3-point rule (n1 = 2 or 3). False if
+// the partial sums do not fit the per-warp area.
+bool ts_tables(int n1, const double* x, std::vector<double>& basis, std::vector<uint32_t>& plan);
 
 // Builds the CSR pattern, block map, colouring and Dirichlet masks. Returns "" or an error text.
 std::string build_pattern(int64_t n_nodes, int64_t n_elems, const int32_t* conn, int64_t n_dir,
