@@ -353,6 +353,15 @@ int vms_mlp_grad(vms_mlp* mlp, int64_t n, const int32_t* rows, const float* X, c
                  double* loss, float* grads);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) with the kept gradient. */
 int vms_mlp_adam(vms_mlp* mlp, float lr);
+/* Training-data scaling (the inputs and targets are brought to unit RMS per column before
+ * training): rms (host, cols doubles) = sqrt(mean over the n rows of X[r][c]^2) for X (device
+ * FP32, n x cols, 1 <= cols <= 16), summed in FP64; synchronises the stream. Errors:
+ * VMS_ERR_INVALID_ARG. */
+int vms_mlp_column_rms(vms_mlp* mlp, int64_t n, int cols, const float* X, double* rms);
+/* out[r][c] = X[r][c] * mul[c] for X, out device FP32 n x cols (out may be X), mul cols host floats
+ * (1 <= cols <= 16), queued on the stream. Errors: VMS_ERR_INVALID_ARG. */
+int vms_mlp_scale_columns(vms_mlp* mlp, int64_t n, int cols, const float* X, const float* mul,
+                          float* out);
 
 /* Features of every node from the context's state u (step n) and u_prev (step n-1), with
  * d = u - u_prev: X[i] = [u_i (4), d_i (4), mean of d over the nodes sharing an element with i (4)]

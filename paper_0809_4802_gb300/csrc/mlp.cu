@@ -3,14 +3,22 @@
 // backward-Euler step. Weights are stored in BF16, biases, activations and accumulation in FP32.
 // Forward, backward (mean squared error) and Adam run in these kernels; Newton then converges to
 // the same tolerance from the predicted start, so the network only changes the starting point.
+// The three 128-wide contractions of a 64-node tile (H1 W2 in the forward pass; H1^T D and D W2^T
+// in the backward pass) run on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
+// accumulation), the FP32 activations split into sums of BF16 terms (mma_bf16.cuh): three terms
+// against the BF16 weights (exact products, FP32-level results), two times two terms (three
+// products) for H1^T D. The 12-wide input layer, the 4-wide output layer and the small gradient
+// blocks stay on the CUDA cores.
 //
 // Layout of the parameter vector (row-major): W1 [12][128], b1 [128], W2 [128][128], b2 [128],
 // W3 [128][4], b3 [4].
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "mma_bf16.cuh"
 #include "solver.h"
 #include "vms_internal.h"
 
@@ -25,11 +33,16 @@ struct vms_mlp {
   float* bias = nullptr;       // b1, b2, b3 in FP32
   double* loss = nullptr;      // device loss accumulator
   float* scratch = nullptr;    // P_N floats (parameter read-back)
+  double* colsum = nullptr;    // 16 column sums of squares (vms_mlp_column_rms)
   int t = 0;                   // Adam steps taken
   std::string err;
 };
 
 namespace {
+
+using vms::bf16x2_split2;
+using vms::bf16x2_split3;
+using vms::mma_bf16;
 
 constexpr int NI = VMS_MLP_IN, NW = VMS_MLP_WIDTH, NO = VMS_MLP_OUT;
 constexpr int P_W1 = 0, P_B1 = P_W1 + NI * NW, P_W2 = P_B1 + NW, P_B2 = P_W2 + NW * NW,
@@ -40,30 +53,84 @@ constexpr int WB_1 = 0, WB_2 = NI * NW, WB_3 = WB_2 + NW * NW, WB_N = WB_3 + NW 
 constexpr int BB_1 = 0, BB_2 = NW, BB_3 = 2 * NW, BB_N = 2 * NW + NO;
 
 constexpr int TILE = 64;       // rows (nodes) per tile
-constexpr int THREADS = 256;   // 8 warps: warp w owns rows 8w..8w+7, lane l columns l + 32 j
-constexpr int W2LD = NW + 1;   // padded row of W2 in shared memory (conflict-free column reads)
+constexpr int THREADS = 256;   // 8 warps
+constexpr int HLD = NW + 4;    // padded FP32 activation row (conflict-free MMA fragment loads)
+constexpr int WLD = NW + 8;    // padded BF16 weight row (68 words: conflict-free fragment loads)
 
 struct Smem {
   float W1[NI][NW];
-  float W2[NW][W2LD];
+  __nv_bfloat16 W2t[NW][WLD];  // W2^T [j][k]: B operand of H1 W2 (K index contiguous)
   float W3[NW][NO];
   float b1[NW], b2[NW], b3[NO];
   float X[TILE][NI];
-  float H1[TILE][NW];
-  float H2[TILE][NW];
+  float H1[TILE][HLD];
+  float H2[TILE][HLD];
 };
 struct SmemGrad : Smem {
-  float D[TILE][NW];
+  __nv_bfloat16 W2[NW][WLD];   // W2 [k][j]: B operand of D W2^T
+  float D[TILE][HLD];
   float dY[TILE][NO];
 };
 
 __device__ void load_weights(Smem& s, const __nv_bfloat16* __restrict__ w,
-                             const float* __restrict__ bias) {
+                             const float* __restrict__ bias, __nv_bfloat16 (*W2)[WLD] = nullptr) {
   for (int i = threadIdx.x; i < NI * NW; i += THREADS) s.W1[i / NW][i % NW] = __bfloat162float(w[WB_1 + i]);
-  for (int i = threadIdx.x; i < NW * NW; i += THREADS) s.W2[i / NW][i % NW] = __bfloat162float(w[WB_2 + i]);
+  for (int i = threadIdx.x; i < NW * NW; i += THREADS) {
+    const int k = i / NW, j = i % NW;
+    s.W2t[j][k] = w[WB_2 + i];
+    if (W2) W2[k][j] = w[WB_2 + i];
+  }
   for (int i = threadIdx.x; i < NW * NO; i += THREADS) s.W3[i / NO][i % NO] = __bfloat162float(w[WB_3 + i]);
   for (int i = threadIdx.x; i < NW; i += THREADS) { s.b1[i] = bias[BB_1 + i]; s.b2[i] = bias[BB_2 + i]; }
   if (threadIdx.x < NO) s.b3[threadIdx.x] = bias[BB_3 + threadIdx.x];
+}
+
+// C[64 x 128] = A[64 x 128] B on the tensor cores, B given as Bk[n][k] (BF16, K contiguous), A
+// FP32 split into three BF16 terms. Warp w owns rows 16 (w & 3) .. + 15 and columns
+// 64 (w >> 2) .. + 63 (eight 8-wide tiles); acc[nt][*] is the standard m16n8 C fragment (rows g,
+// g + 8 and columns 2t, 2t + 1 of tile nt, g = lane / 4, t = lane % 4), initialised by the caller.
+__device__ __forceinline__ void mma_rows64(const float (*A)[HLD], const __nv_bfloat16 (*Bk)[WLD],
+                                           float acc[8][4]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * (w & 3) + g, c0 = 64 * (w >> 2);
+#pragma unroll 2
+  for (int k0 = 0; k0 < NW; k0 += 16) {
+    uint32_t ah[4], am[4], al[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float2 x = *reinterpret_cast<const float2*>(&A[r0 + 8 * (f & 1)][k0 + 2 * t + 8 * (f >> 1)]);
+      bf16x2_split3(x.x, x.y, ah[f], am[f], al[f]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const __nv_bfloat16* br = &Bk[c0 + 8 * nt + g][k0 + 2 * t];
+      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(br);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(br + 8);
+      mma_bf16(acc[nt], al, b0, b1);
+      mma_bf16(acc[nt], am, b0, b1);
+      mma_bf16(acc[nt], ah, b0, b1);
+    }
+  }
+}
+
+// H2 = tanh(H1 W2 + b2) on the tensor cores
+__device__ __forceinline__ void dense2_tanh(Smem& s) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * (w & 3) + g, c0 = 64 * (w >> 2);
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int c = c0 + 8 * nt + 2 * t;
+    acc[nt][0] = acc[nt][2] = s.b2[c];
+    acc[nt][1] = acc[nt][3] = s.b2[c + 1];
+  }
+  mma_rows64(s.H1, s.W2t, acc);
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int c = c0 + 8 * nt + 2 * t;
+    *reinterpret_cast<float2*>(&s.H2[r0][c]) = make_float2(tanhf(acc[nt][0]), tanhf(acc[nt][1]));
+    *reinterpret_cast<float2*>(&s.H2[r0 + 8][c]) = make_float2(tanhf(acc[nt][2]), tanhf(acc[nt][3]));
+  }
 }
 
 // rows [r0, r0 + TILE) of X (through `rows` if given) into shared memory, zero beyond n
@@ -78,9 +145,11 @@ __device__ void load_tile(Smem& s, const float* __restrict__ X, const int32_t* _
   }
 }
 
-// H = tanh(A W + b) for the tile: A [TILE][K] in shared memory, W [K][NW] (leading dimension LD)
+// H = tanh(A W + b) for the tile on the CUDA cores (the 12-wide input layer): A [TILE][K] in
+// shared memory, W [K][NW] (leading dimension LD); warp w owns rows 8w..8w+7, lane l columns
+// l + 32 j
 template <int K, int LD>
-__device__ void dense_tanh(const float (*A)[K], const float* W, const float* b, float (*H)[NW]) {
+__device__ void dense_tanh(const float (*A)[K], const float* W, const float* b, float (*H)[HLD]) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   float acc[8][4];
 #pragma unroll
@@ -126,7 +195,7 @@ __global__ void __launch_bounds__(THREADS) mlp_forward_kernel(const __nv_bfloat1
     __syncthreads();
     dense_tanh<NI, NW>(s.X, &s.W1[0][0], s.b1, s.H1);
     __syncthreads();
-    dense_tanh<NW, W2LD>(s.H1, &s.W2[0][0], s.b2, s.H2);
+    dense2_tanh(s);
     __syncthreads();
     const int r = threadIdx.x >> 2, o = threadIdx.x & 3;
     const float y = dense_out(s, r, o);
@@ -142,14 +211,16 @@ __global__ void __launch_bounds__(THREADS) mlp_grad_kernel(
     float* __restrict__ grad, double* __restrict__ loss) {
   extern __shared__ __align__(16) unsigned char raw[];
   SmemGrad& s = *reinterpret_cast<SmemGrad*>(raw);
-  load_weights(s, w, bias);
-  const int tid = threadIdx.x, wp = tid >> 5, l = tid & 31;
-  // register partials: dW2[k2][2 jj + jpar] (64), dW1 (6 entries), dW3 (2 entries), db1/db2
-  // (threads < 128: column tid), db3 (threads < 4)
-  const int k2 = tid >> 1, jpar = tid & 1;
-  float gW2[64], gW1[6], gW3[2], gb1 = 0.f, gb2 = 0.f, gb3 = 0.f;
+  load_weights(s, w, bias, s.W2);
+  const int tid = threadIdx.x, wp = tid >> 5, l = tid & 31, g = l >> 2, t = l & 3;
+  // register partials: dW2 as MMA C fragments (warp wp: rows k = 16 wp + g (+ 8) of dW2, column
+  // tiles 0..15), dW1 (6 entries), dW3 (2 entries), db1/db2 (threads < 128: column tid), db3
+  // (threads < 4)
+  float gW2[16][4], gW1[6], gW3[2], gb1 = 0.f, gb2 = 0.f, gb3 = 0.f;
 #pragma unroll
-  for (int i = 0; i < 64; ++i) gW2[i] = 0.f;
+  for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) gW2[nt][q] = 0.f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) gW1[i] = 0.f;
   gW3[0] = gW3[1] = 0.f;
@@ -160,15 +231,15 @@ __global__ void __launch_bounds__(THREADS) mlp_grad_kernel(
     __syncthreads();
     dense_tanh<NI, NW>(s.X, &s.W1[0][0], s.b1, s.H1);
     __syncthreads();
-    dense_tanh<NW, W2LD>(s.H1, &s.W2[0][0], s.b2, s.H2);
+    dense2_tanh(s);
     __syncthreads();
     {
       const int r = tid >> 2, o = tid & 3;
-      const int64_t g = r0 + r;
+      const int64_t gr = r0 + r;
       float d = 0.f;
-      if (g < n) {
+      if (gr < n) {
         const float y = dense_out(s, r, o);
-        const float e = y - T[(rows ? (int64_t)rows[g] : g) * NO + o];
+        const float e = y - T[(rows ? (int64_t)rows[gr] : gr) * NO + o];
         lsum += (double)e * (double)e;
         d = 2.f * scale * e;
       }
@@ -185,7 +256,7 @@ __global__ void __launch_bounds__(THREADS) mlp_grad_kernel(
     }
     if (tid < NO)
       for (int r = 0; r < TILE; ++r) gb3 += s.dY[r][tid];
-    // dH2 = (dY W3^T) * (1 - H2^2)
+    // D = dH2 = (dY W3^T) * (1 - H2^2)
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -198,28 +269,49 @@ __global__ void __launch_bounds__(THREADS) mlp_grad_kernel(
         s.D[rr][c] = a * (1.f - h * h);
       }
     __syncthreads();
-    // dW2[k][j] += sum_r H1[r][k] D[r][j]   (this thread: k = k2, j = 2 jj + jpar)
-    for (int r = 0; r < TILE; ++r) {
-      const float h = s.H1[r][k2];
+    // dW2[k][j] += sum_r H1[r][k] D[r][j] on the tensor cores: A = H1^T (rows k = 16 wp ..), B = D,
+    // both split into two BF16 terms, products hi hi + hi lo + lo hi
+#pragma unroll 1
+    for (int k0 = 0; k0 < TILE; k0 += 16) {
+      uint32_t ah[4], al[4];
 #pragma unroll
-      for (int jj = 0; jj < 64; ++jj) gW2[jj] = fmaf(h, s.D[r][2 * jj + jpar], gW2[jj]);
+      for (int f = 0; f < 4; ++f) {
+        const int m = 16 * wp + g + 8 * (f & 1), kr = k0 + 2 * t + 8 * (f >> 1);
+        bf16x2_split2(s.H1[kr][m], s.H1[kr + 1][m], ah[f], al[f]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 16; ++nt) {
+        const int c = 8 * nt + g, kr = k0 + 2 * t;
+        uint32_t bh0, bl0, bh1, bl1;
+        bf16x2_split2(s.D[kr][c], s.D[kr + 1][c], bh0, bl0);
+        bf16x2_split2(s.D[kr + 8][c], s.D[kr + 9][c], bh1, bl1);
+        mma_bf16(gW2[nt], al, bh0, bh1);
+        mma_bf16(gW2[nt], ah, bl0, bl1);
+        mma_bf16(gW2[nt], ah, bh0, bh1);
+      }
     }
     if (tid < NW)
       for (int r = 0; r < TILE; ++r) gb2 += s.D[r][tid];
-    // dH1 = (D W2^T) * (1 - H1^2), written over H2 (no longer needed)
+    // dH1 = (D W2^T) * (1 - H1^2) on the tensor cores (B = W2 [k][j], K = j contiguous), written
+    // over H2 (no longer needed)
+    {
+      const int rr = 16 * (wp & 3) + g, c0 = 64 * (wp >> 2);
+      float acc[8][4];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int rr = 8 * wp + r;
-      float a[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int j = 0; j < NW; ++j) {
-        const float d = s.D[rr][j];
+      for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = fmaf(d, s.W2[l + 32 * q][j], a[q]);
-      }
+        for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+      mma_rows64(s.D, s.W2, acc);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float h = s.H1[rr][l + 32 * q];
-        s.H2[rr][l + 32 * q] = a[q] * (1.f - h * h);
+      for (int nt = 0; nt < 8; ++nt) {
+        const int c = c0 + 8 * nt + 2 * t;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int r = rr + 8 * hf;
+          const float h0 = s.H1[r][c], h1 = s.H1[r][c + 1];
+          *reinterpret_cast<float2*>(&s.H2[r][c]) =
+              make_float2(acc[nt][2 * hf] * (1.f - h0 * h0), acc[nt][2 * hf + 1] * (1.f - h1 * h1));
+        }
       }
     }
     __syncthreads();
@@ -236,7 +328,12 @@ __global__ void __launch_bounds__(THREADS) mlp_grad_kernel(
   }
   // flush the partials
 #pragma unroll
-  for (int jj = 0; jj < 64; ++jj) atomicAdd(grad + P_W2 + k2 * NW + 2 * jj + jpar, gW2[jj]);
+  for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 16 * wp + g + 8 * (q >> 1), j = 8 * nt + 2 * t + (q & 1);
+      atomicAdd(grad + P_W2 + k * NW + j, gW2[nt][q]);
+    }
 #pragma unroll
   for (int q = 0; q < 6; ++q) atomicAdd(grad + P_W1 + tid + THREADS * q, gW1[q]);
 #pragma unroll
@@ -382,6 +479,44 @@ __global__ void apply_increment_kernel(double4_32a* __restrict__ u, int64_t n_no
   u[i] = a;
 }
 
+// per-column sums of squares (FP64): each thread accumulates the columns of a grid-stride set of
+// rows, the block combines them in shared memory and adds them to sums once
+constexpr int COLS_MAX = 16;
+struct ColMul {
+  float m[COLS_MAX];
+};
+
+__global__ void column_sumsq_kernel(const float* __restrict__ X, int64_t n, int cols,
+                                    double* __restrict__ sums) {
+  __shared__ double part[COLS_MAX];
+  if (threadIdx.x < COLS_MAX) part[threadIdx.x] = 0.0;
+  __syncthreads();
+  double acc[COLS_MAX];
+#pragma unroll
+  for (int c = 0; c < COLS_MAX; ++c) acc[c] = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int c = 0; c < COLS_MAX; ++c)
+      if (c < cols) {
+        const double x = X[r * cols + c];
+        acc[c] += x * x;
+      }
+  for (int c = 0; c < cols; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&part[c], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < cols) atomicAdd(sums + threadIdx.x, part[threadIdx.x]);
+}
+
+__global__ void scale_columns_kernel(const float* __restrict__ X, int64_t n, int cols, ColMul mul,
+                                     float* __restrict__ out) {
+  const int64_t total = n * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = X[i] * mul.m[i % cols];
+}
+
 }  // namespace
 
 extern "C" {
@@ -401,6 +536,7 @@ int vms_mlp_create(vms_mlp** out, int device) {
   if (e == cudaSuccess) e = cudaMalloc(&mlp->bias, sizeof(float) * BB_N);
   if (e == cudaSuccess) e = cudaMalloc(&mlp->loss, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&mlp->scratch, sizeof(float) * P_N);
+  if (e == cudaSuccess) e = cudaMalloc(&mlp->colsum, sizeof(double) * 16);
   for (void* p : {(void*)mlp->master, (void*)mlp->m, (void*)mlp->v, (void*)mlp->grad, (void*)mlp->bias})
     if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(float) * (p == (void*)mlp->bias ? BB_N : P_N));
   if (e == cudaSuccess) e = cudaMemset(mlp->w, 0, sizeof(__nv_bfloat16) * WB_N);
@@ -418,7 +554,7 @@ int vms_mlp_destroy(vms_mlp* mlp) {
   cudaSetDevice(mlp->device);
   if (mlp->stream) cudaStreamSynchronize(mlp->stream);
   for (void* p : {(void*)mlp->master, (void*)mlp->m, (void*)mlp->v, (void*)mlp->grad, (void*)mlp->w,
-                  (void*)mlp->bias, (void*)mlp->loss, (void*)mlp->scratch})
+                  (void*)mlp->bias, (void*)mlp->loss, (void*)mlp->scratch, (void*)mlp->colsum})
     if (p) cudaFree(p);
   delete mlp;
   return VMS_OK;
@@ -494,6 +630,35 @@ int vms_mlp_adam(vms_mlp* mlp, float lr) {
   mlp_adam_kernel<<<(P_N + 255) / 256, 256, 0, mlp->stream>>>(mlp->master, mlp->m, mlp->v, mlp->grad,
                                                               mlp->w, mlp->bias, lr, (float)b1,
                                                               (float)b2, 1e-8f, c1, c2);
+  MCK(cudaGetLastError());
+  return VMS_OK;
+}
+
+int vms_mlp_column_rms(vms_mlp* mlp, int64_t n, int cols, const float* X, double* rms) {
+  if (!mlp || n <= 0 || cols < 1 || cols > COLS_MAX || !X || !rms)
+    return mfail(mlp, VMS_ERR_INVALID_ARG, "invalid arguments");
+  MCK(cudaSetDevice(mlp->device));
+  MCK(cudaMemsetAsync(mlp->colsum, 0, sizeof(double) * COLS_MAX, mlp->stream));
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4 * (int64_t)vms::sm_count());
+  column_sumsq_kernel<<<(unsigned)blocks, 256, 0, mlp->stream>>>(X, n, cols, mlp->colsum);
+  MCK(cudaGetLastError());
+  double h[COLS_MAX];
+  MCK(cudaMemcpyAsync(h, mlp->colsum, sizeof(double) * cols, cudaMemcpyDeviceToHost, mlp->stream));
+  MCK(cudaStreamSynchronize(mlp->stream));
+  for (int c = 0; c < cols; ++c) rms[c] = std::sqrt(h[c] / (double)n);
+  return VMS_OK;
+}
+
+int vms_mlp_scale_columns(vms_mlp* mlp, int64_t n, int cols, const float* X, const float* mul,
+                          float* out) {
+  if (!mlp || n < 0 || cols < 1 || cols > COLS_MAX || !mul || (n > 0 && (!X || !out)))
+    return mfail(mlp, VMS_ERR_INVALID_ARG, "invalid arguments");
+  if (n == 0) return VMS_OK;
+  MCK(cudaSetDevice(mlp->device));
+  ColMul m{};
+  for (int c = 0; c < cols; ++c) m.m[c] = mul[c];
+  const int64_t blocks = std::min<int64_t>((n * cols + 255) / 256, 4 * (int64_t)vms::sm_count());
+  scale_columns_kernel<<<(unsigned)blocks, 256, 0, mlp->stream>>>(X, n, cols, m, out);
   MCK(cudaGetLastError());
   return VMS_OK;
 }

@@ -60,19 +60,18 @@ class WarmStart:
         """Set the scales from the recorded data (column RMS, floored) and train with Adam on
         shuffled minibatches of nodes from every recorded step. Returns the final loss."""
         import torch
-        X = torch.cat(rec.X)
-        D = torch.cat(rec.D)
+        Xs = torch.cat(rec.X)   # device copies of the recorded steps, scaled in place below
+        Ds = torch.cat(rec.D)
+        sx = np.maximum(self.mlp.column_rms(Xs), 1e-6).astype(np.float32)
+        sd = np.maximum(self.mlp.column_rms(Ds), 1e-9).astype(np.float32)
+        mul_d = 1.0 / sd
         if not self.apply_pressure:
-            D = D.clone()
-            D[:, 3] = 0.0
-        sx = torch.sqrt((X.double() ** 2).mean(dim=0)).clamp_min(1e-6).float()
-        sd = torch.sqrt((D.double() ** 2).mean(dim=0)).clamp_min(1e-9).float()
-        self.scale_in = sx.cpu().numpy()
-        self.scale_out = sd.cpu().numpy()
-        if not self.apply_pressure:
-            self.scale_out[3] = 0.0  # the start keeps the previous step's pressure
-        Xs = (X / sx).contiguous()
-        Ds = (D / sd).contiguous()   # pressure column zero when the pressure is not applied
+            sd[3] = 0.0      # the start keeps the previous step's pressure
+            mul_d[3] = 0.0   # and the network is trained on zero pressure targets
+        self.scale_in = sx
+        self.scale_out = sd
+        self.mlp.scale_columns(Xs, 1.0 / sx, Xs)
+        self.mlp.scale_columns(Ds, mul_d, Ds)
         n = Xs.shape[0]
         rng = np.random.Generator(np.random.PCG64(seed))
         for _ in range(epochs):

@@ -51,6 +51,7 @@ EXPORTS = [
     "vms_set_tuning", "vms_get_tuning", "vms_autotune",
     "vms_mlp_create", "vms_mlp_destroy", "vms_mlp_last_error", "vms_mlp_set_stream",
     "vms_mlp_set_params", "vms_mlp_get_params", "vms_mlp_forward", "vms_mlp_grad", "vms_mlp_adam",
+    "vms_mlp_column_rms", "vms_mlp_scale_columns",
     "vms_node_features", "vms_node_increment", "vms_apply_increment", "vms_shift_time",
     "vms_newton_solve_to", "vms_state_download_prev", "vms_mesh_upload_tet", "vms_tet_rule",
     "vms_set_wait_limit", "vms_csr_download", "vms_fma_throughput",
@@ -138,6 +139,8 @@ def load_library(path: str = LIB_PATH):
         "vms_mlp_forward": (c_int, [p, c_int64, p, p]),
         "vms_mlp_grad": (c_int, [p, c_int64, p, p, p, POINTER(c_double), p]),
         "vms_mlp_adam": (c_int, [p, ctypes.c_float]),
+        "vms_mlp_column_rms": (c_int, [p, c_int64, c_int, p, p]),
+        "vms_mlp_scale_columns": (c_int, [p, c_int64, c_int, p, p, p]),
         "vms_node_features": (c_int, [p, p, p]),
         "vms_node_increment": (c_int, [p, p, p]),
         "vms_apply_increment": (c_int, [p, p, p]),
@@ -481,6 +484,23 @@ class Mlp:
 
     def adam(self, lr: float):
         self._check(self.lib.vms_mlp_adam(self.h, ctypes.c_float(lr)))
+
+    def column_rms(self, X):
+        """Per-column RMS of a device FP32 (n, cols) tensor (FP64 sums), as a numpy array."""
+        n, cols = int(X.shape[0]), int(X.shape[1])
+        out = np.empty(cols, np.float64)
+        self._check(self.lib.vms_mlp_column_rms(self.h, n, cols, _ptr(X, np.float32, n * cols),
+                                                out.ctypes.data))
+        return out
+
+    def scale_columns(self, X, mul, out):
+        """out = X * mul column-wise (device FP32 (n, cols); out may be X)."""
+        n, cols = int(X.shape[0]), int(X.shape[1])
+        m = np.ascontiguousarray(mul, dtype=np.float32)
+        if m.size != cols:
+            raise ValueError("one multiplier per column")
+        self._check(self.lib.vms_mlp_scale_columns(self.h, n, cols, _ptr(X, np.float32, n * cols),
+                                                   m.ctypes.data, _ptr(out, np.float32, n * cols)))
 
 
 def tet_rule(n: int):

@@ -3,7 +3,9 @@ FP64 oracle (oracle/warmstart.py) with the same BF16 weights, the node features 
 oracle's 1-ring mean, and the gain of the trained network over the previous-step start on a
 transient cavity (Newton converges to the same absolute target from both starts).
 
-Tolerances: the kernels accumulate in FP32 over at most 128 terms and use FP32 tanh; outputs
+Tolerances: the kernels accumulate in FP32 over at most 128 terms and use FP32 tanh; the 128-wide
+contractions run on BF16 tensor cores with the FP32 activations split into three BF16 terms
+(forward, D W2^T) or two (H1^T D, three products), about 2^-24 and 2^-16 of each term; outputs
 1e-5 of the largest output, gradients 1e-4 of each block's largest entry, Adam 1e-6.
 """
 import numpy as np
@@ -183,3 +185,26 @@ def test_trained_warm_start_beats_previous_step_start(env):
     it_warm = sum(s.newton_iterations for s in warm)
     assert ratio < 0.5, (ratio, loss)
     assert it_warm <= it_base, (it_warm, it_base)
+
+
+def test_column_rms_and_scaling(env):
+    """The training-data scaling kernels: per-column RMS (FP64 sums) and column multipliers, on a
+    row count that is not a multiple of the block size."""
+    vms, torch, dev = env
+    mlp = vms.Mlp(0)
+    rng = np.random.default_rng(5)
+    X = (rng.normal(size=(3001, 12)) * np.logspace(-3, 2, 12)).astype(np.float32)
+    Xd = torch.from_numpy(X).to(dev)
+    rms = mlp.column_rms(Xd)
+    ref = np.sqrt((X.astype(np.float64) ** 2).mean(axis=0))
+    np.testing.assert_allclose(rms, ref, rtol=1e-12)
+    mul = (1.0 / ref).astype(np.float32)
+    mul[3] = 0.0
+    Yd = torch.empty_like(Xd)
+    mlp.scale_columns(Xd, mul, Yd)
+    np.testing.assert_array_equal(Yd.cpu().numpy(), X * mul)   # one FP32 product per entry
+    mlp.scale_columns(Xd, mul, Xd)                              # in place
+    np.testing.assert_array_equal(Xd.cpu().numpy(), X * mul)
+    with pytest.raises(vms.VmsError):
+        mlp.column_rms(torch.zeros((4, 17), dtype=torch.float32, device=dev))
+    mlp.close()
