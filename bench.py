@@ -32,16 +32,19 @@ UNIT = "elements/s"
 # per-point cost of a direct evaluation of the formulas (geometry and fields ~600 flops, residual
 # ~300, tangent blocks K_vv ~1.7k + K_vp ~0.4k + fine-coupled blocks ~0.5k) plus the condensation
 # (~7k flops per element). The kernels execute fewer flops than these counts where their
-# formulation needs fewer (the residual's monomial form executes 14,791 FP64 flops per element,
-# ncu opcode counts on the 32^3 cavity); `executed` gives those counts.
+# formulation needs fewer; `executed` gives ncu opcode counts (FMA = 2 flops) on the 32^3 cavity:
+# the FP64 residual's line-factored monomial form 11,542, the FP64 tangent's factorised sums
+# 46,312, the fused kernel's FP64 part (residual + the tangent's FP64 K_ff work) 12,082, the
+# tetrahedral kernel 5,894 (21^3 tetrahedral cavity).
 ALG_FLOPS = {"residual": (600 + 300) * 27, "tangent": (600 + 1700 + 400 + 500) * 27 + 7000}
-EXECUTED_FLOPS = {"residual": 14_791, "tangent_fp64": 129_697, "tet": 5_866}
+EXECUTED_FLOPS = {"residual": 11_542, "tangent_fp64": 46_312, "fused_fp64": 12_082, "tet": 5_894}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the
-# same kernels (profiles/); None where the current kernel has not been captured.
-NCU_TRAFFIC_BYTES = {("residual", "cavity32_re400_mixed"): 4_203_776,
-                     ("residual", "cavity32_re400_fp64"): 4_203_776,
-                     ("tangent", "tetcavity21_re400_mixed"): 20_044_288}
+# current kernels on the named workloads (profiles/); no entry where none was taken.
+NCU_TRAFFIC_BYTES = {("fused", "cavity32_re400_mixed"): 67_433_472 + 34_162_432,
+                     ("residual", "cavity32_re400_fp64"): 4_237_824,
+                     ("tangent", "cavity32_re400_fp64"): 119_540_224 + 101_454_336,
+                     ("tangent", "tetcavity21_re400_mixed"): 15_459_584 + 27_136}
 
 WORKLOADS = {
     # the 32^3 jittered lid-driven cavity at Re 400, random state (mixed precision by default)
@@ -486,7 +489,7 @@ def roofline_entries(kern, E, prec, tet, peaks, workload):
                 fpe = ALG_FLOPS[name]
                 out.append({"bound": "alu", "kernel": "fused_assembly", "pipe": pipe, "unit": "TFLOP/s",
                             "part": part, "flops_per_element": fpe,
-                            "executed_flops_per_element": EXECUTED_FLOPS["residual"] if pipe == "fp64" else None,
+                            "executed_flops_per_element": EXECUTED_FLOPS["fused_fp64"] if pipe == "fp64" else None,
                             "ms": ms, "achieved": fpe * E / (ms * 1e-3) / 1e12,
                             "peak": peaks["fp64_tflops"] if pipe == "fp64" else peaks["fp32_tflops"],
                             "traffic": NCU_TRAFFIC_BYTES.get(("fused", workload))})
