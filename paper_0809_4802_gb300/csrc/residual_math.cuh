@@ -61,13 +61,30 @@ VMS_HD void residual_load(const Store& C, const double X[8][3], const double U[8
   }
 }
 
+// 1 / d for a normal d > 0: the approximate reciprocal of the PTX instruction set, then two Newton
+// steps r <- r + r (1 - d r), each of which squares the relative error of the approximation, so
+// that the result is within rounding of 1 / d; fewer FP64 instructions than a division, whose
+// special-value handling the callers do not need (det J > 0 is checked before).
+VMS_HD double recip_pos(double d) {
+#if defined(__CUDA_ARCH__)
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+#else
+  return 1.0 / d;
+#endif
+}
+
 // Quadrature loop. Rcp[32] (node-major 4a+c) and Rf[3] receive the element residual; returns
 // false if det J <= 0 at some point (the offending point then uses det J = 1).
 //
 // The tensor Gauss rule is walked line by line (xi fastest; the table's point order). Along a
 // line eta and zeta are fixed, so every trilinear field is a + xi b with a, b formed once per line:
-// J[.][0] and the polynomial part of G[.][0] (which is also the xi-slope b of v), v's a, p's a and
-// b, and (transient) those of vbar - vbar_n. The test-function sums are factored the same way: a
+// the three columns of J (J[.][0] constant along the line), the polynomial part of G (its first
+// column is also the xi-slope b of v), v's a, p's a and b, and (transient) those of vbar - vbar_n. The test-function sums are factored the same way: a
 // monomial xi^a eta^b zeta^c (or its derivative) is xi^a times a line constant, so each line keeps
 // seven sums per component (src, xi src, P0, P1, xi P1, P2, xi P2) and two for the continuity term,
 // and adds them into the eight monomial sums, which live in the store, once per line.
@@ -83,12 +100,22 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
     for (int j = 0; j < n1; ++j) {
       const int q0 = (k * n1 + j) * n1;
       const double eta = tab.eta(q0), zeta = tab.zeta(q0), ez = tab.ez(q0);
-      // line constants
+      // line constants: along the line J[i][1] = j1a + xi j1b, J[i][2] = j2a + xi j2b, and the
+      // same for the reference velocity gradient (g1a, g1b, g2a, g2b)
       double J0[3], vb[3], va[3], dva[3], dvb[3];
+      double j1a[3], j1b[3], j2a[3], j2b[3], g1a[3], g1b[3], g2a[3], g2b[3];
       VMS_UNROLL
       for (int i = 0; i < 3; ++i) {
         J0[i] = C.get(RC_X + 7 * i + 0) + C.get(RC_X + 7 * i + 3) * eta +
                 C.get(RC_X + 7 * i + 4) * zeta + C.get(RC_X + 7 * i + 6) * ez;
+        j1a[i] = C.get(RC_X + 7 * i + 1) + C.get(RC_X + 7 * i + 5) * zeta;
+        j1b[i] = C.get(RC_X + 7 * i + 3) + C.get(RC_X + 7 * i + 6) * zeta;
+        j2a[i] = C.get(RC_X + 7 * i + 2) + C.get(RC_X + 7 * i + 5) * eta;
+        j2b[i] = C.get(RC_X + 7 * i + 4) + C.get(RC_X + 7 * i + 6) * eta;
+        g1a[i] = C.get(RC_V + 8 * i + 2) + C.get(RC_V + 8 * i + 6) * zeta;
+        g1b[i] = C.get(RC_V + 8 * i + 4) + C.get(RC_V + 8 * i + 7) * zeta;
+        g2a[i] = C.get(RC_V + 8 * i + 3) + C.get(RC_V + 8 * i + 6) * eta;
+        g2b[i] = C.get(RC_V + 8 * i + 5) + C.get(RC_V + 8 * i + 7) * eta;
         vb[i] = C.get(RC_V + 8 * i + 1) + C.get(RC_V + 8 * i + 4) * eta +
                 C.get(RC_V + 8 * i + 5) * zeta + C.get(RC_V + 8 * i + 7) * ez;
         va[i] = C.get(RC_V + 8 * i + 0) + C.get(RC_V + 8 * i + 2) * eta +
@@ -119,12 +146,9 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         double J[3][3];
         VMS_UNROLL
         for (int i = 0; i < 3; ++i) {
-          const double c2 = C.get(RC_X + 7 * i + 1), c3 = C.get(RC_X + 7 * i + 2);
-          const double c4 = C.get(RC_X + 7 * i + 3), c5 = C.get(RC_X + 7 * i + 4);
-          const double c6 = C.get(RC_X + 7 * i + 5), c7 = C.get(RC_X + 7 * i + 6);
           J[i][0] = J0[i];
-          J[i][1] = c2 + c4 * xi + c6 * zeta + c7 * xz;
-          J[i][2] = c3 + c5 * xi + c6 * eta + c7 * xe;
+          J[i][1] = j1a[i] + xi * j1b[i];
+          J[i][2] = j2a[i] + xi * j2b[i];
         }
         double cof[3][3];
         double det = cofactor3(J, cof);
@@ -134,13 +158,10 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         double v[3], G[3][3];
         VMS_UNROLL
         for (int i = 0; i < 3; ++i) {
-          const double c2 = C.get(RC_V + 8 * i + 2), c3 = C.get(RC_V + 8 * i + 3);
-          const double c4 = C.get(RC_V + 8 * i + 4), c5 = C.get(RC_V + 8 * i + 5);
-          const double c6 = C.get(RC_V + 8 * i + 6), c7 = C.get(RC_V + 8 * i + 7);
           v[i] = va[i] + xi * vb[i] + bq * bet[i];
           G[i][0] = vb[i] + bet[i] * db0;
-          G[i][1] = c2 + c4 * xi + c6 * zeta + c7 * xz + bet[i] * db1;
-          G[i][2] = c3 + c5 * xi + c6 * eta + c7 * xe + bet[i] * db2;
+          G[i][1] = g1a[i] + xi * g1b[i] + bet[i] * db1;
+          G[i][2] = g2a[i] + xi * g2b[i] + bet[i] * db2;
         }
         const double p = pa + xi * pb;
 
@@ -160,7 +181,7 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
           VMS_UNROLL
           for (int i = 0; i < 3; ++i) src[i] += tom * (dva[i] + xi * dvb[i]);
         }
-        const double s = wq * nut / det;
+        const double s = wq * nut * recip_pos(det);
         const double A00 = s * (cof[0][0] * cof[0][0] + cof[1][0] * cof[1][0] + cof[2][0] * cof[2][0]);
         const double A11 = s * (cof[0][1] * cof[0][1] + cof[1][1] * cof[1][1] + cof[2][1] * cof[2][1]);
         const double A22 = s * (cof[0][2] * cof[0][2] + cof[1][2] * cof[1][2] + cof[2][2] * cof[2][2]);
