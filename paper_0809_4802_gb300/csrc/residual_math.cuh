@@ -131,15 +131,14 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
                         C.get(RC_P + 6) * ez;
       const double pb = C.get(RC_P + 1) + C.get(RC_P + 4) * eta + C.get(RC_P + 5) * zeta +
                         C.get(RC_P + 7) * ez;
-      // line sums: src, xi src, P0, P1, xi P1, P2, xi P2 (per component), Tp, xi Tp
-      double s0[3] = {0.0, 0.0, 0.0}, s1[3] = {0.0, 0.0, 0.0}, b0[3] = {0.0, 0.0, 0.0};
-      double c0[3] = {0.0, 0.0, 0.0}, c1[3] = {0.0, 0.0, 0.0};
-      double d0[3] = {0.0, 0.0, 0.0}, d1[3] = {0.0, 0.0, 0.0};
-      double t0 = 0.0, t1 = 0.0;
-      VMS_UNROLL
-      for (int ii = 0; ii < n1; ++ii) {
+      // One point of the line: its source term src_i, the fluxes P_al,i paired with the
+      // reference-gradient components of the test functions, and the continuity term Tp.
+      struct Pt {
+        double src[3], P0[3], P1[3], P2[3], Tp;
+      };
+      auto point = [&](int ii, Pt& o) {
         const int q = q0 + ii;
-        const double xi = tab.xi(q), xz = tab.xz(q), xe = tab.xe(q);
+        const double xi = tab.xi(q);
         const double bq = tab.b(q), db0 = tab.db(q, 0), db1 = tab.db(q, 1), db2 = tab.db(q, 2);
         const double wq = tab.w(q);
 
@@ -169,17 +168,16 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         VMS_UNROLL
         for (int al = 0; al < 3; ++al)
           wv[al] = wq * (cof[0][al] * v[0] + cof[1][al] * v[1] + cof[2][al] * v[2]);
-        double src[3];
         VMS_UNROLL
-        for (int i = 0; i < 3; ++i) src[i] = G[i][0] * wv[0] + G[i][1] * wv[1] + G[i][2] * wv[2];
+        for (int i = 0; i < 3; ++i) o.src[i] = G[i][0] * wv[0] + G[i][1] * wv[1] + G[i][2] * wv[2];
         if (FORCE) {
           VMS_UNROLL
-          for (int i = 0; i < 3; ++i) src[i] -= om * f[i];
+          for (int i = 0; i < 3; ++i) o.src[i] -= om * f[i];
         }
         if (TRANSIENT) {
           const double tom = tau * om;
           VMS_UNROLL
-          for (int i = 0; i < 3; ++i) src[i] += tom * (dva[i] + xi * dvb[i]);
+          for (int i = 0; i < 3; ++i) o.src[i] += tom * (dva[i] + xi * dvb[i]);
         }
         const double s = wq * nut * recip_pos(det);
         const double A00 = s * (cof[0][0] * cof[0][0] + cof[1][0] * cof[1][0] + cof[2][0] * cof[2][0]);
@@ -192,22 +190,58 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         double trw = 0.0;
         VMS_UNROLL
         for (int i = 0; i < 3; ++i) {
-          const double P0 = G[i][0] * A00 + G[i][1] * A01 + G[i][2] * A02 - wp * cof[i][0];
-          const double P1 = G[i][0] * A01 + G[i][1] * A11 + G[i][2] * A12 - wp * cof[i][1];
-          const double P2 = G[i][0] * A02 + G[i][1] * A12 + G[i][2] * A22 - wp * cof[i][2];
+          o.P0[i] = G[i][0] * A00 + G[i][1] * A01 + G[i][2] * A02 - wp * cof[i][0];
+          o.P1[i] = G[i][0] * A01 + G[i][1] * A11 + G[i][2] * A12 - wp * cof[i][1];
+          o.P2[i] = G[i][0] * A02 + G[i][1] * A12 + G[i][2] * A22 - wp * cof[i][2];
           trw += G[i][0] * cof[i][0] + G[i][1] * cof[i][1] + G[i][2] * cof[i][2];
-          Rf[i] += bq * src[i] + db0 * P0 + db1 * P1 + db2 * P2;
-          s0[i] += src[i];
-          s1[i] += xi * src[i];
-          b0[i] += P0;
-          c0[i] += P1;
-          c1[i] += xi * P1;
-          d0[i] += P2;
-          d1[i] += xi * P2;
         }
-        const double Tp = -wq * trw;
-        t0 += Tp;
-        t1 += xi * Tp;
+        o.Tp = -wq * trw;
+      };
+      // line sums: src, xi src, P0, P1, xi P1, P2, xi P2 (per component), Tp, xi Tp. The points
+      // are taken in symmetric pairs (-x, x): the Gauss points are symmetric about 0 (the middle
+      // one of an odd rule is 0), b, db1, db2 are even in xi and db0 is odd, so with
+      // u = y(x) + y(-x) and w = y(x) - y(-x) a pair adds u to a sum, x w to a xi-moment, and
+      // b(x) u_src + db0(x) w_P0 + db1(x) u_P1 + db2(x) u_P2 to R_f.
+      double s0[3], s1[3], b0[3], c0[3], c1[3], d0[3], d1[3], t0, t1;
+      VMS_UNROLL
+      for (int pp = 0; pp < n1 / 2; ++pp) {
+        Pt lo, hi;
+        point(pp, lo);
+        point(n1 - 1 - pp, hi);
+        const int qh = q0 + n1 - 1 - pp;
+        const double x = tab.xi(qh), bh = tab.b(qh);
+        const double e0 = tab.db(qh, 0), e1 = tab.db(qh, 1), e2 = tab.db(qh, 2);
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i) {
+          const double us = hi.src[i] + lo.src[i], ws = hi.src[i] - lo.src[i];
+          const double u0 = hi.P0[i] + lo.P0[i], w0 = hi.P0[i] - lo.P0[i];
+          const double u1 = hi.P1[i] + lo.P1[i], w1 = hi.P1[i] - lo.P1[i];
+          const double u2 = hi.P2[i] + lo.P2[i], w2 = hi.P2[i] - lo.P2[i];
+          Rf[i] += bh * us + e0 * w0 + e1 * u1 + e2 * u2;
+          if (pp == 0) {
+            s0[i] = us; s1[i] = x * ws; b0[i] = u0; c0[i] = u1; c1[i] = x * w1; d0[i] = u2;
+            d1[i] = x * w2;
+          } else {
+            s0[i] += us; s1[i] += x * ws; b0[i] += u0; c0[i] += u1; c1[i] += x * w1; d0[i] += u2;
+            d1[i] += x * w2;
+          }
+        }
+        const double ut = hi.Tp + lo.Tp, wt = hi.Tp - lo.Tp;
+        if (pp == 0) { t0 = ut; t1 = x * wt; }
+        else { t0 += ut; t1 += x * wt; }
+      }
+      if (n1 & 1) {
+        // the middle point, xi = 0: no xi-moment, db0 = 0
+        Pt m;
+        point(n1 / 2, m);
+        const int qm = q0 + n1 / 2;
+        const double bm = tab.b(qm), e1 = tab.db(qm, 1), e2 = tab.db(qm, 2);
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i) {
+          Rf[i] += bm * m.src[i] + e1 * m.P1[i] + e2 * m.P2[i];
+          s0[i] += m.src[i]; b0[i] += m.P0[i]; c0[i] += m.P1[i]; d0[i] += m.P2[i];
+        }
+        t0 += m.Tp;
       }
       // the line's contributions to the monomial sums: xi^a eta^b zeta^c src_i and the
       // derivatives d/dxi (P0), d/deta (P1), d/dzeta (P2) of the same monomials
