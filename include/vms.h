@@ -44,7 +44,8 @@ extern "C" {
 #define VMS_ERR_INVALID_ARG -1      /* null pointer, size out of range, bad mode */
 #define VMS_ERR_CUDA -2             /* a CUDA runtime call failed (message has the CUDA error) */
 #define VMS_ERR_OUT_OF_MEMORY -3    /* device allocation failed */
-#define VMS_ERR_NEG_JACOBIAN -4     /* det J <= 0 at a quadrature point of some element */
+#define VMS_ERR_NEG_JACOBIAN -4     /* det J <= 0 (or below the smallest normal FP64 value) at a
+                                      quadrature point of some element */
 #define VMS_ERR_SINGULAR_KFF -5     /* the 3x3 bubble block K_ff of some element is singular */
 #define VMS_ERR_NAN -6              /* a non-finite value appeared in a residual or matrix */
 #define VMS_ERR_KRYLOV_MAXIT -7     /* linear solve reached maxit without meeting its tolerance */

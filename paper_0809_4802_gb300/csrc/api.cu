@@ -124,7 +124,7 @@ void free_mesh(vms_ctx* c) {
   Work& w = c->work;
   dfree(w.values); dfree(w.rhs); dfree(w.elemR); dfree(w.recX); dfree(w.recKcf); dfree(w.recKinv);
   dfree(w.recY); dfree(w.resid); dfree(w.partial); dfree(w.flags); dfree(w.queues);
-  dfree(w.f32.u); dfree(w.f32.beta);
+  dfree(w.f32.u); dfree(w.f32.beta); dfree(w.f32.xhl);
   cudaStream_t aux = w.aux;
   cudaEvent_t fork = w.fork, join = w.join;
   w = Work();
@@ -554,6 +554,7 @@ static int mesh_upload_impl(vms_ctx* ctx, int npe, int64_t n_nodes, const double
   CK(cudaMalloc(&w.recY, sizeof(double) * 3 * n_elems));
   CK(cudaMalloc(&w.f32.u, sizeof(float4) * n_nodes));
   CK(cudaMalloc(&w.f32.beta, sizeof(float) * 3 * n_elems));
+  CK(cudaMalloc(&w.f32.xhl, sizeof(float4) * 2 * n_nodes));
   CK(cudaGetLastError());
   CK(cudaMalloc(&w.resid, sizeof(double) * (4 * n_nodes + 3 * n_elems)));
   CK(cudaMalloc(&w.partial, sizeof(double) * 1024));

@@ -1,6 +1,6 @@
 // Element-level arithmetic of the VMS Newton-Schur method, shared by the residual and tangent
-// kernels. Everything here is __host__ __device__ and free of CUDA intrinsics, so the same code
-// can be exercised on the host. Section and equation names refer to Turner, Nakshatrala and
+// kernels. Everything here is __host__ __device__ and, but for the device form of the reciprocals,
+// free of CUDA intrinsics, so the same code can be exercised on the host. Section and equation names refer to Turner, Nakshatrala and
 // Hjelmstad, "A variational multiscale Newton-Schur approach for the incompressible
 // Navier-Stokes equations".
 #pragma once
@@ -21,6 +21,36 @@ namespace vms {
 #else
 #define VMS_UNROLL
 #endif
+
+// Smallest positive normal FP64 value: a Jacobian determinant below it is treated as
+// non-positive (a degenerate element), so that recip_normal() applies.
+constexpr double DET_MIN = 2.2250738585072014e-308;
+
+// 1 / d for a normal d (|d| >= DET_MIN, finite). On the device: the approximate reciprocal of the
+// PTX instruction set, then two Newton steps r <- r + r (1 - d r), each of which squares the
+// relative error of the approximation, so that the result is within rounding of 1 / d with fewer
+// FP64 instructions than a division.
+VMS_HD double recip_normal(double d) {
+#if defined(__CUDA_ARCH__)
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+#else
+  return 1.0 / d;
+#endif
+}
+
+// 1 / d for finite d != 0: recip_normal(), or the division for a subnormal d (which the
+// approximation would flush to zero).
+VMS_HD double recip(double d) {
+#if defined(__CUDA_ARCH__)
+  if (((__double_as_longlong(d) >> 52) & 0x7ff) == 0) return 1.0 / d;
+#endif
+  return recip_normal(d);
+}
 
 // Local node a <-> lattice corner bits (i,j,k): a = 0..7 <-> 000 100 110 010 001 101 111 011.
 // Forward butterfly: nodal f[8] (local order) -> monomial coefficients, scaled by 8, of

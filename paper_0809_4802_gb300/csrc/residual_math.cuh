@@ -61,23 +61,6 @@ VMS_HD void residual_load(const Store& C, const double X[8][3], const double U[8
   }
 }
 
-// 1 / d for a normal d > 0: the approximate reciprocal of the PTX instruction set, then two Newton
-// steps r <- r + r (1 - d r), each of which squares the relative error of the approximation, so
-// that the result is within rounding of 1 / d; fewer FP64 instructions than a division, whose
-// special-value handling the callers do not need (det J > 0 is checked before).
-VMS_HD double recip_pos(double d) {
-#if defined(__CUDA_ARCH__)
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-#else
-  return 1.0 / d;
-#endif
-}
-
 // Quadrature loop. Rcp[32] (node-major 4a+c) and Rf[3] receive the element residual; returns
 // false if det J <= 0 at some point (the offending point then uses det J = 1).
 //
@@ -151,7 +134,7 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         }
         double cof[3][3];
         double det = cofactor3(J, cof);
-        if (!(det > 0.0)) { ok = false; det = 1.0; }
+        if (!(det >= DET_MIN)) { ok = false; det = 1.0; }
         const double om = wq * det;
 
         double v[3], G[3][3];
@@ -179,7 +162,7 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
           VMS_UNROLL
           for (int i = 0; i < 3; ++i) o.src[i] += tom * (dva[i] + xi * dvb[i]);
         }
-        const double s = wq * nut * recip_pos(det);
+        const double s = wq * nut * recip_normal(det);
         const double A00 = s * (cof[0][0] * cof[0][0] + cof[1][0] * cof[1][0] + cof[2][0] * cof[2][0]);
         const double A11 = s * (cof[0][1] * cof[0][1] + cof[1][1] * cof[1][1] + cof[2][1] * cof[2][1]);
         const double A22 = s * (cof[0][2] * cof[0][2] + cof[1][2] * cof[1][2] + cof[2][2] * cof[2][2]);

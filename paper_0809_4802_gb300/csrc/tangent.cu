@@ -76,7 +76,7 @@ __device__ void kff_fp64(int lane, int nq, const int nd[8], const double4_32a* _
     double cof[3][3];
     double det = cofactor3(J, cof);
     if (!(det > 0.0)) det = 1.0;  // the FP32 pass has flagged the element already
-    const double r = 1.0 / det;
+    const double r = recip(det);
     double d[3];
     VMS_UNROLL
     for (int j = 0; j < 3; ++j) d[j] = (__ldg(db) * cof[j][0] + __ldg(db + 1) * cof[j][1] + __ldg(db + 2) * cof[j][2]) * r;
@@ -137,7 +137,8 @@ __device__ __forceinline__ void tangent_element(
     const void* __restrict__ ext0, const void* __restrict__ ext1,
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn,
     const T* __restrict__ beta, int nq, T nut, T tau, const double* __restrict__ nu_e,
-    double visc_factor, const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
+    double visc_factor, const double4_32a* __restrict__ xyz64, const float4* __restrict__ xhl,
+    const double4_32a* __restrict__ u64,
     const double* __restrict__ beta64, const double* __restrict__ tab64,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
     const uint32_t* __restrict__ dir_mask, T* __restrict__ values, T* __restrict__ recX,
@@ -148,17 +149,20 @@ __device__ __forceinline__ void tangent_element(
   if (lane < 8) {
     const int nd = conn[8 * e + lane];
     W.nd[lane] = nd;
-    const double4_32a x = xyz64[nd];
     const auto w = u[nd];
     if constexpr (sizeof(T) == 4) {
-      // FP32 geometry from the coordinates relative to the element's first node, taken in
-      // FP64: J is unchanged (the basis gradients sum to zero), while FP32 copies of absolute
-      // coordinates far from the origin would resolve the element's extent only to
-      // |x| * 6e-8 / h (2e-5 at x = 30 with h = 1/13)
-      W.X[lane][0] = (float)(x.x - __shfl_sync(0xffu, x.x, 0));
-      W.X[lane][1] = (float)(x.y - __shfl_sync(0xffu, x.y, 0));
-      W.X[lane][2] = (float)(x.z - __shfl_sync(0xffu, x.z, 0));
+      // FP32 geometry from the coordinates relative to the element's first node: J is unchanged
+      // (the basis gradients sum to zero), while FP32 copies of absolute coordinates far from the
+      // origin would resolve the element's extent only to |x| * 6e-8 / h (2e-5 at x = 30 with
+      // h = 1/13). With x = hi + lo (FP32 parts), (hi - hi_0) + (lo - lo_0) is the relative
+      // coordinate to FP32 rounding: hi - hi_0 is exact where the two agree in sign and exponent
+      // range (far from the origin) and rounds at the level of |x| ~ h near it; no FP64 arithmetic.
+      const float4 h = xhl[2 * nd], l = xhl[2 * nd + 1];
+      W.X[lane][0] = (h.x - __shfl_sync(0xffu, h.x, 0)) + (l.x - __shfl_sync(0xffu, l.x, 0));
+      W.X[lane][1] = (h.y - __shfl_sync(0xffu, h.y, 0)) + (l.y - __shfl_sync(0xffu, l.y, 0));
+      W.X[lane][2] = (h.z - __shfl_sync(0xffu, h.z, 0)) + (l.z - __shfl_sync(0xffu, l.z, 0));
     } else {
+      const double4_32a x = xyz64[nd];
       W.X[lane][0] = x.x; W.X[lane][1] = x.y; W.X[lane][2] = x.z;
     }
     W.V[lane][0] = w.x; W.V[lane][1] = w.y; W.V[lane][2] = w.z;
@@ -314,7 +318,8 @@ template <typename T, bool ELEM_OUT, bool ATOMIC, int WARPS, int ENG = 0>
 __global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : (ENG == TS_ENGINE ? 2 : 4)) tangent_kernel(
     const typename NodeVec<T>::type* __restrict__ u, const int32_t* __restrict__ conn, const T* __restrict__ beta, const T* __restrict__ gtab,
     int nq, T nut, T tau, const double* __restrict__ nu_e, double visc_factor,
-    const double4_32a* __restrict__ xyz64, const double4_32a* __restrict__ u64,
+    const double4_32a* __restrict__ xyz64, const float4* __restrict__ xhl,
+    const double4_32a* __restrict__ u64,
     const double* __restrict__ beta64, const double* __restrict__ tab64, int64_t first,
     int64_t count, const int32_t* __restrict__ elem_list,
     const int32_t* __restrict__ blk, const int32_t* __restrict__ rowlen,
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(WARPS * 32, ENG == 0 ? 1 : (ENG == TS_ENGINE ?
   for (int64_t it = (int64_t)blockIdx.x * WARPS + warp; it < count; it += total) {
     const int64_t e = elem_list ? (int64_t)elem_list[first + it] : first + it;
     tangent_element<T, ELEM_OUT, ATOMIC, 32, ENG>(lane, it, e, W, tab, tcw, ext0, ext1, u, conn, beta, nq, nut, tau, nu_e,
-                                         visc_factor, xyz64, u64, beta64, tab64, blk, rowlen,
+                                         visc_factor, xyz64, xhl, u64, beta64, tab64, blk, rowlen,
                                          dir_mask, values, recX, recKcf, recKinv, oS, oKcc, oKcf,
                                          oKfc, oKff, flags);
   }
@@ -389,7 +394,8 @@ __global__ void __launch_bounds__(FUSED_WARPS * 32, 1) fused_assembly_kernel(
     const double4_32a* __restrict__ xyz, const double4_32a* __restrict__ u64,
     const double4_32a* __restrict__ uprev, const int32_t* __restrict__ conn,
     const double* __restrict__ beta64, KParams kp, const QpRow* __restrict__ qp,
-    double* __restrict__ elemR, const float4* __restrict__ u32, const float* __restrict__ beta32,
+    double* __restrict__ elemR, const float4* __restrict__ u32, const float4* __restrict__ xhl32,
+    const float* __restrict__ beta32,
     const float* __restrict__ gtab, float nut, float tau, const int32_t* __restrict__ blk,
     const int32_t* __restrict__ rowlen, const uint32_t* __restrict__ dir_mask,
     float* __restrict__ values, float* __restrict__ recX, float* __restrict__ recKcf,
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(FUSED_WARPS * 32, 1) fused_assembly_kernel(
     const int64_t end = (int64_t)base + FUSED_TCLAIM < n_elems ? (int64_t)base + FUSED_TCLAIM : n_elems;
     for (int64_t e = (int64_t)base; e < end; ++e)
       tangent_element<float, false, true, FUSED_QCH>(lane, e, e, W, tab, nullptr, nullptr, nullptr, u32, conn, beta32, nq, nut, tau,
-                                          kp.nu_e, kp.visc_factor, xyz, u64, beta64, kp.tab64, blk,
+                                          kp.nu_e, kp.visc_factor, xyz, xhl32, u64, beta64, kp.tab64, blk,
                                           rowlen, dir_mask, values, recX, recKcf, recKinv, nullptr,
                                           nullptr, nullptr, nullptr, nullptr, flags);
   }
@@ -445,7 +451,7 @@ int launch_fused_assembly(const Mesh& m, const State& s, const Fp32Copy& c32, co
   auto launch = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<(unsigned)sm_count(), FUSED_WARPS * 32, smem, st>>>(
-        m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, elemR, c32.u, c32.beta, tab32,
+        m.xyz, s.u, s.u_prev, m.conn, s.beta, kp, qp, elemR, c32.u, c32.xhl, c32.beta, tab32,
         (float)kp.nut, (float)kp.tau, m.blk, m.rowlen, m.dir_mask, reinterpret_cast<float*>(o.values),
         reinterpret_cast<float*>(o.recX), reinterpret_cast<float*>(o.recKcf), o.recKinv, m.n_elems,
         queues, flags);
@@ -495,15 +501,20 @@ __global__ void __launch_bounds__(128) finish_kernel(
   }
 }
 
-// FP32 copies of the nodal state and bubble coefficients for the mixed-precision tangent (its
-// geometry comes from the FP64 coordinates).
+// FP32 copies of the nodal state and bubble coefficients for the mixed-precision tangent, and the
+// coordinates as FP32 high and low parts (x = hi + lo to about 2^-48 |x|) for its geometry.
 __global__ void to_fp32_kernel(const double4_32a* __restrict__ u, const double* __restrict__ beta,
-                               float4* __restrict__ u32, float* __restrict__ beta32,
+                               const double4_32a* __restrict__ xyz, float4* __restrict__ u32,
+                               float* __restrict__ beta32, float4* __restrict__ xhl,
                                int64_t n_nodes, int64_t n_elems) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += stride) {
     const double4_32a w = u[i];
     u32[i] = make_float4((float)w.x, (float)w.y, (float)w.z, (float)w.w);
+    const double4_32a x = xyz[i];
+    const float hx = (float)x.x, hy = (float)x.y, hz = (float)x.z;
+    xhl[2 * i] = make_float4(hx, hy, hz, 0.f);
+    xhl[2 * i + 1] = make_float4((float)(x.x - hx), (float)(x.y - hy), (float)(x.z - hz), 0.f);
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_elems; i += stride)
     beta32[i] = (float)beta[i];
@@ -513,8 +524,8 @@ int launch_to_fp32(const Mesh& m, const State& s, const Fp32Copy& c, cudaStream_
   const int64_t n = m.n_nodes > 3 * m.n_elems ? m.n_nodes : 3 * m.n_elems;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
-  to_fp32_kernel<<<(unsigned)blocks, 256, 0, st>>>(s.u, s.beta, c.u, c.beta, m.n_nodes,
-                                                   m.n_elems);
+  to_fp32_kernel<<<(unsigned)blocks, 256, 0, st>>>(s.u, s.beta, m.xyz, c.u, c.beta, c.xhl,
+                                                   m.n_nodes, m.n_elems);
   return 1;
 }
 
@@ -537,7 +548,7 @@ static void launch_w(const Mesh& m, const State& s, const Fp32Copy& c32, const K
     u = s.u; beta = s.beta;
   }
   kern<<<(unsigned)blocks, WARPS * 32, smem, st>>>(
-      u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, s.u,
+      u, m.conn, beta, tab, nq, T(kp.nut), T(kp.tau), kp.nu_e, kp.visc_factor, m.xyz, c32.xhl, s.u,
       s.beta, kp.tab64, first, count, elem_list, m.blk,
       m.rowlen, m.dir_mask, reinterpret_cast<T*>(o.values), reinterpret_cast<T*>(o.recX),
       reinterpret_cast<T*>(o.recKcf), o.recKinv, o.S, o.Kcc, o.Kcf, o.Kfc, o.Kff, flags, kp.ts_basis,

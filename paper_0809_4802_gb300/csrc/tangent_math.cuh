@@ -319,7 +319,7 @@ VMS_HD void tan_phase3d(int lane, WarpArea<T>& W) {
   uint64_t db;
   memcpy(&db, &det, sizeof db);
   const bool bad = (db << 1) == 0 || ((db >> 52) & 0x7ffu) == 0x7ffu;
-  const double r = bad ? 0.0 : 1.0 / det;
+  const double r = bad ? 0.0 : recip(det);
   if (lane < 9) {
     const double v = W.cof[3 * (lane % 3) + lane / 3] * r;
     W.Kinv[lane] = v;

@@ -81,8 +81,8 @@ __device__ __forceinline__ void ts_phase1(int lane, int nq, WarpArea<double>& W,
     }
   double cof[3][3];
   double det = cofactor3(J, cof);
-  if (!(det > 0.0)) { W.flag = 1u; det = 1.0; }
-  const double rdet = 1.0 / det;
+  if (!(det >= DET_MIN)) { W.flag = 1u; det = 1.0; }
+  const double rdet = recip_normal(det);
   double Ji[3][3];  // (J^-1)[al][j] = cof[j][al] / det
 #pragma unroll
   for (int al = 0; al < 3; ++al)

@@ -234,10 +234,10 @@ __device__ __forceinline__ void tet_element(int a, int64_t e, const double4_32a*
 #pragma unroll
     for (int al = 0; al < 3; ++al) J[i][al] = X[al + 1][i] - X[0][i];
   double det = cofactor3(J, cof);
-  E.ok = det > 0.0;
+  E.ok = det >= DET_MIN;
   if (!E.ok) det = 1.0;
   E.det = det;
-  const double r = 1.0 / det;
+  const double r = recip_normal(det);
 #pragma unroll
   for (int al = 0; al < 3; ++al)
 #pragma unroll

@@ -103,6 +103,7 @@ struct State {
 struct Fp32Copy {
   float4* u = nullptr;        // n_nodes (v, p) in FP32
   float* beta = nullptr;      // n_elems * 3
+  float4* xhl = nullptr;      // n_nodes * 2: FP32 high and low parts of the coordinates (x = hi + lo)
 };
 
 struct Work {
