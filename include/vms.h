@@ -71,6 +71,8 @@ extern "C" {
 /* ---- preconditioners of the Krylov solve (vms_set_preconditioner) ---------------------------- */
 #define VMS_PRECOND_ILU0 0          /* block ILU(0), 4x4 node blocks, natural node order (default) */
 #define VMS_PRECOND_BLOCK_JACOBI 1  /* inverses of the 4x4 diagonal node blocks */
+#define VMS_PRECOND_ILU0_FALLBACK 2 /* ILU(0); a solve that ends at maxit (or on a zero pivot) is
+                                       repeated from zero with block Jacobi and GMRES(480) */
 
 /* ---- scatter modes (vms_params.scatter_mode) ----------------------------------------------- */
 #define VMS_SCATTER_ATOMIC 0  /* one launch, atomic adds into CSR values (order not fixed) */
@@ -261,8 +263,11 @@ int vms_autotune(vms_ctx* ctx, int repeats, vms_tuning* best);
  * (vms_profile_enable). Results are those of the same calls without the graph. */
 int vms_set_graph(vms_ctx* ctx, int enable);
 
-/* Choose the right preconditioner of vms_solve / vms_newton_*: VMS_PRECOND_ILU0 (default) or
- * VMS_PRECOND_BLOCK_JACOBI. Section 6 solved every Newton system with a Krylov solver at its
+/* Choose the right preconditioner of vms_solve / vms_solve_instance / vms_newton_*:
+ * VMS_PRECOND_ILU0 (default), VMS_PRECOND_BLOCK_JACOBI, or VMS_PRECOND_ILU0_FALLBACK (ILU(0), and
+ * for a solve that does not converge, a second solve from zero with block Jacobi and the longest
+ * cycle: on coarse high-Reynolds systems the ILU(0) pivots lose all size while the exact 4x4
+ * block inverses stay stable; *iters then counts both solves). Section 6 solved every Newton system with a Krylov solver at its
  * library defaults; on one process that default preconditioner is an incomplete LU factorisation
  * without fill, which VMS_PRECOND_ILU0 computes on 4x4 node blocks (it is refactored at every
  * solve of a newly assembled system). ILU(0) needs at most 32 neighbours per node

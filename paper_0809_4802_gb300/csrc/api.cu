@@ -331,7 +331,7 @@ int vms_set_stream(vms_ctx* ctx, void* stream) {
 
 int vms_set_preconditioner(vms_ctx* ctx, int kind) {
   if (!ctx) return VMS_ERR_INVALID_ARG;
-  if (kind != VMS_PRECOND_ILU0 && kind != VMS_PRECOND_BLOCK_JACOBI)
+  if (kind != VMS_PRECOND_ILU0 && kind != VMS_PRECOND_BLOCK_JACOBI && kind != VMS_PRECOND_ILU0_FALLBACK)
     return fail(ctx, VMS_ERR_INVALID_ARG, "unknown preconditioner");
   ctx->precond = kind;
   return VMS_OK;

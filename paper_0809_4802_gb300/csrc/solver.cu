@@ -696,7 +696,7 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
 
 // Solve S du = -rhs into w.x (FP64). Mixed: FP32 GMRES inside FP64 iterative refinement.
 static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit, int restart,
-                        int restart_cap, int* iters_out, double* rel_out) {
+                        int restart_cap, int* iters_out, double* rel_out, bool block_jacobi = false) {
   const Mesh& m = ctx_mesh(ctx);
   Work& wk = ctx_work(ctx);
   SolverWork& w = ctx_solver(ctx);
@@ -706,29 +706,28 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
   if (restart < 1 || restart > MAX_RESTART || maxit < 1 || !(rtol > 0.0))
     return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "invalid solver parameters");
   if (int rc = ensure_solver(ctx, restart)) return rc;
-  const int kind = ctx_precond(ctx);
-  w.use_ilu = kind == VMS_PRECOND_ILU0;
+  w.use_ilu = !block_jacobi && ctx_precond(ctx) != VMS_PRECOND_BLOCK_JACOBI;
   // the preconditioner covers the whole matrix (its blocks are independent) and is set up once
-  // per assembly and kind
-  if (w.precond_for != wk.assembly_id || w.precond_kind != kind || (w.use_ilu && !w.ilu.factored)) {
+  // per assembly; the ILU(0) factor and the block-Jacobi inverses are kept apart, so that a
+  // block-Jacobi solve does not discard the factor the other instances use
+  if (w.use_ilu && (w.ilu_for != wk.assembly_id || !w.ilu.factored)) {
     KScope k(ctx, VMS_K_PRECOND);
-    w.precond_for = wk.assembly_id;
-    w.precond_kind = kind;
-    if (w.use_ilu) {
-      int launched = 0;
-      const int rc = ilu_factor(ctx, w.ilu, m, f32, wk.values, st, &launched);
-      k.add(launched);
-      if (rc) {
-        w.precond_for = 0;
-        return rc;
-      }
-    } else if (f32) {
-      block_diag_inv_kernel<float><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, m.n_nodes, w.Dinv);
-      k.add(1);
-    } else {
-      block_diag_inv_kernel<double><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, m.n_nodes, w.Dinv);
-      k.add(1);
+    w.ilu_for = wk.assembly_id;
+    int launched = 0;
+    const int rc = ilu_factor(ctx, w.ilu, m, f32, wk.values, st, &launched);
+    k.add(launched);
+    if (rc) {
+      w.ilu_for = 0;
+      return rc;
     }
+  } else if (!w.use_ilu && w.dinv_for != wk.assembly_id) {
+    KScope k(ctx, VMS_K_PRECOND);
+    w.dinv_for = wk.assembly_id;
+    if (f32)
+      block_diag_inv_kernel<float><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, m.n_nodes, w.Dinv);
+    else
+      block_diag_inv_kernel<double><<<grid_for(m.n_nodes), 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, m.n_nodes, w.Dinv);
+    k.add(1);
   }
   // b = -rhs (FP64) in w.r
   {
@@ -957,6 +956,17 @@ static int solve_impl(vms_ctx* ctx, const SysRange& R, int64_t instance, double 
   int it = 0;
   double r = 0.0;
   int rc = linear_solve(ctx, R, rtol, maxit, restart, restart_cap, &it, &r);
+  if ((rc == VMS_ERR_KRYLOV_MAXIT || rc == VMS_ERR_ZERO_PIVOT) &&
+      ctx_precond(ctx) == VMS_PRECOND_ILU0_FALLBACK && !(rc == VMS_ERR_KRYLOV_MAXIT && r < accept_below)) {
+    // ILU(0) loses all accuracy where its pivots do (growth factors of 1e7-1e16 were measured on
+    // coarse high-Reynolds systems): repeat the solve from zero with the block-Jacobi
+    // preconditioner, whose 4x4 inverses are exact, and the longest cycle
+    int it2 = 0;
+    double r2 = 0.0;
+    rc = linear_solve(ctx, R, rtol, maxit, MAX_RESTART, MAX_RESTART, &it2, &r2, true);
+    it += it2;
+    r = r2;
+  }
   ctx_solver_stats(ctx)[0] += 1;
   ctx_solver_stats(ctx)[1] += it;
   if (iters) *iters = it;

@@ -32,9 +32,9 @@ struct SolverWork {
   double* xb = nullptr;      // n: refinement iterate before the last FP32 correction
   double* rb = nullptr;      // n: its FP64 residual
   Ilu ilu;                   // ILU(0) pattern, factor and sweep work
-  bool use_ilu = false;      // preconditioner of the current solve
-  uint64_t precond_for = 0;  // assembly the preconditioner was set up for (0: none)
-  int precond_kind = -1;     // VMS_PRECOND_* it was set up as
+  bool use_ilu = false;      // preconditioner of the current solve: ILU(0) or block Jacobi
+  uint64_t ilu_for = 0;      // assembly the ILU(0) factor was computed for (0: none)
+  uint64_t dinv_for = 0;     // assembly the block-Jacobi inverses were computed for (0: none)
   int restart = 0;
   int64_t n = 0;
 };

@@ -39,6 +39,7 @@ SCATTER_ATOMIC = 0
 SCATTER_COLOUR = 1
 PRECOND_ILU0 = 0
 PRECOND_BLOCK_JACOBI = 1
+PRECOND_ILU0_FALLBACK = 2
 
 # every symbol include/vms.h declares
 EXPORTS = [

@@ -231,3 +231,27 @@ def test_ilu0_row_with_more_than_16_lower_blocks(vms, prec):
     assert np.linalg.norm(G @ du + rhs) <= 2e-10 * np.linalg.norm(rhs)
     assert np.abs(du - du_ref).max() <= 1e-5 * np.abs(du_ref).max()
     ctx.close()
+
+
+def test_block_jacobi_fallback_solves_a_system_whose_ilu0_is_unstable():
+    """A coarse high-Reynolds cavity (12^3, Re 719, random state, one of the batch's instances):
+    its ILU(0) factor is unstable (CPU study: |M^-1 v| / |A^-1 v| ~ 1e7 and more) and GMRES with it
+    stalls; VMS_PRECOND_ILU0_FALLBACK repeats the solve with block Jacobi and GMRES(480), which
+    reaches the batch's per-instance target of 1e-2."""
+    from paper_0809_4802_gb300 import build, vms
+    build.build()
+    vms.load_library()
+    wl = inputs.cavity_workload(12, 719.1888472918997, jitter_frac=0.15, state="random", seed=1021)
+    ctx = vms.Context(0, vms.PREC_MIXED)
+    ctx.mesh_upload(wl.mesh.xyz, wl.mesh.conn, wl.bc.dofs, wl.bc.vals)
+    ctx.set_params(wl.nu)
+    ctx.state_upload(wl.u, wl.beta)
+    ctx.assemble()
+    with pytest.raises(vms.VmsError) as ei:
+        ctx.solve(rtol=1e-2, maxit=3000, restart=150, update=False)
+    assert ei.value.code == vms.ERR_KRYLOV_MAXIT
+    ctx.set_preconditioner(vms.PRECOND_ILU0_FALLBACK)
+    it, rel = ctx.solve(rtol=1e-2, maxit=3000, restart=150, update=False)
+    assert rel <= 1e-2 and it > 3000   # both solves counted
+    ctx.set_preconditioner(vms.PRECOND_ILU0)
+    ctx.close()
