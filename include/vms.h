@@ -179,6 +179,18 @@ int vms_get_csr(vms_ctx* ctx, vms_csr_view* out);
  * or FP32) and rhs (4 n_nodes doubles). Synchronises the context's stream. Errors: VMS_ERR_STATE
  * (nothing assembled), VMS_ERR_CUDA. */
 int vms_csr_download(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* values, double* rhs);
+/* Asynchronous form of vms_csr_download, for pipelines that overlap the transfer of one assembled
+ * system with the assembly of the next. The values and the right-hand side are first copied into
+ * a device staging buffer on the context's stream (so the next vms_assemble_newton_schur may
+ * overwrite the originals), then to the caller's buffers on a copy stream of the library; the call
+ * returns without waiting. vms_csr_download_wait blocks until the copies have landed. A new
+ * vms_csr_download_async, a new mesh and vms_destroy first wait for a pending one. The host
+ * buffers should be page-locked for the copy to run beside the next assembly; they must stay
+ * valid until the wait. The staging buffer (the size of the values and the right-hand side) is
+ * allocated on the first call. Not part of the paper's method: a transfer pipeline for serving.
+ * Errors: VMS_ERR_STATE (nothing assembled), VMS_ERR_OUT_OF_MEMORY, VMS_ERR_CUDA. */
+int vms_csr_download_async(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* values, double* rhs);
+int vms_csr_download_wait(vms_ctx* ctx);
 
 /* Residual-only evaluation in FP64 (Section 4.1 residual vectors, assembled): writes the 2-norm
  * of [R_c, R_p on free dofs; R_f of every element] to *norm (host). If R (host or device, may

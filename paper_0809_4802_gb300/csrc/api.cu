@@ -51,6 +51,15 @@ struct vms_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t graph_launches[VMS_K_COUNT] = {};
+  // vms_csr_download_async: device snapshot of the assembled system and its copy stream
+  struct Stage {
+    void* values = nullptr;
+    double* rhs = nullptr;
+    size_t vbytes = 0, rbytes = 0;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t snap = nullptr, done = nullptr;
+    bool pending = false;
+  } stage;
 };
 
 namespace vms {
@@ -107,7 +116,30 @@ void dfree(P*& p) {
   p = nullptr;
 }
 
+// Waits for a pending vms_csr_download_async (its copy reads the mesh pattern and the snapshot).
+int stage_wait(vms_ctx* c) {
+  if (!c->stage.pending) return VMS_OK;
+  c->stage.pending = false;
+  const cudaError_t e = cudaEventSynchronize(c->stage.done);
+  if (e != cudaSuccess) {
+    c->err = cudaGetErrorString(e);
+    return VMS_ERR_CUDA;
+  }
+  return VMS_OK;
+}
+
+void stage_free(vms_ctx* c) {
+  stage_wait(c);
+  auto& S = c->stage;
+  dfree(S.values); dfree(S.rhs);
+  if (S.copy) cudaStreamDestroy(S.copy);
+  if (S.snap) cudaEventDestroy(S.snap);
+  if (S.done) cudaEventDestroy(S.done);
+  S = vms_ctx::Stage();
+}
+
 void free_mesh(vms_ctx* c) {
+  stage_free(c);
   Mesh& m = c->mesh;
   dfree(m.xyz); dfree(m.conn); dfree(m.rowptr); dfree(m.colidx); dfree(m.blk); dfree(m.rowlen);
   dfree(m.dir_mask); dfree(m.dir_dof); dfree(m.dir_val); dfree(m.diag_pos); dfree(m.colour_order);
@@ -790,6 +822,54 @@ int vms_csr_download(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* value
   if (rhs) CK(cudaMemcpyAsync(rhs, ctx->work.rhs, sizeof(double) * 4 * m.n_nodes, cudaMemcpyDefault, st));
   CK(cudaStreamSynchronize(st));
   return VMS_OK;
+}
+
+int vms_csr_download_async(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* values, double* rhs) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  if (!ctx->work.assembled) return fail(ctx, VMS_ERR_STATE, "nothing assembled");
+  CK(cudaSetDevice(ctx->device));
+  if (int rc = stage_wait(ctx)) return rc;
+  const Mesh& m = ctx->mesh;
+  auto& S = ctx->stage;
+  cudaStream_t st = ctx->stream;
+  const size_t vbytes = (size_t)m.nnz * (fp32_mode(ctx) ? sizeof(float) : sizeof(double));
+  const size_t rbytes = sizeof(double) * 4 * m.n_nodes;
+  if (!S.copy) {
+    CK(cudaStreamCreateWithFlags(&S.copy, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&S.snap, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
+  }
+  if (S.vbytes != vbytes) {
+    dfree(S.values);
+    S.vbytes = 0;
+    CK(cudaMalloc(&S.values, vbytes));
+    S.vbytes = vbytes;
+  }
+  if (S.rbytes != rbytes) {
+    dfree(S.rhs);
+    S.rbytes = 0;
+    CK(cudaMalloc(&S.rhs, rbytes));
+    S.rbytes = rbytes;
+  }
+  // the snapshot is ordered after the assembly on the context's stream, and the next assembly
+  // after the snapshot; the copy to the host runs on its own stream
+  if (values) CK(cudaMemcpyAsync(S.values, ctx->work.values, vbytes, cudaMemcpyDeviceToDevice, st));
+  if (rhs) CK(cudaMemcpyAsync(S.rhs, ctx->work.rhs, rbytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaEventRecord(S.snap, st));
+  CK(cudaStreamWaitEvent(S.copy, S.snap, 0));
+  if (rowptr) CK(cudaMemcpyAsync(rowptr, m.rowptr, sizeof(int32_t) * (4 * m.n_nodes + 1), cudaMemcpyDefault, S.copy));
+  if (colidx) CK(cudaMemcpyAsync(colidx, m.colidx, sizeof(int32_t) * m.nnz, cudaMemcpyDefault, S.copy));
+  if (values) CK(cudaMemcpyAsync(values, S.values, vbytes, cudaMemcpyDefault, S.copy));
+  if (rhs) CK(cudaMemcpyAsync(rhs, S.rhs, rbytes, cudaMemcpyDefault, S.copy));
+  CK(cudaEventRecord(S.done, S.copy));
+  S.pending = true;
+  return VMS_OK;
+}
+
+int vms_csr_download_wait(vms_ctx* ctx) {
+  if (!ctx) return VMS_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  return stage_wait(ctx);
 }
 
 int vms_residual(vms_ctx* ctx, double* norm, double* R) {

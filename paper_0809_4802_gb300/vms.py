@@ -55,7 +55,8 @@ EXPORTS = [
     "vms_mlp_column_rms", "vms_mlp_scale_columns",
     "vms_node_features", "vms_node_increment", "vms_apply_increment", "vms_shift_time",
     "vms_newton_solve_to", "vms_state_download_prev", "vms_mesh_upload_tet", "vms_tet_rule",
-    "vms_set_wait_limit", "vms_csr_download", "vms_fma_throughput",
+    "vms_set_wait_limit", "vms_csr_download", "vms_fma_throughput", "vms_csr_download_async",
+    "vms_csr_download_wait",
 ]
 MLP_IN, MLP_WIDTH, MLP_OUT, MLP_PARAMS = 12, 128, 4, 18692
 K_NAMES = ["residual", "tangent", "fill", "dirichlet", "reduce", "spmv", "krylov", "precond", "fused"]
@@ -155,6 +156,8 @@ def load_library(path: str = LIB_PATH):
                                               POINTER(VmsParams), p, p, p]),
         "vms_set_wait_limit": (c_int, [p, c_int64]),
         "vms_csr_download": (c_int, [p, p, p, p, p]),
+        "vms_csr_download_async": (c_int, [p, p, p, p, p]),
+        "vms_csr_download_wait": (c_int, [p]),
         "vms_fma_throughput": (c_int, [c_int, c_int, POINTER(c_double)]),
     }
     for name, (res, args) in sig.items():
@@ -302,6 +305,16 @@ class Context:
         vdt = np.float32 if self.precision != PREC_FP64 else np.float64
         self._check(self.lib.vms_csr_download(self.h, _ptr(rowptr, np.int32), _ptr(colidx, np.int32),
                                               _ptr(values, vdt), _ptr(rhs, np.float64)))
+
+    def csr_download_async(self, rowptr=None, colidx=None, values=None, rhs=None):
+        """Start copying the last assembled system into caller buffers (page-locked host buffers
+        overlap with the next assembly); csr_download_wait() blocks until it has landed."""
+        vdt = np.float32 if self.precision != PREC_FP64 else np.float64
+        self._check(self.lib.vms_csr_download_async(self.h, _ptr(rowptr, np.int32), _ptr(colidx, np.int32),
+                                                    _ptr(values, vdt), _ptr(rhs, np.float64)))
+
+    def csr_download_wait(self):
+        self._check(self.lib.vms_csr_download_wait(self.h))
 
     def set_wait_limit(self, polls: int):
         """Polls of one device-side wait of the ILU(0) kernels before the solve gives up
