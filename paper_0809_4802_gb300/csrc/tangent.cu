@@ -186,7 +186,7 @@ __device__ __forceinline__ void tangent_element(
     // FP64 factorised sums (nq = 8 or 27, checked on the host): ext0 = one-dimensional basis
     // (shared), ext1 = plan of the partial sums (global)
     TsArea& C = *reinterpret_cast<TsArea*>(tcw);
-    ts_phase1(lane, nq, W, C, tab, nut_e, tau, A);
+    ts_phase1(lane, nq, W, C, tab, reinterpret_cast<const double*>(ext0), nut_e, tau, A);
     __syncwarp();
     ts_sums(lane, nq, C, reinterpret_cast<const double*>(ext0), reinterpret_cast<const uint32_t*>(ext1));
     __syncwarp();
@@ -591,6 +591,7 @@ bool ts_tables(int n1, const double* x, std::vector<double>& basis, std::vector<
       basis[4 * (TS_ROW_PSI + sm) + i] = phi(sm == 2, x[i]) * phi(sm >= 1, x[i]);
     for (int b = 0; b < 2; ++b) basis[4 * (TS_ROW_PHI + b) + i] = phi(b, x[i]);
     basis[4 * TS_ROW_ONE + i] = 1.0;
+    basis[4 * TS_ROW_X + i] = x[i];
   }
   // one factorised sum family: a field, per direction the first basis row, the row count and the
   // stride of that direction's index in the sums, and where the sums start

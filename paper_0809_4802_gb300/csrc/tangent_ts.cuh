@@ -27,8 +27,8 @@ namespace vms {
 constexpr int TS_FIELDS = 57, TS_SUMS = 738;
 constexpr int TS_ENGINE = 3;
 constexpr int TS_STEPS = 6, TS_PLAN_HEAD = 8;
-// rows of the one-dimensional basis table: psi_0..2, phi_0..1, the constant 1
-constexpr int TS_ROW_PSI = 0, TS_ROW_PHI = 3, TS_ROW_ONE = 5, TS_BASIS_ROWS = 8;
+// rows of the one-dimensional basis table: psi_0..2, phi_0..1, the constant 1, and the Gauss points
+constexpr int TS_ROW_PSI = 0, TS_ROW_PHI = 3, TS_ROW_ONE = 5, TS_ROW_X = 6, TS_BASIS_ROWS = 8;
 // field slots
 constexpr int TF_L = 0, TF_ADV = 9, TF_VP = 12, TF_G = 21, TF_YCF = 27, TF_YFC = 39, TF_ZCF = 51,
               TF_ZFC = 54;
@@ -54,31 +54,49 @@ __host__ __device__ inline int ts_d2(int al) { return al == 2 ? 1 : 2; }
 
 #if defined(__CUDACC__)
 // Lane q = quadrature point (< nq): geometry, fields at q into F[.][q], and the lane's K_ff part.
+// The coordinates and the coarse velocity are first mapped to their trilinear monomial coefficients
+// (lanes 0..5, one field each, into C.T, which the sums overwrite later), so that a point's J, its
+// reference velocity gradient and v take 3 and 7 FMA per entry instead of sums over the 8 nodes.
+// B is the one-dimensional basis table (its row TS_ROW_X holds the Gauss points).
 __device__ __forceinline__ void ts_phase1(int lane, int nq, WarpArea<double>& W, TsArea& C,
-                                          const RefTab<double>& tab, double nut, double tau,
-                                          LaneAcc<double>& A) {
+                                          const RefTab<double>& tab, const double* B, double nut,
+                                          double tau, LaneAcc<double>& A) {
+  double* M = C.T;  // [6][8]: x, y, z, v_x, v_y, v_z
+  if (lane < 6) {
+    double f[8], c[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) f[a] = lane < 3 ? W.X[a][lane] : W.V[a][lane - 3];
+    modal8(f, c);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) M[8 * lane + m] = 0.125 * c[m];
+  }
+  __syncwarp();
   const int q = lane;
   if (q >= nq) return;
   const int ld = ts_ld(nq);
   double* F = C.F;
-  const double* dN = tab.dN + 24 * q;
-  const double* N = tab.N + 8 * q;
+  const int n1 = nq == 8 ? 2 : 3;
+  const double xi = B[4 * TS_ROW_X + q % n1], eta = B[4 * TS_ROW_X + (q / n1) % n1],
+               zeta = B[4 * TS_ROW_X + q / (n1 * n1)];
+  const double ez = eta * zeta, xz = xi * zeta, xe = xi * eta, xez = xe * zeta;
   const double bq = tab.b[q];
   const double db[3] = {tab.db[3 * q], tab.db[3 * q + 1], tab.db[3 * q + 2]};
-  double J[3][3], G[3][3];
+  // monomials 1, xi, eta, zeta, xi eta, xi zeta, eta zeta, xi eta zeta
+  double J[3][3], G[3][3], vc[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int al = 0; al < 3; ++al) {
-      double s = 0.0, g = 0.0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        s += W.X[a][i] * dN[3 * a + al];
-        g += W.V[a][i] * dN[3 * a + al];
-      }
-      J[i][al] = s;
-      G[i][al] = g;  // reference gradient of the coarse velocity
+  for (int f = 0; f < 6; ++f) {
+    const double* c = M + 8 * f;
+    const double d0 = c[1] + c[4] * eta + c[5] * zeta + c[7] * ez;
+    const double d1 = c[2] + c[4] * xi + c[6] * zeta + c[7] * xz;
+    const double d2 = c[3] + c[5] * xi + c[6] * eta + c[7] * xe;
+    if (f < 3) {
+      J[f][0] = d0; J[f][1] = d1; J[f][2] = d2;
+    } else {
+      G[f - 3][0] = d0; G[f - 3][1] = d1; G[f - 3][2] = d2;  // reference gradient of the coarse velocity
+      vc[f - 3] = c[0] + c[1] * xi + c[2] * eta + c[3] * zeta + c[4] * xe + c[5] * xz + c[6] * ez +
+                  c[7] * xez;
     }
+  }
   double cof[3][3];
   double det = cofactor3(J, cof);
   if (!(det >= DET_MIN)) { W.flag = 1u; det = 1.0; }
@@ -95,10 +113,7 @@ __device__ __forceinline__ void ts_phase1(int lane, int nq, WarpArea<double>& W,
   double v[3], L[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) s += N[a] * W.V[a][i];
-    v[i] = s + bq * W.beta[i];
+    v[i] = vc[i] + bq * W.beta[i];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
       L[i][k] = G[i][0] * Ji[0][k] + G[i][1] * Ji[1][k] + G[i][2] * Ji[2][k] + W.beta[i] * d[k];
