@@ -473,6 +473,7 @@ def kernel_times(ctx, steps, flush):
     launch on the stream it is launched on (residual: the context's stream; tangent: its second
     stream), over `steps` assemblies."""
     ctx.profile_enable(True)
+    ctx.profile_read(reset=True)   # launch counts of earlier, untimed calls must not enter the mean
     for _ in range(steps):
         flush.zero_()
         ctx.assemble()
