@@ -180,14 +180,16 @@ int vms_get_csr(vms_ctx* ctx, vms_csr_view* out);
  * (nothing assembled), VMS_ERR_CUDA. */
 int vms_csr_download(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* values, double* rhs);
 /* Asynchronous form of vms_csr_download, for pipelines that overlap the transfer of one assembled
- * system with the assembly of the next. The values and the right-hand side are first copied into
- * a device staging buffer on the context's stream (so the next vms_assemble_newton_schur may
- * overwrite the originals), then to the caller's buffers on a copy stream of the library; the call
- * returns without waiting. vms_csr_download_wait blocks until the copies have landed. A new
- * vms_csr_download_async, a new mesh and vms_destroy first wait for a pending one. The host
- * buffers should be page-locked for the copy to run beside the next assembly; they must stay
- * valid until the wait. The staging buffer (the size of the values and the right-hand side) is
- * allocated on the first call. Not part of the paper's method: a transfer pipeline for serving.
+ * system with the assembly of the next. The copies to the caller's buffers run on a copy stream of
+ * the library after the assembly; the call returns without waiting. While the copy of the values
+ * is pending, the next vms_assemble_newton_schur writes a second values buffer of the same size
+ * (allocated on first use; in graph mode, vms_set_graph, the values are instead first copied into
+ * a device snapshot, as the captured assembly writes one buffer); the right-hand side is copied
+ * through a device snapshot. vms_csr_download_wait blocks until the copies have landed. A new
+ * vms_csr_download_async, a new mesh and vms_destroy first wait for a pending one. Device views
+ * (vms_get_csr) point at the values of the last assembly. The host buffers should be page-locked
+ * for the copy to run beside the next assembly; they must stay valid until the wait. Not part of
+ * the paper's method: a transfer pipeline for serving.
  * Errors: VMS_ERR_STATE (nothing assembled), VMS_ERR_OUT_OF_MEMORY, VMS_ERR_CUDA. */
 int vms_csr_download_async(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void* values, double* rhs);
 int vms_csr_download_wait(vms_ctx* ctx);

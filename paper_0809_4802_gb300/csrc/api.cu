@@ -51,11 +51,14 @@ struct vms_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t graph_launches[VMS_K_COUNT] = {};
-  // vms_csr_download_async: device snapshot of the assembled system and its copy stream
+  // vms_csr_download_async: the copy stream, the buffer a pending copy reads, the second values
+  // buffer the next assembly writes meanwhile, and (graph mode) a device snapshot
   struct Stage {
-    void* values = nullptr;
-    double* rhs = nullptr;
+    void* values = nullptr;      // snapshot of the values (graph mode: the captured buffer is fixed)
+    double* rhs = nullptr;       // snapshot of the right-hand side
     size_t vbytes = 0, rbytes = 0;
+    void* src = nullptr;         // values buffer the pending copy reads (no snapshot)
+    void* alt = nullptr;         // the other values buffer (as large as work.values)
     cudaStream_t copy = nullptr;
     cudaEvent_t snap = nullptr, done = nullptr;
     bool pending = false;
@@ -131,7 +134,7 @@ int stage_wait(vms_ctx* c) {
 void stage_free(vms_ctx* c) {
   stage_wait(c);
   auto& S = c->stage;
-  dfree(S.values); dfree(S.rhs);
+  dfree(S.values); dfree(S.rhs); dfree(S.alt);
   if (S.copy) cudaStreamDestroy(S.copy);
   if (S.snap) cudaEventDestroy(S.snap);
   if (S.done) cudaEventDestroy(S.done);
@@ -786,6 +789,12 @@ int vms_assemble_newton_schur(vms_ctx* ctx, vms_csr_view* out) {
   if (!ctx->state.valid) return fail(ctx, VMS_ERR_STATE, "mesh and state must be uploaded first");
   CK(cudaSetDevice(ctx->device));
   Work& w = ctx->work;
+  if (ctx->stage.pending && ctx->stage.src && ctx->stage.src == w.values && !ctx->use_graph) {
+    // the last system's values are still being copied to the host (vms_csr_download_async):
+    // assemble into the other buffer
+    if (!ctx->stage.alt) CK(cudaMalloc(&ctx->stage.alt, (size_t)ctx->mesh.nnz * sizeof(double)));
+    std::swap(w.values, ctx->stage.alt);
+  }
   if (ctx->use_graph && !ctx->timing) {
     if (ctx->graph_dirty || !ctx->graph) TRY(capture_assembly(ctx));
     CK(cudaGraphLaunch(ctx->graph, ctx->stream));
@@ -839,7 +848,7 @@ int vms_csr_download_async(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void*
     CK(cudaEventCreateWithFlags(&S.snap, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
   }
-  if (S.vbytes != vbytes) {
+  if (ctx->use_graph && S.vbytes != vbytes) {
     dfree(S.values);
     S.vbytes = 0;
     CK(cudaMalloc(&S.values, vbytes));
@@ -851,15 +860,19 @@ int vms_csr_download_async(vms_ctx* ctx, int32_t* rowptr, int32_t* colidx, void*
     CK(cudaMalloc(&S.rhs, rbytes));
     S.rbytes = rbytes;
   }
-  // the snapshot is ordered after the assembly on the context's stream, and the next assembly
-  // after the snapshot; the copy to the host runs on its own stream
-  if (values) CK(cudaMemcpyAsync(S.values, ctx->work.values, vbytes, cudaMemcpyDeviceToDevice, st));
+  // The copy to the host runs on its own stream after an event recorded behind the assembly. The
+  // values are read from the assembled buffer itself: the next assembly writes the other buffer
+  // (vms_assemble_newton_schur swaps them while this copy is pending). A captured assembly graph
+  // writes one fixed buffer, so in graph mode the values are first copied into the snapshot.
+  const bool swap = !ctx->use_graph;
+  if (values && !swap) CK(cudaMemcpyAsync(S.values, ctx->work.values, vbytes, cudaMemcpyDeviceToDevice, st));
   if (rhs) CK(cudaMemcpyAsync(S.rhs, ctx->work.rhs, rbytes, cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(S.snap, st));
   CK(cudaStreamWaitEvent(S.copy, S.snap, 0));
+  S.src = values && swap ? ctx->work.values : nullptr;
   if (rowptr) CK(cudaMemcpyAsync(rowptr, m.rowptr, sizeof(int32_t) * (4 * m.n_nodes + 1), cudaMemcpyDefault, S.copy));
   if (colidx) CK(cudaMemcpyAsync(colidx, m.colidx, sizeof(int32_t) * m.nnz, cudaMemcpyDefault, S.copy));
-  if (values) CK(cudaMemcpyAsync(values, S.values, vbytes, cudaMemcpyDefault, S.copy));
+  if (values) CK(cudaMemcpyAsync(values, swap ? ctx->work.values : S.values, vbytes, cudaMemcpyDefault, S.copy));
   if (rhs) CK(cudaMemcpyAsync(rhs, S.rhs, rbytes, cudaMemcpyDefault, S.copy));
   CK(cudaEventRecord(S.done, S.copy));
   S.pending = true;

@@ -9,7 +9,10 @@ from paper_0809_4802_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def test_async_download_snapshots_the_assembly_before_it():
+@pytest.mark.parametrize("graph", [False, True], ids=["two-buffers", "graph-snapshot"])
+def test_async_download_snapshots_the_assembly_before_it(graph):
+    """Without a captured graph the next assembly writes the second values buffer while the copy
+    reads the first; with one, the values are copied into a device snapshot first."""
     import torch
     from paper_0809_4802_gb300 import build, vms
     build.build()
@@ -19,6 +22,7 @@ def test_async_download_snapshots_the_assembly_before_it():
         ctx = vms.Context(0, prec)
         ctx.mesh_upload(wl.mesh.xyz, wl.mesh.conn, wl.bc.dofs, wl.bc.vals)
         ctx.set_params(wl.nu)
+        ctx.set_graph(graph)
         ctx.state_upload(wl.u, wl.beta)
         ctx.assemble()
         rowptr, colidx, vals, rhs = ctx.csr_host()          # synchronous reference
@@ -44,4 +48,11 @@ def test_async_download_snapshots_the_assembly_before_it():
         np.testing.assert_array_equal(r_h.numpy(), rhs2)
         assert np.abs(vals2 - vals).max() > 0
         ctx.csr_download_wait()   # nothing pending: returns at once
+        # a third assembly after the copies: the values are those of its state (up to the order in
+        # which the atomic scatter sums)
+        ctx.state_upload(wl.u, wl.beta)
+        ctx.assemble()
+        _, _, vals3, _ = ctx.csr_host()
+        tol = 1e-5 if prec == vms.PREC_MIXED else 1e-12
+        assert np.abs(vals3.astype(np.float64) - vals).max() <= tol * np.abs(vals).max()
         ctx.close()
