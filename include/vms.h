@@ -72,7 +72,8 @@ extern "C" {
 #define VMS_PRECOND_ILU0 0          /* block ILU(0), 4x4 node blocks, natural node order (default) */
 #define VMS_PRECOND_BLOCK_JACOBI 1  /* inverses of the 4x4 diagonal node blocks */
 #define VMS_PRECOND_ILU0_FALLBACK 2 /* ILU(0); a solve that ends at maxit (or on a zero pivot) is
-                                       repeated from zero with block Jacobi and GMRES(480) */
+                                       repeated by a banded direct LU solve, or where the band
+                                       would exceed 4 GiB by block Jacobi and GMRES(480) */
 
 /* ---- scatter modes (vms_params.scatter_mode) ----------------------------------------------- */
 #define VMS_SCATTER_ATOMIC 0  /* one launch, atomic adds into CSR values (order not fixed) */
@@ -279,9 +280,14 @@ int vms_set_graph(vms_ctx* ctx, int enable);
 
 /* Choose the right preconditioner of vms_solve / vms_solve_instance / vms_newton_*:
  * VMS_PRECOND_ILU0 (default), VMS_PRECOND_BLOCK_JACOBI, or VMS_PRECOND_ILU0_FALLBACK (ILU(0), and
- * for a solve that does not converge, a second solve from zero with block Jacobi and the longest
- * cycle: on coarse high-Reynolds systems the ILU(0) pivots lose all size while the exact 4x4
- * block inverses stay stable; *iters then counts both solves). Section 6 solved every Newton system with a Krylov solver at its
+ * for a solve that does not converge, a direct solve of the instance by LU with partial pivoting
+ * in band storage, FP64, on the device; the band's half-width is 4 (largest node-number distance
+ * of a row) + 3, and where the band would need more than 4 GiB a second solve from zero with
+ * block Jacobi and the longest cycle instead. On coarse high-Reynolds systems the ILU(0) pivots
+ * lose all size; *iters counts the Krylov iterations of both attempts, *relres is that of the
+ * last. The direct solve's temporary band is allocated and freed within the call:
+ * VMS_ERR_OUT_OF_MEMORY falls through to block Jacobi, VMS_ERR_ZERO_PIVOT reports a singular
+ * band). Section 6 solved every Newton system with a Krylov solver at its
  * library defaults; on one process that default preconditioner is an incomplete LU factorisation
  * without fill, which VMS_PRECOND_ILU0 computes on 4x4 node blocks (it is refactored at every
  * solve of a newly assembled system). ILU(0) needs at most 32 neighbours per node

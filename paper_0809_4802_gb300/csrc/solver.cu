@@ -883,6 +883,250 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
   return rel <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "refined GMRES reached maxit");
 }
 
+// ---------------------------------------------------------------------------------------------
+// Direct solve of one instance by banded LU with partial pivoting (the fallback of
+// VMS_PRECOND_ILU0_FALLBACK for systems whose ILU(0) factor is unstable). Band storage as in
+// LAPACK's band routines: entry (i, j) of the N x N matrix at AB[(kv + i - j) + j * ldab] with
+// kv = kl + ku and ldab = 2 kl + ku + 1 (the top kl rows take the fill of the row interchanges).
+// The factorisation is Doolittle's elimination column by column (pivot search, interchange within
+// the band, multipliers, rank-1 update of the band's trailing block); the solve applies the
+// interchanges and multipliers forward and U backward. FP64 throughout.
+// ---------------------------------------------------------------------------------------------
+
+// the largest node distance |col node - row node| of the instance's rows
+__global__ void band_width_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                  int64_t n0, int64_t nodes, int* __restrict__ bw) {
+  const int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (nd >= nodes) return;
+  const int64_t g = n0 + nd;
+  const int32_t r0 = rowptr[4 * g], r1 = rowptr[4 * g + 1];
+  int w = 0;
+  for (int32_t t = r0; t < r1; t += 4) {
+    const int64_t d = (int64_t)(colidx[t] >> 2) - g;
+    const int a = (int)(d < 0 ? -d : d);
+    w = a > w ? a : w;
+  }
+  atomicMax(bw, w);
+}
+
+// the instance's rows into the band (one warp per node row, one lane per 4x4 block)
+template <typename T>
+__global__ void band_scatter_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                    const T* __restrict__ val, int64_t n0, int64_t nodes, double* __restrict__ AB,
+                                    int64_t ldab, int kl, int ku, int* __restrict__ err) {
+  const int64_t nd = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (nd >= nodes) return;
+  const int64_t g = n0 + nd, N = 4 * nodes, kv = kl + ku;
+  int32_t rp[4];
+  for (int m = 0; m < 4; ++m) rp[m] = rowptr[4 * g + m];
+  const int deg = (rp[1] - rp[0]) >> 2;
+  for (int kk = lane; kk < deg; kk += 32) {
+    const int64_t c = (int64_t)colidx[rp[0] + 4 * kk] - 4 * n0;
+    for (int r = 0; r < 4; ++r)
+      for (int m = 0; m < 4; ++m) {
+        const int64_t i = 4 * nd + r, j = c + m;
+        if (j < 0 || j >= N || i - j > kl || j - i > ku) {
+          atomicOr(err, 1);
+          continue;
+        }
+        AB[(kv + i - j) + j * ldab] = (double)val[rp[r] + 4 * kk + m];
+      }
+  }
+}
+
+constexpr int BAND_THREADS = 1024;
+
+// Column j: pivot search, interchange of rows j and j + jp over the band's columns j..ju, and the
+// multipliers. state[0] = ju (the last column the interchanges have reached), state[1] = the first
+// zero pivot's column + 1 (0: none).
+__global__ void __launch_bounds__(BAND_THREADS) band_pivot_kernel(double* __restrict__ AB, int64_t ldab,
+                                                                  int N, int kl, int ku, int j,
+                                                                  int* __restrict__ ipiv, int* __restrict__ state) {
+  __shared__ double sv[BAND_THREADS];
+  __shared__ int si[BAND_THREADS];
+  __shared__ int s_jp, s_ju;
+  const int tid = threadIdx.x;
+  const int64_t kv = kl + ku;
+  const int km = kl < N - 1 - j ? kl : N - 1 - j;
+  if (state[1] != 0) return;  // uniform: an earlier column was singular
+  double best = -1.0;
+  int bi = 0;
+  for (int t = tid; t <= km; t += BAND_THREADS) {
+    const double a = fabs(AB[kv + t + (int64_t)j * ldab]);
+    if (a > best) { best = a; bi = t; }
+  }
+  sv[tid] = best;
+  si[tid] = bi;
+  __syncthreads();
+  for (int h = BAND_THREADS / 2; h > 0; h >>= 1) {
+    if (tid < h && (sv[tid + h] > sv[tid] || (sv[tid + h] == sv[tid] && si[tid + h] < si[tid]))) {
+      sv[tid] = sv[tid + h];
+      si[tid] = si[tid + h];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const int jp = si[0];
+    ipiv[j] = j + jp;
+    int ju = j + ku + jp < N - 1 ? j + ku + jp : N - 1;
+    ju = ju > state[0] ? ju : state[0];
+    state[0] = ju;
+    s_jp = jp;
+    s_ju = ju;
+    if (!(sv[0] > 0.0)) state[1] = j + 1;  // zero (or not a number) pivot
+  }
+  __syncthreads();
+  if (!(sv[0] > 0.0)) return;
+  const int jp = s_jp, ju = s_ju;
+  if (jp != 0)
+    for (int c = j + tid; c <= ju; c += BAND_THREADS) {
+      double* a = AB + (kv + jp + j - c) + (int64_t)c * ldab;
+      double* b = AB + (kv + j - c) + (int64_t)c * ldab;
+      const double t = *a;
+      *a = *b;
+      *b = t;
+    }
+  __syncthreads();
+  const double piv = AB[kv + (int64_t)j * ldab];
+  for (int t = 1 + tid; t <= km; t += BAND_THREADS) AB[kv + t + (int64_t)j * ldab] /= piv;
+}
+
+// Column j: rank-1 update of rows j+1..j+km, columns j+1..ju
+__global__ void band_update_kernel(double* __restrict__ AB, int64_t ldab, int N, int kl, int ku, int j,
+                                   const int* __restrict__ state) {
+  if (state[1] != 0) return;
+  const int64_t kv = kl + ku;
+  const int km = kl < N - 1 - j ? kl : N - 1 - j;
+  const int ncols = state[0] - j;
+  if (km <= 0 || ncols <= 0) return;
+  const int64_t total = (int64_t)km * ncols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = j + 1 + (int)(t / km), r = 1 + (int)(t % km);
+    AB[(kv + r + j - c) + (int64_t)c * ldab] -= AB[kv + r + (int64_t)j * ldab] * AB[(kv + j - c) + (int64_t)c * ldab];
+  }
+}
+
+// x <- A^-1 x with the factor (one block; the steps are sequential)
+__global__ void __launch_bounds__(BAND_THREADS) band_solve_kernel(const double* __restrict__ AB, int64_t ldab,
+                                                                  int N, int kl, int ku,
+                                                                  const int* __restrict__ ipiv,
+                                                                  const int* __restrict__ state, double* __restrict__ x) {
+  if (state[1] != 0) return;  // singular: the factor (and ipiv past the failing column) is incomplete
+  const int tid = threadIdx.x;
+  const int64_t kv = kl + ku;
+  for (int j = 0; j < N - 1; ++j) {
+    if (tid == 0) {
+      const int l = ipiv[j];
+      if (l != j) { const double t = x[l]; x[l] = x[j]; x[j] = t; }
+    }
+    __syncthreads();
+    const int lm = kl < N - 1 - j ? kl : N - 1 - j;
+    const double xj = x[j];
+    for (int t = 1 + tid; t <= lm; t += BAND_THREADS) x[j + t] -= AB[kv + t + (int64_t)j * ldab] * xj;
+    __syncthreads();
+  }
+  for (int j = N - 1; j >= 0; --j) {
+    if (tid == 0) x[j] /= AB[kv + (int64_t)j * ldab];
+    __syncthreads();
+    const double xj = x[j];
+    const int i0 = j - kl - ku > 0 ? j - kl - ku : 0;
+    for (int i = i0 + tid; i < j; i += BAND_THREADS) x[i] -= AB[(kv + i - j) + (int64_t)j * ldab] * xj;
+    __syncthreads();
+  }
+}
+
+constexpr size_t BAND_MAX_BYTES = (size_t)4 << 30;
+
+// The instance's system S x = -rhs by banded LU into w.x; *rel_out = |b - S x| / |b| (the matrix
+// the assembly left, FP32 or FP64 values). VMS_ERR_UNSUPPORTED if the band would exceed
+// BAND_MAX_BYTES, VMS_ERR_ZERO_PIVOT for a singular band.
+static int band_direct(vms_ctx* ctx, const SysRange& R, double* rel_out) {
+  const Mesh& m = ctx_mesh(ctx);
+  Work& wk = ctx_work(ctx);
+  SolverWork& w = ctx_solver(ctx);
+  cudaStream_t st = ctx_stream(ctx);
+  const bool f32 = ctx_fp32(ctx);
+  const int64_t nodes = R.nodes(), n = 4 * nodes;
+  if (n == 0) {
+    *rel_out = 0.0;
+    return VMS_OK;
+  }
+  if (n > INT32_MAX / 2) return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "band solve: system too large");
+  int* d_int = nullptr;  // [0] band width, [1..2] state, [3] scatter error
+  cudaError_t e = cudaMalloc(&d_int, sizeof(int) * 4);
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_OUT_OF_MEMORY, cudaGetErrorString(e));
+  int h[4] = {0, 0, 0, 0};
+  cudaMemsetAsync(d_int, 0, sizeof(int) * 4, st);
+  {
+    KScope k(ctx, VMS_K_PRECOND);
+    band_width_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(m.rowptr, m.colidx, R.n0, nodes, d_int);
+    k.add(1);
+  }
+  cudaMemcpyAsync(h, d_int, sizeof(int), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { cudaFree(d_int); return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e)); }
+  const int kl = 4 * h[0] + 3, ku = kl;
+  const int64_t ldab = 2 * (int64_t)kl + ku + 1;
+  const size_t bytes = sizeof(double) * (size_t)ldab * (size_t)n;
+  if (bytes > BAND_MAX_BYTES) { cudaFree(d_int); return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "band solve: band too large"); }
+  double* AB = nullptr;
+  int* ipiv = nullptr;
+  e = cudaMalloc(&AB, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&ipiv, sizeof(int) * n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // an allocation failure is not sticky: clear it for the caller's checks
+    cudaFree(AB); cudaFree(d_int);
+    return ctx_fail(ctx, VMS_ERR_OUT_OF_MEMORY, cudaGetErrorString(e));
+  }
+  cudaMemsetAsync(AB, 0, bytes, st);
+  cudaMemsetAsync(ipiv, 0, sizeof(int) * n, st);
+  {
+    KScope kf(ctx, VMS_K_PRECOND);
+    const unsigned wb = (unsigned)((nodes * 32 + 255) / 256);
+    if (f32)
+      band_scatter_kernel<float><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
+    else
+      band_scatter_kernel<double><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
+    const int64_t upd = (int64_t)kl * (kl + ku);
+    const unsigned ub = (unsigned)std::min<int64_t>((upd + 255) / 256, 4 * (int64_t)sm_count());
+    for (int j = 0; j < (int)n; ++j) {
+      band_pivot_kernel<<<1, BAND_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, j, ipiv, d_int + 1);
+      band_update_kernel<<<ub, 256, 0, st>>>(AB, ldab, (int)n, kl, ku, j, d_int + 1);
+    }
+    // b = -rhs into w.rb, x = b into w.x, forward and backward substitution
+    axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(-1.0, wk.rhs + 4 * R.n0, 0.0, (const double*)nullptr, w.rb, n);
+    cudaMemcpyAsync(w.x, w.rb, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    band_solve_kernel<<<1, BAND_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, ipiv, d_int + 1, w.x);
+    kf.add(3 + 2 * (int)n);
+  }
+  cudaMemcpyAsync(h + 1, d_int + 1, sizeof(int) * 3, cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  cudaFree(AB); cudaFree(ipiv); cudaFree(d_int);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  if (h[3] != 0) return ctx_fail(ctx, VMS_ERR_CUDA, "band solve: an entry outside the band");
+  if (h[2] != 0) return ctx_fail(ctx, VMS_ERR_ZERO_PIVOT, "band solve: singular system");
+  // relative residual |b - S x| / |b|
+  double* y = w.rfull;
+  KScope ks(ctx, VMS_K_SPMV);
+  ks.add(f32 ? spmv<float, double>(m, R, wk.values, w.x, y, st) : spmv<double, double>(m, R, wk.values, w.x, y, st));
+  axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(1.0, w.rb, -1.0, y, y, n);
+  ks.add(1);
+  double* hd = w.h;
+  double nb2 = 0.0, nr2 = 0.0;
+  dots<double>(w.rb, n, 1, w.rb, n, hd + H_PART, hd + H_NORM, st);
+  cudaMemcpyAsync(&nb2, hd + H_NORM, sizeof(double), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  dots<double>(y, n, 1, y, n, hd + H_PART, hd + H_NORM, st);
+  ks.add(4);
+  cudaMemcpyAsync(&nr2, hd + H_NORM, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  *rel_out = nb2 > 0.0 ? std::sqrt(nr2 / nb2) : 0.0;
+  return VMS_OK;
+}
+
 static int recover_and_update(vms_ctx* ctx, const SysRange& R) {
   const Mesh& m = ctx_mesh(ctx);
   State& s = ctx_state(ctx);
@@ -959,13 +1203,22 @@ static int solve_impl(vms_ctx* ctx, const SysRange& R, int64_t instance, double 
   if ((rc == VMS_ERR_KRYLOV_MAXIT || rc == VMS_ERR_ZERO_PIVOT) &&
       ctx_precond(ctx) == VMS_PRECOND_ILU0_FALLBACK && !(rc == VMS_ERR_KRYLOV_MAXIT && r < accept_below)) {
     // ILU(0) loses all accuracy where its pivots do (growth factors of 1e7-1e16 were measured on
-    // coarse high-Reynolds systems): repeat the solve from zero with the block-Jacobi
-    // preconditioner, whose 4x4 inverses are exact, and the longest cycle
-    int it2 = 0;
+    // coarse high-Reynolds systems): solve directly by banded LU with partial pivoting where the
+    // band fits, else repeat the solve from zero with the block-Jacobi preconditioner, whose 4x4
+    // inverses are exact, and the longest cycle
     double r2 = 0.0;
-    rc = linear_solve(ctx, R, rtol, maxit, MAX_RESTART, MAX_RESTART, &it2, &r2, true);
-    it += it2;
-    r = r2;
+    int rcb = band_direct(ctx, R, &r2);
+    if (rcb == VMS_OK) {
+      r = r2;
+      rc = r2 <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "banded direct solve above rtol");
+    } else if (rcb == VMS_ERR_UNSUPPORTED || rcb == VMS_ERR_OUT_OF_MEMORY) {
+      int it2 = 0;
+      rc = linear_solve(ctx, R, rtol, maxit, MAX_RESTART, MAX_RESTART, &it2, &r2, true);
+      it += it2;
+      r = r2;
+    } else {
+      rc = rcb;
+    }
   }
   ctx_solver_stats(ctx)[0] += 1;
   ctx_solver_stats(ctx)[1] += it;

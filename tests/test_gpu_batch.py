@@ -128,6 +128,35 @@ def test_graph_replay_reproduces_the_assembly(vms, small_batch):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_direct_fallback_solves_each_instance(vms, regular_batch, prec):
+    """With VMS_PRECOND_ILU0_FALLBACK a Krylov solve stopped at maxit (here after one iteration)
+    is replaced by the banded direct solve of that instance's diagonal block: the increment
+    satisfies the block to rounding level, matches a direct solve of it, and leaves the other
+    instances unchanged."""
+    b = regular_batch
+    ctx = batch_context(vms, b, prec)
+    ctx.set_preconditioner(vms.PRECOND_ILU0_FALLBACK)
+    ctx.assemble()
+    rowptr, colidx, vals, rhs = ctx.csr_host()
+    G = sp.csr_matrix((vals.astype(np.float64), colidx, rowptr)).tocsr()
+    u0, _ = ctx.state_download()
+    for i in range(len(b.members)):
+        it, rel = ctx.solve_instance(i, rtol=1e-11, maxit=1, restart=1, update=True)
+        assert rel <= 1e-11 and it == 1
+        u1, _ = ctx.state_download()
+        n0, n1 = b.node_offsets[i], b.node_offsets[i + 1]
+        np.testing.assert_array_equal(u1[:n0], u0[:n0])
+        np.testing.assert_array_equal(u1[n1:], u0[n1:])
+        blk = G[4 * n0:4 * n1, 4 * n0:4 * n1]
+        r = rhs[4 * n0:4 * n1]
+        du = (u1[n0:n1] - u0[n0:n1]).reshape(-1)
+        assert np.linalg.norm(blk @ du + r) <= 1e-11 * np.linalg.norm(r)
+        assert relerr(du, spla.spsolve(blk.tocsc(), -r)) <= 1e-8
+        u0 = u1
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_instance_solves_update_only_their_instance(vms, regular_batch, prec):
     """vms_solve_instance solves one diagonal block (to 1e-10) and updates only that instance's
     state: its increment satisfies the assembled block and matches a direct solve of it, its
