@@ -71,9 +71,10 @@ extern "C" {
 /* ---- preconditioners of the Krylov solve (vms_set_preconditioner) ---------------------------- */
 #define VMS_PRECOND_ILU0 0          /* block ILU(0), 4x4 node blocks, natural node order (default) */
 #define VMS_PRECOND_BLOCK_JACOBI 1  /* inverses of the 4x4 diagonal node blocks */
-#define VMS_PRECOND_ILU0_FALLBACK 2 /* ILU(0); a solve that ends at maxit (or on a zero pivot) is
-                                       repeated by a banded direct LU solve, or where the band
-                                       would exceed 4 GiB by block Jacobi and GMRES(480) */
+#define VMS_PRECOND_ILU0_FALLBACK 2 /* ILU(0); a solve that does not converge (or meets a zero
+                                       pivot) is repeated by a banded direct LU solve, or where
+                                       the band would exceed 4 GiB by block Jacobi and
+                                       GMRES(480) */
 
 /* ---- scatter modes (vms_params.scatter_mode) ----------------------------------------------- */
 #define VMS_SCATTER_ATOMIC 0  /* one launch, atomic adds into CSR values (order not fixed) */
@@ -284,10 +285,12 @@ int vms_set_graph(vms_ctx* ctx, int enable);
  * in band storage, FP64, on the device; the band's half-width is 4 (largest node-number distance
  * of a row) + 3, and where the band would need more than 4 GiB a second solve from zero with
  * block Jacobi and the longest cycle instead. On coarse high-Reynolds systems the ILU(0) pivots
- * lose all size; *iters counts the Krylov iterations of both attempts, *relres is that of the
- * last. The direct solve's temporary band is allocated and freed within the call:
- * VMS_ERR_OUT_OF_MEMORY falls through to block Jacobi, VMS_ERR_ZERO_PIVOT reports a singular
- * band). Section 6 solved every Newton system with a Krylov solver at its
+ * lose all size. Where the direct solve fits, the ILU(0) attempt also ends before maxit: after a
+ * cycle whose rate would not reach rtol by maxit, or once it has run as long as the direct solve
+ * is estimated to take, so which of the two solves a system depends on timing; either meets
+ * rtol. *iters counts the Krylov iterations of both attempts, *relres is that of the last. The
+ * direct solve's temporary band is allocated and freed within the call: VMS_ERR_OUT_OF_MEMORY
+ * falls through to block Jacobi, VMS_ERR_ZERO_PIVOT reports a singular band). Section 6 solved every Newton system with a Krylov solver at its
  * library defaults; on one process that default preconditioner is an incomplete LU factorisation
  * without fill, which VMS_PRECOND_ILU0 computes on 4x4 node blocks (it is refactored at every
  * solve of a newly assembled system). ILU(0) needs at most 32 neighbours per node

@@ -8,6 +8,7 @@
 // a warp and in FP64 across warps) and an outer FP64 iterative refinement recomputes r = b - S x
 // in FP64 until the tolerance is met.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -18,7 +19,7 @@ namespace vms {
 
 void free_solver(SolverWork& s) {
   void* bufs[] = {s.x, s.r, s.V, s.Z, s.Dinv, s.h, s.rfull, s.bf, s.xf, s.cx, s.pv, s.pz, s.Zf,
-                  s.xb, s.rb};
+                  s.xb, s.rb, s.band};
   for (void* b : bufs)
     if (b) cudaFree(b);
   const uint32_t lim = s.ilu.spin_limit;  // a setting of the context, kept across re-allocations
@@ -458,6 +459,12 @@ struct Gmres {
   void* Zflex = nullptr;  // flexible GMRES: restart preconditioned vectors kept (else null)
   int restart_cap = 0;    // > restart: a cycle that does not halve the residual doubles the
                           // restart length (up to this), the basis growing with it
+  bool stall_exit = false;  // end the solve after a full cycle at the longest length whose rate,
+                            // kept for the remaining iterations, would not reach rtol (a direct
+                            // solve follows it)
+  bool has_deadline = false;  // end the solve at this host time (the direct solve's estimated
+  std::chrono::steady_clock::time_point deadline{};  // duration after the start, a direct solve
+  bool timed_out = false;                             // following it)
 
   // z = M^-1 v with the preconditioner chosen for this solve
   template <typename T, typename VT>
@@ -534,7 +541,7 @@ struct Gmres {
       k.add(1);
     }
     double cycle_res0 = res;
-    while (it < maxit && res > rtol * bnorm) {
+    while (it < maxit && res > rtol * bnorm && !timed_out) {
       // V_0 = r / |r|
       {
         KScope k(ctx, VMS_K_REDUCE);
@@ -600,6 +607,12 @@ struct Gmres {
         for (int i = 0; i <= j; ++i) H[i * restart + j] = hh[i];
         res = std::fabs(g[j + 1]);
         if (!(res > rtol * bnorm) || nrm2 <= 0.0) { ++j; ++it; break; }
+        if (has_deadline && std::chrono::steady_clock::now() > deadline) {
+          timed_out = true;
+          ++j;
+          ++it;
+          break;
+        }
       }
       // y = H^-1 g (upper triangular j x j), x += M^-1 V y
       std::vector<double> y(j, 0.0);
@@ -636,7 +649,7 @@ struct Gmres {
       // a full cycle that did not halve the residual: the cycle is too short to keep the slow
       // directions (coarse modes of large meshes); continue with a longer one
       if (j == restart && it < maxit && res > rtol * bnorm && res > 0.5 * cycle_res0 &&
-          restart < restart_cap) {
+          restart < restart_cap && !timed_out) {
         const int nr = std::min(2 * restart, restart_cap);
         if (int rc2 = grow_basis<VT>(nr)) return rc2;
         V = reinterpret_cast<VT*>(w.V);
@@ -647,6 +660,12 @@ struct Gmres {
         g.assign(restart + 1, 0.0);
         hh.assign(restart + 2, 0.0);
       }
+      // stagnation: the residual projected to maxit at this cycle's reduction factor q stays above
+      // the target, res q^((maxit - it) / restart) > rtol |b|
+      else if (stall_exit && j == restart && it < maxit && res > rtol * bnorm && cycle_res0 > 0.0 &&
+               std::log(res / (rtol * bnorm)) >
+                   -std::log(std::min(res / cycle_res0, 1.0)) * ((double)(maxit - it) / restart))
+        break;
       // true residual norm for the next cycle's test is computed at the top of the loop
       if (!(res > rtol * bnorm)) {
         KScope k(ctx, VMS_K_REDUCE);
@@ -684,6 +703,7 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
   if (e == cudaSuccess) e = cudaMalloc(&w.rb, sizeof(double) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.pv, sizeof(float) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w.pz, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w.band, sizeof(int) * 4);
   if (e != cudaSuccess) {
     free_solver(w);
     return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA,
@@ -693,6 +713,8 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
   w.restart = restart;
   return VMS_OK;
 }
+
+static int band_shape(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits);
 
 // Solve S du = -rhs into w.x (FP64). Mixed: FP32 GMRES inside FP64 iterative refinement.
 static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit, int restart,
@@ -744,6 +766,21 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
   }
   Gmres G{ctx, m, w, st, n, R};
   G.restart_cap = std::min(std::max(restart_cap, restart), MAX_RESTART);
+  if (w.use_ilu && ctx_precond(ctx) == VMS_PRECOND_ILU0_FALLBACK) {
+    // Where the direct solve will follow a failed ILU(0) solve, the Krylov attempt ends early: when
+    // it stagnates, or once it has run as long as the direct solve is estimated to take (so the
+    // two together take at most about twice the faster one). The estimate is per column of the
+    // band a launch (about 10 us) plus the column's update at the rate measured on a GB300
+    // (3.2 ns per thousand entries).
+    int kl = 0;
+    if (int rc = band_shape(ctx, R, &kl, &G.stall_exit)) return rc;
+    if (G.stall_exit) {
+      const double est = (double)n * (1.0e-5 + 3.2e-12 * (double)kl * (2.0 * kl));
+      G.has_deadline = true;
+      G.deadline = std::chrono::steady_clock::now() +
+                   std::chrono::duration_cast<std::chrono::steady_clock::duration>(std::chrono::duration<double>(est));
+    }
+  }
   if (int rc = G.sync_host(&bnorm2, hd + H_NORM, sizeof(double))) return rc;
   const double bnorm = std::sqrt(bnorm2);
   // a non-finite right-hand side is reported as such before any preconditioner sweep runs
@@ -809,7 +846,7 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
       stalled = true;
       break;
     }
-    if (rel <= rtol || outer == 20 || total >= maxit || last_it == 0) break;
+    if (rel <= rtol || outer == 20 || total >= maxit || last_it == 0 || G.timed_out) break;
     if (rel > 0.5 * prev_rel) { stalled = true; break; }
     prev_rel = rel;
     cudaMemcpyAsync(w.xb, w.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
@@ -833,7 +870,7 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
     }
     last_it = it;
   }
-  if (rc == VMS_OK && stalled && total < maxit) {
+  if (rc == VMS_OK && stalled && total < maxit && !G.timed_out) {
     // S c = b - S x with FP64 Krylov vectors, the FP32 matrix values and the FP64 preconditioner
     // (the ILU(0) factor the FP32 sweeps' copy is rounded from)
     int it = 0;
@@ -935,31 +972,31 @@ __global__ void band_scatter_kernel(const int32_t* __restrict__ rowptr, const in
   }
 }
 
-constexpr int BAND_THREADS = 1024;
+constexpr int BAND_THREADS = 1024;  // the substitution kernel's block
+constexpr int BAND_STEP_THREADS = 256;
 
-// Column j: pivot search, interchange of rows j and j + jp over the band's columns j..ju, and the
-// multipliers. state[0] = ju (the last column the interchanges have reached), state[1] = the first
-// zero pivot's column + 1 (0: none).
-__global__ void __launch_bounds__(BAND_THREADS) band_pivot_kernel(double* __restrict__ AB, int64_t ldab,
-                                                                  int N, int kl, int ku, int j,
-                                                                  int* __restrict__ ipiv, int* __restrict__ state) {
-  __shared__ double sv[BAND_THREADS];
-  __shared__ int si[BAND_THREADS];
-  __shared__ int s_jp, s_ju;
+// Pivot of column `col` (its final values): the largest |A(col + t, col)|, t = 0..km, the first on
+// ties. ipiv[col] = col + t, jua[col] = the last column the interchanges up to col reach,
+// state[1] = col + 1 for a zero (or not a number) pivot. All threads of the block call it.
+__device__ void band_pivot_search(const double* __restrict__ AB, int64_t ldab, int N, int kl, int ku,
+                                  int col, int ju_prev, int* __restrict__ ipiv, int* __restrict__ jua,
+                                  int* __restrict__ state) {
+  __shared__ double sv[BAND_STEP_THREADS];
+  __shared__ int si[BAND_STEP_THREADS];
   const int tid = threadIdx.x;
   const int64_t kv = kl + ku;
-  const int km = kl < N - 1 - j ? kl : N - 1 - j;
-  if (state[1] != 0) return;  // uniform: an earlier column was singular
+  const int km = kl < N - 1 - col ? kl : N - 1 - col;
+  const double* a = AB + (int64_t)col * ldab + kv;
   double best = -1.0;
   int bi = 0;
-  for (int t = tid; t <= km; t += BAND_THREADS) {
-    const double a = fabs(AB[kv + t + (int64_t)j * ldab]);
-    if (a > best) { best = a; bi = t; }
+  for (int t = tid; t <= km; t += BAND_STEP_THREADS) {
+    const double v = fabs(a[t]);
+    if (v > best) { best = v; bi = t; }
   }
   sv[tid] = best;
   si[tid] = bi;
   __syncthreads();
-  for (int h = BAND_THREADS / 2; h > 0; h >>= 1) {
+  for (int h = BAND_STEP_THREADS / 2; h > 0; h >>= 1) {
     if (tid < h && (sv[tid + h] > sv[tid] || (sv[tid + h] == sv[tid] && si[tid + h] < si[tid]))) {
       sv[tid] = sv[tid + h];
       si[tid] = si[tid + h];
@@ -968,42 +1005,65 @@ __global__ void __launch_bounds__(BAND_THREADS) band_pivot_kernel(double* __rest
   }
   if (tid == 0) {
     const int jp = si[0];
-    ipiv[j] = j + jp;
-    int ju = j + ku + jp < N - 1 ? j + ku + jp : N - 1;
-    ju = ju > state[0] ? ju : state[0];
-    state[0] = ju;
-    s_jp = jp;
-    s_ju = ju;
-    if (!(sv[0] > 0.0)) state[1] = j + 1;  // zero (or not a number) pivot
+    ipiv[col] = col + jp;
+    const int reach = col + ku + jp < N - 1 ? col + ku + jp : N - 1;
+    jua[col] = reach > ju_prev ? reach : ju_prev;
+    if (!(sv[0] > 0.0)) atomicCAS(state + 1, 0, col + 1);
   }
-  __syncthreads();
-  if (!(sv[0] > 0.0)) return;
-  const int jp = s_jp, ju = s_ju;
-  if (jp != 0)
-    for (int c = j + tid; c <= ju; c += BAND_THREADS) {
-      double* a = AB + (kv + jp + j - c) + (int64_t)c * ldab;
-      double* b = AB + (kv + j - c) + (int64_t)c * ldab;
-      const double t = *a;
-      *a = *b;
-      *b = t;
-    }
-  __syncthreads();
-  const double piv = AB[kv + (int64_t)j * ldab];
-  for (int t = 1 + tid; t <= km; t += BAND_THREADS) AB[kv + t + (int64_t)j * ldab] /= piv;
 }
 
-// Column j: rank-1 update of rows j+1..j+km, columns j+1..ju
-__global__ void band_update_kernel(double* __restrict__ AB, int64_t ldab, int N, int kl, int ku, int j,
-                                   const int* __restrict__ state) {
-  if (state[1] != 0) return;
+__global__ void __launch_bounds__(BAND_STEP_THREADS) band_first_pivot_kernel(const double* __restrict__ AB, int64_t ldab,
+                                                                             int N, int kl, int ku, int* __restrict__ ipiv,
+                                                                             int* __restrict__ jua, int* __restrict__ state) {
+  band_pivot_search(AB, ldab, N, kl, ku, 0, 0, ipiv, jua, state);
+}
+
+// Elimination step of column j, one launch per column. Column j is read as it stands (final, not
+// yet interchanged or scaled): the multiplier of row j + r is l_r = A'(j + r, j) / A(j + jp, j),
+// A' being column j with rows j and j + jp interchanged. Block b updates columns j + 1 + b,
+// j + 1 + b + gridDim.x, ... up to jua[j]: row j takes the pivot row's value u = A(j + jp, c)
+// and row j + r becomes A'(j + r, c) - l_r u. The block that owns column j + 1 (block 0) then
+// searches its pivot for the next launch, and the last block stores column j - 1's multipliers
+// and pivot (no block of this launch reads that column).
+__global__ void __launch_bounds__(BAND_STEP_THREADS) band_step_kernel(double* __restrict__ AB, int64_t ldab, int N,
+                                                                      int kl, int ku, int j, int* __restrict__ ipiv,
+                                                                      int* __restrict__ jua, int* __restrict__ state) {
+  __shared__ int s_stop;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_stop = state[1];
+  __syncthreads();
+  if (s_stop != 0) return;  // an earlier column was singular (uniform within the block)
   const int64_t kv = kl + ku;
   const int km = kl < N - 1 - j ? kl : N - 1 - j;
-  const int ncols = state[0] - j;
-  if (km <= 0 || ncols <= 0) return;
-  const int64_t total = (int64_t)km * ncols;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int c = j + 1 + (int)(t / km), r = 1 + (int)(t % km);
-    AB[(kv + r + j - c) + (int64_t)c * ldab] -= AB[kv + r + (int64_t)j * ldab] * AB[(kv + j - c) + (int64_t)c * ldab];
+  const int jp = ipiv[j] - j;
+  const int ju = jua[j];
+  const double* colj = AB + (int64_t)j * ldab + kv;  // colj[r] = A(j + r, j)
+  const double rp = 1.0 / colj[jp], ajj = colj[0];
+  for (int c = j + 1 + blockIdx.x; c <= ju; c += gridDim.x) {
+    double* colc = AB + (int64_t)c * ldab + (kv + j - c);  // colc[r] = A(j + r, c)
+    const double u = colc[jp], old = colc[0];
+    __syncthreads();  // every thread holds u and old before the column is written
+    for (int r = 1 + tid; r <= km; r += BAND_STEP_THREADS) {
+      const double l = (r == jp ? ajj : colj[r]) * rp;
+      const double v = r == jp ? old : colc[r];
+      colc[r] = fma(-l, u, v);
+    }
+    if (jp != 0 && tid == 0) colc[0] = u;
+    if (c == j + 1) {  // column j + 1 is final now: its pivot for the next launch
+      __syncthreads();
+      band_pivot_search(AB, ldab, N, kl, ku, j + 1, ju, ipiv, jua, state);
+    }
+  }
+  if (j >= 1 && blockIdx.x == gridDim.x - 1) {
+    const int jc = j - 1;
+    double* cc = AB + (int64_t)jc * ldab + kv;
+    const int jpc = ipiv[jc] - jc;
+    const int kmc = kl < N - 1 - jc ? kl : N - 1 - jc;
+    const double pc = cc[jpc], acc = cc[0];
+    const double rpc = 1.0 / pc;
+    __syncthreads();  // every thread holds pc and acc before the column is written
+    for (int r = 1 + tid; r <= kmc; r += BAND_STEP_THREADS) cc[r] = (r == jpc ? acc : cc[r]) * rpc;
+    if (tid == 0) cc[0] = pc;
   }
 }
 
@@ -1038,6 +1098,34 @@ __global__ void __launch_bounds__(BAND_THREADS) band_solve_kernel(const double* 
 
 constexpr size_t BAND_MAX_BYTES = (size_t)4 << 30;
 
+// Half-width kl = ku of the instance's band (4 times its largest node-number distance, plus 3) and
+// whether its band storage fits BAND_MAX_BYTES; w.band[1..3] are zeroed for the factorisation.
+static int band_shape(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits) {
+  const Mesh& m = ctx_mesh(ctx);
+  SolverWork& w = ctx_solver(ctx);
+  cudaStream_t st = ctx_stream(ctx);
+  const int64_t nodes = R.nodes(), n = 4 * nodes;
+  int bw = 0;
+  if (nodes == 0) {
+    *kl_out = 3;
+    *fits = true;
+    return VMS_OK;
+  }
+  cudaMemsetAsync(w.band, 0, sizeof(int) * 4, st);
+  {
+    KScope k(ctx, VMS_K_PRECOND);
+    band_width_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(m.rowptr, m.colidx, R.n0, nodes, w.band);
+    k.add(1);
+  }
+  cudaMemcpyAsync(&bw, w.band, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  *kl_out = 4 * bw + 3;
+  const double ldab = 3.0 * *kl_out + 1.0;
+  *fits = n <= INT32_MAX / 2 && sizeof(double) * ldab * (double)n <= (double)BAND_MAX_BYTES;
+  return VMS_OK;
+}
+
 // The instance's system S x = -rhs by banded LU into w.x; *rel_out = |b - S x| / |b| (the matrix
 // the assembly left, FP32 or FP64 values). VMS_ERR_UNSUPPORTED if the band would exceed
 // BAND_MAX_BYTES, VMS_ERR_ZERO_PIVOT for a singular band.
@@ -1052,35 +1140,28 @@ static int band_direct(vms_ctx* ctx, const SysRange& R, double* rel_out) {
     *rel_out = 0.0;
     return VMS_OK;
   }
-  if (n > INT32_MAX / 2) return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "band solve: system too large");
-  int* d_int = nullptr;  // [0] band width, [1..2] state, [3] scatter error
-  cudaError_t e = cudaMalloc(&d_int, sizeof(int) * 4);
-  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_OUT_OF_MEMORY, cudaGetErrorString(e));
-  int h[4] = {0, 0, 0, 0};
-  cudaMemsetAsync(d_int, 0, sizeof(int) * 4, st);
-  {
-    KScope k(ctx, VMS_K_PRECOND);
-    band_width_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(m.rowptr, m.colidx, R.n0, nodes, d_int);
-    k.add(1);
-  }
-  cudaMemcpyAsync(h, d_int, sizeof(int), cudaMemcpyDeviceToHost, st);
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) { cudaFree(d_int); return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e)); }
-  const int kl = 4 * h[0] + 3, ku = kl;
+  int kl = 0;
+  bool fits = false;
+  if (int rc = band_shape(ctx, R, &kl, &fits)) return rc;
+  if (!fits) return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "band solve: band too large");
+  const int ku = kl;
   const int64_t ldab = 2 * (int64_t)kl + ku + 1;
   const size_t bytes = sizeof(double) * (size_t)ldab * (size_t)n;
-  if (bytes > BAND_MAX_BYTES) { cudaFree(d_int); return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "band solve: band too large"); }
+  int* d_int = w.band;  // [1] the first singular column + 1, [3] scatter error
+  int h[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaSuccess;
   double* AB = nullptr;
   int* ipiv = nullptr;
   e = cudaMalloc(&AB, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&ipiv, sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&ipiv, sizeof(int) * 2 * n);
+  int* jua = ipiv + n;  // per column: the last column the interchanges up to it reach
   if (e != cudaSuccess) {
     cudaGetLastError();  // an allocation failure is not sticky: clear it for the caller's checks
-    cudaFree(AB); cudaFree(d_int);
+    cudaFree(AB);
     return ctx_fail(ctx, VMS_ERR_OUT_OF_MEMORY, cudaGetErrorString(e));
   }
   cudaMemsetAsync(AB, 0, bytes, st);
-  cudaMemsetAsync(ipiv, 0, sizeof(int) * n, st);
+  cudaMemsetAsync(ipiv, 0, sizeof(int) * 2 * n, st);
   {
     KScope kf(ctx, VMS_K_PRECOND);
     const unsigned wb = (unsigned)((nodes * 32 + 255) / 256);
@@ -1088,25 +1169,24 @@ static int band_direct(vms_ctx* ctx, const SysRange& R, double* rel_out) {
       band_scatter_kernel<float><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
     else
       band_scatter_kernel<double><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
-    const int64_t upd = (int64_t)kl * (kl + ku);
-    const unsigned ub = (unsigned)std::min<int64_t>((upd + 255) / 256, 4 * (int64_t)sm_count());
-    for (int j = 0; j < (int)n; ++j) {
-      band_pivot_kernel<<<1, BAND_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, j, ipiv, d_int + 1);
-      band_update_kernel<<<ub, 256, 0, st>>>(AB, ldab, (int)n, kl, ku, j, d_int + 1);
-    }
+    const unsigned gb = (unsigned)std::min<int64_t>((int64_t)kl + ku, 4 * (int64_t)sm_count());
+    band_first_pivot_kernel<<<1, BAND_STEP_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, ipiv, jua, d_int);
+    for (int j = 0; j < (int)n; ++j)
+      band_step_kernel<<<gb, BAND_STEP_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, j, ipiv, jua, d_int);
     // b = -rhs into w.rb, x = b into w.x, forward and backward substitution
     axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(-1.0, wk.rhs + 4 * R.n0, 0.0, (const double*)nullptr, w.rb, n);
     cudaMemcpyAsync(w.x, w.rb, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    band_solve_kernel<<<1, BAND_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, ipiv, d_int + 1, w.x);
-    kf.add(3 + 2 * (int)n);
+    band_solve_kernel<<<1, BAND_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, ipiv, d_int, w.x);
+    kf.add(4 + (int)n);
   }
   cudaMemcpyAsync(h + 1, d_int + 1, sizeof(int) * 3, cudaMemcpyDeviceToHost, st);
   e = cudaStreamSynchronize(st);
-  cudaFree(AB); cudaFree(ipiv); cudaFree(d_int);
+  cudaFree(AB);
+  cudaFree(ipiv);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
   if (h[3] != 0) return ctx_fail(ctx, VMS_ERR_CUDA, "band solve: an entry outside the band");
-  if (h[2] != 0) return ctx_fail(ctx, VMS_ERR_ZERO_PIVOT, "band solve: singular system");
+  if (h[1] != 0) return ctx_fail(ctx, VMS_ERR_ZERO_PIVOT, "band solve: singular system");
   // relative residual |b - S x| / |b|
   double* y = w.rfull;
   KScope ks(ctx, VMS_K_SPMV);

@@ -31,6 +31,7 @@ struct SolverWork {
   int zf_restart = 0;
   double* xb = nullptr;      // n: refinement iterate before the last FP32 correction
   double* rb = nullptr;      // n: its FP64 residual
+  int* band = nullptr;       // 4 ints: the banded direct solve's width, state and error words
   Ilu ilu;                   // ILU(0) pattern, factor and sweep work
   bool use_ilu = false;      // preconditioner of the current solve: ILU(0) or block Jacobi
   uint64_t ilu_for = 0;      // assembly the ILU(0) factor was computed for (0: none)

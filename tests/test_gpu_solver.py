@@ -259,8 +259,8 @@ def test_fallback_solves_a_system_whose_ilu0_is_unstable():
     """A coarse high-Reynolds cavity (12^3, Re 719, random state, one of the batch's instances):
     its ILU(0) factor is unstable (CPU study: |M^-1 v| / |A^-1 v| ~ 1e7 and more) and GMRES with it
     stalls. Block Jacobi with GMRES(480) reaches the batch's per-instance target of 1e-2;
-    VMS_PRECOND_ILU0_FALLBACK solves the system directly (banded LU with partial pivoting, FP64),
-    and the solution's residual, taken on the host with the downloaded CSR matrix, is at rounding
+    VMS_PRECOND_ILU0_FALLBACK ends the stagnating ILU(0) attempt early and solves the system
+    directly (banded LU with partial pivoting, FP64), and the solution's residual, taken on the host with the downloaded CSR matrix, is at rounding
     level."""
     from paper_0809_4802_gb300 import build, vms
     build.build()
@@ -282,7 +282,9 @@ def test_fallback_solves_a_system_whose_ilu0_is_unstable():
     u0 = ctx.state_download()[0]
     ctx.set_preconditioner(vms.PRECOND_ILU0_FALLBACK)
     it, rel = ctx.solve(rtol=1e-2, maxit=3000, restart=150, update=True)
-    assert it >= 3000 and rel <= 1e-9   # the ILU(0) attempt's iterations; the direct solve's residual
+    # the ILU(0) attempt ends early (its cycles' rate would not reach 1e-2 within maxit), then the
+    # direct solve's residual
+    assert 0 < it < 3000 and rel <= 1e-9, (it, rel)
     du = (ctx.state_download()[0] - u0).reshape(-1)
     du[wl.bc.dofs] = 0.0   # the update also imposes the boundary values
     assert np.linalg.norm(G @ du + rhs) <= 1e-9 * np.linalg.norm(rhs)
