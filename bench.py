@@ -722,7 +722,7 @@ def ours(args):
         ctx = make_ctx(prec)
         ctx.set_preconditioner(vms.PRECOND_ILU0_FALLBACK)
         ctx.assemble()
-        times, iters, fails, direct, direct_ms = [], [], 0, 0, []
+        times, iters, iters_all, fails, direct, direct_ms = [], [], [], 0, 0, []
         for i in range(len(batch.members)):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -733,6 +733,7 @@ def ours(args):
                 it = None
                 fails += 1
             times.append(time.perf_counter() - t0)
+            iters_all.append(it)
             if it is not None and it >= 3000:   # the Krylov attempt stopped at maxit: fallback solve
                 direct += 1
                 direct_ms.append(times[-1] * 1e3)
@@ -745,6 +746,10 @@ def ours(args):
                         "krylov_iterations_median": float(np.median(iters)) if iters else None,
                         "fallback_solves": direct,
                         "fallback_ms": [round(t, 1) for t in direct_ms],
+                        "slowest": [{"instance": int(k), "nodes": int(batch.node_offsets[k + 1] - batch.node_offsets[k]),
+                                     "krylov_iterations": iters_all[k], "ms": round(float(ms_i[k]), 1)}
+                                    for k in np.argsort(ms_i)[::-1][:4]],
+                        "note": "instance 0's time includes the ILU(0) factorisation of the whole merged matrix",
                         "solver": "FP32 GMRES(150) + FP64 refinement, block ILU(0) (FP64-eliminated, FP32 sweeps); "
                                   "a solve that reaches maxit is repeated by a banded LU with partial pivoting "
                                   "(FP64, on the device) (VMS_PRECOND_ILU0_FALLBACK)"}
