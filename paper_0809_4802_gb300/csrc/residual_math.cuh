@@ -6,11 +6,12 @@
 // value costs 7 FMA and a reference gradient 9 FMA. Test functions are accumulated in the same
 // basis and mapped back to nodes once per element (nodal8).
 //
-// With omega = w_q det J, cof = det(J) J^-T and G[i][al] = dv_i/dxi_al:
-//   omega conv_i = w_q sum_al G[i][al] (cof^T v)_al
+// With omega = w_q det J, cof = det(J) J^-T, G[i][al] = dv_i/dxi_al and H = G cof^T (H[i][j] =
+// det J dv_i/dx_j, the physical velocity gradient L times det J):
+//   omega conv_i = w_q (H v)_i
 //   P[i][al] = omega sum_j sigma_ij (J^-1)[al][j],  sigma = nut L - p I
-//            = w_q ( (nut/det) sum_be G[i][be] (cof^T cof)[be][al] - p cof[i][al] )
-//   Tp = -omega tr L = -w_q sum_{i,al} G[i][al] cof[i][al]
+//            = w_q sum_j ( (nut/det) H[i][j] - p delta_ij ) cof[j][al]
+//   Tp = -omega tr L = -w_q tr H
 // so R_c[a][i] = sum_q N_a src_i + dN_a/dxi_al P[i][al], R_p[a] = sum_q N_a Tp,
 // R_f[i] = sum_q b src_i + db/dxi_al P[i][al], src_i = omega (conv_i - f_i + tau dvbar_i).
 // One reciprocal (1/det J) per quadrature point.
@@ -135,7 +136,6 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         double cof[3][3];
         double det = cofactor3(J, cof);
         if (!(det >= DET_MIN)) { ok = false; det = 1.0; }
-        const double om = wq * det;
 
         double v[3], G[3][3];
         VMS_UNROLL
@@ -147,38 +147,42 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         }
         const double p = pa + xi * pb;
 
-        double wv[3];
+        // H = G cof^T: det J times the physical velocity gradient (H[i][j] = det dv_i/dx_j)
+        double H[3][3];
         VMS_UNROLL
-        for (int al = 0; al < 3; ++al)
-          wv[al] = wq * (cof[0][al] * v[0] + cof[1][al] * v[1] + cof[2][al] * v[2]);
+        for (int i = 0; i < 3; ++i)
+          VMS_UNROLL
+          for (int j = 0; j < 3; ++j)
+            H[i][j] = G[i][0] * cof[j][0] + G[i][1] * cof[j][1] + G[i][2] * cof[j][2];
+        // src_i = w_q (H v - det f + tau det (vbar - vbar_n))_i, Tp = -w_q tr H
+        double y[3];
         VMS_UNROLL
-        for (int i = 0; i < 3; ++i) o.src[i] = G[i][0] * wv[0] + G[i][1] * wv[1] + G[i][2] * wv[2];
+        for (int i = 0; i < 3; ++i) y[i] = H[i][0] * v[0] + H[i][1] * v[1] + H[i][2] * v[2];
         if (FORCE) {
           VMS_UNROLL
-          for (int i = 0; i < 3; ++i) o.src[i] -= om * f[i];
+          for (int i = 0; i < 3; ++i) y[i] -= det * f[i];
         }
         if (TRANSIENT) {
-          const double tom = tau * om;
+          const double td = tau * det;
           VMS_UNROLL
-          for (int i = 0; i < 3; ++i) o.src[i] += tom * (dva[i] + xi * dvb[i]);
+          for (int i = 0; i < 3; ++i) y[i] += td * (dva[i] + xi * dvb[i]);
         }
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i) o.src[i] = wq * y[i];
+        o.Tp = -wq * (H[0][0] + H[1][1] + H[2][2]);
+        // P = (s H - w_q p I) cof with s = w_q nut / det: w_q (nut L - p I) times det J^-T
         const double s = wq * nut * recip_normal(det);
-        const double A00 = s * (cof[0][0] * cof[0][0] + cof[1][0] * cof[1][0] + cof[2][0] * cof[2][0]);
-        const double A11 = s * (cof[0][1] * cof[0][1] + cof[1][1] * cof[1][1] + cof[2][1] * cof[2][1]);
-        const double A22 = s * (cof[0][2] * cof[0][2] + cof[1][2] * cof[1][2] + cof[2][2] * cof[2][2]);
-        const double A01 = s * (cof[0][0] * cof[0][1] + cof[1][0] * cof[1][1] + cof[2][0] * cof[2][1]);
-        const double A02 = s * (cof[0][0] * cof[0][2] + cof[1][0] * cof[1][2] + cof[2][0] * cof[2][2]);
-        const double A12 = s * (cof[0][1] * cof[0][2] + cof[1][1] * cof[1][2] + cof[2][1] * cof[2][2]);
-        const double wp = wq * p;
-        double trw = 0.0;
+        const double nwp = -wq * p;
+        VMS_UNROLL
+        for (int i = 0; i < 3; ++i)
+          VMS_UNROLL
+          for (int j = 0; j < 3; ++j) H[i][j] = i == j ? s * H[i][j] + nwp : s * H[i][j];
         VMS_UNROLL
         for (int i = 0; i < 3; ++i) {
-          o.P0[i] = G[i][0] * A00 + G[i][1] * A01 + G[i][2] * A02 - wp * cof[i][0];
-          o.P1[i] = G[i][0] * A01 + G[i][1] * A11 + G[i][2] * A12 - wp * cof[i][1];
-          o.P2[i] = G[i][0] * A02 + G[i][1] * A12 + G[i][2] * A22 - wp * cof[i][2];
-          trw += G[i][0] * cof[i][0] + G[i][1] * cof[i][1] + G[i][2] * cof[i][2];
+          o.P0[i] = H[i][0] * cof[0][0] + H[i][1] * cof[1][0] + H[i][2] * cof[2][0];
+          o.P1[i] = H[i][0] * cof[0][1] + H[i][1] * cof[1][1] + H[i][2] * cof[2][1];
+          o.P2[i] = H[i][0] * cof[0][2] + H[i][1] * cof[1][2] + H[i][2] * cof[2][2];
         }
-        o.Tp = -wq * trw;
       };
       // line sums: src, xi src, P0, P1, xi P1, P2, xi P2 (per component), Tp, xi Tp. The points
       // are taken in symmetric pairs (-x, x): the Gauss points are symmetric about 0 (the middle
@@ -316,13 +320,13 @@ __device__ __forceinline__ unsigned residual_element(
       }
     }
     {
-      double P[8];
+      double pn[8];
       VMS_UNROLL
       for (int a = 0; a < 8; ++a) {
         const double4_32a w = u[nd[a]];
-        U[a][0] = w.x; U[a][1] = w.y; U[a][2] = w.z; P[a] = w.w;
+        U[a][0] = w.x; U[a][1] = w.y; U[a][2] = w.z; pn[a] = w.w;
       }
-      modal8(P, c);
+      modal8(pn, c);
       VMS_UNROLL
       for (int m = 0; m < 8; ++m) C.set(RC_P + m, 0.125 * c[m]);
     }
