@@ -81,40 +81,49 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
   Rf[0] = Rf[1] = Rf[2] = 0.0;
   bool ok = true;
   for (int k = 0; k < n1; ++k) {
+    // plane constants (zeta fixed): the parts of the line constants that do not depend on eta
+    const double zeta = tab.zeta(k * n1 * n1);
+    double aj0[3], j1a[3], j1b[3], g1a[3], g1b[3], ava[3], avb[3], ada[3], bda[3], adb[3], bdb[3];
+    VMS_UNROLL
+    for (int i = 0; i < 3; ++i) {
+      aj0[i] = C.get(RC_X + 7 * i + 0) + C.get(RC_X + 7 * i + 4) * zeta;
+      j1a[i] = C.get(RC_X + 7 * i + 1) + C.get(RC_X + 7 * i + 5) * zeta;
+      j1b[i] = C.get(RC_X + 7 * i + 3) + C.get(RC_X + 7 * i + 6) * zeta;
+      g1a[i] = C.get(RC_V + 8 * i + 2) + C.get(RC_V + 8 * i + 6) * zeta;
+      g1b[i] = C.get(RC_V + 8 * i + 4) + C.get(RC_V + 8 * i + 7) * zeta;
+      ava[i] = C.get(RC_V + 8 * i + 0) + C.get(RC_V + 8 * i + 3) * zeta;
+      avb[i] = C.get(RC_V + 8 * i + 1) + C.get(RC_V + 8 * i + 5) * zeta;
+      if (TRANSIENT) {
+        ada[i] = C.get(RC_DV + 8 * i + 0) + C.get(RC_DV + 8 * i + 3) * zeta;
+        bda[i] = C.get(RC_DV + 8 * i + 2) + C.get(RC_DV + 8 * i + 6) * zeta;
+        adb[i] = C.get(RC_DV + 8 * i + 1) + C.get(RC_DV + 8 * i + 5) * zeta;
+        bdb[i] = C.get(RC_DV + 8 * i + 4) + C.get(RC_DV + 8 * i + 7) * zeta;
+      }
+    }
+    const double apa = C.get(RC_P + 0) + C.get(RC_P + 3) * zeta, bpa = C.get(RC_P + 2) + C.get(RC_P + 6) * zeta;
+    const double apb = C.get(RC_P + 1) + C.get(RC_P + 5) * zeta, bpb = C.get(RC_P + 4) + C.get(RC_P + 7) * zeta;
     for (int j = 0; j < n1; ++j) {
       const int q0 = (k * n1 + j) * n1;
-      const double eta = tab.eta(q0), zeta = tab.zeta(q0), ez = tab.ez(q0);
+      const double eta = tab.eta(q0), ez = tab.ez(q0);
       // line constants: along the line J[i][1] = j1a + xi j1b, J[i][2] = j2a + xi j2b, and the
-      // same for the reference velocity gradient (g1a, g1b, g2a, g2b)
-      double J0[3], vb[3], va[3], dva[3], dvb[3];
-      double j1a[3], j1b[3], j2a[3], j2b[3], g1a[3], g1b[3], g2a[3], g2b[3];
+      // same for the reference velocity gradient (g1a, g1b, g2a, g2b); every trilinear field is
+      // its plane part plus eta times its eta-slope
+      double J0[3], vb[3], va[3], dva[3], dvb[3], j2a[3], j2b[3], g2a[3], g2b[3];
       VMS_UNROLL
       for (int i = 0; i < 3; ++i) {
-        J0[i] = C.get(RC_X + 7 * i + 0) + C.get(RC_X + 7 * i + 3) * eta +
-                C.get(RC_X + 7 * i + 4) * zeta + C.get(RC_X + 7 * i + 6) * ez;
-        j1a[i] = C.get(RC_X + 7 * i + 1) + C.get(RC_X + 7 * i + 5) * zeta;
-        j1b[i] = C.get(RC_X + 7 * i + 3) + C.get(RC_X + 7 * i + 6) * zeta;
+        J0[i] = aj0[i] + j1b[i] * eta;
         j2a[i] = C.get(RC_X + 7 * i + 2) + C.get(RC_X + 7 * i + 5) * eta;
         j2b[i] = C.get(RC_X + 7 * i + 4) + C.get(RC_X + 7 * i + 6) * eta;
-        g1a[i] = C.get(RC_V + 8 * i + 2) + C.get(RC_V + 8 * i + 6) * zeta;
-        g1b[i] = C.get(RC_V + 8 * i + 4) + C.get(RC_V + 8 * i + 7) * zeta;
         g2a[i] = C.get(RC_V + 8 * i + 3) + C.get(RC_V + 8 * i + 6) * eta;
         g2b[i] = C.get(RC_V + 8 * i + 5) + C.get(RC_V + 8 * i + 7) * eta;
-        vb[i] = C.get(RC_V + 8 * i + 1) + C.get(RC_V + 8 * i + 4) * eta +
-                C.get(RC_V + 8 * i + 5) * zeta + C.get(RC_V + 8 * i + 7) * ez;
-        va[i] = C.get(RC_V + 8 * i + 0) + C.get(RC_V + 8 * i + 2) * eta +
-                C.get(RC_V + 8 * i + 3) * zeta + C.get(RC_V + 8 * i + 6) * ez;
+        vb[i] = avb[i] + g1b[i] * eta;
+        va[i] = ava[i] + g1a[i] * eta;
         if (TRANSIENT) {
-          dva[i] = C.get(RC_DV + 8 * i + 0) + C.get(RC_DV + 8 * i + 2) * eta +
-                   C.get(RC_DV + 8 * i + 3) * zeta + C.get(RC_DV + 8 * i + 6) * ez;
-          dvb[i] = C.get(RC_DV + 8 * i + 1) + C.get(RC_DV + 8 * i + 4) * eta +
-                   C.get(RC_DV + 8 * i + 5) * zeta + C.get(RC_DV + 8 * i + 7) * ez;
+          dva[i] = ada[i] + bda[i] * eta;
+          dvb[i] = adb[i] + bdb[i] * eta;
         }
       }
-      const double pa = C.get(RC_P + 0) + C.get(RC_P + 2) * eta + C.get(RC_P + 3) * zeta +
-                        C.get(RC_P + 6) * ez;
-      const double pb = C.get(RC_P + 1) + C.get(RC_P + 4) * eta + C.get(RC_P + 5) * zeta +
-                        C.get(RC_P + 7) * ez;
+      const double pa = apa + bpa * eta, pb = apb + bpb * eta;
       // One point of the line: its source term src_i, the fluxes P_al,i paired with the
       // reference-gradient components of the test functions, and the continuity term Tp.
       struct Pt {
