@@ -33,18 +33,18 @@ UNIT = "elements/s"
 # ~300, tangent blocks K_vv ~1.7k + K_vp ~0.4k + fine-coupled blocks ~0.5k) plus the condensation
 # (~7k flops per element). The kernels execute fewer flops than these counts where their
 # formulation needs fewer; `executed` gives ncu opcode counts (FMA = 2 flops) on the 32^3 cavity:
-# the FP64 residual's line-factored monomial form 9,805, the FP64 tangent's factorised sums 46,194,
-# the fused kernel's FP64 part (residual + the tangent's FP64 K_ff work) 10,257, the tetrahedral
+# the FP64 residual's line-factored monomial form 8,614, the FP64 tangent's factorised sums 41,472,
+# the fused kernel's FP64 part (residual + the tangent's FP64 K_ff work) 9,066, the tetrahedral
 # kernel 5,894 (21^3 tetrahedral cavity).
 ALG_FLOPS = {"residual": (600 + 300) * 27, "tangent": (600 + 1700 + 400 + 500) * 27 + 7000}
-EXECUTED_FLOPS = {"residual": 9_805, "tangent_fp64": 46_194, "fused_fp64": 10_257, "tet": 5_894}
+EXECUTED_FLOPS = {"residual": 8_614, "tangent_fp64": 41_472, "fused_fp64": 9_066, "tet": 5_894}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the
 # current kernels on the named workloads (profiles/); no entry where none was taken.
-NCU_TRAFFIC_BYTES = {("fused", "cavity32_re400_mixed"): 68_560_896 + 34_596_096,
-                     ("fused", "channel_re1000_mixed"): 2_073_034_240 + 3_074_973_696,
-                     ("residual", "cavity32_re400_fp64"): 4_228_096 + 256,
-                     ("tangent", "cavity32_re400_fp64"): 119_539_968 + 101_357_312,
+NCU_TRAFFIC_BYTES = {("fused", "cavity32_re400_mixed"): 68_553_472 + 34_592_256,
+                     ("fused", "channel_re1000_mixed"): 2_074_687_744 + 3_088_019_200,
+                     ("residual", "cavity32_re400_fp64"): 4_223_232 + 0,
+                     ("tangent", "cavity32_re400_fp64"): 119_540_480 + 101_472_512,
                      ("tangent", "tetcavity21_re400_mixed"): 15_459_584 + 27_136}
 
 WORKLOADS = {
