@@ -213,7 +213,7 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
           const double u0 = hi.P0[i] + lo.P0[i], w0 = hi.P0[i] - lo.P0[i];
           const double u1 = hi.P1[i] + lo.P1[i], w1 = hi.P1[i] - lo.P1[i];
           const double u2 = hi.P2[i] + lo.P2[i], w2 = hi.P2[i] - lo.P2[i];
-          Rf[i] += bh * us + e0 * w0 + e1 * u1 + e2 * u2;
+          Rf[i] = Rf[i] + bh * us + e0 * w0 + e1 * u1 + e2 * u2;
           if (pp == 0) {
             s0[i] = us; s1[i] = x * ws; b0[i] = u0; c0[i] = u1; c1[i] = x * w1; d0[i] = u2;
             d1[i] = x * w2;
@@ -234,7 +234,7 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         const double bm = tab.b(qm), e1 = tab.db(qm, 1), e2 = tab.db(qm, 2);
         VMS_UNROLL
         for (int i = 0; i < 3; ++i) {
-          Rf[i] += bm * m.src[i] + e1 * m.P1[i] + e2 * m.P2[i];
+          Rf[i] = Rf[i] + bm * m.src[i] + e1 * m.P1[i] + e2 * m.P2[i];
           s0[i] += m.src[i]; b0[i] += m.P0[i]; c0[i] += m.P1[i]; d0[i] += m.P2[i];
         }
         t0 += m.Tp;
@@ -251,8 +251,8 @@ VMS_HD bool residual_qp_loop_n(const Store& C, const Table& tab, const double be
         C.set(r + 3, C.get(r + 3) + (zeta * s0[i] + d0[i]));
         C.set(r + 4, C.get(r + 4) + (eta * sb + c1[i]));
         C.set(r + 5, C.get(r + 5) + (zeta * sb + d1[i]));
-        C.set(r + 6, C.get(r + 6) + (ez * s0[i] + zeta * c0[i] + eta * d0[i]));
-        C.set(r + 7, C.get(r + 7) + (ez * sb + zeta * c1[i] + eta * d1[i]));
+        C.set(r + 6, C.get(r + 6) + ez * s0[i] + zeta * c0[i] + eta * d0[i]);
+        C.set(r + 7, C.get(r + 7) + ez * sb + zeta * c1[i] + eta * d1[i]);
       }
       C.set(RC_RP + 0, C.get(RC_RP + 0) + t0);
       C.set(RC_RP + 1, C.get(RC_RP + 1) + t1);
