@@ -22,6 +22,8 @@ void free_solver(SolverWork& s) {
                   s.xb, s.rb, s.band};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  for (BandOrder& o : s.band_orders)
+    if (o.perm) cudaFree(o.perm);
   const uint32_t lim = s.ilu.spin_limit;  // a setting of the context, kept across re-allocations
   free_ilu(s.ilu);
   s = SolverWork();
@@ -930,39 +932,31 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
 // interchanges and multipliers forward and U backward. FP64 throughout.
 // ---------------------------------------------------------------------------------------------
 
-// the largest node distance |col node - row node| of the instance's rows
-__global__ void band_width_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                  int64_t n0, int64_t nodes, int* __restrict__ bw) {
-  const int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (nd >= nodes) return;
-  const int64_t g = n0 + nd;
-  const int32_t r0 = rowptr[4 * g], r1 = rowptr[4 * g + 1];
-  int w = 0;
-  for (int32_t t = r0; t < r1; t += 4) {
-    const int64_t d = (int64_t)(colidx[t] >> 2) - g;
-    const int a = (int)(d < 0 ? -d : d);
-    w = a > w ? a : w;
-  }
-  atomicMax(bw, w);
-}
-
-// the instance's rows into the band (one warp per node row, one lane per 4x4 block)
+// the block's rows into the band in the band order perm (one warp per node row, one lane per 4x4
+// block): entry (4 perm[a] + r, 4 perm[c] + m)
 template <typename T>
 __global__ void band_scatter_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                    const T* __restrict__ val, int64_t n0, int64_t nodes, double* __restrict__ AB,
-                                    int64_t ldab, int kl, int ku, int* __restrict__ err) {
+                                    const T* __restrict__ val, const int32_t* __restrict__ perm, int64_t n0,
+                                    int64_t nodes, double* __restrict__ AB, int64_t ldab, int kl, int ku,
+                                    int* __restrict__ err) {
   const int64_t nd = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (nd >= nodes) return;
   const int64_t g = n0 + nd, N = 4 * nodes, kv = kl + ku;
+  const int64_t pr = perm[nd];
   int32_t rp[4];
   for (int m = 0; m < 4; ++m) rp[m] = rowptr[4 * g + m];
   const int deg = (rp[1] - rp[0]) >> 2;
   for (int kk = lane; kk < deg; kk += 32) {
-    const int64_t c = (int64_t)colidx[rp[0] + 4 * kk] - 4 * n0;
+    const int64_t hc = (int64_t)(colidx[rp[0] + 4 * kk] >> 2) - n0;
+    if (hc < 0 || hc >= nodes) {
+      atomicOr(err, 1);
+      continue;
+    }
+    const int64_t pc = perm[hc];
     for (int r = 0; r < 4; ++r)
       for (int m = 0; m < 4; ++m) {
-        const int64_t i = 4 * nd + r, j = c + m;
+        const int64_t i = 4 * pr + r, j = 4 * pc + m;
         if (j < 0 || j >= N || i - j > kl || j - i > ku) {
           atomicOr(err, 1);
           continue;
@@ -970,6 +964,16 @@ __global__ void band_scatter_kernel(const int32_t* __restrict__ rowptr, const in
         AB[(kv + i - j) + j * ldab] = (double)val[rp[r] + 4 * kk + m];
       }
   }
+}
+
+// b[4 perm[a] + r] = s v[4 a + r] (to the band order) or v[4 a + r] = b[4 perm[a] + r] (back)
+__global__ void band_permute_kernel(const double* __restrict__ v, const int32_t* __restrict__ perm,
+                                    int64_t nodes, double s, double* __restrict__ b, int to_band) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * nodes) return;
+  const int64_t a = t >> 2, r = t & 3, q = 4 * (int64_t)perm[a] + r;
+  if (to_band) b[q] = s * v[t];
+  else b[t] = v[q];
 }
 
 constexpr int BAND_THREADS = 1024;  // the substitution kernel's block
@@ -1098,29 +1102,167 @@ __global__ void __launch_bounds__(BAND_THREADS) band_solve_kernel(const double* 
 
 constexpr size_t BAND_MAX_BYTES = (size_t)4 << 30;
 
-// Half-width kl = ku of the instance's band (4 times its largest node-number distance, plus 3) and
-// whether its band storage fits BAND_MAX_BYTES; w.band[1..3] are zeroed for the factorisation.
-static int band_shape(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits) {
-  const Mesh& m = ctx_mesh(ctx);
+// Blocks above this many nodes are not ordered for the direct solve (their band would not fit).
+constexpr int64_t BAND_ORDER_MAX_NODES = 262144;
+
+// The block's band order: the one of smallest bandwidth among the block's own node order and two
+// reverse Cuthill-McKee orders (George and Liu): breadth-first numbering with the neighbours of a
+// node queued in order of increasing degree, reversed, started from a pseudo-peripheral node
+// (repeated searches from a node of least degree in the last level while the number of levels
+// grows) or from the whole last level of its level structure. On a lattice numbered line by line
+// the block's own order is the best of the three; on an elongated box the start from a whole end
+// face is (the corner's levels are shells of up to three faces). Computed on the host from the
+// block's node pattern once per mesh.
+static int band_order(vms_ctx* ctx, const SysRange& R, const BandOrder** out) {
   SolverWork& w = ctx_solver(ctx);
-  cudaStream_t st = ctx_stream(ctx);
-  const int64_t nodes = R.nodes(), n = 4 * nodes;
-  int bw = 0;
-  if (nodes == 0) {
-    *kl_out = 3;
-    *fits = true;
+  for (const BandOrder& o : w.band_orders)
+    if (o.n0 == R.n0 && o.n1 == R.n1) {
+      *out = &o;
+      return VMS_OK;
+    }
+  BandOrder o;
+  o.n0 = R.n0;
+  o.n1 = R.n1;
+  const int64_t nodes = R.nodes();
+  if (nodes > 0 && nodes <= BAND_ORDER_MAX_NODES) {
+    const Mesh& m = ctx_mesh(ctx);
+    std::vector<int32_t> rp(4 * nodes + 1);
+    cudaError_t e = cudaMemcpy(rp.data(), m.rowptr + 4 * R.n0, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost);
+    const int32_t c0 = rp[0];
+    std::vector<int32_t> ci(e == cudaSuccess ? (size_t)(rp[4 * nodes] - c0) : 0);
+    if (e == cudaSuccess && !ci.empty())
+      e = cudaMemcpy(ci.data(), m.colidx + c0, sizeof(int32_t) * ci.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+    // node adjacency (the first scalar row of each node carries the node's block columns)
+    std::vector<int32_t> start(nodes + 1, 0), adj;
+    adj.reserve((size_t)(rp[1] - rp[0]) / 4 * nodes);
+    for (int64_t a = 0; a < nodes; ++a) {
+      start[a] = (int32_t)adj.size();
+      for (int32_t t = rp[4 * a] - c0; t < rp[4 * a + 1] - c0; t += 4) {
+        const int64_t b = (int64_t)(ci[t] >> 2) - R.n0;
+        if (b < 0 || b >= nodes) return ctx_fail(ctx, VMS_ERR_INVALID_ARG, "band order: a column outside the block");
+        if (b != a) adj.push_back((int32_t)b);
+      }
+    }
+    start[nodes] = (int32_t)adj.size();
+    auto deg = [&](int64_t a) { return start[a + 1] - start[a]; };
+    auto bandwidth = [&](const std::vector<int32_t>& perm) {
+      int bw = 0;
+      for (int64_t a = 0; a < nodes; ++a)
+        for (int32_t t = start[a]; t < start[a + 1]; ++t) bw = std::max(bw, std::abs(perm[a] - perm[adj[t]]));
+      return bw;
+    };
+    // breadth-first levels from a set of nodes: the depth, and the nodes of the last level
+    std::vector<int32_t> level(nodes), queue;
+    auto levels = [&](const std::vector<int32_t>& src, std::vector<int32_t>& lastv) {
+      std::fill(level.begin(), level.end(), -1);
+      queue.assign(src.begin(), src.end());
+      for (int32_t a : src) level[a] = 0;
+      int depth = 0;
+      for (size_t h = 0; h < queue.size(); ++h) {
+        const int32_t a = queue[h];
+        depth = level[a];
+        for (int32_t t = start[a]; t < start[a + 1]; ++t)
+          if (level[adj[t]] < 0) {
+            level[adj[t]] = level[a] + 1;
+            queue.push_back(adj[t]);
+          }
+      }
+      lastv.clear();
+      for (int32_t a : queue)
+        if (level[a] == depth) lastv.push_back(a);
+      return depth;
+    };
+    // reverse Cuthill-McKee numbering from a set of start nodes (further connected parts from a
+    // node of least degree each); returns perm
+    std::vector<char> placed(nodes);
+    std::vector<int32_t> order, nb;
+    auto rcm = [&](std::vector<int32_t> src) {
+      std::fill(placed.begin(), placed.end(), 0);
+      order.clear();
+      for (int64_t next = 0;;) {
+        std::stable_sort(src.begin(), src.end(), [&](int32_t x, int32_t y) { return deg(x) < deg(y); });
+        const size_t h0 = order.size();
+        for (int32_t a : src) {
+          placed[a] = 1;
+          order.push_back(a);
+        }
+        for (size_t h = h0; h < order.size(); ++h) {
+          const int32_t a = order[h];
+          nb.clear();
+          for (int32_t t = start[a]; t < start[a + 1]; ++t)
+            if (!placed[adj[t]]) {
+              placed[adj[t]] = 1;
+              nb.push_back(adj[t]);
+            }
+          std::stable_sort(nb.begin(), nb.end(), [&](int32_t x, int32_t y) { return deg(x) < deg(y); });
+          for (int32_t x : nb) order.push_back(x);
+        }
+        if ((int64_t)order.size() == nodes) break;
+        while (placed[next]) ++next;
+        int32_t r = (int32_t)next;
+        for (int64_t a = next; a < nodes; ++a)
+          if (!placed[a] && deg(a) < deg(r)) r = (int32_t)a;
+        src.assign(1, r);
+      }
+      std::vector<int32_t> perm(nodes);
+      for (int64_t k = 0; k < nodes; ++k) perm[order[k]] = (int32_t)(nodes - 1 - k);
+      return perm;
+    };
+    std::vector<int32_t> best(nodes);
+    for (int64_t a = 0; a < nodes; ++a) best[a] = (int32_t)a;
+    int bw = bandwidth(best);
+    // a pseudo-peripheral node r of the part holding node 0, and the last level of its levels
+    int32_t r = 0;
+    std::vector<int32_t> last, lc;
+    levels(std::vector<int32_t>(1, 0), last);
+    for (int32_t a : queue)
+      if (deg(a) < deg(r)) r = a;
+    int depth = levels(std::vector<int32_t>(1, r), last);
+    for (int it = 0; it < 8; ++it) {
+      int32_t c = last[0];
+      for (int32_t a : last)
+        if (deg(a) < deg(c)) c = a;
+      const int dc = levels(std::vector<int32_t>(1, c), lc);
+      if (dc <= depth) break;
+      r = c;
+      depth = dc;
+      last.swap(lc);
+    }
+    for (int variant = 0; variant < 2; ++variant) {
+      std::vector<int32_t> perm = rcm(variant == 0 ? std::vector<int32_t>(1, r) : last);
+      const int b = bandwidth(perm);
+      if (b < bw) {
+        bw = b;
+        best.swap(perm);
+      }
+    }
+    e = cudaMalloc(&o.perm, sizeof(int32_t) * nodes);
+    if (e == cudaSuccess) e = cudaMemcpy(o.perm, best.data(), sizeof(int32_t) * nodes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (o.perm) cudaFree(o.perm);
+      return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? VMS_ERR_OUT_OF_MEMORY : VMS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    o.bw = bw;
+  }
+  w.band_orders.push_back(o);
+  *out = &w.band_orders.back();
+  return VMS_OK;
+}
+
+// Half-width kl = ku of the block's band in its band order (4 times the order's bandwidth in nodes,
+// plus 3) and whether the band storage fits BAND_MAX_BYTES.
+static int band_shape(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits) {
+  const int64_t n = 4 * R.nodes();
+  const BandOrder* o = nullptr;
+  if (int rc = band_order(ctx, R, &o)) return rc;
+  if (o->bw < 0) {
+    *kl_out = 0;
+    *fits = false;
     return VMS_OK;
   }
-  cudaMemsetAsync(w.band, 0, sizeof(int) * 4, st);
-  {
-    KScope k(ctx, VMS_K_PRECOND);
-    band_width_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(m.rowptr, m.colidx, R.n0, nodes, w.band);
-    k.add(1);
-  }
-  cudaMemcpyAsync(&bw, w.band, sizeof(int), cudaMemcpyDeviceToHost, st);
-  const cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
-  *kl_out = 4 * bw + 3;
+  *kl_out = 4 * o->bw + 3;
   const double ldab = 3.0 * *kl_out + 1.0;
   *fits = n <= INT32_MAX / 2 && sizeof(double) * ldab * (double)n <= (double)BAND_MAX_BYTES;
   return VMS_OK;
@@ -1144,6 +1286,9 @@ static int band_direct(vms_ctx* ctx, const SysRange& R, double* rel_out) {
   bool fits = false;
   if (int rc = band_shape(ctx, R, &kl, &fits)) return rc;
   if (!fits) return ctx_fail(ctx, VMS_ERR_UNSUPPORTED, "band solve: band too large");
+  const BandOrder* ord = nullptr;
+  if (int rc = band_order(ctx, R, &ord)) return rc;
+  const int32_t* perm = ord->perm;
   const int ku = kl;
   const int64_t ldab = 2 * (int64_t)kl + ku + 1;
   const size_t bytes = sizeof(double) * (size_t)ldab * (size_t)n;
@@ -1162,22 +1307,25 @@ static int band_direct(vms_ctx* ctx, const SysRange& R, double* rel_out) {
   }
   cudaMemsetAsync(AB, 0, bytes, st);
   cudaMemsetAsync(ipiv, 0, sizeof(int) * 2 * n, st);
+  cudaMemsetAsync(d_int, 0, sizeof(int) * 4, st);
   {
     KScope kf(ctx, VMS_K_PRECOND);
     const unsigned wb = (unsigned)((nodes * 32 + 255) / 256);
     if (f32)
-      band_scatter_kernel<float><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
+      band_scatter_kernel<float><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const float*)wk.values, perm, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
     else
-      band_scatter_kernel<double><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
+      band_scatter_kernel<double><<<wb, 256, 0, st>>>(m.rowptr, m.colidx, (const double*)wk.values, perm, R.n0, nodes, AB, ldab, kl, ku, d_int + 3);
     const unsigned gb = (unsigned)std::min<int64_t>((int64_t)kl + ku, 4 * (int64_t)sm_count());
     band_first_pivot_kernel<<<1, BAND_STEP_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, ipiv, jua, d_int);
     for (int j = 0; j < (int)n; ++j)
       band_step_kernel<<<gb, BAND_STEP_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, j, ipiv, jua, d_int);
-    // b = -rhs into w.rb, x = b into w.x, forward and backward substitution
+    // b = -rhs into w.rb (block order) and into w.cx (band order), forward and backward
+    // substitution in w.cx, the solution back into w.x in the block order
     axpby_kernel<double, double, double><<<grid_for(n), 256, 0, st>>>(-1.0, wk.rhs + 4 * R.n0, 0.0, (const double*)nullptr, w.rb, n);
-    cudaMemcpyAsync(w.x, w.rb, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    band_solve_kernel<<<1, BAND_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, ipiv, d_int, w.x);
-    kf.add(4 + (int)n);
+    band_permute_kernel<<<grid_for(n), 256, 0, st>>>(w.rb, perm, nodes, 1.0, w.cx, 1);
+    band_solve_kernel<<<1, BAND_THREADS, 0, st>>>(AB, ldab, (int)n, kl, ku, ipiv, d_int, w.cx);
+    band_permute_kernel<<<grid_for(n), 256, 0, st>>>(w.cx, perm, nodes, 1.0, w.x, 0);
+    kf.add(6 + (int)n);
   }
   cudaMemcpyAsync(h + 1, d_int + 1, sizeof(int) * 3, cudaMemcpyDeviceToHost, st);
   e = cudaStreamSynchronize(st);

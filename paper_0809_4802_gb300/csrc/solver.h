@@ -1,6 +1,8 @@
 // Krylov solve, fine-scale recovery and Newton driver of the condensed system (Sections 4.2, 5, 6).
 #pragma once
 
+#include <vector>
+
 #include "precond.h"
 #include "vms_internal.h"
 
@@ -12,6 +14,15 @@ namespace vms {
 struct SysRange {
   int64_t n0 = 0, n1 = 0, e0 = 0, e1 = 0;
   int64_t nodes() const { return n1 - n0; }
+};
+
+// A bandwidth-reducing node order of one block of the system (reverse Cuthill-McKee), kept for the
+// banded direct solve: perm[a] = position of node n0 + a in the band order (device), bw = the
+// largest |position difference| of two coupled nodes (-1: the block is too large to be ordered).
+struct BandOrder {
+  int64_t n0 = 0, n1 = 0;
+  int32_t* perm = nullptr;
+  int bw = -1;
 };
 
 struct SolverWork {
@@ -31,7 +42,8 @@ struct SolverWork {
   int zf_restart = 0;
   double* xb = nullptr;      // n: refinement iterate before the last FP32 correction
   double* rb = nullptr;      // n: its FP64 residual
-  int* band = nullptr;       // 4 ints: the banded direct solve's width, state and error words
+  int* band = nullptr;       // 4 ints: the banded direct solve's state and error words
+  std::vector<BandOrder> band_orders;  // per block solved directly so far
   Ilu ilu;                   // ILU(0) pattern, factor and sweep work
   bool use_ilu = false;      // preconditioner of the current solve: ILU(0) or block Jacobi
   uint64_t ilu_for = 0;      // assembly the ILU(0) factor was computed for (0: none)

@@ -196,6 +196,37 @@ def test_zero_pivot_falls_back_to_the_pivoted_direct_solve(vms, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_direct_solve_in_a_bandwidth_reducing_order(vms, prec):
+    """An elongated distorted box (12 x 3 x 3 cells, numbered x fastest, so a node couples to nodes
+    66 numbers away): the banded direct fallback orders it by reverse Cuthill-McKee from the far
+    end face (bandwidth about a third of that) and its solution still satisfies the system to
+    rounding level and matches a direct solve."""
+    mesh = inputs.box_mesh(12, 3, 3, hi=(4.0, 1.0, 1.0))
+    rng = np.random.default_rng(17)
+    mesh.xyz += rng.uniform(-0.08, 0.08, mesh.xyz.shape)
+    x0 = np.nonzero(mesh.node_ijk[:, 0] == 0)[0]
+    dofs = np.sort(np.concatenate([4 * x0 + c for c in range(3)]))
+    u = rng.uniform(-0.5, 0.5, (mesh.n_nodes, 4))
+    u.reshape(-1)[dofs] = 0.0
+    beta = rng.uniform(-0.2, 0.2, (mesh.n_elems, 3))
+    ctx = vms.Context(0, prec)
+    ctx.set_preconditioner(vms.PRECOND_ILU0_FALLBACK)
+    ctx.mesh_upload(mesh.xyz, mesh.conn, dofs, np.zeros(dofs.size))
+    ctx.set_params(0.05)
+    ctx.state_upload(u, beta)
+    ctx.assemble()
+    rowptr, colidx, vals, rhs = ctx.csr_host()
+    G = sp.csr_matrix((vals.astype(np.float64), colidx, rowptr))
+    it, rel = ctx.solve(rtol=1e-11, maxit=1, restart=1, update=True)   # one Krylov step, then direct
+    assert it == 1 and rel <= 1e-11
+    du = (ctx.state_download()[0] - u).reshape(-1)
+    assert np.linalg.norm(G @ du + rhs) <= 1e-11 * np.linalg.norm(rhs)
+    du_ref = spla.spsolve(G.tocsc(), -rhs)
+    assert np.abs(du - du_ref).max() <= 1e-8 * np.abs(du_ref).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_ilu0_beats_block_jacobi_on_cavity(vms, prec):
     """12^3 lid-driven cavity at Re 400 from the noisy start: both preconditioners give solutions
     with the requested residual, and ILU(0) needs several times fewer GMRES(50) iterations."""
