@@ -393,15 +393,34 @@ def warmstart_study(vms, ctx, wl, args, dev):
     """Backward-Euler steps from rest: record args.ws_train steps (previous-step start), train the
     network, then run the next args.ws_eval steps twice from the same state: previous-step start
     and learned start; Newton to the same absolute target (1e-8 of the previous-step start's
-    residual) in both."""
+    residual) in both. A failed Newton solve ends that run and is reported."""
     import torch
     from paper_0809_4802_gb300 import transient as tr
+
+    def log(s):
+        print(f"warm-start study: step {s.step} newton {s.newton_iterations} krylov {s.krylov_iterations} "
+              f"{s.seconds:.2f} s", file=sys.stderr, flush=True)
+
+    def summary(st):
+        ok = [s for s in st if s.newton_iterations >= 0]
+        return {"steps": len(ok), "failed_steps": len(st) - len(ok),
+                "newton_iterations": int(sum(s.newton_iterations for s in ok)),
+                "krylov_iterations": int(sum(s.krylov_iterations for s in ok)),
+                "wall_s": float(sum(s.seconds for s in st)),
+                "newton_per_step": [s.newton_iterations for s in st],
+                "start_residual_ratio_mean": (float(np.mean([s.start_residual / s.reference_residual for s in ok]))
+                                              if ok else None)}
+
     ctx.set_graph(False)
     ctx.state_upload(wl.u, wl.beta, wl.u_prev)
     rec = tr.Recorder()
     t0 = time.perf_counter()
-    tr.run_steps(vms, ctx, args.ws_train, rtol=1e-8, record=rec)
+    recorded = tr.run_steps(vms, ctx, args.ws_train, rtol=1e-8, record=rec, log=log)
     t_record = time.perf_counter() - t0
+    out = {"steps_recorded": args.ws_train, "record_wall_s": t_record, "recording": summary(recorded)}
+    if any(s.newton_iterations < 0 for s in recorded):
+        out["note"] = "a Newton solve of the recorded steps failed; no network trained"
+        return out
     u, beta = ctx.state_download()
     up = ctx.state_download_prev()
     torch.cuda.synchronize(dev)
@@ -410,21 +429,15 @@ def warmstart_study(vms, ctx, wl, args, dev):
     loss = ws.fit(rec, epochs=args.ws_epochs, batch=4096, lr=2e-3)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
-    base = tr.run_steps(vms, ctx, args.ws_eval, rtol=1e-8, first_step=args.ws_train)
+    base = tr.run_steps(vms, ctx, args.ws_eval, rtol=1e-8, first_step=args.ws_train, log=log)
     ctx.state_upload(u, beta, up)
-    learned = tr.run_steps(vms, ctx, args.ws_eval, rtol=1e-8, warm=ws, first_step=args.ws_train)
+    learned = tr.run_steps(vms, ctx, args.ws_eval, rtol=1e-8, warm=ws, first_step=args.ws_train, log=log)
     ws.mlp.close()
-
-    def summary(st):
-        return {"newton_iterations": int(sum(s.newton_iterations for s in st)),
-                "krylov_iterations": int(sum(s.krylov_iterations for s in st)),
-                "wall_s": float(sum(s.seconds for s in st)),
-                "start_residual_ratio_mean": float(np.mean([s.start_residual / s.reference_residual for s in st]))}
-    return {"steps_recorded": args.ws_train, "steps_evaluated": args.ws_eval,
-            "record_wall_s": t_record, "train_wall_s": t_train, "train_epochs": args.ws_epochs,
-            "final_loss": loss, "previous_step_start": summary(base), "learned_start": summary(learned),
-            "newton_iterations_saved": summary(base)["newton_iterations"] - summary(learned)["newton_iterations"],
-            "note": "warm start applied to the velocity; Newton to the same absolute target"}
+    out.update({"steps_evaluated": args.ws_eval, "train_wall_s": t_train, "train_epochs": args.ws_epochs,
+                "final_loss": loss, "previous_step_start": summary(base), "learned_start": summary(learned),
+                "newton_iterations_saved": summary(base)["newton_iterations"] - summary(learned)["newton_iterations"],
+                "note": "warm start applied to the velocity; Newton to the same absolute target"})
+    return out
 
 
 def workload_config(name, wl, prec, batch=None):

@@ -85,8 +85,10 @@ class WarmStart:
 
 
 def run_steps(vms, ctx, n_steps: int, rtol: float = 1e-8, warm: WarmStart | None = None,
-              record: Recorder | None = None, maxit: int = 20, first_step: int = 0):
-    """Advance n_steps backward-Euler steps; returns a StepStats per step."""
+              record: Recorder | None = None, maxit: int = 20, first_step: int = 0, log=None):
+    """Advance n_steps backward-Euler steps; returns a StepStats per step. A step whose Newton
+    solve fails ends the run: its StepStats has newton_iterations = -1 and it is the last one.
+    `log`, if given, is called with each step's StepStats."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     n = ctx.n_nodes
@@ -106,11 +108,21 @@ def run_steps(vms, ctx, n_steps: int, rtol: float = 1e-8, warm: WarmStart | None
             ctx.apply_increment(Y, warm.scale_out)
         r_start = ctx.residual()
         ctx.solver_stats(reset=True)
-        its, hist = ctx.newton_solve_to(rtol * r_ref, maxit=maxit)
+        try:
+            its, hist = ctx.newton_solve_to(rtol * r_ref, maxit=maxit)
+        except vms.VmsError:
+            _, kits = ctx.solver_stats(reset=True)
+            torch.cuda.synchronize(dev)
+            out.append(StepStats(first_step + k + 1, -1, kits, r_start, r_ref, time.perf_counter() - t0))
+            if log is not None:
+                log(out[-1])
+            break
         _, kits = ctx.solver_stats(reset=True)
         if record is not None:
             ctx.node_increment(Y)
             record.D.append(Y.clone())
         torch.cuda.synchronize(dev)
         out.append(StepStats(first_step + k + 1, its, kits, r_start, r_ref, time.perf_counter() - t0))
+        if log is not None:
+            log(out[-1])
     return out
