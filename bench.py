@@ -399,7 +399,7 @@ def warmstart_study(vms, ctx, wl, args, dev):
 
     def log(s):
         print(f"warm-start study: step {s.step} newton {s.newton_iterations} krylov {s.krylov_iterations} "
-              f"{s.seconds:.2f} s", file=sys.stderr, flush=True)
+              f"{s.seconds:.2f} s {s.error}", file=sys.stderr, flush=True)
 
     def summary(st):
         ok = [s for s in st if s.newton_iterations >= 0]
@@ -408,6 +408,7 @@ def warmstart_study(vms, ctx, wl, args, dev):
                 "krylov_iterations": int(sum(s.krylov_iterations for s in ok)),
                 "wall_s": float(sum(s.seconds for s in st)),
                 "newton_per_step": [s.newton_iterations for s in st],
+                "errors": [s.error for s in st if s.error],
                 "start_residual_ratio_mean": (float(np.mean([s.start_residual / s.reference_residual for s in ok]))
                                               if ok else None)}
 

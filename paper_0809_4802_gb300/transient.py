@@ -27,6 +27,7 @@ class StepStats:
     start_residual: float     # ||R|| at the starting point of Newton
     reference_residual: float  # ||R|| at the previous-step start
     seconds: float
+    error: str = ""            # the library's error message of a failed Newton solve
 
 
 @dataclass
@@ -110,10 +111,11 @@ def run_steps(vms, ctx, n_steps: int, rtol: float = 1e-8, warm: WarmStart | None
         ctx.solver_stats(reset=True)
         try:
             its, hist = ctx.newton_solve_to(rtol * r_ref, maxit=maxit)
-        except vms.VmsError:
+        except vms.VmsError as err:
             _, kits = ctx.solver_stats(reset=True)
             torch.cuda.synchronize(dev)
-            out.append(StepStats(first_step + k + 1, -1, kits, r_start, r_ref, time.perf_counter() - t0))
+            out.append(StepStats(first_step + k + 1, -1, kits, r_start, r_ref, time.perf_counter() - t0,
+                                 str(err)))
             if log is not None:
                 log(out[-1])
             break
