@@ -73,7 +73,7 @@ extern "C" {
 #define VMS_PRECOND_BLOCK_JACOBI 1  /* inverses of the 4x4 diagonal node blocks */
 #define VMS_PRECOND_ILU0_FALLBACK 2 /* ILU(0); a solve that does not converge (or meets a zero
                                        pivot) is repeated by a banded direct LU solve, or where
-                                       the band would exceed 4 GiB by block Jacobi and
+                                       the band would exceed 48 GiB by block Jacobi and
                                        GMRES(480) */
 
 /* ---- scatter modes (vms_params.scatter_mode) ----------------------------------------------- */
@@ -282,8 +282,10 @@ int vms_set_graph(vms_ctx* ctx, int enable);
 /* Choose the right preconditioner of vms_solve / vms_solve_instance / vms_newton_*:
  * VMS_PRECOND_ILU0 (default), VMS_PRECOND_BLOCK_JACOBI, or VMS_PRECOND_ILU0_FALLBACK (ILU(0), and
  * for a solve that does not converge, a direct solve of the instance by LU with partial pivoting
- * in band storage, FP64, on the device; the band's half-width is 4 (largest node-number distance
- * of a row) + 3, and where the band would need more than 4 GiB a second solve from zero with
+ * in band storage, FP64, on the device; the nodes are taken in the order of smallest bandwidth
+ * among their own order and two reverse Cuthill-McKee orders, the band's half-width is 4 (that
+ * order's largest distance of two coupled nodes) + 3, and where the band would need more than
+ * 48 GiB a second solve from zero with
  * block Jacobi and the longest cycle instead. On coarse high-Reynolds systems the ILU(0) pivots
  * lose all size. Where the direct solve fits, the ILU(0) attempt also ends before maxit: after a
  * cycle whose rate would not reach rtol by maxit, or once it has run as long as the direct solve

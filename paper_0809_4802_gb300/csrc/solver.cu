@@ -1100,7 +1100,8 @@ __global__ void __launch_bounds__(BAND_THREADS) band_solve_kernel(const double* 
   }
 }
 
-constexpr size_t BAND_MAX_BYTES = (size_t)4 << 30;
+// the largest band the direct solve allocates (a sixth of a GB300's memory)
+constexpr size_t BAND_MAX_BYTES = (size_t)48 << 30;
 
 // Blocks above this many nodes are not ordered for the direct solve (their band would not fit).
 constexpr int64_t BAND_ORDER_MAX_NODES = 262144;
