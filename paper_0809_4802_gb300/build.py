@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvms_gb300.so")
-SOURCES = ["api.cu", "residual.cu", "tangent.cu", "misc.cu", "solver.cu", "pattern.cpp", "ts_plan.cpp", "noalloc.cu", "precond.cu", "mlp.cu", "tet.cu"]
+SOURCES = ["api.cu", "residual.cu", "tangent.cu", "misc.cu", "solver.cu", "pattern.cpp", "ts_plan.cpp", "band_order.cpp", "noalloc.cu", "precond.cu", "mlp.cu", "tet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1106,14 +1106,8 @@ constexpr size_t BAND_MAX_BYTES = (size_t)48 << 30;
 // Blocks above this many nodes are not ordered for the direct solve (their band would not fit).
 constexpr int64_t BAND_ORDER_MAX_NODES = 262144;
 
-// The block's band order: the one of smallest bandwidth among the block's own node order and two
-// reverse Cuthill-McKee orders (George and Liu): breadth-first numbering with the neighbours of a
-// node queued in order of increasing degree, reversed, started from a pseudo-peripheral node
-// (repeated searches from a node of least degree in the last level while the number of levels
-// grows) or from the whole last level of its level structure. On a lattice numbered line by line
-// the block's own order is the best of the three; on an elongated box the start from a whole end
-// face is (the corner's levels are shells of up to three faces). Computed on the host from the
-// block's node pattern once per mesh.
+// The block's band order (band_order_host, band_order.cpp) from the block's node pattern, computed
+// on the host once per mesh.
 static int band_order(vms_ctx* ctx, const SysRange& R, const BandOrder** out) {
   SolverWork& w = ctx_solver(ctx);
   for (const BandOrder& o : w.band_orders)
@@ -1146,98 +1140,8 @@ static int band_order(vms_ctx* ctx, const SysRange& R, const BandOrder** out) {
       }
     }
     start[nodes] = (int32_t)adj.size();
-    auto deg = [&](int64_t a) { return start[a + 1] - start[a]; };
-    auto bandwidth = [&](const std::vector<int32_t>& perm) {
-      int bw = 0;
-      for (int64_t a = 0; a < nodes; ++a)
-        for (int32_t t = start[a]; t < start[a + 1]; ++t) bw = std::max(bw, std::abs(perm[a] - perm[adj[t]]));
-      return bw;
-    };
-    // breadth-first levels from a set of nodes: the depth, and the nodes of the last level
-    std::vector<int32_t> level(nodes), queue;
-    auto levels = [&](const std::vector<int32_t>& src, std::vector<int32_t>& lastv) {
-      std::fill(level.begin(), level.end(), -1);
-      queue.assign(src.begin(), src.end());
-      for (int32_t a : src) level[a] = 0;
-      int depth = 0;
-      for (size_t h = 0; h < queue.size(); ++h) {
-        const int32_t a = queue[h];
-        depth = level[a];
-        for (int32_t t = start[a]; t < start[a + 1]; ++t)
-          if (level[adj[t]] < 0) {
-            level[adj[t]] = level[a] + 1;
-            queue.push_back(adj[t]);
-          }
-      }
-      lastv.clear();
-      for (int32_t a : queue)
-        if (level[a] == depth) lastv.push_back(a);
-      return depth;
-    };
-    // reverse Cuthill-McKee numbering from a set of start nodes (further connected parts from a
-    // node of least degree each); returns perm
-    std::vector<char> placed(nodes);
-    std::vector<int32_t> order, nb;
-    auto rcm = [&](std::vector<int32_t> src) {
-      std::fill(placed.begin(), placed.end(), 0);
-      order.clear();
-      for (int64_t next = 0;;) {
-        std::stable_sort(src.begin(), src.end(), [&](int32_t x, int32_t y) { return deg(x) < deg(y); });
-        const size_t h0 = order.size();
-        for (int32_t a : src) {
-          placed[a] = 1;
-          order.push_back(a);
-        }
-        for (size_t h = h0; h < order.size(); ++h) {
-          const int32_t a = order[h];
-          nb.clear();
-          for (int32_t t = start[a]; t < start[a + 1]; ++t)
-            if (!placed[adj[t]]) {
-              placed[adj[t]] = 1;
-              nb.push_back(adj[t]);
-            }
-          std::stable_sort(nb.begin(), nb.end(), [&](int32_t x, int32_t y) { return deg(x) < deg(y); });
-          for (int32_t x : nb) order.push_back(x);
-        }
-        if ((int64_t)order.size() == nodes) break;
-        while (placed[next]) ++next;
-        int32_t r = (int32_t)next;
-        for (int64_t a = next; a < nodes; ++a)
-          if (!placed[a] && deg(a) < deg(r)) r = (int32_t)a;
-        src.assign(1, r);
-      }
-      std::vector<int32_t> perm(nodes);
-      for (int64_t k = 0; k < nodes; ++k) perm[order[k]] = (int32_t)(nodes - 1 - k);
-      return perm;
-    };
     std::vector<int32_t> best(nodes);
-    for (int64_t a = 0; a < nodes; ++a) best[a] = (int32_t)a;
-    int bw = bandwidth(best);
-    // a pseudo-peripheral node r of the part holding node 0, and the last level of its levels
-    int32_t r = 0;
-    std::vector<int32_t> last, lc;
-    levels(std::vector<int32_t>(1, 0), last);
-    for (int32_t a : queue)
-      if (deg(a) < deg(r)) r = a;
-    int depth = levels(std::vector<int32_t>(1, r), last);
-    for (int it = 0; it < 8; ++it) {
-      int32_t c = last[0];
-      for (int32_t a : last)
-        if (deg(a) < deg(c)) c = a;
-      const int dc = levels(std::vector<int32_t>(1, c), lc);
-      if (dc <= depth) break;
-      r = c;
-      depth = dc;
-      last.swap(lc);
-    }
-    for (int variant = 0; variant < 2; ++variant) {
-      std::vector<int32_t> perm = rcm(variant == 0 ? std::vector<int32_t>(1, r) : last);
-      const int b = bandwidth(perm);
-      if (b < bw) {
-        bw = b;
-        best.swap(perm);
-      }
-    }
+    const int bw = band_order_host(nodes, start.data(), adj.data(), best.data());
     e = cudaMalloc(&o.perm, sizeof(int32_t) * nodes);
     if (e == cudaSuccess) e = cudaMemcpy(o.perm, best.data(), sizeof(int32_t) * nodes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

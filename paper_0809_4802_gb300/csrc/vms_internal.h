@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/vms.h"
+#include "band_order.h"
 
 struct vms_ctx;
 
