@@ -716,7 +716,7 @@ static int ensure_solver(vms_ctx* ctx, int restart) {
   return VMS_OK;
 }
 
-static int band_shape(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits);
+static int band_estimate(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits);
 
 // Solve S du = -rhs into w.x (FP64). Mixed: FP32 GMRES inside FP64 iterative refinement.
 static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit, int restart,
@@ -775,7 +775,7 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
     // band a launch (about 10 us) plus the column's update at the rate measured on a GB300
     // (3.2 ns per thousand entries).
     int kl = 0;
-    if (int rc = band_shape(ctx, R, &kl, &G.stall_exit)) return rc;
+    if (int rc = band_estimate(ctx, R, &kl, &G.stall_exit)) return rc;
     if (G.stall_exit) {
       const double est = (double)n * (1.0e-5 + 3.2e-12 * (double)kl * (2.0 * kl));
       G.has_deadline = true;
@@ -931,6 +931,20 @@ static int linear_solve(vms_ctx* ctx, const SysRange& R, double rtol, int maxit,
 // the band, multipliers, rank-1 update of the band's trailing block); the solve applies the
 // interchanges and multipliers forward and U backward. FP64 throughout.
 // ---------------------------------------------------------------------------------------------
+
+// the largest |column node - row node| of the block's rows: the bandwidth of its own node order
+__global__ void band_width_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                  int64_t n0, int64_t nodes, int* __restrict__ bw) {
+  const int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (nd >= nodes) return;
+  const int64_t g = n0 + nd;
+  int w = 0;
+  for (int32_t t = rowptr[4 * g]; t < rowptr[4 * g + 1]; t += 4) {
+    const int64_t d = (int64_t)(colidx[t] >> 2) - g;
+    w = (int)std::max<int64_t>(w, d < 0 ? -d : d);
+  }
+  atomicMax(bw, w);
+}
 
 // the block's rows into the band in the band order perm (one warp per node row, one lane per 4x4
 // block): entry (4 perm[a] + r, 4 perm[c] + m)
@@ -1168,6 +1182,37 @@ static int band_shape(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits) 
     return VMS_OK;
   }
   *kl_out = 4 * o->bw + 3;
+  const double ldab = 3.0 * *kl_out + 1.0;
+  *fits = n <= INT32_MAX / 2 && sizeof(double) * ldab * (double)n <= (double)BAND_MAX_BYTES;
+  return VMS_OK;
+}
+
+// kl and whether the band fits, for the deadline of a Krylov attempt that a direct solve would
+// follow: from the block's band order where it has one, else from its own order (a device
+// reduction; the band order, a host computation, is made only when a direct solve runs).
+static int band_estimate(vms_ctx* ctx, const SysRange& R, int* kl_out, bool* fits) {
+  SolverWork& w = ctx_solver(ctx);
+  for (const BandOrder& o : w.band_orders)
+    if (o.n0 == R.n0 && o.n1 == R.n1) return band_shape(ctx, R, kl_out, fits);
+  const Mesh& m = ctx_mesh(ctx);
+  cudaStream_t st = ctx_stream(ctx);
+  const int64_t nodes = R.nodes(), n = 4 * nodes;
+  if (nodes == 0) {
+    *kl_out = 3;
+    *fits = true;
+    return VMS_OK;
+  }
+  int bw = 0;
+  cudaMemsetAsync(w.band, 0, sizeof(int), st);
+  {
+    KScope k(ctx, VMS_K_PRECOND);
+    band_width_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(m.rowptr, m.colidx, R.n0, nodes, w.band);
+    k.add(1);
+  }
+  cudaMemcpyAsync(&bw, w.band, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ctx_fail(ctx, VMS_ERR_CUDA, cudaGetErrorString(e));
+  *kl_out = 4 * bw + 3;
   const double ldab = 3.0 * *kl_out + 1.0;
   *fits = n <= INT32_MAX / 2 && sizeof(double) * ldab * (double)n <= (double)BAND_MAX_BYTES;
   return VMS_OK;
