@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <type_traits>
 #include <vector>
 
@@ -1388,7 +1389,9 @@ static int solve_impl(vms_ctx* ctx, const SysRange& R, int64_t instance, double 
     int rcb = band_direct(ctx, R, &r2);
     if (rcb == VMS_OK) {
       r = r2;
-      rc = r2 <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, "banded direct solve above rtol");
+      char msg[96];
+      std::snprintf(msg, sizeof msg, "banded direct solve above rtol (relative residual %.3e)", r2);
+      rc = r2 <= rtol ? VMS_OK : ctx_fail(ctx, VMS_ERR_KRYLOV_MAXIT, msg);
     } else if (rcb == VMS_ERR_UNSUPPORTED || rcb == VMS_ERR_OUT_OF_MEMORY) {
       int it2 = 0;
       rc = linear_solve(ctx, R, rtol, maxit, MAX_RESTART, MAX_RESTART, &it2, &r2, true);
