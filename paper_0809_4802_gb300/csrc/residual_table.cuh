@@ -21,10 +21,7 @@ struct GlobalTable {
   __device__ __forceinline__ double xi(int q) const { return __ldg(&t[q].xi); }
   __device__ __forceinline__ double eta(int q) const { return __ldg(&t[q].eta); }
   __device__ __forceinline__ double zeta(int q) const { return __ldg(&t[q].zeta); }
-  __device__ __forceinline__ double xe(int q) const { return __ldg(&t[q].xe); }
-  __device__ __forceinline__ double xz(int q) const { return __ldg(&t[q].xz); }
   __device__ __forceinline__ double ez(int q) const { return __ldg(&t[q].ez); }
-  __device__ __forceinline__ double xez(int q) const { return __ldg(&t[q].xez); }
   __device__ __forceinline__ double b(int q) const { return __ldg(&t[q].b); }
   __device__ __forceinline__ double db(int q, int al) const {
     return al == 0 ? __ldg(&t[q].db0) : (al == 1 ? __ldg(&t[q].db1) : __ldg(&t[q].db2));

@@ -375,8 +375,7 @@ __global__ void __launch_bounds__(256) vcomb_kernel(const VT* __restrict__ V, in
 
 // y = x / sqrt(*nrm2) (device-side normalisation, no host round trip)
 template <typename VT>
-__global__ void scale_kernel(const VT* __restrict__ x, const double* __restrict__ nrm2,
-                             VT* __restrict__ y, int64_t n) {
+__global__ void scale_kernel(const VT* x, const double* __restrict__ nrm2, VT* y, int64_t n) {  // y may be x
   const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
